@@ -1,0 +1,265 @@
+"""ctypes front end of the FP64 CPU oracle (``nrrs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's CPU
+baseline leg load it.  The product package never imports this module, and this
+module never imports the product package.
+
+Parity unpinned: the GGX lobe (``or_sample_ggx``) has no formula in the paper; it is
+checked only against closed forms (energy bound, reciprocity of the weight) in tests/.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nrrs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MODE_NONE, MODE_PLAIN_RR, MODE_HEUR_NORM, MODE_NET, MODE_NET_MIX = range(5)
+GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
+MAX_DEPTH = 64
+NO_HIT = 0xFFFFFFFF
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
+               "-ffp-contract=off", _SRC, "-o", _LIB, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class Material(C.Structure):
+    _fields_ = [("type", C.c_int32), ("albedo", C.c_float * 3), ("Le", C.c_float * 3),
+                ("roughness", C.c_float), ("F0", C.c_float), ("two_sided", C.c_int32)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float)]
+
+
+class SceneC(C.Structure):
+    _fields_ = [("tri", C.c_void_p), ("mat_id", C.c_void_p), ("mats", C.c_void_p),
+                ("n_tri", C.c_int32), ("n_mat", C.c_int32), ("cam", C.c_void_p)]
+
+
+class RenderArgs(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
+                ("max_depth", C.c_int32), ("mode", C.c_int32), ("seed_lo", C.c_uint32),
+                ("seed_hi", C.c_uint32), ("frame", C.c_uint32), ("cap", C.c_int64),
+                ("f_rate", C.c_double), ("alpha0", C.c_double), ("q_max", C.c_double),
+                ("eps_rel", C.c_double), ("boxcox_lambda", C.c_double), ("gate", C.c_uint64),
+                ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
+                ("n_pixels", C.c_int64)]
+
+
+class RenderStats(C.Structure):
+    _fields_ = [("live", C.c_int64 * (MAX_DEPTH + 1)), ("sum_q", C.c_double * (MAX_DEPTH + 1)),
+                ("F", C.c_float * (MAX_DEPTH + 1)), ("alpha", C.c_double * (MAX_DEPTH + 1)),
+                ("dropped", C.c_int64 * (MAX_DEPTH + 1)),
+                ("requested", C.c_int64 * (MAX_DEPTH + 1)),
+                ("segments", C.c_int64), ("nonfinite", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.or_philox4x32_10.argtypes = [P, P, P]
+        _lib.or_intersect.argtypes = [P, P, P, P]
+        _lib.or_intersect.restype = C.c_int32
+        _lib.or_camera_ray.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_double, C.c_double, P, P]
+        _lib.or_sample_lambert.argtypes = [P, C.c_double, C.c_double, P]
+        _lib.or_sample_ggx.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, P, P]
+        _lib.or_sample_ggx.restype = C.c_int
+        _lib.or_softplus_mod.argtypes = [C.c_double]
+        _lib.or_softplus_mod.restype = C.c_double
+        _lib.or_softplus_mod_grad.argtypes = [C.c_double]
+        _lib.or_softplus_mod_grad.restype = C.c_double
+        _lib.or_mlp_forward.argtypes = [P, P, P, P, P]
+        _lib.or_mlp_forward.restype = C.c_double
+        _lib.or_mlp_backward.argtypes = [P, P, C.c_double, P]
+        _lib.or_mlp_forward_batch.argtypes = [P, P, C.c_int64, P]
+        _lib.or_boxcox.argtypes = [C.c_double, C.c_double]
+        _lib.or_boxcox.restype = C.c_double
+        _lib.or_normalize.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_double, P]
+        _lib.or_normalize.restype = C.c_double
+        _lib.or_split.argtypes = [P, C.c_int64, C.c_float, P, P, P, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_uint32, C.c_int64, P, P, P, P, P]
+        _lib.or_split.restype = C.c_int64
+        _lib.or_bernstein_exponent.argtypes = [C.c_double]
+        _lib.or_bernstein_exponent.restype = C.c_double
+        _lib.or_render.argtypes = [P, P, P, P, P, P]
+        _lib.or_render.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+class _SceneHolder:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, scene):
+        self.tri = np.ascontiguousarray(scene.tri, dtype=np.float32)
+        self.mat_id = np.ascontiguousarray(scene.mat_id, dtype=np.int32)
+        self.mats = np.ascontiguousarray(scene.mats)
+        self.cam = np.ascontiguousarray(scene.cam)
+        self.c = SceneC(_p(self.tri), _p(self.mat_id), _p(self.mats), self.tri.shape[0],
+                        len(self.mats), _p(self.cam))
+
+
+def intersect(scene, o, d):
+    h = _SceneHolder(scene)
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    t = np.zeros(1)
+    tri = lib().or_intersect(C.byref(h.c), _p(o), _p(d), _p(t))
+    return int(tri), float(t[0])
+
+
+def camera_ray(scene, W, H, px, py, jx, jy):
+    cam = np.ascontiguousarray(scene.cam)
+    o = np.zeros(3)
+    d = np.zeros(3)
+    lib().or_camera_ray(_p(cam), W, H, px, py, jx, jy, _p(o), _p(d))
+    return o, d
+
+
+def sample_lambert(n, u1, u2):
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wi = np.zeros(3)
+    lib().or_sample_lambert(_p(n), u1, u2, _p(wi))
+    return wi
+
+
+def sample_ggx(n, wo, albedo, rough, F0, ulobe, u1, u2):
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    alb = np.ascontiguousarray(albedo, dtype=np.float64)
+    wi = np.zeros(3)
+    w = np.zeros(3)
+    ok = lib().or_sample_ggx(_p(n), _p(wo), _p(alb), rough, F0, ulobe, u1, u2, _p(wi), _p(w))
+    return ok, wi, w
+
+
+def softplus_mod(x):
+    return lib().or_softplus_mod(float(x))
+
+
+def softplus_mod_grad(x):
+    return lib().or_softplus_mod_grad(float(x))
+
+
+def boxcox(t, lam=0.5):
+    return lib().or_boxcox(float(t), float(lam))
+
+
+def mlp_forward(params, x):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    pre = np.zeros(96)
+    hid = np.zeros(96)
+    z = np.zeros(1)
+    q = lib().or_mlp_forward(_p(P), _p(x), _p(pre), _p(hid), _p(z))
+    return q, float(z[0]), pre, hid
+
+
+def mlp_forward_batch(params, X):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    q = np.zeros(X.shape[0])
+    lib().or_mlp_forward_batch(_p(P), _p(X), X.shape[0], _p(q))
+    return q
+
+
+def mlp_backward(params, x, dq):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    G = np.zeros_like(P)
+    lib().or_mlp_backward(_p(P), _p(x), float(dq), _p(G))
+    return G
+
+
+def normalize(q, budget, f_rate=0.85, alpha=1.0):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    s = np.zeros(1)
+    F = lib().or_normalize(_p(q), q.shape[0], float(budget), float(f_rate), float(alpha), _p(s))
+    return F, float(s[0])
+
+
+def split(q_orig, F32, pixel, sample, lineage, depth, seed=(1, 0), frame=0, cap=None):
+    """Eq. rrs_factor over one queue; returns X, prefix, child parent, child lineage, S, dropped."""
+    q = np.ascontiguousarray(q_orig, dtype=np.float32)
+    n = q.shape[0]
+    pixel = np.ascontiguousarray(pixel, dtype=np.uint32)
+    sample = np.ascontiguousarray(sample, dtype=np.uint32)
+    lineage = np.ascontiguousarray(lineage, dtype=np.uint32)
+    cap = int(cap if cap is not None else 2 * n + 16)
+    X = np.zeros(n, dtype=np.uint32)
+    prefix = np.zeros(n, dtype=np.int64)
+    cp = np.zeros(max(cap, 1), dtype=np.uint32)
+    cl = np.zeros(max(cap, 1), dtype=np.uint32)
+    dropped = np.zeros(1, dtype=np.int64)
+    S = lib().or_split(_p(q), n, C.c_float(F32), _p(pixel), _p(sample), _p(lineage), depth,
+                       seed[0], seed[1], frame, cap, _p(X), _p(prefix), _p(cp), _p(cl),
+                       _p(dropped))
+    m = min(S, cap)
+    return X, prefix, cp[:m], cl[:m], int(S), int(dropped[0])
+
+
+def bernstein_exponent(f_rate):
+    return lib().or_bernstein_exponent(float(f_rate))
+
+
+def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
+           f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
+           params=None, pixel_ref=None, pixels=None, trace=False):
+    """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None)."""
+    h = _SceneHolder(scene)
+    P = np.ascontiguousarray(params, dtype=np.float64) if params is not None else None
+    ref = np.ascontiguousarray(pixel_ref, dtype=np.float64) if pixel_ref is not None else None
+    pix = np.ascontiguousarray(pixels, dtype=np.int32) if pixels is not None else None
+    args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
+                      alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
+                      0 if pix is None else pix.shape[0])
+    out = np.zeros((height, width, 3))
+    st = RenderStats()
+    capv = cap if cap > 0 else 2 * width * height * spp
+    tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None
+    tc = np.zeros(max_depth, dtype=np.int64) if trace else None
+    rc = lib().or_render(C.byref(h.c), C.byref(args), _p(out), C.byref(st), _p(tr), _p(tc))
+    if rc != 0:
+        raise RuntimeError(f"oracle render failed with code {rc}")
+    D = max_depth
+    stats = {
+        "live": np.array(st.live[1:D + 1]), "sum_q": np.array(st.sum_q[1:D + 1]),
+        "F": np.array(st.F[1:D + 1], dtype=np.float32), "alpha": np.array(st.alpha[1:D + 1]),
+        "dropped": np.array(st.dropped[1:D + 1]), "requested": np.array(st.requested[1:D + 1]),
+        "segments": int(st.segments), "nonfinite": int(st.nonfinite),
+    }
+    trace_out = None
+    if trace:
+        trace_out = [tr[d, :tc[d]] for d in range(D)]
+    return out, stats, trace_out
