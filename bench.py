@@ -1,0 +1,374 @@
+"""Benchmark of the NRRS bounce loop on B300.
+
+Step = one frame of the whole hot path through the C ABI (nrrs_render): camera rays,
+then for every depth the extension (BVH traversal, emission deposit, RRSNet FP32
+factors), normalization, split counts + accumulation, scan and scatter (children and
+BSDF sampling), and the frame estimate.  Workload: the occluded room (2,018 triangles),
+256 x 256 px, 16 spp, max depth 16, queue capacity 2 x pixels x spp, NET factors.
+
+`value` is path segments per second (rays traced, summed over depths and ranks) with
+the scene, weights and queues resident on the device; `e2e` is the same metric through
+the public API with the per-frame weights copied from pinned host memory and the frame
+read back every step.  `--impl reference` times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "efficiency 1/(relMSE·s) vs plain RR, same B300; path segments/s; RRSNet TFLOP/s"
+UNIT = "path segments/s"
+W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
+WORKLOAD = "occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P"
+# algorithmic bytes per unit of each stage ("Kernels and rooflines")
+BYTES_PER_RAY_EXTEND = 48 + 8 + 4 + 16          # path state in; hit, q, deposit out
+BYTES_PER_SLOT_COUNT = 16 + 4 + 48              # deposit, q, path state (Philox keys)
+BYTES_PER_PARENT_SCATTER = 48 + 8 + 4           # path state, hit, q
+BYTES_PER_CHILD_SCATTER = 48                    # child path state
+RRSNET_FLOP_PER_PATH = 2 * (16 * 32 + 32 * 32 + 32 * 32 + 32)
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                          "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profiles(kernel_tag):
+    """DRAM bytes per launch recorded by ncu for `kernel_tag`, if the recorded source
+    hash still matches the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2510_07868_b300", "csrc", "wavefront.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(
+            os.path.join(ROOT, "profiles")) else []:
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(ROOT, "profiles", fn)):
+            m = re.match(r"traffic\s+(\S+)\s+source_sha=(\w+)\s+bytes_per_launch=([\d.]+)", line)
+            if m and m.group(1) == kernel_tag and m.group(2) == sha:
+                return float(m.group(3))
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample(seconds_target=15.0, mode=None):
+    """Times the FP64 oracle on a reduced image of the same scene, spp, depth and mode;
+    returns (segments/s, cores, sample description, wall seconds)."""
+    import oracle
+    from paper_2510_07868_b300 import inputs as I
+
+    scene = I.occluded_room(1)
+    params = I.rrsnet_init_params(1).astype(np.float64)
+    mode = oracle.MODE_NET if mode is None else mode
+    side = 8
+    t0 = time.perf_counter()
+    _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
+    dt = time.perf_counter() - t0
+    # grow the image until one sample takes about `seconds_target`
+    scale = max(1.0, seconds_target / max(dt, 1e-3))
+    side = int(min(W_IMG, max(8, side * np.sqrt(scale))))
+    t0 = time.perf_counter()
+    _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
+    dt = time.perf_counter() - t0
+    cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+    desc = (f"occluded_room {side}x{side} px (of 256x256), 16 spp, depth 16, NET factors, "
+            f"cap 2*P; {st['segments']} segments in {dt:.2f} s")
+    return st["segments"] / dt, cores, desc, dt, side
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle
+    from paper_2510_07868_b300 import inputs as I
+
+    oracle.build()
+    scene = I.occluded_room(1)
+    params = I.rrsnet_init_params(1).astype(np.float64)
+    _, _, _, _, side = oracle_sample(seconds_target=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+    for k in range(args.warmup):
+        oracle.render(scene, side, side, SPP, DEPTH, oracle.MODE_NET, params=params, frame=k)
+    segs = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, oracle.MODE_NET, params=params,
+                                 frame=args.warmup + k)
+        segs += st["segments"]
+    dt = time.perf_counter() - t0
+    value = segs / dt
+    cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+    sample = f"occluded_room {side}x{side} px per step (of 256x256), 16 spp, depth 16, NET"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2510_07868_b300 import inputs as I
+    from paper_2510_07868_b300 import nrrs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    scene = I.occluded_room(1)
+    params = I.rrsnet_init_params(1)
+    sc = nrrs.Scene(scene, device=local_rank)
+    sc.set_params(params)
+    out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    mode = nrrs.RRS_NET
+    seed_hi = rank  # independent replicas: different Philox streams per rank
+
+    def render(frame, profile=0):
+        return nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
+                                nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi,
+                                                         profile=profile), out, stream, True)
+
+    for k in range(args.warmup):
+        render(k)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    segs = 0
+    launches = 0
+    stage_ms = np.zeros(nrrs.STAGES)
+    stage_n = np.zeros(nrrs.STAGES, dtype=np.int64)
+    live_total = 0
+    net_evals = 0
+    children = 0
+    ev0.record(stream)
+    for k in range(args.steps):
+        st = render(args.warmup + k, profile=1)
+        segs += st["segments"]
+        launches += st["kernel_launches"]
+        stage_ms += st["stage_ms"]
+        stage_n += st["stage_launches"]
+        live_total += int(st["live"].sum())
+        net_evals += st["net_evals"]
+        children += int(st["live"][1:].sum())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+
+    # end to end through the public API: weights from pinned host memory in, frame out
+    pinned_params = torch.from_numpy(params).pin_memory()
+    pinned_out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32).pin_memory()
+    e2e_segs = 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        nrrs.nrrs_set_rrsnet_params(sc.handle, pinned_params.numpy(), stream)
+        st = render(10_000 + k)
+        e2e_segs += st["segments"]
+        pinned_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # standalone RRSNet throughput on a live-queue-sized batch
+    n_q = 1 << 21
+    feats = torch.from_numpy(I.random_features(n_q, seed=3)).to(dev)
+    qout = torch.empty(n_q, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sc.query(feats, out=qout)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        sc.query(feats, out=qout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    q_ms = e0.elapsed_time(e1) / 10
+
+    if dist:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+        c = torch.tensor([segs, e2e_segs], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        segs, e2e_segs = int(c[0]), int(c[1])
+    if rank != 0:
+        return
+    hbm, bf16, peak_kind = measured_peaks()
+    value = segs / (ms / 1000.0)
+
+    # roofline of the dominant stage
+    names = nrrs.STAGE_NAMES
+    dom = int(np.argmax(stage_ms))
+    alg_bytes = {
+        "extend": BYTES_PER_RAY_EXTEND * live_total,
+        "split_count": BYTES_PER_SLOT_COUNT * live_total,
+        "split_scatter": BYTES_PER_PARENT_SCATTER * (live_total - children // 1) +
+        BYTES_PER_CHILD_SCATTER * children,
+    }
+    bytes_dom = alg_bytes.get(names[dom])
+    per_launch_ms = stage_ms[dom] / max(1, stage_n[dom])
+    achieved = (bytes_dom / (stage_ms[dom] / 1000.0) / 1e9) if bytes_dom else None
+    traffic = traffic_from_profiles(names[dom])
+    roofline = {
+        "kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+        else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
+        "launches": int(stage_n[dom]),
+        "stage_share": {n: float(stage_ms[i] / stage_ms.sum()) for i, n in enumerate(names)},
+    }
+    fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
+    rrsnet = {
+        "tflops_standalone_fp32": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12,
+        "fp32_simt_peak_tflops": fp32_peak,
+        "frac_of_fp32_peak": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12 / fp32_peak,
+        "tflops_in_extend": RRSNET_FLOP_PER_PATH * net_evals / (stage_ms[1] / 1000) / 1e12,
+        "batch": n_q,
+    }
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, _, _ = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
+                   "parallelism": f"replicas{world}",
+                   "l2": "no flush: each step rewrites ~0.26 GB of path queues (> 126 MB L2)"},
+        "e2e": {"value": e2e_segs / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(params.nbytes),
+                "d2h_bytes_per_step": int(W_IMG * H_IMG * 3 * 4)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "rrsnet": rrsnet,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    sc.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * nrrs.h -- C ABI of the B300 (sm_103a) implementation of one bounce of wavefront
+ * path tracing with normalized Russian roulette and splitting (RRS) and RRSNet,
+ * after "NRRS: Neural Russian Roulette and Splitting" (arXiv 2510.07868).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an nrrs_status; nothing throws across the ABI.
+ *     nrrs_last_error() returns a short text for the calling thread's last failure.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller (for example torch
+ *     tensors); they must be contiguous, of the stated element type, and stay valid
+ *     until the enqueued work finishes.  Pointers without the prefix are HOST pointers
+ *     owned by the caller and are only read (or written) during the call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device work is
+ *     enqueued on it; a call returns before the work completes unless stated.
+ *   - Device-side failures (queue overflow drops, non-finite factors, timeouts) are
+ *     reported through status bits in the stats structs; kernels never trap.
+ *   - A scene and the buffers it owns belong to the device passed to
+ *     nrrs_create_scene; calls on a scene make that device current.
+ */
+#ifndef NRRS_H
+#define NRRS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NRRS_API __attribute__((visibility("default")))
+#else
+#define NRRS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nrrs_status {
+    NRRS_OK = 0,
+    NRRS_ERR_INVALID_ARG = 1,      /* a pointer, size or enum is out of range */
+    NRRS_ERR_CUDA = 2,             /* a CUDA runtime call failed (see nrrs_last_error) */
+    NRRS_ERR_OOM = 3,              /* device allocation failed */
+    NRRS_ERR_TIMEOUT = 4,          /* a bounded device wait gave up */
+    NRRS_ERR_NONFINITE = 5,        /* RRSNet produced NaN/Inf factors (paths terminated) */
+    NRRS_ERR_OVERFLOW_DROPPED = 6, /* children beyond the queue capacity were dropped */
+    NRRS_ERR_UNSUPPORTED = 7       /* valid request this build does not implement */
+} nrrs_status;
+
+/* Device status bits reported in nrrs_render_stats.status_bits. */
+#define NRRS_STATUS_OVERFLOW_DROPPED 0x1u
+#define NRRS_STATUS_NONFINITE 0x2u
+#define NRRS_STATUS_TIMEOUT 0x4u
+
+/* How the RRS factor q of a path vertex is chosen (Sec. 2 "Unified RRS Framework",
+ * Sec. 3.1 normalization, Sec. 3.3 Mix-Depth). */
+typedef enum nrrs_rrs_mode {
+    NRRS_RRS_NONE = 0,      /* q = 1 and no normalization: the plain path tracer */
+    NRRS_RRS_PLAIN_RR = 1,  /* q = min(1, lum(t)): throughput roulette, no normalization */
+    NRRS_RRS_HEUR_NORM = 2, /* q = min(lum(t) / max(I_px, eps_I), q_max), normalized */
+    NRRS_RRS_NET = 3,       /* q = RRSNet(features), normalized */
+    NRRS_RRS_NET_MIX = 4    /* per-depth choice among NET / HEUR / FIXED, normalized */
+} nrrs_rrs_mode;
+
+/* Mix-Depth methods, 2 bits per depth in nrrs_render_opts.gate (depth d uses bits
+ * 2(d-1)..2(d-1)+1).  FIXED is fixed RR = 1 (q = 1). */
+#define NRRS_GATE_NET 0u
+#define NRRS_GATE_HEUR 1u
+#define NRRS_GATE_FIXED 2u
+
+#define NRRS_MAX_DEPTH 32
+#define NRRS_N_FEATURES 16
+#define NRRS_HIDDEN 32
+#define NRRS_RRSNET_PARAMS 2592 /* 32x16 + 32x32 + 32x32 + 1x32, no biases */
+
+/* Material record, 40 bytes.  type 0 = Lambertian (albedo), 1 = GGX + Lambert
+ * "plastic" mixture (roughness is the GGX alpha, F0 the Schlick reflectance at normal
+ * incidence).  Emission Le leaves the front face (the side of e1 x e2 with
+ * e1 = v1 - v0, e2 = v2 - v0) or both faces when two_sided != 0.  Scattering is
+ * always two-sided.  A material whose albedo is 0 in every channel ends the path. */
+typedef struct nrrs_material {
+    int32_t type;
+    float albedo[3];
+    float Le[3];
+    float roughness;
+    float F0;
+    int32_t two_sided;
+} nrrs_material;
+
+/* Pinhole camera, 40 bytes.  right = normalize(up x look), up' = look x right; pixel
+ * (x, y) with y = 0 at the top maps to look + sx right + sy up' with
+ * sx = (2 (x + jx) / W - 1) tan(vfov/2) W/H and sy = (1 - 2 (y + jy) / H) tan(vfov/2). */
+typedef struct nrrs_camera {
+    float pos[3];
+    float look[3];
+    float up[3];
+    float vfov_deg;
+} nrrs_camera;
+
+typedef struct nrrs_scene nrrs_scene; /* opaque; owns every device buffer it allocates */
+
+/* Options of one render (NULL = all defaults, shown in brackets). */
+typedef struct nrrs_render_opts {
+    uint32_t seed_lo, seed_hi;  /* Philox key = (seed_lo, seed_hi ^ frame)         [1, 0] */
+    uint32_t frame;             /* frame index                                      [0]    */
+    int32_t cap_factor;         /* queue capacity C = cap_factor * W * H * spp      [2]    */
+    float f_rate;               /* rate-control factor, Eq. q_norm_rate             [0.85] */
+    float alpha0;               /* initial adaptive alpha, Eq. f_rate_prime         [1]    */
+    float q_max;                /* HEUR cap                                         [16]   */
+    float eps_rel;              /* HEUR: eps_I = eps_rel * mean(I_ref)              [0.01] */
+    float boxcox_lambda;        /* throughput feature encoding                      [0.5]  */
+    int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT)                [32]   */
+    uint64_t gate;              /* NET_MIX method per depth (NRRS_GATE_*)           [0]    */
+    const float* d_pixel_ref;   /* device [H*W*3] reference I_px for HEUR, or NULL to use
+                                   the scene's running mean of earlier frames       [NULL] */
+    int32_t update_ref;         /* fold this frame into the scene's running mean    [1]    */
+    int32_t reset_ref;          /* forget the running mean before this frame        [0]    */
+    uint32_t* d_trace;          /* device [max_depth][C][5] u32 or NULL: per depth and
+                                   queue slot (pixel, sample, lineage, triangle or
+                                   0xFFFFFFFF, X); for tests                        [NULL] */
+    int32_t profile;            /* record CUDA events around every kernel launch on
+                                   `stream`; per-stage times land in stats          [0]    */
+    int32_t reserved0;
+} nrrs_render_opts;
+
+/* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
+#define NRRS_STAGE_INIT 0      /* reference mean + camera rays                      */
+#define NRRS_STAGE_EXTEND 1    /* traversal, emission deposit, RRS factor (+RRSNet) */
+#define NRRS_STAGE_NORMALIZE 2 /* FP64 sum of q, F                                  */
+#define NRRS_STAGE_COUNT 3     /* split counts per block + per-pixel accumulation   */
+#define NRRS_STAGE_SCAN 4      /* block offsets, next queue length, alpha           */
+#define NRRS_STAGE_SCATTER 5   /* children + BSDF sampling into the next queue      */
+#define NRRS_STAGE_FINALIZE 6  /* frame estimate + running reference                */
+#define NRRS_N_STAGES 7
+
+/* Per-render statistics; filled only when a non-NULL pointer is passed (the call then
+ * synchronizes `stream`).  Index d-1 holds depth d (1-based, camera hit = depth 1). */
+typedef struct nrrs_render_stats {
+    int64_t live[NRRS_MAX_DEPTH];      /* queue length traced at depth d                */
+    double sum_q[NRRS_MAX_DEPTH];      /* FP64 sum of q_orig over the queue             */
+    float F[NRRS_MAX_DEPTH];           /* applied factor min(1, f alpha C / sum_q)      */
+    double alpha[NRRS_MAX_DEPTH];      /* adaptive alpha used at depth d                */
+    int64_t requested[NRRS_MAX_DEPTH]; /* children requested (sum of X)                 */
+    int64_t dropped[NRRS_MAX_DEPTH];   /* children beyond the capacity                  */
+    int64_t segments;                  /* sum of live: rays traced                      */
+    int64_t nonfinite;                 /* vertices whose factor was NaN/Inf/negative    */
+    int64_t net_evals;                 /* RRSNet evaluations                            */
+    int64_t capacity;                  /* C                                             */
+    uint32_t status_bits;              /* NRRS_STATUS_* seen during the render          */
+    uint32_t kernel_launches;          /* kernels this render launched                  */
+    float stage_ms[8];                 /* opts->profile: summed event time per stage    */
+    int32_t stage_launches[8];         /* opts->profile: launches per stage             */
+} nrrs_render_stats;
+
+NRRS_API const char* nrrs_status_string(nrrs_status s);
+NRRS_API const char* nrrs_last_error(void);
+
+/* Build a scene on `device`: copies the triangles ([n_tri][9] float, v0 v1 v2),
+ * per-triangle material ids ([n_tri] int32 in [0, n_mat)), materials and camera to the
+ * device and builds a binned-SAH BVH2 on the host.  RRSNet weights start at zero
+ * (q = ln 2 everywhere) until nrrs_set_rrsnet_params.  *out receives the scene.
+ * Errors: INVALID_ARG on NULL pointers, n_tri < 1, n_mat < 1 or a bad material id;
+ * OOM / CUDA on device failures (nothing is leaked). */
+NRRS_API nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tri_mat,
+                              const nrrs_material* mats, int32_t n_mat, const nrrs_camera* cam,
+                              int32_t device, nrrs_scene** out);
+
+/* Free every device buffer of the scene (synchronizes the device). NULL is a no-op. */
+NRRS_API nrrs_status nrrs_destroy_scene(nrrs_scene* scene);
+
+/* Host copies of the BVH for inspection: node count and triangle count after build. */
+NRRS_API nrrs_status nrrs_scene_info(const nrrs_scene* scene, int64_t* n_nodes, int64_t* n_tri);
+
+/* Replace / read the RRSNet weights (host, NRRS_RRSNET_PARAMS floats, packed
+ * W1[32][16] | W2[32][32] | W3[32][32] | W4[1][32], row-major).  Sec. 4 "Network
+ * Architecture": three hidden layers of 32 with Leaky ReLU (slope 0.01), output
+ * activation of Eq. rrsnet_activation.  set is stream-ordered on `stream`. */
+NRRS_API nrrs_status nrrs_set_rrsnet_params(nrrs_scene* scene, const float* params, int32_t n,
+                                   void* stream);
+NRRS_API nrrs_status nrrs_get_rrsnet_params(nrrs_scene* scene, float* params, int32_t n, void* stream);
+
+/* One frame: W x H pixels, spp samples, camera hit = depth 1 ... max_depth, with the RRS
+ * factors of `rrs_mode` (Sec. 3.1: every depth is normalized for HEUR/NET/NET_MIX,
+ * downscale only, Sec. 4 "Compromise").  Writes the frame estimate, the mean over spp
+ * of the deposited radiance, to d_rgb (device [H][W][3] float).
+ * Limits: 1 <= max_depth <= NRRS_MAX_DEPTH, W*H*spp*cap_factor < 2^31.
+ * Errors: INVALID_ARG (bad sizes, mode, NULL d_rgb); OOM; CUDA.  Overflow drops and
+ * non-finite factors are not errors: they are counted in stats (status_bits). */
+NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
+                        int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts* opts,
+                        float* d_rgb, void* stream, nrrs_render_stats* stats);
+
+/* RRSNet inference on n feature rows (device [n][16] float, 16-byte aligned) -> device
+ * d_q [n] float.
+ * precision 32 = FP32 SIMT.  Feature layout (16 raw features in place of the paper's
+ * encoded inputs of Sec. 4 "Input Encoding"): position normalised to the scene box (3),
+ * outgoing direction (3), shading normal (3), albedo (3), depth / max_depth (1),
+ * Box-Cox(t) with lambda = boxcox_lambda per throughput channel (3).
+ * Errors: INVALID_ARG (n < 0, NULL with n > 0, unknown precision). */
+NRRS_API nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64_t n,
+                               int32_t precision, float* d_q, void* stream);
+
+/* Normalization of one queue (Eq. q_norm, Eq. F_norm, Eq. q_norm_rate, downscale only):
+ * sum = FP64 sum of d_q[0..n), F = min(1, f_rate * alpha * budget / sum) (1 if
+ * sum == 0) rounded to FP32.  Writes d_F[0] (float) and d_sum[0] (double).
+ * `scene` only selects the device (NULL = the current device).  Scratch: per-block
+ * partial sums in a per-device pool the library allocates once; calls that overlap on
+ * the GPU (different streams) share it and race, so keep them on one stream. */
+NRRS_API nrrs_status nrrs_normalize(nrrs_scene* scene, const float* d_q, int64_t n, double budget,
+                           double f_rate, double alpha, float* d_F, double* d_sum,
+                           void* stream);
+
+/* Split counts and compaction of one queue (Eq. rrs_factor), the integer core of the
+ * bounce.  For parent i: q_used = fp32(F * q_orig_i), k = floor(q_used),
+ * r = q_used - k, U = (Philox4x32-10(key, ctr).x >> 8) * 2^-24 with
+ * key = (seed_lo, seed_hi ^ frame), ctr = (pixel_i, sample_i, depth << 8 | 3, lineage_i),
+ * X_i = k + [U < r].  Children of i take slots [prefix_i, prefix_i + X_i) in parent
+ * order; child j gets lineage (ctr-output.y + j * 0x9E3779B9) mod 2^32.  Slots >= cap
+ * are not written (dropped).  Outputs (device): d_X[n] u32, d_prefix[n] i64 exclusive
+ * prefix of X, d_child_parent[cap] u32, d_child_lineage[cap] u32, d_total[0] i64 = sum X,
+ * d_dropped[0] i64.  d_F is a device float.  Requires n < 2^31, cap < 2^31; X is
+ * clamped at 2^23 (q_used >= 2^23 has no fractional part in FP32).
+ * `scene` only selects the device (NULL = the current device).  Scratch: per-block
+ * child counts and offsets in the same per-device pool as nrrs_normalize (same race
+ * rule: overlapping calls on different streams race). */
+NRRS_API nrrs_status nrrs_split(nrrs_scene* scene, const float* d_q_orig, int64_t n, const float* d_F,
+                       const uint32_t* d_pixel, const uint32_t* d_sample,
+                       const uint32_t* d_lineage, uint32_t depth, uint32_t seed_lo,
+                       uint32_t seed_hi, uint32_t frame, int64_t cap, uint32_t* d_X,
+                       int64_t* d_prefix, uint32_t* d_child_parent, uint32_t* d_child_lineage,
+                       int64_t* d_total, int64_t* d_dropped, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRRS_H */

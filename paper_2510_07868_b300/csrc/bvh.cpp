@@ -1,0 +1,191 @@
+// Host-side BVH2 build (binned SAH) and the device layouts it produces.
+//
+// Node (64 bytes, 4 x float4), both children's boxes stored in the parent so one fetch
+// decides which children to visit:
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   d = (child0, child1, count0, count1)   child >= 0: inner node index;
+//                                          child <  0: leaf, first triangle ~child.
+// Triangles (48 bytes, 3 x float4, in BVH leaf order):
+//   (v0.xyz, original index), (e1 = v1 - v0, material id), (e2 = v2 - v0, 0)
+#include "bvh.h"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+namespace nrrs {
+
+namespace {
+
+struct Box {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX};
+    float hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    void grow(const float* p) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], p[k]);
+            hi[k] = std::max(hi[k], p[k]);
+        }
+    }
+    void grow(const Box& b) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], b.lo[k]);
+            hi[k] = std::max(hi[k], b.hi[k]);
+        }
+    }
+    bool empty() const { return lo[0] > hi[0]; }
+    double area() const {
+        if (empty()) return 0.0;
+        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct Prim {
+    Box box;
+    float c[3];
+    int32_t id;
+};
+
+constexpr int kBins = 16;
+constexpr int kLeafMax = 4;
+constexpr int kMaxBuildDepth = 60;  // traversal stack holds 64 entries
+
+struct Builder {
+    std::vector<Prim>& prims;
+    std::vector<BvhNode>& nodes;
+
+    // Returns the child encoding for prims[begin, end) and its bounds.
+    int32_t build(int32_t begin, int32_t end, int depth, Box* out_box, int32_t* out_count) {
+        Box b, cb;
+        for (int32_t i = begin; i < end; ++i) {
+            b.grow(prims[i].box);
+            cb.grow(prims[i].c);
+        }
+        *out_box = b;
+        const int32_t n = end - begin;
+        if (n <= kLeafMax || depth >= kMaxBuildDepth) {
+            *out_count = n;
+            return ~begin;
+        }
+        // binned SAH over centroid bounds
+        int best_axis = -1, best_split = -1;
+        double best_cost = DBL_MAX;
+        for (int ax = 0; ax < 3; ++ax) {
+            const float ext = cb.hi[ax] - cb.lo[ax];
+            if (!(ext > 0.0f)) continue;
+            Box bb[kBins];
+            int cnt[kBins] = {0};
+            const float scale = kBins / ext;
+            for (int32_t i = begin; i < end; ++i) {
+                int k = std::min(kBins - 1, (int)((prims[i].c[ax] - cb.lo[ax]) * scale));
+                cnt[k]++;
+                bb[k].grow(prims[i].box);
+            }
+            double rA[kBins];
+            int rN[kBins];
+            Box acc;
+            int na = 0;
+            for (int k = kBins - 1; k > 0; --k) {
+                acc.grow(bb[k]);
+                na += cnt[k];
+                rA[k] = acc.area();
+                rN[k] = na;
+            }
+            Box lacc;
+            int nl = 0;
+            for (int k = 0; k < kBins - 1; ++k) {
+                lacc.grow(bb[k]);
+                nl += cnt[k];
+                if (nl == 0 || rN[k + 1] == 0) continue;
+                double cost = lacc.area() * nl + rA[k + 1] * rN[k + 1];
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_axis = ax;
+                    best_split = k;
+                }
+            }
+        }
+        int32_t mid;
+        if (best_axis < 0) {
+            mid = begin + n / 2;  // coincident centroids: split by count
+        } else {
+            const float ext = cb.hi[best_axis] - cb.lo[best_axis];
+            const float scale = kBins / ext;
+            auto it = std::partition(prims.begin() + begin, prims.begin() + end, [&](const Prim& p) {
+                int k = std::min(kBins - 1, (int)((p.c[best_axis] - cb.lo[best_axis]) * scale));
+                return k <= best_split;
+            });
+            mid = (int32_t)(it - prims.begin());
+            if (mid == begin || mid == end) mid = begin + n / 2;
+        }
+        const int32_t self = (int32_t)nodes.size();
+        nodes.emplace_back();
+        Box lb, rb;
+        int32_t lc = 0, rc = 0;
+        int32_t l = build(begin, mid, depth + 1, &lb, &lc);
+        int32_t r = build(mid, end, depth + 1, &rb, &rc);
+        fill(nodes[self], lb, l, lc, rb, r, rc);
+        *out_count = 0;
+        return self;
+    }
+
+    static void fill(BvhNode& nd, const Box& l, int32_t lc, int32_t ln, const Box& r, int32_t rcode,
+                     int32_t rn) {
+        nd.a[0] = l.lo[0]; nd.a[1] = l.hi[0]; nd.a[2] = l.lo[1]; nd.a[3] = l.hi[1];
+        nd.b[0] = r.lo[0]; nd.b[1] = r.hi[0]; nd.b[2] = r.lo[1]; nd.b[3] = r.hi[1];
+        nd.c[0] = l.lo[2]; nd.c[1] = l.hi[2]; nd.c[2] = r.lo[2]; nd.c[3] = r.hi[2];
+        nd.d[0] = lc; nd.d[1] = rcode; nd.d[2] = ln; nd.d[3] = rn;
+    }
+};
+
+}  // namespace
+
+void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* out) {
+    std::vector<Prim> prims(n_tri);
+    for (int32_t i = 0; i < n_tri; ++i) {
+        Prim& p = prims[i];
+        for (int k = 0; k < 3; ++k) p.box.grow(tri + (size_t)i * 9 + 3 * k);
+        for (int a = 0; a < 3; ++a)
+            p.c[a] = (tri[(size_t)i * 9 + a] + tri[(size_t)i * 9 + 3 + a] + tri[(size_t)i * 9 + 6 + a]) /
+                     3.0f;
+        p.id = i;
+    }
+    out->nodes.clear();
+    Builder bld{prims, out->nodes};
+    Box root_box;
+    int32_t root_count = 0;
+    int32_t root = bld.build(0, n_tri, 0, &root_box, &root_count);
+    if (root < 0) {
+        // whole scene is one leaf: make a root whose second child is empty
+        out->nodes.emplace_back();
+        Box empty;
+        Builder::fill(out->nodes[0], root_box, root, root_count, empty, ~0, 0);
+    }
+    out->tris.assign((size_t)n_tri * 12, 0.0f);
+    for (int32_t s = 0; s < n_tri; ++s) {
+        const int32_t i = prims[s].id;
+        const float* v = tri + (size_t)i * 9;
+        float* o = out->tris.data() + (size_t)s * 12;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = v[k];
+            o[4 + k] = v[3 + k] - v[k];  // correctly rounded FP32 difference
+            o[8 + k] = v[6 + k] - v[k];
+        }
+        std::memcpy(&o[3], &i, 4);
+        std::memcpy(&o[7], &mat_id[i], 4);
+    }
+    for (int k = 0; k < 3; ++k) {
+        out->lo[k] = FLT_MAX;
+        out->hi[k] = -FLT_MAX;
+    }
+    for (int64_t i = 0; i < (int64_t)n_tri * 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            out->lo[k] = std::min(out->lo[k], tri[i * 3 + k]);
+            out->hi[k] = std::max(out->hi[k], tri[i * 3 + k]);
+        }
+}
+
+}  // namespace nrrs

@@ -1,0 +1,849 @@
+// Wavefront bounce kernels for sm_103a: camera rays, extension (BVH2 traversal,
+// emission deposit, RRS factor), normalization, split counts + compaction, and the
+// per-pixel accumulation.  The method: "NRRS: Neural Russian Roulette and Splitting",
+// Sec. 2 (Eq. rrs_factor), Sec. 3.1 (Eq. q_norm, F_norm, q_norm_rate, f_rate_prime),
+// Sec. 4 (network, Eq. rrsnet_activation, "Compromise").
+#include <cfloat>
+#include <cstdio>
+
+#include "wavefront.cuh"
+
+namespace nrrs {
+
+namespace {
+
+constexpr int kExtendThreads = 256;
+constexpr int kSplitThreads = 256;
+constexpr int kReduceThreads = 1024;
+constexpr int kStack = 64;
+constexpr uint32_t kMaxX = 1u << 23;  // q_used >= 2^23 has no fractional part in FP32
+
+__device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
+__device__ __forceinline__ float bitsf(uint32_t u) { return __uint_as_float(u); }
+
+// ------------------------------------------------------------------ traversal
+struct Hit {
+    float t;
+    int slot;      // BVH-order triangle slot, -1 = miss
+    uint32_t id;   // original triangle index (tie-break)
+};
+
+// Closest hit along o + t d, t > 0.  Equal distances go to the lower original
+// triangle index, so the answer does not depend on the traversal order.
+__device__ __forceinline__ Hit trace_closest(const SceneView& sc, V3 o, V3 d) {
+    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    const V3 oi = v3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    Hit h{FLT_MAX, -1, 0xFFFFFFFFu};
+    int stack[kStack];
+    int sp = 0;
+    int cur = 0;
+    for (;;) {
+        const float4 a = __ldg(&sc.nodes[4 * cur + 0]);
+        const float4 b = __ldg(&sc.nodes[4 * cur + 1]);
+        const float4 c = __ldg(&sc.nodes[4 * cur + 2]);
+        const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * cur + 3]));
+        // child 0
+        float lx = fmaf(a.x, inv.x, -oi.x), hx = fmaf(a.y, inv.x, -oi.x);
+        float ly = fmaf(a.z, inv.y, -oi.y), hy = fmaf(a.w, inv.y, -oi.y);
+        float lz = fmaf(c.x, inv.z, -oi.z), hz = fmaf(c.y, inv.z, -oi.z);
+        float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+        float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+        bool h0 = t0n <= t0f;
+        // child 1
+        lx = fmaf(b.x, inv.x, -oi.x); hx = fmaf(b.y, inv.x, -oi.x);
+        ly = fmaf(b.z, inv.y, -oi.y); hy = fmaf(b.w, inv.y, -oi.y);
+        lz = fmaf(c.z, inv.z, -oi.z); hz = fmaf(c.w, inv.z, -oi.z);
+        float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+        float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+        bool h1 = t1n <= t1f;
+        int c0 = e.x, c1 = e.y;
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            const int code = side ? c1 : c0;
+            const bool hitbox = side ? h1 : h0;
+            if (!hitbox || code >= 0) continue;
+            const int first = ~code, count = side ? e.w : e.z;
+            for (int k = 0; k < count; ++k) {
+                const int s = first + k;
+                const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
+                const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
+                const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
+                const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
+                const V3 pv = cross3(d, e2);
+                const float det = dot3(e1, pv);
+                if (det == 0.0f) continue;
+                const float idet = 1.0f / det;
+                const V3 tv = o - v0;
+                const float u = dot3(tv, pv) * idet;
+                if (u < 0.0f || u > 1.0f) continue;
+                const V3 qv = cross3(tv, e1);
+                const float v = dot3(d, qv) * idet;
+                if (v < 0.0f || u + v > 1.0f) continue;
+                const float t = dot3(e2, qv) * idet;
+                const uint32_t id = fbits(t0.w);
+                if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
+                    h.t = t;
+                    h.slot = s;
+                    h.id = id;
+                }
+            }
+            if (side) h1 = false; else h0 = false;
+        }
+        if (h0 && h1) {
+            if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
+            if (sp < kStack) stack[sp++] = c1;
+            cur = c0;
+        } else if (h0) {
+            cur = c0;
+        } else if (h1) {
+            cur = c1;
+        } else {
+            if (sp == 0) break;
+            cur = stack[--sp];
+        }
+    }
+    if (h.slot < 0) h.t = FLT_MAX;
+    return h;
+}
+
+__device__ __forceinline__ V3 tri_geom_normal(const SceneView& sc, int slot, int* mat) {
+    const float4 t1 = __ldg(&sc.tris[3 * slot + 1]);
+    const float4 t2 = __ldg(&sc.tris[3 * slot + 2]);
+    *mat = (int)fbits(t1.w);
+    return normalize3(cross3(xyz(t1), xyz(t2)));
+}
+
+// ------------------------------------------------------------------ RRSNet (FP32)
+// Sec. 4 "Network Architecture": 16 -> 32 -> 32 -> 32 -> 1, no biases, Leaky ReLU
+// after each hidden layer; output through Eq. rrsnet_activation.  `w` points at the
+// 2592 weights (shared memory), rows contiguous.
+__device__ __forceinline__ float softplus_mod(float z) {
+    return z < 0.0f ? log1pf(expf(z)) : fmaf(0.5f, z, 0.693147180559945f);
+}
+
+__device__ __forceinline__ float rrsnet_forward(const float* __restrict__ w, const float (&x)[kNF]) {
+    float h[kNH], g[kNH];
+    const float4* W1 = reinterpret_cast<const float4*>(w);
+#pragma unroll
+    for (int j = 0; j < kNH; ++j) {
+        float a = 0.0f;
+#pragma unroll
+        for (int k4 = 0; k4 < kNF / 4; ++k4) {
+            const float4 ww = W1[j * (kNF / 4) + k4];
+            a = fmaf(ww.x, x[4 * k4 + 0], a);
+            a = fmaf(ww.y, x[4 * k4 + 1], a);
+            a = fmaf(ww.z, x[4 * k4 + 2], a);
+            a = fmaf(ww.w, x[4 * k4 + 3], a);
+        }
+        h[j] = a > 0.0f ? a : kLeak * a;
+    }
+    const float4* W2 = reinterpret_cast<const float4*>(w + kNH * kNF);
+#pragma unroll
+    for (int j = 0; j < kNH; ++j) {
+        float a = 0.0f;
+#pragma unroll
+        for (int k4 = 0; k4 < kNH / 4; ++k4) {
+            const float4 ww = W2[j * (kNH / 4) + k4];
+            a = fmaf(ww.x, h[4 * k4 + 0], a);
+            a = fmaf(ww.y, h[4 * k4 + 1], a);
+            a = fmaf(ww.z, h[4 * k4 + 2], a);
+            a = fmaf(ww.w, h[4 * k4 + 3], a);
+        }
+        g[j] = a > 0.0f ? a : kLeak * a;
+    }
+    const float4* W3 = reinterpret_cast<const float4*>(w + kNH * kNF + kNH * kNH);
+#pragma unroll
+    for (int j = 0; j < kNH; ++j) {
+        float a = 0.0f;
+#pragma unroll
+        for (int k4 = 0; k4 < kNH / 4; ++k4) {
+            const float4 ww = W3[j * (kNH / 4) + k4];
+            a = fmaf(ww.x, g[4 * k4 + 0], a);
+            a = fmaf(ww.y, g[4 * k4 + 1], a);
+            a = fmaf(ww.z, g[4 * k4 + 2], a);
+            a = fmaf(ww.w, g[4 * k4 + 3], a);
+        }
+        h[j] = a > 0.0f ? a : kLeak * a;
+    }
+    const float4* W4 = reinterpret_cast<const float4*>(w + kNH * kNF + 2 * kNH * kNH);
+    float z = 0.0f;
+#pragma unroll
+    for (int k4 = 0; k4 < kNH / 4; ++k4) {
+        const float4 ww = W4[k4];
+        z = fmaf(ww.x, h[4 * k4 + 0], z);
+        z = fmaf(ww.y, h[4 * k4 + 1], z);
+        z = fmaf(ww.z, h[4 * k4 + 2], z);
+        z = fmaf(ww.w, h[4 * k4 + 3], z);
+    }
+    return softplus_mod(z);
+}
+
+__device__ __forceinline__ void load_weights_smem(float* sw, const float* __restrict__ params) {
+    for (int i = threadIdx.x; i < kNParams / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(sw)[i] = __ldg(reinterpret_cast<const float4*>(params) + i);
+    __syncthreads();
+}
+
+__device__ __forceinline__ float boxcox(float t, float lambda) {
+    if (lambda == 0.5f) return 2.0f * (sqrtf(t) - 1.0f);
+    if (lambda == 0.0f) return logf(t);
+    return (powf(t, lambda) - 1.0f) / lambda;
+}
+
+// ------------------------------------------------------------------ RRS split rule
+// Eq. rrs_factor with the factor scaled by F (Eq. q_norm / q_norm_rate), decided in
+// FP32: q_used = F * q (one rounding), X = floor(q_used) + [U < q_used - floor(q_used)].
+__device__ __forceinline__ uint32_t split_decide(float F, float q, uint32_t key0, uint32_t key1,
+                                                 uint32_t pixel, uint32_t sample, uint32_t depth,
+                                                 uint32_t lineage, float* q_used,
+                                                 uint32_t* lineage_base) {
+    const float qu = __fmul_rn(F, q);
+    *q_used = qu;
+    if (!(qu > 0.0f)) {
+        *lineage_base = 0u;
+        return 0u;
+    }
+    const float k = floorf(qu);
+    const float r = __fsub_rn(qu, k);
+    const U4 w = draw(key0, key1, pixel, sample, depth, kPurposeRrs, lineage);
+    *lineage_base = w.y;
+    uint32_t X = (k >= (float)kMaxX ? kMaxX : (uint32_t)k) + (u01(w.x) < r ? 1u : 0u);
+    return X > kMaxX ? kMaxX : X;
+}
+
+// ------------------------------------------------------------------ BSDF sampling
+__device__ __forceinline__ void onb(V3 n, V3* b1, V3* b2) {  // Duff et al. 2017
+    const float sign = copysignf(1.0f, n.z);
+    const float a = -1.0f / (sign + n.z);
+    const float b = n.x * n.y * a;
+    *b1 = v3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+    *b2 = v3(b, sign + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ V3 cosine_dir(V3 n, float u1, float u2) {  // Shirley & Chiu 1997
+    const float a = 2.0f * u1 - 1.0f, b = 2.0f * u2 - 1.0f;
+    float x = 0.0f, y = 0.0f;
+    if (a != 0.0f || b != 0.0f) {
+        float r, phi;
+        if (fabsf(a) > fabsf(b)) {
+            r = a;
+            phi = 0.785398163397448f * (b / a);
+        } else {
+            r = b;
+            phi = 1.570796326794897f - 0.785398163397448f * (a / b);
+        }
+        float s, c;
+        sincosf(phi, &s, &c);
+        x = r * c;
+        y = r * s;
+    }
+    const float z = sqrtf(fmaxf(0.0f, 1.0f - x * x - y * y));
+    V3 b1, b2;
+    onb(n, &b1, &b2);
+    return b1 * x + b2 * y + n * z;
+}
+
+// GGX (Walter et al. 2007) + Lambert mixture, lobes picked with probability 1/2.
+// Returns the weight f cos / pdf per channel (0 below the shading hemisphere).
+__device__ __forceinline__ V3 sample_ggx(V3 n, V3 wo, const nrrs_material& m, float ulobe,
+                                         float u1, float u2, V3* wi_out) {
+    const float a = m.roughness;
+    V3 wi;
+    if (ulobe < 0.5f) {
+        const float tan2 = a * a * u1 / (1.0f - u1);
+        const float cos_h = 1.0f / sqrtf(1.0f + tan2);
+        const float sin_h = sqrtf(fmaxf(0.0f, 1.0f - cos_h * cos_h));
+        float s, c;
+        sincosf(6.283185307179586f * u2, &s, &c);
+        V3 b1, b2;
+        onb(n, &b1, &b2);
+        const V3 h = b1 * (sin_h * c) + b2 * (sin_h * s) + n * cos_h;
+        wi = h * (2.0f * dot3(wo, h)) - wo;
+    } else {
+        wi = cosine_dir(n, u1, u2);
+    }
+    *wi_out = wi;
+    const float cos_i = dot3(wi, n), cos_o = dot3(wo, n);
+    if (cos_i <= 0.0f || cos_o <= 0.0f) return v3(0.0f, 0.0f, 0.0f);
+    const V3 h = normalize3(wo + wi);
+    const float cos_h = dot3(h, n), oh = dot3(wo, h);
+    const float a2 = a * a;
+    const float den = (a2 - 1.0f) * cos_h * cos_h + 1.0f;
+    const float D = a2 / (3.141592653589793f * den * den);
+    auto G1 = [&](float cw) {
+        const float c2 = cw * cw;
+        return 2.0f / (1.0f + sqrtf(1.0f + a2 * (1.0f - c2) / c2));
+    };
+    const float G = G1(cos_o) * G1(cos_i);
+    const float om = 1.0f - dot3(wi, h);
+    const float om2 = om * om;
+    const float Fr = m.F0 + (1.0f - m.F0) * (om2 * om2 * om);
+    const float spec = D * G * Fr / (4.0f * cos_o * cos_i);
+    const float pdf = 0.5f * D * cos_h / (4.0f * fabsf(oh)) + 0.5f * cos_i / 3.141592653589793f;
+    const float kd = (1.0f - m.F0) / 3.141592653589793f;
+    const float s = cos_i / pdf;
+    return v3((spec + kd * m.albedo[0]) * s, (spec + kd * m.albedo[1]) * s,
+              (spec + kd * m.albedo[2]) * s);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_ref_prepare(const float* __restrict__ ref, long long n3, float eps_rel,
+                              double alpha0, long long P, DevStats* st) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    if (ref)
+        for (long long i = threadIdx.x; i < n3; i += blockDim.x) s += (double)ref[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        st->has_ref = ref != nullptr;
+        st->eps_I = ref ? (float)((double)eps_rel * (s / (double)n3)) : 0.0f;
+        st->alpha_cur = alpha0;
+        st->live[0] = P;
+    }
+}
+
+__global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
+    const long long P = (long long)rp.W * rp.H * rp.spp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const uint32_t pixel = (uint32_t)(i / rp.spp), sample = (uint32_t)(i % rp.spp);
+    const U4 w = draw(rp.key0, rp.key1, pixel, sample, 0u, kPurposeJitter, 0u);
+    const int px = (int)(pixel % (uint32_t)rp.W), py = (int)(pixel / (uint32_t)rp.W);
+    const float sx = (2.0f * ((float)px + u01(w.x)) / (float)rp.W - 1.0f) * cam.tan_half * cam.aspect;
+    const float sy = (1.0f - 2.0f * ((float)py + u01(w.y)) / (float)rp.H) * cam.tan_half;
+    const V3 fw = v3(cam.fw[0], cam.fw[1], cam.fw[2]);
+    const V3 rt = v3(cam.right[0], cam.right[1], cam.right[2]);
+    const V3 up = v3(cam.up[0], cam.up[1], cam.up[2]);
+    const V3 d = normalize3(fw + (rt * sx + up * sy));
+    out.o[i] = make_float4(cam.pos[0], cam.pos[1], cam.pos[2], bitsf(pixel));
+    out.d[i] = make_float4(d.x, d.y, d.z, bitsf(0u));
+    out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
+}
+
+// Extension of depth `depth`: closest hit, emission deposit, RRS factor q_orig and the
+// block's FP64 partial sum of q (persistent grid-stride loop; fixed assignment, so the
+// sum is reproducible).
+template <int KIND>
+__global__ void __launch_bounds__(kExtendThreads)
+k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
+    __shared__ __align__(16) float sW[KIND == kFactorNet ? kNParams : 4];
+    __shared__ double sh[32];
+    if (KIND == kFactorNet) load_weights_smem(sW, rp.params);
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    const int has_ref = st->has_ref;
+    const float eps_I = st->eps_I;
+    double qsum = 0.0;
+    unsigned int nonfinite = 0, evals = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 o4 = cur.o[i];
+        const float4 d4 = cur.d[i];
+        const float4 t4 = cur.t[i];
+        const V3 o = xyz(o4), d = xyz(d4);
+        const Hit h = trace_closest(sc, o, d);
+        float q = 0.0f;
+        float4 dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
+        if (h.slot >= 0) {
+            int mi;
+            const V3 ng = tri_geom_normal(sc, h.slot, &mi);
+            const nrrs_material m = sc.mats[mi];
+            const bool front = dot3(ng, d) < 0.0f;
+            if (front || m.two_sided) {
+                dep.x = t4.x * m.Le[0];
+                dep.y = t4.y * m.Le[1];
+                dep.z = t4.z * m.Le[2];
+            }
+            const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
+            const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
+            if (!black && !dead && depth < rp.D) {
+                if (KIND == kFactorOne) {
+                    q = 1.0f;
+                } else if (KIND == kFactorPlain) {
+                    q = fminf(1.0f, lum(t4.x, t4.y, t4.z));
+                } else if (KIND == kFactorHeur) {
+                    const float l = lum(t4.x, t4.y, t4.z);
+                    if (!has_ref) {
+                        q = l;
+                    } else {
+                        const uint32_t pix = fbits(o4.w);
+                        const float* r = rp.ref + 3 * (size_t)pix;
+                        const float den = fmaxf((r[0] + r[1] + r[2]) / 3.0f, eps_I);
+                        q = den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
+                    }
+                } else {
+                    const V3 p = o + d * h.t;
+                    const V3 ns = front ? ng : ng * -1.0f;
+                    float x[kNF];
+                    x[0] = sc.inv_ext[0] > 0.0f ? (p.x - sc.lo[0]) * sc.inv_ext[0] : 0.5f;
+                    x[1] = sc.inv_ext[1] > 0.0f ? (p.y - sc.lo[1]) * sc.inv_ext[1] : 0.5f;
+                    x[2] = sc.inv_ext[2] > 0.0f ? (p.z - sc.lo[2]) * sc.inv_ext[2] : 0.5f;
+                    x[3] = -d.x; x[4] = -d.y; x[5] = -d.z;
+                    x[6] = ns.x; x[7] = ns.y; x[8] = ns.z;
+                    x[9] = m.albedo[0]; x[10] = m.albedo[1]; x[11] = m.albedo[2];
+                    x[12] = (float)depth / (float)rp.D;
+                    x[13] = boxcox(t4.x, rp.boxcox_lambda);
+                    x[14] = boxcox(t4.y, rp.boxcox_lambda);
+                    x[15] = boxcox(t4.z, rp.boxcox_lambda);
+                    q = rrsnet_forward(sW, x);
+                    ++evals;
+                }
+                if (!(q >= 0.0f && q <= FLT_MAX)) {  // NaN, Inf or negative
+                    q = 0.0f;
+                    ++nonfinite;
+                }
+            }
+        }
+        w.hit[i] = make_float2(h.t, __int_as_float(h.slot));
+        w.q[i] = q;
+        w.dep[i] = dep;
+        qsum += (double)q;
+    }
+    qsum = block_sum(qsum, sh);
+    if (threadIdx.x == 0) w.part[blockIdx.x] = qsum;
+    if (KIND == kFactorNet) {
+        evals = warp_sum(evals);
+        if ((threadIdx.x & 31) == 0 && evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+    }
+    nonfinite = warp_sum(nonfinite);
+    if ((threadIdx.x & 31) == 0 && nonfinite) {
+        atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+        atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+    }
+}
+
+// Eq. F_norm / q_norm_rate / f_rate_prime, downscale only:
+// F = min(1, f_rate * alpha * C / sum q), computed in FP64 and rounded to FP32.
+__global__ void k_normalize_depth(WorkView w, RenderParams rp, int depth, int normalized) {
+    __shared__ double sh[32];
+    DevStats* st = w.st;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < w.grid_extend; b += blockDim.x) s += w.part[b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double alpha = st->alpha_cur;
+        double F = 1.0;
+        if (normalized && s > 0.0) {
+            F = (double)rp.f_rate * alpha * (double)rp.cap / s;
+            if (F > 1.0) F = 1.0;
+        }
+        st->sum_q[depth - 1] = s;
+        st->alpha[depth - 1] = alpha;
+        st->F[depth - 1] = (float)F;
+        st->F_cur = (float)F;
+    }
+}
+
+__device__ __forceinline__ void block_range(long long n, int* tiles_out, long long* begin,
+                                            long long* end) {
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long chunk = ((per + kSplitThreads - 1) / kSplitThreads) * kSplitThreads;
+    *begin = (long long)blockIdx.x * chunk;
+    *end = *begin + chunk < n ? *begin + chunk : n;
+    *tiles_out = *begin < *end ? (int)((*end - *begin + kSplitThreads - 1) / kSplitThreads) : 0;
+}
+
+__device__ __forceinline__ void kahan_add(float4* s_, float4* c_, float x, float y, float z) {
+    float4 s = *s_, c = *c_;
+    float in[3] = {x, y, z};
+    float* sp[3] = {&s.x, &s.y, &s.z};
+    float* cp[3] = {&c.x, &c.y, &c.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float yy = __fsub_rn(in[k], *cp[k]);
+        const float t = __fadd_rn(*sp[k], yy);
+        *cp[k] = __fsub_rn(__fsub_rn(t, *sp[k]), yy);
+        *sp[k] = t;
+    }
+    *s_ = s;
+    *c_ = c;
+}
+
+// Split counts of depth `depth` per block (Eq. rrs_factor), the optional trace, and the
+// per-pixel accumulation of this depth's deposits: the queue is sorted by pixel, so the
+// first slot of each pixel's run sums the run in order and adds it to the pixel's
+// Kahan pair (deterministic, no atomics).
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth, int do_split) {
+    __shared__ unsigned long long sh[32];
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    const float F = st->F_cur;
+    long long begin, end;
+    int tiles;
+    block_range(n, &tiles, &begin, &end);
+    unsigned long long total = 0;
+    for (int tile = 0; tile < tiles; ++tile) {
+        const long long i = begin + (long long)tile * kSplitThreads + threadIdx.x;
+        uint32_t X = 0;
+        if (i < end) {
+            const float4 dep = w.dep[i];
+            const uint32_t pix = fbits(dep.w);
+            const bool head = i == 0 || fbits(w.dep[i - 1].w) != pix;
+            if (head) {
+                float sx = dep.x, sy = dep.y, sz = dep.z;
+                for (long long j = i + 1; j < n; ++j) {
+                    const float4 e = w.dep[j];
+                    if (fbits(e.w) != pix) break;
+                    sx += e.x; sy += e.y; sz += e.z;
+                }
+                kahan_add(&w.acc_s[pix], &w.acc_c[pix], sx, sy, sz);
+            }
+            if (do_split || rp.trace) {
+                const float4 o4 = cur.o[i];
+                const float4 d4 = cur.d[i];
+                const float4 t4 = cur.t[i];
+                float qu;
+                uint32_t base;
+                X = split_decide(F, w.q[i], rp.key0, rp.key1, fbits(o4.w), fbits(t4.w),
+                                 (uint32_t)depth, fbits(d4.w), &qu, &base);
+                if (rp.trace) {
+                    const int slot = __float_as_int(w.hit[i].y);
+                    uint32_t* r = rp.trace + ((size_t)(depth - 1) * rp.cap + i) * 5;
+                    r[0] = fbits(o4.w);
+                    r[1] = fbits(t4.w);
+                    r[2] = fbits(d4.w);
+                    r[3] = slot < 0 ? kNoHit : fbits(__ldg(&sc.tris[3 * slot].w));
+                    r[4] = X;
+                }
+            }
+        }
+        total += (unsigned long long)X;
+    }
+    if (!do_split) return;
+    total = block_sum(total, sh);
+    if (threadIdx.x == 0) w.bcnt[blockIdx.x] = (unsigned int)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+}
+
+// Exclusive scan of the per-block counts in 64-bit; sets the next queue length
+// min(S, C), the drop count and the alpha back-off (Eq. f_rate_prime, epsilon 0.01).
+__device__ void scan_counts(const unsigned int* cnt, unsigned long long* off, int G,
+                            unsigned long long* total_out) {
+    __shared__ unsigned long long sh[kReduceThreads];
+    const int per = (G + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    unsigned long long s = 0;
+    for (int k = 0; k < per && b0 + k < G; ++k) s += cnt[b0 + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over thread sums (1024 entries, 10 steps)
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        unsigned long long v = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = sh[threadIdx.x] - s;
+    for (int k = 0; k < per && b0 + k < G; ++k) {
+        off[b0 + k] = run;
+        run += cnt[b0 + k];
+    }
+    if (threadIdx.x == blockDim.x - 1) *total_out = sh[threadIdx.x];
+}
+
+__global__ void k_split_scan(WorkView w, RenderParams rp, int depth) {
+    __shared__ unsigned long long total;
+    scan_counts(w.bcnt, w.boff, w.grid_split, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevStats* st = w.st;
+        const unsigned long long S = total;
+        const unsigned long long C = (unsigned long long)rp.cap;
+        const unsigned long long nn = S < C ? S : C;
+        st->requested[depth - 1] = (long long)S;
+        st->dropped[depth - 1] = (long long)(S - nn);
+        st->live[depth] = (long long)nn;
+        if (S > nn) {
+            st->alpha_cur *= 0.99;
+            st->status |= NRRS_STATUS_OVERFLOW_DROPPED;
+        }
+    }
+}
+
+// Scatter of depth `depth`: each parent writes its X children to consecutive slots
+// (stable, parent order) and samples one BSDF direction per child with the child's own
+// lineage; child throughput = t * weight / q_used.  Slots >= C are dropped.
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderParams rp,
+                int depth) {
+    __shared__ uint32_t sh[33];
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    const float F = st->F_cur;
+    long long begin, end;
+    int tiles;
+    block_range(n, &tiles, &begin, &end);
+    unsigned long long carry = tiles ? w.boff[blockIdx.x] : 0ull;
+    for (int tile = 0; tile < tiles; ++tile) {
+        const long long i = begin + (long long)tile * kSplitThreads + threadIdx.x;
+        uint32_t X = 0, base = 0;
+        float qu = 0.0f;
+        float4 o4, d4, t4;
+        if (i < end) {
+            o4 = cur.o[i];
+            d4 = cur.d[i];
+            t4 = cur.t[i];
+            X = split_decide(F, w.q[i], rp.key0, rp.key1, fbits(o4.w), fbits(t4.w),
+                             (uint32_t)depth, fbits(d4.w), &qu, &base);
+        }
+        uint32_t tile_total;
+        const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
+        if (X > 0) {
+            const float2 hh = w.hit[i];
+            const int slot = __float_as_int(hh.y);
+            int mi;
+            const V3 ng = tri_geom_normal(sc, slot, &mi);
+            const nrrs_material m = sc.mats[mi];
+            const V3 d = xyz(d4);
+            const V3 ns = dot3(ng, d) < 0.0f ? ng : ng * -1.0f;
+            const V3 p = xyz(o4) + d * hh.x;
+            const V3 org = p + ns * kRayOffset;
+            const uint32_t pix = fbits(o4.w), smp = fbits(t4.w);
+            const float iq = 1.0f / qu;
+            for (uint32_t j = 0; j < X; ++j) {
+                const unsigned long long dst = carry + pre + j;
+                if (dst >= (unsigned long long)rp.cap) break;
+                const uint32_t lin = base + j * kLineageStep;
+                const U4 r = draw(rp.key0, rp.key1, pix, smp, (uint32_t)depth, kPurposeBsdf, lin);
+                V3 wi, wt;
+                if (m.type == 0) {
+                    wi = cosine_dir(ns, u01(r.y), u01(r.z));
+                    wt = v3(m.albedo[0], m.albedo[1], m.albedo[2]);
+                } else {
+                    wt = sample_ggx(ns, d * -1.0f, m, u01(r.x), u01(r.y), u01(r.z), &wi);
+                }
+                nxt.o[dst] = make_float4(org.x, org.y, org.z, o4.w);
+                nxt.d[dst] = make_float4(wi.x, wi.y, wi.z, bitsf(lin));
+                nxt.t[dst] = make_float4(t4.x * wt.x * iq, t4.y * wt.y * iq, t4.z * wt.z * iq, t4.w);
+            }
+        }
+        carry += tile_total;
+    }
+    (void)st;
+}
+
+__global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
+                           float* __restrict__ ref_mean, int ref_count, int update_ref) {
+    const long long npix = (long long)rp.W * rp.H;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const float4 s = w.acc_s[p], c = w.acc_c[p];
+    const float inv = 1.0f / (float)rp.spp;
+    const float r = (s.x - c.x) * inv, g = (s.y - c.y) * inv, b = (s.z - c.z) * inv;
+    rgb[3 * p + 0] = r;
+    rgb[3 * p + 1] = g;
+    rgb[3 * p + 2] = b;
+    if (update_ref && ref_mean) {
+        // running mean of the frames so far (the reference I_px of Sec. 4 "Compromise")
+        const float k = (float)ref_count;
+        const float ik = 1.0f / (k + 1.0f);
+        float* m = ref_mean + 3 * p;
+        m[0] = (m[0] * k + r) * ik;
+        m[1] = (m[1] * k + g) * ik;
+        m[2] = (m[2] * k + b) * ik;
+    }
+}
+
+// ------------------------------------------------------------------ plain-array entry points
+__global__ void __launch_bounds__(256) k_query(const float* __restrict__ params,
+                                               const float* __restrict__ feat, long long n,
+                                               float* __restrict__ q) {
+    __shared__ __align__(16) float sW[kNParams];
+    load_weights_smem(sW, params);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4* f = reinterpret_cast<const float4*>(feat + i * kNF);
+        float x[kNF];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = __ldg(f + k);
+            x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+        }
+        q[i] = rrsnet_forward(sW, x);
+    }
+}
+
+__global__ void k_sum_part(const float* __restrict__ q, long long n, double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s += (double)q[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_norm_final(const double* part, int G, double budget, double f_rate, double alpha,
+                             float* F_out, double* sum_out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        double F = 1.0;
+        if (s > 0.0) {
+            F = f_rate * alpha * budget / s;
+            if (F > 1.0) F = 1.0;
+        }
+        *F_out = (float)F;
+        *sum_out = s;
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_arr_count(SplitArrays a, unsigned int* bcnt) {
+    __shared__ unsigned long long sh[32];
+    const float F = *a.F;
+    long long begin, end;
+    int tiles;
+    block_range(a.n, &tiles, &begin, &end);
+    unsigned long long total = 0;
+    for (int tile = 0; tile < tiles; ++tile) {
+        const long long i = begin + (long long)tile * kSplitThreads + threadIdx.x;
+        if (i < end) {
+            float qu;
+            uint32_t base;
+            const uint32_t X = split_decide(F, a.q[i], a.key0, a.key1, a.pixel[i], a.sample[i],
+                                            a.depth, a.lineage[i], &qu, &base);
+            a.X[i] = X;
+            total += X;
+        }
+    }
+    total = block_sum(total, sh);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = (unsigned int)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+}
+
+__global__ void k_split_arr_scan(SplitArrays a, const unsigned int* bcnt, unsigned long long* boff,
+                                 int G) {
+    __shared__ unsigned long long total;
+    scan_counts(bcnt, boff, G, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long C = (unsigned long long)a.cap;
+        *a.total = (long long)total;
+        *a.dropped = (long long)(total > C ? total - C : 0ull);
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_arr_scatter(SplitArrays a, const unsigned long long* boff) {
+    __shared__ uint32_t sh[33];
+    const float F = *a.F;
+    long long begin, end;
+    int tiles;
+    block_range(a.n, &tiles, &begin, &end);
+    unsigned long long carry = tiles ? boff[blockIdx.x] : 0ull;
+    for (int tile = 0; tile < tiles; ++tile) {
+        const long long i = begin + (long long)tile * kSplitThreads + threadIdx.x;
+        uint32_t X = 0, base = 0;
+        if (i < end) {
+            float qu;
+            X = split_decide(F, a.q[i], a.key0, a.key1, a.pixel[i], a.sample[i], a.depth,
+                             a.lineage[i], &qu, &base);
+        }
+        uint32_t tile_total;
+        const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
+        if (i < end) a.prefix[i] = (long long)(carry + pre);
+        for (uint32_t j = 0; j < X; ++j) {
+            const unsigned long long dst = carry + pre + j;
+            if (dst >= (unsigned long long)a.cap) break;
+            a.child_parent[dst] = (uint32_t)i;
+            a.child_lineage[dst] = base + j * kLineageStep;
+        }
+        carry += tile_total;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+int extend_block_threads() { return kExtendThreads; }
+int split_block_threads() { return kSplitThreads; }
+
+int max_blocks_extend(int kind) {
+    int nb = 1;
+    switch (kind) {
+        case kFactorOne: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorOne>, kExtendThreads, 0); break;
+        case kFactorPlain: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorPlain>, kExtendThreads, 0); break;
+        case kFactorHeur: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorHeur>, kExtendThreads, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorNet>, kExtendThreads, 0); break;
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0, long long P,
+                        DevStats* st, cudaStream_t s) {
+    k_ref_prepare<<<1, kReduceThreads, 0, s>>>(ref, n3, eps_rel, alpha0, P, st);
+}
+
+void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s) {
+    const long long P = (long long)rp.W * rp.H * rp.spp;
+    const int threads = 256;
+    k_camera<<<(unsigned)((P + threads - 1) / threads), threads, 0, s>>>(cam, rp, out);
+}
+
+void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
+                   const RenderParams& rp, int depth, cudaStream_t s) {
+    const int G = w.grid_extend;
+    switch (kind) {
+        case kFactorOne: k_extend<kFactorOne><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorPlain: k_extend<kFactorPlain><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorHeur: k_extend<kFactorHeur><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
+        default: k_extend<kFactorNet><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
+    }
+}
+
+void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
+                            cudaStream_t s) {
+    k_normalize_depth<<<1, kReduceThreads, 0, s>>>(w, rp, depth, normalized);
+}
+
+void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,
+                        const RenderParams& rp, int depth, int do_split, cudaStream_t s) {
+    k_split_count<<<w.grid_split, kSplitThreads, 0, s>>>(sc, cur, w, rp, depth, do_split);
+}
+
+void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
+    k_split_scan<<<1, kReduceThreads, 0, s>>>(w, rp, depth);
+}
+
+void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
+                          const RenderParams& rp, int depth, cudaStream_t s) {
+    k_split_scatter<<<w.grid_split, kSplitThreads, 0, s>>>(sc, cur, nxt, w, rp, depth);
+}
+
+void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
+                     int ref_count, int update_ref, cudaStream_t s) {
+    const long long npix = (long long)rp.W * rp.H;
+    k_finalize<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(w, rp, rgb, ref_mean, ref_count,
+                                                               update_ref);
+}
+
+void launch_query_factors(const float* params, const float* feat, long long n, float* q,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    int dev = 0, nsm = 148, nb = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_query, 256, 0);
+    long long need = (n + 255) / 256;
+    long long G = (long long)nsm * (nb < 1 ? 1 : nb);
+    if (G > need) G = need;
+    k_query<<<(unsigned)G, 256, 0, s>>>(params, feat, n, q);
+}
+
+void launch_normalize_array(const float* q, long long n, double budget, double f_rate,
+                            double alpha, double* part, int grid, float* F, double* sum,
+                            cudaStream_t s) {
+    k_sum_part<<<grid, 256, 0, s>>>(q, n, part);
+    k_norm_final<<<1, kReduceThreads, 0, s>>>(part, grid, budget, f_rate, alpha, F, sum);
+}
+
+void launch_split_arrays(const SplitArrays& a, unsigned int* bcnt, unsigned long long* boff,
+                         int grid, cudaStream_t s) {
+    k_split_arr_count<<<grid, kSplitThreads, 0, s>>>(a, bcnt);
+    k_split_arr_scan<<<1, kReduceThreads, 0, s>>>(a, bcnt, boff, grid);
+    k_split_arr_scatter<<<grid, kSplitThreads, 0, s>>>(a, boff);
+}
+
+}  // namespace nrrs

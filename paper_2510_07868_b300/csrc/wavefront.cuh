@@ -1,0 +1,122 @@
+// Device views and launchers of the wavefront bounce kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/nrrs.h"
+#include "common.cuh"
+
+namespace nrrs {
+
+struct SceneView {
+    const float4* nodes;  // 4 float4 per node (bvh.cpp)
+    const float4* tris;   // 3 float4 per triangle, BVH order
+    const nrrs_material* mats;
+    float lo[3];          // scene box, for the position feature
+    float inv_ext[3];     // 1 / extent, 0 for a flat axis (feature = 0.5 there)
+};
+
+struct CamView {
+    float pos[3], fw[3], right[3], up[3];
+    float tan_half, aspect;
+};
+
+// Path state, structure of arrays (one slot per path, 48 bytes):
+//   o = (origin, pixel bits), d = (direction, lineage bits), t = (throughput, sample bits)
+struct QueueView {
+    float4* o;
+    float4* d;
+    float4* t;
+};
+
+// Device-resident per-render statistics; the host copies it once per render.
+struct DevStats {
+    long long live[kMaxDepth + 1];  // live[d-1] = queue length at depth d
+    double sum_q[kMaxDepth];
+    double alpha[kMaxDepth];
+    long long requested[kMaxDepth];
+    long long dropped[kMaxDepth];
+    float F[kMaxDepth];
+    unsigned long long nonfinite;
+    unsigned long long net_evals;
+    double alpha_cur;               // adaptive alpha (Eq. f_rate_prime), carried over depths
+    float F_cur;                    // factor applied at the current depth
+    float eps_I;                    // HEUR floor eps_rel * mean(reference)
+    unsigned int status;            // NRRS_STATUS_* bits
+    int has_ref;
+};
+
+// Per-bounce scratch shared by the kernels of one render.
+struct WorkView {
+    float2* hit;       // [C] (distance, BVH triangle slot bits; -1 = miss)
+    float* q;          // [C] q_orig
+    float4* dep;       // [C] (deposited radiance rgb, pixel bits)
+    double* part;      // [grid_extend] partial sums of q
+    int grid_extend;
+    unsigned int* bcnt;  // [grid_split] children per block
+    unsigned long long* boff;  // [grid_split] exclusive prefix of bcnt
+    int grid_split;
+    float4* acc_s;     // [npix] Kahan sum (rgb)
+    float4* acc_c;     // [npix] Kahan compensation (rgb)
+    DevStats* st;
+};
+
+struct RenderParams {
+    int W, H, spp, D;
+    long long cap;        // C
+    uint32_t key0, key1;  // Philox key
+    float f_rate;
+    float q_max;
+    float boxcox_lambda;
+    const float* ref;     // reference image [npix*3] (running mean or caller's) or null
+    const float* params;  // RRSNet weights (device, 2592 floats)
+    uint32_t* trace;      // optional per-depth trace
+};
+
+enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFactorNet = 3 };
+
+int extend_block_threads();
+int split_block_threads();
+int max_blocks_extend(int kind);  // resident blocks per SM
+
+void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
+                        long long P, DevStats* st, cudaStream_t s);
+void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
+void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
+                   const RenderParams& rp, int depth, cudaStream_t s);
+void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
+                            cudaStream_t s);
+void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,
+                        const RenderParams& rp, int depth, int do_split, cudaStream_t s);
+void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
+void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
+                          const RenderParams& rp, int depth, cudaStream_t s);
+void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
+                     int ref_count, int update_ref, cudaStream_t s);
+
+// Stand-alone entry points on plain arrays.
+void launch_query_factors(const float* params, const float* feat, long long n, float* q,
+                          cudaStream_t s);
+void launch_normalize_array(const float* q, long long n, double budget, double f_rate,
+                            double alpha, double* part, int grid, float* F, double* sum,
+                            cudaStream_t s);
+struct SplitArrays {
+    const float* q;
+    long long n;
+    const float* F;
+    const uint32_t* pixel;
+    const uint32_t* sample;
+    const uint32_t* lineage;
+    uint32_t depth, key0, key1;
+    long long cap;
+    uint32_t* X;
+    long long* prefix;
+    uint32_t* child_parent;
+    uint32_t* child_lineage;
+    long long* total;
+    long long* dropped;
+};
+void launch_split_arrays(const SplitArrays& a, unsigned int* bcnt, unsigned long long* boff,
+                         int grid, cudaStream_t s);
+
+}  // namespace nrrs

@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C ABI in include/nrrs.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in libnrrs.so; all
+computation runs in the library's CUDA kernels.  Device buffers are passed as torch
+CUDA tensors (or raw integer addresses); streams as torch.cuda.Stream (or raw handles).
+Importing this module fails loudly when the compiled library is missing: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnrrs.so")
+
+NRRS_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
+                4: "timeout", 5: "non-finite", 6: "overflow dropped", 7: "unsupported"}
+RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
+GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
+STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
+MAX_DEPTH = 32
+STAGES = 7
+STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
+               "finalize"]
+N_FEATURES = 16
+RRSNET_PARAMS = 2592
+
+EXPORTED = [
+    "nrrs_status_string", "nrrs_last_error", "nrrs_create_scene", "nrrs_destroy_scene",
+    "nrrs_scene_info", "nrrs_set_rrsnet_params", "nrrs_get_rrsnet_params", "nrrs_render",
+    "nrrs_query_factors", "nrrs_normalize", "nrrs_split",
+]
+
+
+class NrrsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32),
+                ("cap_factor", C.c_int32), ("f_rate", C.c_float), ("alpha0", C.c_float),
+                ("q_max", C.c_float), ("eps_rel", C.c_float), ("boxcox_lambda", C.c_float),
+                ("precision", C.c_int32), ("gate", C.c_uint64), ("d_pixel_ref", C.c_void_p),
+                ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
+                ("profile", C.c_int32), ("reserved0", C.c_int32)]
+
+    @classmethod
+    def defaults(cls, **kw):
+        o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
+                eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
+                update_ref=1, reset_ref=0, d_trace=None, profile=0, reserved0=0)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+
+class RenderStats(C.Structure):
+    _fields_ = [("live", C.c_int64 * MAX_DEPTH), ("sum_q", C.c_double * MAX_DEPTH),
+                ("F", C.c_float * MAX_DEPTH), ("alpha", C.c_double * MAX_DEPTH),
+                ("requested", C.c_int64 * MAX_DEPTH), ("dropped", C.c_int64 * MAX_DEPTH),
+                ("segments", C.c_int64), ("nonfinite", C.c_int64), ("net_evals", C.c_int64),
+                ("capacity", C.c_int64), ("status_bits", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("stage_ms", C.c_float * 8),
+                ("stage_launches", C.c_int32 * 8)]
+
+    def as_dict(self, depth):
+        return {
+            "live": np.array(self.live[:depth]), "sum_q": np.array(self.sum_q[:depth]),
+            "F": np.array(self.F[:depth], dtype=np.float32), "alpha": np.array(self.alpha[:depth]),
+            "requested": np.array(self.requested[:depth]),
+            "dropped": np.array(self.dropped[:depth]), "segments": int(self.segments),
+            "nonfinite": int(self.nonfinite), "net_evals": int(self.net_evals),
+            "capacity": int(self.capacity), "status_bits": int(self.status_bits),
+            "kernel_launches": int(self.kernel_launches),
+            "stage_ms": np.array(self.stage_ms[:STAGES], dtype=np.float64),
+            "stage_launches": np.array(self.stage_launches[:STAGES]),
+        }
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2510_07868_b300.build` (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, U32, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+    sig = {
+        "nrrs_status_string": ([I32], C.c_char_p),
+        "nrrs_last_error": ([], C.c_char_p),
+        "nrrs_create_scene": ([P, I32, P, P, I32, P, I32, P], I32),
+        "nrrs_destroy_scene": ([P], I32),
+        "nrrs_scene_info": ([P, P, P], I32),
+        "nrrs_set_rrsnet_params": ([P, P, I32, P], I32),
+        "nrrs_get_rrsnet_params": ([P, P, I32, P], I32),
+        "nrrs_render": ([P, I32, I32, I32, I32, I32, P, P, P, P], I32),
+        "nrrs_query_factors": ([P, P, I64, I32, P, P], I32),
+        "nrrs_normalize": ([P, P, I64, D, D, D, P, P, P], I32),
+        "nrrs_split": ([P, P, I64, P, P, P, P, U32, U32, U32, U32, I64, P, P, P, P, P, P, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(x):
+    """Device address of a torch tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover - torch without CUDA
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc):
+    if rc != NRRS_OK:
+        raise NrrsError(rc, _lib.nrrs_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------------ ABI functions
+def nrrs_status_string(code):
+    return _lib.nrrs_status_string(code).decode()
+
+
+def nrrs_last_error():
+    return _lib.nrrs_last_error().decode()
+
+
+def nrrs_create_scene(tri, tri_mat, mats, cam, device=0):
+    tri = np.ascontiguousarray(tri, dtype=np.float32).reshape(-1, 9)
+    tri_mat = np.ascontiguousarray(tri_mat, dtype=np.int32)
+    mats = np.ascontiguousarray(mats)
+    cam = np.ascontiguousarray(cam)
+    assert mats.dtype.itemsize == 40 and cam.dtype.itemsize == 40
+    out = C.c_void_p()
+    _check(_lib.nrrs_create_scene(tri.ctypes.data, tri.shape[0], tri_mat.ctypes.data,
+                                  mats.ctypes.data, len(mats), cam.ctypes.data, device,
+                                  C.byref(out)))
+    return out.value
+
+
+def nrrs_destroy_scene(scene):
+    _check(_lib.nrrs_destroy_scene(scene))
+
+
+def nrrs_scene_info(scene):
+    nn, nt = C.c_int64(), C.c_int64()
+    _check(_lib.nrrs_scene_info(scene, C.byref(nn), C.byref(nt)))
+    return nn.value, nt.value
+
+
+def nrrs_set_rrsnet_params(scene, params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.nrrs_set_rrsnet_params(scene, p.ctypes.data, p.size, _stream(stream)))
+
+
+def nrrs_get_rrsnet_params(scene, stream=None):
+    p = np.zeros(RRSNET_PARAMS, dtype=np.float32)
+    _check(_lib.nrrs_get_rrsnet_params(scene, p.ctypes.data, p.size, _stream(stream)))
+    return p
+
+
+def nrrs_render(scene, width, height, spp, max_depth, rrs_mode, opts, d_rgb, stream=None,
+                stats=True):
+    st = RenderStats() if stats else None
+    _check(_lib.nrrs_render(scene, width, height, spp, max_depth, rrs_mode,
+                            C.byref(opts) if opts is not None else None, _ptr(d_rgb),
+                            _stream(stream), C.byref(st) if st is not None else None))
+    return st.as_dict(max_depth) if st is not None else None
+
+
+def nrrs_query_factors(scene, d_features, n, precision, d_q, stream=None):
+    _check(_lib.nrrs_query_factors(scene, _ptr(d_features), n, precision, _ptr(d_q),
+                                   _stream(stream)))
+
+
+def nrrs_normalize(scene, d_q, n, budget, f_rate, alpha, d_F, d_sum, stream=None):
+    _check(_lib.nrrs_normalize(scene, _ptr(d_q), n, budget, f_rate, alpha, _ptr(d_F),
+                               _ptr(d_sum), _stream(stream)))
+
+
+def nrrs_split(scene, d_q_orig, n, d_F, d_pixel, d_sample, d_lineage, depth, seed_lo, seed_hi,
+               frame, cap, d_X, d_prefix, d_child_parent, d_child_lineage, d_total, d_dropped,
+               stream=None):
+    _check(_lib.nrrs_split(scene, _ptr(d_q_orig), n, _ptr(d_F), _ptr(d_pixel), _ptr(d_sample),
+                           _ptr(d_lineage), depth, seed_lo, seed_hi, frame, cap, _ptr(d_X),
+                           _ptr(d_prefix), _ptr(d_child_parent), _ptr(d_child_lineage),
+                           _ptr(d_total), _ptr(d_dropped), _stream(stream)))
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class Scene:
+    """Owns one nrrs_scene handle built from an ``inputs.Scene``."""
+
+    def __init__(self, scene, device=0):
+        self.handle = nrrs_create_scene(scene.tri, scene.mat_id, scene.mats, scene.cam, device)
+        self.device = device
+        self.n_tri = scene.n_tri
+
+    def close(self):
+        if self.handle:
+            nrrs_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        nrrs_set_rrsnet_params(self.handle, params)
+
+    def get_params(self):
+        return nrrs_get_rrsnet_params(self.handle)
+
+    def render(self, width, height, spp, max_depth, mode, out=None, stats=True, stream=None,
+               **opts):
+        import torch
+
+        if out is None:
+            out = torch.empty((height, width, 3), dtype=torch.float32, device=f"cuda:{self.device}")
+        o = RenderOpts.defaults(**opts)
+        st = nrrs_render(self.handle, width, height, spp, max_depth, mode, o, out, stream, stats)
+        return out, st
+
+    def query(self, features, precision=32, out=None, stream=None):
+        import torch
+
+        n = features.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=features.device)
+        nrrs_query_factors(self.handle, features, n, precision, out, stream)
+        return out

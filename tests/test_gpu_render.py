@@ -1,0 +1,230 @@
+"""Parity of whole renders (camera -> D bounces -> accumulation) with the FP64 oracle.
+
+Decisions are compared on integers: per depth and queue slot the traced
+(pixel, sample, lineage, triangle, X) records.  Pixels whose decision multiset matches
+the oracle's must agree to 1e-5 relative (FP32 path on identical decisions); the
+matching fraction must stay near 1 (FP32 and FP64 geometry can differ on near-ties).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07868_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def nrrs():
+    from paper_2510_07868_b300 import nrrs as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def _mix(x):
+    x = x.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    return x
+
+
+def pixel_hashes(trace_per_depth, npix):
+    """Order-insensitive per-pixel hash of every (depth, sample, lineage, tri, X) record."""
+    h = np.zeros(npix, dtype=np.uint64)
+    cnt = np.zeros(npix, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        for d, tr in enumerate(trace_per_depth):
+            if len(tr) == 0:
+                continue
+            tr = tr.astype(np.uint64)
+            v = _mix(tr[:, 1] + np.uint64(d) * np.uint64(1 << 40))
+            v = _mix(v ^ tr[:, 2])
+            v = _mix(v ^ (tr[:, 3] << np.uint64(8)))
+            v = _mix(v ^ tr[:, 4])
+            np.add.at(h, tr[:, 0].astype(np.int64), v)
+            np.add.at(cnt, tr[:, 0].astype(np.int64), 1)
+    return h, cnt
+
+
+def gpu_render(nrrs, scene, W, H, spp, D, mode, params=None, ref=None, trace=True, **kw):
+    sc = nrrs.Scene(scene)
+    if params is not None:
+        sc.set_params(params)
+    C = 2 * W * H * spp
+    tr = torch.zeros((D, C, 5), dtype=torch.int32, device="cuda") if trace else None
+    dref = torch.from_numpy(ref.astype(np.float32)).cuda() if ref is not None else None
+    img, st = sc.render(W, H, spp, D, mode, d_trace=tr.data_ptr() if trace else None,
+                        d_pixel_ref=dref.data_ptr() if dref is not None else None, **kw)
+    torch.cuda.synchronize()
+    out = img.cpu().numpy().astype(np.float64)
+    trace_list = None
+    if trace:
+        trn = tr.cpu().numpy().view(np.uint32)
+        trace_list = [trn[d, :st["live"][d]] for d in range(D)]
+    sc.close()
+    return out, st, trace_list
+
+
+def compare(gimg, gtr, oimg, otr, W, H, min_match=0.995):
+    hg, cg = pixel_hashes(gtr, W * H)
+    ho, co = pixel_hashes(otr, W * H)
+    match = (hg == ho) & (cg == co)
+    frac = match.mean()
+    assert frac >= min_match, f"only {frac:.4f} of pixels share every decision"
+    g = gimg.reshape(-1, 3)[match]
+    o = oimg.reshape(-1, 3)[match]
+    err = np.abs(g - o)
+    bad = err > RTOL * np.abs(o) + 1e-30
+    assert not bad.any(), f"max rel err {np.max(err / np.maximum(np.abs(o), 1e-30)):.3e}"
+    return frac
+
+
+def test_furnace_exact(nrrs):
+    """Closed furnace, no RRS: every pixel is exactly (1 - 0.5^8) / (1 - 0.5)."""
+    s = I.box_scene(1, furnace=True)
+    img, st, _ = gpu_render(nrrs, s, 64, 64, 4, 8, nrrs.RRS_NONE, trace=False)
+    exact = np.mean(img == 1.9921875)
+    assert exact >= 0.999, exact
+    assert np.all(np.abs(img - 1.9921875) <= 1.9921875 * 0.51)
+    assert st["segments"] <= 64 * 64 * 4 * 8
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_box_scene_parity(nrrs, mode):
+    s = I.box_scene(1)
+    P = I.rrsnet_init_params(1)
+    W = H = 64
+    spp, D = 4, 8
+    gimg, gst, gtr = gpu_render(nrrs, s, W, H, spp, D, mode, params=P)
+    oimg, ost, otr = oracle.render(s, W, H, spp, D, mode, params=P.astype(np.float64), trace=True)
+    # depth-1 queue and decisions are identical slot by slot
+    assert gst["live"][0] == ost["live"][0] == W * H * spp
+    np.testing.assert_array_equal(gtr[0][:, [0, 1, 2]], otr[0][:, [0, 1, 2]])
+    same_tri = gtr[0][:, 3] == otr[0][:, 3]
+    assert same_tri.mean() > 0.999
+    np.testing.assert_array_equal(gtr[0][same_tri, 4], otr[0][same_tri, 4])
+    compare(gimg, gtr, oimg, otr, W, H)
+    np.testing.assert_allclose(gst["F"], ost["F"], rtol=1e-6)
+
+
+def test_heuristic_with_reference_parity(nrrs):
+    """Normalised heuristic RRS with a reference image: F < 1 at every depth."""
+    s = I.box_scene(2)
+    W = H = 48
+    spp, D = 4, 8
+    ref, _, _ = oracle.render(s, W, H, 4, D, oracle.MODE_NONE, frame=9)
+    ref32 = ref.astype(np.float32)
+    gimg, gst, gtr = gpu_render(nrrs, s, W, H, spp, D, nrrs.RRS_HEUR_NORM, ref=ref32, frame=1)
+    oimg, ost, otr = oracle.render(s, W, H, spp, D, oracle.MODE_HEUR_NORM, frame=1,
+                                   pixel_ref=ref32.astype(np.float64), trace=True)
+    assert np.all(ost["F"][:-1] < 1)
+    np.testing.assert_allclose(gst["sum_q"][:2], ost["sum_q"][:2], rtol=1e-5)
+    assert gst["F"][0] == ost["F"][0]
+    compare(gimg, gtr, oimg, otr, W, H, min_match=0.98)
+
+
+def test_net_mix_gate_parity(nrrs):
+    s = I.box_scene(3)
+    P = I.rrsnet_init_params(2)
+    gate = 0
+    for d, g in enumerate([2, 0, 1, 0, 2, 1, 0, 0]):
+        gate |= g << (2 * d)
+    W = H = 40
+    gimg, gst, gtr = gpu_render(nrrs, s, W, H, 4, 8, nrrs.RRS_NET_MIX, params=P, gate=gate)
+    oimg, ost, otr = oracle.render(s, W, H, 4, 8, oracle.MODE_NET_MIX, params=P.astype(np.float64),
+                                   gate=gate, trace=True)
+    compare(gimg, gtr, oimg, otr, W, H)
+
+
+def test_overflow_and_alpha_backoff(nrrs):
+    """Tight capacity with f_rate = 1: drops happen, the queue never exceeds C, alpha
+    backs off by 0.99 per overflowing depth (Eq. f_rate_prime), like the oracle."""
+    s = I.box_scene(1)
+    W = H = 32
+    ref, _, _ = oracle.render(s, W, H, 4, 8, oracle.MODE_NONE, frame=3)
+    ref32 = ref.astype(np.float32)
+    gimg, gst, gtr = gpu_render(nrrs, s, W, H, 4, 10, nrrs.RRS_HEUR_NORM, ref=ref32, f_rate=1.0,
+                                cap_factor=1, trace=False)
+    C = W * H * 4
+    assert np.all(gst["live"] <= C)
+    assert gst["dropped"].sum() > 0 and gst["status_bits"] & nrrs.STATUS_OVERFLOW_DROPPED
+    alpha = 1.0
+    for d in range(10):
+        assert gst["alpha"][d] == pytest.approx(alpha, rel=1e-15)
+        if gst["dropped"][d] > 0:
+            alpha *= 0.99
+
+
+def test_determinism(nrrs):
+    s = I.box_scene(1)
+    P = I.rrsnet_init_params(1)
+    a, sa, _ = gpu_render(nrrs, s, 64, 64, 4, 8, nrrs.RRS_NET, params=P, trace=False)
+    b, sb, _ = gpu_render(nrrs, s, 64, 64, 4, 8, nrrs.RRS_NET, params=P, trace=False)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(sa["live"], sb["live"])
+
+
+def test_nonfinite_weights_terminate_paths(nrrs):
+    s = I.box_scene(1)
+    P = I.rrsnet_init_params(1)
+    P[2560:] = np.inf
+    img, st, _ = gpu_render(nrrs, s, 16, 16, 1, 4, nrrs.RRS_NET, params=P, trace=False)
+    assert st["nonfinite"] == 256 and st["status_bits"] & nrrs.STATUS_NONFINITE
+    assert st["live"][1:].sum() == 0 and np.all(np.isfinite(img))
+
+
+def test_full_size_occluded_room_sampled_pixels(nrrs):
+    """256 x 256 x 16 spp, depth 16, the bench workload's scene: without normalisation
+    pixels are independent, so the oracle renders sampled pixels one by one."""
+    s = I.occluded_room(1)
+    W = H = 256
+    spp, D = 16, 16
+    for mode in (nrrs.RRS_NONE, nrrs.RRS_PLAIN_RR):
+        gimg, gst, _ = gpu_render(nrrs, s, W, H, spp, D, mode, trace=False)
+        rng = np.random.default_rng(mode)
+        pix = np.sort(rng.choice(W * H, 48, replace=False)).astype(np.int32)
+        oimg, _, _ = oracle.render(s, W, H, spp, D, mode, pixels=pix)
+        g = gimg.reshape(-1, 3)[pix]
+        o = oimg.reshape(-1, 3)[pix]
+        close = np.all(np.abs(g - o) <= RTOL * np.abs(o) + 1e-30, axis=1)
+        assert close.mean() >= 0.95, close.mean()
+
+
+def test_full_size_net_properties(nrrs):
+    """Full-size NET render: counts bounded by C, requested children consistent with
+    the next queue, finite non-negative image, F within (0, 1]."""
+    s = I.occluded_room(1)
+    P = I.rrsnet_init_params(1)
+    W = H = 256
+    spp, D = 16, 16
+    img, st, _ = gpu_render(nrrs, s, W, H, spp, D, nrrs.RRS_NET, params=P, trace=False)
+    C = 2 * W * H * spp
+    assert st["capacity"] == C and np.all(st["live"] <= C)
+    for d in range(D - 1):
+        assert st["live"][d + 1] == min(st["requested"][d], C)
+    assert np.all(np.isfinite(img)) and img.min() >= 0
+    assert np.all((st["F"] > 0) & (st["F"] <= 1))
+    assert st["net_evals"] > 0 and st["segments"] == st["live"].sum()
+
+
+def test_invalid_arguments(nrrs):
+    s = nrrs.Scene(I.box_scene(1))
+    out = torch.empty((8, 8, 3), device="cuda")
+    for bad in ({"width": 0}, {"max_depth": 33}, {"mode": 7}):
+        args = dict(width=8, height=8, spp=1, max_depth=4, mode=0)
+        args.update(bad)
+        with pytest.raises(nrrs.NrrsError) as e:
+            s.render(args["width"], args["height"], args["spp"], args["max_depth"], args["mode"],
+                     out=out)
+        assert e.value.code == 1
+    with pytest.raises(nrrs.NrrsError) as e:
+        s.render(8, 8, 1, 4, nrrs.RRS_NET_MIX, out=out, gate=3)
+    assert e.value.code == 1
+    s.close()

@@ -1,0 +1,137 @@
+"""Parity of the stand-alone stage kernels with the FP64 oracle (GPU).
+
+Integer work (split counts, prefixes, compacted parents and lineages, totals, drops)
+must match bit for bit given identical FP32 inputs; the FP64 sum of the normalisation
+to 1e-12 relative and its FP32 factor exactly; RRSNet FP32 factors to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07868_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nrrs():
+    from paper_2510_07868_b300 import nrrs as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to(dtype).to("cuda")
+
+
+def _gpu_split(nrrs, q, F, pix, smp, lin, depth, seed, frame, cap):
+    n = len(q)
+    dq = _dev(q.astype(np.float32))
+    dF = _dev(np.array([F], np.float32))
+    dpix = _dev(pix.astype(np.int32).view(np.int32))
+    dsmp = _dev(smp.astype(np.int32).view(np.int32))
+    dlin = _dev(lin.view(np.int32))
+    X = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    prefix = torch.zeros(max(n, 1), dtype=torch.int64, device="cuda")
+    cp = torch.full((max(cap, 1),), -1, dtype=torch.int32, device="cuda")
+    cl = torch.zeros(max(cap, 1), dtype=torch.int32, device="cuda")
+    tot = torch.zeros(1, dtype=torch.int64, device="cuda")
+    drop = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nrrs.nrrs_split(None, dq, n, dF, dpix, dsmp, dlin, depth, seed[0], seed[1], frame, cap, X,
+                    prefix, cp, cl, tot, drop)
+    torch.cuda.synchronize()
+    S = int(tot.item())
+    m = min(S, cap)
+    return (X.cpu().numpy()[:n].view(np.uint32), prefix.cpu().numpy()[:n],
+            cp.cpu().numpy()[:m].view(np.uint32), cl.cpu().numpy()[:m].view(np.uint32), S,
+            int(drop.item()))
+
+
+@pytest.mark.parametrize("n,F,scale,capmul", [
+    (1, 1.0, 2.0, 2.0),
+    (255, 0.7, 3.0, 2.0),
+    (3 * 256 * 7 + 77, 0.85, 2.0, 2.0),   # several tiles per block and a ragged tail
+    (200_003, 0.31, 6.0, 2.0),            # many blocks
+    (50_000, 1.0, 4.0, 0.5),              # capacity overflow: drops
+])
+def test_split_bit_exact(nrrs, n, F, scale, capmul):
+    rng = np.random.default_rng(n)
+    q = I.random_q(n, seed=n, scale=scale)
+    pix = np.sort(rng.integers(0, max(1, n // 3), n)).astype(np.uint32)
+    smp = rng.integers(0, 16, n).astype(np.uint32)
+    lin = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    cap = max(1, int(capmul * n))
+    g = _gpu_split(nrrs, q, F, pix, smp, lin, 5, (7, 3), 2, cap)
+    o = oracle.split(q, np.float32(F), pix, smp, lin, 5, seed=(7, 3), frame=2, cap=cap)
+    np.testing.assert_array_equal(g[0], o[0])           # X
+    np.testing.assert_array_equal(g[1], o[1])           # prefix
+    np.testing.assert_array_equal(g[2], o[2])           # child parent
+    np.testing.assert_array_equal(g[3], o[3])           # child lineage
+    assert g[4] == o[4] and g[5] == o[5]                # total, dropped
+    if capmul < 1:
+        assert g[5] > 0
+
+
+def test_split_empty_queue(nrrs):
+    q = np.zeros(0, np.float32)
+    e = np.zeros(0, np.uint32)
+    g = _gpu_split(nrrs, q, 1.0, e, e, e, 1, (1, 0), 0, 4)
+    assert g[4] == 0 and g[5] == 0
+
+
+def test_split_integer_and_zero_factors(nrrs):
+    q = np.array([0, 1, 2, 3, 0, 5, 0.0], np.float32)
+    n = len(q)
+    ids = np.arange(n, dtype=np.uint32)
+    g = _gpu_split(nrrs, q, 1.0, ids, ids * 0, ids * 0, 1, (1, 0), 0, 64)
+    assert list(g[0]) == [0, 1, 2, 3, 0, 5, 0]
+    assert list(g[2]) == [1, 2, 2, 3, 3, 3, 5, 5, 5, 5, 5]
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 3 * 148 * 8 * 256 + 13, 4_000_000])
+def test_normalize_matches_oracle(nrrs, n):
+    q = I.random_q(n, seed=n + 1, scale=5.0)
+    dq = _dev(q) if n else torch.zeros(1, device="cuda")
+    F = torch.zeros(1, dtype=torch.float32, device="cuda")
+    s = torch.zeros(1, dtype=torch.float64, device="cuda")
+    budget = max(1.0, 0.3 * n)
+    nrrs.nrrs_normalize(None, dq, n, budget, 0.85, 0.97, F, s)
+    torch.cuda.synchronize()
+    Fo, so = oracle.normalize(q.astype(np.float64), budget, 0.85, 0.97)
+    assert abs(s.item() - so) <= 1e-12 * max(abs(so), 1.0)
+    assert np.float32(F.item()) == np.float32(Fo)
+
+
+def test_query_factors_fp32_matches_oracle(nrrs):
+    from paper_2510_07868_b300.nrrs import Scene
+
+    sc = Scene(I.box_scene(1))
+    P = I.rrsnet_init_params(3)
+    sc.set_params(P)
+    np.testing.assert_array_equal(sc.get_params(), P)
+    for n in (1, 77, 256 * 148 * 3 + 5):
+        X = I.random_features(n, seed=n)
+        q = sc.query(_dev(X)).cpu().numpy()
+        qo = oracle.mlp_forward_batch(P.astype(np.float64), X)
+        np.testing.assert_allclose(q, qo, rtol=1e-5, atol=1e-7)
+    # empty batch is a no-op
+    sc.query(torch.zeros((0, 16), device="cuda"))
+    sc.close()
+
+
+def test_query_factors_large_activations(nrrs):
+    """Large pre-activations exercise both branches of the output activation."""
+    from paper_2510_07868_b300.nrrs import Scene
+
+    sc = Scene(I.box_scene(1))
+    P = I.rrsnet_init_params(4) * 6.0
+    sc.set_params(P)
+    X = I.random_features(20000, seed=5) * 3.0
+    q = sc.query(_dev(X)).cpu().numpy()
+    qo = oracle.mlp_forward_batch(P.astype(np.float64), X.astype(np.float32))
+    np.testing.assert_allclose(q, qo, rtol=1e-5, atol=1e-6)
+    sc.close()
