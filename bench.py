@@ -57,60 +57,61 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """SM clocks and clock-event (throttle) reasons sampled through NVML every 10 ms in a
+    background thread during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
     def __init__(self, index):
         self.index = index
-        self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = None
 
     def start(self):
+        import threading
+
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
-                                          f"--query-gpu={self.Q}", "--format=csv,noheader",
-                                          "-lms", "100"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+            import pynvml
+
+            pynvml.nvmlInit()
+            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
         except Exception:
-            self.proc = None
+            return
+        self._stop = threading.Event()
+
+        def loop():
+            while not self._stop.is_set():
+                try:
+                    self.samples.append(float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)))
+                    bits = pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+                    for name, bit in self.REASONS.items():
+                        if bits & bit:
+                            self.reasons.add(name)
+                except Exception:
+                    pass
+                self._stop.wait(0.01)
+
+        self._t = threading.Thread(target=loop, daemon=True)
+        self._t.start()
 
     def stop(self):
-        if self.proc is None:
+        if self._stop is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1].split()[0]))
-                smax.append(float(parts[2].split()[0]))
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        self._stop.set()
+        self._t.join(timeout=2)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
 def traffic_from_profiles(kernel_tag):
-    """DRAM bytes per launch recorded by ncu for `kernel_tag`, if the recorded source
-    hash still matches the current kernel source (else None)."""
+    """DRAM bytes per unit (ray / slot) recorded by ncu for `kernel_tag`, if the recorded
+    source hash still matches the current kernel source (else None)."""
     src = os.path.join(ROOT, "paper_2510_07868_b300", "csrc", "wavefront.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
     for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(
@@ -118,7 +119,7 @@ def traffic_from_profiles(kernel_tag):
         if not fn.endswith((".md", ".txt")):
             continue
         for line in open(os.path.join(ROOT, "profiles", fn)):
-            m = re.match(r"traffic\s+(\S+)\s+source_sha=(\w+)\s+bytes_per_launch=([\d.]+)", line)
+            m = re.match(r"traffic\s+(\S+)\s+source_sha=(\w+)\s+bytes_per_unit=([\d.]+)", line)
             if m and m.group(1) == kernel_tag and m.group(2) == sha:
                 return float(m.group(3))
     return None
@@ -134,16 +135,15 @@ def oracle_sample(seconds_target=15.0, mode=None):
     scene = I.occluded_room(1)
     params = I.rrsnet_init_params(1).astype(np.float64)
     mode = oracle.MODE_NET if mode is None else mode
-    side = 8
-    t0 = time.perf_counter()
-    _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
-    dt = time.perf_counter() - t0
-    # grow the image until one sample takes about `seconds_target`
-    scale = max(1.0, seconds_target / max(dt, 1e-3))
-    side = int(min(W_IMG, max(8, side * np.sqrt(scale))))
-    t0 = time.perf_counter()
-    _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
-    dt = time.perf_counter() - t0
+    side = 16
+    while True:
+        t0 = time.perf_counter()
+        _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * seconds_target or side >= W_IMG:
+            break
+        # grow the image toward about `seconds_target` of work (at most 4x area per try)
+        side = int(min(W_IMG, side * min(2.0, np.sqrt(seconds_target / max(dt, 1e-3)))))
     cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
     desc = (f"occluded_room {side}x{side} px (of 256x256), 16 spp, depth 16, NET factors, "
             f"cap 2*P; {st['segments']} segments in {dt:.2f} s")
@@ -302,7 +302,9 @@ def run_ours(args, rank, world, local_rank):
     bytes_dom = alg_bytes.get(names[dom])
     per_launch_ms = stage_ms[dom] / max(1, stage_n[dom])
     achieved = (bytes_dom / (stage_ms[dom] / 1000.0) / 1e9) if bytes_dom else None
-    traffic = traffic_from_profiles(names[dom])
+    per_unit = traffic_from_profiles(names[dom])
+    units_per_launch = live_total / max(1, stage_n[dom])
+    traffic = per_unit * units_per_launch if per_unit is not None else None
     roofline = {
         "kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
@@ -346,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
