@@ -226,6 +226,28 @@ NRRS_API nrrs_status nrrs_split(nrrs_scene* scene, const float* d_q_orig, int64_
                        int64_t* d_prefix, uint32_t* d_child_parent, uint32_t* d_child_lineage,
                        int64_t* d_total, int64_t* d_dropped, void* stream);
 
+/* nrrs_split without any device allocation.  The paper has no counterpart: this
+ * exists for callers that cannot allocate device memory on the call path, such as an
+ * engine that gave all device memory to its own arena at start-up, or a frame loop
+ * that cannot afford the device-wide synchronization cudaMalloc / cudaFree may cause.
+ * Same arguments, layouts, outputs and results as nrrs_split (without `scene`); it
+ * runs on the current device.  Its per-block scratch (192 KiB) is a fixed array
+ * compiled into the library, present on every GPU that loads it until the process
+ * exits; no cudaMalloc, cudaFree or other allocating routine is called.
+ * Limit: n <= 67,108,864 parents (4096 per block, 16384 blocks); larger n returns
+ * NRRS_ERR_INVALID_ARG with a message in nrrs_last_error().
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  Every call shares the one array,
+ * so calls that overlap on the GPU (for example on two streams) race and corrupt each
+ * other's results; keep them ordered on one stream. */
+NRRS_API nrrs_status nrrs_split_noalloc(const float* d_q_orig, int64_t n, const float* d_F,
+                                        const uint32_t* d_pixel, const uint32_t* d_sample,
+                                        const uint32_t* d_lineage, uint32_t depth,
+                                        uint32_t seed_lo, uint32_t seed_hi, uint32_t frame,
+                                        int64_t cap, uint32_t* d_X, int64_t* d_prefix,
+                                        uint32_t* d_child_parent, uint32_t* d_child_lineage,
+                                        int64_t* d_total, int64_t* d_dropped, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,10 @@ nrrs_status pool_for_device(int dev, Pool** out) {
 
 }  // namespace
 
+namespace nrrs {
+nrrs_status record_error(nrrs_status s, const char* msg) { return fail(s, msg); }
+}  // namespace nrrs
+
 struct nrrs_scene {
     int device = 0;
     int n_sm = 148;

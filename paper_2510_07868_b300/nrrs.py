@@ -32,7 +32,7 @@ RRSNET_PARAMS = 2592
 EXPORTED = [
     "nrrs_status_string", "nrrs_last_error", "nrrs_create_scene", "nrrs_destroy_scene",
     "nrrs_scene_info", "nrrs_set_rrsnet_params", "nrrs_get_rrsnet_params", "nrrs_render",
-    "nrrs_query_factors", "nrrs_normalize", "nrrs_split",
+    "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
 ]
 
 
@@ -101,6 +101,8 @@ def _load():
         "nrrs_query_factors": ([P, P, I64, I32, P, P], I32),
         "nrrs_normalize": ([P, P, I64, D, D, D, P, P, P], I32),
         "nrrs_split": ([P, P, I64, P, P, P, P, U32, U32, U32, U32, I64, P, P, P, P, P, P, P], I32),
+        "nrrs_split_noalloc": ([P, I64, P, P, P, P, U32, U32, U32, U32, I64, P, P, P, P, P, P, P],
+                               I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -213,6 +215,19 @@ def nrrs_split(scene, d_q_orig, n, d_F, d_pixel, d_sample, d_lineage, depth, see
                            _ptr(d_lineage), depth, seed_lo, seed_hi, frame, cap, _ptr(d_X),
                            _ptr(d_prefix), _ptr(d_child_parent), _ptr(d_child_lineage),
                            _ptr(d_total), _ptr(d_dropped), _stream(stream)))
+
+
+def nrrs_split_noalloc(d_q_orig, n, d_F, d_pixel, d_sample, d_lineage, depth, seed_lo, seed_hi,
+                       frame, cap, d_X, d_prefix, d_child_parent, d_child_lineage, d_total,
+                       d_dropped, stream=None):
+    """nrrs_split for callers that cannot allocate device memory on the call path; its
+    scratch is a fixed array inside the library (n <= 67,108,864).  Runs on the current
+    device; the first call on a device must precede any stream capture."""
+    _check(_lib.nrrs_split_noalloc(_ptr(d_q_orig), n, _ptr(d_F), _ptr(d_pixel), _ptr(d_sample),
+                                   _ptr(d_lineage), depth, seed_lo, seed_hi, frame, cap,
+                                   _ptr(d_X), _ptr(d_prefix), _ptr(d_child_parent),
+                                   _ptr(d_child_lineage), _ptr(d_total), _ptr(d_dropped),
+                                   _stream(stream)))
 
 
 # ------------------------------------------------------------------ convenience wrapper
