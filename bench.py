@@ -69,6 +69,7 @@ class ClockSampler:
         self.reasons = set()
         self.max_mhz = None
         self._stop = None
+        self.error = None
 
     def start(self):
         import threading
@@ -79,7 +80,8 @@ class ClockSampler:
             pynvml.nvmlInit()
             h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
             self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
-        except Exception:
+        except Exception as e:  # reported in the JSON line
+            self.error = f"{type(e).__name__}: {e}"
             return
         self._stop = threading.Event()
 
@@ -91,8 +93,8 @@ class ClockSampler:
                     for name, bit in self.REASONS.items():
                         if bits & bit:
                             self.reasons.add(name)
-                except Exception:
-                    pass
+                except Exception as e:
+                    self.error = f"{type(e).__name__}: {e}"
                 self._stop.wait(0.01)
 
         self._t = threading.Thread(target=loop, daemon=True)
@@ -100,11 +102,13 @@ class ClockSampler:
 
     def stop(self):
         if self._stop is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "error": self.error}
         self._stop.set()
         self._t.join(timeout=2)
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"],
+                    "error": self.error}
         return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
                 "reasons": sorted(self.reasons), "samples": len(self.samples)}
 

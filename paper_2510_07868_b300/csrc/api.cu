@@ -55,13 +55,15 @@ cudaError_t dalloc(T** p, size_t count) {
 
 struct Workspace {
     long long cap = 0, npix = 0;
-    int grid_extend_max = 0, grid_split = 0;
+    int grid_red = 0, grid_split = 0;
+    bool has_feat = false;
     float4* qo[2] = {nullptr, nullptr};
     float4* qd[2] = {nullptr, nullptr};
     float4* qt[2] = {nullptr, nullptr};
     float2* hit = nullptr;
     float* q = nullptr;
     float4* dep = nullptr;
+    float4* feat = nullptr;
     double* part = nullptr;
     unsigned int* bcnt = nullptr;
     unsigned long long* boff = nullptr;
@@ -76,9 +78,10 @@ struct Workspace {
             cudaFree(qt[k]);
             qo[k] = qd[k] = qt[k] = nullptr;
         }
-        cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(part); cudaFree(bcnt);
+        cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(feat); cudaFree(part); cudaFree(bcnt);
         cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st);
-        hit = nullptr; q = nullptr; dep = nullptr; part = nullptr; bcnt = nullptr;
+        hit = nullptr; q = nullptr; dep = nullptr; feat = nullptr; part = nullptr; bcnt = nullptr;
+        has_feat = false;
         boff = nullptr; acc_s = acc_c = nullptr; st = nullptr;
         cap = npix = 0;
     }
@@ -131,6 +134,7 @@ struct nrrs_scene {
     CamView cam{};
     Workspace ws;
     int grid_extend[4] = {0, 0, 0, 0};
+    int grid_rrsnet = 0, grid_sum = 0;
     // running mean of earlier frames (HEUR reference), [npix * 3]
     float* ref_mean = nullptr;
     int ref_count = 0;
@@ -140,9 +144,15 @@ struct nrrs_scene {
 
 namespace {
 
-nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix) {
+nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool need_feat) {
     Workspace& w = sc->ws;
-    if (w.cap >= cap && w.npix >= npix && w.st) return NRRS_OK;
+    if (w.cap >= cap && w.npix >= npix && w.st) {
+        if (need_feat && !w.has_feat) {
+            CK(dalloc(&w.feat, (size_t)w.cap * 4));
+            w.has_feat = true;
+        }
+        return NRRS_OK;
+    }
     w.release();
     for (int k = 0; k < 2; ++k) {
         CK(dalloc(&w.qo[k], cap));
@@ -152,11 +162,13 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix) {
     CK(dalloc(&w.hit, cap));
     CK(dalloc(&w.q, cap));
     CK(dalloc(&w.dep, cap));
-    w.grid_extend_max = 0;
-    for (int k = 0; k < 4; ++k)
-        w.grid_extend_max = sc->grid_extend[k] > w.grid_extend_max ? sc->grid_extend[k] : w.grid_extend_max;
+    if (need_feat) {
+        CK(dalloc(&w.feat, (size_t)cap * 4));
+        w.has_feat = true;
+    }
+    w.grid_red = sc->grid_sum;
     w.grid_split = sc->n_sm * 8;
-    CK(dalloc(&w.part, w.grid_extend_max));
+    CK(dalloc(&w.part, w.grid_red));
     CK(dalloc(&w.bcnt, w.grid_split));
     CK(dalloc(&w.boff, w.grid_split));
     CK(dalloc(&w.acc_s, npix));
@@ -318,6 +330,8 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     s->cam.up[0] = (float)up2.x; s->cam.up[1] = (float)up2.y; s->cam.up[2] = (float)up2.z;
     s->cam.tan_half = (float)std::tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0);
     for (int k = 0; k < 4; ++k) s->grid_extend[k] = s->n_sm * max_blocks_extend(k);
+    s->grid_rrsnet = s->n_sm * max_blocks_rrsnet();
+    s->grid_sum = s->n_sm * 4;
     *out = s;
     return NRRS_OK;
 }
@@ -383,7 +397,11 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     DeviceGuard g(scene->device);
     if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
-    nrrs_status rc = ensure_workspace(scene, C, npix);
+    bool uses_net = rrs_mode == NRRS_RRS_NET;
+    if (rrs_mode == NRRS_RRS_NET_MIX)
+        for (int d = 1; d <= max_depth; ++d)
+            if (factor_kind(rrs_mode, o.gate, d) == kFactorNet) uses_net = true;
+    nrrs_status rc = ensure_workspace(scene, C, npix, uses_net);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
 
@@ -434,14 +452,21 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
     TIMED(NRRS_STAGE_INIT, launch_camera(scene->cam, rp, q[0], s));
     WorkView w{};
-    w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.part = ws.part;
+    w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.feat = ws.feat; w.part = ws.part;
+    w.grid_red = ws.grid_red;
     w.bcnt = ws.bcnt; w.boff = ws.boff; w.grid_split = ws.grid_split;
     w.acc_s = ws.acc_s; w.acc_c = ws.acc_c; w.st = ws.st;
     int cur = 0;
     for (int d = 1; d <= max_depth; ++d) {
         const int kind = factor_kind(rrs_mode, o.gate, d);
-        w.grid_extend = scene->grid_extend[kind];
-        TIMED(NRRS_STAGE_EXTEND, launch_extend(kind, scene->view, q[cur], w, rp, d, s));
+        TIMED(NRRS_STAGE_EXTEND,
+              launch_extend(kind, scene->view, q[cur], w, rp, d, scene->grid_extend[kind], s));
+        if (kind == kFactorNet) {
+            WorkView wn = w;
+            wn.grid_red = scene->grid_rrsnet;
+            TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_depth(wn, rp, d, s));
+        }
+        TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
         TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, rp, d, normalized, s));
         const int do_split = d < max_depth;
         TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, rp, d, do_split, s));

@@ -51,11 +51,12 @@ struct Prim {
 
 constexpr int kBins = 16;
 constexpr int kLeafMax = 4;
-constexpr int kMaxBuildDepth = 60;  // traversal stack holds 64 entries
+constexpr int kMaxBuildDepth = 38;  // traversal stack holds 40 entries
 
 struct Builder {
     std::vector<Prim>& prims;
     std::vector<BvhNode>& nodes;
+    float pad;  // boxes grow by this much so FP32 slab tests never cut off a hit
 
     // Returns the child encoding for prims[begin, end) and its bounds.
     int32_t build(int32_t begin, int32_t end, int depth, Box* out_box, int32_t* out_count) {
@@ -127,9 +128,18 @@ struct Builder {
         int32_t lc = 0, rc = 0;
         int32_t l = build(begin, mid, depth + 1, &lb, &lc);
         int32_t r = build(mid, end, depth + 1, &rb, &rc);
-        fill(nodes[self], lb, l, lc, rb, r, rc);
+        fill(nodes[self], inflate(lb), l, lc, inflate(rb), r, rc);
         *out_count = 0;
         return self;
+    }
+
+    Box inflate(Box b) const {
+        if (b.empty()) return b;
+        for (int k = 0; k < 3; ++k) {
+            b.lo[k] -= pad;
+            b.hi[k] += pad;
+        }
+        return b;
     }
 
     static void fill(BvhNode& nd, const Box& l, int32_t lc, int32_t ln, const Box& r, int32_t rcode,
@@ -154,7 +164,11 @@ void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* 
         p.id = i;
     }
     out->nodes.clear();
-    Builder bld{prims, out->nodes};
+    Box all;
+    for (const Prim& p : prims) all.grow(p.box);
+    float ext = 0.0f;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, all.hi[k] - all.lo[k]);
+    Builder bld{prims, out->nodes, 1e-5f * ext + 1e-30f};
     Box root_box;
     int32_t root_count = 0;
     int32_t root = bld.build(0, n_tri, 0, &root_box, &root_count);
@@ -162,7 +176,7 @@ void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* 
         // whole scene is one leaf: make a root whose second child is empty
         out->nodes.emplace_back();
         Box empty;
-        Builder::fill(out->nodes[0], root_box, root, root_count, empty, ~0, 0);
+        Builder::fill(out->nodes[0], bld.inflate(root_box), root, root_count, empty, ~0, 0);
     }
     out->tris.assign((size_t)n_tri * 12, 0.0f);
     for (int32_t s = 0; s < n_tri; ++s) {

@@ -15,7 +15,8 @@ namespace {
 constexpr int kExtendThreads = 256;
 constexpr int kSplitThreads = 256;
 constexpr int kReduceThreads = 1024;
-constexpr int kStack = 64;
+constexpr int kStack = 40;        // BVH build depth is capped below this
+constexpr int kSteps = 12;        // node visits between ray fetch rounds
 constexpr uint32_t kMaxX = 1u << 23;  // q_used >= 2^23 has no fractional part in FP32
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
@@ -28,82 +29,89 @@ struct Hit {
     uint32_t id;   // original triangle index (tie-break)
 };
 
-// Closest hit along o + t d, t > 0.  Equal distances go to the lower original
-// triangle index, so the answer does not depend on the traversal order.
-__device__ __forceinline__ Hit trace_closest(const SceneView& sc, V3 o, V3 d) {
-    const V3 inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    const V3 oi = v3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
-    Hit h{FLT_MAX, -1, 0xFFFFFFFFu};
-    int stack[kStack];
-    int sp = 0;
-    int cur = 0;
-    for (;;) {
-        const float4 a = __ldg(&sc.nodes[4 * cur + 0]);
-        const float4 b = __ldg(&sc.nodes[4 * cur + 1]);
-        const float4 c = __ldg(&sc.nodes[4 * cur + 2]);
-        const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * cur + 3]));
-        // child 0
-        float lx = fmaf(a.x, inv.x, -oi.x), hx = fmaf(a.y, inv.x, -oi.x);
-        float ly = fmaf(a.z, inv.y, -oi.y), hy = fmaf(a.w, inv.y, -oi.y);
-        float lz = fmaf(c.x, inv.z, -oi.z), hz = fmaf(c.y, inv.z, -oi.z);
-        float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-        float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-        bool h0 = t0n <= t0f;
-        // child 1
-        lx = fmaf(b.x, inv.x, -oi.x); hx = fmaf(b.y, inv.x, -oi.x);
-        ly = fmaf(b.z, inv.y, -oi.y); hy = fmaf(b.w, inv.y, -oi.y);
-        lz = fmaf(c.z, inv.z, -oi.z); hz = fmaf(c.w, inv.z, -oi.z);
-        float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-        float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-        bool h1 = t1n <= t1f;
-        int c0 = e.x, c1 = e.y;
+// One ray's traversal state.  The stack lives in shared memory, one column per thread
+// (entry k at stk[k * stride]) so that lanes hit different banks.
+struct Ray {
+    V3 o, d, inv, oi;
+    int node, sp;
+};
+
+__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, Hit& h) {
+    r.o = o;
+    r.d = d;
+    r.inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    r.node = 0;
+    r.sp = 0;
+    h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
+}
+
+// Visits one BVH2 node of the closest-hit query along o + t d (t > 0): both child boxes
+// are tested, leaf children are intersected at once (Moller-Trumbore), inner children
+// are visited near-first.  Equal distances go to the lower original triangle index, so
+// the answer does not depend on the visiting order.  Returns true when the query ends.
+__device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, int* stk,
+                                           int stride) {
+    const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
+    const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
+    const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
+    const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
+    float lx = fmaf(a.x, r.inv.x, -r.oi.x), hx = fmaf(a.y, r.inv.x, -r.oi.x);
+    float ly = fmaf(a.z, r.inv.y, -r.oi.y), hy = fmaf(a.w, r.inv.y, -r.oi.y);
+    float lz = fmaf(c.x, r.inv.z, -r.oi.z), hz = fmaf(c.y, r.inv.z, -r.oi.z);
+    const float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+    const float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+    bool h0 = t0n <= t0f;
+    lx = fmaf(b.x, r.inv.x, -r.oi.x); hx = fmaf(b.y, r.inv.x, -r.oi.x);
+    ly = fmaf(b.z, r.inv.y, -r.oi.y); hy = fmaf(b.w, r.inv.y, -r.oi.y);
+    lz = fmaf(c.z, r.inv.z, -r.oi.z); hz = fmaf(c.w, r.inv.z, -r.oi.z);
+    const float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+    const float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+    bool h1 = t1n <= t1f;
+    int c0 = e.x, c1 = e.y;
 #pragma unroll 1
-        for (int side = 0; side < 2; ++side) {
-            const int code = side ? c1 : c0;
-            const bool hitbox = side ? h1 : h0;
-            if (!hitbox || code >= 0) continue;
-            const int first = ~code, count = side ? e.w : e.z;
-            for (int k = 0; k < count; ++k) {
-                const int s = first + k;
-                const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
-                const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
-                const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
-                const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
-                const V3 pv = cross3(d, e2);
-                const float det = dot3(e1, pv);
-                if (det == 0.0f) continue;
-                const float idet = 1.0f / det;
-                const V3 tv = o - v0;
-                const float u = dot3(tv, pv) * idet;
-                if (u < 0.0f || u > 1.0f) continue;
-                const V3 qv = cross3(tv, e1);
-                const float v = dot3(d, qv) * idet;
-                if (v < 0.0f || u + v > 1.0f) continue;
-                const float t = dot3(e2, qv) * idet;
-                const uint32_t id = fbits(t0.w);
-                if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
-                    h.t = t;
-                    h.slot = s;
-                    h.id = id;
-                }
+    for (int side = 0; side < 2; ++side) {
+        const int code = side ? c1 : c0;
+        const bool hitbox = side ? h1 : h0;
+        if (!hitbox || code >= 0) continue;
+        const int first = ~code, count = side ? e.w : e.z;
+        for (int k = 0; k < count; ++k) {
+            const int s = first + k;
+            const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
+            const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
+            const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
+            const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
+            const V3 pv = cross3(r.d, e2);
+            const float det = dot3(e1, pv);
+            if (det == 0.0f) continue;
+            const float idet = 1.0f / det;
+            const V3 tv = r.o - v0;
+            const float u = dot3(tv, pv) * idet;
+            if (u < 0.0f || u > 1.0f) continue;
+            const V3 qv = cross3(tv, e1);
+            const float v = dot3(r.d, qv) * idet;
+            if (v < 0.0f || u + v > 1.0f) continue;
+            const float t = dot3(e2, qv) * idet;
+            const uint32_t id = fbits(t0.w);
+            if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
+                h.t = t;
+                h.slot = s;
+                h.id = id;
             }
-            if (side) h1 = false; else h0 = false;
         }
-        if (h0 && h1) {
-            if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
-            if (sp < kStack) stack[sp++] = c1;
-            cur = c0;
-        } else if (h0) {
-            cur = c0;
-        } else if (h1) {
-            cur = c1;
-        } else {
-            if (sp == 0) break;
-            cur = stack[--sp];
-        }
+        if (side) h1 = false; else h0 = false;
     }
-    if (h.slot < 0) h.t = FLT_MAX;
-    return h;
+    if (h0 && h1) {
+        if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
+        if (r.sp < kStack) stk[(r.sp++) * stride] = c1;
+        r.node = c0;
+        return false;
+    }
+    if (h0) { r.node = c0; return false; }
+    if (h1) { r.node = c1; return false; }
+    if (r.sp == 0) return true;
+    r.node = stk[(--r.sp) * stride];
+    return false;
 }
 
 __device__ __forceinline__ V3 tri_geom_normal(const SceneView& sc, int slot, int* mat) {
@@ -320,34 +328,66 @@ __global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
     out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
 }
 
-// Extension of depth `depth`: closest hit, emission deposit, RRS factor q_orig and the
-// block's FP64 partial sum of q (persistent grid-stride loop; fixed assignment, so the
-// sum is reproducible).
+// Extension of depth `depth`: closest hit, emission deposit, and the RRS factor q_orig
+// (NET depths store the 16 features and q = -1; k_rrsnet_fp32 fills q).  Persistent
+// warps fetch rays dynamically: a lane whose query has ended finishes that ray and takes
+// the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
+// Every slot's outputs depend only on that slot, so the result is deterministic.
 template <int KIND>
-__global__ void __launch_bounds__(kExtendThreads)
+__global__ void __launch_bounds__(kExtendThreads, 4)
 k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
-    __shared__ __align__(16) float sW[KIND == kFactorNet ? kNParams : 4];
-    __shared__ double sh[32];
-    if (KIND == kFactorNet) load_weights_smem(sW, rp.params);
+    __shared__ int s_stack[kStack * kExtendThreads];
+    int* stk = s_stack + threadIdx.x;
     DevStats* st = w.st;
     const long long n = st->live[depth - 1];
+    unsigned long long* ctr = &st->fetch[depth - 1];
     const int has_ref = st->has_ref;
     const float eps_I = st->eps_I;
-    double qsum = 0.0;
-    unsigned int nonfinite = 0, evals = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float4 o4 = cur.o[i];
-        const float4 d4 = cur.d[i];
-        const float4 t4 = cur.t[i];
-        const V3 o = xyz(o4), d = xyz(d4);
-        const Hit h = trace_closest(sc, o, d);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned int nonfinite = 0;
+    long long idx = -1;
+    bool exhausted = false;
+    Ray ray;
+    Hit h;
+    float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t pix = 0;
+    for (;;) {
+        const bool need = idx < 0 && !exhausted;
+        const unsigned need_mask = __ballot_sync(0xffffffffu, need);
+        if (need_mask) {
+            const int leader = __ffs(need_mask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(need_mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const long long my = (long long)base + __popc(need_mask & lt_mask);
+                if (my < n) {
+                    idx = my;
+                    const float4 o4 = cur.o[idx];
+                    const float4 d4 = cur.d[idx];
+                    t4 = cur.t[idx];
+                    pix = fbits(o4.w);
+                    ray_init(ray, xyz(o4), xyz(d4), h);
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, idx < 0)) break;
+        if (idx < 0) continue;
+        bool done = false;
+        for (int step = 0; step < kSteps && !done; ++step)
+            done = visit_node(sc, ray, h, stk, kExtendThreads);
+        if (!done) continue;
+        // ---- the query of slot idx has ended: shade it
         float q = 0.0f;
-        float4 dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
+        float4 dep = make_float4(0.0f, 0.0f, 0.0f, bitsf(pix));
         if (h.slot >= 0) {
             int mi;
             const V3 ng = tri_geom_normal(sc, h.slot, &mi);
             const nrrs_material m = sc.mats[mi];
+            const V3 d = ray.d;
             const bool front = dot3(ng, d) < 0.0f;
             if (front || m.two_sided) {
                 dep.x = t4.x * m.Le[0];
@@ -366,50 +406,91 @@ k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     if (!has_ref) {
                         q = l;
                     } else {
-                        const uint32_t pix = fbits(o4.w);
-                        const float* r = rp.ref + 3 * (size_t)pix;
-                        const float den = fmaxf((r[0] + r[1] + r[2]) / 3.0f, eps_I);
+                        const float* rr = rp.ref + 3 * (size_t)pix;
+                        const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
                         q = den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
                     }
                 } else {
-                    const V3 p = o + d * h.t;
+                    const V3 p = ray.o + d * h.t;
                     const V3 ns = front ? ng : ng * -1.0f;
-                    float x[kNF];
-                    x[0] = sc.inv_ext[0] > 0.0f ? (p.x - sc.lo[0]) * sc.inv_ext[0] : 0.5f;
-                    x[1] = sc.inv_ext[1] > 0.0f ? (p.y - sc.lo[1]) * sc.inv_ext[1] : 0.5f;
-                    x[2] = sc.inv_ext[2] > 0.0f ? (p.z - sc.lo[2]) * sc.inv_ext[2] : 0.5f;
-                    x[3] = -d.x; x[4] = -d.y; x[5] = -d.z;
-                    x[6] = ns.x; x[7] = ns.y; x[8] = ns.z;
-                    x[9] = m.albedo[0]; x[10] = m.albedo[1]; x[11] = m.albedo[2];
-                    x[12] = (float)depth / (float)rp.D;
-                    x[13] = boxcox(t4.x, rp.boxcox_lambda);
-                    x[14] = boxcox(t4.y, rp.boxcox_lambda);
-                    x[15] = boxcox(t4.z, rp.boxcox_lambda);
-                    q = rrsnet_forward(sW, x);
-                    ++evals;
+                    float4* f = w.feat + 4 * idx;
+                    f[0] = make_float4(
+                        sc.inv_ext[0] > 0.0f ? (p.x - sc.lo[0]) * sc.inv_ext[0] : 0.5f,
+                        sc.inv_ext[1] > 0.0f ? (p.y - sc.lo[1]) * sc.inv_ext[1] : 0.5f,
+                        sc.inv_ext[2] > 0.0f ? (p.z - sc.lo[2]) * sc.inv_ext[2] : 0.5f, -d.x);
+                    f[1] = make_float4(-d.y, -d.z, ns.x, ns.y);
+                    f[2] = make_float4(ns.z, m.albedo[0], m.albedo[1], m.albedo[2]);
+                    f[3] = make_float4((float)depth / (float)rp.D, boxcox(t4.x, rp.boxcox_lambda),
+                                       boxcox(t4.y, rp.boxcox_lambda),
+                                       boxcox(t4.z, rp.boxcox_lambda));
+                    q = -1.0f;  // filled by the RRSNet kernel
                 }
-                if (!(q >= 0.0f && q <= FLT_MAX)) {  // NaN, Inf or negative
+                if (KIND != kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {
                     q = 0.0f;
                     ++nonfinite;
                 }
             }
         }
-        w.hit[i] = make_float2(h.t, __int_as_float(h.slot));
-        w.q[i] = q;
-        w.dep[i] = dep;
-        qsum += (double)q;
-    }
-    qsum = block_sum(qsum, sh);
-    if (threadIdx.x == 0) w.part[blockIdx.x] = qsum;
-    if (KIND == kFactorNet) {
-        evals = warp_sum(evals);
-        if ((threadIdx.x & 31) == 0 && evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
+        w.q[idx] = q;
+        w.dep[idx] = dep;
+        idx = -1;
     }
     nonfinite = warp_sum(nonfinite);
-    if ((threadIdx.x & 31) == 0 && nonfinite) {
+    if (lane == 0 && nonfinite) {
         atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
         atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
     }
+}
+
+// RRSNet (FP32 SIMT) on the slots the extension marked with q = -1.
+__global__ void __launch_bounds__(256, 2)
+k_rrsnet_fp32(WorkView w, const float* __restrict__ params, int depth) {
+    __shared__ __align__(16) float sW[kNParams];
+    load_weights_smem(sW, params);
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    unsigned int evals = 0, nonfinite = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (w.q[i] < 0.0f) {
+            const float4* f = w.feat + 4 * i;
+            float x[kNF];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = __ldg(f + k);
+                x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+            }
+            float q = rrsnet_forward(sW, x);
+            ++evals;
+            if (!(q >= 0.0f && q <= FLT_MAX)) {
+                q = 0.0f;
+                ++nonfinite;
+            }
+            w.q[i] = q;
+        }
+    }
+    evals = warp_sum(evals);
+    nonfinite = warp_sum(nonfinite);
+    if ((threadIdx.x & 31) == 0) {
+        if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+        if (nonfinite) {
+            atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+            atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+        }
+    }
+}
+
+// FP64 partial sums of q over a fixed grid-stride assignment, so Sigma q is reproducible.
+__global__ void __launch_bounds__(256) k_sum_q(WorkView w, int depth) {
+    __shared__ double sh[32];
+    const long long n = w.st->live[depth - 1];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s += (double)w.q[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) w.part[blockIdx.x] = s;
 }
 
 // Eq. F_norm / q_norm_rate / f_rate_prime, downscale only:
@@ -418,7 +499,7 @@ __global__ void k_normalize_depth(WorkView w, RenderParams rp, int depth, int no
     __shared__ double sh[32];
     DevStats* st = w.st;
     double s = 0.0;
-    for (int b = threadIdx.x; b < w.grid_extend; b += blockDim.x) s += w.part[b];
+    for (int b = threadIdx.x; b < w.grid_red; b += blockDim.x) s += w.part[b];
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
         const double alpha = st->alpha_cur;
@@ -645,7 +726,7 @@ __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
 }
 
 // ------------------------------------------------------------------ plain-array entry points
-__global__ void __launch_bounds__(256) k_query(const float* __restrict__ params,
+__global__ void __launch_bounds__(256, 2) k_query(const float* __restrict__ params,
                                                const float* __restrict__ feat, long long n,
                                                float* __restrict__ q) {
     __shared__ __align__(16) float sW[kNParams];
@@ -771,6 +852,12 @@ int max_blocks_extend(int kind) {
     return nb < 1 ? 1 : nb;
 }
 
+int max_blocks_rrsnet() {
+    int nb = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rrsnet_fp32, 256, 0);
+    return nb < 1 ? 1 : nb;
+}
+
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0, long long P,
                         DevStats* st, cudaStream_t s) {
     k_ref_prepare<<<1, kReduceThreads, 0, s>>>(ref, n3, eps_rel, alpha0, P, st);
@@ -783,14 +870,22 @@ void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cu
 }
 
 void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
-                   const RenderParams& rp, int depth, cudaStream_t s) {
-    const int G = w.grid_extend;
+                   const RenderParams& rp, int depth, int grid, cudaStream_t s) {
+    const int G = grid;
     switch (kind) {
         case kFactorOne: k_extend<kFactorOne><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
         case kFactorPlain: k_extend<kFactorPlain><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
         case kFactorHeur: k_extend<kFactorHeur><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
         default: k_extend<kFactorNet><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
     }
+}
+
+void launch_rrsnet_depth(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
+    k_rrsnet_fp32<<<w.grid_red, 256, 0, s>>>(w, rp.params, depth);
+}
+
+void launch_sum_q(const WorkView& w, int depth, cudaStream_t s) {
+    k_sum_q<<<w.grid_red, 256, 0, s>>>(w, depth);
 }
 
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,

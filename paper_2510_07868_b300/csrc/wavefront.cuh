@@ -37,6 +37,7 @@ struct DevStats {
     long long requested[kMaxDepth];
     long long dropped[kMaxDepth];
     float F[kMaxDepth];
+    unsigned long long fetch[kMaxDepth];  // dynamic ray-fetch counters of k_extend
     unsigned long long nonfinite;
     unsigned long long net_evals;
     double alpha_cur;               // adaptive alpha (Eq. f_rate_prime), carried over depths
@@ -51,8 +52,9 @@ struct WorkView {
     float2* hit;       // [C] (distance, BVH triangle slot bits; -1 = miss)
     float* q;          // [C] q_orig
     float4* dep;       // [C] (deposited radiance rgb, pixel bits)
-    double* part;      // [grid_extend] partial sums of q
-    int grid_extend;
+    float4* feat;      // [C][4] RRSNet features (NET depths)
+    double* part;      // [grid_red] partial sums of q
+    int grid_red;      // blocks of the kernel that produced `part` at this depth
     unsigned int* bcnt;  // [grid_split] children per block
     unsigned long long* boff;  // [grid_split] exclusive prefix of bcnt
     int grid_split;
@@ -78,12 +80,15 @@ enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFact
 int extend_block_threads();
 int split_block_threads();
 int max_blocks_extend(int kind);  // resident blocks per SM
+int max_blocks_rrsnet();
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
                         long long P, DevStats* st, cudaStream_t s);
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
 void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
-                   const RenderParams& rp, int depth, cudaStream_t s);
+                   const RenderParams& rp, int depth, int grid, cudaStream_t s);
+void launch_rrsnet_depth(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
+void launch_sum_q(const WorkView& w, int depth, cudaStream_t s);
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
                             cudaStream_t s);
 void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,

@@ -23,9 +23,9 @@ RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
 GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
 STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 MAX_DEPTH = 32
-STAGES = 7
+STAGES = 8
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
-               "finalize"]
+               "finalize", "rrsnet"]
 N_FEATURES = 16
 RRSNET_PARAMS = 2592
 
