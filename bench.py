@@ -57,21 +57,28 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """SM clocks and clock-event (throttle) reasons sampled through NVML every 10 ms in a
-    background thread during the timed region."""
+    """SM clocks and clock-event (throttle) reasons during the timed region: NVML in a
+    background thread when pynvml is importable, else an `nvidia-smi -lms 50` subprocess
+    started before the warm-up and filtered to the timed window by timestamp."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
+    SMI_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.samples = []
         self.reasons = set()
         self.max_mhz = None
-        self._stop = None
         self.error = None
+        self._stop = None
+        self._proc = None
+        self._t0 = self._t1 = None
 
-    def start(self):
+    def launch(self):
+        """Start sampling (call before the warm-up so samples exist when timing starts)."""
         import threading
 
         try:
@@ -80,19 +87,19 @@ class ClockSampler:
             pynvml.nvmlInit()
             h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
             self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
-        except Exception as e:  # reported in the JSON line
-            self.error = f"{type(e).__name__}: {e}"
+        except Exception as e:
+            self.error = f"pynvml: {type(e).__name__}"
+            self._launch_smi()
             return
         self._stop = threading.Event()
 
         def loop():
             while not self._stop.is_set():
                 try:
-                    self.samples.append(float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)))
+                    now = time.time()
+                    mhz = float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM))
                     bits = pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(h)
-                    for name, bit in self.REASONS.items():
-                        if bits & bit:
-                            self.reasons.add(name)
+                    self.samples.append((now, mhz, bits))
                 except Exception as e:
                     self.error = f"{type(e).__name__}: {e}"
                 self._stop.wait(0.01)
@@ -100,17 +107,79 @@ class ClockSampler:
         self._t = threading.Thread(target=loop, daemon=True)
         self._t.start()
 
+    def _launch_smi(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self._path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.index}.csv")
+            self._f = open(self._path, "w")
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.SMI_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self._f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(1.0)  # first samples before the timed region
+        except Exception as e:
+            self.error = (self.error or "") + f"; nvidia-smi: {type(e).__name__}"
+            self._proc = None
+
+    def start(self):
+        self._t0 = time.time()
+
     def stop(self):
-        if self._stop is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
-                    "error": self.error}
-        self._stop.set()
-        self._t.join(timeout=2)
-        if not self.samples:
+        self._t1 = time.time()
+        if self._stop is not None:
+            self._stop.set()
+            self._t.join(timeout=2)
+            names = {b: n for n, b in self.REASONS.items()}
+            sm = []
+            for t, mhz, bits in self.samples:
+                if self._t0 - 0.05 <= t <= self._t1 + 0.05:
+                    sm.append(mhz)
+                    for b, n in names.items():
+                        if bits & b:
+                            self.reasons.add(n)
+            return self._summary(sm)
+        if self._proc is not None:
+            time.sleep(0.2)
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+            self._f.close()
+            return self._parse_smi()
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                "error": self.error}
+
+    def _parse_smi(self):
+        import datetime
+
+        sm, smax = [], []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self._path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                mhz, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            if not (self._t0 - 0.1 <= ts <= self._t1 + 0.1):
+                continue
+            sm.append(mhz)
+            smax.append(mx)
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    self.reasons.add(name)
+        self.max_mhz = max(smax) if smax else None
+        return self._summary(sm)
+
+    def _summary(self, sm):
+        if not sm:
             return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"],
                     "error": self.error}
-        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(sm)}
 
 
 def traffic_from_profiles(kernel_tag):
@@ -216,11 +285,11 @@ def run_ours(args, rank, world, local_rank):
                                 nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi,
                                                          profile=profile), out, stream, True)
 
+    clocks = ClockSampler(local_rank)
+    clocks.launch()
     for k in range(args.warmup):
         render(k)
     torch.cuda.synchronize()
-
-    clocks = ClockSampler(local_rank)
     clocks.start()
     if dist:
         dist.barrier()

@@ -121,14 +121,15 @@ typedef struct nrrs_render_opts {
 
 /* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
 #define NRRS_STAGE_INIT 0      /* reference mean + camera rays                      */
-#define NRRS_STAGE_EXTEND 1    /* traversal, emission deposit, RRS factor / features */
+#define NRRS_STAGE_EXTEND 1    /* BVH traversal: closest hit per live ray           */
 #define NRRS_STAGE_NORMALIZE 2 /* FP64 sum of q, F                                  */
 #define NRRS_STAGE_COUNT 3     /* split counts per block + per-pixel accumulation   */
 #define NRRS_STAGE_SCAN 4      /* block offsets, next queue length, alpha           */
 #define NRRS_STAGE_SCATTER 5   /* children + BSDF sampling into the next queue      */
 #define NRRS_STAGE_FINALIZE 6  /* frame estimate + running reference                */
 #define NRRS_STAGE_RRSNET 7    /* RRSNet (FP32) on the NET depths' features         */
-#define NRRS_N_STAGES 8
+#define NRRS_STAGE_SHADE 8     /* emission deposit, RRS factor or features, sum q   */
+#define NRRS_N_STAGES 9
 
 /* Per-render statistics; filled only when a non-NULL pointer is passed (the call then
  * synchronizes `stream`).  Index d-1 holds depth d (1-based, camera hit = depth 1). */
@@ -145,8 +146,8 @@ typedef struct nrrs_render_stats {
     int64_t capacity;                  /* C                                             */
     uint32_t status_bits;              /* NRRS_STATUS_* seen during the render          */
     uint32_t kernel_launches;          /* kernels this render launched                  */
-    float stage_ms[8];                 /* opts->profile: summed event time per stage    */
-    int32_t stage_launches[8];         /* opts->profile: launches per stage             */
+    float stage_ms[12];                /* opts->profile: summed event time per stage    */
+    int32_t stage_launches[12];        /* opts->profile: launches per stage             */
 } nrrs_render_stats;
 
 NRRS_API const char* nrrs_status_string(nrrs_status s);

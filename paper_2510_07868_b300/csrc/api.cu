@@ -133,8 +133,7 @@ struct nrrs_scene {
     SceneView view{};
     CamView cam{};
     Workspace ws;
-    int grid_extend[4] = {0, 0, 0, 0};
-    int grid_rrsnet = 0, grid_sum = 0;
+    int grid_trace = 0, grid_rrsnet = 0, grid_sum = 0;
     // running mean of earlier frames (HEUR reference), [npix * 3]
     float* ref_mean = nullptr;
     int ref_count = 0;
@@ -329,7 +328,7 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     s->cam.right[0] = (float)right.x; s->cam.right[1] = (float)right.y; s->cam.right[2] = (float)right.z;
     s->cam.up[0] = (float)up2.x; s->cam.up[1] = (float)up2.y; s->cam.up[2] = (float)up2.z;
     s->cam.tan_half = (float)std::tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0);
-    for (int k = 0; k < 4; ++k) s->grid_extend[k] = s->n_sm * max_blocks_extend(k);
+    s->grid_trace = s->n_sm * max_blocks_trace();
     s->grid_rrsnet = s->n_sm * max_blocks_rrsnet();
     s->grid_sum = s->n_sm * 4;
     *out = s;
@@ -459,14 +458,14 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     int cur = 0;
     for (int d = 1; d <= max_depth; ++d) {
         const int kind = factor_kind(rrs_mode, o.gate, d);
-        TIMED(NRRS_STAGE_EXTEND,
-              launch_extend(kind, scene->view, q[cur], w, rp, d, scene->grid_extend[kind], s));
+        TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
+        TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, rp, d, s));
         if (kind == kFactorNet) {
             WorkView wn = w;
             wn.grid_red = scene->grid_rrsnet;
             TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_depth(wn, rp, d, s));
+            TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
         }
-        TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
         TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, rp, d, normalized, s));
         const int do_split = d < max_depth;
         TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, rp, d, do_split, s));

@@ -16,7 +16,7 @@ constexpr int kExtendThreads = 256;
 constexpr int kSplitThreads = 256;
 constexpr int kReduceThreads = 1024;
 constexpr int kStack = 40;        // BVH build depth is capped below this
-constexpr int kSteps = 12;        // node visits between ray fetch rounds
+constexpr int kSteps = 4;         // node visits between ray fetch rounds
 constexpr uint32_t kMaxX = 1u << 23;  // q_used >= 2^23 has no fractional part in FP32
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
@@ -328,30 +328,23 @@ __global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
     out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
 }
 
-// Extension of depth `depth`: closest hit, emission deposit, and the RRS factor q_orig
-// (NET depths store the 16 features and q = -1; k_rrsnet_fp32 fills q).  Persistent
-// warps fetch rays dynamically: a lane whose query has ended finishes that ray and takes
+// Extension of depth `depth`, part 1: the closest hit of every live ray.  Persistent
+// warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
 // the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
-// Every slot's outputs depend only on that slot, so the result is deterministic.
-template <int KIND>
+// Each slot's hit depends only on that slot's ray, so the result is deterministic.
 __global__ void __launch_bounds__(kExtendThreads, 4)
-k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
+k_trace(SceneView sc, QueueView cur, WorkView w, int depth) {
     __shared__ int s_stack[kStack * kExtendThreads];
     int* stk = s_stack + threadIdx.x;
     DevStats* st = w.st;
     const long long n = st->live[depth - 1];
     unsigned long long* ctr = &st->fetch[depth - 1];
-    const int has_ref = st->has_ref;
-    const float eps_I = st->eps_I;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned int nonfinite = 0;
     long long idx = -1;
     bool exhausted = false;
     Ray ray;
     Hit h;
-    float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t pix = 0;
     for (;;) {
         const bool need = idx < 0 && !exhausted;
         const unsigned need_mask = __ballot_sync(0xffffffffu, need);
@@ -364,11 +357,7 @@ k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                 const long long my = (long long)base + __popc(need_mask & lt_mask);
                 if (my < n) {
                     idx = my;
-                    const float4 o4 = cur.o[idx];
-                    const float4 d4 = cur.d[idx];
-                    t4 = cur.t[idx];
-                    pix = fbits(o4.w);
-                    ray_init(ray, xyz(o4), xyz(d4), h);
+                    ray_init(ray, xyz(cur.o[idx]), xyz(cur.d[idx]), h);
                 } else {
                     exhausted = true;
                 }
@@ -380,14 +369,39 @@ k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
         for (int step = 0; step < kSteps && !done; ++step)
             done = visit_node(sc, ray, h, stk, kExtendThreads);
         if (!done) continue;
-        // ---- the query of slot idx has ended: shade it
+        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
+        idx = -1;
+    }
+}
+
+// Extension of depth `depth`, part 2 (fixed grid-stride, coherent): emission deposit,
+// termination, and the RRS factor q_orig of each vertex; NET depths store the 16
+// features and q = -1 for the RRSNet kernel.  Non-NET depths also write the block's
+// FP64 partial sum of q (fixed assignment, so the sum is reproducible).
+template <int KIND>
+__global__ void __launch_bounds__(256)
+k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
+    __shared__ double sh[32];
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    const int has_ref = st->has_ref;
+    const float eps_I = st->eps_I;
+    double qsum = 0.0;
+    unsigned int nonfinite = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 hh = w.hit[i];
+        const int slot = __float_as_int(hh.y);
+        const float4 o4 = cur.o[i];
         float q = 0.0f;
-        float4 dep = make_float4(0.0f, 0.0f, 0.0f, bitsf(pix));
-        if (h.slot >= 0) {
+        float4 dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
+        if (slot >= 0) {
+            const float4 d4 = cur.d[i];
+            const float4 t4 = cur.t[i];
             int mi;
-            const V3 ng = tri_geom_normal(sc, h.slot, &mi);
+            const V3 ng = tri_geom_normal(sc, slot, &mi);
             const nrrs_material m = sc.mats[mi];
-            const V3 d = ray.d;
+            const V3 d = xyz(d4);
             const bool front = dot3(ng, d) < 0.0f;
             if (front || m.two_sided) {
                 dep.x = t4.x * m.Le[0];
@@ -406,14 +420,14 @@ k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     if (!has_ref) {
                         q = l;
                     } else {
-                        const float* rr = rp.ref + 3 * (size_t)pix;
+                        const float* rr = rp.ref + 3 * (size_t)fbits(o4.w);
                         const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
                         q = den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
                     }
                 } else {
-                    const V3 p = ray.o + d * h.t;
+                    const V3 p = xyz(o4) + d * hh.x;
                     const V3 ns = front ? ng : ng * -1.0f;
-                    float4* f = w.feat + 4 * idx;
+                    float4* f = w.feat + 4 * i;
                     f[0] = make_float4(
                         sc.inv_ext[0] > 0.0f ? (p.x - sc.lo[0]) * sc.inv_ext[0] : 0.5f,
                         sc.inv_ext[1] > 0.0f ? (p.y - sc.lo[1]) * sc.inv_ext[1] : 0.5f,
@@ -431,19 +445,22 @@ k_extend(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                 }
             }
         }
-        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
-        w.q[idx] = q;
-        w.dep[idx] = dep;
-        idx = -1;
+        w.q[i] = q;
+        w.dep[i] = dep;
+        if (KIND != kFactorNet) qsum += (double)q;
+    }
+    if (KIND != kFactorNet) {
+        qsum = block_sum(qsum, sh);
+        if (threadIdx.x == 0) w.part[blockIdx.x] = qsum;
     }
     nonfinite = warp_sum(nonfinite);
-    if (lane == 0 && nonfinite) {
+    if ((threadIdx.x & 31) == 0 && nonfinite) {
         atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
         atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
     }
 }
 
-// RRSNet (FP32 SIMT) on the slots the extension marked with q = -1.
+// RRSNet (FP32 SIMT) on the slots k_shade marked with q = -1.
 __global__ void __launch_bounds__(256, 2)
 k_rrsnet_fp32(WorkView w, const float* __restrict__ params, int depth) {
     __shared__ __align__(16) float sW[kNParams];
@@ -841,14 +858,9 @@ k_split_arr_scatter(SplitArrays a, const unsigned long long* boff) {
 int extend_block_threads() { return kExtendThreads; }
 int split_block_threads() { return kSplitThreads; }
 
-int max_blocks_extend(int kind) {
+int max_blocks_trace() {
     int nb = 1;
-    switch (kind) {
-        case kFactorOne: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorOne>, kExtendThreads, 0); break;
-        case kFactorPlain: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorPlain>, kExtendThreads, 0); break;
-        case kFactorHeur: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorHeur>, kExtendThreads, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<kFactorNet>, kExtendThreads, 0); break;
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, kExtendThreads, 0);
     return nb < 1 ? 1 : nb;
 }
 
@@ -869,14 +881,19 @@ void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cu
     k_camera<<<(unsigned)((P + threads - 1) / threads), threads, 0, s>>>(cam, rp, out);
 }
 
-void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
-                   const RenderParams& rp, int depth, int grid, cudaStream_t s) {
-    const int G = grid;
+void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
+                  cudaStream_t s) {
+    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth);
+}
+
+void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
+                  const RenderParams& rp, int depth, cudaStream_t s) {
+    const int G = w.grid_red;
     switch (kind) {
-        case kFactorOne: k_extend<kFactorOne><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
-        case kFactorPlain: k_extend<kFactorPlain><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
-        case kFactorHeur: k_extend<kFactorHeur><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
-        default: k_extend<kFactorNet><<<G, kExtendThreads, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorOne: k_shade<kFactorOne><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorPlain: k_shade<kFactorPlain><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorHeur: k_shade<kFactorHeur><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        default: k_shade<kFactorNet><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
     }
 }
 

@@ -79,14 +79,16 @@ enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFact
 
 int extend_block_threads();
 int split_block_threads();
-int max_blocks_extend(int kind);  // resident blocks per SM
+int max_blocks_trace();  // resident blocks per SM
 int max_blocks_rrsnet();
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
                         long long P, DevStats* st, cudaStream_t s);
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
-void launch_extend(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
-                   const RenderParams& rp, int depth, int grid, cudaStream_t s);
+void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
+                  cudaStream_t s);
+void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
+                  const RenderParams& rp, int depth, cudaStream_t s);
 void launch_rrsnet_depth(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
 void launch_sum_q(const WorkView& w, int depth, cudaStream_t s);
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,

@@ -23,9 +23,9 @@ RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
 GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
 STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 MAX_DEPTH = 32
-STAGES = 8
+STAGES = 9
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
-               "finalize", "rrsnet"]
+               "finalize", "rrsnet", "shade"]
 N_FEATURES = 16
 RRSNET_PARAMS = 2592
 
@@ -66,8 +66,8 @@ class RenderStats(C.Structure):
                 ("requested", C.c_int64 * MAX_DEPTH), ("dropped", C.c_int64 * MAX_DEPTH),
                 ("segments", C.c_int64), ("nonfinite", C.c_int64), ("net_evals", C.c_int64),
                 ("capacity", C.c_int64), ("status_bits", C.c_uint32),
-                ("kernel_launches", C.c_uint32), ("stage_ms", C.c_float * 8),
-                ("stage_launches", C.c_int32 * 8)]
+                ("kernel_launches", C.c_uint32), ("stage_ms", C.c_float * 12),
+                ("stage_launches", C.c_int32 * 12)]
 
     def as_dict(self, depth):
         return {
