@@ -299,12 +299,12 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     };
     cudaError_t e;
     if ((e = dalloc(&s->nodes, bvh.nodes.size() * 4)) != cudaSuccess) return bail(e, "alloc nodes");
-    if ((e = dalloc(&s->tris, (size_t)n_tri * 3)) != cudaSuccess) return bail(e, "alloc tris");
+    if ((e = dalloc(&s->tris, (size_t)bvh.n_ref * 3)) != cudaSuccess) return bail(e, "alloc tris");
     if ((e = dalloc(&s->mats, n_mat)) != cudaSuccess) return bail(e, "alloc mats");
     if ((e = dalloc(&s->params, kNParams)) != cudaSuccess) return bail(e, "alloc params");
     if ((e = cudaMemcpy(s->nodes, bvh.nodes.data(), bvh.nodes.size() * 64, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy nodes");
-    if ((e = cudaMemcpy(s->tris, bvh.tris.data(), (size_t)n_tri * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy(s->tris, bvh.tris.data(), (size_t)bvh.n_ref * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy tris");
     if ((e = cudaMemcpy(s->mats, mats, sizeof(nrrs_material) * n_mat, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy mats");

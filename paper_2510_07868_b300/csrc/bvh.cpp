@@ -9,6 +9,12 @@
 //                                          child <  0: leaf, first triangle ~child.
 // Triangles (48 bytes, 3 x float4, in BVH leaf order):
 //   (v0.xyz, original index), (e1 = v1 - v0, material id), (e2 = v2 - v0, 0)
+//
+// Large triangles enter the build as several references ("early split clipping",
+// Ernst & Greiner 2007): a triangle whose box is long compared with the scene is cut
+// into sub-boxes, each bounding the part of the triangle inside it, so walls do not
+// make every node span the whole scene.  A reference carries the full triangle, so the
+// intersection test and its result do not change; duplicates return the same hit.
 #include "bvh.h"
 
 #include <algorithm>
@@ -50,6 +56,81 @@ struct Prim {
 };
 
 constexpr int kBins = 16;
+constexpr int kSplitLevels = 10;       // at most 2^10 references per triangle
+constexpr double kSplitFraction = 1.0 / 16.0;  // split boxes longer than this x scene size
+
+// Bounds of the part of triangle v[3][3] inside box `clip` (Sutherland-Hodgman in FP64,
+// rounded outward to float).  Returns an empty box if they do not overlap.
+Box clipped_bounds(const double v[3][3], const double lo[3], const double hi[3]) {
+    double poly[16][3], tmp[16][3];
+    int n = 3;
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) poly[i][k] = v[i][k];
+    for (int ax = 0; ax < 3 && n > 0; ++ax) {
+        for (int side = 0; side < 2 && n > 0; ++side) {
+            const double plane = side ? hi[ax] : lo[ax];
+            auto inside = [&](const double* p) { return side ? p[ax] <= plane : p[ax] >= plane; };
+            int m = 0;
+            for (int i = 0; i < n; ++i) {
+                const double* a = poly[i];
+                const double* b = poly[(i + 1) % n];
+                const bool ia = inside(a), ib = inside(b);
+                if (ia && m < 16) {
+                    for (int k = 0; k < 3; ++k) tmp[m][k] = a[k];
+                    ++m;
+                }
+                if (ia != ib && m < 16) {
+                    const double t = (plane - a[ax]) / (b[ax] - a[ax]);
+                    for (int k = 0; k < 3; ++k) tmp[m][k] = a[k] + t * (b[k] - a[k]);
+                    tmp[m][ax] = plane;
+                    ++m;
+                }
+            }
+            n = m;
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < 3; ++k) poly[i][k] = tmp[i][k];
+        }
+    }
+    Box out;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            out.lo[k] = std::min(out.lo[k], std::nextafter((float)poly[i][k], -FLT_MAX));
+            out.hi[k] = std::max(out.hi[k], std::nextafter((float)poly[i][k], FLT_MAX));
+        }
+    return out;
+}
+
+void add_references(const double v[3][3], const Box& b, int32_t id, int level, double limit,
+                    std::vector<Prim>& out) {
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (b.hi[k] - b.lo[k] > b.hi[ax] - b.lo[ax]) ax = k;
+    if ((double)b.hi[ax] - b.lo[ax] <= limit || level >= kSplitLevels) {
+        Prim p;
+        p.box = b;
+        for (int k = 0; k < 3; ++k) p.c[k] = 0.5f * (b.lo[k] + b.hi[k]);
+        p.id = id;
+        out.push_back(p);
+        return;
+    }
+    const double mid = 0.5 * ((double)b.lo[ax] + b.hi[ax]);
+    for (int half = 0; half < 2; ++half) {
+        double lo[3], hi[3];
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = b.lo[k];
+            hi[k] = b.hi[k];
+        }
+        if (half) lo[ax] = mid; else hi[ax] = mid;
+        Box c = clipped_bounds(v, lo, hi);
+        if (c.empty()) continue;
+        // never grow past the parent box
+        for (int k = 0; k < 3; ++k) {
+            c.lo[k] = std::max(c.lo[k], b.lo[k]);
+            c.hi[k] = std::min(c.hi[k], b.hi[k]);
+        }
+        add_references(v, c, id, level + 1, limit, out);
+    }
+}
 constexpr int kLeafMax = 4;
 constexpr int kMaxBuildDepth = 38;  // traversal stack holds 40 entries
 
@@ -154,15 +235,23 @@ struct Builder {
 }  // namespace
 
 void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* out) {
-    std::vector<Prim> prims(n_tri);
+    Box scene_box;
+    for (int64_t i = 0; i < (int64_t)n_tri * 3; ++i) scene_box.grow(tri + i * 3);
+    double scene_ext = 0.0;
+    for (int k = 0; k < 3; ++k) scene_ext = std::max(scene_ext, (double)scene_box.hi[k] - scene_box.lo[k]);
+    const double limit = kSplitFraction * scene_ext;
+    std::vector<Prim> prims;
+    prims.reserve((size_t)n_tri + 1024);
     for (int32_t i = 0; i < n_tri; ++i) {
-        Prim& p = prims[i];
-        for (int k = 0; k < 3; ++k) p.box.grow(tri + (size_t)i * 9 + 3 * k);
-        for (int a = 0; a < 3; ++a)
-            p.c[a] = (tri[(size_t)i * 9 + a] + tri[(size_t)i * 9 + 3 + a] + tri[(size_t)i * 9 + 6 + a]) /
-                     3.0f;
-        p.id = i;
+        Box b;
+        double v[3][3];
+        for (int k = 0; k < 3; ++k) {
+            b.grow(tri + (size_t)i * 9 + 3 * k);
+            for (int a = 0; a < 3; ++a) v[k][a] = tri[(size_t)i * 9 + 3 * k + a];
+        }
+        add_references(v, b, i, 0, limit, prims);
     }
+    const int32_t n_ref = (int32_t)prims.size();
     out->nodes.clear();
     Box all;
     for (const Prim& p : prims) all.grow(p.box);
@@ -171,15 +260,16 @@ void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* 
     Builder bld{prims, out->nodes, 1e-5f * ext + 1e-30f};
     Box root_box;
     int32_t root_count = 0;
-    int32_t root = bld.build(0, n_tri, 0, &root_box, &root_count);
+    int32_t root = bld.build(0, n_ref, 0, &root_box, &root_count);
     if (root < 0) {
         // whole scene is one leaf: make a root whose second child is empty
         out->nodes.emplace_back();
         Box empty;
         Builder::fill(out->nodes[0], bld.inflate(root_box), root, root_count, empty, ~0, 0);
     }
-    out->tris.assign((size_t)n_tri * 12, 0.0f);
-    for (int32_t s = 0; s < n_tri; ++s) {
+    out->n_ref = n_ref;
+    out->tris.assign((size_t)n_ref * 12, 0.0f);
+    for (int32_t s = 0; s < n_ref; ++s) {
         const int32_t i = prims[s].id;
         const float* v = tri + (size_t)i * 9;
         float* o = out->tris.data() + (size_t)s * 12;

@@ -13,7 +13,8 @@ static_assert(sizeof(BvhNode) == 64, "node is 4 x float4");
 
 struct BvhHost {
     std::vector<BvhNode> nodes;  // nodes[0] is the root (always an inner node)
-    std::vector<float> tris;     // 12 floats per triangle, BVH order
+    std::vector<float> tris;     // 12 floats per triangle reference, BVH order
+    int32_t n_ref = 0;           // triangle references (>= triangles: large ones are split)
     float lo[3], hi[3];          // scene bounds over all vertices
 };
 

@@ -16,7 +16,7 @@ constexpr int kExtendThreads = 256;
 constexpr int kSplitThreads = 256;
 constexpr int kReduceThreads = 1024;
 constexpr int kStack = 40;        // BVH build depth is capped below this
-constexpr int kSteps = 4;         // node visits between ray fetch rounds
+constexpr int kSteps = 8;         // node visits between ray fetch rounds
 constexpr uint32_t kMaxX = 1u << 23;  // q_used >= 2^23 has no fractional part in FP32
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
