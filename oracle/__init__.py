@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nrrs_oracle.c")
+_SRC_TRAIN = os.path.join(_HERE, "nrrs_oracle_train.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODE_NONE, MODE_PLAIN_RR, MODE_HEUR_NORM, MODE_NET, MODE_NET_MIX = range(5)
@@ -27,9 +28,11 @@ NO_HIT = 0xFFFFFFFF
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(
+        os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC_TRAIN))
+    if force or stale:
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
-               "-ffp-contract=off", _SRC, "-o", _LIB, "-lm"]
+               "-ffp-contract=off", _SRC, _SRC_TRAIN, "-o", _LIB, "-lm"]
         subprocess.run(cmd, check=True)
     return _LIB
 
@@ -56,7 +59,7 @@ class RenderArgs(C.Structure):
                 ("f_rate", C.c_double), ("alpha0", C.c_double), ("q_max", C.c_double),
                 ("eps_rel", C.c_double), ("boxcox_lambda", C.c_double), ("gate", C.c_uint64),
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
-                ("n_pixels", C.c_int64)]
+                ("n_pixels", C.c_int64), ("rec", C.c_void_p)]
 
 
 class RenderStats(C.Structure):
@@ -103,6 +106,18 @@ def lib():
         _lib.or_bernstein_exponent.restype = C.c_double
         _lib.or_render.argtypes = [P, P, P, P, P, P]
         _lib.or_render.restype = C.c_int
+        _lib.or_mlpn_param_count.argtypes = [C.c_int]
+        _lib.or_mlpn_param_count.restype = C.c_int64
+        _lib.or_mlpn_forward.argtypes = [P, C.c_int, P, P, P, P]
+        _lib.or_mlpn_backward.argtypes = [P, C.c_int, P, P, P]
+        _lib.or_statnet_dloss.argtypes = [P, P, C.c_double, P]
+        _lib.or_statnet_dloss.restype = C.c_double
+        _lib.or_pixel_error.argtypes = [P, C.c_int64, C.c_int32, P, C.c_double, P, P]
+        _lib.or_rrsnet_dloss.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int64, P, P, P,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, P, P]
+        _lib.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                      C.c_double, C.c_double]
+        _lib.or_ema.argtypes = [P, P, C.c_int64, C.c_double]
     return _lib
 
 
@@ -235,18 +250,21 @@ def bernstein_exponent(f_rate):
 
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
-           params=None, pixel_ref=None, pixels=None, trace=False):
-    """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None)."""
+           params=None, pixel_ref=None, pixels=None, trace=False, record=False):
+    """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
+    With record=True the stats dict also holds "rec": per depth an array [live, 13] of
+    (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
     h = _SceneHolder(scene)
     P = np.ascontiguousarray(params, dtype=np.float64) if params is not None else None
     ref = np.ascontiguousarray(pixel_ref, dtype=np.float64) if pixel_ref is not None else None
     pix = np.ascontiguousarray(pixels, dtype=np.int32) if pixels is not None else None
+    capv = cap if cap > 0 else 2 * width * height * spp
+    rec = np.zeros((max_depth, capv, 13)) if record else None
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
-                      0 if pix is None else pix.shape[0])
+                      0 if pix is None else pix.shape[0], _p(rec))
     out = np.zeros((height, width, 3))
     st = RenderStats()
-    capv = cap if cap > 0 else 2 * width * height * spp
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None
     tc = np.zeros(max_depth, dtype=np.int64) if trace else None
     rc = lib().or_render(C.byref(h.c), C.byref(args), _p(out), C.byref(st), _p(tr), _p(tc))
@@ -259,7 +277,76 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
         "dropped": np.array(st.dropped[1:D + 1]), "requested": np.array(st.requested[1:D + 1]),
         "segments": int(st.segments), "nonfinite": int(st.nonfinite),
     }
+    if record:
+        stats["rec"] = [rec[d, :stats["live"][d]] for d in range(D)]
     trace_out = None
     if trace:
         trace_out = [tr[d, :tc[d]] for d in range(D)]
     return out, stats, trace_out
+
+
+# ------------------------------------------------------------------ training side
+def mlpn_param_count(n_out):
+    return int(lib().or_mlpn_param_count(n_out))
+
+
+def mlpn_forward(params, n_out, x):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(n_out)
+    lib().or_mlpn_forward(_p(P), n_out, _p(x), _p(out), None, None)
+    return out
+
+
+def mlpn_backward(params, n_out, x, dout):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    d = np.ascontiguousarray(dout, dtype=np.float64)
+    G = np.zeros_like(P)
+    lib().or_mlpn_backward(_p(P), n_out, _p(x), _p(d), _p(G))
+    return G
+
+
+def statnet_dloss(pred, L, eps=0.01):
+    pred = np.ascontiguousarray(pred, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    d = np.zeros(6)
+    loss = lib().or_statnet_dloss(_p(pred), _p(L), eps, _p(d))
+    return loss, d
+
+
+def pixel_error(S1, spp, ref, eps=0.01):
+    S1 = np.ascontiguousarray(S1, dtype=np.float64)
+    ref = np.ascontiguousarray(ref, dtype=np.float64)
+    npix = ref.size // 3
+    V = np.zeros(npix)
+    E = np.zeros(npix)
+    lib().or_pixel_error(_p(S1), npix, spp, _p(ref), eps, _p(V), _p(E))
+    return V, E
+
+
+def rrsnet_dloss(q_nrrs, F, Fn, t, pixel, m1, m2, E, Iref, k, eps=0.01, g=(0.01, 0.05, 0.01)):
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (q_nrrs, F, Fn, t, m1, m2)]
+    pixel = np.ascontiguousarray(pixel, dtype=np.int32)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    Iref = np.ascontiguousarray(Iref, dtype=np.float64)
+    k = np.ascontiguousarray(k, dtype=np.int64)
+    n = a[0].shape[0]
+    dq = np.zeros(n)
+    terms = np.zeros(3)
+    lib().or_rrsnet_dloss(n, _p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), _p(pixel), _p(a[4]), _p(a[5]),
+                          E.shape[0], _p(E), _p(Iref), _p(k), eps, g[0], g[1], g[2], _p(dq),
+                          _p(terms))
+    return dq, terms
+
+
+def adam_step(P, G, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    for arr in (P, m, v):
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    lib().or_adam_step(_p(P), _p(G), _p(m), _p(v), P.shape[0], step, lr, b1, b2, eps)
+
+
+def ema(Eavg, P, decay=0.99):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    lib().or_ema(_p(Eavg), _p(P), P.shape[0], decay)

@@ -450,7 +450,12 @@ typedef struct {
     const double* pixel_ref;/* previous estimate [H*W*3] or NULL */
     const int32_t* pixels;  /* optional ascending pixel subset (NONE / PLAIN_RR only) */
     int64_t n_pixels;
+    double* rec;            /* optional per-vertex record [D][cap][OR_REC], see or_render */
 } or_render_args;
+
+/* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
+ * q_orig, q_used, X, first child slot. */
+#define OR_REC 13
 
 typedef struct {
     int64_t live[OR_MAX_DEPTH + 1];
@@ -484,7 +489,11 @@ static int or_is_normalized(int mode) {
  * depth is processed before any of the next).  Deposits are summed per pixel in FP64
  * and divided by spp.  With trace != NULL, trace[(d-1)*cap*5 + 5*i + {0..4}] holds
  * (pixel, sample, lineage, triangle or 0xFFFFFFFF, X) of slot i at depth d, and
- * trace_count[d-1] the queue length. */
+ * trace_count[d-1] the queue length.  With a->rec != NULL every vertex is recorded and,
+ * after the last depth, a reverse pass fills its suffix sum: S = own deposit + the sum
+ * of its children's S (children are the slots [first, first + X) of the next depth that
+ * fit in the queue).  S / t is the vertex's estimate of outgoing radiance, the target
+ * StatNet learns (Sec. 3.2 "Loss Design"). */
 int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
               or_render_stats* st, uint32_t* trace, int64_t* trace_count) {
     const int32_t W = a->width, H = a->height, spp = a->spp, D = a->max_depth;
@@ -610,7 +619,10 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             v3 ng = cross(sub(or_tri_vertex(s, v->tri, 1), v0), sub(or_tri_vertex(s, v->tri, 2), v0));
             int front = dot(ng, mk(p->d[0], p->d[1], p->d[2])) < 0.0;
             if (front || m->two_sided)
-                for (int c = 0; c < 3; ++c) acc[3 * (int64_t)p->pixel + c] += p->t[c] * m->Le[c];
+                for (int c = 0; c < 3; ++c) {
+                    acc[3 * (int64_t)p->pixel + c] += p->t[c] * m->Le[c];
+                    if (a->rec) a->rec[((int64_t)(depth - 1) * cap + i) * OR_REC + 3 + c] = p->t[c] * m->Le[c];
+                }
         }
         /* non-finite factors terminate their path */
         for (int64_t i = 0; i < n; ++i) {
@@ -641,6 +653,14 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             uint32_t base;
             uint32_t X = or_split_one(F32, (float)qbuf[i], a->seed_lo, a->seed_hi, a->frame,
                                       p->pixel, p->sample, (uint32_t)depth, p->lineage, &qu, &base);
+            if (a->rec) {
+                double* r = a->rec + ((int64_t)(depth - 1) * cap + i) * OR_REC;
+                for (int c = 0; c < 3; ++c) r[6 + c] = p->t[c];
+                r[9] = qbuf[i];
+                r[10] = (double)qu;
+                r[11] = (double)X;
+                r[12] = (double)S;
+            }
             if (trace) {
                 uint32_t* r = trace + ((int64_t)(depth - 1) * cap + i) * 5;
                 r[0] = p->pixel; r[1] = p->sample; r[2] = p->lineage;
@@ -684,6 +704,22 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
         n = S < cap ? S : cap;
     }
     for (int64_t i = 0; i < npix * 3; ++i) out_rgb[i] = acc[i] / (double)spp;
+    if (a->rec) {
+        /* reverse pass, deepest depth first */
+        for (int32_t d = D; d >= 1; --d) {
+            const int64_t nd = st->live[d];
+            const int64_t nn = d < D ? st->live[d + 1] : 0;
+            for (int64_t i = 0; i < nd; ++i) {
+                double* r = a->rec + ((int64_t)(d - 1) * cap + i) * OR_REC;
+                for (int c = 0; c < 3; ++c) r[c] = r[3 + c];
+                const int64_t first = (int64_t)r[12], X = (int64_t)r[11];
+                for (int64_t j = first; j < first + X && j < nn; ++j) {
+                    const double* ch = a->rec + ((int64_t)d * cap + j) * OR_REC;
+                    for (int c = 0; c < 3; ++c) r[c] += ch[c];
+                }
+            }
+        }
+    }
     free(cur); free(nxt); free(vx); free(acc); free(qbuf);
     return OR_OK;
 }

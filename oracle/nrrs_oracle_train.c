@@ -1,0 +1,191 @@
+/*
+ * NRRS oracle, training side: plain FP64 restatements of the pieces the GPU trains
+ * RRSNet and StatNet with.  TEST INFRASTRUCTURE ONLY (see nrrs_oracle.c).
+ *
+ *   or_mlpn_forward / or_mlpn_backward
+ *       A bias-free MLP 16 -> 32 -> 32 -> 32 -> n_out with Leaky ReLU (slope 0.01) after
+ *       each hidden layer and no output activation (Sec. 4 "Network Architecture";
+ *       StatNet has no output activation, Sec. 4 "Output & Activation").
+ *   or_statnet_dloss
+ *       Eq. loss-function_StatNet: relative L2, L2(a, b) = (a - b)^2 / (sg(b)^2 + eps),
+ *       on the two predicted moments E[<L>] and E[<L>^2] (Sec. 4 "Output & Activation")
+ *       against the one-sample targets <L> and <L>^2, per RGB channel.
+ *   or_pixel_error
+ *       Eq. loss-function_min: E_i = V[<I_i>] / (I_i^2 + eps), V from the spp samples of
+ *       the pixel, I_i the reference (Sec. 4 "Compromise": the accumulated earlier frames).
+ *   or_rrsnet_dloss
+ *       d L_RRSNet / d q_nrrs for L_RRSNet = g1 L_avg + g2 L_min + g3 L_rrs
+ *       (Eq. loss-function_rrsnet, loss-function_avg, loss-function_min,
+ *       loss-function_rrs), with dV/dq from Eq. gradient_transfer_rr_mc (q_used < 1) or
+ *       Eq. gradient_transfer_splitting_mc (q_used >= 1), the pixel loss shared 1/k_i
+ *       among the pixel's k_i training samples (Sec. 3.2), and q_used = F q_nrrs with F
+ *       held constant.
+ *   or_adam_step, or_ema
+ *       Adam (Kingma & Ba) and the exponential moving average of the weights used for
+ *       inference (Sec. 4 "Training").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define NF 16
+#define NH 32
+#define LEAK 0.01
+
+static void layer_ptrs(const double* P, int n_out, const double* W[4]) {
+    (void)n_out;
+    W[0] = P;
+    W[1] = P + NH * NF;
+    W[2] = P + NH * NF + NH * NH;
+    W[3] = P + NH * NF + 2 * NH * NH;
+}
+
+int64_t or_mlpn_param_count(int n_out) { return NH * NF + 2 * NH * NH + (int64_t)n_out * NH; }
+
+void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, double* pre,
+                     double* hid) {
+    const double* W[4];
+    layer_ptrs(P, n_out, W);
+    double in[NH], h[NH];
+    int nin = NF;
+    for (int k = 0; k < NF; ++k) in[k] = x[k];
+    for (int l = 0; l < 3; ++l) {
+        for (int j = 0; j < NH; ++j) {
+            double a = 0.0;
+            for (int k = 0; k < nin; ++k) a += W[l][j * nin + k] * in[k];
+            if (pre) pre[l * NH + j] = a;
+            h[j] = a > 0.0 ? a : LEAK * a;
+            if (hid) hid[l * NH + j] = h[j];
+        }
+        for (int j = 0; j < NH; ++j) in[j] = h[j];
+        nin = NH;
+    }
+    for (int o = 0; o < n_out; ++o) {
+        double a = 0.0;
+        for (int k = 0; k < NH; ++k) a += W[3][o * NH + k] * in[k];
+        out[o] = a;
+    }
+}
+
+/* Accumulates into G the gradient of sum_o dout[o] * out[o] with respect to P. */
+void or_mlpn_backward(const double* P, int n_out, const double* x, const double* dout,
+                      double* G) {
+    double pre[3 * NH], hid[3 * NH], out[8];
+    or_mlpn_forward(P, n_out, x, out, pre, hid);
+    const double* W[4];
+    layer_ptrs(P, n_out, W);
+    double* GW[4] = {G, G + NH * NF, G + NH * NF + NH * NH, G + NH * NF + 2 * NH * NH};
+    double dh[NH], da[NH];
+    for (int k = 0; k < NH; ++k) dh[k] = 0.0;
+    for (int o = 0; o < n_out; ++o)
+        for (int k = 0; k < NH; ++k) {
+            GW[3][o * NH + k] += dout[o] * hid[2 * NH + k];
+            dh[k] += dout[o] * W[3][o * NH + k];
+        }
+    for (int l = 2; l >= 0; --l) {
+        const int nin = l == 0 ? NF : NH;
+        const double* input = l == 0 ? x : hid + (l - 1) * NH;
+        for (int j = 0; j < NH; ++j) da[j] = dh[j] * (pre[l * NH + j] > 0.0 ? 1.0 : LEAK);
+        for (int j = 0; j < NH; ++j)
+            for (int k = 0; k < nin; ++k) GW[l][j * nin + k] += da[j] * input[k];
+        if (l > 0)
+            for (int k = 0; k < NH; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < NH; ++j) s += W[l][j * nin + k] * da[j];
+                dh[k] = s;
+            }
+    }
+}
+
+/* Relative L2 of both moments; returns the loss of one sample, writes d/dpred. */
+double or_statnet_dloss(const double* pred /*6: m1 rgb, m2 rgb*/, const double* L /*3*/,
+                        double eps, double* dpred) {
+    double loss = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double t1 = L[c], t2 = L[c] * L[c];
+        const double d1 = pred[c] - t1, d2 = pred[3 + c] - t2;
+        const double w1 = 1.0 / (t1 * t1 + eps), w2 = 1.0 / (t2 * t2 + eps);
+        loss += d1 * d1 * w1 + d2 * d2 * w2;
+        dpred[c] = 2.0 * d1 * w1;
+        dpred[3 + c] = 2.0 * d2 * w2;
+    }
+    return loss;
+}
+
+/* Per pixel: V = unbiased variance of the spp sample values / spp (mean over RGB), and
+ * E = V / (I_ref^2 + eps) with I_ref the mean over RGB of the reference pixel.
+ * S1 holds the spp sample values of every pixel, [npix][spp][3]. */
+void or_pixel_error(const double* S1, int64_t npix, int32_t spp, const double* ref, double eps,
+                    double* V, double* E) {
+    for (int64_t p = 0; p < npix; ++p) {
+        double v = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double m = 0.0;
+            for (int s = 0; s < spp; ++s) m += S1[(p * spp + s) * 3 + c];
+            m /= spp;
+            double q = 0.0;
+            for (int s = 0; s < spp; ++s) {
+                const double d = S1[(p * spp + s) * 3 + c] - m;
+                q += d * d;
+            }
+            v += spp > 1 ? q / (spp - 1) / spp : 0.0;
+        }
+        V[p] = v / 3.0;
+        const double I = (ref[3 * p] + ref[3 * p + 1] + ref[3 * p + 2]) / 3.0;
+        E[p] = V[p] / (I * I + eps);
+    }
+}
+
+/* d L_RRSNet / d q_nrrs for every training sample s.  Inputs per sample: the network
+ * output q_nrrs, the applied factor F (q_used = F q_nrrs), the normalization factor
+ * Fn of Eq. F_norm without rate control (q_norm = Fn q_nrrs, a constant), the mean
+ * prefix throughput t, the pixel, and the StatNet moments m1 = E[<H>], m2 = E[<H>^2]
+ * (means over RGB).  Per pixel: E_i, the reference I_i (mean over RGB) and the count k_i
+ * of training samples.  terms[0..2] receive L_avg, L_min and L_rrs. */
+void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const double* Fn,
+                     const double* t, const int32_t* pixel, const double* m1, const double* m2,
+                     int64_t npix, const double* E, const double* Iref, const int64_t* k,
+                     double eps, double g1, double g2, double g3, double* dq, double* terms) {
+    double Ebar = 0.0;
+    for (int64_t p = 0; p < npix; ++p) Ebar += E[p];
+    Ebar /= (double)npix;
+    double Lavg = 0.0, Lmin = 0.0, Lrrs = 0.0;
+    for (int64_t p = 0; p < npix; ++p) {
+        Lavg += (E[p] - Ebar) * (E[p] - Ebar);
+        Lmin += E[p];
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        const int32_t i = pixel[s];
+        const double qu = F[s] * q_nrrs[s];
+        /* dV_i/dq_used: Eq. gradient_transfer_rr_mc for roulette (q_used < 1),
+         * Eq. gradient_transfer_splitting_mc for splitting (q_used >= 1) */
+        const double VH = fmax(m2[s] - m1[s] * m1[s], 0.0);
+        const double H = qu < 1.0 ? m2[s] : VH;
+        const double dV_dqu = -t[s] * t[s] * H / (qu * qu);
+        /* d(g1 L_avg + g2 L_min)/dE_i = g1 2 (E_i - Ebar) + g2 (the Ebar terms cancel),
+         * dE_i/dV_i = 1 / (I_i^2 + eps), shared 1/k_i */
+        const double dL_dE = g1 * 2.0 * (E[i] - Ebar) + g2;
+        const double dL_dV = dL_dE / (Iref[i] * Iref[i] + eps) / (double)k[i];
+        const double qn = Fn[s] * q_nrrs[s];
+        Lrrs += (q_nrrs[s] - qn) * (q_nrrs[s] - qn);
+        dq[s] = dL_dV * dV_dqu * F[s] + g3 * 2.0 * (q_nrrs[s] - qn);
+    }
+    terms[0] = Lavg;
+    terms[1] = Lmin;
+    terms[2] = Lrrs;
+}
+
+/* Adam (Kingma & Ba 2015), step number `step` >= 1. */
+void or_adam_step(double* P, const double* G, double* m, double* v, int64_t n, int64_t step,
+                  double lr, double b1, double b2, double eps) {
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * G[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * G[i] * G[i];
+        P[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}
+
+void or_ema(double* Eavg, const double* P, int64_t n, double decay) {
+    for (int64_t i = 0; i < n; ++i) Eavg[i] = decay * Eavg[i] + (1.0 - decay) * P[i];
+}
