@@ -68,6 +68,12 @@ typedef enum nrrs_rrs_mode {
 #define NRRS_N_FEATURES 16
 #define NRRS_HIDDEN 32
 #define NRRS_RRSNET_PARAMS 2592 /* 32x16 + 32x32 + 32x32 + 1x32, no biases */
+#define NRRS_STATNET_PARAMS 2752 /* 32x16 + 32x32 + 32x32 + 6x32, no biases */
+
+/* Networks for nrrs_set_params / nrrs_get_params. */
+#define NRRS_NET_RRSNET 0       /* RRSNet weights renders use (the EMA of the trained ones) */
+#define NRRS_NET_RRSNET_TRAIN 1 /* RRSNet weights Adam updates                             */
+#define NRRS_NET_STATNET 2      /* StatNet: 16 -> 32 -> 32 -> 32 -> 6, no output activation */
 
 /* Material record, 40 bytes.  type 0 = Lambertian (albedo), 1 = GGX + Lambert
  * "plastic" mixture (roughness is the GGX alpha, F0 the Schlick reflectance at normal
@@ -117,6 +123,10 @@ typedef struct nrrs_render_opts {
     int32_t profile;            /* record CUDA events around every kernel launch on
                                    `stream`; per-stage times land in stats          [0]    */
     int32_t reserved0;
+    float* d_suffix;            /* device [max_depth][C][4] float or NULL: record the frame
+                                   and write every vertex's suffix sum S (rgb, pixel bits):
+                                   its own deposit plus its children's S, so S / t is the
+                                   vertex's outgoing-radiance estimate               [NULL] */
 } nrrs_render_opts;
 
 /* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
@@ -129,7 +139,8 @@ typedef struct nrrs_render_opts {
 #define NRRS_STAGE_FINALIZE 6  /* frame estimate + running reference                */
 #define NRRS_STAGE_RRSNET 7    /* RRSNet (FP32) on the NET depths' features         */
 #define NRRS_STAGE_SHADE 8     /* emission deposit, RRS factor or features, sum q   */
-#define NRRS_N_STAGES 9
+#define NRRS_STAGE_REVERSE 9   /* record mode: suffix sums, deepest depth first     */
+#define NRRS_N_STAGES 10
 
 /* Per-render statistics; filled only when a non-NULL pointer is passed (the call then
  * synchronizes `stream`).  Index d-1 holds depth d (1-based, camera hit = depth 1). */
@@ -249,6 +260,84 @@ NRRS_API nrrs_status nrrs_split_noalloc(const float* d_q_orig, int64_t n, const 
                                         int64_t cap, uint32_t* d_X, int64_t* d_prefix,
                                         uint32_t* d_child_parent, uint32_t* d_child_lineage,
                                         int64_t* d_total, int64_t* d_dropped, void* stream);
+
+/* ------------------------------------------------------------------ training */
+
+/* One online training step (Sec. 3.2 "Loss Design", Sec. 4 "Training").  Options (NULL =
+ * defaults in brackets). */
+typedef struct nrrs_train_opts {
+    int32_t width, height, spp, max_depth; /* training frame          [256, 256, 2, 16] */
+    uint32_t seed_lo, seed_hi, frame;      /* Philox key; frame = frame + step  [1, 0, 0] */
+    int32_t warmup_steps;                  /* steps of step (1): RRSNet -> 1        [20] */
+    float lr_rrsnet, lr_statnet;           /* Adam learning rates        [3e-4, 5e-3]   */
+    float gamma1, gamma2, gamma3;          /* Eq. loss-function_rrsnet [.01, .05, .01] */
+    float eps;                             /* Eq. loss-function_min / StatNet     [0.01] */
+    float ema_decay;                       /* EMA of the RRSNet weights for rendering [0.99] */
+    float f_rate;                          /* rate control of the training frame  [0.85] */
+    const float* d_pixel_ref;              /* device [H*W*3] reference I, or NULL for the
+                                              scene's running mean of its frames   [NULL] */
+} nrrs_train_opts;
+
+typedef struct nrrs_train_stats {
+    int64_t step;         /* successful steps so far                                     */
+    int64_t samples;      /* training samples: vertices where RRSNet was evaluated        */
+    int64_t segments;     /* rays traced by the training frame                            */
+    double loss_statnet;  /* mean relative L2 of StatNet (Eq. loss-function_StatNet)      */
+    double loss_rrsnet;   /* phase 1: mean relative L2 to 1; phase 2: L_RRSNet            */
+    double loss_avg;      /* L_avg = sum_i (E_i - mean E)^2                               */
+    double loss_min;      /* L_min = sum_i E_i                                            */
+    double loss_rrs;      /* L_rrs = sum_s (q_nrrs - q_norm)^2 (phase 2)                  */
+    int32_t phase;        /* 1 = warm-up (step (1) of Sec. 4), 2 = full loss              */
+    int32_t fallback;     /* 0 ok; 1 non-finite gradients or loss, 2 loss EMA rose above
+                             1.5x its minimum: the last good weights were restored and the
+                             step was not counted                                         */
+} nrrs_train_stats;
+
+/* Renders one recorded frame with NET factors at every depth (the inference weights),
+ * runs the reverse pass (suffix sums S; reflected radiance (S - deposit) / t per vertex),
+ * computes pixel errors E_i = V_i / (I_i^2 + eps) from the spp samples of each pixel, then
+ * trains StatNet on <L> and <L>^2 (relative L2) and RRSNet (phase 1: relative L2 to 1;
+ * phase 2: g1 L_avg + g2 L_min + g3 L_rrs with dV/dq from Eq. gradient_transfer_rr_mc /
+ * splitting_mc using the StatNet moments, shared 1/k_i per pixel), one Adam step each,
+ * and updates the rendering weights to the EMA of the trained ones.  Synchronizes
+ * `stream`.  Errors: INVALID_ARG (sizes as nrrs_render, bad options); OOM; CUDA. */
+NRRS_API nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void* stream,
+                                     nrrs_train_stats* stats);
+
+/* Host copies in/out of a network's weights (n = NRRS_RRSNET_PARAMS or
+ * NRRS_STATNET_PARAMS).  Setting StatNet also clears its Adam moments. */
+NRRS_API nrrs_status nrrs_set_params(nrrs_scene* scene, int32_t which, const float* params,
+                                     int32_t n, void* stream);
+NRRS_API nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int32_t n,
+                                     void* stream);
+
+/* Backward pass of the bias-free MLP 16 -> 32 -> 32 -> 32 -> n_out (n_out 1 = RRSNet
+ * before its output activation, 6 = StatNet): d_grad = sum over the n rows of
+ * d(gout_s . out_s) / dW, with inputs d_x [n][16] (16-byte aligned), output gradients
+ * d_gout [n][n_out], weights d_params (packed as nrrs_set_rrsnet_params).  Sums per
+ * block of 128 rows, then over blocks in a fixed order (reproducible).  Scratch: the
+ * scene's training buffers. */
+NRRS_API nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params,
+                                   const float* d_x, const float* d_gout, int64_t n, float* d_grad,
+                                   void* stream);
+
+/* d L_RRSNet / d q_nrrs for n training samples (Sec. 3.2): with q_used = F q_nrrs,
+ * dV/dq_used = -t^2 H / q_used^2, H = m2 if q_used < 1 (Eq. gradient_transfer_rr_mc) else
+ * max(m2 - m1^2, 0) (Eq. gradient_transfer_splitting_mc);
+ * dq = (g1 2 (E_i - Ebar) + g2) / (I_i^2 + eps) / k_i * dV/dq_used * F + g3 2 (q - Fn q).
+ * Per-sample arrays [n]; per-pixel arrays d_E, d_Iref, d_k indexed by d_pixel. */
+NRRS_API nrrs_status nrrs_rrsnet_dloss(const float* d_q_nrrs, const float* d_F, const float* d_Fn,
+                                       const float* d_t, const int32_t* d_pixel, const float* d_m1,
+                                       const float* d_m2, const float* d_E, double Ebar,
+                                       const float* d_Iref, const int32_t* d_k, int64_t n,
+                                       float eps, float g1, float g2, float g3, float* d_dq,
+                                       void* stream);
+
+/* One Adam step (Kingma & Ba, bias-corrected) on n weights, step >= 1.  Non-finite
+ * gradients leave their weight and moments untouched. */
+NRRS_API nrrs_status nrrs_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v,
+                                    int32_t n, int32_t step, float lr, float b1, float b2,
+                                    float eps, void* stream);
 
 #ifdef __cplusplus
 }

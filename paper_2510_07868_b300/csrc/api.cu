@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bvh.h"
+#include "train.cuh"
 #include "wavefront.cuh"
 
 using namespace nrrs;
@@ -122,6 +123,47 @@ namespace nrrs {
 nrrs_status record_error(nrrs_status s, const char* msg) { return fail(s, msg); }
 }  // namespace nrrs
 
+// Training state of a scene: the recorded frame and both networks with their optimizer
+// state (allocated on first use).
+struct TrainState {
+    RecordView rec{};
+    long long rec_C = 0, npix = 0;
+    int rec_D = 0;
+    float *m1 = nullptr, *m2 = nullptr, *V = nullptr, *E = nullptr, *rgb = nullptr;
+    int* k = nullptr;
+    bool nets = false;
+    float *rrs_raw = nullptr, *rrs_m = nullptr, *rrs_v = nullptr, *rrs_good = nullptr;
+    float *stat = nullptr, *stat_m = nullptr, *stat_v = nullptr, *stat_good = nullptr;
+    float *grad_rrs = nullptr, *grad_stat = nullptr, *part = nullptr;
+    double *loss_part = nullptr, *scal = nullptr;
+    float *Fd = nullptr, *Fnd = nullptr;
+    int* bad = nullptr;
+    int part_blocks = 0;
+    long long step = 0, full_steps = 0;
+    double loss_ema = 0.0, loss_min = 0.0;
+
+    void release_record() {
+        cudaFree(rec.dep); cudaFree(rec.q); cudaFree(rec.t); cudaFree(rec.feat);
+        cudaFree(rec.first); cudaFree(rec.X); cudaFree(rec.S);
+        cudaFree(m1); cudaFree(m2); cudaFree(V); cudaFree(E); cudaFree(k); cudaFree(rgb);
+        rec = RecordView{};
+        m1 = m2 = V = E = rgb = nullptr;
+        k = nullptr;
+        rec_C = npix = 0;
+        rec_D = 0;
+    }
+    void release_all() {
+        release_record();
+        float* fs[] = {rrs_raw, rrs_m, rrs_v, rrs_good, stat, stat_m, stat_v, stat_good,
+                       grad_rrs, grad_stat, part, Fd, Fnd};
+        for (float* f : fs) cudaFree(f);
+        cudaFree(loss_part);
+        cudaFree(scal);
+        cudaFree(bad);
+        nets = false;
+    }
+};
+
 struct nrrs_scene {
     int device = 0;
     int n_sm = 148;
@@ -139,6 +181,7 @@ struct nrrs_scene {
     int ref_count = 0;
     int ref_w = 0, ref_h = 0;
     std::vector<cudaEvent_t> events;  // reused by profiled renders
+    TrainState train;
 };
 
 namespace {
@@ -181,6 +224,7 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
 void destroy(nrrs_scene* s) {
     if (!s) return;
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    s->train.release_all();
     s->ws.release();
     cudaFree(s->nodes);
     cudaFree(s->tris);
@@ -368,19 +412,26 @@ nrrs_status nrrs_get_rrsnet_params(nrrs_scene* scene, float* params, int32_t n, 
     return NRRS_OK;
 }
 
-nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
-                        int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts* opts,
-                        float* d_rgb, void* stream, nrrs_render_stats* stats) {
-    if (!scene || !d_rgb) return fail(NRRS_ERR_INVALID_ARG, "scene or d_rgb is NULL");
-    if (width < 1 || height < 1 || spp < 1 || max_depth < 1 || max_depth > NRRS_MAX_DEPTH)
-        return fail(NRRS_ERR_INVALID_ARG, "bad image size, spp or depth");
-    if (rrs_mode < NRRS_RRS_NONE || rrs_mode > NRRS_RRS_NET_MIX)
-        return fail(NRRS_ERR_INVALID_ARG, "unknown rrs_mode");
+}  // extern "C"
+
+namespace {
+
+// Fills defaults into a render-options struct.
+nrrs_render_opts render_defaults() {
     nrrs_render_opts o;
     std::memset(&o, 0, sizeof(o));
     o.seed_lo = 1; o.cap_factor = 2; o.f_rate = 0.85f; o.alpha0 = 1.0f; o.q_max = 16.0f;
     o.eps_rel = 0.01f; o.boxcox_lambda = 0.5f; o.precision = 32; o.update_ref = 1;
-    if (opts) o = *opts;
+    return o;
+}
+
+nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
+                            int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts& o) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (width < 1 || height < 1 || spp < 1 || max_depth < 1 || max_depth > NRRS_MAX_DEPTH)
+        return fail(NRRS_ERR_INVALID_ARG, "bad image size, spp or depth");
+    if (rrs_mode < NRRS_RRS_NONE || rrs_mode > NRRS_RRS_NET_MIX)
+        return fail(NRRS_ERR_INVALID_ARG, "unknown rrs_mode");
     if (o.cap_factor < 1) return fail(NRRS_ERR_INVALID_ARG, "cap_factor < 1");
     if (!(o.f_rate > 0.0f && o.f_rate <= 1.0f) || !(o.alpha0 > 0.0f && o.alpha0 <= 1.0f))
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
@@ -388,14 +439,45 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     if (rrs_mode == NRRS_RRS_NET_MIX)
         for (int d = 1; d <= max_depth; ++d)
             if (((o.gate >> (2 * (d - 1))) & 3u) == 3u) return fail(NRRS_ERR_INVALID_ARG, "gate value 3");
+    const long long C = (long long)width * height * spp * o.cap_factor;
+    if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
+    return NRRS_OK;
+}
+
+// Record buffers of a frame (every depth's slots) for the reverse pass and training.
+nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
+    TrainState& t = sc->train;
+    if (t.rec_C >= C && t.rec_D >= D && t.npix >= npix) return NRRS_OK;
+    t.release_record();
+    const size_t n = (size_t)C * D;
+    CK(dalloc(&t.rec.dep, n));
+    CK(dalloc(&t.rec.q, n));
+    CK(dalloc(&t.rec.t, n));
+    CK(dalloc(&t.rec.feat, n * 4));
+    CK(dalloc(&t.rec.first, n));
+    CK(dalloc(&t.rec.X, n));
+    CK(dalloc(&t.rec.S, n));
+    CK(dalloc(&t.m1, n));
+    CK(dalloc(&t.m2, n));
+    CK(dalloc(&t.V, npix));
+    CK(dalloc(&t.E, npix));
+    CK(dalloc(&t.k, npix));
+    CK(dalloc(&t.rgb, npix * 3));
+    t.rec.C = C;
+    t.rec_C = C;
+    t.rec_D = D;
+    t.npix = npix;
+    return NRRS_OK;
+}
+
+// One frame (see nrrs_render); with `rec` every depth's slots are recorded.
+nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
+                        int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts& o,
+                        float* d_rgb, cudaStream_t s, nrrs_render_stats* stats,
+                        const RecordView* rec, const float* params) {
     const long long npix = (long long)width * height;
     const long long P = npix * spp;
     const long long C = P * o.cap_factor;
-    if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
-
-    DeviceGuard g(scene->device);
-    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
-    cudaStream_t s = (cudaStream_t)stream;
     bool uses_net = rrs_mode == NRRS_RRS_NET;
     if (rrs_mode == NRRS_RRS_NET_MIX)
         for (int d = 1; d <= max_depth; ++d)
@@ -429,7 +511,7 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     rp.q_max = o.q_max;
     rp.boxcox_lambda = o.boxcox_lambda;
     rp.ref = uses_heur ? ref : nullptr;
-    rp.params = scene->params;
+    rp.params = params ? params : scene->params;
     rp.trace = o.d_trace;
 
     scene->cam.aspect = (float)width / (float)height;
@@ -458,6 +540,15 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     int cur = 0;
     for (int d = 1; d <= max_depth; ++d) {
         const int kind = factor_kind(rrs_mode, o.gate, d);
+        if (rec) {  // this depth's factors, deposits and features go straight to the record
+            const size_t off = (size_t)(d - 1) * rec->C;
+            w.q = rec->q + off;
+            w.dep = rec->dep + off;
+            w.feat = rec->feat + off * 4;
+            rp.rec_first = rec->first + off;
+            rp.rec_X = rec->X + off;
+            CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C, cudaMemcpyDeviceToDevice, s));
+        }
         TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
         TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, rp, d, s));
         if (kind == kFactorNet) {
@@ -473,11 +564,16 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
             TIMED(NRRS_STAGE_SCAN, launch_split_scan(w, rp, d, s));
             TIMED(NRRS_STAGE_SCATTER, launch_split_scatter(scene->view, q[cur], q[cur ^ 1], w, rp, d, s));
             cur ^= 1;
+        } else if (rec) {
+            CK(cudaMemsetAsync(rp.rec_X, 0, sizeof(uint32_t) * C, s));
         }
     }
     const int update = o.update_ref && !o.d_pixel_ref;
     TIMED(NRRS_STAGE_FINALIZE,
           launch_finalize(w, rp, d_rgb, scene->ref_mean, scene->ref_count, update, s));
+    if (rec)
+        for (int d = max_depth; d >= 1; --d)
+            TIMED(NRRS_STAGE_REVERSE, launch_reverse(*rec, d, max_depth, ws.st->live, ws.grid_red, s));
 #undef TIMED
     CK(cudaGetLastError());
     if (update) scene->ref_count++;
@@ -504,6 +600,43 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
     }
     return NRRS_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
+                        int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts* opts,
+                        float* d_rgb, void* stream, nrrs_render_stats* stats) {
+    if (!scene || !d_rgb) return fail(NRRS_ERR_INVALID_ARG, "scene or d_rgb is NULL");
+    nrrs_render_opts o = opts ? *opts : render_defaults();
+    nrrs_status rc = validate_render(scene, width, height, spp, max_depth, rrs_mode, o);
+    if (rc != NRRS_OK) return rc;
+    DeviceGuard g(scene->device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long npix = (long long)width * height;
+    const long long C = npix * spp * o.cap_factor;
+    const RecordView* rec = nullptr;
+    if (o.d_suffix) {
+        rc = ensure_record(scene, C, max_depth, npix);
+        if (rc != NRRS_OK) return rc;
+        scene->train.rec.C = C;
+        rec = &scene->train.rec;
+    }
+    rc = render_impl(scene, width, height, spp, max_depth, rrs_mode, o, d_rgb, s, stats, rec,
+                     nullptr);
+    if (rc != NRRS_OK) return rc;
+    if (o.d_suffix)
+        for (int d = 0; d < max_depth; ++d)
+            CK(cudaMemcpyAsync(o.d_suffix + (size_t)d * C * 4, rec->S + (size_t)d * C,
+                               sizeof(float4) * C, cudaMemcpyDeviceToDevice, s));
+    return NRRS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64_t n,
                                int32_t precision, float* d_q, void* stream) {
@@ -563,6 +696,312 @@ nrrs_status nrrs_split(nrrs_scene* scene, const float* d_q_orig, int64_t n, cons
     std::lock_guard<std::mutex> lk(g_pool_mu);
     launch_split_arrays(a, p->bcnt, p->boff, p->grid, (cudaStream_t)stream);
     CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Xavier-uniform start for StatNet from a fixed linear congruential stream (the library
+// has no other source of randomness for it; callers may overwrite it with nrrs_set_params).
+void default_statnet(std::vector<float>& w) {
+    const int shapes[4][2] = {{kNH, kNF}, {kNH, kNH}, {kNH, kNH}, {kStatOut, kNH}};
+    uint64_t x = 0x5eed5eed12345ull;
+    size_t p = 0;
+    for (auto& sh : shapes) {
+        const double a = std::sqrt(6.0 / (sh[0] + sh[1]));
+        for (int i = 0; i < sh[0] * sh[1]; ++i) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            const double u = (double)(x >> 11) * (1.0 / 9007199254740992.0);
+            w[p++] = (float)((2.0 * u - 1.0) * a);
+        }
+    }
+}
+
+nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
+    TrainState& t = sc->train;
+    if (t.nets) return NRRS_OK;
+    CK(dalloc(&t.rrs_raw, kNParams));
+    CK(dalloc(&t.rrs_m, kNParams));
+    CK(dalloc(&t.rrs_v, kNParams));
+    CK(dalloc(&t.rrs_good, kNParams));
+    CK(dalloc(&t.stat, kStatParams));
+    CK(dalloc(&t.stat_m, kStatParams));
+    CK(dalloc(&t.stat_v, kStatParams));
+    CK(dalloc(&t.stat_good, kStatParams));
+    CK(dalloc(&t.grad_rrs, kNParams));
+    CK(dalloc(&t.grad_stat, kStatParams));
+    t.part_blocks = sc->n_sm * 2;
+    CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParams));
+    CK(dalloc(&t.loss_part, t.part_blocks));
+    CK(dalloc(&t.scal, 8));
+    CK(dalloc(&t.Fd, kMaxDepth));
+    CK(dalloc(&t.Fnd, kMaxDepth));
+    CK(dalloc(&t.bad, 1));
+    CK(cudaMemcpyAsync(t.rrs_raw, sc->params, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t.rrs_good, sc->params, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
+    CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
+    std::vector<float> w(kStatParams);
+    default_statnet(w);
+    CK(cudaMemcpy(t.stat, w.data(), sizeof(float) * kStatParams, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.stat_good, w.data(), sizeof(float) * kStatParams, cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * kStatParams, s));
+    CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * kStatParams, s));
+    t.nets = true;
+    return NRRS_OK;
+}
+
+nrrs_train_opts train_defaults() {
+    nrrs_train_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.width = 256; o.height = 256; o.spp = 2; o.max_depth = 16;
+    o.seed_lo = 1; o.warmup_steps = 20;
+    o.lr_rrsnet = 3e-4f; o.lr_statnet = 5e-3f;
+    o.gamma1 = 0.01f; o.gamma2 = 0.05f; o.gamma3 = 0.01f;
+    o.eps = 0.01f; o.ema_decay = 0.99f; o.f_rate = 0.85f;
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+nrrs_status nrrs_set_params(nrrs_scene* scene, int32_t which, const float* params, int32_t n,
+                            void* stream) {
+    if (!scene || !params) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or params");
+    const int want = which == NRRS_NET_STATNET ? kStatParams : kNParams;
+    if (which < 0 || which > 2 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+    DeviceGuard g(scene->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nrrs_status rc = ensure_train_nets(scene, s);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = scene->train;
+    float* dst = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw : t.stat;
+    CK(cudaMemcpyAsync(dst, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    if (which == NRRS_NET_STATNET) {
+        CK(cudaMemcpyAsync(t.stat_good, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * n, s));
+        CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * n, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int32_t n, void* stream) {
+    if (!scene || !params) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or params");
+    const int want = which == NRRS_NET_STATNET ? kStatParams : kNParams;
+    if (which < 0 || which > 2 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+    DeviceGuard g(scene->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nrrs_status rc = ensure_train_nets(scene, s);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = scene->train;
+    const float* src = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw : t.stat;
+    CK(cudaMemcpyAsync(params, src, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params, const float* d_x,
+                          const float* d_gout, int64_t n, float* d_grad, void* stream) {
+    if (!scene || (n_out != 1 && n_out != kStatOut) || n < 0 || !d_params || !d_grad ||
+        (n > 0 && (!d_x || !d_gout)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad mlp_grad arguments");
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0)
+        return fail(NRRS_ERR_INVALID_ARG, "d_x must be 16-byte aligned");
+    DeviceGuard g(scene->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nrrs_status rc = ensure_train_nets(scene, s);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = scene->train;
+    const int P = kNH * kNF + 2 * kNH * kNH + n_out * kNH;
+    TrainArgs a{};
+    a.params = d_params;
+    a.gin = d_gout;
+    a.scale = 1.0f;
+    RecordView r{};
+    r.feat = reinterpret_cast<float4*>(const_cast<float*>(d_x));
+    r.C = n;
+    TrainBatch b{};
+    b.D = 1;
+    b.total = n;
+    b.net_mask = 1u;
+    CK(launch_mlp_grad_given(n_out, a, r, b, t.part_blocks, t.part, t.loss_part, s));
+    launch_reduce_grad(t.part, t.part_blocks, P, d_grad, s);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_rrsnet_dloss(const float* d_q_nrrs, const float* d_F, const float* d_Fn,
+                              const float* d_t, const int32_t* d_pixel, const float* d_m1,
+                              const float* d_m2, const float* d_E, double Ebar, const float* d_Iref,
+                              const int32_t* d_k, int64_t n, float eps, float g1, float g2, float g3,
+                              float* d_dq, void* stream) {
+    if (n < 0 || (n > 0 && (!d_q_nrrs || !d_F || !d_Fn || !d_t || !d_pixel || !d_m1 || !d_m2 ||
+                            !d_E || !d_Iref || !d_k || !d_dq)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad rrsnet_dloss arguments");
+    launch_rrsnet_dloss(d_q_nrrs, d_F, d_Fn, d_t, d_pixel, d_m1, d_m2, d_E, Ebar, d_Iref, d_k, n,
+                        eps, g1, g2, g3, d_dq, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int32_t n,
+                           int32_t step, float lr, float b1, float b2, float eps, void* stream) {
+    if (n < 0 || step < 1 || (n > 0 && (!d_params || !d_grad || !d_m || !d_v)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad adam arguments");
+    if (n > 0) launch_adam(d_params, d_grad, d_m, d_v, n, step, lr, b1, b2, eps, nullptr, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void* stream,
+                            nrrs_train_stats* out) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    nrrs_train_opts o = opts ? *opts : train_defaults();
+    nrrs_render_opts ro = render_defaults();
+    ro.seed_lo = o.seed_lo;
+    ro.seed_hi = o.seed_hi;
+    ro.f_rate = o.f_rate;
+    ro.d_pixel_ref = o.d_pixel_ref;
+    nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, o.max_depth, NRRS_RRS_NET, ro);
+    if (rc != NRRS_OK) return rc;
+    if (o.warmup_steps < 0 || !(o.eps > 0.0f) || !(o.ema_decay >= 0.0f && o.ema_decay < 1.0f))
+        return fail(NRRS_ERR_INVALID_ARG, "bad training options");
+    DeviceGuard g(scene->device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    TrainState& t = scene->train;
+    rc = ensure_train_nets(scene, s);
+    if (rc != NRRS_OK) return rc;
+    const int D = o.max_depth;
+    const long long npix = (long long)o.width * o.height;
+    const long long C = npix * o.spp * 2;
+    rc = ensure_record(scene, C, D, npix);
+    if (rc != NRRS_OK) return rc;
+    t.rec.C = C;
+    ro.frame = o.frame + (uint32_t)t.step;
+
+    // 1. a recorded frame with the inference weights, NET factors at every depth
+    nrrs_render_stats rs;
+    rc = render_impl(scene, o.width, o.height, o.spp, D, NRRS_RRS_NET, ro, t.rgb, s, &rs, &t.rec,
+                     nullptr);
+    if (rc != NRRS_OK) return rc;
+    TrainBatch b{};
+    b.D = D;
+    b.net_mask = D >= 32 ? 0xFFFFFFFFu : ((1u << D) - 1u);
+    float Fh[kMaxDepth], Fnh[kMaxDepth];
+    long long off = 0;
+    for (int d = 0; d < D; ++d) {
+        b.offset[d] = off;
+        off += rs.live[d];
+        Fh[d] = rs.F[d];
+        const double fn = rs.sum_q[d] > 0.0 ? (double)C / rs.sum_q[d] : 1.0;
+        Fnh[d] = (float)(fn < 1.0 ? fn : 1.0);  // Eq. F_norm, downscale only, no rate control
+    }
+    b.offset[D] = off;
+    b.total = off;
+    CK(cudaMemcpy(t.Fd, Fh, sizeof(float) * D, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.Fnd, Fnh, sizeof(float) * D, cudaMemcpyHostToDevice));
+
+    // 2. pixel errors against the reference, samples per pixel, mean error
+    const float* ref = o.d_pixel_ref ? o.d_pixel_ref : scene->ref_mean;
+    launch_pixel_error(t.rec, o.spp, npix, ref, o.eps, t.V, t.E, s);
+    CK(cudaMemsetAsync(t.k, 0, sizeof(int) * npix, s));
+    launch_count_samples(t.rec, b, t.k, scene->n_sm * 4, s);
+    launch_mean(t.E, npix, t.scal + 0, s);
+    launch_pixel_terms(t.E, npix, t.scal + 0, t.k, t.scal + 4, s);  // L_min, L_avg, N
+    double host_terms[3];
+    CK(cudaMemcpyAsync(host_terms, t.scal + 4, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double N = host_terms[2];
+
+    // 3. StatNet (moments for the gradient transfer), then RRSNet
+    TrainArgs a{};
+    a.m1 = t.m1;
+    a.m2 = t.m2;
+    a.F = t.Fd;
+    a.Fn = t.Fnd;
+    a.E = t.E;
+    a.Ebar = t.scal + 0;
+    a.ref = ref;
+    a.k = t.k;
+    a.eps = o.eps;
+    a.g1 = o.gamma1;
+    a.g2 = o.gamma2;
+    a.g3 = o.gamma3;
+    a.params = t.stat;
+    a.scale = N > 0 ? (float)(1.0 / N) : 0.0f;
+    CK(launch_mlp_train(kTrainStatNet, a, t.rec, b, t.part_blocks, t.part, t.loss_part, s));
+    launch_reduce_grad(t.part, t.part_blocks, kStatParams, t.grad_stat, s);
+    launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 1, s);
+    const bool warm = t.step < o.warmup_steps;
+    a.params = t.rrs_raw;
+    a.scale = warm ? (N > 0 ? (float)(1.0 / N) : 0.0f) : 1.0f;
+    CK(launch_mlp_train(warm ? kTrainRrsWarmup : kTrainRrsFull, a, t.rec, b, t.part_blocks, t.part,
+                        t.loss_part, s));
+    launch_reduce_grad(t.part, t.part_blocks, kNParams, t.grad_rrs, s);
+    launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 2, s);
+
+    // 4. Adam for both networks (Sec. 4 "Training": lr 0.005 StatNet, 0.0003 RRSNet)
+    CK(cudaMemsetAsync(t.bad, 0, sizeof(int), s));
+    const int step = (int)t.step + 1;
+    launch_adam(t.stat, t.grad_stat, t.stat_m, t.stat_v, kStatParams, step, o.lr_statnet, 0.9f,
+                0.999f, 1e-8f, t.bad, s);
+    launch_adam(t.rrs_raw, t.grad_rrs, t.rrs_m, t.rrs_v, kNParams, step, o.lr_rrsnet, 0.9f, 0.999f,
+                1e-8f, t.bad, s);
+    int bad = 0;
+    double losses[2];
+    CK(cudaMemcpyAsync(&bad, t.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(losses, t.scal + 1, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double loss_stat = N > 0 ? losses[0] / N : 0.0;
+    const double loss_rrs_warm = N > 0 ? losses[1] / N : 0.0;
+    const double L_rrs = losses[1];
+    const double L_total = warm ? loss_rrs_warm
+                                : o.gamma1 * host_terms[1] + o.gamma2 * host_terms[0] + o.gamma3 * L_rrs;
+    int fallback = 0;
+    if (bad || !std::isfinite(L_total) || !std::isfinite(loss_stat)) fallback = 1;
+    // fallback monitor: after the warm-up, a loss EMA far above its running minimum
+    if (!fallback && !warm) {
+        t.loss_ema = t.full_steps == 0 ? L_total : 0.9 * t.loss_ema + 0.1 * L_total;
+        t.loss_min = t.full_steps == 0 ? t.loss_ema : std::min(t.loss_min, t.loss_ema);
+        t.full_steps++;
+        if (t.full_steps > 10 && t.loss_ema > 1.5 * t.loss_min) fallback = 2;
+    }
+    if (fallback) {  // restore the last good weights and forget the moments
+        CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.stat, t.stat_good, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
+        CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
+        CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * kStatParams, s));
+        CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * kStatParams, s));
+        if (fallback == 2) {
+            t.loss_ema = t.loss_min;
+        }
+    } else {
+        CK(cudaMemcpyAsync(t.rrs_good, t.rrs_raw, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.stat_good, t.stat, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
+        // inference weights: EMA of the trained weights (Sec. 4 "Training", as in NRC)
+        launch_ema(scene->params, t.rrs_raw, kNParams, o.ema_decay, s);
+        t.step++;
+    }
+    CK(cudaGetLastError());
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->step = t.step;
+        out->samples = (int64_t)N;
+        out->segments = rs.segments;
+        out->loss_statnet = loss_stat;
+        out->loss_rrsnet = warm ? loss_rrs_warm : L_total;
+        out->loss_avg = host_terms[1];
+        out->loss_min = host_terms[0];
+        out->loss_rrs = warm ? 0.0 : L_rrs;
+        out->phase = warm ? 1 : 2;
+        out->fallback = fallback;
+    }
     return NRRS_OK;
 }
 

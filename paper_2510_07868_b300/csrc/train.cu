@@ -1,0 +1,486 @@
+// Online training of RRSNet and StatNet on the GPU (Sec. 3.2 "Loss Design", Sec. 4
+// "Training"): the reverse pass over a recorded frame, pixel errors, one persistent
+// forward + backward kernel for both networks, the reduction of per-block gradients,
+// Adam and the EMA of the weights.
+#include <cfloat>
+
+#include "train.cuh"
+
+namespace nrrs {
+
+namespace {
+
+constexpr int kTile = 128;  // samples per block tile of the training kernel
+
+__device__ __forceinline__ uint32_t fb(float f) { return __float_as_uint(f); }
+
+// ------------------------------------------------------------------ reverse pass
+// Suffix sums of depth d: S = own deposit + sum of the children's S (children of slot i
+// are the slots [first_i, first_i + X_i) of depth d+1 that fit in the queue).  S / t is
+// the vertex's estimate of outgoing radiance.
+__global__ void k_reverse(RecordView r, int d, int D, const long long* live) {
+    const long long n = live[d - 1];
+    const long long nn = d < D ? live[d] : 0;
+    const size_t base = (size_t)(d - 1) * r.C, nbase = (size_t)d * r.C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 dep = r.dep[base + i];
+        float sx = dep.x, sy = dep.y, sz = dep.z;
+        if (d < D) {
+            const long long first = r.first[base + i];
+            const long long last = first + r.X[base + i];
+            for (long long j = first; j < last && j < nn; ++j) {
+                const float4 c = r.S[nbase + j];
+                sx += c.x; sy += c.y; sz += c.z;
+            }
+        }
+        r.S[base + i] = make_float4(sx, sy, sz, dep.w);
+    }
+}
+
+// Per pixel: V = unbiased variance over the spp primary samples of their suffix sums,
+// divided by spp (the variance of the pixel estimate), mean over RGB; E = V / (I^2 + eps)
+// with I the mean over RGB of the reference (Eq. loss-function_min).  Samples of pixel p
+// are the depth-1 slots p*spp .. p*spp+spp-1.
+__global__ void k_pixel_error(RecordView r, int spp, long long npix, const float* ref, float eps,
+                              float* V, float* E) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    double v = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double m = 0.0;
+        for (int s = 0; s < spp; ++s) {
+            const float4 S = r.S[p * spp + s];
+            m += c == 0 ? S.x : c == 1 ? S.y : S.z;
+        }
+        m /= spp;
+        double q = 0.0;
+        for (int s = 0; s < spp; ++s) {
+            const float4 S = r.S[p * spp + s];
+            const double dd = (c == 0 ? S.x : c == 1 ? S.y : S.z) - m;
+            q += dd * dd;
+        }
+        v += spp > 1 ? q / (spp - 1) / spp : 0.0;
+    }
+    V[p] = (float)(v / 3.0);
+    const double I = ref ? ((double)ref[3 * p] + ref[3 * p + 1] + ref[3 * p + 2]) / 3.0 : 0.0;
+    E[p] = (float)(v / 3.0 / (I * I + eps));
+}
+
+// k_i: trainable samples (recorded q_orig > 0 at a network depth) of every pixel.
+__global__ void k_count_samples(RecordView r, TrainBatch b, int* k) {
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < b.total;
+         u += (long long)gridDim.x * blockDim.x) {
+        int d = 0;
+        while (d + 1 < b.D && b.offset[d + 1] <= u) ++d;
+        if (!((b.net_mask >> d) & 1u)) continue;
+        const long long i = u - b.offset[d];
+        const size_t g = (size_t)d * r.C + i;
+        if (r.q[g] > 0.0f) atomicAdd(&k[fb(r.dep[g].w)], 1);
+    }
+}
+
+// FP64 mean of E over pixels (fixed order).
+__global__ void k_mean(const float* E, long long n, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += E[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = n > 0 ? s / (double)n : 0.0;
+}
+
+// L_min = sum_i E_i, L_avg = sum_i (E_i - Ebar)^2 (Eq. loss-function_min / _avg), and the
+// number of training samples, all in FP64 and fixed order.
+__global__ void k_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
+                              double* out) {
+    __shared__ double sh[32];
+    const double eb = *Ebar;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        a += E[i];
+        b += ((double)E[i] - eb) * ((double)E[i] - eb);
+        c += k[i];
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+        out[2] = c;
+    }
+}
+
+// ------------------------------------------------------------------ MLP training
+// Shared-memory layout of one tile (kTile samples): inputs X[kTile][16], hidden
+// activations A1..A3[kTile][32] (post Leaky ReLU; their sign is the sign of the
+// pre-activation), output gradients G[kTile][8], then the weights.
+struct TrainSmem {
+    float X[kTile][kNF];
+    float A[3][kTile][kNH];
+    float G[kTile][8];
+};
+
+__device__ __forceinline__ float lrelu(float a) { return a > 0.0f ? a : kLeak * a; }
+
+// Loss gradient of one sample at the network outputs; returns false for a sample that
+// does not train.  `out` holds the raw outputs (RRSNet: pre-activation z).
+template <int MODE>
+__device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView& r, int d,
+                                            long long i, const float* out, float* gout,
+                                            double* loss) {
+    const size_t g = (size_t)d * r.C + i;
+    const float4 dep = r.dep[g];
+    const float4 t = r.t[g];
+    if (MODE == kTrainStatNet) {
+        // targets: one-sample reflected radiance <L> = (S - deposit) / t per channel and <L>^2
+        const float4 S = r.S[g];
+        const float tt[3] = {t.x, t.y, t.z};
+        const float ss[3] = {S.x - dep.x, S.y - dep.y, S.z - dep.z};
+        for (int c = 0; c < 3; ++c) {
+            const float L = tt[c] > 0.0f ? ss[c] / tt[c] : 0.0f;
+            const float L2 = L * L;
+            const float w1 = 1.0f / (L2 + a.eps), w2 = 1.0f / (L2 * L2 + a.eps);
+            const float d1 = out[c] - L, d2 = out[3 + c] - L2;
+            gout[c] = 2.0f * d1 * w1 * a.scale;
+            gout[3 + c] = 2.0f * d2 * w2 * a.scale;
+            *loss += (double)(d1 * d1 * w1 + d2 * d2 * w2);
+        }
+        return true;
+    }
+    // RRSNet: q_nrrs = softplus'(z)
+    const float z = out[0];
+    const float q = z < 0.0f ? log1pf(expf(z)) : fmaf(0.5f, z, 0.693147180559945f);
+    const float dqdz = z < 0.0f ? 1.0f / (1.0f + expf(-z)) : 0.5f;
+    float dq;
+    if (MODE == kTrainRrsWarmup) {
+        // Sec. 4 "Training" step (1): regress to 1 with the relative L2 loss
+        dq = 2.0f * (q - 1.0f) / (1.0f + a.eps);
+        *loss += (double)((q - 1.0f) * (q - 1.0f) / (1.0f + a.eps));
+    } else {
+        const float F = a.F[d], Fn = a.Fn[d];
+        const float qu = F * r.q[g];  // factor the frame actually used
+        const float tm = (t.x + t.y + t.z) * (1.0f / 3.0f);
+        const float m1 = a.m1[g], m2 = a.m2[g];
+        const float VH = fmaxf(m2 - m1 * m1, 0.0f);
+        const float H = qu < 1.0f ? m2 : VH;  // Eq. gradient_transfer_rr_mc / splitting_mc
+        const float dV = -tm * tm * H / (qu * qu);
+        const uint32_t pix = fb(dep.w);
+        const float I = a.ref ? (a.ref[3 * pix] + a.ref[3 * pix + 1] + a.ref[3 * pix + 2]) *
+                                    (1.0f / 3.0f)
+                              : 0.0f;
+        const float dLdE = a.g1 * 2.0f * (a.E[pix] - (float)*a.Ebar) + a.g2;
+        const float dLdV = dLdE / (I * I + a.eps) / (float)max(a.k[pix], 1);
+        const float qn = Fn * q;  // stop-gradient target of L_rrs
+        dq = dLdV * dV * F + a.g3 * 2.0f * (q - qn);
+        *loss += (double)((q - qn) * (q - qn));
+    }
+    gout[0] = dq * dqdz * a.scale;
+    return true;
+}
+
+template <int NOUT, int MODE>
+__global__ void __launch_bounds__(kTile)
+k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    float* W = reinterpret_cast<float*>(smem_raw + sizeof(TrainSmem));
+    constexpr int P = kNH * kNF + 2 * kNH * kNH + NOUT * kNH;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) W[p] = a.params[p];
+    const float* W1 = W;
+    const float* W2 = W + kNH * kNF;
+    const float* W3 = W2 + kNH * kNH;
+    const float* W4 = W3 + kNH * kNH;
+    // weight-gradient entries owned by this thread, accumulated over all tiles
+    constexpr int PER = (P + kTile - 1) / kTile;
+    float acc[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) acc[e] = 0.0f;
+    double loss = 0.0;
+    const int tid = threadIdx.x;
+    const long long tiles = (b.total + kTile - 1) / kTile;
+    __syncthreads();
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long u = tile * kTile + tid;
+        // ---- forward of this thread's sample
+        float x[kNF];
+        bool active = false;
+        int d = 0;
+        long long i = 0;
+        if (MODE == kTrainGiven && u < b.total) {
+            active = true;
+            const float4* f = r.feat + 4 * u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = f[k];
+                x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+            }
+        } else if (u < b.total) {
+            while (d + 1 < b.D && b.offset[d + 1] <= u) ++d;
+            i = u - b.offset[d];
+            const size_t g = (size_t)d * r.C + i;
+            active = ((b.net_mask >> d) & 1u) && r.q[g] > 0.0f;
+            if (active) {
+                const float4* f = r.feat + 4 * g;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 v = f[k];
+                    x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+                }
+                if (MODE == kTrainStatNet) x[13] = x[14] = x[15] = 0.0f;  // no throughput
+            }
+        }
+        if (!active)
+            for (int k = 0; k < kNF; ++k) x[k] = 0.0f;
+        for (int k = 0; k < kNF; ++k) sm.X[tid][k] = x[k];
+        float h[kNH], hn[kNH];
+        for (int j = 0; j < kNH; ++j) {
+            float s = 0.0f;
+            for (int k = 0; k < kNF; ++k) s = fmaf(W1[j * kNF + k], x[k], s);
+            h[j] = lrelu(s);
+            sm.A[0][tid][j] = h[j];
+        }
+        for (int j = 0; j < kNH; ++j) {
+            float s = 0.0f;
+            for (int k = 0; k < kNH; ++k) s = fmaf(W2[j * kNH + k], h[k], s);
+            hn[j] = lrelu(s);
+            sm.A[1][tid][j] = hn[j];
+        }
+        for (int j = 0; j < kNH; ++j) {
+            float s = 0.0f;
+            for (int k = 0; k < kNH; ++k) s = fmaf(W3[j * kNH + k], hn[k], s);
+            h[j] = lrelu(s);
+            sm.A[2][tid][j] = h[j];
+        }
+        float out[NOUT], gout[8];
+        for (int o = 0; o < NOUT; ++o) {
+            float s = 0.0f;
+            for (int k = 0; k < kNH; ++k) s = fmaf(W4[o * kNH + k], h[k], s);
+            out[o] = s;
+        }
+        for (int o = 0; o < 8; ++o) gout[o] = 0.0f;
+        if (MODE == kTrainGiven) {
+            if (active)
+                for (int o = 0; o < NOUT; ++o) gout[o] = a.gin[u * NOUT + o];
+        } else if (active) {
+            if (MODE == kTrainStatNet && a.m1) {  // moments for the RRSNet gradient
+                const size_t g = (size_t)d * r.C + i;
+                a.m1[g] = (out[0] + out[1] + out[2]) * (1.0f / 3.0f);
+                a.m2[g] = (out[3] + out[4] + out[5]) * (1.0f / 3.0f);
+            }
+            sample_grad<MODE>(a, r, d, i, out, gout, &loss);
+        }
+        for (int o = 0; o < NOUT; ++o) sm.G[tid][o] = gout[o];
+        __syncthreads();
+        // ---- weight gradients of the output layer: sum_s G[s][o] A3[s][k]
+        constexpr int o4 = kNH * kNF + 2 * kNH * kNH;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int p = tid + e * kTile;
+            if (p >= o4 && p < P) {
+                const int o = (p - o4) / kNH, k = (p - o4) % kNH;
+                float s = 0.0f;
+                for (int q = 0; q < kTile; ++q) s = fmaf(sm.G[q][o], sm.A[2][q][k], s);
+                acc[e] += s;
+            }
+        }
+        // ---- this sample's delta at layer 3: (W4^T g) * lrelu'(a3)
+        float dl[kNH];
+        for (int k = 0; k < kNH; ++k) {
+            float s = 0.0f;
+            for (int o = 0; o < NOUT; ++o) s = fmaf(W4[o * kNH + k], gout[o], s);
+            dl[k] = s * (sm.A[2][tid][k] > 0.0f ? 1.0f : kLeak);
+        }
+        __syncthreads();
+        for (int k = 0; k < kNH; ++k) sm.A[2][tid][k] = dl[k];  // A3 now holds delta3
+        __syncthreads();
+        // layers 3, 2, 1: grads sum_s delta_l[s][j] in_l[s][k], then delta_{l-1}
+        for (int l = 2; l >= 0; --l) {
+            const int nin = l == 0 ? kNF : kNH;
+            const int off = l == 0 ? 0 : kNH * kNF + (l - 1) * kNH * kNH;
+            const int cnt = kNH * nin;
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const int p = tid + e * kTile;
+                if (p >= off && p < off + cnt) {
+                    const int j = (p - off) / nin, k = (p - off) % nin;
+                    float s = 0.0f;
+                    if (l == 0) {
+                        for (int q = 0; q < kTile; ++q) s = fmaf(sm.A[0][q][j], sm.X[q][k], s);
+                    } else {
+                        for (int q = 0; q < kTile; ++q) s = fmaf(sm.A[l][q][j], sm.A[l - 1][q][k], s);
+                    }
+                    acc[e] += s;
+                }
+            }
+            if (l == 0) break;
+            const float* Wl = l == 2 ? W3 : W2;
+            float dn[kNH];
+            for (int k = 0; k < kNH; ++k) {
+                float s = 0.0f;
+                for (int j = 0; j < kNH; ++j) s = fmaf(Wl[j * kNH + k], sm.A[l][tid][j], s);
+                dn[k] = s * (sm.A[l - 1][tid][k] > 0.0f ? 1.0f : kLeak);
+            }
+            __syncthreads();
+            for (int k = 0; k < kNH; ++k) sm.A[l - 1][tid][k] = dn[k];
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int p = tid + e * kTile;
+        if (p < P) part[(size_t)blockIdx.x * P + p] = acc[e];
+    }
+    __shared__ double shl[32];
+    loss = block_sum(loss, shl);
+    if (tid == 0) loss_part[blockIdx.x] = loss;
+}
+
+// Sum of the per-block gradients in block order (deterministic).
+__global__ void k_reduce_grad(const float* part, int G, int P, float* grad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float s = 0.0f;
+    for (int b = 0; b < G; ++b) s += part[(size_t)b * P + p];
+    grad[p] = s;
+}
+
+__global__ void k_reduce_loss(const double* part, int G, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// Adam (Kingma & Ba): bias-corrected first and second moments; non-finite gradients
+// set *bad and leave the weights untouched.
+__global__ void k_adam(float* P, const float* G, float* m, float* v, int n, int step, float lr,
+                       float b1, float b2, float eps, int* bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    if (!(fabsf(g) <= FLT_MAX)) {
+        if (bad) atomicOr(bad, 1);
+        return;
+    }
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_ema(float* E, const float* P, int n, float decay) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) E[i] = decay * E[i] + (1.0f - decay) * P[i];
+}
+
+// Stand-alone loss gradient on plain arrays (for parity tests): one thread per sample.
+__global__ void k_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn,
+                               const float* t, const int* pixel, const float* m1, const float* m2,
+                               const float* E, double Ebar, const float* Iref,
+                               const int* k, long long n, float eps, float g1, float g2,
+                               float g3, float* dq) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = pixel[s];
+    const float qu = F[s] * q_nrrs[s];
+    const float VH = fmaxf(m2[s] - m1[s] * m1[s], 0.0f);
+    const float H = qu < 1.0f ? m2[s] : VH;
+    const float dV = -t[s] * t[s] * H / (qu * qu);
+    const float dLdE = g1 * 2.0f * (E[i] - (float)Ebar) + g2;
+    const float dLdV = dLdE / (Iref[i] * Iref[i] + eps) / (float)max(k[i], 1);
+    dq[s] = dLdV * dV * F[s] + g3 * 2.0f * (q_nrrs[s] - Fn[s] * q_nrrs[s]);
+}
+
+template <int NOUT, int MODE>
+size_t train_smem() {
+    return sizeof(TrainSmem) + sizeof(float) * (kNH * kNF + 2 * kNH * kNH + NOUT * kNH);
+}
+
+template <int NOUT, int MODE>
+cudaError_t launch_train_t(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
+                           float* part, double* loss_part, cudaStream_t s) {
+    const size_t smem = train_smem<NOUT, MODE>();
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train<NOUT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_train<NOUT, MODE><<<grid, kTile, smem, s>>>(a, r, b, part, loss_part);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int train_tile() { return kTile; }
+
+void launch_reverse(const RecordView& r, int d, int D, const long long* live, int grid,
+                    cudaStream_t s) {
+    k_reverse<<<grid, 256, 0, s>>>(r, d, D, live);
+}
+
+void launch_pixel_error(const RecordView& r, int spp, long long npix, const float* ref, float eps,
+                        float* V, float* E, cudaStream_t s) {
+    k_pixel_error<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(r, spp, npix, ref, eps, V, E);
+}
+
+void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
+                          cudaStream_t s) {
+    k_count_samples<<<grid, 256, 0, s>>>(r, b, k);
+}
+
+void launch_mean(const float* E, long long n, double* out, cudaStream_t s) {
+    k_mean<<<1, 1024, 0, s>>>(E, n, out);
+}
+
+void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
+                        double* out, cudaStream_t s) {
+    k_pixel_terms<<<1, 1024, 0, s>>>(E, n, Ebar, k, out);
+}
+
+cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
+                             const TrainBatch& b, int grid, float* part, double* loss_part,
+                             cudaStream_t s) {
+    switch (which) {
+        case kTrainStatNet: return launch_train_t<6, kTrainStatNet>(a, r, b, grid, part, loss_part, s);
+        case kTrainRrsWarmup: return launch_train_t<1, kTrainRrsWarmup>(a, r, b, grid, part, loss_part, s);
+        default: return launch_train_t<1, kTrainRrsFull>(a, r, b, grid, part, loss_part, s);
+    }
+}
+
+cudaError_t launch_mlp_grad_given(int n_out, const TrainArgs& a, const RecordView& r,
+                                  const TrainBatch& b, int grid, float* part, double* loss_part,
+                                  cudaStream_t s) {
+    return n_out == 1 ? launch_train_t<1, kTrainGiven>(a, r, b, grid, part, loss_part, s)
+                      : launch_train_t<6, kTrainGiven>(a, r, b, grid, part, loss_part, s);
+}
+
+void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream_t s) {
+    k_reduce_grad<<<(P + 255) / 256, 256, 0, s>>>(part, G, P, grad);
+}
+
+void launch_reduce_loss(const double* part, int G, double* out, cudaStream_t s) {
+    k_reduce_loss<<<1, 256, 0, s>>>(part, G, out);
+}
+
+void launch_adam(float* P, const float* G, float* m, float* v, int n, int step, float lr,
+                 float b1, float b2, float eps, int* bad, cudaStream_t s) {
+    k_adam<<<(n + 255) / 256, 256, 0, s>>>(P, G, m, v, n, step, lr, b1, b2, eps, bad);
+}
+
+void launch_ema(float* E, const float* P, int n, float decay, cudaStream_t s) {
+    k_ema<<<(n + 255) / 256, 256, 0, s>>>(E, P, n, decay);
+}
+
+void launch_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn, const float* t,
+                         const int* pixel, const float* m1, const float* m2, const float* E,
+                         double Ebar, const float* Iref, const int* k, long long n,
+                         float eps, float g1, float g2, float g3, float* dq, cudaStream_t s) {
+    if (n <= 0) return;
+    k_rrsnet_dloss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q_nrrs, F, Fn, t, pixel, m1, m2, E,
+                                                              Ebar, Iref, k, n, eps, g1, g2, g3, dq);
+}
+
+}  // namespace nrrs

@@ -1,0 +1,79 @@
+// Device views and launchers of the training kernels (train.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wavefront.cuh"
+
+namespace nrrs {
+
+constexpr int kStatOut = 6;  // StatNet outputs: E[<L>] and E[<L>^2] per RGB channel
+constexpr int kStatParams = kNH * kNF + 2 * kNH * kNH + kStatOut * kNH;  // 2752
+
+// A recorded frame: slot (d, i) of depth d (0-based here) lives at d * C + i.
+struct RecordView {
+    float4* dep;      // deposit rgb, pixel bits
+    float* q;         // q_orig
+    float4* t;        // prefix throughput rgb, sample bits
+    float4* feat;     // 4 float4 of RRSNet features per slot
+    uint32_t* first;  // first child slot in the next depth
+    uint32_t* X;      // children requested
+    float4* S;        // suffix sum rgb, pixel bits (reverse pass)
+    long long C;
+};
+
+// The training batch: every slot of every depth, concatenated in depth order.
+struct TrainBatch {
+    long long offset[kMaxDepth + 1];  // offset[d] = first batch index of depth d
+    long long total;
+    int D;
+    uint32_t net_mask;  // depths whose slots carry RRSNet features
+};
+
+// kTrainGiven: plain inputs in RecordView::feat ([n][16]) and given output gradients in
+// TrainArgs::gin ([n][n_out]); the kernel returns sum_s d(gin_s . out_s)/dW.
+enum TrainMode : int { kTrainStatNet = 0, kTrainRrsWarmup = 1, kTrainRrsFull = 2, kTrainGiven = 3 };
+
+struct TrainArgs {
+    const float* params;  // weights of the network being trained
+    float* m1;            // StatNet moments per slot (written by the StatNet pass)
+    float* m2;
+    const float* F;       // applied factor per depth
+    const float* Fn;      // normalization factor without rate control per depth
+    const float* E;       // pixel errors
+    const double* Ebar;   // mean pixel error
+    const float* ref;     // reference image [npix * 3] or null
+    const int* k;         // training samples per pixel
+    float eps, g1, g2, g3;
+    float scale;          // factor on every sample's gradient (1/N for mean losses)
+    const float* gin;     // kTrainGiven: output gradients [n][n_out]
+};
+
+int train_tile();
+void launch_reverse(const RecordView& r, int d, int D, const long long* live, int grid,
+                    cudaStream_t s);
+void launch_pixel_error(const RecordView& r, int spp, long long npix, const float* ref, float eps,
+                        float* V, float* E, cudaStream_t s);
+void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
+                          cudaStream_t s);
+void launch_mean(const float* E, long long n, double* out, cudaStream_t s);
+// out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), out[2] = sum k (samples)
+void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
+                        double* out, cudaStream_t s);
+cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
+                             const TrainBatch& b, int grid, float* part, double* loss_part,
+                             cudaStream_t s);
+cudaError_t launch_mlp_grad_given(int n_out, const TrainArgs& a, const RecordView& r,
+                                  const TrainBatch& b, int grid, float* part, double* loss_part,
+                                  cudaStream_t s);
+void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream_t s);
+void launch_reduce_loss(const double* part, int G, double* out, cudaStream_t s);
+void launch_adam(float* P, const float* G, float* m, float* v, int n, int step, float lr,
+                 float b1, float b2, float eps, int* bad, cudaStream_t s);
+void launch_ema(float* E, const float* P, int n, float decay, cudaStream_t s);
+void launch_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn, const float* t,
+                         const int* pixel, const float* m1, const float* m2, const float* E,
+                         double Ebar, const float* Iref, const int* k, long long n,
+                         float eps, float g1, float g2, float g3, float* dq, cudaStream_t s);
+
+}  // namespace nrrs

@@ -686,6 +686,11 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
         }
         uint32_t tile_total;
         const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
+        if (rp.rec_first && i < end) {
+            const unsigned long long f = carry + pre;
+            rp.rec_first[i] = (uint32_t)(f < (unsigned long long)rp.cap ? f : (unsigned long long)rp.cap);
+            rp.rec_X[i] = X;
+        }
         if (X > 0) {
             const float2 hh = w.hit[i];
             const int slot = __float_as_int(hh.y);

@@ -73,6 +73,8 @@ struct RenderParams {
     const float* ref;     // reference image [npix*3] (running mean or caller's) or null
     const float* params;  // RRSNet weights (device, 2592 floats)
     uint32_t* trace;      // optional per-depth trace
+    uint32_t* rec_first;  // record mode: first child slot of every parent of this depth
+    uint32_t* rec_X;      // record mode: children requested by every parent of this depth
 };
 
 enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFactorNet = 3 };

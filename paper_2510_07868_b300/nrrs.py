@@ -23,9 +23,11 @@ RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
 GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
 STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 MAX_DEPTH = 32
-STAGES = 9
+STAGES = 10
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
-               "finalize", "rrsnet", "shade"]
+               "finalize", "rrsnet", "shade", "reverse"]
+NET_RRSNET, NET_RRSNET_TRAIN, NET_STATNET = 0, 1, 2
+STATNET_PARAMS = 2752
 N_FEATURES = 16
 RRSNET_PARAMS = 2592
 
@@ -33,6 +35,8 @@ EXPORTED = [
     "nrrs_status_string", "nrrs_last_error", "nrrs_create_scene", "nrrs_destroy_scene",
     "nrrs_scene_info", "nrrs_set_rrsnet_params", "nrrs_get_rrsnet_params", "nrrs_render",
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
+    "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
+    "nrrs_rrsnet_dloss", "nrrs_adam_step",
 ]
 
 
@@ -48,13 +52,13 @@ class RenderOpts(C.Structure):
                 ("q_max", C.c_float), ("eps_rel", C.c_float), ("boxcox_lambda", C.c_float),
                 ("precision", C.c_int32), ("gate", C.c_uint64), ("d_pixel_ref", C.c_void_p),
                 ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
-                ("profile", C.c_int32), ("reserved0", C.c_int32)]
+                ("profile", C.c_int32), ("reserved0", C.c_int32), ("d_suffix", C.c_void_p)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
                 eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
-                update_ref=1, reset_ref=0, d_trace=None, profile=0, reserved0=0)
+                update_ref=1, reset_ref=0, d_trace=None, profile=0, reserved0=0, d_suffix=None)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -83,6 +87,34 @@ class RenderStats(C.Structure):
         }
 
 
+class TrainOpts(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
+                ("max_depth", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
+                ("frame", C.c_uint32), ("warmup_steps", C.c_int32), ("lr_rrsnet", C.c_float),
+                ("lr_statnet", C.c_float), ("gamma1", C.c_float), ("gamma2", C.c_float),
+                ("gamma3", C.c_float), ("eps", C.c_float), ("ema_decay", C.c_float),
+                ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p)]
+
+    @classmethod
+    def defaults(cls, **kw):
+        o = cls(width=256, height=256, spp=2, max_depth=16, seed_lo=1, seed_hi=0, frame=0,
+                warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
+                gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+
+class TrainStats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("samples", C.c_int64), ("segments", C.c_int64),
+                ("loss_statnet", C.c_double), ("loss_rrsnet", C.c_double),
+                ("loss_avg", C.c_double), ("loss_min", C.c_double), ("loss_rrs", C.c_double),
+                ("phase", C.c_int32), ("fallback", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -103,6 +135,14 @@ def _load():
         "nrrs_split": ([P, P, I64, P, P, P, P, U32, U32, U32, U32, I64, P, P, P, P, P, P, P], I32),
         "nrrs_split_noalloc": ([P, I64, P, P, P, P, U32, U32, U32, U32, I64, P, P, P, P, P, P, P],
                                I32),
+        "nrrs_train_step": ([P, P, P, P], I32),
+        "nrrs_set_params": ([P, I32, P, I32, P], I32),
+        "nrrs_get_params": ([P, I32, P, I32, P], I32),
+        "nrrs_mlp_grad": ([P, I32, P, P, P, I64, P, P], I32),
+        "nrrs_rrsnet_dloss": ([P, P, P, P, P, P, P, P, D, P, P, I64, C.c_float, C.c_float,
+                               C.c_float, C.c_float, P, P], I32),
+        "nrrs_adam_step": ([P, P, P, P, I32, I32, C.c_float, C.c_float, C.c_float, C.c_float, P],
+                           I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -230,6 +270,43 @@ def nrrs_split_noalloc(d_q_orig, n, d_F, d_pixel, d_sample, d_lineage, depth, se
                                    _stream(stream)))
 
 
+def nrrs_train_step(scene, opts=None, stream=None):
+    st = TrainStats()
+    _check(_lib.nrrs_train_step(scene, C.byref(opts) if opts is not None else None,
+                                _stream(stream), C.byref(st)))
+    return st.as_dict()
+
+
+def nrrs_set_params(scene, which, params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.nrrs_set_params(scene, which, p.ctypes.data, p.size, _stream(stream)))
+
+
+def nrrs_get_params(scene, which, stream=None):
+    n = STATNET_PARAMS if which == NET_STATNET else RRSNET_PARAMS
+    p = np.zeros(n, dtype=np.float32)
+    _check(_lib.nrrs_get_params(scene, which, p.ctypes.data, n, _stream(stream)))
+    return p
+
+
+def nrrs_mlp_grad(scene, n_out, d_params, d_x, d_gout, n, d_grad, stream=None):
+    _check(_lib.nrrs_mlp_grad(scene, n_out, _ptr(d_params), _ptr(d_x), _ptr(d_gout), n,
+                              _ptr(d_grad), _stream(stream)))
+
+
+def nrrs_rrsnet_dloss(d_q_nrrs, d_F, d_Fn, d_t, d_pixel, d_m1, d_m2, d_E, Ebar, d_Iref, d_k, n,
+                      eps, g1, g2, g3, d_dq, stream=None):
+    _check(_lib.nrrs_rrsnet_dloss(_ptr(d_q_nrrs), _ptr(d_F), _ptr(d_Fn), _ptr(d_t), _ptr(d_pixel),
+                                  _ptr(d_m1), _ptr(d_m2), _ptr(d_E), float(Ebar), _ptr(d_Iref),
+                                  _ptr(d_k), n, eps, g1, g2, g3, _ptr(d_dq), _stream(stream)))
+
+
+def nrrs_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, b1=0.9, b2=0.999, eps=1e-8,
+                   stream=None):
+    _check(_lib.nrrs_adam_step(_ptr(d_params), _ptr(d_grad), _ptr(d_m), _ptr(d_v), n, step, lr,
+                               b1, b2, eps, _stream(stream)))
+
+
 # ------------------------------------------------------------------ convenience wrapper
 class Scene:
     """Owns one nrrs_scene handle built from an ``inputs.Scene``."""
@@ -265,6 +342,9 @@ class Scene:
         o = RenderOpts.defaults(**opts)
         st = nrrs_render(self.handle, width, height, spp, max_depth, mode, o, out, stream, stats)
         return out, st
+
+    def train_step(self, stream=None, **opts):
+        return nrrs_train_step(self.handle, TrainOpts.defaults(**opts), stream)
 
     def query(self, features, precision=32, out=None, stream=None):
         import torch
