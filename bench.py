@@ -1,10 +1,11 @@
 """Benchmark of the NRRS bounce loop on B300.
 
-Step = one frame of the whole hot path through the C ABI (nrrs_render): camera rays,
-then for every depth the extension (BVH traversal, emission deposit, RRSNet FP32
-factors), normalization, split counts + accumulation, scan and scatter (children and
-BSDF sampling), and the frame estimate.  Workload: the occluded room (2,018 triangles),
-256 x 256 px, 16 spp, max depth 16, queue capacity 2 x pixels x spp, NET factors.
+Step = one online NRRS frame through the C ABI: nrrs_train_step (a recorded 256 x 256 x
+2 spp frame, reverse pass, pixel errors, StatNet and RRSNet forward/backward, Adam, EMA)
+and nrrs_render (camera rays, then for every depth the traversal, shading, RRSNet FP32
+factors, normalization, split counts + accumulation, scan and scatter with BSDF sampling,
+and the frame estimate).  Workload: the occluded room (2,018 triangles), 256 x 256 px,
+16 spp, max depth 16, queue capacity 2 x pixels x spp.
 
 `value` is path segments per second (rays traced, summed over depths and ranks) with
 the scene, weights and queues resident on the device; `e2e` is the same metric through
@@ -31,7 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = "efficiency 1/(relMSE·s) vs plain RR, same B300; path segments/s; RRSNet TFLOP/s"
 UNIT = "path segments/s"
 W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
-WORKLOAD = "occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P"
+TRAIN_SPP = 2          # recorded training frame: 256x256x2 spp ~ 2^19 training vertices
+PRETRAIN_STEPS = 40    # untimed online training before the timed steps (20 warm-up + 20 full)
+WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P; "
+            "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
+            "+ the 16 spp inference frame")
 # algorithmic bytes per unit of each stage ("Kernels and rooflines")
 BYTES_PER_RAY_EXTEND = 48 + 8 + 4 + 16          # path state in; hit, q, deposit out
 BYTES_PER_SLOT_COUNT = 16 + 4 + 48              # deposit, q, path state (Philox keys)
@@ -259,6 +264,64 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU leg
+def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
+    """1/(relMSE x seconds) of the estimators on the same B300: PLAIN_RR (throughput
+    roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet) and NET_MIX (the
+    Mix-Depth gate found by the search), each averaging 16 frames of 16 spp, against a
+    4096-spp plain path-traced reference (256 frames x 16 spp, no RRS)."""
+    ref = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
+    img = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
+    n_ref = 256
+    for f in range(n_ref):
+        nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NONE,
+                         nrrs.RenderOpts.defaults(frame=50_000 + f, seed_hi=seed_hi, update_ref=0),
+                         img, stream, False)
+        ref += img
+    ref32 = (ref / n_ref).float().contiguous()
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    gate_res = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
+                                         d_pixel_ref=None, stream=stream)
+    search_s = time.perf_counter() - t0
+    res = {}
+    for name, mode, gate in (("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0),
+                             ("NET", nrrs.RRS_NET, 0), ("NET_MIX", nrrs.RRS_NET_MIX,
+                                                        gate_res["gate"])):
+        acc = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
+        frames = 16
+        segs = 0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f in range(frames):
+            st = nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
+                                  nrrs.RenderOpts.defaults(frame=90_000 + f, seed_hi=seed_hi,
+                                                           gate=gate, update_ref=0),
+                                  img, stream, True)
+            segs += st["segments"]
+            acc += img
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1000.0
+        mean = (acc / frames).float().contiguous()
+        nrrs.nrrs_relmse(mean, ref32, W_IMG * H_IMG, 0.01, out, stream)
+        torch.cuda.synchronize()
+        rel = out.item()
+        res[name] = {"relmse": rel, "seconds": sec, "efficiency": 1.0 / (rel * sec),
+                     "segments": segs, "ray_efficiency": 1.0 / (rel * segs)}
+    base = res["PLAIN_RR"]["efficiency"]
+    return {
+        "reference": f"no-RRS path tracing, {n_ref * SPP} spp",
+        "frames_per_mode": 16, "modes": res,
+        "net_vs_plain_rr": res["NET"]["efficiency"] / base,
+        "net_mix_vs_plain_rr": res["NET_MIX"]["efficiency"] / base,
+        "heur_norm_vs_plain_rr": res["HEUR_NORM"]["efficiency"] / base,
+        "mixdepth_gate": nrrs.gate_methods(gate_res["gate"], DEPTH),
+        "mixdepth_candidates": gate_res["evaluated"], "mixdepth_search_s": search_s,
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -277,17 +340,28 @@ def run_ours(args, rank, world, local_rank):
     sc.set_params(params)
     out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    mode = nrrs.RRS_NET
     seed_hi = rank  # independent replicas: different Philox streams per rank
+    topts = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP, max_depth=DEPTH,
+                                    seed_hi=seed_hi)
+
+    def train(frame):
+        topts.frame = frame
+        return nrrs.nrrs_train_step(sc.handle, topts, stream)
 
     def render(frame, profile=0):
-        return nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
+        return nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
                                 nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi,
                                                          profile=profile), out, stream, True)
 
+    # set-up (untimed): online training through the warm-up phase into the full loss
+    pre = []
+    for k in range(PRETRAIN_STEPS):
+        pre.append(train(10_000 + k))
+        render(20_000 + k)
     clocks = ClockSampler(local_rank)
     clocks.launch()
     for k in range(args.warmup):
+        train(30_000 + k)
         render(k)
     torch.cuda.synchronize()
     clocks.start()
@@ -296,18 +370,28 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    segs = 0
+    et0 = torch.cuda.Event(enable_timing=True)
+    et1 = torch.cuda.Event(enable_timing=True)
+    segs = render_segs = 0
     launches = 0
+    train_ms = 0.0
     stage_ms = np.zeros(nrrs.STAGES)
     stage_n = np.zeros(nrrs.STAGES, dtype=np.int64)
     live_total = 0
     net_evals = 0
     children = 0
+    fallbacks = 0
     ev0.record(stream)
     for k in range(args.steps):
+        et0.record(stream)
+        ts = train(40_000 + k)
+        et1.record(stream)
         st = render(args.warmup + k, profile=1)
-        segs += st["segments"]
-        launches += st["kernel_launches"]
+        train_ms += et0.elapsed_time(et1)
+        segs += st["segments"] + ts["segments"]
+        render_segs += st["segments"]
+        launches += st["kernel_launches"] + ts["kernel_launches"]
+        fallbacks += ts["fallback"] != 0
         stage_ms += st["stage_ms"]
         stage_n += st["stage_launches"]
         live_total += int(st["live"].sum())
@@ -319,9 +403,10 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    last_train = ts
 
     # end to end through the public API: weights from pinned host memory in, frame out
-    pinned_params = torch.from_numpy(params).pin_memory()
+    pinned_params = torch.from_numpy(nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET)).pin_memory()
     pinned_out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32).pin_memory()
     e2e_segs = 0
     torch.cuda.synchronize()
@@ -330,13 +415,14 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(args.steps):
         nrrs.nrrs_set_rrsnet_params(sc.handle, pinned_params.numpy(), stream)
-        st = render(10_000 + k)
-        e2e_segs += st["segments"]
+        ts = train(60_000 + k)
+        st = render(70_000 + k)
+        e2e_segs += st["segments"] + ts["segments"]
         pinned_out.copy_(out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
 
-    # standalone RRSNet throughput on a live-queue-sized batch
+    # stand-alone RRSNet throughput on a live-queue-sized batch
     n_q = 1 << 21
     feats = torch.from_numpy(I.random_features(n_q, seed=3)).to(dev)
     qout = torch.empty(n_q, dtype=torch.float32, device=dev)
@@ -351,6 +437,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     q_ms = e0.elapsed_time(e1) / 10
 
+    eff = None
+    if rank == 0 and not args.no_efficiency:
+        eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi)
+
     if dist:
         t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -363,14 +453,13 @@ def run_ours(args, rank, world, local_rank):
     hbm, bf16, peak_kind = measured_peaks()
     value = segs / (ms / 1000.0)
 
-    # roofline of the dominant stage
+    # roofline of the dominant render stage (event times on the launching stream)
     names = nrrs.STAGE_NAMES
     dom = int(np.argmax(stage_ms))
     alg_bytes = {
-        "extend": BYTES_PER_RAY_EXTEND * live_total,
+        "extend": 32 * live_total + 8 * live_total,  # ray in, hit out
         "split_count": BYTES_PER_SLOT_COUNT * live_total,
-        "split_scatter": BYTES_PER_PARENT_SCATTER * (live_total - children // 1) +
-        BYTES_PER_CHILD_SCATTER * children,
+        "split_scatter": BYTES_PER_PARENT_SCATTER * live_total + BYTES_PER_CHILD_SCATTER * children,
     }
     bytes_dom = alg_bytes.get(names[dom])
     per_launch_ms = stage_ms[dom] / max(1, stage_n[dom])
@@ -379,19 +468,22 @@ def run_ours(args, rank, world, local_rank):
     units_per_launch = live_total / max(1, stage_n[dom])
     traffic = per_unit * units_per_launch if per_unit is not None else None
     roofline = {
-        "kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "kernel": "k_trace" if names[dom] == "extend" else names[dom], "bound": "hbm",
+        "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
         else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
         "launches": int(stage_n[dom]),
-        "stage_share": {n: float(stage_ms[i] / stage_ms.sum()) for i, n in enumerate(names)},
+        "stage_share_of_render": {n: float(stage_ms[i] / stage_ms.sum()) for i, n in enumerate(names)},
+        "note": "k_trace is latency/divergence bound (see DESIGN.md); 40 B/ray algorithmic",
     }
     fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
     rrsnet = {
         "tflops_standalone_fp32": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12,
         "fp32_simt_peak_tflops": fp32_peak,
         "frac_of_fp32_peak": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12 / fp32_peak,
-        "tflops_in_extend": RRSNET_FLOP_PER_PATH * net_evals / (stage_ms[1] / 1000) / 1e12,
+        "tflops_in_render": RRSNET_FLOP_PER_PATH * net_evals / (stage_ms[7] / 1000) / 1e12
+        if stage_ms[7] > 0 else None,
         "batch": n_q,
     }
     cpu = None
@@ -404,13 +496,21 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
                    "parallelism": f"replicas{world}",
-                   "l2": "no flush: each step rewrites ~0.26 GB of path queues (> 126 MB L2)"},
+                   "l2": "no flush: each step rewrites ~0.3 GB of path queues and records (> 126 MB L2)"},
+        "step_breakdown": {"train_step_ms": train_ms / args.steps,
+                           "render_ms": (ms - train_ms) / args.steps,
+                           "render_segments_per_s": render_segs / ((ms - train_ms) / 1000.0),
+                           "train_phase": last_train["phase"], "train_fallbacks": fallbacks,
+                           "train_loss_rrsnet": last_train["loss_rrsnet"],
+                           "train_loss_statnet": last_train["loss_statnet"],
+                           "pretrain_steps": PRETRAIN_STEPS},
         "e2e": {"value": e2e_segs / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(W_IMG * H_IMG * 3 * 4)},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "rrsnet": rrsnet,
+        "efficiency": eff,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
@@ -425,6 +525,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-efficiency", action="store_true")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

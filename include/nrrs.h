@@ -291,6 +291,7 @@ typedef struct nrrs_train_stats {
     int32_t fallback;     /* 0 ok; 1 non-finite gradients or loss, 2 loss EMA rose above
                              1.5x its minimum: the last good weights were restored and the
                              step was not counted                                         */
+    int64_t kernel_launches; /* kernels the step launched (frame and training)            */
 } nrrs_train_stats;
 
 /* Renders one recorded frame with NET factors at every depth (the inference weights),
@@ -338,6 +339,45 @@ NRRS_API nrrs_status nrrs_rrsnet_dloss(const float* d_q_nrrs, const float* d_F, 
 NRRS_API nrrs_status nrrs_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v,
                                     int32_t n, int32_t step, float lr, float b1, float b2,
                                     float eps, void* stream);
+
+/* ------------------------------------------------------------------ Mix-Depth */
+
+/* Candidates Mix-Depth evaluates (Sec. 3.3): the depths are cut into segments of t_d
+ * bounces and each segment is searched exhaustively over {NET, HEUR, FIXED}^len, so
+ * sum over segments of 3^len (brute force 3^D when max_depth <= t_d).  -1 on bad input. */
+NRRS_API int64_t nrrs_mixdepth_candidates(int32_t max_depth, int32_t t_d);
+
+typedef struct nrrs_mixdepth_opts {
+    int32_t width, height, spp, max_depth; /* the estimation renders (spp 1 in the paper) */
+    int32_t t_d;                           /* segment length of the heuristic search (6)  */
+    int32_t max_candidates;                /* refuse larger searches (0 = no limit)        */
+    uint32_t seed_lo, seed_hi, frame;      /* one key for every candidate render           */
+    const float* d_pixel_ref;              /* device [H*W*3] reference, or NULL for the
+                                              scene's running mean of its frames            */
+} nrrs_mixdepth_opts;
+
+typedef struct nrrs_mixdepth_result {
+    uint64_t gate;     /* chosen method per depth (NRRS_GATE_*, 2 bits per depth)          */
+    double score;      /* relMSE x segments of the chosen candidate (lower is better)      */
+    double relmse;     /* relMSE of its estimation render against the reference            */
+    int64_t segments;  /* rays it traced                                                   */
+    int64_t evaluated; /* candidates rendered                                              */
+} nrrs_mixdepth_result;
+
+/* Mix-Depth search (Sec. 3.3, Brute-Force and Heuristic Search): segment by segment from
+ * the shallowest, every combination of {FIXED, HEUR, NET} for the segment's depths is
+ * rendered with the earlier depths at their chosen methods and the later ones at fixed
+ * RR, and scored by relMSE(render, reference) x segments traced (the inverse of the
+ * efficiency 1 / (error x cost) with the deterministic ray count as the cost); the lowest
+ * score wins, ties keep the cheaper method.  Synchronizes `stream` per candidate.
+ * Errors: INVALID_ARG (sizes, no reference, too many candidates); OOM; CUDA. */
+NRRS_API nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* opts,
+                                          void* stream, nrrs_mixdepth_result* out);
+
+/* relMSE = mean over pixels and RGB of (I - R)^2 / (R^2 + eps) (Sec. 5), in FP64; device
+ * images [n_pixels][3], result written to the device double d_out. */
+NRRS_API nrrs_status nrrs_relmse(const float* d_img, const float* d_ref, int64_t n_pixels,
+                                 double eps, double* d_out, void* stream);
 
 #ifdef __cplusplus
 }

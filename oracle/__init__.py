@@ -118,6 +118,8 @@ def lib():
         _lib.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                       C.c_double, C.c_double]
         _lib.or_ema.argtypes = [P, P, C.c_int64, C.c_double]
+        _lib.or_relmse.argtypes = [P, P, C.c_int64, C.c_double]
+        _lib.or_relmse.restype = C.c_double
     return _lib
 
 
@@ -350,3 +352,9 @@ def adam_step(P, G, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 def ema(Eavg, P, decay=0.99):
     P = np.ascontiguousarray(P, dtype=np.float64)
     lib().or_ema(_p(Eavg), _p(P), P.shape[0], decay)
+
+
+def relmse(img, ref, eps=0.01):
+    img = np.ascontiguousarray(img, dtype=np.float64).reshape(-1)
+    ref = np.ascontiguousarray(ref, dtype=np.float64).reshape(-1)
+    return float(lib().or_relmse(_p(img), _p(ref), img.shape[0], eps))

@@ -189,3 +189,13 @@ void or_adam_step(double* P, const double* G, double* m, double* v, int64_t n, i
 void or_ema(double* Eavg, const double* P, int64_t n, double decay) {
     for (int64_t i = 0; i < n; ++i) Eavg[i] = decay * Eavg[i] + (1.0 - decay) * P[i];
 }
+
+/* relMSE (Sec. 5): mean over pixels and channels of (I - R)^2 / (R^2 + eps). */
+double or_relmse(const double* img, const double* ref, int64_t n3, double eps) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n3; ++i) {
+        const double d = img[i] - ref[i];
+        s += d * d / (ref[i] * ref[i] + eps);
+    }
+    return n3 > 0 ? s / (double)n3 : 0.0;
+}

@@ -1001,7 +1001,119 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         out->loss_rrs = warm ? 0.0 : L_rrs;
         out->phase = warm ? 1 : 2;
         out->fallback = fallback;
+        // frame kernels, then pixel error, counts, mean, terms, 2 x (train, reduce grad,
+        // reduce loss), 2 Adam, EMA
+        out->kernel_launches = (int64_t)rs.kernel_launches + 4 + 6 + 2 + (fallback ? 0 : 1);
     }
+    return NRRS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ Mix-Depth (Sec. 3.3)
+extern "C" {
+
+int64_t nrrs_mixdepth_candidates(int32_t max_depth, int32_t t_d) {
+    if (max_depth < 1 || max_depth > NRRS_MAX_DEPTH || t_d < 1) return -1;
+    int64_t total = 0;
+    for (int start = 0; start < max_depth; start += t_d) {
+        const int len = std::min(t_d, max_depth - start);
+        int64_t c = 1;
+        for (int k = 0; k < len; ++k) c *= 3;
+        total += c;
+    }
+    return total;
+}
+
+nrrs_status nrrs_relmse(const float* d_img, const float* d_ref, int64_t n_pixels, double eps,
+                        double* d_out, void* stream) {
+    if (n_pixels < 0 || !d_out || (n_pixels > 0 && (!d_img || !d_ref)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad relmse arguments");
+    launch_relmse(d_img, d_ref, n_pixels * 3, eps, d_out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* opts, void* stream,
+                                 nrrs_mixdepth_result* out) {
+    if (!scene || !opts || !out) return fail(NRRS_ERR_INVALID_ARG, "NULL argument");
+    const nrrs_mixdepth_opts o = *opts;
+    const int D = o.max_depth;
+    const int64_t total = nrrs_mixdepth_candidates(D, o.t_d);
+    if (total < 0) return fail(NRRS_ERR_INVALID_ARG, "bad max_depth or t_d");
+    if (o.max_candidates > 0 && total > o.max_candidates)
+        return fail(NRRS_ERR_INVALID_ARG, "more candidates than max_candidates");
+    nrrs_render_opts ro = render_defaults();
+    ro.seed_lo = o.seed_lo;
+    ro.seed_hi = o.seed_hi;
+    ro.frame = o.frame;  // every candidate sees the same random numbers
+    ro.update_ref = 0;
+    nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, D, NRRS_RRS_NET_MIX, ro);
+    if (rc != NRRS_OK) return rc;
+    DeviceGuard g(scene->device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long npix = (long long)o.width * o.height;
+    const float* ref = o.d_pixel_ref ? o.d_pixel_ref
+                                     : (scene->ref_count > 0 && scene->ref_w == o.width &&
+                                        scene->ref_h == o.height ? scene->ref_mean : nullptr);
+    if (!ref) return fail(NRRS_ERR_INVALID_ARG, "no reference image for the relMSE estimate");
+    ro.d_pixel_ref = ref;
+    rc = ensure_train_nets(scene, s);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = scene->train;
+    if (t.npix < npix) {
+        rc = ensure_record(scene, npix * o.spp * 2, 1, npix);
+        if (rc != NRRS_OK) return rc;
+    }
+    // method digit order per depth: FIXED, HEUR, NET (cheapest first; ties keep the first)
+    const uint64_t digit_gate[3] = {NRRS_GATE_FIXED, NRRS_GATE_HEUR, NRRS_GATE_NET};
+    uint64_t gate = 0;
+    for (int d = 0; d < D; ++d) gate |= (uint64_t)NRRS_GATE_FIXED << (2 * d);
+    double best_score = 0.0, best_rel = 0.0;
+    int64_t best_segs = 0, evaluated = 0;
+    for (int start = 0; start < D; start += o.t_d) {
+        const int len = std::min(o.t_d, D - start);
+        int64_t ncand = 1;
+        for (int k = 0; k < len; ++k) ncand *= 3;
+        uint64_t seg_best = gate;
+        double seg_score = INFINITY;
+        for (int64_t c = 0; c < ncand; ++c) {
+            uint64_t gc = gate;
+            int64_t x = c;
+            for (int k = 0; k < len; ++k) {
+                const int depth = start + k;
+                gc &= ~(3ull << (2 * depth));
+                gc |= digit_gate[x % 3] << (2 * depth);
+                x /= 3;
+            }
+            ro.gate = gc;
+            nrrs_render_stats rs;
+            rc = render_impl(scene, o.width, o.height, o.spp, D, NRRS_RRS_NET_MIX, ro, t.rgb, s, &rs,
+                             nullptr, nullptr);
+            if (rc != NRRS_OK) return rc;
+            launch_relmse(t.rgb, ref, npix * 3, 0.01, t.scal + 7, s);
+            double rel = 0.0;
+            CK(cudaMemcpyAsync(&rel, t.scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            ++evaluated;
+            const double score = rel * (double)rs.segments;  // inverse efficiency
+            if (score < seg_score) {
+                seg_score = score;
+                seg_best = gc;
+                best_rel = rel;
+                best_segs = rs.segments;
+            }
+        }
+        gate = seg_best;
+        best_score = seg_score;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->gate = gate;
+    out->score = best_score;
+    out->relmse = best_rel;
+    out->segments = best_segs;
+    out->evaluated = evaluated;
     return NRRS_OK;
 }
 

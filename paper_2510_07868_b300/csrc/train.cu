@@ -111,6 +111,19 @@ __global__ void k_pixel_terms(const float* E, long long n, const double* Ebar, c
     }
 }
 
+// relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + eps), FP64, fixed order.
+__global__ void k_relmse(const float* img, const float* ref, long long n3, double eps,
+                         double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n3; i += blockDim.x) {
+        const double d = (double)img[i] - ref[i];
+        s += d * d / ((double)ref[i] * ref[i] + eps);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = n3 > 0 ? s / (double)n3 : 0.0;
+}
+
 // ------------------------------------------------------------------ MLP training
 // Shared-memory layout of one tile (kTile samples): inputs X[kTile][16], hidden
 // activations A1..A3[kTile][32] (post Leaky ReLU; their sign is the sign of the
@@ -433,6 +446,11 @@ void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int 
 
 void launch_mean(const float* E, long long n, double* out, cudaStream_t s) {
     k_mean<<<1, 1024, 0, s>>>(E, n, out);
+}
+
+void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
+                   cudaStream_t s) {
+    k_relmse<<<1, 1024, 0, s>>>(img, ref, n3, eps, out);
 }
 
 void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,

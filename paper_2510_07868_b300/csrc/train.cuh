@@ -57,6 +57,8 @@ void launch_pixel_error(const RecordView& r, int spp, long long npix, const floa
 void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
                           cudaStream_t s);
 void launch_mean(const float* E, long long n, double* out, cudaStream_t s);
+void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
+                   cudaStream_t s);
 // out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), out[2] = sum k (samples)
 void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
                         double* out, cudaStream_t s);

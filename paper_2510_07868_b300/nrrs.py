@@ -36,7 +36,8 @@ EXPORTED = [
     "nrrs_scene_info", "nrrs_set_rrsnet_params", "nrrs_get_rrsnet_params", "nrrs_render",
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
-    "nrrs_rrsnet_dloss", "nrrs_adam_step",
+    "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
+    "nrrs_relmse",
 ]
 
 
@@ -109,10 +110,22 @@ class TrainStats(C.Structure):
     _fields_ = [("step", C.c_int64), ("samples", C.c_int64), ("segments", C.c_int64),
                 ("loss_statnet", C.c_double), ("loss_rrsnet", C.c_double),
                 ("loss_avg", C.c_double), ("loss_min", C.c_double), ("loss_rrs", C.c_double),
-                ("phase", C.c_int32), ("fallback", C.c_int32)]
+                ("phase", C.c_int32), ("fallback", C.c_int32), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class MixDepthOpts(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
+                ("max_depth", C.c_int32), ("t_d", C.c_int32), ("max_candidates", C.c_int32),
+                ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32),
+                ("d_pixel_ref", C.c_void_p)]
+
+
+class MixDepthResult(C.Structure):
+    _fields_ = [("gate", C.c_uint64), ("score", C.c_double), ("relmse", C.c_double),
+                ("segments", C.c_int64), ("evaluated", C.c_int64)]
 
 
 def _load():
@@ -143,6 +156,9 @@ def _load():
                                C.c_float, C.c_float, P, P], I32),
         "nrrs_adam_step": ([P, P, P, P, I32, I32, C.c_float, C.c_float, C.c_float, C.c_float, P],
                            I32),
+        "nrrs_mixdepth_candidates": ([I32, I32], I64),
+        "nrrs_mixdepth_search": ([P, P, P, P], I32),
+        "nrrs_relmse": ([P, P, I64, D, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -305,6 +321,29 @@ def nrrs_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, b1=0.9, b2=0.999, ep
                    stream=None):
     _check(_lib.nrrs_adam_step(_ptr(d_params), _ptr(d_grad), _ptr(d_m), _ptr(d_v), n, step, lr,
                                b1, b2, eps, _stream(stream)))
+
+
+def nrrs_mixdepth_candidates(max_depth, t_d):
+    return int(_lib.nrrs_mixdepth_candidates(max_depth, t_d))
+
+
+def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1, 0), frame=0,
+                         d_pixel_ref=None, max_candidates=0, stream=None):
+    o = MixDepthOpts(width, height, spp, max_depth, t_d, max_candidates, seed[0], seed[1], frame,
+                     _ptr(d_pixel_ref))
+    r = MixDepthResult()
+    _check(_lib.nrrs_mixdepth_search(scene, C.byref(o), _stream(stream), C.byref(r)))
+    return {name: getattr(r, name) for name, _ in r._fields_}
+
+
+def nrrs_relmse(d_img, d_ref, n_pixels, eps, d_out, stream=None):
+    _check(_lib.nrrs_relmse(_ptr(d_img), _ptr(d_ref), n_pixels, eps, _ptr(d_out), _stream(stream)))
+
+
+def gate_methods(gate, max_depth):
+    """Per-depth method names of a Mix-Depth gate."""
+    names = {GATE_NET: "NET", GATE_HEUR: "HEUR", GATE_FIXED: "FIXED"}
+    return [names[(gate >> (2 * d)) & 3] for d in range(max_depth)]
 
 
 # ------------------------------------------------------------------ convenience wrapper
