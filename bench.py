@@ -33,7 +33,7 @@ METRIC = "efficiency 1/(relMSE·s) vs plain RR, same B300; path segments/s; RRSN
 UNIT = "path segments/s"
 W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
 TRAIN_SPP = 2          # recorded training frame: 256x256x2 spp ~ 2^19 training vertices
-PRETRAIN_STEPS = 40    # untimed online training before the timed steps (20 warm-up + 20 full)
+PRETRAIN_STEPS = 300   # untimed online training before the timed steps (20 warm-up + 280 full)
 WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P; "
             "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
             "+ the 16 spp inference frame")

@@ -272,7 +272,8 @@ typedef struct nrrs_train_opts {
     float lr_rrsnet, lr_statnet;           /* Adam learning rates        [3e-4, 5e-3]   */
     float gamma1, gamma2, gamma3;          /* Eq. loss-function_rrsnet [.01, .05, .01] */
     float eps;                             /* Eq. loss-function_min / StatNet     [0.01] */
-    float ema_decay;                       /* EMA of the RRSNet weights for rendering [0.99] */
+    float ema_decay;                       /* EMA of the RRSNet weights for rendering; step t
+                                              uses min(ema_decay, (1+t)/(10+t))     [0.99] */
     float f_rate;                          /* rate control of the training frame  [0.85] */
     const float* d_pixel_ref;              /* device [H*W*3] reference I, or NULL for the
                                               scene's running mean of its frames   [NULL] */
@@ -288,9 +289,10 @@ typedef struct nrrs_train_stats {
     double loss_min;      /* L_min = sum_i E_i                                            */
     double loss_rrs;      /* L_rrs = sum_s (q_nrrs - q_norm)^2 (phase 2)                  */
     int32_t phase;        /* 1 = warm-up (step (1) of Sec. 4), 2 = full loss              */
-    int32_t fallback;     /* 0 ok; 1 non-finite gradients or loss, 2 loss EMA rose above
-                             1.5x its minimum: the last good weights were restored and the
-                             step was not counted                                         */
+    int32_t fallback;     /* 0 ok; 1 non-finite gradients or loss; 2 divergence (after 50
+                             full-loss steps, a 0.98-EMA of the loss above 10x its running
+                             minimum): the last good weights were restored and the step
+                             was not counted                                              */
     int64_t kernel_launches; /* kernels the step launched (frame and training)            */
 } nrrs_train_stats;
 

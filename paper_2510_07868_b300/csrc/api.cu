@@ -964,12 +964,13 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
                                 : o.gamma1 * host_terms[1] + o.gamma2 * host_terms[0] + o.gamma3 * L_rrs;
     int fallback = 0;
     if (bad || !std::isfinite(L_total) || !std::isfinite(loss_stat)) fallback = 1;
-    // fallback monitor: after the warm-up, a loss EMA far above its running minimum
+    // fallback monitor: after the warm-up, a slow loss EMA far above its running minimum
+    // (divergence; single-frame Monte Carlo noise of the pixel errors is heavy-tailed)
     if (!fallback && !warm) {
-        t.loss_ema = t.full_steps == 0 ? L_total : 0.9 * t.loss_ema + 0.1 * L_total;
+        t.loss_ema = t.full_steps == 0 ? L_total : 0.98 * t.loss_ema + 0.02 * L_total;
         t.loss_min = t.full_steps == 0 ? t.loss_ema : std::min(t.loss_min, t.loss_ema);
         t.full_steps++;
-        if (t.full_steps > 10 && t.loss_ema > 1.5 * t.loss_min) fallback = 2;
+        if (t.full_steps > 50 && t.loss_ema > 10.0 * t.loss_min) fallback = 2;
     }
     if (fallback) {  // restore the last good weights and forget the moments
         CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
@@ -984,8 +985,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     } else {
         CK(cudaMemcpyAsync(t.rrs_good, t.rrs_raw, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(t.stat_good, t.stat, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
-        // inference weights: EMA of the trained weights (Sec. 4 "Training", as in NRC)
-        launch_ema(scene->params, t.rrs_raw, kNParams, o.ema_decay, s);
+        // inference weights: EMA of the trained weights (Sec. 4 "Training", as in NRC), with
+        // the usual warm start decay_t = min(decay, (1 + t) / (10 + t))
+        const float warm_decay = (float)(1.0 + (double)t.step) / (float)(10.0 + (double)t.step);
+        launch_ema(scene->params, t.rrs_raw, kNParams, std::min(o.ema_decay, warm_decay), s);
         t.step++;
     }
     CK(cudaGetLastError());
