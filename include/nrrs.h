@@ -277,6 +277,10 @@ typedef struct nrrs_train_opts {
     float f_rate;                          /* rate control of the training frame  [0.85] */
     const float* d_pixel_ref;              /* device [H*W*3] reference I, or NULL for the
                                               scene's running mean of its frames   [NULL] */
+    float alpha_mix;                       /* temporal EMA of the error map, Eq.
+                                              error_temporal                        [0.5] */
+    int32_t error_filter_radius;           /* (2r+1)^2 box filter on the error map in place
+                                              of the paper's denoiser; 0 = off        [2] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {

@@ -130,6 +130,8 @@ struct TrainState {
     long long rec_C = 0, npix = 0;
     int rec_D = 0;
     float *m1 = nullptr, *m2 = nullptr, *V = nullptr, *E = nullptr, *rgb = nullptr;
+    float *E_cur = nullptr, *E_acc = nullptr;  // error map: this frame, temporal EMA
+    bool e_first = true;
     int* k = nullptr;
     bool nets = false;
     float *rrs_raw = nullptr, *rrs_m = nullptr, *rrs_v = nullptr, *rrs_good = nullptr;
@@ -146,8 +148,10 @@ struct TrainState {
         cudaFree(rec.dep); cudaFree(rec.q); cudaFree(rec.t); cudaFree(rec.feat);
         cudaFree(rec.first); cudaFree(rec.X); cudaFree(rec.S);
         cudaFree(m1); cudaFree(m2); cudaFree(V); cudaFree(E); cudaFree(k); cudaFree(rgb);
+        cudaFree(E_cur); cudaFree(E_acc);
         rec = RecordView{};
-        m1 = m2 = V = E = rgb = nullptr;
+        m1 = m2 = V = E = rgb = E_cur = E_acc = nullptr;
+        e_first = true;
         k = nullptr;
         rec_C = npix = 0;
         rec_D = 0;
@@ -461,6 +465,8 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     CK(dalloc(&t.m2, n));
     CK(dalloc(&t.V, npix));
     CK(dalloc(&t.E, npix));
+    CK(dalloc(&t.E_cur, npix));
+    CK(dalloc(&t.E_acc, npix));
     CK(dalloc(&t.k, npix));
     CK(dalloc(&t.rgb, npix * 3));
     t.rec.C = C;
@@ -761,6 +767,7 @@ nrrs_train_opts train_defaults() {
     o.lr_rrsnet = 3e-4f; o.lr_statnet = 5e-3f;
     o.gamma1 = 0.01f; o.gamma2 = 0.05f; o.gamma3 = 0.01f;
     o.eps = 0.01f; o.ema_decay = 0.99f; o.f_rate = 0.85f;
+    o.alpha_mix = 0.5f; o.error_filter_radius = 2;
     return o;
 }
 
@@ -879,10 +886,12 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     const int D = o.max_depth;
     const long long npix = (long long)o.width * o.height;
     const long long C = npix * o.spp * 2;
+    if (t.npix != npix || scene->ref_w != o.width || scene->ref_h != o.height) t.e_first = true;
     rc = ensure_record(scene, C, D, npix);
     if (rc != NRRS_OK) return rc;
     t.rec.C = C;
     ro.frame = o.frame + (uint32_t)t.step;
+    ro.update_ref = 0;  // the reference is the mean of the earlier frames; folded in below
 
     // 1. a recorded frame with the inference weights, NET factors at every depth
     nrrs_render_stats rs;
@@ -906,9 +915,19 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     CK(cudaMemcpy(t.Fd, Fh, sizeof(float) * D, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(t.Fnd, Fnh, sizeof(float) * D, cudaMemcpyHostToDevice));
 
-    // 2. pixel errors against the reference, samples per pixel, mean error
-    const float* ref = o.d_pixel_ref ? o.d_pixel_ref : scene->ref_mean;
-    launch_pixel_error(t.rec, o.spp, npix, ref, o.eps, t.V, t.E, s);
+    // 2. pixel errors against the reference (the mean of the earlier frames), smoothed in
+    //    time (alpha_mix) and space (box filter standing in for the denoiser)
+    const bool have_ref = o.d_pixel_ref != nullptr || scene->ref_count > 0;
+    const float* ref = o.d_pixel_ref ? o.d_pixel_ref : (scene->ref_count > 0 ? scene->ref_mean : t.rgb);
+    launch_pixel_error(t.rec, o.spp, npix, ref, o.eps, t.V, t.E_cur, s);
+    launch_error_smoothing(t.E_cur, t.E_acc, t.E, o.width, o.height, o.alpha_mix, t.e_first ? 1 : 0,
+                           o.error_filter_radius, s);
+    t.e_first = false;
+    if (!o.d_pixel_ref) {
+        launch_ref_fold(scene->ref_mean, t.rgb, npix * 3, scene->ref_count, s);
+        scene->ref_count++;
+    }
+    (void)have_ref;
     CK(cudaMemsetAsync(t.k, 0, sizeof(int) * npix, s));
     launch_count_samples(t.rec, b, t.k, scene->n_sm * 4, s);
     launch_mean(t.E, npix, t.scal + 0, s);
@@ -1004,9 +1023,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         out->loss_rrs = warm ? 0.0 : L_rrs;
         out->phase = warm ? 1 : 2;
         out->fallback = fallback;
-        // frame kernels, then pixel error, counts, mean, terms, 2 x (train, reduce grad,
-        // reduce loss), 2 Adam, EMA
-        out->kernel_launches = (int64_t)rs.kernel_launches + 4 + 6 + 2 + (fallback ? 0 : 1);
+        // frame kernels; pixel error, temporal EMA, box filter, reference fold, sample
+        // counts, mean, loss terms; 2 x (train, reduce grad, reduce loss); 2 Adam; EMA
+        out->kernel_launches = (int64_t)rs.kernel_launches + 2 + (o.error_filter_radius > 0) +
+                               (o.d_pixel_ref ? 0 : 1) + 3 + 6 + 2 + (fallback ? 0 : 1);
     }
     return NRRS_OK;
 }

@@ -67,6 +67,39 @@ __global__ void k_pixel_error(RecordView r, int spp, long long npix, const float
     E[p] = (float)(v / 3.0 / (I * I + eps));
 }
 
+// Temporal smoothing of the error map (Sec. 4 "Tackle Low Spp", Eq. error_temporal with
+// alpha_mix): E_acc = (1 - alpha) E_acc + alpha E_cur (E_acc = E_cur on the first frame).
+__global__ void k_error_temporal(const float* E_cur, float* E_acc, long long n, float alpha,
+                                 int first) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    E_acc[p] = first ? E_cur[p] : (1.0f - alpha) * E_acc[p] + alpha * E_cur[p];
+}
+
+// Spatial smoothing of the error map, a (2r+1)^2 box filter clipped at the image border
+// (stands in for the denoiser the paper applies to the error map, Sec. 4).
+__global__ void k_error_box(const float* in, int W, int H, int r, float* out) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long long)W * H) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    double s = 0.0;
+    int c = 0;
+    for (int yy = max(0, y - r); yy <= min(H - 1, y + r); ++yy)
+        for (int xx = max(0, x - r); xx <= min(W - 1, x + r); ++xx) {
+            s += in[(long long)yy * W + xx];
+            ++c;
+        }
+    out[p] = (float)(s / c);
+}
+
+// Folds the frame into the running mean of the frames so far.
+__global__ void k_ref_fold(float* ref, const float* rgb, long long n3, int count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const float k = (float)count;
+    ref[i] = (ref[i] * k + rgb[i]) / (k + 1.0f);
+}
+
 // k_i: trainable samples (recorded q_orig > 0 at a network depth) of every pixel.
 __global__ void k_count_samples(RecordView r, TrainBatch b, int* k) {
     for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < b.total;
@@ -451,6 +484,21 @@ void launch_mean(const float* E, long long n, double* out, cudaStream_t s) {
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s) {
     k_relmse<<<1, 1024, 0, s>>>(img, ref, n3, eps, out);
+}
+
+void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
+                            float alpha, int first, int radius, cudaStream_t s) {
+    const long long n = (long long)W * H;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_error_temporal<<<g, 256, 0, s>>>(E_cur, E_acc, n, alpha, first);
+    if (radius > 0)
+        k_error_box<<<g, 256, 0, s>>>(E_acc, W, H, radius, E_out);
+    else
+        cudaMemcpyAsync(E_out, E_acc, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cudaStream_t s) {
+    k_ref_fold<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(ref, rgb, n3, count);
 }
 
 void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,

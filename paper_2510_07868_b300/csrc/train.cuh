@@ -57,6 +57,10 @@ void launch_pixel_error(const RecordView& r, int spp, long long npix, const floa
 void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
                           cudaStream_t s);
 void launch_mean(const float* E, long long n, double* out, cudaStream_t s);
+// E_acc = temporal EMA of E_cur; E_out = (2r+1)^2 box filter of E_acc (copy when r = 0)
+void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
+                            float alpha, int first, int radius, cudaStream_t s);
+void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cudaStream_t s);
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s);
 // out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), out[2] = sum k (samples)
