@@ -355,7 +355,7 @@ def run_ours(args, rank, world, local_rank):
 
     # set-up (untimed): online training through the warm-up phase into the full loss
     pre = []
-    for k in range(PRETRAIN_STEPS):
+    for k in range(args.pretrain):
         pre.append(train(10_000 + k))
         render(20_000 + k)
     clocks = ClockSampler(local_rank)
@@ -503,7 +503,7 @@ def run_ours(args, rank, world, local_rank):
                            "train_phase": last_train["phase"], "train_fallbacks": fallbacks,
                            "train_loss_rrsnet": last_train["loss_rrsnet"],
                            "train_loss_statnet": last_train["loss_statnet"],
-                           "pretrain_steps": PRETRAIN_STEPS},
+                           "pretrain_steps": args.pretrain},
         "e2e": {"value": e2e_segs / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(W_IMG * H_IMG * 3 * 4)},
@@ -526,6 +526,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-efficiency", action="store_true")
+    ap.add_argument("--pretrain", type=int, default=PRETRAIN_STEPS,
+                    help="untimed online training steps before the timed region")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
