@@ -738,7 +738,7 @@ nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     CK(dalloc(&t.stat_good, kStatParams));
     CK(dalloc(&t.grad_rrs, kNParams));
     CK(dalloc(&t.grad_stat, kStatParams));
-    t.part_blocks = sc->n_sm * 2;
+    t.part_blocks = sc->n_sm * 3;
     CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParams));
     CK(dalloc(&t.loss_part, t.part_blocks));
     CK(dalloc(&t.scal, 8));

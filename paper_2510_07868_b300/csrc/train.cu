@@ -225,8 +225,12 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
     return true;
 }
 
+// Weight-gradient ownership (register blocking): thread t owns row j = t / 4 of the
+// gradients of W1, W2 and W3, columns [4 (t % 4), +4) of W1 and [8 (t % 4), +8) of W2 and
+// W3, and entries t and t + kTile of W4.  Per sample it reads delta[j] once (shared by the
+// row's 4 threads) and its inputs with 128-bit loads.
 template <int NOUT, int MODE>
-__global__ void __launch_bounds__(kTile)
+__global__ void __launch_bounds__(kTile, 3)
 k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -237,13 +241,15 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
     const float* W2 = W + kNH * kNF;
     const float* W3 = W2 + kNH * kNH;
     const float* W4 = W3 + kNH * kNH;
-    // weight-gradient entries owned by this thread, accumulated over all tiles
-    constexpr int PER = (P + kTile - 1) / kTile;
-    float acc[PER];
-#pragma unroll
-    for (int e = 0; e < PER; ++e) acc[e] = 0.0f;
-    double loss = 0.0;
     const int tid = threadIdx.x;
+    const int gj = tid >> 2, gq = tid & 3;
+    float g1[4], g2[8], g3[8], g4[2];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) g1[e] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) g2[e] = g3[e] = 0.0f;
+    g4[0] = g4[1] = 0.0f;
+    double loss = 0.0;
     const long long tiles = (b.total + kTile - 1) / kTile;
     __syncthreads();
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -276,37 +282,50 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
                 if (MODE == kTrainStatNet) x[13] = x[14] = x[15] = 0.0f;  // no throughput
             }
         }
-        if (!active)
+        if (!active) {
+#pragma unroll
             for (int k = 0; k < kNF; ++k) x[k] = 0.0f;
+        }
+#pragma unroll
         for (int k = 0; k < kNF; ++k) sm.X[tid][k] = x[k];
         float h[kNH], hn[kNH];
+#pragma unroll
         for (int j = 0; j < kNH; ++j) {
             float s = 0.0f;
+#pragma unroll
             for (int k = 0; k < kNF; ++k) s = fmaf(W1[j * kNF + k], x[k], s);
             h[j] = lrelu(s);
             sm.A[0][tid][j] = h[j];
         }
+#pragma unroll
         for (int j = 0; j < kNH; ++j) {
             float s = 0.0f;
+#pragma unroll
             for (int k = 0; k < kNH; ++k) s = fmaf(W2[j * kNH + k], h[k], s);
             hn[j] = lrelu(s);
             sm.A[1][tid][j] = hn[j];
         }
+#pragma unroll
         for (int j = 0; j < kNH; ++j) {
             float s = 0.0f;
+#pragma unroll
             for (int k = 0; k < kNH; ++k) s = fmaf(W3[j * kNH + k], hn[k], s);
             h[j] = lrelu(s);
             sm.A[2][tid][j] = h[j];
         }
         float out[NOUT], gout[8];
+#pragma unroll
         for (int o = 0; o < NOUT; ++o) {
             float s = 0.0f;
+#pragma unroll
             for (int k = 0; k < kNH; ++k) s = fmaf(W4[o * kNH + k], h[k], s);
             out[o] = s;
         }
+#pragma unroll
         for (int o = 0; o < 8; ++o) gout[o] = 0.0f;
         if (MODE == kTrainGiven) {
             if (active)
+#pragma unroll
                 for (int o = 0; o < NOUT; ++o) gout[o] = a.gin[u * NOUT + o];
         } else if (active) {
             if (MODE == kTrainStatNet && a.m1) {  // moments for the RRSNet gradient
@@ -316,67 +335,98 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             }
             sample_grad<MODE>(a, r, d, i, out, gout, &loss);
         }
-        for (int o = 0; o < NOUT; ++o) sm.G[tid][o] = gout[o];
-        __syncthreads();
-        // ---- weight gradients of the output layer: sum_s G[s][o] A3[s][k]
-        constexpr int o4 = kNH * kNF + 2 * kNH * kNH;
 #pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const int p = tid + e * kTile;
-            if (p >= o4 && p < P) {
-                const int o = (p - o4) / kNH, k = (p - o4) % kNH;
-                float s = 0.0f;
-                for (int q = 0; q < kTile; ++q) s = fmaf(sm.G[q][o], sm.A[2][q][k], s);
-                acc[e] += s;
-            }
-        }
-        // ---- this sample's delta at layer 3: (W4^T g) * lrelu'(a3)
+        for (int o = 0; o < NOUT; ++o) sm.G[tid][o] = gout[o];
+        // this sample's delta at layer 3: (W4^T g) * lrelu'(a3)
         float dl[kNH];
+#pragma unroll
         for (int k = 0; k < kNH; ++k) {
             float s = 0.0f;
+#pragma unroll
             for (int o = 0; o < NOUT; ++o) s = fmaf(W4[o * kNH + k], gout[o], s);
-            dl[k] = s * (sm.A[2][tid][k] > 0.0f ? 1.0f : kLeak);
+            dl[k] = s * (h[k] > 0.0f ? 1.0f : kLeak);
         }
         __syncthreads();
+        // ---- W4 gradients: sum_s G[s][o] A3[s][k]
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int p = tid + e * kTile;
+            if (p < NOUT * kNH) {
+                const int o = p / kNH, k = p % kNH;
+                float sacc = 0.0f;
+                for (int q = 0; q < kTile; ++q) sacc = fmaf(sm.G[q][o], sm.A[2][q][k], sacc);
+                g4[e] += sacc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
         for (int k = 0; k < kNH; ++k) sm.A[2][tid][k] = dl[k];  // A3 now holds delta3
         __syncthreads();
-        // layers 3, 2, 1: grads sum_s delta_l[s][j] in_l[s][k], then delta_{l-1}
-        for (int l = 2; l >= 0; --l) {
-            const int nin = l == 0 ? kNF : kNH;
-            const int off = l == 0 ? 0 : kNH * kNF + (l - 1) * kNH * kNH;
-            const int cnt = kNH * nin;
+        // ---- W3 gradients: sum_s delta3[s][j] A2[s][k]
+        for (int q = 0; q < kTile; ++q) {
+            const float dj = sm.A[2][q][gj];
+            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[1][q][8 * gq]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[1][q][8 * gq + 4]);
+            g3[0] = fmaf(dj, a0.x, g3[0]); g3[1] = fmaf(dj, a0.y, g3[1]);
+            g3[2] = fmaf(dj, a0.z, g3[2]); g3[3] = fmaf(dj, a0.w, g3[3]);
+            g3[4] = fmaf(dj, a1.x, g3[4]); g3[5] = fmaf(dj, a1.y, g3[5]);
+            g3[6] = fmaf(dj, a1.z, g3[6]); g3[7] = fmaf(dj, a1.w, g3[7]);
+        }
+        // delta2 = (W3^T delta3) * lrelu'(a2)
 #pragma unroll
-            for (int e = 0; e < PER; ++e) {
-                const int p = tid + e * kTile;
-                if (p >= off && p < off + cnt) {
-                    const int j = (p - off) / nin, k = (p - off) % nin;
-                    float s = 0.0f;
-                    if (l == 0) {
-                        for (int q = 0; q < kTile; ++q) s = fmaf(sm.A[0][q][j], sm.X[q][k], s);
-                    } else {
-                        for (int q = 0; q < kTile; ++q) s = fmaf(sm.A[l][q][j], sm.A[l - 1][q][k], s);
-                    }
-                    acc[e] += s;
-                }
-            }
-            if (l == 0) break;
-            const float* Wl = l == 2 ? W3 : W2;
-            float dn[kNH];
-            for (int k = 0; k < kNH; ++k) {
-                float s = 0.0f;
-                for (int j = 0; j < kNH; ++j) s = fmaf(Wl[j * kNH + k], sm.A[l][tid][j], s);
-                dn[k] = s * (sm.A[l - 1][tid][k] > 0.0f ? 1.0f : kLeak);
-            }
-            __syncthreads();
-            for (int k = 0; k < kNH; ++k) sm.A[l - 1][tid][k] = dn[k];
-            __syncthreads();
+        for (int k = 0; k < kNH; ++k) {
+            float sacc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kNH; ++j) sacc = fmaf(W3[j * kNH + k], dl[j], sacc);
+            h[k] = sacc * (hn[k] > 0.0f ? 1.0f : kLeak);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kNH; ++k) sm.A[1][tid][k] = h[k];  // A2 now holds delta2
+        __syncthreads();
+        // ---- W2 gradients: sum_s delta2[s][j] A1[s][k]
+        for (int q = 0; q < kTile; ++q) {
+            const float dj = sm.A[1][q][gj];
+            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[0][q][8 * gq]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[0][q][8 * gq + 4]);
+            g2[0] = fmaf(dj, a0.x, g2[0]); g2[1] = fmaf(dj, a0.y, g2[1]);
+            g2[2] = fmaf(dj, a0.z, g2[2]); g2[3] = fmaf(dj, a0.w, g2[3]);
+            g2[4] = fmaf(dj, a1.x, g2[4]); g2[5] = fmaf(dj, a1.y, g2[5]);
+            g2[6] = fmaf(dj, a1.z, g2[6]); g2[7] = fmaf(dj, a1.w, g2[7]);
+        }
+        // delta1 = (W2^T delta2) * lrelu'(a1); a1 is still in A1 for this thread
+#pragma unroll
+        for (int k = 0; k < kNH; ++k) {
+            float sacc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kNH; ++j) sacc = fmaf(W2[j * kNH + k], h[j], sacc);
+            dl[k] = sacc * (sm.A[0][tid][k] > 0.0f ? 1.0f : kLeak);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kNH; ++k) sm.A[0][tid][k] = dl[k];  // A1 now holds delta1
+        __syncthreads();
+        // ---- W1 gradients: sum_s delta1[s][j] X[s][k]
+        for (int q = 0; q < kTile; ++q) {
+            const float dj = sm.A[0][q][gj];
+            const float4 x0 = *reinterpret_cast<const float4*>(&sm.X[q][4 * gq]);
+            g1[0] = fmaf(dj, x0.x, g1[0]); g1[1] = fmaf(dj, x0.y, g1[1]);
+            g1[2] = fmaf(dj, x0.z, g1[2]); g1[3] = fmaf(dj, x0.w, g1[3]);
         }
         __syncthreads();
     }
+    float* pb = part + (size_t)blockIdx.x * P;
 #pragma unroll
-    for (int e = 0; e < PER; ++e) {
+    for (int e = 0; e < 4; ++e) pb[gj * kNF + 4 * gq + e] = g1[e];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        pb[kNH * kNF + gj * kNH + 8 * gq + e] = g2[e];
+        pb[kNH * kNF + kNH * kNH + gj * kNH + 8 * gq + e] = g3[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
         const int p = tid + e * kTile;
-        if (p < P) part[(size_t)blockIdx.x * P + p] = acc[e];
+        if (p < NOUT * kNH) pb[kNH * kNF + 2 * kNH * kNH + p] = g4[e];
     }
     __shared__ double shl[32];
     loss = block_sum(loss, shl);
