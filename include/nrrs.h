@@ -111,7 +111,8 @@ typedef struct nrrs_render_opts {
     float q_max;                /* HEUR cap                                         [16]   */
     float eps_rel;              /* HEUR: eps_I = eps_rel * mean(I_ref)              [0.01] */
     float boxcox_lambda;        /* throughput feature encoding                      [0.5]  */
-    int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT)                [32]   */
+    int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT) or 16 (BF16 operands,
+                                   FP32 accumulation, tcgen05 tensor cores)         [32]   */
     uint64_t gate;              /* NET_MIX method per depth (NRRS_GATE_*)           [0]    */
     const float* d_pixel_ref;   /* device [H*W*3] reference I_px for HEUR, or NULL to use
                                    the scene's running mean of earlier frames       [NULL] */
@@ -201,7 +202,10 @@ NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t heigh
 
 /* RRSNet inference on n feature rows (device [n][16] float, 16-byte aligned) -> device
  * d_q [n] float.
- * precision 32 = FP32 SIMT.  Feature layout (16 raw features in place of the paper's
+ * precision 32 = FP32 SIMT; 16 = tensor cores (tcgen05.mma kind::f16): features, weights
+ * and the two hidden activations feeding an MMA rounded to BF16 (nearest even), products
+ * accumulated in FP32, the last hidden layer, output layer and activation in FP32.
+ * Feature layout (16 raw features in place of the paper's
  * encoded inputs of Sec. 4 "Input Encoding"): position normalised to the scene box (3),
  * outgoing direction (3), shading normal (3), albedo (3), depth / max_depth (1),
  * Box-Cox(t) with lambda = boxcox_lambda per throughput channel (3).

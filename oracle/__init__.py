@@ -119,6 +119,7 @@ def lib():
                                       C.c_double, C.c_double]
         _lib.or_ema.argtypes = [P, P, C.c_int64, C.c_double]
         _lib.or_relmse.argtypes = [P, P, C.c_int64, C.c_double]
+
         _lib.or_relmse.restype = C.c_double
     return _lib
 

@@ -1,0 +1,312 @@
+// RRSNet forward on the 5th-generation tensor cores (tcgen05, sm_103a), BF16 operands,
+// FP32 accumulation in tensor memory.  Sec. 4 "Network Architecture": 16 -> 32 -> 32 ->
+// 32 -> 1, no biases, Leaky ReLU after each hidden layer, Eq. rrsnet_activation on the
+// output.  Layers 1-3 are M=128 x N=32 MMAs (K = 16, then K = 32 as two K = 16 steps);
+// the 32 -> 1 output layer and the activation run in FP32 on the CUDA cores.
+//
+// Every operand v is split into two BF16 numbers, hi = bf16(v) and lo = bf16(v - hi), and
+// each product is taken as hi*hi + lo*hi + hi*lo (three MMAs into the same FP32
+// accumulator); the dropped lo*lo term and the rounding of lo leave a relative error near
+// 2^-16 per product instead of the 2^-8 of one BF16 pass.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle: 8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups
+// (K / 8) * 128 bytes apart (SBO).  One CTA of 128 threads owns one TMEM allocation of 32
+// columns; thread t of the tile is row t and TMEM lane t.
+#include <cuda_bf16.h>
+
+#include <cfloat>
+
+#include "wavefront.cuh"
+
+namespace nrrs {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 32;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz: a wait this long is a fault
+
+struct __align__(128) TcSmem {
+    unsigned char w1[2][32 * 16 * 2];   // B of layer 1 (hi, lo): N = 32 rows, K = 16
+    unsigned char w2[2][32 * 32 * 2];   // B of layer 2 (hi, lo)
+    unsigned char w3[2][32 * 32 * 2];   // B of layer 3 (hi, lo)
+    unsigned char a1[2][128 * 16 * 2];  // A of layer 1 (hi, lo): 128 rows, K = 16
+    unsigned char a2[2][128 * 32 * 2];  // A of layers 2 and 3 (hi, lo): 128 rows, K = 32
+    float w4[32];
+    unsigned long long bar;
+    uint32_t tmem;
+};
+
+// Byte offset of element (r, k) in a K-major, no-swizzle operand with K columns.
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, leading and stride byte offsets (>> 4),
+// descriptor version 1 at bit 46, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 and
+// 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
+                                ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// Bounded wait on phase `phase` of the mbarrier; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Writes 8 consecutive values of row r (columns 8c .. 8c+7) into K-major tiles as the
+// BF16 pair hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* lo, int r, int c,
+                                             int K, const float* v) {
+    __nv_bfloat162 ph[4], pl[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        ph[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        const float2 f = __bfloat1622float2(ph[j]);
+        pl[j] = __floats2bfloat162_rn(v[2 * j] - f.x, v[2 * j + 1] - f.y);
+    }
+    const uint32_t off = kmajor_off(r, 8 * c, K);
+    *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<uint4*>(ph);
+    *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<uint4*>(pl);
+}
+
+__device__ __forceinline__ void store_split1(unsigned char* hi, unsigned char* lo, uint32_t off,
+                                             float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo + off) = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ float softplus_mod_tc(float z) {
+    return z < 0.0f ? log1pf(expf(z)) : fmaf(0.5f, z, 0.693147180559945f);
+}
+
+// n_ptr: device row count (render) or null with n_host (stand-alone).  q_in: when set,
+// only rows with q_in < 0 are written (the render's NET slots).
+__global__ void __launch_bounds__(kTcThreads)
+k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
+            const long long* n_ptr, long long n_host, float* q, int sentinel, DevStats* st,
+            unsigned int* status) {
+    __shared__ TcSmem sm;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long n = n_ptr ? *n_ptr : n_host;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights -> split BF16 B operands (W is [out][in] row-major = N rows of K)
+    for (int e = tid; e < 32 * 16; e += kTcThreads)
+        store_split1(sm.w1[0], sm.w1[1], kmajor_off(e / 16, e % 16, 16), params[e]);
+    for (int e = tid; e < 32 * 32; e += kTcThreads) {
+        const uint32_t off = kmajor_off(e / 32, e % 32, 32);
+        store_split1(sm.w2[0], sm.w2[1], off, params[512 + e]);
+        store_split1(sm.w3[0], sm.w3[1], off, params[1536 + e]);
+    }
+    if (tid < 32) sm.w4[tid] = params[2560 + tid];
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t bar = smem_u32(&sm.bar);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    uint64_t dw1[2], dw2[2], dw3[2], da1[2], da2[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        dw1[h2] = smem_desc(smem_u32(sm.w1[h2]), 128, 256);
+        dw2[h2] = smem_desc(smem_u32(sm.w2[h2]), 128, 512);
+        dw3[h2] = smem_desc(smem_u32(sm.w3[h2]), 128, 512);
+        da1[h2] = smem_desc(smem_u32(sm.a1[h2]), 128, 256);
+        da2[h2] = smem_desc(smem_u32(sm.a2[h2]), 128, 512);
+    }
+    const uint64_t k16 = 256 >> 4;  // start address step of K = 16 (two core matrices)
+    uint32_t phase = 0;
+    unsigned int evals = 0, nonfinite = 0;
+    bool failed = false;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+        const long long row = tile * kTcThreads + tid;
+        bool active = row < n;
+        if (active && sentinel) active = q[row] < 0.0f;
+        float x[16];
+        if (active) {
+            const float4* f = feat + 4 * row;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = __ldg(f + k);
+                x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+        }
+        store_split8(sm.a1[0], sm.a1[1], tid, 0, 16, x);
+        store_split8(sm.a1[0], sm.a1[1], tid, 1, 16, x + 8);
+        float h[32];
+        for (int layer = 0; layer < 3 && !failed; ++layer) {
+            fence_async_smem();
+            fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                // hi*hi + lo*hi + hi*lo for every K = 16 step, one FP32 accumulator
+                const uint64_t* A = layer == 0 ? da1 : da2;
+                const uint64_t* B = layer == 0 ? dw1 : layer == 1 ? dw2 : dw3;
+                const int ksteps = layer == 0 ? 1 : 2;
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint64_t o = ks * k16;
+                    mma_bf16(tmem, A[0] + o, B[0] + o, ks > 0 ? 1u : 0u);
+                    mma_bf16(tmem, A[1] + o, B[0] + o, 1u);
+                    mma_bf16(tmem, A[0] + o, B[1] + o, 1u);
+                }
+                mma_commit(bar);
+            }
+            const bool ok = mbar_wait(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            tmem_ld32(taddr, h);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) h[j] = h[j] > 0.0f ? h[j] : kLeak * h[j];
+            if (layer < 2) {
+                fence_before();
+                __syncthreads();  // every lane's MMA reads of a2 are complete (barrier fired)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) store_split8(sm.a2[0], sm.a2[1], tid, c, 32, h + 8 * c);
+            }
+        }
+        if (failed) break;
+        float z = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z = fmaf(sm.w4[k], h[k], z);
+        float qv = softplus_mod_tc(z);
+        if (active) {
+            ++evals;
+            if (!(qv >= 0.0f && qv <= FLT_MAX)) {
+                qv = 0.0f;
+                ++nonfinite;
+            }
+            q[row] = qv;
+        }
+        fence_before();
+        __syncthreads();  // TMEM reads done before the next tile's MMA overwrites it
+    }
+    if (failed && tid == 0 && status) atomicOr(status, (unsigned int)NRRS_STATUS_TIMEOUT);
+    if (st) {
+        evals = warp_sum(evals);
+        nonfinite = warp_sum(nonfinite);
+        if ((tid & 31) == 0) {
+            if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+            if (nonfinite) {
+                atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+                atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
+int tc_grid(long long n) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    long long g = (long long)nsm * 8;
+    if (n >= 0 && tiles < g) g = tiles > 0 ? tiles : 1;
+    return (int)g;
+}
+
+}  // namespace
+
+void launch_rrsnet_tc_query(const float* params, const float* feat, long long n, float* q,
+                            unsigned int* status, cudaStream_t s) {
+    if (n <= 0) return;
+    k_rrsnet_tc<<<tc_grid(n), kTcThreads, 0, s>>>(params, reinterpret_cast<const float4*>(feat),
+                                                  nullptr, n, q, 0, nullptr, status);
+}
+
+void launch_rrsnet_tc_depth(const WorkView& w, const RenderParams& rp, int depth, int grid,
+                            cudaStream_t s) {
+    k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q, 1,
+                                            w.st, &w.st->status);
+}
+
+}  // namespace nrrs
