@@ -131,7 +131,7 @@ void add_references(const double v[3][3], const Box& b, int32_t id, int level, d
         add_references(v, c, id, level + 1, limit, out);
     }
 }
-constexpr int kLeafMax = 4;
+constexpr int kLeafMax = 1;  // single-triangle leaves: no divergent multi-triangle loops
 constexpr int kMaxBuildDepth = 38;  // traversal stack holds 40 entries
 
 struct Builder {
