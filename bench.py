@@ -444,6 +444,14 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     q16_ms = e0.elapsed_time(e1) / 10
+    for _ in range(3):
+        sc.query(feats, out=qout, precision=8)
+    e0.record(stream)
+    for _ in range(10):
+        sc.query(feats, out=qout, precision=8)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    q8_ms = e0.elapsed_time(e1) / 10
 
     eff = None
     if rank == 0 and not args.no_efficiency:
@@ -487,6 +495,7 @@ def run_ours(args, rank, world, local_rank):
     }
     fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
     tf16 = RRSNET_FLOP_PER_PATH * n_q / (q16_ms / 1000) / 1e12
+    tf8 = RRSNET_FLOP_PER_PATH * n_q / (q8_ms / 1000) / 1e12  # FP8 peak: 2x BF16 (nominal)
     rows_per_s_hbm = hbm * 1e9 / (16 * 4 + 4)  # FP32 features in, factor out
     rrsnet = {
         "tflops_tensor_bf16x3": tf16,
@@ -496,6 +505,9 @@ def run_ours(args, rank, world, local_rank):
                             "frac_of_bf16_tensor_peak": tf16 / bf16,
                             "note": "algorithmic FLOP (5184/row); the split BF16 runs 3 MMAs "
                                     "per product"},
+        "tflops_tensor_e4m3": tf8,
+        "e4m3_hbm_frac": 68 * n_q / (q8_ms / 1000) / 1e9 / hbm,
+        "frac_of_fp8_tensor_peak": tf8 / (2 * bf16),
         "tflops_standalone_fp32": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12,
         "fp32_simt_peak_tflops": fp32_peak,
         "frac_of_fp32_peak": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12 / fp32_peak,

@@ -111,8 +111,9 @@ typedef struct nrrs_render_opts {
     float q_max;                /* HEUR cap                                         [16]   */
     float eps_rel;              /* HEUR: eps_I = eps_rel * mean(I_ref)              [0.01] */
     float boxcox_lambda;        /* throughput feature encoding                      [0.5]  */
-    int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT) or 16 (BF16 operands,
-                                   FP32 accumulation, tcgen05 tensor cores)         [32]   */
+    int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT), 16 (split BF16
+                                   operands) or 8 (E4M3 operands), tensor cores with
+                                   FP32 accumulation                                [32]   */
     uint64_t gate;              /* NET_MIX method per depth (NRRS_GATE_*)           [0]    */
     const float* d_pixel_ref;   /* device [H*W*3] reference I_px for HEUR, or NULL to use
                                    the scene's running mean of earlier frames       [NULL] */
@@ -202,9 +203,11 @@ NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t heigh
 
 /* RRSNet inference on n feature rows (device [n][16] float, 16-byte aligned) -> device
  * d_q [n] float.
- * precision 32 = FP32 SIMT; 16 = tensor cores (tcgen05.mma kind::f16): features, weights
- * and the two hidden activations feeding an MMA rounded to BF16 (nearest even), products
- * accumulated in FP32, the last hidden layer, output layer and activation in FP32.
+ * precision 32 = FP32 SIMT; 16 = tensor cores (tcgen05.mma kind::f16) with every MMA
+ * operand split into two BF16 numbers (hi + lo, three MMAs per product) and FP32
+ * accumulation; 8 = tensor cores (kind::f8f6f4) with E4M3 operands, one scale per weight
+ * matrix and per 128-row activation tile mapping its largest magnitude to 448, FP32
+ * accumulation.  The 32 -> 1 output layer and the activation run in FP32 in all three.
  * Feature layout (16 raw features in place of the paper's
  * encoded inputs of Sec. 4 "Input Encoding"): position normalised to the scene box (3),
  * outgoing direction (3), shading normal (3), albedo (3), depth / max_depth (1),

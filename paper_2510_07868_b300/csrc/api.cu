@@ -439,8 +439,8 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
     if (o.cap_factor < 1) return fail(NRRS_ERR_INVALID_ARG, "cap_factor < 1");
     if (!(o.f_rate > 0.0f && o.f_rate <= 1.0f) || !(o.alpha0 > 0.0f && o.alpha0 <= 1.0f))
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
-    if (o.precision != 32 && o.precision != 16)
-        return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32 and 16");
+    if (o.precision != 32 && o.precision != 16 && o.precision != 8)
+        return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16 and 8");
     if (rrs_mode == NRRS_RRS_NET_MIX)
         for (int d = 1; d <= max_depth; ++d)
             if (((o.gate >> (2 * (d - 1))) & 3u) == 3u) return fail(NRRS_ERR_INVALID_ARG, "gate value 3");
@@ -559,8 +559,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
         TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, rp, d, s));
         if (kind == kFactorNet) {
-            if (o.precision == 16) {
-                TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_tc_depth(w, rp, d, scene->n_sm * 8, s));
+            if (o.precision != 32) {
+                TIMED(NRRS_STAGE_RRSNET,
+                      launch_rrsnet_tc_depth(o.precision, w, rp, d, scene->n_sm * 8, s));
             } else {
                 WorkView wn = w;
                 wn.grid_red = scene->grid_rrsnet;
@@ -653,14 +654,15 @@ nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64
                                int32_t precision, float* d_q, void* stream) {
     if (!scene || n < 0 || (n > 0 && (!d_features || !d_q)))
         return fail(NRRS_ERR_INVALID_ARG, "bad query arguments");
-    if (precision != 32 && precision != 16)
-        return fail(NRRS_ERR_UNSUPPORTED, "precision must be 32 or 16");
+    if (precision != 32 && precision != 16 && precision != 8)
+        return fail(NRRS_ERR_UNSUPPORTED, "precision must be 32, 16 or 8");
     if (n == 0) return NRRS_OK;
     if ((reinterpret_cast<uintptr_t>(d_features) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_features must be 16-byte aligned");
     DeviceGuard g(scene->device);
-    if (precision == 16)
-        launch_rrsnet_tc_query(scene->params, d_features, n, d_q, nullptr, (cudaStream_t)stream);
+    if (precision != 32)
+        launch_rrsnet_tc_query(precision, scene->params, d_features, n, d_q, nullptr,
+                               (cudaStream_t)stream);
     else
         launch_query_factors(scene->params, d_features, n, d_q, (cudaStream_t)stream);
     CK(cudaGetLastError());

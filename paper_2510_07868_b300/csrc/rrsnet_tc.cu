@@ -14,6 +14,7 @@
 // (K / 8) * 128 bytes apart (SBO).  One CTA of 128 threads owns one TMEM allocation of 32
 // columns; thread t of the tile is row t and TMEM lane t.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cfloat>
 
@@ -284,6 +285,212 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
     }
 }
 
+// ------------------------------------------------------------------ FP8 (E4M3)
+// Same network with E4M3 operands (kind::f8f6f4, K = 32 per MMA, layer 1 zero-padded from
+// 16 to 32) and FP32 accumulation.  Each operand tensor gets a power-of-two scale that
+// puts its largest finite magnitude in (224, 448] (448 is the E4M3 maximum): one per
+// weight matrix, one per 128-row activation tile (the A operand of each MMA).  Powers of
+// two make the FP32 readback's unscaling exact, so the only error is the E4M3 rounding of
+// the operands (relative 2^-4, absolute 2^-10 / scale in the subnormal range).  A row with
+// a non-finite feature or hidden value is left out of its tile's scale and reports a
+// non-finite factor; a non-finite hidden weight makes every factor non-finite.
+struct __align__(128) Fp8Smem {
+    unsigned char w[3][32 * 32];  // B of layers 1-3: N = 32 rows, K = 32 bytes
+    unsigned char a[128 * 32];    // A: 128 rows, K = 32 bytes
+    float w4[32];
+    float red[4];
+    float winv[3];  // 1 / weight scale of layers 1-3
+    int wbad;       // a hidden-layer weight is not finite
+    unsigned long long bar;
+    uint32_t tmem;
+};
+
+// Byte offset of element (r, k) in a K-major, no-swizzle 8-bit operand with 32 columns.
+__device__ __forceinline__ uint32_t kmajor8_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 256 + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
+}
+
+// kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3 (format 0), K-major, N = 32, M = 128.
+constexpr uint32_t kIdescE4m3 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, 0, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdescE4m3));
+}
+
+__device__ __forceinline__ float block_max128(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+}
+
+// Largest power of two s with s * amax <= 448 (exponent clamped to +-60; 1 for amax 0).
+__device__ __forceinline__ float e4m3_scale(float amax) {
+    if (!(amax > 0.0f)) return 1.0f;
+    int e;
+    frexpf(448.0f / amax, &e);  // 448 / amax = m 2^e, m in [0.5, 1)
+    return ldexpf(1.0f, max(-60, min(60, e - 1)));
+}
+
+// 32 values of row r (scaled by s) as E4M3 into the A tile.
+__device__ __forceinline__ void store_e4m3_row(unsigned char* tile, int r, const float* v, float s) {
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const __nv_fp8x2_storage_t lo =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[4 * j] * s, v[4 * j + 1] * s), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t hi =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[4 * j + 2] * s, v[4 * j + 3] * s), __NV_SATFINITE, __NV_E4M3);
+        w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+    }
+    *reinterpret_cast<uint4*>(tile + kmajor8_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(tile + kmajor8_off(r, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+__global__ void __launch_bounds__(kTcThreads)
+k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
+             const long long* n_ptr, long long n_host, float* q, int sentinel, DevStats* st,
+             unsigned int* status) {
+    __shared__ Fp8Smem sm;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long n = n_ptr ? *n_ptr : n_host;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // per-matrix weight scales, then E4M3 B operands (W1 zero-padded to K = 32)
+    const int off[3] = {0, 512, 1536}, kin[3] = {16, 32, 32};
+    bool wbad = false;
+    for (int l = 0; l < 3; ++l) {
+        float m = 0.0f;
+        for (int e = tid; e < 32 * kin[l]; e += kTcThreads) {
+            const float a = fabsf(params[off[l] + e]);
+            if (a <= FLT_MAX) m = fmaxf(m, a);
+            else wbad = true;
+        }
+        m = block_max128(m, sm.red);
+        const float sw = e4m3_scale(m);
+        if (tid == 0) sm.winv[l] = 1.0f / sw;
+        if (tid < 32) {
+            float row[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) row[k] = k < kin[l] ? params[off[l] + tid * kin[l] + k] : 0.0f;
+            store_e4m3_row(sm.w[l], tid, row, sw);
+        }
+    }
+    if (tid < 32) sm.w4[tid] = params[2560 + tid];
+    fence_async_smem();
+    fence_before();
+    wbad = __syncthreads_or(wbad);
+    fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t bar = smem_u32(&sm.bar);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint64_t da = smem_desc(smem_u32(sm.a), 128, 256);
+    uint64_t dw[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) dw[l] = smem_desc(smem_u32(sm.w[l]), 128, 256);
+    uint32_t phase = 0;
+    unsigned int evals = 0, nonfinite = 0;
+    bool failed = false;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+        const long long row = tile * kTcThreads + tid;
+        bool active = row < n;
+        if (active && sentinel) active = q[row] < 0.0f;
+        float h[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) h[k] = 0.0f;
+        if (active) {
+            const float4* f = feat + 4 * row;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = __ldg(f + k);
+                h[4 * k] = v.x; h[4 * k + 1] = v.y; h[4 * k + 2] = v.z; h[4 * k + 3] = v.w;
+            }
+        }
+        bool bad = wbad;
+        for (int layer = 0; layer < 3 && !failed; ++layer) {
+            float m = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float a = fabsf(h[k]);
+                bad |= !(a <= FLT_MAX);
+                m = fmaxf(m, a);
+            }
+            const float sa = e4m3_scale(block_max128(bad ? 0.0f : m, sm.red));
+            store_e4m3_row(sm.a, tid, h, sa);
+            fence_async_smem();
+            fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                mma_e4m3(tmem, da, dw[layer]);
+                mma_commit(bar);
+            }
+            const bool ok = mbar_wait(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            tmem_ld32(taddr, h);
+            const float inv = (1.0f / sa) * sm.winv[layer];  // exact: powers of two
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float v = h[j] * inv;
+                h[j] = v > 0.0f ? v : kLeak * v;
+            }
+            fence_before();
+            __syncthreads();  // the MMA's reads of the A tile and this layer's TMEM reads are done
+        }
+        if (failed) break;
+        float z = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z = fmaf(sm.w4[k], h[k], z);
+        float qv = softplus_mod_tc(z);
+        if (active) {
+            ++evals;
+            if (bad || !(qv >= 0.0f && qv <= FLT_MAX)) {
+                qv = 0.0f;
+                ++nonfinite;
+            }
+            q[row] = qv;
+        }
+    }
+    if (failed && tid == 0 && status) atomicOr(status, (unsigned int)NRRS_STATUS_TIMEOUT);
+    if (st) {
+        evals = warp_sum(evals);
+        nonfinite = warp_sum(nonfinite);
+        if ((tid & 31) == 0) {
+            if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+            if (nonfinite) {
+                atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+                atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
 int tc_grid(long long n) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
@@ -296,17 +503,24 @@ int tc_grid(long long n) {
 
 }  // namespace
 
-void launch_rrsnet_tc_query(const float* params, const float* feat, long long n, float* q,
-                            unsigned int* status, cudaStream_t s) {
+void launch_rrsnet_tc_query(int precision, const float* params, const float* feat, long long n,
+                            float* q, unsigned int* status, cudaStream_t s) {
     if (n <= 0) return;
-    k_rrsnet_tc<<<tc_grid(n), kTcThreads, 0, s>>>(params, reinterpret_cast<const float4*>(feat),
-                                                  nullptr, n, q, 0, nullptr, status);
+    const float4* f = reinterpret_cast<const float4*>(feat);
+    if (precision == 8)
+        k_rrsnet_fp8<<<tc_grid(n), kTcThreads, 0, s>>>(params, f, nullptr, n, q, 0, nullptr, status);
+    else
+        k_rrsnet_tc<<<tc_grid(n), kTcThreads, 0, s>>>(params, f, nullptr, n, q, 0, nullptr, status);
 }
 
-void launch_rrsnet_tc_depth(const WorkView& w, const RenderParams& rp, int depth, int grid,
-                            cudaStream_t s) {
-    k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q, 1,
-                                            w.st, &w.st->status);
+void launch_rrsnet_tc_depth(int precision, const WorkView& w, const RenderParams& rp, int depth,
+                            int grid, cudaStream_t s) {
+    if (precision == 8)
+        k_rrsnet_fp8<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q,
+                                                 1, w.st, &w.st->status);
+    else
+        k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q,
+                                                1, w.st, &w.st->status);
 }
 
 }  // namespace nrrs

@@ -103,11 +103,12 @@ void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, con
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
                      int ref_count, int update_ref, cudaStream_t s);
 
-// RRSNet on the tensor cores (BF16 operands, FP32 accumulation), rrsnet_tc.cu.
-void launch_rrsnet_tc_query(const float* params, const float* feat, long long n, float* q,
-                            unsigned int* status, cudaStream_t s);
-void launch_rrsnet_tc_depth(const WorkView& w, const RenderParams& rp, int depth, int grid,
-                            cudaStream_t s);
+// RRSNet on the tensor cores (rrsnet_tc.cu): precision 16 = split BF16 operands,
+// 8 = E4M3 operands with per-tensor scales; FP32 accumulation.
+void launch_rrsnet_tc_query(int precision, const float* params, const float* feat, long long n,
+                            float* q, unsigned int* status, cudaStream_t s);
+void launch_rrsnet_tc_depth(int precision, const WorkView& w, const RenderParams& rp, int depth,
+                            int grid, cudaStream_t s);
 
 // Stand-alone entry points on plain arrays.
 void launch_query_factors(const float* params, const float* feat, long long n, float* q,

@@ -165,6 +165,121 @@ def test_query_factors_bf16_tensor_cores(nrrs, n):
     sc.close()
 
 
+def _e4m3_bound(P, X):
+    """A-priori bound on |q_fp8 - q| for the E4M3 tensor-core network, per row.
+
+    Every operand is rounded to E4M3 after a power-of-two scale that puts its tensor's
+    largest magnitude in (224, 448]: relative error u = 2^-4 for normal numbers plus an
+    absolute 2^-10 / scale <= 2^-10 * amax / 224 in the subnormal range (amax taken over
+    the whole batch, which bounds every tile's).  The MMA accumulation is granted only 14
+    significant bits (a conservative stand-in for its internal precision: K * 2^-13
+    relative to the sum of absolute products); the FP32 output layer K * 2^-24.  Errors
+    pass unchanged through Leaky ReLU and the output activation (both have slope <= 1).
+    The bound is propagated layer by layer in FP64 alongside the exact activations."""
+    u = 2.0**-4
+    g = 32 * 2.0**-13
+    P = P.astype(np.float64)
+    Ws = [P[:512].reshape(32, 16), P[512:1536].reshape(32, 32), P[1536:2560].reshape(32, 32)]
+    w4 = P[2560:2592]
+    x = X.astype(np.float32).astype(np.float64)
+    e = np.zeros_like(x)
+    for W in Ws:
+        A = np.abs(W)
+        tw = 2.0**-10 * A.max() / 224.0
+        xa = np.abs(x) + e
+        tx = 2.0**-10 * xa.max() / 224.0
+        xq = xa * (1 + u) + tx                     # bound on |x~|
+        wq = A * (1 + u) + tw                      # bound on |W~|
+        err = (e + u * xa + tx) @ A.T + xq @ (u * A + tw).T + g * (xq @ wq.T)
+        a = x @ W.T
+        x = np.where(a > 0, a, 0.01 * a)
+        e = err
+    return np.abs(e) @ np.abs(w4) + 32 * 2.0**-24 * ((np.abs(x) + e) @ np.abs(w4))
+
+
+def _e4m3(v):
+    """Round to E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; smallest
+    normal 2^-6, subnormal spacing 2^-9, largest finite 448), nearest-even, saturating."""
+    a = np.minimum(np.abs(v), 448.0)
+    e = np.maximum(np.floor(np.log2(np.maximum(a, 1e-300))), -6.0)
+    step = 2.0 ** (e - 3)
+    return np.sign(v) * np.round(a / step) * step
+
+
+def _pow2_scale(amax):
+    if not amax > 0:
+        return 1.0
+    _, e = np.frexp(448.0 / amax)
+    return 2.0 ** max(-60, min(60, int(e) - 1))
+
+
+def _e4m3_network(P, X):
+    """The quantised network the precision-8 kernel evaluates, in FP64: per weight
+    matrix and per 128-row tile of activations, a power-of-two scale putting the largest
+    magnitude in (224, 448], E4M3 rounding, exact products, FP32 results unscaled."""
+    P = P.astype(np.float64)
+    Ws = [P[:512].reshape(32, 16), P[512:1536].reshape(32, 32), P[1536:2560].reshape(32, 32)]
+    h = X.astype(np.float32).astype(np.float64)
+    for W in Ws:
+        sw = _pow2_scale(np.abs(W).max())
+        Wq = _e4m3(W * sw)
+        out = np.empty((h.shape[0], 32))
+        for t in range(0, h.shape[0], 128):
+            blk = h[t:t + 128]
+            sa = _pow2_scale(np.abs(blk).max())
+            out[t:t + 128] = (_e4m3(blk * sa) @ Wq.T).astype(np.float32) / (sa * sw)
+        h = np.where(out > 0, out, 0.01 * out)
+    z = h @ P[2560:2592]
+    return np.where(z < 0, np.log1p(np.exp(np.minimum(z, 0.0))), 0.5 * z + np.log(2.0))
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 148 * 8 * 128 + 77, 1_000_000])
+def test_query_factors_fp8_tensor_cores(nrrs, n):
+    """tcgen05 RRSNet with E4M3 operands.  Against the quantised network of
+    _e4m3_network: 99% of the factors within 1e-4 relative (the rest differ by an
+    E4M3 rounding decision that FP32 and FP64 sums took on either side of a tie).
+    Against the exact FP64 network: every factor within the a-priori bound of
+    _e4m3_bound, and the median relative error below 2^-4, one E4M3 unit roundoff."""
+    from paper_2510_07868_b300.nrrs import Scene
+
+    sc = Scene(I.box_scene(1))
+    P = I.rrsnet_init_params(6)
+    sc.set_params(P)
+    X = I.random_features(n, seed=n + 3)
+    q = sc.query(_dev(X), precision=8).cpu().numpy().astype(np.float64)
+    m = min(n, 100_096)  # whole tiles, so the emulated scales match the kernel's
+    qe = _e4m3_network(P, X[:m])
+    close = np.abs(q[:m] - qe) <= 1e-4 * qe + 1e-7
+    assert close.mean() >= 0.99, close.mean()
+    qx = oracle.mlp_forward_batch(P.astype(np.float64), X[:m])
+    err = np.abs(q[:m] - qx)
+    assert np.all(err <= _e4m3_bound(P, X[:m]))
+    assert np.median(err / qx) < 2.0**-4, np.median(err / qx)
+    assert np.all(np.isfinite(q)) and q.min() >= 0
+    sc.close()
+
+
+def test_query_factors_fp8_nonfinite_rows(nrrs):
+    """A row with a NaN or infinite feature gets factor 0 and leaves the scale of its
+    tile, so the other rows are bit-identical to a run without it."""
+    from paper_2510_07868_b300.nrrs import Scene
+
+    sc = Scene(I.box_scene(1))
+    sc.set_params(I.rrsnet_init_params(2))
+    X = I.random_features(300, seed=11)
+    clean = sc.query(_dev(X), precision=8).cpu().numpy()
+    Xb = X.copy()
+    Xb[5, 3] = np.nan
+    Xb[9, 0] = np.inf
+    Xb[200, 15] = -np.inf
+    q = sc.query(_dev(Xb), precision=8).cpu().numpy()
+    bad = np.zeros(300, bool)
+    bad[[5, 9, 200]] = True
+    assert np.all(q[bad] == 0)
+    np.testing.assert_array_equal(q[~bad], clean[~bad])
+    sc.close()
+
+
 def test_render_bf16_precision_runs(nrrs):
     """The render takes its NET factors from the tensor-core kernel at precision 16:
     counts stay within the capacity and the image is finite."""
@@ -179,4 +294,9 @@ def test_render_bf16_precision_runs(nrrs):
     # same decisions up to a handful of near-ties: the depth-1 live count is identical
     assert st["live"][0] == st32["live"][0]
     assert abs(st["live"][1] - st32["live"][1]) <= 0.01 * st32["live"][1]
+    img8, st8 = sc.render(64, 64, 4, 8, nrrs.RRS_NET, precision=8)
+    assert st8["net_evals"] > 0 and np.all(st8["live"] <= st8["capacity"])
+    assert np.isfinite(img8.cpu().numpy()).all() and st8["nonfinite"] == 0
+    assert st8["live"][0] == st32["live"][0]
+    assert abs(st8["live"][1] - st32["live"][1]) <= 0.05 * st32["live"][1]
     sc.close()
