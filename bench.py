@@ -38,7 +38,7 @@ WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NE
             "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
             "+ the 16 spp inference frame")
 # algorithmic bytes per unit of each stage ("Kernels and rooflines")
-BYTES_PER_RAY_EXTEND = 48 + 8 + 4 + 16          # path state in; hit, q, deposit out
+BYTES_PER_RAY_SHADE = 48 + 8 + 4 + 16           # path state, hit in; q, deposit out
 BYTES_PER_SLOT_COUNT = 16 + 4 + 48              # deposit, q, path state (Philox keys)
 BYTES_PER_PARENT_SCATTER = 48 + 8 + 4           # path state, hit, q
 BYTES_PER_CHILD_SCATTER = 48                    # child path state
@@ -341,8 +341,9 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     seed_hi = rank  # independent replicas: different Philox streams per rank
+    graph = 0 if args.no_graph else 1
     topts = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP, max_depth=DEPTH,
-                                    seed_hi=seed_hi)
+                                    seed_hi=seed_hi, graph=graph)
 
     def train(frame):
         topts.frame = frame
@@ -351,7 +352,8 @@ def run_ours(args, rank, world, local_rank):
     def render(frame, profile=0):
         return nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
                                 nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi,
-                                                         profile=profile), out, stream, True)
+                                                         profile=profile, graph=graph),
+                                out, stream, True)
 
     # set-up (untimed): online training through the warm-up phase into the full loss
     pre = []
@@ -493,6 +495,26 @@ def run_ours(args, rank, world, local_rank):
         "stage_share_of_render": {n: float(stage_ms[i] / stage_ms.sum()) for i, n in enumerate(names)},
         "note": "k_trace is latency/divergence bound (see DESIGN.md); 40 B/ray algorithmic",
     }
+    # every render stage against HBM: algorithmic bytes over its summed event time
+    stage_bytes = {
+        "extend": 40 * live_total,
+        "shade": BYTES_PER_RAY_SHADE * live_total + 64 * net_evals,
+        "rrsnet": 68 * net_evals,
+        "split_count": BYTES_PER_SLOT_COUNT * live_total,
+        "split_scatter": BYTES_PER_PARENT_SCATTER * live_total + BYTES_PER_CHILD_SCATTER * children,
+    }
+    stages = {}
+    for i, n in enumerate(names):
+        if stage_n[i] == 0:
+            continue
+        e = {"ms_per_step": float(stage_ms[i] / args.steps), "launches": int(stage_n[i]),
+             "share": float(stage_ms[i] / stage_ms.sum())}
+        if n in stage_bytes and stage_ms[i] > 0:
+            gbs = stage_bytes[n] / (stage_ms[i] / 1000.0) / 1e9
+            e.update({"bytes_per_step": int(stage_bytes[n] / args.steps), "achieved_gbs": gbs,
+                      "frac_of_hbm": gbs / hbm})
+        stages[n] = e
+    roofline["stages"] = stages
     fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
     tf16 = RRSNET_FLOP_PER_PATH * n_q / (q16_ms / 1000) / 1e12
     tf8 = RRSNET_FLOP_PER_PATH * n_q / (q8_ms / 1000) / 1e12  # FP8 peak: 2x BF16 (nominal)
@@ -525,6 +547,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
                    "parallelism": f"replicas{world}",
+                   "bounce_loop": "CUDA graph per frame" if graph else "stream launches",
                    "l2": "no flush: each step rewrites ~0.3 GB of path queues and records (> 126 MB L2)"},
         "step_breakdown": {"train_step_ms": train_ms / args.steps,
                            "render_ms": (ms - train_ms) / args.steps,
@@ -555,6 +578,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-efficiency", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the bounce loop kernel by kernel instead of as a CUDA graph")
     ap.add_argument("--pretrain", type=int, default=PRETRAIN_STEPS,
                     help="untimed online training steps before the timed region")
     args = ap.parse_args()

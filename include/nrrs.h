@@ -124,7 +124,11 @@ typedef struct nrrs_render_opts {
                                    0xFFFFFFFF, X); for tests                        [NULL] */
     int32_t profile;            /* record CUDA events around every kernel launch on
                                    `stream`; per-stage times land in stats          [0]    */
-    int32_t reserved0;
+    int32_t graph;              /* capture the frame's launches (the whole bounce loop)
+                                   into a CUDA graph on a scene-owned stream and launch
+                                   that graph on `stream`; the executable graph is kept
+                                   per launch shape and updated in place with each
+                                   call's arguments                                 [0]    */
     float* d_suffix;            /* device [max_depth][C][4] float or NULL: record the frame
                                    and write every vertex's suffix sum S (rgb, pixel bits):
                                    its own deposit plus its children's S, so S / t is the
@@ -206,8 +210,8 @@ NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t heigh
  * precision 32 = FP32 SIMT; 16 = tensor cores (tcgen05.mma kind::f16) with every MMA
  * operand split into two BF16 numbers (hi + lo, three MMAs per product) and FP32
  * accumulation; 8 = tensor cores (kind::f8f6f4) with E4M3 operands, one scale per weight
- * matrix and per 128-row activation tile mapping its largest magnitude to 448, FP32
- * accumulation.  The 32 -> 1 output layer and the activation run in FP32 in all three.
+ * matrix and per 128-row activation tile, a power of two putting its largest magnitude
+ * in (224, 448], FP32 accumulation.  The 32 -> 1 output layer and the activation run in FP32 in all three.
  * Feature layout (16 raw features in place of the paper's
  * encoded inputs of Sec. 4 "Input Encoding"): position normalised to the scene box (3),
  * outgoing direction (3), shading normal (3), albedo (3), depth / max_depth (1),
@@ -288,6 +292,8 @@ typedef struct nrrs_train_opts {
                                               error_temporal                        [0.5] */
     int32_t error_filter_radius;           /* (2r+1)^2 box filter on the error map in place
                                               of the paper's denoiser; 0 = off        [2] */
+    int32_t graph;                         /* record the training frame through a CUDA
+                                              graph (nrrs_render_opts.graph)          [0] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {
@@ -334,6 +340,21 @@ NRRS_API nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* pa
 NRRS_API nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params,
                                    const float* d_x, const float* d_gout, int64_t n, float* d_grad,
                                    void* stream);
+
+/* RRSNet forward with caller-supplied weights (Sec. 4 "Network Architecture", Eq.
+ * rrsnet_activation): d_q[s] = softplus'(MLP(d_x[s])) in FP32 on the CUDA cores, d_params
+ * device [2592] packed as nrrs_set_rrsnet_params, d_x device [n][16] (16-byte aligned).
+ * Needs no scene.  Errors: INVALID_ARG (n < 0, NULL pointers, misaligned d_x). */
+NRRS_API nrrs_status nrrs_rrsnet_forward(const float* d_params, const float* d_x, int64_t n,
+                                         float* d_q, void* stream);
+
+/* RRSNet backward through its output activation: d_grad [2592] = sum over the n rows of
+ * gq_s d q_s / d W, q_s = softplus'(MLP(x_s)) as nrrs_rrsnet_forward, gq device [n].
+ * Summation order as nrrs_mlp_grad (reproducible); scratch: the scene's training
+ * buffers.  Errors: INVALID_ARG (n < 0, NULL pointers, misaligned d_x); OOM; CUDA. */
+NRRS_API nrrs_status nrrs_rrsnet_backward(nrrs_scene* scene, const float* d_params,
+                                          const float* d_x, const float* d_gq, int64_t n,
+                                          float* d_grad, void* stream);
 
 /* d L_RRSNet / d q_nrrs for n training samples (Sec. 3.2): with q_used = F q_nrrs,
  * dV/dq_used = -t^2 H / q_used^2, H = m2 if q_used < 1 (Eq. gradient_transfer_rr_mc) else

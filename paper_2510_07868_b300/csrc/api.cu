@@ -186,6 +186,13 @@ struct nrrs_scene {
     int ref_w = 0, ref_h = 0;
     std::vector<cudaEvent_t> events;  // reused by profiled renders
     TrainState train;
+    // graph-captured renders: capture stream and executable graphs per launch shape
+    cudaStream_t capture_stream = nullptr;
+    struct GraphEntry {
+        uint64_t key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -228,6 +235,8 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
 void destroy(nrrs_scene* s) {
     if (!s) return;
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     s->train.release_all();
     s->ws.release();
     cudaFree(s->nodes);
@@ -253,6 +262,7 @@ struct StageTimer {
     nrrs_scene* sc;
     cudaStream_t s;
     bool on;
+    bool capturing = false;  // events become graph nodes (recorded when the graph runs)
     int used = 0;
     unsigned launches = 0;
     std::vector<int> stage_of;
@@ -266,11 +276,15 @@ struct StageTimer {
             sc->events.push_back(e);
         }
         stage_of.push_back(stage);
-        return cudaEventRecord(sc->events[used++], s);
+        return record(sc->events[used++]);
     }
     cudaError_t end() {
         if (!on) return cudaSuccess;
-        return cudaEventRecord(sc->events[used++], s);
+        return record(sc->events[used++]);
+    }
+    cudaError_t record(cudaEvent_t e) {
+        return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                         : cudaEventRecord(e, s);
     }
     void collect(nrrs_render_stats* st) {
         for (size_t k = 0; k < stage_of.size(); ++k) {
@@ -477,6 +491,61 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     return NRRS_OK;
 }
 
+// Ends a stream capture left open by an early return.
+struct CaptureGuard {
+    cudaStream_t cs = nullptr;
+    bool active = false;
+    ~CaptureGuard() {
+        if (!active) return;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+    }
+};
+
+uint64_t mix_key(uint64_t h, uint64_t v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Ends the capture on `cs`, brings the scene's executable graph for `key` up to date
+// (in-place update when the topology matches, else a new instantiation) and launches it
+// on `s`.
+nrrs_status launch_captured(nrrs_scene* sc, CaptureGuard& cg, uint64_t key, cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    cg.active = false;
+    CK(cudaStreamEndCapture(cg.cs, &g));
+    cudaGraphExec_t exec = nullptr;
+    size_t slot = sc->graphs.size();
+    for (size_t k = 0; k < sc->graphs.size(); ++k)
+        if (sc->graphs[k].key == key) slot = k;
+    if (slot < sc->graphs.size()) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(sc->graphs[slot].exec, g, &info) == cudaSuccess) {
+            exec = sc->graphs[slot].exec;
+        } else {
+            cudaGetLastError();  // clear the failed update
+            cudaGraphExecDestroy(sc->graphs[slot].exec);
+            sc->graphs.erase(sc->graphs.begin() + slot);
+        }
+    }
+    if (!exec) {
+        cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        if (sc->graphs.size() >= 8) {  // keep the 8 most recent launch shapes
+            cudaGraphExecDestroy(sc->graphs.front().exec);
+            sc->graphs.erase(sc->graphs.begin());
+        }
+        sc->graphs.push_back({key, exec});
+    }
+    cudaGraphDestroy(g);
+    CK(cudaGraphLaunch(exec, s));
+    return NRRS_OK;
+}
+
 // One frame (see nrrs_render); with `rec` every depth's slots are recorded.
 nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
                         int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts& o,
@@ -525,10 +594,30 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     const int normalized = rrs_mode == NRRS_RRS_HEUR_NORM || rrs_mode == NRRS_RRS_NET ||
                            rrs_mode == NRRS_RRS_NET_MIX;
 
+    // graph mode: record every launch below on the scene's capture stream, then run the
+    // graph on the caller's stream
+    const cudaStream_t s_exec = s;
+    CaptureGuard cg;
+    uint64_t gkey = 0;
+    if (o.graph) {
+        if (!scene->capture_stream)
+            CK(cudaStreamCreateWithFlags(&scene->capture_stream, cudaStreamNonBlocking));
+        const uint64_t shape[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
+                                  (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
+                                  o.gate, (uint64_t)o.cap_factor, (uint64_t)(rec != nullptr),
+                                  (uint64_t)(o.d_trace != nullptr), (uint64_t)o.profile,
+                                  (uint64_t)(rp.ref != nullptr), (uint64_t)o.update_ref};
+        for (uint64_t v : shape) gkey = mix_key(gkey, v);
+        cg.cs = scene->capture_stream;
+        CK(cudaStreamBeginCapture(cg.cs, cudaStreamCaptureModeRelaxed));
+        cg.active = true;
+        s = cg.cs;
+    }
     CK(cudaMemsetAsync(ws.st, 0, sizeof(DevStats), s));
     CK(cudaMemsetAsync(ws.acc_s, 0, sizeof(float4) * npix, s));
     CK(cudaMemsetAsync(ws.acc_c, 0, sizeof(float4) * npix, s));
     StageTimer tm{scene, s, o.profile != 0};
+    tm.capturing = o.graph != 0;
 #define TIMED(stage, call)           \
     do {                             \
         CK(tm.begin(stage));         \
@@ -588,6 +677,11 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             TIMED(NRRS_STAGE_REVERSE, launch_reverse(*rec, d, max_depth, ws.st->live, ws.grid_red, s));
 #undef TIMED
     CK(cudaGetLastError());
+    if (o.graph) {
+        nrrs_status grc = launch_captured(scene, cg, gkey, s_exec);
+        if (grc != NRRS_OK) return grc;
+        s = s_exec;
+    }
     if (update) scene->ref_count++;
     if (stats) {
         DevStats h;
@@ -822,11 +916,10 @@ nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int
     return NRRS_OK;
 }
 
-nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params, const float* d_x,
-                          const float* d_gout, int64_t n, float* d_grad, void* stream) {
-    if (!scene || (n_out != 1 && n_out != kStatOut) || n < 0 || !d_params || !d_grad ||
-        (n > 0 && (!d_x || !d_gout)))
-        return fail(NRRS_ERR_INVALID_ARG, "bad mlp_grad arguments");
+namespace {
+nrrs_status mlp_grad_impl(nrrs_scene* scene, int32_t n_out, bool at_q, const float* d_params,
+                          const float* d_x, const float* d_gout, int64_t n, float* d_grad,
+                          void* stream) {
     if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_x must be 16-byte aligned");
     DeviceGuard g(scene->device);
@@ -846,8 +939,36 @@ nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_param
     b.D = 1;
     b.total = n;
     b.net_mask = 1u;
-    CK(launch_mlp_grad_given(n_out, a, r, b, t.part_blocks, t.part, t.loss_part, s));
+    CK(launch_mlp_grad_given(n_out, at_q, a, r, b, t.part_blocks, t.part, t.loss_part, s));
     launch_reduce_grad(t.part, t.part_blocks, P, d_grad, s);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+}  // namespace
+
+nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params, const float* d_x,
+                          const float* d_gout, int64_t n, float* d_grad, void* stream) {
+    if (!scene || (n_out != 1 && n_out != kStatOut) || n < 0 || !d_params || !d_grad ||
+        (n > 0 && (!d_x || !d_gout)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad mlp_grad arguments");
+    return mlp_grad_impl(scene, n_out, false, d_params, d_x, d_gout, n, d_grad, stream);
+}
+
+nrrs_status nrrs_rrsnet_backward(nrrs_scene* scene, const float* d_params, const float* d_x,
+                                 const float* d_gq, int64_t n, float* d_grad, void* stream) {
+    if (!scene || n < 0 || !d_params || !d_grad || (n > 0 && (!d_x || !d_gq)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad rrsnet_backward arguments");
+    return mlp_grad_impl(scene, 1, true, d_params, d_x, d_gq, n, d_grad, stream);
+}
+
+nrrs_status nrrs_rrsnet_forward(const float* d_params, const float* d_x, int64_t n, float* d_q,
+                                void* stream) {
+    if (n < 0 || !d_params || (n > 0 && (!d_x || !d_q)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad rrsnet_forward arguments");
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0)
+        return fail(NRRS_ERR_INVALID_ARG, "d_x must be 16-byte aligned");
+    if (n == 0) return NRRS_OK;
+    launch_query_factors(d_params, d_x, n, d_q, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NRRS_OK;
 }
@@ -884,6 +1005,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     ro.seed_hi = o.seed_hi;
     ro.f_rate = o.f_rate;
     ro.d_pixel_ref = o.d_pixel_ref;
+    ro.graph = o.graph;
     nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, o.max_depth, NRRS_RRS_NET, ro);
     if (rc != NRRS_OK) return rc;
     if (o.warmup_steps < 0 || !(o.eps > 0.0f) || !(o.ema_decay >= 0.0f && o.ema_decay < 1.0f))

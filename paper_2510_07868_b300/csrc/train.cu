@@ -259,7 +259,7 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         bool active = false;
         int d = 0;
         long long i = 0;
-        if (MODE == kTrainGiven && u < b.total) {
+        if ((MODE == kTrainGiven || MODE == kTrainGivenQ) && u < b.total) {
             active = true;
             const float4* f = r.feat + 4 * u;
 #pragma unroll
@@ -327,6 +327,10 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             if (active)
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) gout[o] = a.gin[u * NOUT + o];
+        } else if (MODE == kTrainGivenQ) {
+            // chain dL/dq through Eq. rrsnet_activation: dq/dz = sigmoid(z) (z < 0), 1/2
+            const float z = out[0];
+            if (active) gout[0] = a.gin[u] * (z < 0.0f ? 1.0f / (1.0f + expf(-z)) : 0.5f);
         } else if (active) {
             if (MODE == kTrainStatNet && a.m1) {  // moments for the RRSNet gradient
                 const size_t g = (size_t)d * r.C + i;
@@ -566,9 +570,10 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
     }
 }
 
-cudaError_t launch_mlp_grad_given(int n_out, const TrainArgs& a, const RecordView& r,
+cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
                                   const TrainBatch& b, int grid, float* part, double* loss_part,
                                   cudaStream_t s) {
+    if (at_q) return launch_train_t<1, kTrainGivenQ>(a, r, b, grid, part, loss_part, s);
     return n_out == 1 ? launch_train_t<1, kTrainGiven>(a, r, b, grid, part, loss_part, s)
                       : launch_train_t<6, kTrainGiven>(a, r, b, grid, part, loss_part, s);
 }

@@ -32,7 +32,13 @@ struct TrainBatch {
 
 // kTrainGiven: plain inputs in RecordView::feat ([n][16]) and given output gradients in
 // TrainArgs::gin ([n][n_out]); the kernel returns sum_s d(gin_s . out_s)/dW.
-enum TrainMode : int { kTrainStatNet = 0, kTrainRrsWarmup = 1, kTrainRrsFull = 2, kTrainGiven = 3 };
+enum TrainMode : int {
+    kTrainStatNet = 0,
+    kTrainRrsWarmup = 1,
+    kTrainRrsFull = 2,
+    kTrainGiven = 3,
+    kTrainGivenQ = 4  // as kTrainGiven, n_out 1, gradients given at q = softplus'(z)
+};
 
 struct TrainArgs {
     const float* params;  // weights of the network being trained
@@ -69,7 +75,7 @@ void launch_pixel_terms(const float* E, long long n, const double* Ebar, const i
 cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
                              const TrainBatch& b, int grid, float* part, double* loss_part,
                              cudaStream_t s);
-cudaError_t launch_mlp_grad_given(int n_out, const TrainArgs& a, const RecordView& r,
+cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
                                   const TrainBatch& b, int grid, float* part, double* loss_part,
                                   cudaStream_t s);
 void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream_t s);

@@ -37,7 +37,7 @@ EXPORTED = [
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
-    "nrrs_relmse",
+    "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward",
 ]
 
 
@@ -53,13 +53,13 @@ class RenderOpts(C.Structure):
                 ("q_max", C.c_float), ("eps_rel", C.c_float), ("boxcox_lambda", C.c_float),
                 ("precision", C.c_int32), ("gate", C.c_uint64), ("d_pixel_ref", C.c_void_p),
                 ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
-                ("profile", C.c_int32), ("reserved0", C.c_int32), ("d_suffix", C.c_void_p)]
+                ("profile", C.c_int32), ("graph", C.c_int32), ("d_suffix", C.c_void_p)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
                 eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
-                update_ref=1, reset_ref=0, d_trace=None, profile=0, reserved0=0, d_suffix=None)
+                update_ref=1, reset_ref=0, d_trace=None, profile=0, graph=0, d_suffix=None)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -95,14 +95,14 @@ class TrainOpts(C.Structure):
                 ("lr_statnet", C.c_float), ("gamma1", C.c_float), ("gamma2", C.c_float),
                 ("gamma3", C.c_float), ("eps", C.c_float), ("ema_decay", C.c_float),
                 ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p), ("alpha_mix", C.c_float),
-                ("error_filter_radius", C.c_int32)]
+                ("error_filter_radius", C.c_int32), ("graph", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(width=256, height=256, spp=2, max_depth=16, seed_lo=1, seed_hi=0, frame=0,
                 warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
                 gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None,
-                alpha_mix=0.5, error_filter_radius=2)
+                alpha_mix=0.5, error_filter_radius=2, graph=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -161,6 +161,8 @@ def _load():
         "nrrs_mixdepth_candidates": ([I32, I32], I64),
         "nrrs_mixdepth_search": ([P, P, P, P], I32),
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
+        "nrrs_rrsnet_forward": ([P, P, I64, P, P], I32),
+        "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -310,6 +312,56 @@ def nrrs_get_params(scene, which, stream=None):
 def nrrs_mlp_grad(scene, n_out, d_params, d_x, d_gout, n, d_grad, stream=None):
     _check(_lib.nrrs_mlp_grad(scene, n_out, _ptr(d_params), _ptr(d_x), _ptr(d_gout), n,
                               _ptr(d_grad), _stream(stream)))
+
+
+def nrrs_rrsnet_forward(d_params, d_x, n, d_q, stream=None):
+    _check(_lib.nrrs_rrsnet_forward(_ptr(d_params), _ptr(d_x), n, _ptr(d_q), _stream(stream)))
+
+
+def nrrs_rrsnet_backward(scene, d_params, d_x, d_gq, n, d_grad, stream=None):
+    _check(_lib.nrrs_rrsnet_backward(scene, _ptr(d_params), _ptr(d_x), _ptr(d_gq), n,
+                                     _ptr(d_grad), _stream(stream)))
+
+
+def _rrsnet_function():
+    import torch
+
+    class RRSNetFunction(torch.autograd.Function):
+        """q = RRSNet(x; W) with the forward and the weight gradient computed by the
+        library's kernels (nrrs_rrsnet_forward / nrrs_rrsnet_backward).  Features are not
+        differentiated (they come from the renderer)."""
+
+        @staticmethod
+        def forward(ctx, scene, x, params):
+            x = x.contiguous()
+            params = params.contiguous()
+            q = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+            nrrs_rrsnet_forward(params, x, x.shape[0], q)
+            ctx.scene = scene
+            ctx.save_for_backward(x, params)
+            return q
+
+        @staticmethod
+        def backward(ctx, gq):
+            x, params = ctx.saved_tensors
+            grad = torch.empty_like(params)
+            nrrs_rrsnet_backward(ctx.scene, params, x, gq.contiguous(), x.shape[0], grad)
+            return None, None, grad
+
+    return RRSNetFunction
+
+
+_RRSNET_FN = None
+
+
+def rrsnet(scene, x, params):
+    """Differentiable RRSNet: x [n][16] float32 CUDA, params [2592] float32 CUDA (requires
+    grad for training) -> q [n].  `scene` supplies the backward's scratch buffers."""
+    global _RRSNET_FN
+    if _RRSNET_FN is None:
+        _RRSNET_FN = _rrsnet_function()
+    handle = scene.handle if hasattr(scene, "handle") else scene
+    return _RRSNET_FN.apply(handle, x, params)
 
 
 def nrrs_rrsnet_dloss(d_q_nrrs, d_F, d_Fn, d_t, d_pixel, d_m1, d_m2, d_E, Ebar, d_Iref, d_k, n,

@@ -73,3 +73,34 @@ def test_invalid_arguments_are_rejected_without_gpu():
     with pytest.raises(nrrs.NrrsError) as e:
         nrrs.nrrs_query_factors(None, 0, -1, 32, 0, stream=0)
     assert e.value.code == 1
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and field
+    offsets (gcc on include/nrrs.h)."""
+    import ctypes
+    import subprocess
+
+    from paper_2510_07868_b300 import nrrs
+
+    pairs = {"nrrs_render_opts": nrrs.RenderOpts, "nrrs_render_stats": nrrs.RenderStats,
+             "nrrs_train_opts": nrrs.TrainOpts, "nrrs_train_stats": nrrs.TrainStats,
+             "nrrs_mixdepth_opts": nrrs.MixDepthOpts,
+             "nrrs_mixdepth_result": nrrs.MixDepthResult}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "nrrs.h"', "int main(void) {"]
+    expect = []
+    for cname, cls in pairs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for fname, *_ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            expect.append(getattr(cls, fname).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect

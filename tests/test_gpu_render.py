@@ -253,3 +253,54 @@ def test_ggx_scene_parity(nrrs, mode):
     rel[np.all(o == 0, axis=1) & np.all(g == 0, axis=1)] = 0.0
     assert np.mean(rel <= RTOL) >= 0.99, np.mean(rel <= RTOL)
     assert rel.max() <= 1e-4, rel.max()
+
+
+def _same_stats(a, b):
+    for k in ("live", "sum_q", "F", "alpha", "requested", "dropped"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["segments"] == b["segments"] and a["net_evals"] == b["net_evals"]
+
+
+@pytest.mark.parametrize("mode,prec", [("RRS_NET", 32), ("RRS_HEUR_NORM", 32),
+                                       ("RRS_NET_MIX", 32), ("RRS_NET", 16), ("RRS_PLAIN_RR", 32)])
+def test_graph_captured_render_is_bit_identical(nrrs, mode, prec):
+    """The bounce loop captured into a CUDA graph (opts.graph) renders exactly what the
+    stream-launched loop renders, frame after frame (the cached graph is updated in place
+    with each frame's seeds) and across alternating image shapes (one graph per shape)."""
+    s = I.box_scene(2)
+    P = I.rrsnet_init_params(5)
+    sg, sp = nrrs.Scene(s), nrrs.Scene(s)
+    sg.set_params(P)
+    sp.set_params(P)
+    m = getattr(nrrs, mode)
+    gate = 0
+    for d, g in enumerate([2, 1, 0, 0, 1, 0, 2, 1]):
+        gate |= g << (2 * d)
+    shapes = [(64, 48, 4), (32, 32, 2), (64, 48, 4), (64, 48, 4), (32, 32, 2)]
+    for frame, (W, H, spp) in enumerate(shapes):
+        kw = dict(frame=frame, precision=prec, gate=gate if m == nrrs.RRS_NET_MIX else 0)
+        ig, stg = sg.render(W, H, spp, 8, m, graph=1, **kw)
+        ip, stp = sp.render(W, H, spp, 8, m, graph=0, **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(ig, ip), (frame, W, H)
+        _same_stats(stg, stp)
+    # profiling inside the graph: the event pairs become graph nodes
+    _, st = sg.render(64, 48, 4, 8, m, graph=1, profile=1, frame=9, precision=prec)
+    assert st["stage_launches"][1] == 8 and st["stage_ms"][1] > 0
+    sg.close()
+    sp.close()
+
+
+def test_graph_captured_train_step_matches(nrrs):
+    """The training frame recorded through a graph gives the same step as without."""
+    out = []
+    for graph in (0, 1):
+        sc = nrrs.Scene(I.box_scene(1))
+        sc.set_params(I.rrsnet_init_params(1))
+        sts = [sc.train_step(width=32, height=32, spp=2, max_depth=6, warmup_steps=2,
+                             graph=graph) for _ in range(4)]
+        out.append((sts, nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET)))
+        sc.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert a["loss_rrsnet"] == b["loss_rrsnet"] and a["segments"] == b["segments"]
+    np.testing.assert_array_equal(out[0][1], out[1][1])

@@ -201,3 +201,62 @@ def test_train_step_nonfinite_weights_fall_back(nrrs):
     assert st["fallback"] == 1 and st["step"] == 1
     np.testing.assert_array_equal(nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET_TRAIN), good)
     sc.close()
+
+
+def test_rrsnet_autograd_matches_oracle_and_finite_differences(nrrs):
+    """The differentiable RRSNet (library forward and backward behind a
+    torch.autograd.Function): its weight gradient of L = sum_s c_s q_s equals the FP64
+    oracle's chain rule through Eq. rrsnet_activation (1e-4 of the largest entry: FP32
+    sums of n products), and a central difference of the library's own forward along a
+    random direction (relative 2e-3: FP32 forward noise over the step)."""
+    sc = nrrs.Scene(I.box_scene(1))
+    rng = np.random.default_rng(21)
+    P = (I.rrsnet_init_params(8) * 2.0).astype(np.float32)  # both activation branches
+    n = 3000
+    X = I.random_features(n, seed=21)
+    c = rng.normal(size=n).astype(np.float32)
+    w = torch.tensor(P, device="cuda", requires_grad=True)
+    xs = _dev(X)
+    q = nrrs.rrsnet(sc, xs, w)
+    # the forward is the query kernel with these weights
+    sc.set_params(P)
+    np.testing.assert_array_equal(q.detach().cpu().numpy(), sc.query(xs).cpu().numpy())
+    (q * _dev(c)).sum().backward()
+    g = w.grad.cpu().numpy().astype(np.float64)
+    G = np.zeros(P.size)
+    P64 = P.astype(np.float64)
+    zs = [oracle.mlp_forward(P64, X[s])[1] for s in range(n)]
+    assert min(zs) < 0 < max(zs)
+    for s in range(n):
+        G += oracle.mlp_backward(P64, X[s].astype(np.float64), float(c[s]))
+    assert np.max(np.abs(g - G)) <= 1e-4 * np.max(np.abs(G))
+    # central difference of the library forward along v (sums in FP64 on the host)
+    v = rng.normal(size=P.size).astype(np.float32)
+    h = 1e-2 / np.linalg.norm(v)
+
+    def L(p):
+        with torch.no_grad():
+            qq = nrrs.rrsnet(sc, xs, _dev(p.astype(np.float32)))
+        return float(np.dot(qq.cpu().numpy().astype(np.float64), c.astype(np.float64)))
+
+    fd = (L(P + h * v) - L(P - h * v)) / (2 * h)
+    assert abs(fd - float(g @ v)) <= 2e-3 * abs(float(g @ v)) + 1e-3
+    sc.close()
+
+
+def test_rrsnet_autograd_trains(nrrs):
+    """A few Adam steps through the autograd path regress RRSNet towards a target factor
+    (the warm-up objective of Sec. 4 "Training", here with torch's optimizer)."""
+    sc = nrrs.Scene(I.box_scene(1))
+    w = torch.tensor(I.rrsnet_init_params(3), device="cuda", requires_grad=True)
+    xs = _dev(I.random_features(8192, seed=4))
+    opt = torch.optim.Adam([w], lr=3e-3)
+    losses = []
+    for _ in range(60):
+        opt.zero_grad()
+        loss = ((nrrs.rrsnet(sc, xs, w) - 1.5) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert losses[-1] < 0.1 * losses[0]
+    sc.close()
