@@ -189,9 +189,14 @@ class ClockSampler:
 
 def traffic_from_profiles(kernel_tag):
     """DRAM bytes per unit (ray / slot) recorded by ncu for `kernel_tag`, if the recorded
-    source hash still matches the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2510_07868_b300", "csrc", "wavefront.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    source hash still matches the current kernel source (else None).  The traversal's
+    hash covers its kernel file and the BVH builder that lays out what it reads."""
+    csrc = os.path.join(ROOT, "paper_2510_07868_b300", "csrc")
+    files = {"extend": ["trace.cu", "bvh.cpp"]}.get(kernel_tag, ["wavefront.cu"])
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    sha = h.hexdigest()[:12]
     for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(
             os.path.join(ROOT, "profiles")) else []:
         if not fn.endswith((".md", ".txt")):
@@ -362,9 +367,20 @@ def run_ours(args, rank, world, local_rank):
         render(20_000 + k)
     clocks = ClockSampler(local_rank)
     clocks.launch()
+    # warm-up steps time every render stage (events around each launch); the timed steps
+    # bracket only the dominant stage's launches, which the roofline needs
+    warm_ms = np.zeros(nrrs.STAGES)
+    warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
+    warm_live = warm_evals = warm_children = 0
     for k in range(args.warmup):
         train(30_000 + k)
-        render(k)
+        st = render(k, profile=1)
+        warm_ms += st["stage_ms"]
+        warm_n += st["stage_launches"]
+        warm_live += int(st["live"].sum())
+        warm_evals += st["net_evals"]
+        warm_children += int(st["live"][1:].sum())
+    dom = int(np.argmax(warm_ms))
     torch.cuda.synchronize()
     clocks.start()
     if dist:
@@ -388,7 +404,7 @@ def run_ours(args, rank, world, local_rank):
         et0.record(stream)
         ts = train(40_000 + k)
         et1.record(stream)
-        st = render(args.warmup + k, profile=1)
+        st = render(args.warmup + k, profile=1 << (dom + 1))
         train_ms += et0.elapsed_time(et1)
         segs += st["segments"] + ts["segments"]
         render_segs += st["segments"]
@@ -473,7 +489,6 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant render stage (event times on the launching stream)
     names = nrrs.STAGE_NAMES
-    dom = int(np.argmax(stage_ms))
     alg_bytes = {
         "extend": 32 * live_total + 8 * live_total,  # ray in, hit out
         "split_count": BYTES_PER_SLOT_COUNT * live_total,
@@ -492,27 +507,27 @@ def run_ours(args, rank, world, local_rank):
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
         else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
         "launches": int(stage_n[dom]),
-        "stage_share_of_render": {n: float(stage_ms[i] / stage_ms.sum()) for i, n in enumerate(names)},
+
         "note": "k_trace is latency/divergence bound (see DESIGN.md); 40 B/ray algorithmic",
     }
-    # every render stage against HBM: algorithmic bytes over its summed event time
+    # every render stage against HBM: algorithmic bytes over its summed event time, from
+    # the warm-up steps (events around every launch)
     stage_bytes = {
-        "extend": 40 * live_total,
-        "shade": BYTES_PER_RAY_SHADE * live_total + 64 * net_evals,
-        "rrsnet": 68 * net_evals,
-        "split_count": BYTES_PER_SLOT_COUNT * live_total,
-        "split_scatter": BYTES_PER_PARENT_SCATTER * live_total + BYTES_PER_CHILD_SCATTER * children,
+        "extend": 40 * warm_live,
+        "shade": BYTES_PER_RAY_SHADE * warm_live + 64 * warm_evals,
+        "rrsnet": 68 * warm_evals,
+        "split_count": BYTES_PER_SLOT_COUNT * warm_live,
+        "split_scatter": BYTES_PER_PARENT_SCATTER * warm_live + BYTES_PER_CHILD_SCATTER * warm_children,
     }
-    stages = {}
+    stages = {"timed_over": f"{args.warmup} warm-up steps"}
     for i, n in enumerate(names):
-        if stage_n[i] == 0:
+        if warm_n[i] == 0:
             continue
-        e = {"ms_per_step": float(stage_ms[i] / args.steps), "launches": int(stage_n[i]),
-             "share": float(stage_ms[i] / stage_ms.sum())}
-        if n in stage_bytes and stage_ms[i] > 0:
-            gbs = stage_bytes[n] / (stage_ms[i] / 1000.0) / 1e9
-            e.update({"bytes_per_step": int(stage_bytes[n] / args.steps), "achieved_gbs": gbs,
-                      "frac_of_hbm": gbs / hbm})
+        e = {"ms_per_frame": float(warm_ms[i] / args.warmup), "launches": int(warm_n[i]),
+             "share": float(warm_ms[i] / warm_ms.sum())}
+        if n in stage_bytes and warm_ms[i] > 0:
+            gbs = stage_bytes[n] / (warm_ms[i] / 1000.0) / 1e9
+            e.update({"achieved_gbs": gbs, "frac_of_hbm": gbs / hbm})
         stages[n] = e
     roofline["stages"] = stages
     fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
@@ -533,8 +548,8 @@ def run_ours(args, rank, world, local_rank):
         "tflops_standalone_fp32": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12,
         "fp32_simt_peak_tflops": fp32_peak,
         "frac_of_fp32_peak": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12 / fp32_peak,
-        "tflops_in_render": RRSNET_FLOP_PER_PATH * net_evals / (stage_ms[7] / 1000) / 1e12
-        if stage_ms[7] > 0 else None,
+        "tflops_in_render": RRSNET_FLOP_PER_PATH * warm_evals / (warm_ms[7] / 1000) / 1e12
+        if warm_ms[7] > 0 else None,
         "batch": n_q,
     }
     cpu = None

@@ -122,8 +122,10 @@ typedef struct nrrs_render_opts {
     uint32_t* d_trace;          /* device [max_depth][C][5] u32 or NULL: per depth and
                                    queue slot (pixel, sample, lineage, triangle or
                                    0xFFFFFFFF, X); for tests                        [NULL] */
-    int32_t profile;            /* record CUDA events around every kernel launch on
-                                   `stream`; per-stage times land in stats          [0]    */
+    int32_t profile;            /* record CUDA events around kernel launches on
+                                   `stream`; per-stage times land in stats.  1 = every
+                                   launch; otherwise bit (k + 1) times the launches of
+                                   stage k only (4 = NRRS_STAGE_EXTEND)             [0]    */
     int32_t graph;              /* capture the frame's launches (the whole bounce loop)
                                    into a CUDA graph on a scene-owned stream and launch
                                    that graph on `stream`; the executable graph is kept

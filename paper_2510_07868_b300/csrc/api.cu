@@ -71,6 +71,7 @@ struct Workspace {
     float4* acc_s = nullptr;
     float4* acc_c = nullptr;
     DevStats* st = nullptr;
+    FrameConsts* fc = nullptr;
 
     void release() {
         for (int k = 0; k < 2; ++k) {
@@ -80,7 +81,8 @@ struct Workspace {
             qo[k] = qd[k] = qt[k] = nullptr;
         }
         cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(feat); cudaFree(part); cudaFree(bcnt);
-        cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st);
+        cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st); cudaFree(fc);
+        fc = nullptr;
         hit = nullptr; q = nullptr; dep = nullptr; feat = nullptr; part = nullptr; bcnt = nullptr;
         has_feat = false;
         boff = nullptr; acc_s = acc_c = nullptr; st = nullptr;
@@ -189,8 +191,11 @@ struct nrrs_scene {
     // graph-captured renders: capture stream and executable graphs per launch shape
     cudaStream_t capture_stream = nullptr;
     struct GraphEntry {
-        uint64_t key;
+        uint64_t shape;             // launch shape: kernels and their order
+        uint64_t args;              // every launch argument except the per-frame constants
         cudaGraphExec_t exec;
+        unsigned launches;          // kernels in the graph
+        std::vector<int> stage_of;  // stage of every bracketed launch (profiled graphs)
     };
     std::vector<GraphEntry> graphs;
 };
@@ -227,6 +232,7 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
     CK(dalloc(&w.acc_s, npix));
     CK(dalloc(&w.acc_c, npix));
     CK(dalloc(&w.st, 1));
+    CK(dalloc(&w.fc, 1));
     w.cap = cap;
     w.npix = npix;
     return NRRS_OK;
@@ -261,14 +267,16 @@ V3d vnorm(V3d a) {
 struct StageTimer {
     nrrs_scene* sc;
     cudaStream_t s;
-    bool on;
+    unsigned mask;           // stages to time (bit k = stage k)
     bool capturing = false;  // events become graph nodes (recorded when the graph runs)
+    bool open = false;       // the current launch is bracketed
     int used = 0;
     unsigned launches = 0;
     std::vector<int> stage_of;
     cudaError_t begin(int stage) {
         ++launches;
-        if (!on) return cudaSuccess;
+        open = ((mask >> stage) & 1u) != 0;
+        if (!open) return cudaSuccess;
         while ((int)sc->events.size() < used + 2) {
             cudaEvent_t e;
             cudaError_t err = cudaEventCreate(&e);
@@ -279,7 +287,8 @@ struct StageTimer {
         return record(sc->events[used++]);
     }
     cudaError_t end() {
-        if (!on) return cudaSuccess;
+        if (!open) return cudaSuccess;
+        open = false;
         return record(sc->events[used++]);
     }
     cudaError_t record(cudaEvent_t e) {
@@ -508,41 +517,44 @@ uint64_t mix_key(uint64_t h, uint64_t v) {
     return h;
 }
 
-// Ends the capture on `cs`, brings the scene's executable graph for `key` up to date
-// (in-place update when the topology matches, else a new instantiation) and launches it
-// on `s`.
-nrrs_status launch_captured(nrrs_scene* sc, CaptureGuard& cg, uint64_t key, cudaStream_t s) {
+// Ends the capture on `cs` and brings the scene's executable graph for this launch shape
+// up to date: an in-place update when the topology matches, else a new instantiation.
+// Returns the entry, which the caller launches.
+nrrs_status finish_capture(nrrs_scene* sc, CaptureGuard& cg, uint64_t shape, uint64_t args,
+                           nrrs_scene::GraphEntry** out) {
     cudaGraph_t g = nullptr;
     cg.active = false;
     CK(cudaStreamEndCapture(cg.cs, &g));
-    cudaGraphExec_t exec = nullptr;
-    size_t slot = sc->graphs.size();
-    for (size_t k = 0; k < sc->graphs.size(); ++k)
-        if (sc->graphs[k].key == key) slot = k;
-    if (slot < sc->graphs.size()) {
+    auto& gs = sc->graphs;
+    size_t slot = gs.size();
+    for (size_t k = 0; k < gs.size(); ++k)
+        if (gs[k].shape == shape) slot = k;
+    if (slot < gs.size()) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(sc->graphs[slot].exec, g, &info) == cudaSuccess) {
-            exec = sc->graphs[slot].exec;
-        } else {
+        if (cudaGraphExecUpdate(gs[slot].exec, g, &info) != cudaSuccess) {
             cudaGetLastError();  // clear the failed update
-            cudaGraphExecDestroy(sc->graphs[slot].exec);
-            sc->graphs.erase(sc->graphs.begin() + slot);
+            cudaGraphExecDestroy(gs[slot].exec);
+            gs.erase(gs.begin() + slot);
+            slot = gs.size();
         }
     }
-    if (!exec) {
+    if (slot == gs.size()) {
+        cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             return cuda_fail(e, "cudaGraphInstantiate");
         }
-        if (sc->graphs.size() >= 8) {  // keep the 8 most recent launch shapes
-            cudaGraphExecDestroy(sc->graphs.front().exec);
-            sc->graphs.erase(sc->graphs.begin());
+        if (gs.size() >= 8) {  // keep the 8 most recent launch shapes
+            cudaGraphExecDestroy(gs.front().exec);
+            gs.erase(gs.begin());
         }
-        sc->graphs.push_back({key, exec});
+        gs.push_back({shape, 0, exec, 0, {}});
+        slot = gs.size() - 1;
     }
     cudaGraphDestroy(g);
-    CK(cudaGraphLaunch(exec, s));
+    gs[slot].args = args;
+    *out = &gs[slot];
     return NRRS_OK;
 }
 
@@ -581,8 +593,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     RenderParams rp{};
     rp.W = width; rp.H = height; rp.spp = spp; rp.D = max_depth;
     rp.cap = C;
-    rp.key0 = o.seed_lo;
-    rp.key1 = o.seed_hi ^ o.frame;
+    rp.fc = ws.fc;
     rp.f_rate = o.f_rate;
     rp.q_max = o.q_max;
     rp.boxcox_lambda = o.boxcox_lambda;
@@ -593,95 +604,136 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     scene->cam.aspect = (float)width / (float)height;
     const int normalized = rrs_mode == NRRS_RRS_HEUR_NORM || rrs_mode == NRRS_RRS_NET ||
                            rrs_mode == NRRS_RRS_NET_MIX;
+    const int update = o.update_ref && !o.d_pixel_ref;
 
-    // graph mode: record every launch below on the scene's capture stream, then run the
-    // graph on the caller's stream
-    const cudaStream_t s_exec = s;
-    CaptureGuard cg;
-    uint64_t gkey = 0;
-    if (o.graph) {
-        if (!scene->capture_stream)
-            CK(cudaStreamCreateWithFlags(&scene->capture_stream, cudaStreamNonBlocking));
-        const uint64_t shape[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
-                                  (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
-                                  o.gate, (uint64_t)o.cap_factor, (uint64_t)(rec != nullptr),
-                                  (uint64_t)(o.d_trace != nullptr), (uint64_t)o.profile,
-                                  (uint64_t)(rp.ref != nullptr), (uint64_t)o.update_ref};
-        for (uint64_t v : shape) gkey = mix_key(gkey, v);
-        cg.cs = scene->capture_stream;
-        CK(cudaStreamBeginCapture(cg.cs, cudaStreamCaptureModeRelaxed));
-        cg.active = true;
-        s = cg.cs;
-    }
-    CK(cudaMemsetAsync(ws.st, 0, sizeof(DevStats), s));
-    CK(cudaMemsetAsync(ws.acc_s, 0, sizeof(float4) * npix, s));
-    CK(cudaMemsetAsync(ws.acc_c, 0, sizeof(float4) * npix, s));
-    StageTimer tm{scene, s, o.profile != 0};
-    tm.capturing = o.graph != 0;
+    // the per-frame constants go to device memory ahead of the frame's launches
+    launch_frame_consts(ws.fc, o.seed_lo, o.seed_hi ^ o.frame, scene->ref_count, s);
+    unsigned extra_launches = 1;
+
+    // profile 1 = every stage; otherwise bit (k + 1) selects stage k
+    const unsigned pmask = o.profile == 1 ? 0xFFFFFFFFu : ((unsigned)o.profile >> 1);
+    StageTimer tm{scene, s, pmask};
+
+    // The frame's launch sequence.  In graph mode it is recorded once per set of launch
+    // arguments on the scene's capture stream and replayed on the caller's stream.
+    auto enqueue = [&](cudaStream_t s) -> nrrs_status {
+        CK(cudaMemsetAsync(ws.st, 0, sizeof(DevStats), s));
+        CK(cudaMemsetAsync(ws.acc_s, 0, sizeof(float4) * npix, s));
+        CK(cudaMemsetAsync(ws.acc_c, 0, sizeof(float4) * npix, s));
 #define TIMED(stage, call)           \
     do {                             \
         CK(tm.begin(stage));         \
         call;                        \
         CK(tm.end());                \
     } while (0)
-    TIMED(NRRS_STAGE_INIT, launch_ref_prepare(rp.ref, npix * 3, o.eps_rel, (double)o.alpha0, P, ws.st, s));
-    QueueView q[2];
-    for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
-    TIMED(NRRS_STAGE_INIT, launch_camera(scene->cam, rp, q[0], s));
-    WorkView w{};
-    w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.feat = ws.feat; w.part = ws.part;
-    w.grid_red = ws.grid_red;
-    w.bcnt = ws.bcnt; w.boff = ws.boff; w.grid_split = ws.grid_split;
-    w.acc_s = ws.acc_s; w.acc_c = ws.acc_c; w.st = ws.st;
-    int cur = 0;
-    for (int d = 1; d <= max_depth; ++d) {
-        const int kind = factor_kind(rrs_mode, o.gate, d);
-        if (rec) {  // this depth's factors, deposits and features go straight to the record
-            const size_t off = (size_t)(d - 1) * rec->C;
-            w.q = rec->q + off;
-            w.dep = rec->dep + off;
-            w.feat = rec->feat + off * 4;
-            rp.rec_first = rec->first + off;
-            rp.rec_X = rec->X + off;
-            CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C, cudaMemcpyDeviceToDevice, s));
-        }
-        TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
-        TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, rp, d, s));
-        if (kind == kFactorNet) {
-            if (o.precision != 32) {
-                TIMED(NRRS_STAGE_RRSNET,
-                      launch_rrsnet_tc_depth(o.precision, w, rp, d, scene->n_sm * 8, s));
-            } else {
-                WorkView wn = w;
-                wn.grid_red = scene->grid_rrsnet;
-                TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_depth(wn, rp, d, s));
+        TIMED(NRRS_STAGE_INIT,
+              launch_ref_prepare(rp.ref, npix * 3, o.eps_rel, (double)o.alpha0, P, ws.st, s));
+        QueueView q[2];
+        for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
+        TIMED(NRRS_STAGE_INIT, launch_camera(scene->cam, rp, q[0], s));
+        WorkView w{};
+        w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.feat = ws.feat; w.part = ws.part;
+        w.grid_red = ws.grid_red;
+        w.bcnt = ws.bcnt; w.boff = ws.boff; w.grid_split = ws.grid_split;
+        w.acc_s = ws.acc_s; w.acc_c = ws.acc_c; w.st = ws.st;
+        RenderParams r = rp;
+        int cur = 0;
+        for (int d = 1; d <= max_depth; ++d) {
+            const int kind = factor_kind(rrs_mode, o.gate, d);
+            if (rec) {  // this depth's factors, deposits and features go straight to the record
+                const size_t off = (size_t)(d - 1) * rec->C;
+                w.q = rec->q + off;
+                w.dep = rec->dep + off;
+                w.feat = rec->feat + off * 4;
+                r.rec_first = rec->first + off;
+                r.rec_X = rec->X + off;
+                CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C,
+                                   cudaMemcpyDeviceToDevice, s));
             }
-            TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
+            TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
+            TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
+            if (kind == kFactorNet) {
+                if (o.precision != 32) {
+                    TIMED(NRRS_STAGE_RRSNET,
+                          launch_rrsnet_tc_depth(o.precision, w, r, d, scene->n_sm * 8, s));
+                } else {
+                    WorkView wn = w;
+                    wn.grid_red = scene->grid_rrsnet;
+                    TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_depth(wn, r, d, s));
+                }
+                TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
+            }
+            TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
+            const int do_split = d < max_depth;
+            TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, r, d, do_split, s));
+            if (do_split) {
+                TIMED(NRRS_STAGE_SCAN, launch_split_scan(w, r, d, s));
+                TIMED(NRRS_STAGE_SCATTER,
+                      launch_split_scatter(scene->view, q[cur], q[cur ^ 1], w, r, d, s));
+                cur ^= 1;
+            } else if (rec) {
+                CK(cudaMemsetAsync(r.rec_X, 0, sizeof(uint32_t) * C, s));
+            }
         }
-        TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, rp, d, normalized, s));
-        const int do_split = d < max_depth;
-        TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, rp, d, do_split, s));
-        if (do_split) {
-            TIMED(NRRS_STAGE_SCAN, launch_split_scan(w, rp, d, s));
-            TIMED(NRRS_STAGE_SCATTER, launch_split_scatter(scene->view, q[cur], q[cur ^ 1], w, rp, d, s));
-            cur ^= 1;
-        } else if (rec) {
-            CK(cudaMemsetAsync(rp.rec_X, 0, sizeof(uint32_t) * C, s));
-        }
-    }
-    const int update = o.update_ref && !o.d_pixel_ref;
-    TIMED(NRRS_STAGE_FINALIZE,
-          launch_finalize(w, rp, d_rgb, scene->ref_mean, scene->ref_count, update, s));
-    if (rec)
-        for (int d = max_depth; d >= 1; --d)
-            TIMED(NRRS_STAGE_REVERSE, launch_reverse(*rec, d, max_depth, ws.st->live, ws.grid_red, s));
+        TIMED(NRRS_STAGE_FINALIZE, launch_finalize(w, r, d_rgb, scene->ref_mean, update, s));
+        if (rec)
+            for (int d = max_depth; d >= 1; --d)
+                TIMED(NRRS_STAGE_REVERSE,
+                      launch_reverse(*rec, d, max_depth, ws.st->live, ws.grid_red, s));
 #undef TIMED
-    CK(cudaGetLastError());
-    if (o.graph) {
-        nrrs_status grc = launch_captured(scene, cg, gkey, s_exec);
-        if (grc != NRRS_OK) return grc;
-        s = s_exec;
+        CK(cudaGetLastError());
+        return NRRS_OK;
+    };
+
+    if (!o.graph) {
+        nrrs_status erc = enqueue(s);
+        if (erc != NRRS_OK) return erc;
+    } else {
+        // shape: what fixes the kernels and their order; args: every launch argument
+        // (pointers, sizes, options) apart from the per-frame constants
+        uint64_t shape = 0;
+        const uint64_t sv[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
+                               (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
+                               o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile};
+        for (uint64_t v : sv) shape = mix_key(shape, v);
+        uint64_t args = shape;
+        auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };
+        const uint64_t av[] = {(uint64_t)o.cap_factor, fbits(o.f_rate), fbits(o.alpha0),
+                               fbits(o.q_max), fbits(o.eps_rel), fbits(o.boxcox_lambda),
+                               (uint64_t)update, (uint64_t)(uintptr_t)rp.ref,
+                               (uint64_t)(uintptr_t)rp.params, (uint64_t)(uintptr_t)o.d_trace,
+                               (uint64_t)(uintptr_t)d_rgb, (uint64_t)(uintptr_t)scene->ref_mean,
+                               (uint64_t)(uintptr_t)ws.st, (uint64_t)(uintptr_t)ws.qo[0],
+                               (uint64_t)(uintptr_t)ws.feat, (uint64_t)ws.cap,
+                               (uint64_t)(uintptr_t)(rec ? rec->q : nullptr),
+                               (uint64_t)(rec ? rec->C : 0),
+                               (uint64_t)fbits(scene->cam.aspect)};
+        for (uint64_t v : av) args = mix_key(args, v);
+        nrrs_scene::GraphEntry* ge = nullptr;
+        for (auto& e : scene->graphs)
+            if (e.shape == shape && e.args == args) ge = &e;
+        if (!ge) {
+            if (!scene->capture_stream)
+                CK(cudaStreamCreateWithFlags(&scene->capture_stream, cudaStreamNonBlocking));
+            CaptureGuard cg;
+            cg.cs = scene->capture_stream;
+            CK(cudaStreamBeginCapture(cg.cs, cudaStreamCaptureModeRelaxed));
+            cg.active = true;
+            tm.s = cg.cs;
+            tm.capturing = true;
+            nrrs_status erc = enqueue(cg.cs);
+            if (erc != NRRS_OK) return erc;
+            erc = finish_capture(scene, cg, shape, args, &ge);
+            if (erc != NRRS_OK) return erc;
+            ge->launches = tm.launches;
+            ge->stage_of = tm.stage_of;
+        } else {
+            tm.launches = ge->launches;
+            tm.stage_of = ge->stage_of;
+        }
+        CK(cudaGraphLaunch(ge->exec, s));
     }
+    tm.launches += extra_launches;
     if (update) scene->ref_count++;
     if (stats) {
         DevStats h;

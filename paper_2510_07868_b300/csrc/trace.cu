@@ -1,0 +1,171 @@
+// Closest-hit BVH2 traversal for sm_103a: the extension stage of one bounce (Sec. 2,
+// the wavefront formulation the method runs in).  Persistent warps claim rays from the
+// live queue; the traversal stack lives in shared memory.
+#include <cfloat>
+
+#include "wavefront.cuh"
+
+namespace nrrs {
+
+namespace {
+
+constexpr int kExtendThreads = 256;
+constexpr int kStack = 40;  // BVH build depth is capped below this
+constexpr int kSteps = 8;   // node visits between ray fetch rounds
+
+__device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
+
+// ------------------------------------------------------------------ traversal
+struct Hit {
+    float t;
+    int slot;      // BVH-order triangle slot, -1 = miss
+    uint32_t id;   // original triangle index (tie-break)
+};
+
+// One ray's traversal state.  The stack lives in shared memory, one column per thread
+// (entry k at stk[k * stride]) so that lanes hit different banks.
+struct Ray {
+    V3 o, d, inv, oi;
+    int node, sp;
+};
+
+__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, Hit& h) {
+    r.o = o;
+    r.d = d;
+    r.inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    r.node = 0;
+    r.sp = 0;
+    h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
+}
+
+// Visits one BVH2 node of the closest-hit query along o + t d (t > 0): both child boxes
+// are tested, leaf children are intersected at once (Moller-Trumbore), inner children
+// are visited near-first.  Equal distances go to the lower original triangle index, so
+// the answer does not depend on the visiting order.  Returns true when the query ends.
+__device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, int* stk,
+                                           int stride) {
+    const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
+    const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
+    const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
+    const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
+    float lx = fmaf(a.x, r.inv.x, -r.oi.x), hx = fmaf(a.y, r.inv.x, -r.oi.x);
+    float ly = fmaf(a.z, r.inv.y, -r.oi.y), hy = fmaf(a.w, r.inv.y, -r.oi.y);
+    float lz = fmaf(c.x, r.inv.z, -r.oi.z), hz = fmaf(c.y, r.inv.z, -r.oi.z);
+    const float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+    const float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+    bool h0 = t0n <= t0f;
+    lx = fmaf(b.x, r.inv.x, -r.oi.x); hx = fmaf(b.y, r.inv.x, -r.oi.x);
+    ly = fmaf(b.z, r.inv.y, -r.oi.y); hy = fmaf(b.w, r.inv.y, -r.oi.y);
+    lz = fmaf(c.z, r.inv.z, -r.oi.z); hz = fmaf(c.w, r.inv.z, -r.oi.z);
+    const float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
+    const float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
+    bool h1 = t1n <= t1f;
+    int c0 = e.x, c1 = e.y;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int code = side ? c1 : c0;
+        const bool hitbox = side ? h1 : h0;
+        if (!hitbox || code >= 0) continue;
+        const int first = ~code, count = side ? e.w : e.z;
+        for (int k = 0; k < count; ++k) {
+            const int s = first + k;
+            const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
+            const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
+            const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
+            const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
+            const V3 pv = cross3(r.d, e2);
+            const float det = dot3(e1, pv);
+            if (det == 0.0f) continue;
+            const float idet = 1.0f / det;
+            const V3 tv = r.o - v0;
+            const float u = dot3(tv, pv) * idet;
+            if (u < 0.0f || u > 1.0f) continue;
+            const V3 qv = cross3(tv, e1);
+            const float v = dot3(r.d, qv) * idet;
+            if (v < 0.0f || u + v > 1.0f) continue;
+            const float t = dot3(e2, qv) * idet;
+            const uint32_t id = fbits(t0.w);
+            if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
+                h.t = t;
+                h.slot = s;
+                h.id = id;
+            }
+        }
+        if (side) h1 = false; else h0 = false;
+    }
+    if (h0 && h1) {
+        if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
+        if (r.sp < kStack) stk[(r.sp++) * stride] = c1;
+        r.node = c0;
+        return false;
+    }
+    if (h0) { r.node = c0; return false; }
+    if (h1) { r.node = c1; return false; }
+    if (r.sp == 0) return true;
+    r.node = stk[(--r.sp) * stride];
+    return false;
+}
+
+// Extension of depth `depth`, part 1: the closest hit of every live ray.  Persistent
+// warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
+// the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
+// Each slot's hit depends only on that slot's ray, so the result is deterministic.
+__global__ void __launch_bounds__(kExtendThreads, 4)
+k_trace(SceneView sc, QueueView cur, WorkView w, int depth) {
+    __shared__ int s_stack[kStack * kExtendThreads];
+    int* stk = s_stack + threadIdx.x;
+    DevStats* st = w.st;
+    const long long n = st->live[depth - 1];
+    unsigned long long* ctr = &st->fetch[depth - 1];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    long long idx = -1;
+    bool exhausted = false;
+    Ray ray;
+    Hit h;
+    for (;;) {
+        const bool need = idx < 0 && !exhausted;
+        const unsigned need_mask = __ballot_sync(0xffffffffu, need);
+        if (need_mask) {
+            const int leader = __ffs(need_mask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(need_mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const long long my = (long long)base + __popc(need_mask & lt_mask);
+                if (my < n) {
+                    idx = my;
+                    ray_init(ray, xyz(cur.o[idx]), xyz(cur.d[idx]), h);
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, idx < 0)) break;
+        if (idx < 0) continue;
+        bool done = false;
+        for (int step = 0; step < kSteps && !done; ++step)
+            done = visit_node(sc, ray, h, stk, kExtendThreads);
+        if (!done) continue;
+        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
+        idx = -1;
+    }
+}
+
+}  // namespace
+
+int extend_block_threads() { return kExtendThreads; }
+
+int max_blocks_trace() {
+    int nb = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, kExtendThreads, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
+                  cudaStream_t s) {
+    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth);
+}
+
+}  // namespace nrrs

@@ -1,6 +1,6 @@
-// Wavefront bounce kernels for sm_103a: camera rays, extension (BVH2 traversal,
-// emission deposit, RRS factor), normalization, split counts + compaction, and the
-// per-pixel accumulation.  The method: "NRRS: Neural Russian Roulette and Splitting",
+// Wavefront bounce kernels for sm_103a: camera rays, shading (emission deposit, RRS
+// factor), normalization, split counts + compaction, and the per-pixel accumulation
+// (the closest-hit traversal is in trace.cu).  The method: "NRRS: Neural Russian Roulette and Splitting",
 // Sec. 2 (Eq. rrs_factor), Sec. 3.1 (Eq. q_norm, F_norm, q_norm_rate, f_rate_prime),
 // Sec. 4 (network, Eq. rrsnet_activation, "Compromise").
 #include <cfloat>
@@ -12,107 +12,12 @@ namespace nrrs {
 
 namespace {
 
-constexpr int kExtendThreads = 256;
 constexpr int kSplitThreads = 256;
 constexpr int kReduceThreads = 1024;
-constexpr int kStack = 40;        // BVH build depth is capped below this
-constexpr int kSteps = 8;         // node visits between ray fetch rounds
 constexpr uint32_t kMaxX = 1u << 23;  // q_used >= 2^23 has no fractional part in FP32
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 __device__ __forceinline__ float bitsf(uint32_t u) { return __uint_as_float(u); }
-
-// ------------------------------------------------------------------ traversal
-struct Hit {
-    float t;
-    int slot;      // BVH-order triangle slot, -1 = miss
-    uint32_t id;   // original triangle index (tie-break)
-};
-
-// One ray's traversal state.  The stack lives in shared memory, one column per thread
-// (entry k at stk[k * stride]) so that lanes hit different banks.
-struct Ray {
-    V3 o, d, inv, oi;
-    int node, sp;
-};
-
-__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, Hit& h) {
-    r.o = o;
-    r.d = d;
-    r.inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
-    r.node = 0;
-    r.sp = 0;
-    h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
-}
-
-// Visits one BVH2 node of the closest-hit query along o + t d (t > 0): both child boxes
-// are tested, leaf children are intersected at once (Moller-Trumbore), inner children
-// are visited near-first.  Equal distances go to the lower original triangle index, so
-// the answer does not depend on the visiting order.  Returns true when the query ends.
-__device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, int* stk,
-                                           int stride) {
-    const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
-    const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
-    const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
-    const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
-    float lx = fmaf(a.x, r.inv.x, -r.oi.x), hx = fmaf(a.y, r.inv.x, -r.oi.x);
-    float ly = fmaf(a.z, r.inv.y, -r.oi.y), hy = fmaf(a.w, r.inv.y, -r.oi.y);
-    float lz = fmaf(c.x, r.inv.z, -r.oi.z), hz = fmaf(c.y, r.inv.z, -r.oi.z);
-    const float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-    const float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-    bool h0 = t0n <= t0f;
-    lx = fmaf(b.x, r.inv.x, -r.oi.x); hx = fmaf(b.y, r.inv.x, -r.oi.x);
-    ly = fmaf(b.z, r.inv.y, -r.oi.y); hy = fmaf(b.w, r.inv.y, -r.oi.y);
-    lz = fmaf(c.z, r.inv.z, -r.oi.z); hz = fmaf(c.w, r.inv.z, -r.oi.z);
-    const float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-    const float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-    bool h1 = t1n <= t1f;
-    int c0 = e.x, c1 = e.y;
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-        const int code = side ? c1 : c0;
-        const bool hitbox = side ? h1 : h0;
-        if (!hitbox || code >= 0) continue;
-        const int first = ~code, count = side ? e.w : e.z;
-        for (int k = 0; k < count; ++k) {
-            const int s = first + k;
-            const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
-            const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
-            const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
-            const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
-            const V3 pv = cross3(r.d, e2);
-            const float det = dot3(e1, pv);
-            if (det == 0.0f) continue;
-            const float idet = 1.0f / det;
-            const V3 tv = r.o - v0;
-            const float u = dot3(tv, pv) * idet;
-            if (u < 0.0f || u > 1.0f) continue;
-            const V3 qv = cross3(tv, e1);
-            const float v = dot3(r.d, qv) * idet;
-            if (v < 0.0f || u + v > 1.0f) continue;
-            const float t = dot3(e2, qv) * idet;
-            const uint32_t id = fbits(t0.w);
-            if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
-                h.t = t;
-                h.slot = s;
-                h.id = id;
-            }
-        }
-        if (side) h1 = false; else h0 = false;
-    }
-    if (h0 && h1) {
-        if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
-        if (r.sp < kStack) stk[(r.sp++) * stride] = c1;
-        r.node = c0;
-        return false;
-    }
-    if (h0) { r.node = c0; return false; }
-    if (h1) { r.node = c1; return false; }
-    if (r.sp == 0) return true;
-    r.node = stk[(--r.sp) * stride];
-    return false;
-}
 
 __device__ __forceinline__ V3 tri_geom_normal(const SceneView& sc, int slot, int* mat) {
     const float4 t1 = __ldg(&sc.tris[3 * slot + 1]);
@@ -315,7 +220,7 @@ __global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const uint32_t pixel = (uint32_t)(i / rp.spp), sample = (uint32_t)(i % rp.spp);
-    const U4 w = draw(rp.key0, rp.key1, pixel, sample, 0u, kPurposeJitter, 0u);
+    const U4 w = draw(rp.fc->key0, rp.fc->key1, pixel, sample, 0u, kPurposeJitter, 0u);
     const int px = (int)(pixel % (uint32_t)rp.W), py = (int)(pixel / (uint32_t)rp.W);
     const float sx = (2.0f * ((float)px + u01(w.x)) / (float)rp.W - 1.0f) * cam.tan_half * cam.aspect;
     const float sy = (1.0f - 2.0f * ((float)py + u01(w.y)) / (float)rp.H) * cam.tan_half;
@@ -326,52 +231,6 @@ __global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
     out.o[i] = make_float4(cam.pos[0], cam.pos[1], cam.pos[2], bitsf(pixel));
     out.d[i] = make_float4(d.x, d.y, d.z, bitsf(0u));
     out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
-}
-
-// Extension of depth `depth`, part 1: the closest hit of every live ray.  Persistent
-// warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
-// the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
-// Each slot's hit depends only on that slot's ray, so the result is deterministic.
-__global__ void __launch_bounds__(kExtendThreads, 4)
-k_trace(SceneView sc, QueueView cur, WorkView w, int depth) {
-    __shared__ int s_stack[kStack * kExtendThreads];
-    int* stk = s_stack + threadIdx.x;
-    DevStats* st = w.st;
-    const long long n = st->live[depth - 1];
-    unsigned long long* ctr = &st->fetch[depth - 1];
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    long long idx = -1;
-    bool exhausted = false;
-    Ray ray;
-    Hit h;
-    for (;;) {
-        const bool need = idx < 0 && !exhausted;
-        const unsigned need_mask = __ballot_sync(0xffffffffu, need);
-        if (need_mask) {
-            const int leader = __ffs(need_mask) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(need_mask));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (need) {
-                const long long my = (long long)base + __popc(need_mask & lt_mask);
-                if (my < n) {
-                    idx = my;
-                    ray_init(ray, xyz(cur.o[idx]), xyz(cur.d[idx]), h);
-                } else {
-                    exhausted = true;
-                }
-            }
-        }
-        if (__all_sync(0xffffffffu, idx < 0)) break;
-        if (idx < 0) continue;
-        bool done = false;
-        for (int step = 0; step < kSteps && !done; ++step)
-            done = visit_node(sc, ray, h, stk, kExtendThreads);
-        if (!done) continue;
-        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
-        idx = -1;
-    }
 }
 
 // Extension of depth `depth`, part 2 (fixed grid-stride, coherent): emission deposit,
@@ -565,6 +424,7 @@ __global__ void __launch_bounds__(kSplitThreads)
 k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth, int do_split) {
     __shared__ unsigned long long sh[32];
     DevStats* st = w.st;
+    const uint32_t key0 = rp.fc->key0, key1 = rp.fc->key1;
     const long long n = st->live[depth - 1];
     const float F = st->F_cur;
     long long begin, end;
@@ -593,7 +453,7 @@ k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int dept
                 const float4 t4 = cur.t[i];
                 float qu;
                 uint32_t base;
-                X = split_decide(F, w.q[i], rp.key0, rp.key1, fbits(o4.w), fbits(t4.w),
+                X = split_decide(F, w.q[i], key0, key1, fbits(o4.w), fbits(t4.w),
                                  (uint32_t)depth, fbits(d4.w), &qu, &base);
                 if (rp.trace) {
                     const int slot = __float_as_int(w.hit[i].y);
@@ -666,6 +526,7 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
                 int depth) {
     __shared__ uint32_t sh[33];
     DevStats* st = w.st;
+    const uint32_t key0 = rp.fc->key0, key1 = rp.fc->key1;
     const long long n = st->live[depth - 1];
     const float F = st->F_cur;
     long long begin, end;
@@ -681,7 +542,7 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
             o4 = cur.o[i];
             d4 = cur.d[i];
             t4 = cur.t[i];
-            X = split_decide(F, w.q[i], rp.key0, rp.key1, fbits(o4.w), fbits(t4.w),
+            X = split_decide(F, w.q[i], key0, key1, fbits(o4.w), fbits(t4.w),
                              (uint32_t)depth, fbits(d4.w), &qu, &base);
         }
         uint32_t tile_total;
@@ -707,7 +568,7 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
                 const unsigned long long dst = carry + pre + j;
                 if (dst >= (unsigned long long)rp.cap) break;
                 const uint32_t lin = base + j * kLineageStep;
-                const U4 r = draw(rp.key0, rp.key1, pix, smp, (uint32_t)depth, kPurposeBsdf, lin);
+                const U4 r = draw(key0, key1, pix, smp, (uint32_t)depth, kPurposeBsdf, lin);
                 V3 wi, wt;
                 if (m.type == 0) {
                     wi = cosine_dir(ns, u01(r.y), u01(r.z));
@@ -726,7 +587,7 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
 }
 
 __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
-                           float* __restrict__ ref_mean, int ref_count, int update_ref) {
+                           float* __restrict__ ref_mean, int update_ref) {
     const long long npix = (long long)rp.W * rp.H;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
@@ -738,7 +599,7 @@ __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
     rgb[3 * p + 2] = b;
     if (update_ref && ref_mean) {
         // running mean of the frames so far (the reference I_px of Sec. 4 "Compromise")
-        const float k = (float)ref_count;
+        const float k = (float)rp.fc->ref_count;
         const float ik = 1.0f / (k + 1.0f);
         float* m = ref_mean + 3 * p;
         m[0] = (m[0] * k + r) * ik;
@@ -860,14 +721,7 @@ k_split_arr_scatter(SplitArrays a, const unsigned long long* boff) {
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-int extend_block_threads() { return kExtendThreads; }
 int split_block_threads() { return kSplitThreads; }
-
-int max_blocks_trace() {
-    int nb = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, kExtendThreads, 0);
-    return nb < 1 ? 1 : nb;
-}
 
 int max_blocks_rrsnet() {
     int nb = 1;
@@ -884,11 +738,6 @@ void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cu
     const long long P = (long long)rp.W * rp.H * rp.spp;
     const int threads = 256;
     k_camera<<<(unsigned)((P + threads - 1) / threads), threads, 0, s>>>(cam, rp, out);
-}
-
-void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
-                  cudaStream_t s) {
-    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth);
 }
 
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
@@ -930,10 +779,21 @@ void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, con
 }
 
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
-                     int ref_count, int update_ref, cudaStream_t s) {
+                     int update_ref, cudaStream_t s) {
     const long long npix = (long long)rp.W * rp.H;
-    k_finalize<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(w, rp, rgb, ref_mean, ref_count,
-                                                               update_ref);
+    k_finalize<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(w, rp, rgb, ref_mean, update_ref);
+}
+
+__global__ void k_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count) {
+    fc->key0 = key0;
+    fc->key1 = key1;
+    fc->ref_count = ref_count;
+    fc->pad = 0;
+}
+
+void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count,
+                         cudaStream_t s) {
+    k_frame_consts<<<1, 1, 0, s>>>(fc, key0, key1, ref_count);
 }
 
 void launch_query_factors(const float* params, const float* feat, long long n, float* q,

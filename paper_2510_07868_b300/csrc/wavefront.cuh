@@ -63,10 +63,18 @@ struct WorkView {
     DevStats* st;
 };
 
+// Per-frame values read by the kernels from device memory, so that one recorded launch
+// sequence (a CUDA graph) serves every frame of the same shape.
+struct FrameConsts {
+    uint32_t key0, key1;  // Philox key
+    int ref_count;        // frames folded into the running reference mean so far
+    int pad;
+};
+
 struct RenderParams {
     int W, H, spp, D;
     long long cap;        // C
-    uint32_t key0, key1;  // Philox key
+    const FrameConsts* fc;
     float f_rate;
     float q_max;
     float boxcox_lambda;
@@ -101,7 +109,9 @@ void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cud
 void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
                           const RenderParams& rp, int depth, cudaStream_t s);
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
-                     int ref_count, int update_ref, cudaStream_t s);
+                     int update_ref, cudaStream_t s);
+void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count,
+                         cudaStream_t s);
 
 // RRSNet on the tensor cores (rrsnet_tc.cu): precision 16 = split BF16 operands,
 // 8 = E4M3 operands with per-tensor scales; FP32 accumulation.
