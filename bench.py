@@ -360,7 +360,9 @@ def run_ours(args, rank, world, local_rank):
                                                          profile=profile, graph=graph),
                                 out, stream, True)
 
-    # set-up (untimed): online training through the warm-up phase into the full loss
+    # set-up (untimed): RRSNet launch shapes per queue-size bucket for each precision
+    tuner = {p: sc.tune(p) for p in (32, 16, 8)}
+    # online training through the warm-up phase into the full loss
     pre = []
     for k in range(args.pretrain):
         pre.append(train(10_000 + k))
@@ -551,6 +553,12 @@ def run_ours(args, rank, world, local_rank):
         "tflops_in_render": RRSNET_FLOP_PER_PATH * warm_evals / (warm_ms[7] / 1000) / 1e12
         if warm_ms[7] > 0 else None,
         "batch": n_q,
+        "tuned_shapes": {
+            str(p): {"rows": r["rows"], "variant": r["variant"],
+                     "blocks_per_sm": r["blocks_per_sm"],
+                     "speedup_vs_default": [d / b if b > 0 else None
+                                            for b, d in zip(r["ms_best"], r["ms_default"])]}
+            for p, r in tuner.items()},
     }
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -181,7 +181,14 @@ struct nrrs_scene {
     SceneView view{};
     CamView cam{};
     Workspace ws;
-    int grid_trace = 0, grid_rrsnet = 0, grid_sum = 0;
+    int grid_trace = 0, grid_sum = 0;
+    // RRSNet launch shapes per queue-size bucket (FP32, BF16, E4M3), set by the tuner
+    RrsnetChoice tune[3][kTuneBuckets];
+    bool tuned[3] = {false, false, false};
+    // live counts of the last render that returned stats: the queue sizes expected at
+    // each depth of the next frame (scaled by its primary count)
+    long long last_live[NRRS_MAX_DEPTH] = {};
+    long long last_P = 0;
     // running mean of earlier frames (HEUR reference), [npix * 3]
     float* ref_mean = nullptr;
     int ref_count = 0;
@@ -305,6 +312,14 @@ struct StageTimer {
     }
 };
 
+int precision_index(int precision) { return precision == 32 ? 0 : precision == 16 ? 1 : 2; }
+
+// Launch shape of the RRSNet kernel for a queue of about n rows.
+RrsnetChoice rrsnet_choice(const nrrs_scene* sc, int precision, long long n) {
+    const int p = precision_index(precision);
+    return sc->tuned[p] ? sc->tune[p][tune_bucket(n)] : default_choice(precision);
+}
+
 int factor_kind(int mode, uint64_t gate, int depth) {
     switch (mode) {
         case kNone: return kFactorOne;
@@ -400,7 +415,6 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     s->cam.up[0] = (float)up2.x; s->cam.up[1] = (float)up2.y; s->cam.up[2] = (float)up2.z;
     s->cam.tan_half = (float)std::tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0);
     s->grid_trace = s->n_sm * max_blocks_trace();
-    s->grid_rrsnet = s->n_sm * max_blocks_rrsnet();
     s->grid_sum = s->n_sm * 4;
     *out = s;
     return NRRS_OK;
@@ -606,6 +620,15 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                            rrs_mode == NRRS_RRS_NET_MIX;
     const int update = o.update_ref && !o.d_pixel_ref;
 
+    // RRSNet launch shape per depth, from the queue sizes of the last frame
+    RrsnetChoice net_shape[NRRS_MAX_DEPTH];
+    for (int d = 1; d <= max_depth; ++d) {
+        long long n = P;
+        if (d > 1 && scene->last_P > 0)
+            n = (long long)((double)scene->last_live[d - 1] * (double)P / (double)scene->last_P);
+        net_shape[d - 1] = rrsnet_choice(scene, o.precision, n);
+    }
+
     // the per-frame constants go to device memory ahead of the frame's launches
     launch_frame_consts(ws.fc, o.seed_lo, o.seed_hi ^ o.frame, scene->ref_count, s);
     unsigned extra_launches = 1;
@@ -653,14 +676,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
             TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
             if (kind == kFactorNet) {
-                if (o.precision != 32) {
-                    TIMED(NRRS_STAGE_RRSNET,
-                          launch_rrsnet_tc_depth(o.precision, w, r, d, scene->n_sm * 8, s));
-                } else {
-                    WorkView wn = w;
-                    wn.grid_red = scene->grid_rrsnet;
-                    TIMED(NRRS_STAGE_RRSNET, launch_rrsnet_depth(wn, r, d, s));
-                }
+                TIMED(NRRS_STAGE_RRSNET,
+                      launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
+                                    &w.st->live[d - 1], 0, w.q, 1, w.st, &w.st->status, s));
                 TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
             }
             TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
@@ -709,6 +727,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(rec ? rec->C : 0),
                                (uint64_t)fbits(scene->cam.aspect)};
         for (uint64_t v : av) args = mix_key(args, v);
+        for (int d = 1; d <= max_depth; ++d)
+            args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
+                                            net_shape[d - 1].blocks_per_sm));
         nrrs_scene::GraphEntry* ge = nullptr;
         for (auto& e : scene->graphs)
             if (e.shape == shape && e.args == args) ge = &e;
@@ -755,6 +776,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         stats->status_bits = h.status;
         stats->kernel_launches = tm.launches;
         tm.collect(stats);
+        for (int d = 0; d < NRRS_MAX_DEPTH; ++d) scene->last_live[d] = d < max_depth ? h.live[d] : 0;
+        scene->last_P = P;
     }
     return NRRS_OK;
 }
@@ -806,11 +829,9 @@ nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64
     if ((reinterpret_cast<uintptr_t>(d_features) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_features must be 16-byte aligned");
     DeviceGuard g(scene->device);
-    if (precision != 32)
-        launch_rrsnet_tc_query(precision, scene->params, d_features, n, d_q, nullptr,
-                               (cudaStream_t)stream);
-    else
-        launch_query_factors(scene->params, d_features, n, d_q, (cudaStream_t)stream);
+    launch_rrsnet(precision, rrsnet_choice(scene, precision, n), scene->n_sm, scene->params,
+                  reinterpret_cast<const float4*>(d_features), nullptr, n, d_q, 0, nullptr,
+                  nullptr, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NRRS_OK;
 }
@@ -1013,6 +1034,59 @@ nrrs_status nrrs_rrsnet_backward(nrrs_scene* scene, const float* d_params, const
     return mlp_grad_impl(scene, 1, true, d_params, d_x, d_gq, n, d_grad, stream);
 }
 
+nrrs_status nrrs_tune_rrsnet(nrrs_scene* scene, int32_t precision, void* stream,
+                             nrrs_tune_report* report) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (precision != 32 && precision != 16 && precision != 8)
+        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16 or 8");
+    static_assert(NRRS_TUNE_BUCKETS == kTuneBuckets, "bucket count");
+    DeviceGuard g(scene->device);
+    RrsnetChoice table[kTuneBuckets];
+    long long rows[kTuneBuckets];
+    float best[kTuneBuckets], dflt[kTuneBuckets];
+    cudaError_t e = tune_rrsnet(precision, scene->n_sm, scene->params, 12582912ll,
+                                (cudaStream_t)stream, table, rows, best, dflt);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(NRRS_ERR_OOM, "tuner buffers");
+    }
+    CK(e);
+    const int p = precision_index(precision);
+    for (int b = 0; b < kTuneBuckets; ++b) scene->tune[p][b] = table[b];
+    scene->tuned[p] = true;
+    if (report) {
+        std::memset(report, 0, sizeof(*report));
+        report->precision = precision;
+        report->n_buckets = kTuneBuckets;
+        for (int b = 0; b < kTuneBuckets; ++b) {
+            report->rows[b] = rows[b];
+            report->variant[b] = table[b].variant;
+            report->blocks_per_sm[b] = table[b].blocks_per_sm;
+            report->ms_best[b] = best[b];
+            report->ms_default[b] = dflt[b];
+        }
+    }
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_set_rrsnet_shape(nrrs_scene* scene, int32_t precision, int32_t bucket,
+                                  int32_t variant, int32_t blocks_per_sm) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (precision != 32 && precision != 16 && precision != 8)
+        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16 or 8");
+    if (bucket < -1 || bucket >= kTuneBuckets) return fail(NRRS_ERR_INVALID_ARG, "bad bucket");
+    const bool ok_variant = precision == 32 ? (variant == 1 || variant == 2) : variant == 0;
+    if (!ok_variant || blocks_per_sm < 1 || blocks_per_sm > 32)
+        return fail(NRRS_ERR_INVALID_ARG, "bad launch shape");
+    const int p = precision_index(precision);
+    if (!scene->tuned[p])
+        for (int b = 0; b < kTuneBuckets; ++b) scene->tune[p][b] = default_choice(precision);
+    for (int b = 0; b < kTuneBuckets; ++b)
+        if (bucket < 0 || b == bucket) scene->tune[p][b] = RrsnetChoice{variant, blocks_per_sm};
+    scene->tuned[p] = true;
+    return NRRS_OK;
+}
+
 nrrs_status nrrs_rrsnet_forward(const float* d_params, const float* d_x, int64_t n, float* d_q,
                                 void* stream) {
     if (n < 0 || !d_params || (n > 0 && (!d_x || !d_q)))
@@ -1020,7 +1094,11 @@ nrrs_status nrrs_rrsnet_forward(const float* d_params, const float* d_x, int64_t
     if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_x must be 16-byte aligned");
     if (n == 0) return NRRS_OK;
-    launch_query_factors(d_params, d_x, n, d_q, (cudaStream_t)stream);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    launch_rrsnet(32, default_choice(32), sm_count(dev), d_params,
+                  reinterpret_cast<const float4*>(d_x), nullptr, n, d_q, 0, nullptr, nullptr,
+                  (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NRRS_OK;
 }

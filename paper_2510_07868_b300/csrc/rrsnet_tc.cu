@@ -154,6 +154,7 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
     __shared__ TcSmem sm;
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long n = n_ptr ? *n_ptr : n_host;
+    if ((long long)blockIdx.x * kTcThreads >= n) return;  // no tile: allocate nothing
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&sm.tmem)),
@@ -359,6 +360,7 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
     __shared__ Fp8Smem sm;
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long n = n_ptr ? *n_ptr : n_host;
+    if ((long long)blockIdx.x * kTcThreads >= n) return;  // no tile: allocate nothing
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&sm.tmem)),
@@ -491,36 +493,17 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
     }
 }
 
-int tc_grid(long long n) {
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
-    long long g = (long long)nsm * 8;
-    if (n >= 0 && tiles < g) g = tiles > 0 ? tiles : 1;
-    return (int)g;
-}
-
 }  // namespace
 
-void launch_rrsnet_tc_query(int precision, const float* params, const float* feat, long long n,
-                            float* q, unsigned int* status, cudaStream_t s) {
-    if (n <= 0) return;
-    const float4* f = reinterpret_cast<const float4*>(feat);
+void launch_rrsnet_tc(int precision, int grid, const float* params, const float4* feat,
+                      const long long* n_ptr, long long n_host, float* q, int sentinel,
+                      DevStats* st, unsigned int* status, cudaStream_t s) {
     if (precision == 8)
-        k_rrsnet_fp8<<<tc_grid(n), kTcThreads, 0, s>>>(params, f, nullptr, n, q, 0, nullptr, status);
+        k_rrsnet_fp8<<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel, st,
+                                                 status);
     else
-        k_rrsnet_tc<<<tc_grid(n), kTcThreads, 0, s>>>(params, f, nullptr, n, q, 0, nullptr, status);
-}
-
-void launch_rrsnet_tc_depth(int precision, const WorkView& w, const RenderParams& rp, int depth,
-                            int grid, cudaStream_t s) {
-    if (precision == 8)
-        k_rrsnet_fp8<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q,
-                                                 1, w.st, &w.st->status);
-    else
-        k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(rp.params, w.feat, &w.st->live[depth - 1], 0, w.q,
-                                                1, w.st, &w.st->status);
+        k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel, st,
+                                                status);
 }
 
 }  // namespace nrrs

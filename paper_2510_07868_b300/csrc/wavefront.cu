@@ -26,77 +26,6 @@ __device__ __forceinline__ V3 tri_geom_normal(const SceneView& sc, int slot, int
     return normalize3(cross3(xyz(t1), xyz(t2)));
 }
 
-// ------------------------------------------------------------------ RRSNet (FP32)
-// Sec. 4 "Network Architecture": 16 -> 32 -> 32 -> 32 -> 1, no biases, Leaky ReLU
-// after each hidden layer; output through Eq. rrsnet_activation.  `w` points at the
-// 2592 weights (shared memory), rows contiguous.
-__device__ __forceinline__ float softplus_mod(float z) {
-    return z < 0.0f ? log1pf(expf(z)) : fmaf(0.5f, z, 0.693147180559945f);
-}
-
-__device__ __forceinline__ float rrsnet_forward(const float* __restrict__ w, const float (&x)[kNF]) {
-    float h[kNH], g[kNH];
-    const float4* W1 = reinterpret_cast<const float4*>(w);
-#pragma unroll
-    for (int j = 0; j < kNH; ++j) {
-        float a = 0.0f;
-#pragma unroll
-        for (int k4 = 0; k4 < kNF / 4; ++k4) {
-            const float4 ww = W1[j * (kNF / 4) + k4];
-            a = fmaf(ww.x, x[4 * k4 + 0], a);
-            a = fmaf(ww.y, x[4 * k4 + 1], a);
-            a = fmaf(ww.z, x[4 * k4 + 2], a);
-            a = fmaf(ww.w, x[4 * k4 + 3], a);
-        }
-        h[j] = a > 0.0f ? a : kLeak * a;
-    }
-    const float4* W2 = reinterpret_cast<const float4*>(w + kNH * kNF);
-#pragma unroll
-    for (int j = 0; j < kNH; ++j) {
-        float a = 0.0f;
-#pragma unroll
-        for (int k4 = 0; k4 < kNH / 4; ++k4) {
-            const float4 ww = W2[j * (kNH / 4) + k4];
-            a = fmaf(ww.x, h[4 * k4 + 0], a);
-            a = fmaf(ww.y, h[4 * k4 + 1], a);
-            a = fmaf(ww.z, h[4 * k4 + 2], a);
-            a = fmaf(ww.w, h[4 * k4 + 3], a);
-        }
-        g[j] = a > 0.0f ? a : kLeak * a;
-    }
-    const float4* W3 = reinterpret_cast<const float4*>(w + kNH * kNF + kNH * kNH);
-#pragma unroll
-    for (int j = 0; j < kNH; ++j) {
-        float a = 0.0f;
-#pragma unroll
-        for (int k4 = 0; k4 < kNH / 4; ++k4) {
-            const float4 ww = W3[j * (kNH / 4) + k4];
-            a = fmaf(ww.x, g[4 * k4 + 0], a);
-            a = fmaf(ww.y, g[4 * k4 + 1], a);
-            a = fmaf(ww.z, g[4 * k4 + 2], a);
-            a = fmaf(ww.w, g[4 * k4 + 3], a);
-        }
-        h[j] = a > 0.0f ? a : kLeak * a;
-    }
-    const float4* W4 = reinterpret_cast<const float4*>(w + kNH * kNF + 2 * kNH * kNH);
-    float z = 0.0f;
-#pragma unroll
-    for (int k4 = 0; k4 < kNH / 4; ++k4) {
-        const float4 ww = W4[k4];
-        z = fmaf(ww.x, h[4 * k4 + 0], z);
-        z = fmaf(ww.y, h[4 * k4 + 1], z);
-        z = fmaf(ww.z, h[4 * k4 + 2], z);
-        z = fmaf(ww.w, h[4 * k4 + 3], z);
-    }
-    return softplus_mod(z);
-}
-
-__device__ __forceinline__ void load_weights_smem(float* sw, const float* __restrict__ params) {
-    for (int i = threadIdx.x; i < kNParams / 4; i += blockDim.x)
-        reinterpret_cast<float4*>(sw)[i] = __ldg(reinterpret_cast<const float4*>(params) + i);
-    __syncthreads();
-}
-
 __device__ __forceinline__ float boxcox(float t, float lambda) {
     if (lambda == 0.5f) return 2.0f * (sqrtf(t) - 1.0f);
     if (lambda == 0.0f) return logf(t);
@@ -316,44 +245,6 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
     if ((threadIdx.x & 31) == 0 && nonfinite) {
         atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
         atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
-    }
-}
-
-// RRSNet (FP32 SIMT) on the slots k_shade marked with q = -1.
-__global__ void __launch_bounds__(256, 2)
-k_rrsnet_fp32(WorkView w, const float* __restrict__ params, int depth) {
-    __shared__ __align__(16) float sW[kNParams];
-    load_weights_smem(sW, params);
-    DevStats* st = w.st;
-    const long long n = st->live[depth - 1];
-    unsigned int evals = 0, nonfinite = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (w.q[i] < 0.0f) {
-            const float4* f = w.feat + 4 * i;
-            float x[kNF];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float4 v = __ldg(f + k);
-                x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
-            }
-            float q = rrsnet_forward(sW, x);
-            ++evals;
-            if (!(q >= 0.0f && q <= FLT_MAX)) {
-                q = 0.0f;
-                ++nonfinite;
-            }
-            w.q[i] = q;
-        }
-    }
-    evals = warp_sum(evals);
-    nonfinite = warp_sum(nonfinite);
-    if ((threadIdx.x & 31) == 0) {
-        if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
-        if (nonfinite) {
-            atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
-            atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
-        }
     }
 }
 
@@ -609,24 +500,6 @@ __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
 }
 
 // ------------------------------------------------------------------ plain-array entry points
-__global__ void __launch_bounds__(256, 2) k_query(const float* __restrict__ params,
-                                               const float* __restrict__ feat, long long n,
-                                               float* __restrict__ q) {
-    __shared__ __align__(16) float sW[kNParams];
-    load_weights_smem(sW, params);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float4* f = reinterpret_cast<const float4*>(feat + i * kNF);
-        float x[kNF];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4 v = __ldg(f + k);
-            x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
-        }
-        q[i] = rrsnet_forward(sW, x);
-    }
-}
-
 __global__ void k_sum_part(const float* __restrict__ q, long long n, double* part) {
     __shared__ double sh[32];
     double s = 0.0;
@@ -723,12 +596,6 @@ k_split_arr_scatter(SplitArrays a, const unsigned long long* boff) {
 // ------------------------------------------------------------------ launchers
 int split_block_threads() { return kSplitThreads; }
 
-int max_blocks_rrsnet() {
-    int nb = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rrsnet_fp32, 256, 0);
-    return nb < 1 ? 1 : nb;
-}
-
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0, long long P,
                         DevStats* st, cudaStream_t s) {
     k_ref_prepare<<<1, kReduceThreads, 0, s>>>(ref, n3, eps_rel, alpha0, P, st);
@@ -749,10 +616,6 @@ void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& 
         case kFactorHeur: k_shade<kFactorHeur><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
         default: k_shade<kFactorNet><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
     }
-}
-
-void launch_rrsnet_depth(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
-    k_rrsnet_fp32<<<w.grid_red, 256, 0, s>>>(w, rp.params, depth);
 }
 
 void launch_sum_q(const WorkView& w, int depth, cudaStream_t s) {
@@ -796,18 +659,6 @@ void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_
     k_frame_consts<<<1, 1, 0, s>>>(fc, key0, key1, ref_count);
 }
 
-void launch_query_factors(const float* params, const float* feat, long long n, float* q,
-                          cudaStream_t s) {
-    if (n <= 0) return;
-    int dev = 0, nsm = 148, nb = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_query, 256, 0);
-    long long need = (n + 255) / 256;
-    long long G = (long long)nsm * (nb < 1 ? 1 : nb);
-    if (G > need) G = need;
-    k_query<<<(unsigned)G, 256, 0, s>>>(params, feat, n, q);
-}
 
 void launch_normalize_array(const float* q, long long n, double budget, double f_rate,
                             double alpha, double* part, int grid, float* F, double* sum,

@@ -90,7 +90,6 @@ enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFact
 int extend_block_threads();
 int split_block_threads();
 int max_blocks_trace();  // resident blocks per SM
-int max_blocks_rrsnet();
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
                         long long P, DevStats* st, cudaStream_t s);
@@ -99,7 +98,6 @@ void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int dep
                   cudaStream_t s);
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s);
-void launch_rrsnet_depth(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
 void launch_sum_q(const WorkView& w, int depth, cudaStream_t s);
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
                             cudaStream_t s);
@@ -113,16 +111,34 @@ void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, floa
 void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count,
                          cudaStream_t s);
 
-// RRSNet on the tensor cores (rrsnet_tc.cu): precision 16 = split BF16 operands,
-// 8 = E4M3 operands with per-tensor scales; FP32 accumulation.
-void launch_rrsnet_tc_query(int precision, const float* params, const float* feat, long long n,
-                            float* q, unsigned int* status, cudaStream_t s);
-void launch_rrsnet_tc_depth(int precision, const WorkView& w, const RenderParams& rp, int depth,
-                            int grid, cudaStream_t s);
+// RRSNet forward over n feature rows (n_ptr: device count, else n_host); with `sentinel`
+// only rows whose q is negative are evaluated; st / status are nullable.
+// rrsnet_simt.cu: FP32 on the CUDA cores, `rows` (1 or 2) rows per thread.
+void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* feat,
+                        const long long* n_ptr, long long n_host, float* q, int sentinel,
+                        DevStats* st, cudaStream_t s);
+// rrsnet_tc.cu: tensor cores; precision 16 = split BF16 operands, 8 = E4M3 operands with
+// per-tensor scales; FP32 accumulation.
+void launch_rrsnet_tc(int precision, int grid, const float* params, const float4* feat,
+                      const long long* n_ptr, long long n_host, float* q, int sentinel,
+                      DevStats* st, unsigned int* status, cudaStream_t s);
+
+// Launch shape of the RRSNet kernel for one queue size: the autotuner's unit (tune.cu).
+struct RrsnetChoice {
+    int variant;        // FP32: rows per thread (1 or 2); tensor cores: 0
+    int blocks_per_sm;  // grid = SMs x blocks_per_sm (extra blocks exit at once)
+};
+constexpr int kTuneBuckets = 17;  // bucket b: floor(log2 n) = b + 8, clamped to [0, 16]
+int tune_bucket(long long n);
+RrsnetChoice default_choice(int precision);
+void launch_rrsnet(int precision, RrsnetChoice c, int n_sm, const float* params,
+                   const float4* feat, const long long* n_ptr, long long n_host, float* q,
+                   int sentinel, DevStats* st, unsigned int* status, cudaStream_t s);
+cudaError_t tune_rrsnet(int precision, int n_sm, const float* params, long long max_rows,
+                        cudaStream_t s, RrsnetChoice* table, long long* rows, float* ms_best,
+                        float* ms_default);
 
 // Stand-alone entry points on plain arrays.
-void launch_query_factors(const float* params, const float* feat, long long n, float* q,
-                          cudaStream_t s);
 void launch_normalize_array(const float* q, long long n, double budget, double f_rate,
                             double alpha, double* part, int grid, float* F, double* sum,
                             cudaStream_t s);

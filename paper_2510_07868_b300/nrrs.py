@@ -37,7 +37,8 @@ EXPORTED = [
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
-    "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward",
+    "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
+    "nrrs_set_rrsnet_shape",
 ]
 
 
@@ -108,6 +109,22 @@ class TrainOpts(C.Structure):
         return o
 
 
+TUNE_BUCKETS = 17
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_buckets", C.c_int32),
+                ("rows", C.c_int64 * TUNE_BUCKETS), ("variant", C.c_int32 * TUNE_BUCKETS),
+                ("blocks_per_sm", C.c_int32 * TUNE_BUCKETS),
+                ("ms_best", C.c_float * TUNE_BUCKETS), ("ms_default", C.c_float * TUNE_BUCKETS)]
+
+    def as_dict(self):
+        n = self.n_buckets
+        return {"precision": self.precision, "rows": list(self.rows[:n]),
+                "variant": list(self.variant[:n]), "blocks_per_sm": list(self.blocks_per_sm[:n]),
+                "ms_best": list(self.ms_best[:n]), "ms_default": list(self.ms_default[:n])}
+
+
 class TrainStats(C.Structure):
     _fields_ = [("step", C.c_int64), ("samples", C.c_int64), ("segments", C.c_int64),
                 ("loss_statnet", C.c_double), ("loss_rrsnet", C.c_double),
@@ -163,6 +180,8 @@ def _load():
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
         "nrrs_rrsnet_forward": ([P, P, I64, P, P], I32),
         "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
+        "nrrs_tune_rrsnet": ([P, I32, P, P], I32),
+        "nrrs_set_rrsnet_shape": ([P, I32, I32, I32, I32], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -314,6 +333,16 @@ def nrrs_mlp_grad(scene, n_out, d_params, d_x, d_gout, n, d_grad, stream=None):
                               _ptr(d_grad), _stream(stream)))
 
 
+def nrrs_tune_rrsnet(scene, precision, stream=None):
+    rep = TuneReport()
+    _check(_lib.nrrs_tune_rrsnet(scene, precision, _stream(stream), C.byref(rep)))
+    return rep.as_dict()
+
+
+def nrrs_set_rrsnet_shape(scene, precision, bucket, variant, blocks_per_sm):
+    _check(_lib.nrrs_set_rrsnet_shape(scene, precision, bucket, variant, blocks_per_sm))
+
+
 def nrrs_rrsnet_forward(d_params, d_x, n, d_q, stream=None):
     _check(_lib.nrrs_rrsnet_forward(_ptr(d_params), _ptr(d_x), n, _ptr(d_q), _stream(stream)))
 
@@ -435,6 +464,9 @@ class Scene:
         o = RenderOpts.defaults(**opts)
         st = nrrs_render(self.handle, width, height, spp, max_depth, mode, o, out, stream, stats)
         return out, st
+
+    def tune(self, precision=32, stream=None):
+        return nrrs_tune_rrsnet(self.handle, precision, stream)
 
     def train_step(self, stream=None, **opts):
         return nrrs_train_step(self.handle, TrainOpts.defaults(**opts), stream)

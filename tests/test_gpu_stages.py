@@ -300,3 +300,56 @@ def test_render_bf16_precision_runs(nrrs):
     assert st8["live"][0] == st32["live"][0]
     assert abs(st8["live"][1] - st32["live"][1]) <= 0.05 * st32["live"][1]
     sc.close()
+
+
+@pytest.mark.parametrize("precision", [32, 16, 8])
+def test_rrsnet_launch_shapes_give_identical_factors(nrrs, precision):
+    """Every launch shape the autotuner may pick (rows per thread, blocks per SM) gives
+    bit-identical factors, for queue sizes across several buckets and ragged tails."""
+    from paper_2510_07868_b300.nrrs import Scene
+
+    sc = Scene(I.box_scene(1))
+    sc.set_params(I.rrsnet_init_params(7))
+    shapes = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2)] if precision == 32 else \
+        [(0, 1), (0, 2), (0, 4), (0, 6), (0, 8)]
+    for n in (1, 300, 5000, 100_003, (1 << 21) + 7):
+        X = _dev(I.random_features(n, seed=n))
+        ref = None
+        for v, b in shapes:
+            nrrs.nrrs_set_rrsnet_shape(sc.handle, precision, -1, v, b)
+            q = sc.query(X, precision=precision).cpu().numpy()
+            if ref is None:
+                ref = q
+            np.testing.assert_array_equal(q, ref)
+    sc.close()
+
+
+@pytest.mark.parametrize("precision", [32, 16])
+def test_tuner_table_and_render_invariance(nrrs, precision):
+    """The tuner fills one shape per bucket (timed on 1.5 x 2^(b+8) rows), never slower
+    than the default shape it also timed; renders before and after tuning are
+    bit-identical (the per-depth shape follows the last frame's queue sizes)."""
+    from paper_2510_07868_b300.nrrs import Scene
+
+    s = I.box_scene(2)
+    P = I.rrsnet_init_params(5)
+    a, b = Scene(s), Scene(s)
+    a.set_params(P)
+    b.set_params(P)
+    rep = a.tune(precision)
+    assert rep["rows"] == [min(12582912, 3 << (k + 7)) for k in range(17)]
+    assert all(x <= y for x, y in zip(rep["ms_best"], rep["ms_default"]))
+    ok = {1, 2} if precision == 32 else {0}
+    assert set(rep["variant"]) <= ok and min(rep["blocks_per_sm"]) >= 1
+    for frame in range(3):
+        for graph in (0, 1):
+            ia, sa = a.render(96, 64, 8, 8, nrrs.RRS_NET, precision=precision, frame=frame,
+                              graph=graph)
+            ib, sb = b.render(96, 64, 8, 8, nrrs.RRS_NET, precision=precision, frame=frame,
+                              graph=graph)
+            torch.cuda.synchronize()
+            assert torch.equal(ia, ib)
+            np.testing.assert_array_equal(sa["live"], sb["live"])
+            assert sa["net_evals"] == sb["net_evals"]
+    a.close()
+    b.close()
