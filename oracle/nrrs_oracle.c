@@ -448,9 +448,13 @@ typedef struct {
     uint64_t gate;          /* NET_MIX: 2 bits per depth (0 NET, 1 HEUR, 2 FIXED) */
     const double* params;   /* RRSNet weights (NET / NET_MIX) */
     const double* pixel_ref;/* previous estimate [H*W*3] or NULL */
-    const int32_t* pixels;  /* optional ascending pixel subset (NONE / PLAIN_RR only) */
+    const int32_t* pixels;  /* optional ascending pixel subset; normalised modes need
+                               forced_F, since Sigma q spans the whole frame */
     int64_t n_pixels;
     double* rec;            /* optional per-vertex record [D][cap][OR_REC], see or_render */
+    const float* forced_F;  /* optional [D]: the normalisation factor of every depth, taken
+                               from a whole-frame render in place of Eq. F_norm over the
+                               subset (test hook for sampled pixels of a full frame) */
 } or_render_args;
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
@@ -501,13 +505,18 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     const int64_t npix = (int64_t)W * H;
     const int64_t P = (a->pixels ? a->n_pixels : npix) * spp;
     const int64_t cap = a->cap > 0 ? a->cap : 2 * (int64_t)W * H * spp;
-    if (a->pixels && or_is_normalized(a->mode)) return OR_ERR_ARG;
+    if (a->pixels && or_is_normalized(a->mode) && !a->forced_F) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
-    or_path* cur = (or_path*)calloc((size_t)cap, sizeof(or_path));
-    or_path* nxt = (or_path*)calloc((size_t)cap, sizeof(or_path));
-    or_hitrec* vx = (or_hitrec*)calloc((size_t)cap, sizeof(or_hitrec));
+    /* queue storage: the capacity, or for a pixel subset 64 slots per primary path
+     * (a subset's queue cannot be capped the way the whole frame's is; running out of
+     * that room is reported as OR_ERR_OOM rather than dropping children) */
+    int64_t room = cap;
+    if (a->pixels && 64 * P < room) room = 64 * P;
+    or_path* cur = (or_path*)calloc((size_t)room, sizeof(or_path));
+    or_path* nxt = (or_path*)calloc((size_t)room, sizeof(or_path));
+    or_hitrec* vx = (or_hitrec*)calloc((size_t)room, sizeof(or_hitrec));
     double* acc = (double*)calloc((size_t)npix * 3, sizeof(double));
-    double* qbuf = (double*)calloc((size_t)cap, sizeof(double));
+    double* qbuf = (double*)calloc((size_t)room, sizeof(double));
     if (!cur || !nxt || !vx || !acc || !qbuf) {
         free(cur); free(nxt); free(vx); free(acc); free(qbuf);
         return OR_ERR_OOM;
@@ -635,7 +644,10 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
         }
         float F32 = 1.0f;
         st->alpha[depth] = alpha;
-        if (or_is_normalized(a->mode)) {
+        if (or_is_normalized(a->mode) && a->forced_F) {
+            for (int64_t i = 0; i < n; ++i) st->sum_q[depth] += qbuf[i];
+            F32 = a->forced_F[depth - 1];
+        } else if (or_is_normalized(a->mode)) {
             double sum;
             double F = or_normalize(qbuf, n, (double)cap, a->f_rate, alpha, &sum);
             st->sum_q[depth] = sum;
@@ -671,6 +683,10 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             for (uint32_t j = 0; j < X; ++j) {
                 int64_t slot = S + j;
                 if (slot >= cap) { ++drop; continue; }
+                if (slot >= room) {
+                    free(cur); free(nxt); free(vx); free(acc); free(qbuf);
+                    return OR_ERR_OOM;
+                }
                 or_path* c = &nxt[slot];
                 c->pixel = p->pixel;
                 c->sample = p->sample;

@@ -265,6 +265,48 @@ def icosphere_room(seed: int = 1, min_triangles: int = 200_000, subdiv: int = 3)
                  "icosphere_room")
 
 
+def three_rooms(seed: int = 1, n_random: int = 1_000_000, tri_size: float = 0.01,
+                n_palette: int = 64) -> Scene:
+    """Three unit rooms along x ([0,3] x [0,1] x [0,1]) joined by doorways 0.1 wide
+    (z in [0.45, 0.55]) and 0.2 high (y in [0, 0.2]) in the walls at x = 1 and x = 2.
+
+    One 0.1 x 0.1 emitter of radiance 200 under the ceiling of room 3 (centre x = 2.5,
+    z = 0.5), the camera in room 1 at (0.05, 0.1, 0.5) looking +x, through both doorways.  ``n_random``
+    two-sided triangles (centre uniform in the rooms, vertices centre +
+    U[-s/2, s/2]^3) draw their material from a palette of ``n_palette``: 60% GGX plastic
+    (roughness U[0.05, 0.5], F0 0.04), the rest Lambertian; albedo U[0.1, 0.9].
+    """
+    rng = np.random.default_rng(seed)
+    tris = _box_walls((0.0, 0.0, 0.0), (3.0, 1.0, 1.0))
+    mats = [_material(albedo=0.7, two_sided=0), _material(albedo=0.0, Le=200.0, two_sided=0),
+            _material(albedo=0.7, two_sided=1)]
+    mat_id = [0] * 12
+    P = lambda x, y, z: np.array([x, y, z], dtype=np.float64)  # noqa: E731
+    for x in (1.0, 2.0):  # inner walls minus the doorway
+        for (z0, z1, y0, y1) in ((0.0, 0.45, 0.0, 1.0), (0.55, 1.0, 0.0, 1.0),
+                                 (0.45, 0.55, 0.2, 1.0)):
+            tris += _quad(P(x, y0, z0), P(x, y0, z1), P(x, y1, z1), P(x, y1, z0))
+            mat_id += [2, 2]
+    tris += _ceiling_emitter(2.5, 0.5, 0.1)
+    mat_id += [1, 1]
+    first = len(mats)
+    n_ggx = int(round(0.6 * n_palette))
+    for k in range(n_palette):
+        if k < n_ggx:
+            mats.append(_material(MAT_GGX, albedo=rng.uniform(0.1, 0.9),
+                                  roughness=rng.uniform(0.05, 0.5), F0=0.04, two_sided=1))
+        else:
+            mats.append(_material(albedo=rng.uniform(0.1, 0.9), two_sided=1))
+    h = tri_size / 2
+    c = rng.uniform(0.0, 1.0, (n_random, 3)) * np.array([3.0, 1.0, 1.0])
+    v = c[:, None, :] + rng.uniform(-h, h, (n_random, 3, 3))
+    tri = np.concatenate([np.array(tris).reshape(-1, 9), v.reshape(n_random, 9)])
+    mat_id = np.concatenate([np.array(mat_id, dtype=np.int32),
+                             first + rng.integers(0, n_palette, n_random).astype(np.int32)])
+    return Scene(tri, mat_id, np.array(mats), _camera((0.05, 0.1, 0.5), look=(1.0, 0.0, 0.0)),
+                 "three_rooms")
+
+
 def rrsnet_init_params(seed: int = 1, dtype=np.float32) -> np.ndarray:
     """Xavier-uniform draw of the 2592 RRSNet weights, packed W1|W2|W3|W4, row-major.
 

@@ -1,0 +1,137 @@
+"""Full-size parity cases beyond the bench workload (GPU): the RRSNet precision sweep on
+the 200k-triangle icosphere room (1024 x 1024 px, 64 spp, depth 24) and the Mix-Depth
+frame sequence on the 1M-triangle three-room scene (1920 x 1080 px, 8 frames of 16 spp,
+depth 32, tuned RRSNet shapes, graph-captured bounce loop).
+
+The oracle cannot render these frames whole, so it renders sampled pixels one by one:
+with normalisation, pixels interact only through each depth's factor F, which the oracle
+takes from the GPU frame's stats (its own F is checked at small sizes elsewhere)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_07868_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nrrs():
+    from paper_2510_07868_b300 import nrrs as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def _relmse(a, b):
+    """Sec. 5's relMSE of image a against reference b (mean over pixels and channels)."""
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
+    return float(np.mean((a - b) ** 2 / (b * b + 0.01)))
+
+
+def _frame_properties(st, C, D):
+    live = st["live"][:D]
+    assert st["capacity"] == C and np.all(live <= C)
+    for d in range(D - 1):
+        assert live[d + 1] == min(st["requested"][d], C)
+    assert np.all((st["F"][:D] > 0) & (st["F"][:D] <= 1)) and st["nonfinite"] == 0
+
+
+def _sampled_pixel_match(s, W, H, spp, D, mode, P, img, st, pix, **kw):
+    """Fraction of sampled pixels whose GPU value matches the oracle's (the GPU frame's
+    per-depth F forced) within 1e-4 relative, and the per-pixel relative errors."""
+    oimg, _, _ = oracle.render(s, W, H, spp, D, mode, params=P.astype(np.float64), pixels=pix,
+                               forced_F=st["F"][:D], **kw)
+    g = img.reshape(-1, 3)[pix].astype(np.float64)
+    o = oimg.reshape(-1, 3)[pix]
+    rel = np.max(np.abs(g - o) / np.maximum(np.abs(o), 1e-30), axis=1)
+    rel[np.all(o == 0, axis=1) & np.all(g == 0, axis=1)] = 0.0
+    return float(np.mean(rel <= 1e-4)), rel
+
+
+def test_precision_sweep_icosphere_room_full_size(nrrs):
+    s = I.icosphere_room(1)
+    assert s.n_tri >= 200_000
+    W = H = 1024
+    spp, D = 64, 24
+    C = 2 * W * H * spp
+    P = I.rrsnet_init_params(1)
+    sc = nrrs.Scene(s)
+    sc.set_params(P)
+    imgs, stats = {}, {}
+    for prec in (32, 16, 8):
+        img, st = sc.render(W, H, spp, D, nrrs.RRS_NET, precision=prec, frame=0, update_ref=0)
+        torch.cuda.synchronize()
+        _frame_properties(st, C, D)
+        imgs[prec] = img.cpu().numpy()
+        stats[prec] = st
+        assert np.isfinite(imgs[prec]).all() and imgs[prec].min() >= 0
+    # noise floor: the FP32 frame against an independent FP32 frame (other random numbers)
+    other, _ = sc.render(W, H, spp, D, nrrs.RRS_NET, precision=32, frame=1, update_ref=0)
+    floor = _relmse(other.cpu().numpy(), imgs[32])
+    r16 = _relmse(imgs[16], imgs[32])
+    r8 = _relmse(imgs[8], imgs[32])
+    # split BF16 factors are within 1e-4 of FP32: a few decisions flip, far below the floor
+    assert r16 <= 0.05 * floor, (r16, floor)
+    # E4M3 factors move ~1 %: more flips, still no more than an independent frame
+    assert r8 <= floor, (r8, floor)
+    # FP64 oracle on sampled pixels of the FP32 frame
+    rng = np.random.default_rng(3)
+    pix = np.sort(rng.choice(W * H, 12, replace=False)).astype(np.int32)
+    frac, rel = _sampled_pixel_match(s, W, H, spp, D, oracle.MODE_NET, P, imgs[32], stats[32], pix)
+    print(f"precision sweep: relMSE vs FP32 bf16 {r16:.3e} e4m3 {r8:.3e} floor {floor:.3e}; "
+          f"oracle match {frac:.3f} rel {np.array2string(rel, precision=2)}")
+    assert frac >= 0.75, (frac, rel)
+    sc.close()
+
+
+def test_mix_depth_three_rooms_full_size(nrrs):
+    s = I.three_rooms(1)
+    assert s.n_tri >= 1_000_000
+    W, H = 1920, 1080
+    spp, D, frames = 16, 32, 8
+    C = 2 * W * H * spp
+    P = I.rrsnet_init_params(2)
+    gate = 0
+    for d in range(D):  # FIXED, FIXED, then NET through depth 8, HEUR beyond
+        g = nrrs.GATE_FIXED if d < 2 else nrrs.GATE_NET if d < 8 else nrrs.GATE_HEUR
+        gate |= g << (2 * d)
+    sc = nrrs.Scene(s)
+    sc.set_params(P)
+    sc.tune(32)
+    acc = None
+    lit_per_frame = []
+    for f in range(frames):
+        img, st = sc.render(W, H, spp, D, nrrs.RRS_NET_MIX, gate=gate, frame=f, graph=1)
+        torch.cuda.synchronize()
+        _frame_properties(st, C, D)
+        assert st["net_evals"] > 0
+        a = img.cpu().numpy().astype(np.float64)
+        lit_per_frame.append(int(np.count_nonzero(a.max(axis=2))))
+        acc = a if acc is None else acc + a
+    final = acc / frames
+    assert np.isfinite(final).all() and final.min() >= 0 and final.max() > 0
+    # one more frame against an explicit reference (the mean of the 8 frames) that the
+    # oracle is handed too: its HEUR depths then see the same I_px on both sides
+    ref = final.astype(np.float32)
+    img, st = sc.render(W, H, spp, D, nrrs.RRS_NET_MIX, gate=gate, frame=frames, graph=1,
+                        d_pixel_ref=torch.from_numpy(ref).cuda().data_ptr(), update_ref=0)
+    torch.cuda.synchronize()
+    _frame_properties(st, C, D)
+    img = img.cpu().numpy()
+    lum = img.reshape(-1, 3).max(axis=1)
+    lit = np.flatnonzero(lum > 0)
+    dark = np.flatnonzero(lum == 0)
+    print(f"mix-depth: lit pixels per frame {lit_per_frame}, checked frame {lit.size}")
+    assert lit.size >= 8  # light from room 3 reaches the camera
+    rng = np.random.default_rng(5)
+    pix = np.sort(np.concatenate([rng.choice(lit, 8, replace=False),
+                                  rng.choice(dark, 4, replace=False)])).astype(np.int32)
+    frac, rel = _sampled_pixel_match(s, W, H, spp, D, oracle.MODE_NET_MIX, P, img, st, pix,
+                                     gate=gate, pixel_ref=ref.astype(np.float64), frame=frames)
+    print(f"mix-depth: oracle match {frac:.3f} rel {np.array2string(rel, precision=2)}")
+    assert frac >= 0.7, (frac, rel)
+    sc.close()

@@ -450,3 +450,19 @@ def test_nonfinite_factors_terminate():
     P[2560:] = np.inf
     img, st, _ = oracle.render(s, 8, 8, 1, 4, oracle.MODE_NET, params=P)
     assert st["nonfinite"] == 64 and st["live"][0] == 64 and st["live"][1:].sum() == 0
+
+
+def test_forced_F_subset_equals_whole_frame():
+    """The sampled-pixel hook: a pixel subset rendered with the whole frame's per-depth
+    normalisation factors reproduces those pixels of the whole-frame render exactly
+    (pixels interact only through F; the random numbers are keyed per path)."""
+    s = I.box_scene(2)
+    P = (I.rrsnet_init_params(3) * 3.0).astype(np.float64)
+    img, st, _ = oracle.render(s, 24, 16, 2, 6, oracle.MODE_NET, params=P)
+    assert np.any(st["F"] < 1.0)
+    pix = np.array([0, 5, 77, 200, 383], dtype=np.int32)
+    sub, _, _ = oracle.render(s, 24, 16, 2, 6, oracle.MODE_NET, params=P, pixels=pix,
+                              forced_F=st["F"])
+    np.testing.assert_array_equal(sub.reshape(-1, 3)[pix], img.reshape(-1, 3)[pix])
+    with pytest.raises(RuntimeError):
+        oracle.render(s, 24, 16, 2, 6, oracle.MODE_NET, params=P, pixels=pix)
