@@ -182,6 +182,52 @@ NRRS_API nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const in
                               const nrrs_material* mats, int32_t n_mat, const nrrs_camera* cam,
                               int32_t device, nrrs_scene** out);
 
+/* ---------------------------------------------------------------- batched renders
+ * Many independent render jobs, each with its own scene, camera, image size, spp and
+ * depth, traced together: every kernel of a bounce processes all jobs' paths at once and
+ * all jobs share one RRSNet (the batch's weights, nrrs_set_rrsnet_params).  Eq. F_norm is
+ * applied per job (the sum of q and the budget C_j = cap_factor * W_j * H_j * spp_j of
+ * each job); the queue capacity sum_j C_j is enforced on the shared queue.  A job's
+ * paths draw the random numbers a render of that job alone would draw (Philox counters
+ * use the job-local pixel), so a job's image equals its own nrrs_render output up to
+ * last-bit differences of the per-job FP64 sum of q.  No counterpart in the paper, which
+ * renders one scene at a time. */
+#define NRRS_MAX_JOBS 256
+typedef struct nrrs_job {
+    const float* tri;            /* host [n_tri][9], as nrrs_create_scene               */
+    int32_t n_tri;
+    const int32_t* tri_mat;      /* host [n_tri]                                        */
+    const nrrs_material* mats;   /* host [n_mat]                                        */
+    int32_t n_mat;
+    const nrrs_camera* cam;      /* host                                                */
+    int32_t width, height, spp, max_depth;
+} nrrs_job;
+
+/* Builds a batch scene: one BVH per job, merged into shared arrays with one root per
+ * job.  Jobs are laid out in order: job j's pixels start at pixel_base_j = sum of the
+ * earlier jobs' W * H (see nrrs_batch_info).  The result is an nrrs_scene: weights,
+ * tuning and destruction use the scene entry points; nrrs_render, nrrs_train_step and
+ * nrrs_mixdepth_search refuse it.  Errors: INVALID_ARG (NULL or empty job, bad sizes,
+ * more than NRRS_MAX_JOBS jobs, 2^31 or more pixels or paths); OOM; CUDA. */
+NRRS_API nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t device,
+                                       nrrs_scene** out);
+
+/* One frame of every job (Sec. 3.1 per job, as nrrs_render).  d_rgb: device float
+ * [sum_j H_j W_j][3], job j's image at pixel_base_j.  stats (nullable): totals over the
+ * batch (F is 0: factors are per job).  job_live, job_F, job_sum_q (nullable, host,
+ * [n_jobs][NRRS_MAX_DEPTH]): per job and depth the queue length, the factor F_j and the
+ * sum of q.  Options as nrrs_render except d_trace and d_suffix (UNSUPPORTED).
+ * Errors: INVALID_ARG (not a batch, bad options); UNSUPPORTED; OOM; CUDA. */
+NRRS_API nrrs_status nrrs_render_batch(nrrs_scene* batch, int32_t rrs_mode,
+                                       const nrrs_render_opts* opts, float* d_rgb, void* stream,
+                                       nrrs_render_stats* stats, int64_t* job_live, float* job_F,
+                                       double* job_sum_q);
+
+/* Number of jobs (0 for a single scene), each job's first pixel ([n_jobs], nullable) and
+ * the total pixel count (nullable). */
+NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
+                                     int64_t* pixel_base, int64_t* n_pixels_total);
+
 /* Free every device buffer of the scene (synchronizes the device). NULL is a no-op. */
 NRRS_API nrrs_status nrrs_destroy_scene(nrrs_scene* scene);
 

@@ -197,6 +197,17 @@ struct nrrs_scene {
     TrainState train;
     // graph-captured renders: capture stream and executable graphs per launch shape
     cudaStream_t capture_stream = nullptr;
+    // batched render (nrrs_create_batch): the job table and its per-job work arrays
+    int n_jobs = 0;
+    std::vector<JobDev> jobs_host;
+    JobDev* jobs_dev = nullptr;
+    long long batch_P = 0, batch_npix = 0;
+    int batch_D = 0;
+    JobWork jw{};
+    int jw_grid = 0;
+    std::vector<float> job_F;        // last batched render with stats, [D][n_jobs]
+    std::vector<double> job_sum_q;
+    std::vector<long long> job_live;
     struct GraphEntry {
         uint64_t shape;             // launch shape: kernels and their order
         uint64_t args;              // every launch argument except the per-frame constants
@@ -249,6 +260,9 @@ void destroy(nrrs_scene* s) {
     if (!s) return;
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
     for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+    cudaFree(s->jobs_dev);
+    cudaFree(s->jw.F_cur); cudaFree(s->jw.eps_I); cudaFree(s->jw.part); cudaFree(s->jw.cnt);
+    cudaFree(s->jw.F); cudaFree(s->jw.sum_q); cudaFree(s->jw.live);
     if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     s->train.release_all();
     s->ws.release();
@@ -335,6 +349,67 @@ int factor_kind(int mode, uint64_t gate, int depth) {
 
 }  // namespace
 
+namespace {
+
+// Camera basis in FP64, rounded once (nrrs_camera).
+CamView cam_view(const nrrs_camera& cam) {
+    CamView c{};
+    V3d fw = vnorm({cam.look[0], cam.look[1], cam.look[2]});
+    V3d up = {cam.up[0], cam.up[1], cam.up[2]};
+    V3d right = vnorm(vcross(up, fw));
+    V3d up2 = vcross(fw, right);
+    for (int k = 0; k < 3; ++k) c.pos[k] = cam.pos[k];
+    c.fw[0] = (float)fw.x; c.fw[1] = (float)fw.y; c.fw[2] = (float)fw.z;
+    c.right[0] = (float)right.x; c.right[1] = (float)right.y; c.right[2] = (float)right.z;
+    c.up[0] = (float)up2.x; c.up[1] = (float)up2.y; c.up[2] = (float)up2.z;
+    c.tan_half = (float)std::tan(0.5 * (double)cam.vfov_deg * M_PI / 180.0);
+    c.aspect = 1.0f;
+    return c;
+}
+
+// Uploads a built BVH (and its triangle references), the materials and the camera
+// (NULL for a batch, whose cameras live in the job table) into a new scene.
+nrrs_status upload_scene(const BvhHost& bvh, int64_t n_tri, const nrrs_material* mats,
+                         int32_t n_mat, const nrrs_camera* cam, int device, nrrs_scene** out) {
+    nrrs_scene* s = new nrrs_scene();
+    s->device = device;
+    s->n_sm = sm_count(device);
+    s->n_nodes = (int64_t)bvh.nodes.size();
+    s->n_tri = n_tri;
+    auto bail = [&](cudaError_t e, const char* what) {
+        nrrs_status st = cuda_fail(e, what);
+        destroy(s);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = dalloc(&s->nodes, bvh.nodes.size() * 4)) != cudaSuccess) return bail(e, "alloc nodes");
+    if ((e = dalloc(&s->tris, (size_t)bvh.n_ref * 3)) != cudaSuccess) return bail(e, "alloc tris");
+    if ((e = dalloc(&s->mats, n_mat)) != cudaSuccess) return bail(e, "alloc mats");
+    if ((e = dalloc(&s->params, kNParams)) != cudaSuccess) return bail(e, "alloc params");
+    if ((e = cudaMemcpy(s->nodes, bvh.nodes.data(), bvh.nodes.size() * 64, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "copy nodes");
+    if ((e = cudaMemcpy(s->tris, bvh.tris.data(), (size_t)bvh.n_ref * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "copy tris");
+    if ((e = cudaMemcpy(s->mats, mats, sizeof(nrrs_material) * n_mat, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "copy mats");
+    if ((e = cudaMemset(s->params, 0, kNParams * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
+
+    s->view.nodes = s->nodes;
+    s->view.tris = s->tris;
+    s->view.mats = s->mats;
+    for (int k = 0; k < 3; ++k) {
+        s->view.lo[k] = bvh.lo[k];
+        const float ext = bvh.hi[k] - bvh.lo[k];
+        s->view.inv_ext[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
+    }
+    if (cam) s->cam = cam_view(*cam);
+    s->grid_trace = s->n_sm * max_blocks_trace();
+    s->grid_sum = s->n_sm * 4;
+    *out = s;
+    return NRRS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* nrrs_status_string(nrrs_status s) {
@@ -372,52 +447,7 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
 
     BvhHost bvh;
     build_bvh(tri, n_tri, tri_mat, &bvh);
-
-    nrrs_scene* s = new nrrs_scene();
-    s->device = device;
-    s->n_sm = sm_count(device);
-    s->n_nodes = (int64_t)bvh.nodes.size();
-    s->n_tri = n_tri;
-    auto bail = [&](cudaError_t e, const char* what) {
-        nrrs_status st = cuda_fail(e, what);
-        destroy(s);
-        return st;
-    };
-    cudaError_t e;
-    if ((e = dalloc(&s->nodes, bvh.nodes.size() * 4)) != cudaSuccess) return bail(e, "alloc nodes");
-    if ((e = dalloc(&s->tris, (size_t)bvh.n_ref * 3)) != cudaSuccess) return bail(e, "alloc tris");
-    if ((e = dalloc(&s->mats, n_mat)) != cudaSuccess) return bail(e, "alloc mats");
-    if ((e = dalloc(&s->params, kNParams)) != cudaSuccess) return bail(e, "alloc params");
-    if ((e = cudaMemcpy(s->nodes, bvh.nodes.data(), bvh.nodes.size() * 64, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "copy nodes");
-    if ((e = cudaMemcpy(s->tris, bvh.tris.data(), (size_t)bvh.n_ref * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "copy tris");
-    if ((e = cudaMemcpy(s->mats, mats, sizeof(nrrs_material) * n_mat, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "copy mats");
-    if ((e = cudaMemset(s->params, 0, kNParams * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
-
-    s->view.nodes = s->nodes;
-    s->view.tris = s->tris;
-    s->view.mats = s->mats;
-    for (int k = 0; k < 3; ++k) {
-        s->view.lo[k] = bvh.lo[k];
-        const float ext = bvh.hi[k] - bvh.lo[k];
-        s->view.inv_ext[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
-    }
-    // camera basis in FP64, rounded once
-    V3d fw = vnorm({cam->look[0], cam->look[1], cam->look[2]});
-    V3d up = {cam->up[0], cam->up[1], cam->up[2]};
-    V3d right = vnorm(vcross(up, fw));
-    V3d up2 = vcross(fw, right);
-    for (int k = 0; k < 3; ++k) s->cam.pos[k] = cam->pos[k];
-    s->cam.fw[0] = (float)fw.x; s->cam.fw[1] = (float)fw.y; s->cam.fw[2] = (float)fw.z;
-    s->cam.right[0] = (float)right.x; s->cam.right[1] = (float)right.y; s->cam.right[2] = (float)right.z;
-    s->cam.up[0] = (float)up2.x; s->cam.up[1] = (float)up2.y; s->cam.up[2] = (float)up2.z;
-    s->cam.tan_half = (float)std::tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0);
-    s->grid_trace = s->n_sm * max_blocks_trace();
-    s->grid_sum = s->n_sm * 4;
-    *out = s;
-    return NRRS_OK;
+    return upload_scene(bvh, n_tri, mats, n_mat, cam, device, out);
 }
 
 nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
@@ -577,8 +607,10 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                         int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts& o,
                         float* d_rgb, cudaStream_t s, nrrs_render_stats* stats,
                         const RecordView* rec, const float* params) {
-    const long long npix = (long long)width * height;
-    const long long P = npix * spp;
+    // a batched render takes its sizes from the job table (width = all pixels, height 1)
+    const bool batch = scene->n_jobs > 0;
+    const long long npix = batch ? scene->batch_npix : (long long)width * height;
+    const long long P = batch ? scene->batch_P : npix * spp;
     const long long C = P * o.cap_factor;
     bool uses_net = rrs_mode == NRRS_RRS_NET;
     if (rrs_mode == NRRS_RRS_NET_MIX)
@@ -587,6 +619,16 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     nrrs_status rc = ensure_workspace(scene, C, npix, uses_net);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
+    if (batch && scene->jw_grid < ws.grid_red) {  // per-block, per-job partials
+        const int n = scene->n_jobs;
+        cudaFree(scene->jw.part);
+        cudaFree(scene->jw.cnt);
+        scene->jw.part = nullptr;
+        scene->jw.cnt = nullptr;
+        CK(dalloc(&scene->jw.part, (size_t)ws.grid_red * n));
+        CK(dalloc(&scene->jw.cnt, (size_t)ws.grid_red * n));
+        scene->jw_grid = ws.grid_red;
+    }
 
     // reference image for HEUR factors
     bool uses_heur = rrs_mode == NRRS_RRS_HEUR_NORM;
@@ -614,8 +656,12 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     rp.ref = uses_heur ? ref : nullptr;
     rp.params = params ? params : scene->params;
     rp.trace = o.d_trace;
-
-    scene->cam.aspect = (float)width / (float)height;
+    if (batch) {
+        rp.jobs = scene->jw;
+        rp.jobs.cap_factor = o.cap_factor;
+    } else {
+        scene->cam.aspect = (float)width / (float)height;
+    }
     const int normalized = rrs_mode == NRRS_RRS_HEUR_NORM || rrs_mode == NRRS_RRS_NET ||
                            rrs_mode == NRRS_RRS_NET_MIX;
     const int update = o.update_ref && !o.d_pixel_ref;
@@ -651,9 +697,13 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     } while (0)
         TIMED(NRRS_STAGE_INIT,
               launch_ref_prepare(rp.ref, npix * 3, o.eps_rel, (double)o.alpha0, P, ws.st, s));
+        if (batch) TIMED(NRRS_STAGE_INIT, launch_ref_prepare_jobs(rp, o.eps_rel, s));
         QueueView q[2];
         for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
-        TIMED(NRRS_STAGE_INIT, launch_camera(scene->cam, rp, q[0], s));
+        if (batch)
+            TIMED(NRRS_STAGE_INIT, launch_camera_jobs(rp, P, q[0], s));
+        else
+            TIMED(NRRS_STAGE_INIT, launch_camera(scene->cam, rp, q[0], s));
         WorkView w{};
         w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.feat = ws.feat; w.part = ws.part;
         w.grid_red = ws.grid_red;
@@ -673,15 +723,21 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C,
                                    cudaMemcpyDeviceToDevice, s));
             }
-            TIMED(NRRS_STAGE_EXTEND, launch_trace(scene->view, q[cur], w, d, scene->grid_trace, s));
+            TIMED(NRRS_STAGE_EXTEND,
+                  launch_trace(scene->view, q[cur], w, d, scene->grid_trace, r.jobs, s));
             TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
             if (kind == kFactorNet) {
                 TIMED(NRRS_STAGE_RRSNET,
                       launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
                                     &w.st->live[d - 1], 0, w.q, 1, w.st, &w.st->status, s));
-                TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
+                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
             }
-            TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
+            if (batch) {  // Eq. F_norm per job
+                TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q_jobs(w, r, d, s));
+                TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_jobs(w, r, d, normalized, s));
+            } else {
+                TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
+            }
             const int do_split = d < max_depth;
             TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, r, d, do_split, s));
             if (do_split) {
@@ -693,7 +749,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 CK(cudaMemsetAsync(r.rec_X, 0, sizeof(uint32_t) * C, s));
             }
         }
-        TIMED(NRRS_STAGE_FINALIZE, launch_finalize(w, r, d_rgb, scene->ref_mean, update, s));
+        TIMED(NRRS_STAGE_FINALIZE,
+              launch_finalize(w, r, d_rgb, scene->ref_mean, update, npix, s));
         if (rec)
             for (int d = max_depth; d >= 1; --d)
                 TIMED(NRRS_STAGE_REVERSE,
@@ -725,7 +782,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)ws.feat, (uint64_t)ws.cap,
                                (uint64_t)(uintptr_t)(rec ? rec->q : nullptr),
                                (uint64_t)(rec ? rec->C : 0),
-                               (uint64_t)fbits(scene->cam.aspect)};
+                               (uint64_t)fbits(scene->cam.aspect),
+                               (uint64_t)(uintptr_t)scene->jw.part,
+                               (uint64_t)o.cap_factor};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -778,6 +837,18 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         tm.collect(stats);
         for (int d = 0; d < NRRS_MAX_DEPTH; ++d) scene->last_live[d] = d < max_depth ? h.live[d] : 0;
         scene->last_P = P;
+        if (batch) {
+            const size_t m = (size_t)max_depth * scene->n_jobs;
+            scene->job_F.resize(m);
+            scene->job_sum_q.resize(m);
+            scene->job_live.resize(m);
+            CK(cudaMemcpy(scene->job_F.data(), scene->jw.F, sizeof(float) * m,
+                          cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(scene->job_sum_q.data(), scene->jw.sum_q, sizeof(double) * m,
+                          cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(scene->job_live.data(), scene->jw.live, sizeof(long long) * m,
+                          cudaMemcpyDeviceToHost));
+        }
     }
     return NRRS_OK;
 }
@@ -790,6 +861,7 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
                         int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts* opts,
                         float* d_rgb, void* stream, nrrs_render_stats* stats) {
     if (!scene || !d_rgb) return fail(NRRS_ERR_INVALID_ARG, "scene or d_rgb is NULL");
+    if (scene->n_jobs > 0) return fail(NRRS_ERR_INVALID_ARG, "a batch renders with nrrs_render_batch");
     nrrs_render_opts o = opts ? *opts : render_defaults();
     nrrs_status rc = validate_render(scene, width, height, spp, max_depth, rrs_mode, o);
     if (rc != NRRS_OK) return rc;
@@ -812,6 +884,162 @@ nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_
         for (int d = 0; d < max_depth; ++d)
             CK(cudaMemcpyAsync(o.d_suffix + (size_t)d * C * 4, rec->S + (size_t)d * C,
                                sizeof(float4) * C, cudaMemcpyDeviceToDevice, s));
+    return NRRS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t device,
+                              nrrs_scene** out) {
+    if (!out) return fail(NRRS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n_jobs < 1 || n_jobs > NRRS_MAX_JOBS)
+        return fail(NRRS_ERR_INVALID_ARG, "need 1 .. NRRS_MAX_JOBS jobs");
+    long long npix = 0, P = 0;
+    int Dmax = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const nrrs_job& J = jobs[j];
+        if (!J.tri || !J.tri_mat || !J.mats || !J.cam || J.n_tri < 1 || J.n_mat < 1)
+            return fail(NRRS_ERR_INVALID_ARG, "NULL job array or empty job scene");
+        if (J.width < 1 || J.height < 1 || J.spp < 1 || J.max_depth < 1 ||
+            J.max_depth > NRRS_MAX_DEPTH)
+            return fail(NRRS_ERR_INVALID_ARG, "bad job image size, spp or depth");
+        for (int32_t i = 0; i < J.n_tri; ++i)
+            if (J.tri_mat[i] < 0 || J.tri_mat[i] >= J.n_mat)
+                return fail(NRRS_ERR_INVALID_ARG, "material id out of range");
+        for (int32_t i = 0; i < J.n_mat; ++i)
+            if (J.mats[i].type != 0 && J.mats[i].type != 1)
+                return fail(NRRS_ERR_INVALID_ARG, "unknown material type");
+        npix += (long long)J.width * J.height;
+        P += (long long)J.width * J.height * J.spp;
+        Dmax = std::max(Dmax, (int)J.max_depth);
+    }
+    if (npix >= (1ll << 31) || 2 * P >= (1ll << 31))
+        return fail(NRRS_ERR_INVALID_ARG, "batch too large (pixels or paths >= 2^31)");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(NRRS_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+
+    // one BVH per job, merged: child indices, triangle references and material ids are
+    // rebased so that every job's tree is a separate root in the same arrays
+    BvhHost all;
+    std::vector<nrrs_material> mats;
+    std::vector<JobDev> jd(n_jobs);
+    int64_t n_tri = 0;
+    long long pbase = 0, prim = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const nrrs_job& J = jobs[j];
+        BvhHost b;
+        build_bvh(J.tri, J.n_tri, J.tri_mat, &b);
+        const int32_t node_off = (int32_t)all.nodes.size();
+        const int32_t ref_off = all.n_ref;
+        const int32_t mat_off = (int32_t)mats.size();
+        for (BvhNode nd : b.nodes) {
+            for (int k = 0; k < 2; ++k)
+                nd.d[k] = nd.d[k] >= 0 ? nd.d[k] + node_off : ~(~nd.d[k] + ref_off);
+            all.nodes.push_back(nd);
+        }
+        for (int32_t r = 0; r < b.n_ref; ++r) {
+            float t[12];
+            std::memcpy(t, &b.tris[(size_t)r * 12], sizeof(t));
+            int32_t m;
+            std::memcpy(&m, &t[7], 4);
+            m += mat_off;
+            std::memcpy(&t[7], &m, 4);
+            all.tris.insert(all.tris.end(), t, t + 12);
+        }
+        all.n_ref += b.n_ref;
+        mats.insert(mats.end(), J.mats, J.mats + J.n_mat);
+        n_tri += J.n_tri;
+        JobDev& d = jd[j];
+        d.pixel_base = pbase;
+        d.prim_base = prim;
+        d.prims = (long long)J.width * J.height * J.spp;
+        d.W = J.width; d.H = J.height; d.spp = J.spp; d.D = J.max_depth;
+        d.root = node_off;
+        for (int k = 0; k < 3; ++k) {
+            d.lo[k] = b.lo[k];
+            const float ext = b.hi[k] - b.lo[k];
+            d.inv_ext[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
+            all.lo[k] = j == 0 ? b.lo[k] : std::min(all.lo[k], b.lo[k]);
+            all.hi[k] = j == 0 ? b.hi[k] : std::max(all.hi[k], b.hi[k]);
+        }
+        d.cam = cam_view(*J.cam);
+        d.cam.aspect = (float)J.width / (float)J.height;
+        pbase += (long long)J.width * J.height;
+        prim += d.prims;
+    }
+    nrrs_scene* s = nullptr;
+    nrrs_status rc = upload_scene(all, n_tri, mats.data(), (int32_t)mats.size(), nullptr, device, &s);
+    if (rc != NRRS_OK) return rc;
+    s->n_jobs = n_jobs;
+    s->jobs_host = jd;
+    s->batch_P = P;
+    s->batch_npix = npix;
+    s->batch_D = Dmax;
+    JobWork& w = s->jw;
+    w.n = n_jobs;
+    cudaError_t e = dalloc(&s->jobs_dev, (size_t)n_jobs);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->jobs_dev, jd.data(), sizeof(JobDev) * n_jobs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&w.F_cur, (size_t)n_jobs);
+    if (e == cudaSuccess) e = dalloc(&w.eps_I, (size_t)n_jobs);
+    if (e == cudaSuccess) e = dalloc(&w.F, (size_t)kMaxDepth * n_jobs);
+    if (e == cudaSuccess) e = dalloc(&w.sum_q, (size_t)kMaxDepth * n_jobs);
+    if (e == cudaSuccess) e = dalloc(&w.live, (size_t)kMaxDepth * n_jobs);
+    w.job = s->jobs_dev;
+    if (e != cudaSuccess) {
+        nrrs_status st = cuda_fail(e, "batch tables");
+        destroy(s);
+        return st;
+    }
+    *out = s;
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_render_batch(nrrs_scene* scene, int32_t rrs_mode, const nrrs_render_opts* opts,
+                              float* d_rgb, void* stream, nrrs_render_stats* stats,
+                              int64_t* job_live, float* job_F, double* job_sum_q) {
+    if (!scene || !d_rgb) return fail(NRRS_ERR_INVALID_ARG, "scene or d_rgb is NULL");
+    if (scene->n_jobs == 0) return fail(NRRS_ERR_INVALID_ARG, "not a batch (nrrs_create_batch)");
+    nrrs_render_opts o = opts ? *opts : render_defaults();
+    if (o.d_trace || o.d_suffix)
+        return fail(NRRS_ERR_UNSUPPORTED, "trace and suffix records are single-scene only");
+    nrrs_status rc = validate_render(scene, 1, 1, 1, scene->batch_D, rrs_mode, o);
+    if (rc != NRRS_OK) return rc;
+    if (scene->batch_P * o.cap_factor >= (1ll << 31))
+        return fail(NRRS_ERR_INVALID_ARG, "capacity >= 2^31");
+    DeviceGuard g(scene->device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+    nrrs_render_stats local;
+    const bool want_jobs = job_live || job_F || job_sum_q;
+    rc = render_impl(scene, (int32_t)scene->batch_npix, 1, 1, scene->batch_D, rrs_mode, o, d_rgb,
+                     (cudaStream_t)stream, stats ? stats : (want_jobs ? &local : nullptr),
+                     nullptr, nullptr);
+    if (rc != NRRS_OK) return rc;
+    const int n = scene->n_jobs, D = scene->batch_D;
+    for (int j = 0; j < n; ++j)
+        for (int d = 0; d < NRRS_MAX_DEPTH; ++d) {
+            const bool in = d < D;
+            const size_t k = (size_t)d * n + j;
+            if (job_live) job_live[(size_t)j * NRRS_MAX_DEPTH + d] = in ? scene->job_live[k] : 0;
+            if (job_F) job_F[(size_t)j * NRRS_MAX_DEPTH + d] = in ? scene->job_F[k] : 0.0f;
+            if (job_sum_q) job_sum_q[(size_t)j * NRRS_MAX_DEPTH + d] = in ? scene->job_sum_q[k] : 0.0;
+        }
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs, int64_t* pixel_base,
+                            int64_t* n_pixels_total) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (n_jobs) *n_jobs = scene->n_jobs;
+    if (pixel_base)
+        for (int j = 0; j < scene->n_jobs; ++j) pixel_base[j] = scene->jobs_host[j].pixel_base;
+    if (n_pixels_total) *n_pixels_total = scene->batch_npix;
     return NRRS_OK;
 }
 
@@ -1129,6 +1357,7 @@ nrrs_status nrrs_adam_step(float* d_params, const float* d_grad, float* d_m, flo
 nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void* stream,
                             nrrs_train_stats* out) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (scene->n_jobs > 0) return fail(NRRS_ERR_UNSUPPORTED, "training runs on a single scene");
     nrrs_train_opts o = opts ? *opts : train_defaults();
     nrrs_render_opts ro = render_defaults();
     ro.seed_lo = o.seed_lo;
@@ -1323,6 +1552,7 @@ nrrs_status nrrs_relmse(const float* d_img, const float* d_ref, int64_t n_pixels
 nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* opts, void* stream,
                                  nrrs_mixdepth_result* out) {
     if (!scene || !opts || !out) return fail(NRRS_ERR_INVALID_ARG, "NULL argument");
+    if (scene->n_jobs > 0) return fail(NRRS_ERR_UNSUPPORTED, "Mix-Depth search runs on a single scene");
     const nrrs_mixdepth_opts o = *opts;
     const int D = o.max_depth;
     const int64_t total = nrrs_mixdepth_candidates(D, o.t_d);

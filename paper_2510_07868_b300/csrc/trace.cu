@@ -29,12 +29,12 @@ struct Ray {
     int node, sp;
 };
 
-__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, Hit& h) {
+__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, int root, Hit& h) {
     r.o = o;
     r.d = d;
     r.inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
-    r.node = 0;
+    r.node = root;
     r.sp = 0;
     h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
 }
@@ -112,7 +112,7 @@ __device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, 
 // the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
 // Each slot's hit depends only on that slot's ray, so the result is deterministic.
 __global__ void __launch_bounds__(kExtendThreads, 4)
-k_trace(SceneView sc, QueueView cur, WorkView w, int depth) {
+k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
     __shared__ int s_stack[kStack * kExtendThreads];
     int* stk = s_stack + threadIdx.x;
     DevStats* st = w.st;
@@ -136,7 +136,13 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth) {
                 const long long my = (long long)base + __popc(need_mask & lt_mask);
                 if (my < n) {
                     idx = my;
-                    ray_init(ray, xyz(cur.o[idx]), xyz(cur.d[idx]), h);
+                    const float4 o4 = cur.o[idx];
+                    // a batched render starts each ray at the root of its job's scene
+                    const int root =
+                        jobs.job ? __ldg(&jobs.job[job_of_pixel(jobs.job, jobs.n,
+                                                                __float_as_uint(o4.w))].root)
+                                 : 0;
+                    ray_init(ray, xyz(o4), xyz(cur.d[idx]), root, h);
                 } else {
                     exhausted = true;
                 }
@@ -164,8 +170,8 @@ int max_blocks_trace() {
 }
 
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
-                  cudaStream_t s) {
-    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth);
+                  const JobWork& jobs, cudaStream_t s) {
+    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
 }
 
 }  // namespace nrrs

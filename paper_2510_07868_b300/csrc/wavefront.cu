@@ -162,6 +162,36 @@ __global__ void k_camera(CamView cam, RenderParams rp, QueueView out) {
     out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
 }
 
+// Primary rays of a batched render: slot i belongs to the job whose primary range holds
+// it; the job's camera and image size apply, and the random numbers are keyed by the
+// job-local pixel (so each job sees the numbers a render of it alone would).
+__global__ void k_camera_jobs(RenderParams rp, long long P, QueueView out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const JobDev* job = rp.jobs.job;
+    int lo = 0, hi = rp.jobs.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&job[mid].prim_base) <= i) lo = mid; else hi = mid - 1;
+    }
+    const JobDev& J = job[lo];
+    const long long li = i - J.prim_base;
+    const uint32_t pixel = (uint32_t)(li / J.spp), sample = (uint32_t)(li % J.spp);
+    const U4 w = draw(rp.fc->key0, rp.fc->key1, pixel, sample, 0u, kPurposeJitter, 0u);
+    const CamView& cam = J.cam;
+    const int px = (int)(pixel % (uint32_t)J.W), py = (int)(pixel / (uint32_t)J.W);
+    const float sx = (2.0f * ((float)px + u01(w.x)) / (float)J.W - 1.0f) * cam.tan_half * cam.aspect;
+    const float sy = (1.0f - 2.0f * ((float)py + u01(w.y)) / (float)J.H) * cam.tan_half;
+    const V3 fw = v3(cam.fw[0], cam.fw[1], cam.fw[2]);
+    const V3 rt = v3(cam.right[0], cam.right[1], cam.right[2]);
+    const V3 up = v3(cam.up[0], cam.up[1], cam.up[2]);
+    const V3 d = normalize3(fw + (rt * sx + up * sy));
+    out.o[i] = make_float4(cam.pos[0], cam.pos[1], cam.pos[2],
+                           bitsf((uint32_t)(J.pixel_base + pixel)));
+    out.d[i] = make_float4(d.x, d.y, d.z, bitsf(0u));
+    out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
+}
+
 // Extension of depth `depth`, part 2 (fixed grid-stride, coherent): emission deposit,
 // termination, and the RRS factor q_orig of each vertex; NET depths store the 16
 // features and q = -1 for the RRSNet kernel.  Non-NET depths also write the block's
@@ -198,7 +228,22 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
             }
             const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
             const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
-            if (!black && !dead && depth < rp.D) {
+            // the job's depth limit, scene box and HEUR floor in a batched render
+            int Dmax = rp.D;
+            float lo3[3] = {sc.lo[0], sc.lo[1], sc.lo[2]};
+            float ie3[3] = {sc.inv_ext[0], sc.inv_ext[1], sc.inv_ext[2]};
+            float epsI = eps_I;
+            if (rp.jobs.job) {
+                const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, fbits(o4.w));
+                const JobDev* J = rp.jobs.job + j;
+                Dmax = J->D;
+                for (int k = 0; k < 3; ++k) {
+                    lo3[k] = J->lo[k];
+                    ie3[k] = J->inv_ext[k];
+                }
+                epsI = rp.jobs.eps_I[j];
+            }
+            if (!black && !dead && depth < Dmax) {
                 if (KIND == kFactorOne) {
                     q = 1.0f;
                 } else if (KIND == kFactorPlain) {
@@ -209,7 +254,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                         q = l;
                     } else {
                         const float* rr = rp.ref + 3 * (size_t)fbits(o4.w);
-                        const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
+                        const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, epsI);
                         q = den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
                     }
                 } else {
@@ -217,12 +262,12 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     const V3 ns = front ? ng : ng * -1.0f;
                     float4* f = w.feat + 4 * i;
                     f[0] = make_float4(
-                        sc.inv_ext[0] > 0.0f ? (p.x - sc.lo[0]) * sc.inv_ext[0] : 0.5f,
-                        sc.inv_ext[1] > 0.0f ? (p.y - sc.lo[1]) * sc.inv_ext[1] : 0.5f,
-                        sc.inv_ext[2] > 0.0f ? (p.z - sc.lo[2]) * sc.inv_ext[2] : 0.5f, -d.x);
+                        ie3[0] > 0.0f ? (p.x - lo3[0]) * ie3[0] : 0.5f,
+                        ie3[1] > 0.0f ? (p.y - lo3[1]) * ie3[1] : 0.5f,
+                        ie3[2] > 0.0f ? (p.z - lo3[2]) * ie3[2] : 0.5f, -d.x);
                     f[1] = make_float4(-d.y, -d.z, ns.x, ns.y);
                     f[2] = make_float4(ns.z, m.albedo[0], m.albedo[1], m.albedo[2]);
-                    f[3] = make_float4((float)depth / (float)rp.D, boxcox(t4.x, rp.boxcox_lambda),
+                    f[3] = make_float4((float)depth / (float)Dmax, boxcox(t4.x, rp.boxcox_lambda),
                                        boxcox(t4.y, rp.boxcox_lambda),
                                        boxcox(t4.z, rp.boxcox_lambda));
                     q = -1.0f;  // filled by the RRSNet kernel
@@ -291,6 +336,95 @@ __device__ __forceinline__ void block_range(long long n, int* tiles_out, long lo
     *tiles_out = *begin < *end ? (int)((*end - *begin + kSplitThreads - 1) / kSplitThreads) : 0;
 }
 
+// ------------------------------------------------------------------ batched renders
+// Eq. F_norm per job: the queue holds the jobs one after another (it stays sorted by
+// global pixel), so each block's contiguous slot range meets few jobs; the block writes
+// an FP64 partial sum of q and a slot count for every job (zero where it meets none).
+__global__ void __launch_bounds__(kSplitThreads) k_sum_q_jobs(WorkView w, RenderParams rp,
+                                                              int depth) {
+    __shared__ double shd[32];
+    __shared__ unsigned long long shc[32];
+    const JobWork& J = rp.jobs;
+    const long long n = w.st->live[depth - 1];
+    long long begin, end;
+    int tiles;
+    block_range(n, &tiles, &begin, &end);
+    double* part = J.part + (size_t)blockIdx.x * J.n;
+    long long* cnt = J.cnt + (size_t)blockIdx.x * J.n;
+    int j0 = 0, j1 = -1;
+    if (begin < end) {
+        j0 = job_of_pixel(J.job, J.n, fbits(w.dep[begin].w));
+        j1 = job_of_pixel(J.job, J.n, fbits(w.dep[end - 1].w));
+    }
+    for (int j = threadIdx.x; j < J.n; j += blockDim.x)
+        if (j < j0 || j > j1) {
+            part[j] = 0.0;
+            cnt[j] = 0;
+        }
+    for (int j = j0; j <= j1; ++j) {
+        const long long pb = J.job[j].pixel_base;
+        const long long pe = j + 1 < J.n ? J.job[j + 1].pixel_base : 0x7FFFFFFFFFFFll;
+        double s = 0.0;
+        unsigned long long c = 0;
+        for (long long i = begin + threadIdx.x; i < end; i += blockDim.x) {
+            const long long pix = fbits(w.dep[i].w);
+            if (pix >= pb && pix < pe) {
+                s += (double)w.q[i];
+                ++c;
+            }
+        }
+        s = block_sum(s, shd);
+        c = block_sum(c, shc);
+        if (threadIdx.x == 0) {
+            part[j] = s;
+            cnt[j] = (long long)c;
+        }
+    }
+}
+
+// F_j = min(1, f_rate * alpha * C_j / sum_j q), summed over the blocks in a fixed order.
+__global__ void k_normalize_jobs(WorkView w, RenderParams rp, int depth, int normalized,
+                                 int G) {
+    const JobWork& J = rp.jobs;
+    DevStats* st = w.st;
+    const double alpha = st->alpha_cur;
+    for (int j = threadIdx.x; j < J.n; j += blockDim.x) {
+        double s = 0.0;
+        long long c = 0;
+        for (int b = 0; b < G; ++b) {
+            s += J.part[(size_t)b * J.n + j];
+            c += J.cnt[(size_t)b * J.n + j];
+        }
+        double F = 1.0;
+        if (normalized && s > 0.0) {
+            F = (double)rp.f_rate * alpha * (double)J.cap_factor * (double)J.job[j].prims / s;
+            if (F > 1.0) F = 1.0;
+        }
+        J.F_cur[j] = (float)F;
+        J.F[(size_t)(depth - 1) * J.n + j] = (float)F;
+        J.sum_q[(size_t)(depth - 1) * J.n + j] = s;
+        J.live[(size_t)(depth - 1) * J.n + j] = c;
+    }
+    if (threadIdx.x == 0) {
+        st->alpha[depth - 1] = alpha;
+        st->F[depth - 1] = 0.0f;  // per job: see JobWork::F
+        st->F_cur = 0.0f;
+    }
+}
+
+// HEUR floor per job: eps_rel * mean of the reference over the job's pixels.
+__global__ void k_ref_prepare_jobs(const float* __restrict__ ref, RenderParams rp, float eps_rel) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    const JobDev& J = rp.jobs.job[j];
+    const long long n3 = 3ll * J.W * J.H;
+    double s = 0.0;
+    if (ref)
+        for (long long i = threadIdx.x; i < n3; i += blockDim.x) s += (double)ref[3 * J.pixel_base + i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) rp.jobs.eps_I[j] = ref ? (float)((double)eps_rel * (s / (double)n3)) : 0.0f;
+}
+
 __device__ __forceinline__ void kahan_add(float4* s_, float4* c_, float x, float y, float z) {
     float4 s = *s_, c = *c_;
     float in[3] = {x, y, z};
@@ -344,7 +478,14 @@ k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int dept
                 const float4 t4 = cur.t[i];
                 float qu;
                 uint32_t base;
-                X = split_decide(F, w.q[i], key0, key1, fbits(o4.w), fbits(t4.w),
+                float Fi = F;
+                uint32_t lpix = fbits(o4.w);
+                if (rp.jobs.job) {  // the job's factor; random numbers by job-local pixel
+                    const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, lpix);
+                    Fi = rp.jobs.F_cur[j];
+                    lpix -= (uint32_t)rp.jobs.job[j].pixel_base;
+                }
+                X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w),
                                  (uint32_t)depth, fbits(d4.w), &qu, &base);
                 if (rp.trace) {
                     const int slot = __float_as_int(w.hit[i].y);
@@ -429,11 +570,19 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
         uint32_t X = 0, base = 0;
         float qu = 0.0f;
         float4 o4, d4, t4;
+        uint32_t lpix = 0;
         if (i < end) {
             o4 = cur.o[i];
             d4 = cur.d[i];
             t4 = cur.t[i];
-            X = split_decide(F, w.q[i], key0, key1, fbits(o4.w), fbits(t4.w),
+            float Fi = F;
+            lpix = fbits(o4.w);
+            if (rp.jobs.job) {
+                const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, lpix);
+                Fi = rp.jobs.F_cur[j];
+                lpix -= (uint32_t)rp.jobs.job[j].pixel_base;
+            }
+            X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w),
                              (uint32_t)depth, fbits(d4.w), &qu, &base);
         }
         uint32_t tile_total;
@@ -453,13 +602,13 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
             const V3 ns = dot3(ng, d) < 0.0f ? ng : ng * -1.0f;
             const V3 p = xyz(o4) + d * hh.x;
             const V3 org = p + ns * kRayOffset;
-            const uint32_t pix = fbits(o4.w), smp = fbits(t4.w);
+            const uint32_t smp = fbits(t4.w);
             const float iq = 1.0f / qu;
             for (uint32_t j = 0; j < X; ++j) {
                 const unsigned long long dst = carry + pre + j;
                 if (dst >= (unsigned long long)rp.cap) break;
                 const uint32_t lin = base + j * kLineageStep;
-                const U4 r = draw(key0, key1, pix, smp, (uint32_t)depth, kPurposeBsdf, lin);
+                const U4 r = draw(key0, key1, lpix, smp, (uint32_t)depth, kPurposeBsdf, lin);
                 V3 wi, wt;
                 if (m.type == 0) {
                     wi = cosine_dir(ns, u01(r.y), u01(r.z));
@@ -478,12 +627,13 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
 }
 
 __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
-                           float* __restrict__ ref_mean, int update_ref) {
-    const long long npix = (long long)rp.W * rp.H;
+                           float* __restrict__ ref_mean, int update_ref, long long npix) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
     const float4 s = w.acc_s[p], c = w.acc_c[p];
-    const float inv = 1.0f / (float)rp.spp;
+    const int spp = rp.jobs.job ? rp.jobs.job[job_of_pixel(rp.jobs.job, rp.jobs.n, (uint32_t)p)].spp
+                                : rp.spp;
+    const float inv = 1.0f / (float)spp;
     const float r = (s.x - c.x) * inv, g = (s.y - c.y) * inv, b = (s.z - c.z) * inv;
     rgb[3 * p + 0] = r;
     rgb[3 * p + 1] = g;
@@ -642,9 +792,26 @@ void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, con
 }
 
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
-                     int update_ref, cudaStream_t s) {
-    const long long npix = (long long)rp.W * rp.H;
-    k_finalize<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(w, rp, rgb, ref_mean, update_ref);
+                     int update_ref, long long npix, cudaStream_t s) {
+    k_finalize<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(w, rp, rgb, ref_mean, update_ref,
+                                                               npix);
+}
+
+void launch_ref_prepare_jobs(const RenderParams& rp, float eps_rel, cudaStream_t s) {
+    k_ref_prepare_jobs<<<rp.jobs.n, 256, 0, s>>>(rp.ref, rp, eps_rel);
+}
+
+void launch_sum_q_jobs(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
+    k_sum_q_jobs<<<w.grid_red, kSplitThreads, 0, s>>>(w, rp, depth);
+}
+
+void launch_normalize_jobs(const WorkView& w, const RenderParams& rp, int depth, int normalized,
+                           cudaStream_t s) {
+    k_normalize_jobs<<<1, 256, 0, s>>>(w, rp, depth, normalized, w.grid_red);
+}
+
+void launch_camera_jobs(const RenderParams& rp, long long P, QueueView out, cudaStream_t s) {
+    k_camera_jobs<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(rp, P, out);
 }
 
 __global__ void k_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count) {

@@ -71,10 +71,49 @@ struct FrameConsts {
     int pad;
 };
 
+// One job of a batched render: its own scene (BVH root, materials already rebased into
+// the merged arrays), camera, image and depth, sharing the queue and the RRSNet.  Jobs
+// are laid out one after another: global pixel = pixel_base + local pixel, primary slot
+// = prim_base + local primary index (pixel-major, sample-minor).
+struct JobDev {
+    long long pixel_base, prim_base;
+    long long prims;     // W * H * spp; the job's budget is C_j = cap_factor * prims
+    int W, H, spp, D;
+    int root;            // BVH root node of the job's scene
+    int pad;
+    float lo[3], inv_ext[3];  // the job's scene box (position feature)
+    CamView cam;
+};
+
+// Per-job device arrays of a batched render.
+struct JobWork {
+    const JobDev* job;   // [n]
+    int n;
+    int cap_factor;
+    float* F_cur;        // [n] normalisation factor of the current depth
+    float* eps_I;        // [n] HEUR floor of each job
+    double* part;        // [grid_red][n] per-block partial sums of q
+    long long* cnt;      // [grid_red][n] per-block slot counts
+    float* F;            // [kMaxDepth][n]
+    double* sum_q;       // [kMaxDepth][n]
+    long long* live;     // [kMaxDepth][n]
+};
+
+// Job of a global pixel (binary search over the jobs' pixel bases).
+__device__ __forceinline__ int job_of_pixel(const JobDev* job, int n, uint32_t pix) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&job[mid].pixel_base) <= (long long)pix) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 struct RenderParams {
     int W, H, spp, D;
     long long cap;        // C
     const FrameConsts* fc;
+    JobWork jobs;         // batched render (jobs.job != nullptr), else unused
     float f_rate;
     float q_max;
     float boxcox_lambda;
@@ -95,7 +134,7 @@ void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double al
                         long long P, DevStats* st, cudaStream_t s);
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
-                  cudaStream_t s);
+                  const JobWork& jobs, cudaStream_t s);
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s);
 void launch_sum_q(const WorkView& w, int depth, cudaStream_t s);
@@ -107,7 +146,13 @@ void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cud
 void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
                           const RenderParams& rp, int depth, cudaStream_t s);
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
-                     int update_ref, cudaStream_t s);
+                     int update_ref, long long npix, cudaStream_t s);
+// Batched renders: per-job HEUR floors, per-job sums of q and normalisation factors.
+void launch_ref_prepare_jobs(const RenderParams& rp, float eps_rel, cudaStream_t s);
+void launch_sum_q_jobs(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
+void launch_normalize_jobs(const WorkView& w, const RenderParams& rp, int depth, int normalized,
+                           cudaStream_t s);
+void launch_camera_jobs(const RenderParams& rp, long long P, QueueView out, cudaStream_t s);
 void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_count,
                          cudaStream_t s);
 

@@ -307,6 +307,24 @@ def three_rooms(seed: int = 1, n_random: int = 1_000_000, tri_size: float = 0.01
                  "three_rooms")
 
 
+def uneven_jobs(seed: int = 1, n_jobs: int = 64, tri_range=(1_000, 50_000), side_log2=(5, 9),
+                spp_range=(1, 64), depth_range=(8, 32), subdiv: int = 2):
+    """Render jobs of uneven size for a batched render: per job an ``icosphere_room``
+    scene with log-uniform triangle count in ``tri_range`` (half GGX), a square image of
+    side round(2^U[side_log2]), spp uniform in ``spp_range`` and depth uniform in
+    ``depth_range`` (bounds inclusive).  Returns a list of (Scene, W, H, spp, D)."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k in range(n_jobs):
+        n_tri = int(np.exp(rng.uniform(np.log(tri_range[0]), np.log(tri_range[1]))))
+        side = int(round(2.0 ** rng.uniform(*side_log2)))
+        spp = int(rng.integers(spp_range[0], spp_range[1] + 1))
+        D = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        scene = icosphere_room(1000 * seed + k, min_triangles=n_tri, subdiv=subdiv)
+        jobs.append((scene, side, side, spp, D))
+    return jobs
+
+
 def rrsnet_init_params(seed: int = 1, dtype=np.float32) -> np.ndarray:
     """Xavier-uniform draw of the 2592 RRSNet weights, packed W1|W2|W3|W4, row-major.
 

@@ -38,7 +38,7 @@ EXPORTED = [
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
     "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
-    "nrrs_set_rrsnet_shape",
+    "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
 ]
 
 
@@ -110,6 +110,14 @@ class TrainOpts(C.Structure):
 
 
 TUNE_BUCKETS = 17
+MAX_JOBS = 256
+
+
+class Job(C.Structure):
+    _fields_ = [("tri", C.c_void_p), ("n_tri", C.c_int32), ("tri_mat", C.c_void_p),
+                ("mats", C.c_void_p), ("n_mat", C.c_int32), ("cam", C.c_void_p),
+                ("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
+                ("max_depth", C.c_int32)]
 
 
 class TuneReport(C.Structure):
@@ -182,6 +190,9 @@ def _load():
         "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
         "nrrs_tune_rrsnet": ([P, I32, P, P], I32),
         "nrrs_set_rrsnet_shape": ([P, I32, I32, I32, I32], I32),
+        "nrrs_create_batch": ([P, I32, I32, P], I32),
+        "nrrs_render_batch": ([P, I32, P, P, P, P, P, P, P], I32),
+        "nrrs_batch_info": ([P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -245,6 +256,44 @@ def nrrs_create_scene(tri, tri_mat, mats, cam, device=0):
                                   mats.ctypes.data, len(mats), cam.ctypes.data, device,
                                   C.byref(out)))
     return out.value
+
+
+def nrrs_create_batch(jobs, device=0):
+    """jobs: sequence of (inputs.Scene, width, height, spp, max_depth)."""
+    keep = []
+    arr = (Job * len(jobs))()
+    for k, (sc, w, h, spp, D) in enumerate(jobs):
+        tri = np.ascontiguousarray(sc.tri, dtype=np.float32).reshape(-1, 9)
+        tm = np.ascontiguousarray(sc.mat_id, dtype=np.int32)
+        mats = np.ascontiguousarray(sc.mats)
+        cam = np.ascontiguousarray(sc.cam)
+        keep += [tri, tm, mats, cam]
+        arr[k] = Job(tri.ctypes.data, tri.shape[0], tm.ctypes.data, mats.ctypes.data, len(mats),
+                     cam.ctypes.data, w, h, spp, D)
+    out = C.c_void_p()
+    _check(_lib.nrrs_create_batch(arr, len(jobs), device, C.byref(out)))
+    return out.value
+
+
+def nrrs_render_batch(batch, rrs_mode, opts, d_rgb, n_jobs, stream=None, stats=True):
+    st = RenderStats() if stats else None
+    live = np.zeros((n_jobs, MAX_DEPTH), dtype=np.int64)
+    F = np.zeros((n_jobs, MAX_DEPTH), dtype=np.float32)
+    sq = np.zeros((n_jobs, MAX_DEPTH), dtype=np.float64)
+    _check(_lib.nrrs_render_batch(batch, rrs_mode, C.byref(opts) if opts is not None else None,
+                                  _ptr(d_rgb), _stream(stream),
+                                  C.byref(st) if st is not None else None, live.ctypes.data,
+                                  F.ctypes.data, sq.ctypes.data))
+    return (st.as_dict(MAX_DEPTH) if st is not None else None), live, F, sq
+
+
+def nrrs_batch_info(batch):
+    n = C.c_int32()
+    total = C.c_int64()
+    _check(_lib.nrrs_batch_info(batch, C.byref(n), None, C.byref(total)))
+    base = np.zeros(max(n.value, 1), dtype=np.int64)
+    _check(_lib.nrrs_batch_info(batch, None, base.ctypes.data, None))
+    return n.value, base[:n.value], total.value
 
 
 def nrrs_destroy_scene(scene):
@@ -430,6 +479,48 @@ def gate_methods(gate, max_depth):
 
 
 # ------------------------------------------------------------------ convenience wrapper
+class Batch:
+    """Owns a batch scene of many render jobs: ``jobs`` is a sequence of
+    (inputs.Scene, width, height, spp, max_depth)."""
+
+    def __init__(self, jobs, device=0):
+        self.handle = nrrs_create_batch(jobs, device)
+        self.device = device
+        self.shapes = [(h, w) for (_, w, h, _, _) in jobs]
+        self.max_depth = max(j[4] for j in jobs)
+        self.n_jobs, self.pixel_base, self.n_pixels = nrrs_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            nrrs_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        nrrs_set_rrsnet_params(self.handle, params)
+
+    def tune(self, precision=32, stream=None):
+        return nrrs_tune_rrsnet(self.handle, precision, stream)
+
+    def render(self, mode, out=None, stream=None, **opts):
+        """One frame of every job; returns (list of per-job [H, W, 3] views of the output,
+        totals, per-job live [n][32], per-job F, per-job sum of q)."""
+        import torch
+
+        if out is None:
+            out = torch.empty((self.n_pixels, 3), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        st, live, F, sq = nrrs_render_batch(self.handle, mode, RenderOpts.defaults(**opts), out,
+                                            self.n_jobs, stream)
+        imgs = [out[b:b + h * w].view(h, w, 3) for b, (h, w) in zip(self.pixel_base, self.shapes)]
+        return imgs, st, live, F, sq
+
+
 class Scene:
     """Owns one nrrs_scene handle built from an ``inputs.Scene``."""
 

@@ -86,7 +86,8 @@ def test_struct_offsets_match_the_c_compiler(tmp_path):
     pairs = {"nrrs_render_opts": nrrs.RenderOpts, "nrrs_render_stats": nrrs.RenderStats,
              "nrrs_train_opts": nrrs.TrainOpts, "nrrs_train_stats": nrrs.TrainStats,
              "nrrs_mixdepth_opts": nrrs.MixDepthOpts,
-             "nrrs_mixdepth_result": nrrs.MixDepthResult, "nrrs_tune_report": nrrs.TuneReport}
+             "nrrs_mixdepth_result": nrrs.MixDepthResult, "nrrs_tune_report": nrrs.TuneReport,
+             "nrrs_job": nrrs.Job}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "nrrs.h"', "int main(void) {"]
     expect = []
     for cname, cls in pairs.items():
