@@ -343,6 +343,8 @@ def run_ours(args, rank, world, local_rank):
     params = I.rrsnet_init_params(1)
     sc = nrrs.Scene(scene, device=local_rank)
     sc.set_params(params)
+    if args.bvh4:
+        sc.set_traversal(4)
     out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     seed_hi = rank  # independent replicas: different Philox streams per rank
@@ -571,6 +573,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
                    "parallelism": f"replicas{world}",
                    "bounce_loop": "CUDA graph per frame" if graph else "stream launches",
+                   "bvh": "four-wide" if args.bvh4 else "BVH2",
                    "l2": "no flush: each step rewrites ~0.3 GB of path queues and records (> 126 MB L2)"},
         "step_breakdown": {"train_step_ms": train_ms / args.steps,
                            "render_ms": (ms - train_ms) / args.steps,
@@ -601,6 +604,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-efficiency", action="store_true")
+    ap.add_argument("--bvh4", action="store_true",
+                    help="traverse the four-wide tree instead of the binary BVH")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the bounce loop kernel by kernel instead of as a CUDA graph")
     ap.add_argument("--pretrain", type=int, default=PRETRAIN_STEPS,

@@ -175,6 +175,8 @@ struct nrrs_scene {
     int n_sm = 148;
     int64_t n_nodes = 0, n_tri = 0;
     float4* nodes = nullptr;
+    float4* nodes4 = nullptr;  // four-wide tree (NULL when its stack bound exceeds the kernel's)
+    int bvh_width = 2;
     float4* tris = nullptr;
     nrrs_material* mats = nullptr;
     float* params = nullptr;  // RRSNet weights, 2592 floats
@@ -267,6 +269,7 @@ void destroy(nrrs_scene* s) {
     s->train.release_all();
     s->ws.release();
     cudaFree(s->nodes);
+    cudaFree(s->nodes4);
     cudaFree(s->tris);
     cudaFree(s->mats);
     cudaFree(s->params);
@@ -369,8 +372,9 @@ CamView cam_view(const nrrs_camera& cam) {
 
 // Uploads a built BVH (and its triangle references), the materials and the camera
 // (NULL for a batch, whose cameras live in the job table) into a new scene.
-nrrs_status upload_scene(const BvhHost& bvh, int64_t n_tri, const nrrs_material* mats,
-                         int32_t n_mat, const nrrs_camera* cam, int device, nrrs_scene** out) {
+nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri,
+                         const nrrs_material* mats, int32_t n_mat, const nrrs_camera* cam,
+                         int device, nrrs_scene** out) {
     nrrs_scene* s = new nrrs_scene();
     s->device = device;
     s->n_sm = sm_count(device);
@@ -394,7 +398,14 @@ nrrs_status upload_scene(const BvhHost& bvh, int64_t n_tri, const nrrs_material*
         return bail(e, "copy mats");
     if ((e = cudaMemset(s->params, 0, kNParams * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
 
+    if (bvh4 && !bvh4->nodes.empty()) {
+        if ((e = dalloc(&s->nodes4, bvh4->nodes.size() * 8)) != cudaSuccess) return bail(e, "alloc nodes4");
+        if ((e = cudaMemcpy(s->nodes4, bvh4->nodes.data(), bvh4->nodes.size() * 128,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy nodes4");
+    }
     s->view.nodes = s->nodes;
+    s->view.nodes4 = nullptr;  // the BVH2 unless nrrs_set_traversal(4): measured no faster
     s->view.tris = s->tris;
     s->view.mats = s->mats;
     for (int k = 0; k < 3; ++k) {
@@ -447,7 +458,10 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
 
     BvhHost bvh;
     build_bvh(tri, n_tri, tri_mat, &bvh);
-    return upload_scene(bvh, n_tri, mats, n_mat, cam, device, out);
+    Bvh4Host bvh4;
+    collapse_bvh4(bvh, &bvh4);
+    const bool wide = bvh4.max_stack <= trace_stack_entries();
+    return upload_scene(bvh, wide ? &bvh4 : nullptr, n_tri, mats, n_mat, cam, device, out);
 }
 
 nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
@@ -455,6 +469,16 @@ nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
     DeviceGuard g(scene->device);
     cudaDeviceSynchronize();
     destroy(scene);
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (width != 2 && width != 4) return fail(NRRS_ERR_INVALID_ARG, "width must be 2 or 4");
+    if (width == 4 && !scene->nodes4)
+        return fail(NRRS_ERR_UNSUPPORTED, "no four-wide tree (its stack bound is too deep)");
+    scene->bvh_width = width;
+    scene->view.nodes4 = width == 4 ? scene->nodes4 : nullptr;
     return NRRS_OK;
 }
 
@@ -784,6 +808,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(rec ? rec->C : 0),
                                (uint64_t)fbits(scene->cam.aspect),
                                (uint64_t)(uintptr_t)scene->jw.part,
+                               (uint64_t)(uintptr_t)scene->view.nodes4,
                                (uint64_t)o.cap_factor};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
@@ -927,6 +952,8 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
     // one BVH per job, merged: child indices, triangle references and material ids are
     // rebased so that every job's tree is a separate root in the same arrays
     BvhHost all;
+    Bvh4Host all4;
+    bool wide = true;
     std::vector<nrrs_material> mats;
     std::vector<JobDev> jd(n_jobs);
     int64_t n_tri = 0;
@@ -935,6 +962,10 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
         const nrrs_job& J = jobs[j];
         BvhHost b;
         build_bvh(J.tri, J.n_tri, J.tri_mat, &b);
+        Bvh4Host b4;
+        collapse_bvh4(b, &b4);
+        wide = wide && b4.max_stack <= trace_stack_entries();
+        const int32_t node4_off = (int32_t)all4.nodes.size();
         const int32_t node_off = (int32_t)all.nodes.size();
         const int32_t ref_off = all.n_ref;
         const int32_t mat_off = (int32_t)mats.size();
@@ -942,6 +973,12 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
             for (int k = 0; k < 2; ++k)
                 nd.d[k] = nd.d[k] >= 0 ? nd.d[k] + node_off : ~(~nd.d[k] + ref_off);
             all.nodes.push_back(nd);
+        }
+        for (Bvh4Node nd : b4.nodes) {
+            for (int k = 0; k < 4; ++k)
+                nd.child[k] = nd.child[k] >= 0 ? nd.child[k] + node4_off
+                                               : ~(~nd.child[k] + ref_off);
+            all4.nodes.push_back(nd);
         }
         for (int32_t r = 0; r < b.n_ref; ++r) {
             float t[12];
@@ -961,6 +998,7 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
         d.prims = (long long)J.width * J.height * J.spp;
         d.W = J.width; d.H = J.height; d.spp = J.spp; d.D = J.max_depth;
         d.root = node_off;
+        d.root4 = node4_off;
         for (int k = 0; k < 3; ++k) {
             d.lo[k] = b.lo[k];
             const float ext = b.hi[k] - b.lo[k];
@@ -974,7 +1012,8 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
         prim += d.prims;
     }
     nrrs_scene* s = nullptr;
-    nrrs_status rc = upload_scene(all, n_tri, mats.data(), (int32_t)mats.size(), nullptr, device, &s);
+    nrrs_status rc = upload_scene(all, wide ? &all4 : nullptr, n_tri, mats.data(),
+                                  (int32_t)mats.size(), nullptr, device, &s);
     if (rc != NRRS_OK) return rc;
     s->n_jobs = n_jobs;
     s->jobs_host = jd;

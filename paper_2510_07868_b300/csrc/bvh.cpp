@@ -292,4 +292,96 @@ void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* 
         }
 }
 
+namespace {
+
+struct Entry {
+    float lo[3], hi[3];
+    int32_t code, count;
+    double area() const {
+        const double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1],
+                     dz = (double)hi[2] - lo[2];
+        return dx < 0.0 ? 0.0 : 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+Entry child_entry(const BvhNode& n, int side) {
+    Entry e;
+    const float* xy = side ? n.b : n.a;
+    e.lo[0] = xy[0]; e.hi[0] = xy[1]; e.lo[1] = xy[2]; e.hi[1] = xy[3];
+    e.lo[2] = n.c[2 * side]; e.hi[2] = n.c[2 * side + 1];
+    e.code = n.d[side];
+    e.count = n.d[2 + side];
+    return e;
+}
+
+struct Collapser {
+    const std::vector<BvhNode>& in;
+    std::vector<Bvh4Node>& out;
+
+    // Builds the four-wide node for BVH2 node n2: its two children, then repeatedly the
+    // inner child of largest surface area replaced by its own two children, up to four.
+    // Returns the node index and, in *stack, the most stack entries below it.
+    int32_t build(int32_t n2, int* stack) {
+        Entry e[4];
+        int m = 2;
+        e[0] = child_entry(in[n2], 0);
+        e[1] = child_entry(in[n2], 1);
+        while (m < 4) {
+            int pick = -1;
+            double best = -1.0;
+            for (int k = 0; k < m; ++k)
+                if (e[k].code >= 0 && e[k].area() > best) {
+                    best = e[k].area();
+                    pick = k;
+                }
+            if (pick < 0) break;
+            const BvhNode& nd = in[e[pick].code];
+            e[pick] = child_entry(nd, 0);
+            e[m++] = child_entry(nd, 1);
+        }
+        const int32_t self = (int32_t)out.size();
+        out.emplace_back();
+        int inner = 0, below = 0;
+        int32_t code[4], count[4];
+        for (int k = 0; k < 4; ++k) {
+            if (k < m && e[k].code >= 0) {
+                int st = 0;
+                code[k] = build(e[k].code, &st);
+                count[k] = 0;
+                below = std::max(below, st);
+                ++inner;
+            } else if (k < m) {
+                code[k] = e[k].code;
+                count[k] = e[k].count;
+            } else {
+                code[k] = ~0;
+                count[k] = 0;
+            }
+        }
+        Bvh4Node& o = out[self];
+        for (int k = 0; k < 4; ++k) {
+            const bool used = k < m;
+            o.lox[k] = used ? e[k].lo[0] : 0.0f; o.hix[k] = used ? e[k].hi[0] : 0.0f;
+            o.loy[k] = used ? e[k].lo[1] : 0.0f; o.hiy[k] = used ? e[k].hi[1] : 0.0f;
+            o.loz[k] = used ? e[k].lo[2] : 0.0f; o.hiz[k] = used ? e[k].hi[2] : 0.0f;
+            o.child[k] = code[k];
+            o.count[k] = count[k];
+        }
+        // a visit pushes every inner child it enters but the nearest
+        *stack = std::max(0, inner - 1) + below;
+        return self;
+    }
+};
+
+}  // namespace
+
+void collapse_bvh4(const BvhHost& b2, Bvh4Host* out) {
+    out->nodes.clear();
+    out->nodes.reserve(b2.nodes.size() / 2 + 1);
+    Collapser c{b2.nodes, out->nodes};
+    int stack = 0;
+    c.build(0, &stack);
+    out->max_stack = stack;
+}
+
 }  // namespace nrrs

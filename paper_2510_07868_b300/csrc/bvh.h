@@ -20,4 +20,22 @@ struct BvhHost {
 
 void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* out);
 
+// Four-wide tree collapsed from the BVH2 (bvh.cpp): 128 bytes per node, the children's
+// boxes as six float4 rows (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of children 0..3), then the
+// child codes (as BvhNode) and the leaf reference counts.  An unused slot is a leaf with
+// no references.  The triangle references are the BVH2's, unchanged.
+struct Bvh4Node {
+    float lox[4], hix[4], loy[4], hiy[4], loz[4], hiz[4];
+    int32_t child[4];
+    int32_t count[4];
+};
+static_assert(sizeof(Bvh4Node) == 128, "node is 8 x float4");
+
+struct Bvh4Host {
+    std::vector<Bvh4Node> nodes;  // nodes[0] is the root
+    int max_stack = 0;            // most stack entries a closest-hit traversal can hold
+};
+
+void collapse_bvh4(const BvhHost& b2, Bvh4Host* out);
+
 }  // namespace nrrs

@@ -29,14 +29,113 @@ struct Ray {
     int node, sp;
 };
 
+// A direction component that is exactly zero would make the slab products 0 * inf and
+// inf - inf (NaN) and lose boxes; the reciprocal uses a tiny component of the same sign
+// instead (the slab then spans everything or nothing along that axis, as it should).
+__device__ __forceinline__ float safe_rcp(float x) {
+    return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x);
+}
+
 __device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, int root, Hit& h) {
     r.o = o;
     r.d = d;
-    r.inv = v3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    r.inv = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     r.node = root;
     r.sp = 0;
     h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
+}
+
+// Moller-Trumbore against triangle reference s; keeps the closest hit, equal distances
+// going to the lower original triangle index.
+__device__ __forceinline__ void intersect_tri(const SceneView& sc, const Ray& r, Hit& h, int s) {
+    const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
+    const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
+    const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
+    const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
+    const V3 pv = cross3(r.d, e2);
+    const float det = dot3(e1, pv);
+    if (det == 0.0f) return;
+    const float idet = 1.0f / det;
+    const V3 tv = r.o - v0;
+    const float u = dot3(tv, pv) * idet;
+    if (u < 0.0f || u > 1.0f) return;
+    const V3 qv = cross3(tv, e1);
+    const float v = dot3(r.d, qv) * idet;
+    if (v < 0.0f || u + v > 1.0f) return;
+    const float t = dot3(e2, qv) * idet;
+    const uint32_t id = fbits(t0.w);
+    if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
+        h.t = t;
+        h.slot = s;
+        h.id = id;
+    }
+}
+
+// Slab test of one box against the ray, clipped to (0, h.t]; writes the entry distance.
+__device__ __forceinline__ bool slab(const Ray& r, float hit_t, float lx, float hx, float ly,
+                                     float hy, float lz, float hz, float* tn) {
+    const float ax = fmaf(lx, r.inv.x, -r.oi.x), bx = fmaf(hx, r.inv.x, -r.oi.x);
+    const float ay = fmaf(ly, r.inv.y, -r.oi.y), by = fmaf(hy, r.inv.y, -r.oi.y);
+    const float az = fmaf(lz, r.inv.z, -r.oi.z), bz = fmaf(hz, r.inv.z, -r.oi.z);
+    const float n = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
+    const float f = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), hit_t));
+    *tn = n;
+    return n <= f;
+}
+
+// Visits one four-wide node: the four child boxes are tested together, leaf children
+// are intersected at once, and the inner children entered are ordered near to far: the
+// nearest is visited next and the others pushed farthest first.  The same closest hit
+// as the BVH2 visit (same triangle test, same tie rule).  Returns true when the query
+// ends.
+__device__ __forceinline__ bool visit_node4(const SceneView& sc, Ray& r, Hit& h, int* stk,
+                                            int stride) {
+    const float4* N = sc.nodes4 + 8 * r.node;
+    const float4 lx = __ldg(N + 0), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
+    const float4 lz = __ldg(N + 4), hz = __ldg(N + 5);
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(N + 6));
+    const int4 cn = __ldg(reinterpret_cast<const int4*>(N + 7));
+    float tn[4];
+    bool hit[4];
+    hit[0] = slab(r, h.t, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, &tn[0]);
+    hit[1] = slab(r, h.t, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, &tn[1]);
+    hit[2] = slab(r, h.t, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, &tn[2]);
+    hit[3] = slab(r, h.t, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, &tn[3]);
+    const int code[4] = {ch.x, ch.y, ch.z, ch.w};
+    const int count[4] = {cn.x, cn.y, cn.z, cn.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!hit[k] || code[k] >= 0) continue;
+        const int first = ~code[k];
+        for (int j = 0; j < count[k]; ++j) intersect_tri(sc, r, h, first + j);
+    }
+    // inner children still in reach after the leaf hits, sorted by entry distance
+    float key[4];
+    int nxt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool in = hit[k] && code[k] >= 0 && tn[k] <= h.t;
+        key[k] = in ? tn[k] : FLT_MAX;
+        nxt[k] = in ? code[k] : -1;
+    }
+    auto cswap = [&](int i, int j) {
+        if (key[j] < key[i]) {
+            const float tk = key[i]; key[i] = key[j]; key[j] = tk;
+            const int tc = nxt[i]; nxt[i] = nxt[j]; nxt[j] = tc;
+        }
+    };
+    cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+#pragma unroll
+    for (int k = 3; k >= 1; --k)
+        if (nxt[k] >= 0 && r.sp < kStack) stk[(r.sp++) * stride] = nxt[k];
+    if (nxt[0] >= 0) {
+        r.node = nxt[0];
+        return false;
+    }
+    if (r.sp == 0) return true;
+    r.node = stk[(--r.sp) * stride];
+    return false;
 }
 
 // Visits one BVH2 node of the closest-hit query along o + t d (t > 0): both child boxes
@@ -68,30 +167,7 @@ __device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, 
         const bool hitbox = side ? h1 : h0;
         if (!hitbox || code >= 0) continue;
         const int first = ~code, count = side ? e.w : e.z;
-        for (int k = 0; k < count; ++k) {
-            const int s = first + k;
-            const float4 t0 = __ldg(&sc.tris[3 * s + 0]);
-            const float4 t1 = __ldg(&sc.tris[3 * s + 1]);
-            const float4 t2 = __ldg(&sc.tris[3 * s + 2]);
-            const V3 v0 = xyz(t0), e1 = xyz(t1), e2 = xyz(t2);
-            const V3 pv = cross3(r.d, e2);
-            const float det = dot3(e1, pv);
-            if (det == 0.0f) continue;
-            const float idet = 1.0f / det;
-            const V3 tv = r.o - v0;
-            const float u = dot3(tv, pv) * idet;
-            if (u < 0.0f || u > 1.0f) continue;
-            const V3 qv = cross3(tv, e1);
-            const float v = dot3(r.d, qv) * idet;
-            if (v < 0.0f || u + v > 1.0f) continue;
-            const float t = dot3(e2, qv) * idet;
-            const uint32_t id = fbits(t0.w);
-            if (t > 0.0f && (t < h.t || (t == h.t && id < h.id))) {
-                h.t = t;
-                h.slot = s;
-                h.id = id;
-            }
-        }
+        for (int k = 0; k < count; ++k) intersect_tri(sc, r, h, first + k);
         if (side) h1 = false; else h0 = false;
     }
     if (h0 && h1) {
@@ -111,6 +187,7 @@ __device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, 
 // warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
 // the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
 // Each slot's hit depends only on that slot's ray, so the result is deterministic.
+template <int WIDTH>
 __global__ void __launch_bounds__(kExtendThreads, 4)
 k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
     __shared__ int s_stack[kStack * kExtendThreads];
@@ -138,10 +215,12 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
                     idx = my;
                     const float4 o4 = cur.o[idx];
                     // a batched render starts each ray at the root of its job's scene
-                    const int root =
-                        jobs.job ? __ldg(&jobs.job[job_of_pixel(jobs.job, jobs.n,
-                                                                __float_as_uint(o4.w))].root)
-                                 : 0;
+                    int root = 0;
+                    if (jobs.job) {
+                        const JobDev* J =
+                            jobs.job + job_of_pixel(jobs.job, jobs.n, __float_as_uint(o4.w));
+                        root = WIDTH == 4 ? __ldg(&J->root4) : __ldg(&J->root);
+                    }
                     ray_init(ray, xyz(o4), xyz(cur.d[idx]), root, h);
                 } else {
                     exhausted = true;
@@ -152,7 +231,8 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
         if (idx < 0) continue;
         bool done = false;
         for (int step = 0; step < kSteps && !done; ++step)
-            done = visit_node(sc, ray, h, stk, kExtendThreads);
+            done = WIDTH == 4 ? visit_node4(sc, ray, h, stk, kExtendThreads)
+                              : visit_node(sc, ray, h, stk, kExtendThreads);
         if (!done) continue;
         w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
         idx = -1;
@@ -163,15 +243,22 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
 
 int extend_block_threads() { return kExtendThreads; }
 
+int trace_stack_entries() { return kStack; }
+
 int max_blocks_trace() {
-    int nb = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, kExtendThreads, 0);
+    int n2 = 1, n4 = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_trace<2>, kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n4, k_trace<4>, kExtendThreads, 0);
+    const int nb = n2 < n4 ? n2 : n4;
     return nb < 1 ? 1 : nb;
 }
 
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
                   const JobWork& jobs, cudaStream_t s) {
-    k_trace<<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+    if (sc.nodes4)
+        k_trace<4><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+    else
+        k_trace<2><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
 }
 
 }  // namespace nrrs

@@ -10,6 +10,7 @@ namespace nrrs {
 
 struct SceneView {
     const float4* nodes;  // 4 float4 per node (bvh.cpp)
+    const float4* nodes4; // four-wide tree, 8 float4 per node; NULL = traverse the BVH2
     const float4* tris;   // 3 float4 per triangle, BVH order
     const nrrs_material* mats;
     float lo[3];          // scene box, for the position feature
@@ -79,8 +80,8 @@ struct JobDev {
     long long pixel_base, prim_base;
     long long prims;     // W * H * spp; the job's budget is C_j = cap_factor * prims
     int W, H, spp, D;
-    int root;            // BVH root node of the job's scene
-    int pad;
+    int root;            // BVH2 root node of the job's scene
+    int root4;           // four-wide root node (when the batch has a four-wide tree)
     float lo[3], inv_ext[3];  // the job's scene box (position feature)
     CamView cam;
 };
@@ -129,6 +130,7 @@ enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFact
 int extend_block_threads();
 int split_block_threads();
 int max_blocks_trace();  // resident blocks per SM
+int trace_stack_entries();  // traversal stack size per ray
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
                         long long P, DevStats* st, cudaStream_t s);

@@ -39,6 +39,7 @@ EXPORTED = [
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
     "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
+    "nrrs_set_traversal",
 ]
 
 
@@ -193,6 +194,7 @@ def _load():
         "nrrs_create_batch": ([P, I32, I32, P], I32),
         "nrrs_render_batch": ([P, I32, P, P, P, P, P, P, P], I32),
         "nrrs_batch_info": ([P, P, P, P], I32),
+        "nrrs_set_traversal": ([P, I32], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -294,6 +296,10 @@ def nrrs_batch_info(batch):
     base = np.zeros(max(n.value, 1), dtype=np.int64)
     _check(_lib.nrrs_batch_info(batch, None, base.ctypes.data, None))
     return n.value, base[:n.value], total.value
+
+
+def nrrs_set_traversal(scene, width):
+    _check(_lib.nrrs_set_traversal(scene, width))
 
 
 def nrrs_destroy_scene(scene):
@@ -558,6 +564,9 @@ class Scene:
 
     def tune(self, precision=32, stream=None):
         return nrrs_tune_rrsnet(self.handle, precision, stream)
+
+    def set_traversal(self, width):
+        nrrs_set_traversal(self.handle, width)
 
     def train_step(self, stream=None, **opts):
         return nrrs_train_step(self.handle, TrainOpts.defaults(**opts), stream)

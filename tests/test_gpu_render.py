@@ -304,3 +304,27 @@ def test_graph_captured_train_step_matches(nrrs):
     for a, b in zip(out[0][0], out[1][0]):
         assert a["loss_rrsnet"] == b["loss_rrsnet"] and a["segments"] == b["segments"]
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("scene_name", ["box", "occluded", "ggx", "three_rooms"])
+def test_four_wide_traversal_equals_bvh2(nrrs, scene_name):
+    """The four-wide tree collapsed from the BVH2 finds the same closest hits (same
+    triangle test, same tie rule), so whole renders are bit-identical."""
+    s = {"box": lambda: I.box_scene(2), "occluded": lambda: I.occluded_room(1),
+         "ggx": lambda: I.icosphere_room(4, min_triangles=20000, subdiv=2),
+         "three_rooms": lambda: I.three_rooms(1)}[scene_name]()
+    P = I.rrsnet_init_params(3)
+    W, H, spp, D = (128, 96, 8, 12) if scene_name != "three_rooms" else (320, 180, 4, 16)
+    out = []
+    for width in (2, 4):
+        sc = nrrs.Scene(s)
+        sc.set_params(P)
+        sc.set_traversal(width)
+        for mode in (nrrs.RRS_NONE, nrrs.RRS_NET):
+            img, st = sc.render(W, H, spp, D, mode, frame=1)
+            torch.cuda.synchronize()
+            out.append((img.cpu().numpy(), st))
+        sc.close()
+    for (a, sa), (b, sb) in zip(out[:2], out[2:]):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(sa["live"], sb["live"])
