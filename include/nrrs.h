@@ -349,6 +349,10 @@ typedef struct nrrs_train_opts {
                                               of the paper's denoiser; 0 = off        [2] */
     int32_t graph;                         /* record the training frame through a CUDA
                                               graph (nrrs_render_opts.graph)          [0] */
+    int32_t batch_size;                    /* training vertices per step, drawn from the
+                                              recorded frame by systematic sampling
+                                              with a per-step offset; 0 = 2^19
+                                              (Sec. 4 "Training")                     [0] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {

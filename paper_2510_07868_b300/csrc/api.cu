@@ -1278,6 +1278,7 @@ nrrs_status mlp_grad_impl(nrrs_scene* scene, int32_t n_out, bool at_q, const flo
     TrainBatch b{};
     b.D = 1;
     b.total = n;
+    b.batch = n;
     b.net_mask = 1u;
     CK(launch_mlp_grad_given(n_out, at_q, a, r, b, t.part_blocks, t.part, t.loss_part, s));
     launch_reduce_grad(t.part, t.part_blocks, P, d_grad, s);
@@ -1406,7 +1407,8 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     ro.graph = o.graph;
     nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, o.max_depth, NRRS_RRS_NET, ro);
     if (rc != NRRS_OK) return rc;
-    if (o.warmup_steps < 0 || !(o.eps > 0.0f) || !(o.ema_decay >= 0.0f && o.ema_decay < 1.0f))
+    if (o.warmup_steps < 0 || !(o.eps > 0.0f) || !(o.ema_decay >= 0.0f && o.ema_decay < 1.0f) ||
+        o.batch_size < 0)
         return fail(NRRS_ERR_INVALID_ARG, "bad training options");
     DeviceGuard g(scene->device);
     if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
@@ -1443,6 +1445,17 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     }
     b.offset[D] = off;
     b.total = off;
+    // Sec. 4 "Training": batches of 2^19 vertices, drawn by systematic sampling with an
+    // offset that changes every step (a hash of the seeds and the step)
+    const long long bs = o.batch_size > 0 ? o.batch_size : (1ll << 19);
+    b.batch = std::min(off, bs);
+    {
+        uint64_t z = ((uint64_t)o.seed_lo << 32 | o.seed_hi) ^ (0x9E3779B97F4A7C15ull * (t.step + 1));
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;  // splitmix64 finaliser
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        b.phase = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
     CK(cudaMemcpy(t.Fd, Fh, sizeof(float) * D, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(t.Fnd, Fnh, sizeof(float) * D, cudaMemcpyHostToDevice));
 

@@ -102,8 +102,9 @@ __global__ void k_ref_fold(float* ref, const float* rgb, long long n3, int count
 
 // k_i: trainable samples (recorded q_orig > 0 at a network depth) of every pixel.
 __global__ void k_count_samples(RecordView r, TrainBatch b, int* k) {
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < b.total;
-         u += (long long)gridDim.x * blockDim.x) {
+    for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < b.batch;
+         slot += (long long)gridDim.x * blockDim.x) {
+        const long long u = batch_vertex(b, slot);
         int d = 0;
         while (d + 1 < b.D && b.offset[d + 1] <= u) ++d;
         if (!((b.net_mask >> d) & 1u)) continue;
@@ -250,10 +251,13 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
     for (int e = 0; e < 8; ++e) g2[e] = g3[e] = 0.0f;
     g4[0] = g4[1] = 0.0f;
     double loss = 0.0;
-    const long long tiles = (b.total + kTile - 1) / kTile;
+    const long long tiles = (b.batch + kTile - 1) / kTile;
     __syncthreads();
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long long u = tile * kTile + tid;
+        const long long slot = tile * kTile + tid;
+        // recorded vertex of this training slot (given rows: the slot itself)
+        const long long u = MODE == kTrainGiven || MODE == kTrainGivenQ ? slot
+                            : slot < b.batch ? batch_vertex(b, slot) : b.total;
         // ---- forward of this thread's sample
         float x[kNF];
         bool active = false;

@@ -25,10 +25,21 @@ struct RecordView {
 // The training batch: every slot of every depth, concatenated in depth order.
 struct TrainBatch {
     long long offset[kMaxDepth + 1];  // offset[d] = first batch index of depth d
-    long long total;
+    long long total;    // recorded vertices of the frame
+    long long batch;    // training slots: min(total, batch size)
+    double phase;       // systematic-sampling offset in [0, 1)
     int D;
     uint32_t net_mask;  // depths whose slots carry RRSNet features
 };
+
+// Vertex of training slot i: systematic sampling of `batch` of the `total` recorded
+// vertices with a random offset (every vertex has inclusion probability batch / total;
+// the identity when batch == total).
+__host__ __device__ __forceinline__ long long batch_vertex(const TrainBatch& b, long long i) {
+    if (b.batch >= b.total) return i;
+    const long long u = (long long)(((double)i + b.phase) * ((double)b.total / (double)b.batch));
+    return u < b.total ? u : b.total - 1;
+}
 
 // kTrainGiven: plain inputs in RecordView::feat ([n][16]) and given output gradients in
 // TrainArgs::gin ([n][n_out]); the kernel returns sum_s d(gin_s . out_s)/dW.

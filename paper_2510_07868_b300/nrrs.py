@@ -97,14 +97,15 @@ class TrainOpts(C.Structure):
                 ("lr_statnet", C.c_float), ("gamma1", C.c_float), ("gamma2", C.c_float),
                 ("gamma3", C.c_float), ("eps", C.c_float), ("ema_decay", C.c_float),
                 ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p), ("alpha_mix", C.c_float),
-                ("error_filter_radius", C.c_int32), ("graph", C.c_int32)]
+                ("error_filter_radius", C.c_int32), ("graph", C.c_int32),
+                ("batch_size", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(width=256, height=256, spp=2, max_depth=16, seed_lo=1, seed_hi=0, frame=0,
                 warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
                 gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None,
-                alpha_mix=0.5, error_filter_radius=2, graph=0)
+                alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o

@@ -260,3 +260,27 @@ def test_rrsnet_autograd_trains(nrrs):
         losses.append(loss.item())
     assert losses[-1] < 0.1 * losses[0]
     sc.close()
+
+
+def test_train_step_batch_subsampling(nrrs):
+    """Sec. 4's fixed training batch: with batch_size below the recorded vertex count the
+    step trains on batch_size systematic samples of the frame's vertices, so the count
+    of trainable samples among them follows the frame's trainable fraction; the warm-up
+    regression still converges on the smaller batches."""
+    kw = dict(width=64, height=64, spp=4, max_depth=8)
+    a = nrrs.Scene(I.box_scene(1))
+    a.set_params(I.rrsnet_init_params(1))
+    full = a.train_step(**kw)
+    frac = full["samples"] / full["segments"]
+    assert full["segments"] > 20_000
+    b = nrrs.Scene(I.box_scene(1))
+    b.set_params(I.rrsnet_init_params(1))
+    losses = []
+    for k in range(30):
+        st = b.train_step(batch_size=5000, warmup_steps=100, lr_rrsnet=3e-3, **kw)
+        assert st["fallback"] == 0 and st["samples"] <= 5000
+        assert abs(st["samples"] - 5000 * frac) <= 0.05 * 5000 * frac + 20, (st["samples"], frac)
+        losses.append(st["loss_rrsnet"])
+    assert losses[-1] < 0.2 * losses[0]
+    a.close()
+    b.close()
