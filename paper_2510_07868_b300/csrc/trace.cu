@@ -138,55 +138,43 @@ __device__ __forceinline__ bool visit_node4(const SceneView& sc, Ray& r, Hit& h,
     return false;
 }
 
-// Visits one BVH2 node of the closest-hit query along o + t d (t > 0): both child boxes
-// are tested, leaf children are intersected at once (Moller-Trumbore), inner children
-// are visited near-first.  Equal distances go to the lower original triangle index, so
-// the answer does not depend on the visiting order.  Returns true when the query ends.
-__device__ __forceinline__ bool visit_node(const SceneView& sc, Ray& r, Hit& h, int* stk,
-                                           int stride) {
+// Inner-node step of the postponed-leaf traversal: tests both child boxes; leaf children
+// hit become the lane's pending leaves (tested later, together with the other lanes'),
+// inner children are entered near-first.  node < 0 afterwards: nothing left to visit.
+__device__ __forceinline__ void visit_inner(const SceneView& sc, Ray& r, const Hit& h, int* stk,
+                                            int stride, int* leaf0, int* cnt0, int* leaf1,
+                                            int* cnt1) {
     const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
     const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
     const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
     const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
-    float lx = fmaf(a.x, r.inv.x, -r.oi.x), hx = fmaf(a.y, r.inv.x, -r.oi.x);
-    float ly = fmaf(a.z, r.inv.y, -r.oi.y), hy = fmaf(a.w, r.inv.y, -r.oi.y);
-    float lz = fmaf(c.x, r.inv.z, -r.oi.z), hz = fmaf(c.y, r.inv.z, -r.oi.z);
-    const float t0n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-    const float t0f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-    bool h0 = t0n <= t0f;
-    lx = fmaf(b.x, r.inv.x, -r.oi.x); hx = fmaf(b.y, r.inv.x, -r.oi.x);
-    ly = fmaf(b.z, r.inv.y, -r.oi.y); hy = fmaf(b.w, r.inv.y, -r.oi.y);
-    lz = fmaf(c.z, r.inv.z, -r.oi.z); hz = fmaf(c.w, r.inv.z, -r.oi.z);
-    const float t1n = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.0f));
-    const float t1f = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), h.t));
-    bool h1 = t1n <= t1f;
+    float t0n, t1n;
+    bool h0 = slab(r, h.t, a.x, a.y, a.z, a.w, c.x, c.y, &t0n);
+    bool h1 = slab(r, h.t, b.x, b.y, b.z, b.w, c.z, c.w, &t1n);
     int c0 = e.x, c1 = e.y;
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-        const int code = side ? c1 : c0;
-        const bool hitbox = side ? h1 : h0;
-        if (!hitbox || code >= 0) continue;
-        const int first = ~code, count = side ? e.w : e.z;
-        for (int k = 0; k < count; ++k) intersect_tri(sc, r, h, first + k);
-        if (side) h1 = false; else h0 = false;
-    }
+    if (h0 && c0 < 0) { *leaf0 = ~c0; *cnt0 = e.z; h0 = false; }
+    if (h1 && c1 < 0) { *leaf1 = ~c1; *cnt1 = e.w; h1 = false; }
     if (h0 && h1) {
         if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
         if (r.sp < kStack) stk[(r.sp++) * stride] = c1;
         r.node = c0;
-        return false;
+    } else if (h0) {
+        r.node = c0;
+    } else if (h1) {
+        r.node = c1;
+    } else {
+        r.node = r.sp == 0 ? -1 : stk[(--r.sp) * stride];
     }
-    if (h0) { r.node = c0; return false; }
-    if (h1) { r.node = c1; return false; }
-    if (r.sp == 0) return true;
-    r.node = stk[(--r.sp) * stride];
-    return false;
 }
 
 // Extension of depth `depth`, part 1: the closest hit of every live ray.  Persistent
 // warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
-// the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.
-// Each slot's hit depends only on that slot's ray, so the result is deterministic.
+// the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.  On
+// the BVH2 the leaf tests are postponed (Aila & Laine's "while-while"): lanes descend
+// through inner nodes until every lane of the warp holds a leaf or has finished, then
+// test their leaves together.  Each slot's hit depends only on that slot's ray (the
+// closest hit with the lower-index tie rule does not depend on the visiting order), so
+// the result is deterministic.
 template <int WIDTH>
 __global__ void __launch_bounds__(kExtendThreads, 4)
 k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
@@ -228,12 +216,26 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
             }
         }
         if (__all_sync(0xffffffffu, idx < 0)) break;
-        if (idx < 0) continue;
-        bool done = false;
-        for (int step = 0; step < kSteps && !done; ++step)
-            done = WIDTH == 4 ? visit_node4(sc, ray, h, stk, kExtendThreads)
-                              : visit_node(sc, ray, h, stk, kExtendThreads);
-        if (!done) continue;
+        if (WIDTH == 4) {
+            if (idx < 0) continue;
+            bool done = false;
+            for (int step = 0; step < kSteps && !done; ++step)
+                done = visit_node4(sc, ray, h, stk, kExtendThreads);
+            if (!done) continue;
+        } else {
+            // every lane of the warp runs the step loop (the vote needs all of them)
+            int leaf0 = -1, cnt0 = 0, leaf1 = -1, cnt1 = 0;
+            for (int step = 0; step < kSteps; ++step) {
+                const bool go = idx >= 0 && ray.node >= 0 && leaf0 < 0 && leaf1 < 0;
+                if (go) visit_inner(sc, ray, h, stk, kExtendThreads, &leaf0, &cnt0, &leaf1, &cnt1);
+                const bool more = idx >= 0 && ray.node >= 0 && leaf0 < 0 && leaf1 < 0;
+                if (!__any_sync(0xffffffffu, more)) break;
+            }
+            if (idx < 0) continue;
+            for (int k = 0; k < cnt0 && leaf0 >= 0; ++k) intersect_tri(sc, ray, h, leaf0 + k);
+            for (int k = 0; k < cnt1 && leaf1 >= 0; ++k) intersect_tri(sc, ray, h, leaf1 + k);
+            if (ray.node >= 0) continue;
+        }
         w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
         idx = -1;
     }
