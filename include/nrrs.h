@@ -47,6 +47,8 @@ typedef enum nrrs_status {
 #define NRRS_STATUS_OVERFLOW_DROPPED 0x1u
 #define NRRS_STATUS_NONFINITE 0x2u
 #define NRRS_STATUS_TIMEOUT 0x4u
+#define NRRS_STATUS_HEUR_FALLBACK 0x8u /* NET depths used the heuristic this frame (the
+                                          last training step fell back)               */
 
 /* How the RRS factor q of a path vertex is chosen (Sec. 2 "Unified RRS Framework",
  * Sec. 3.1 normalization, Sec. 3.3 Mix-Depth). */
@@ -254,6 +256,10 @@ NRRS_API nrrs_status nrrs_get_rrsnet_params(nrrs_scene* scene, float* params, in
  * downscale only, Sec. 4 "Compromise").  Writes the frame estimate, the mean over spp
  * of the deposited radiance, to d_rgb (device [H][W][3] float).
  * Limits: 1 <= max_depth <= NRRS_MAX_DEPTH, W*H*spp*cap_factor < 2^31.
+ * A network factor that comes out non-finite takes the throughput heuristic's factor
+ * (the method degrades to plain heuristic normalised RRS for that vertex), and after a
+ * training step that fell back the next frame uses the heuristic at every network depth
+ * (NRRS_STATUS_HEUR_FALLBACK).
  * Errors: INVALID_ARG (bad sizes, mode, NULL d_rgb); OOM; CUDA.  Overflow drops and
  * non-finite factors are not errors: they are counted in stats (status_bits). */
 NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,

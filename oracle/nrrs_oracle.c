@@ -481,6 +481,7 @@ typedef struct {
     int32_t tri;            /* -1 = miss */
     double p[3], n[3];      /* hit point, shading normal facing -d */
     double q;               /* q_orig (0 = terminate) */
+    int net_fallback;       /* the network's factor was non-finite: q is the heuristic's */
 } or_hitrec;
 
 static double or_lum(const double t[3]) { return 0.2126 * t[0] + 0.7152 * t[1] + 0.0722 * t[2]; }
@@ -568,6 +569,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             double t;
             v->tri = or_intersect(s, p->o, p->d, &t);
             v->q = 0.0;
+            v->net_fallback = 0;
             if (v->tri < 0) continue;
             v3 o = mk(p->o[0], p->o[1], p->o[2]), d = mk(p->d[0], p->d[1], p->d[2]);
             v3 hp = add(o, scl(d, t));
@@ -590,19 +592,20 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 default: method = (int)((a->gate >> (2 * (depth - 1))) & 3u); break;
             }
             double q;
+            /* the throughput heuristic: HEUR factors, and the stand-in for a network
+             * factor that comes out non-finite */
+            double heur = or_lum(p->t);
+            if (a->pixel_ref) {
+                const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
+                double den = fmax((r[0] + r[1] + r[2]) / 3.0, eps_I);
+                heur = den > 0.0 ? fmin(heur / den, a->q_max) : a->q_max;
+            }
             if (method == -1 || method == OR_GATE_FIXED) {
                 q = 1.0;
             } else if (method == -2) {
                 q = fmin(1.0, or_lum(p->t));
             } else if (method == OR_GATE_HEUR) {
-                double l = or_lum(p->t);
-                if (!a->pixel_ref) {
-                    q = l;
-                } else {
-                    const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
-                    double den = fmax((r[0] + r[1] + r[2]) / 3.0, eps_I);
-                    q = den > 0.0 ? fmin(l / den, a->q_max) : a->q_max;
-                }
+                q = heur;
             } else {
                 double x[OR_NF];
                 for (int c = 0; c < 3; ++c) {
@@ -615,6 +618,10 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 x[12] = (double)depth / (double)D;
                 for (int c = 0; c < 3; ++c) x[13 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
                 q = or_mlp_forward(a->params, x, NULL, NULL, NULL);
+                if (!(isfinite(q) && q >= 0.0)) {  /* a failing network: the heuristic */
+                    q = heur;
+                    v->net_fallback = 1;
+                }
             }
             v->q = q;
         }
@@ -633,8 +640,10 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                     if (a->rec) a->rec[((int64_t)(depth - 1) * cap + i) * OR_REC + 3 + c] = p->t[c] * m->Le[c];
                 }
         }
-        /* non-finite factors terminate their path */
+        /* non-finite network factors took the heuristic's; any other non-finite factor
+         * terminates its path */
         for (int64_t i = 0; i < n; ++i) {
+            if (vx[i].net_fallback) st->nonfinite++;
             if (!(isfinite(vx[i].q) && vx[i].q >= 0.0)) {
                 vx[i].q = 0.0;
                 st->nonfinite++;

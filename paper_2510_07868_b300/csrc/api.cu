@@ -191,6 +191,8 @@ struct nrrs_scene {
     // each depth of the next frame (scaled by its primary count)
     long long last_live[NRRS_MAX_DEPTH] = {};
     long long last_P = 0;
+    // the last training step fell back: the next render uses the heuristic at NET depths
+    bool heur_next = false;
     // running mean of earlier frames (HEUR reference), [npix * 3]
     float* ref_mean = nullptr;
     int ref_count = 0;
@@ -636,10 +638,17 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     const long long npix = batch ? scene->batch_npix : (long long)width * height;
     const long long P = batch ? scene->batch_P : npix * spp;
     const long long C = P * o.cap_factor;
-    bool uses_net = rrs_mode == NRRS_RRS_NET;
-    if (rrs_mode == NRRS_RRS_NET_MIX)
-        for (int d = 1; d <= max_depth; ++d)
-            if (factor_kind(rrs_mode, o.gate, d) == kFactorNet) uses_net = true;
+    // after a failed training step the network sits out one frame: its depths take the
+    // throughput heuristic (plain heuristic normalised RRS)
+    const bool heur_frame = scene->heur_next && !rec &&
+                            (rrs_mode == NRRS_RRS_NET || rrs_mode == NRRS_RRS_NET_MIX);
+    auto kind_of = [&](int d) {
+        const int k = factor_kind(rrs_mode, o.gate, d);
+        return heur_frame && k == kFactorNet ? (int)kFactorHeur : k;
+    };
+    bool uses_net = false;
+    for (int d = 1; d <= max_depth; ++d)
+        if (kind_of(d) == kFactorNet) uses_net = true;
     nrrs_status rc = ensure_workspace(scene, C, npix, uses_net);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
@@ -655,10 +664,10 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     }
 
     // reference image for HEUR factors
-    bool uses_heur = rrs_mode == NRRS_RRS_HEUR_NORM;
-    if (rrs_mode == NRRS_RRS_NET_MIX)
-        for (int d = 1; d <= max_depth; ++d)
-            if (factor_kind(rrs_mode, o.gate, d) == kFactorHeur) uses_heur = true;
+    // HEUR factors, and the repair of non-finite network factors, read the reference
+    bool uses_heur = uses_net;
+    for (int d = 1; d <= max_depth; ++d)
+        if (kind_of(d) == kFactorHeur) uses_heur = true;
     if (o.reset_ref || scene->ref_w != width || scene->ref_h != height) {
         scene->ref_count = 0;
         scene->ref_w = width;
@@ -736,7 +745,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         RenderParams r = rp;
         int cur = 0;
         for (int d = 1; d <= max_depth; ++d) {
-            const int kind = factor_kind(rrs_mode, o.gate, d);
+            const int kind = kind_of(d);
             if (rec) {  // this depth's factors, deposits and features go straight to the record
                 const size_t off = (size_t)(d - 1) * rec->C;
                 w.q = rec->q + off;
@@ -754,10 +763,10 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 TIMED(NRRS_STAGE_RRSNET,
                       launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
                                     &w.st->live[d - 1], 0, w.q, 1, w.st, &w.st->status, s));
-                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, d, s));
+                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             }
             if (batch) {  // Eq. F_norm per job
-                TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q_jobs(w, r, d, s));
+                TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q_jobs(w, q[cur], r, d, s));
                 TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_jobs(w, r, d, normalized, s));
             } else {
                 TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
@@ -793,7 +802,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         uint64_t shape = 0;
         const uint64_t sv[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
                                (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
-                               o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile};
+                               o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile,
+                               (uint64_t)heur_frame};
         for (uint64_t v : sv) shape = mix_key(shape, v);
         uint64_t args = shape;
         auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };
@@ -839,6 +849,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         CK(cudaGraphLaunch(ge->exec, s));
     }
     tm.launches += extra_launches;
+    if (heur_frame) scene->heur_next = false;
     if (update) scene->ref_count++;
     if (stats) {
         DevStats h;
@@ -857,7 +868,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         stats->nonfinite = (int64_t)h.nonfinite;
         stats->net_evals = (int64_t)h.net_evals;
         stats->capacity = C;
-        stats->status_bits = h.status;
+        stats->status_bits = h.status | (heur_frame ? NRRS_STATUS_HEUR_FALLBACK : 0u);
         stats->kernel_launches = tm.launches;
         tm.collect(stats);
         for (int d = 0; d < NRRS_MAX_DEPTH; ++d) scene->last_live[d] = d < max_depth ? h.live[d] : 0;
@@ -1536,6 +1547,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         if (t.full_steps > 50 && t.loss_ema > 10.0 * t.loss_min) fallback = 2;
     }
     if (fallback) {  // restore the last good weights and forget the moments
+        scene->heur_next = true;
         CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(t.stat, t.stat_good, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));

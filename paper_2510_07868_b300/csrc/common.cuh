@@ -12,6 +12,9 @@ constexpr int kNF = 16;        // RRSNet input features
 constexpr int kNH = 32;        // RRSNet hidden width (Sec. 4 "Network Architecture")
 constexpr int kNParams = kNH * kNF + 2 * kNH * kNH + kNH;  // 2592
 constexpr float kLeak = 0.01f; // Leaky ReLU slope
+// Marks a vertex whose RRSNet factor came out non-finite during a render; the sum of q
+// that follows replaces it with the throughput heuristic's factor.
+constexpr float kQRepair = -2.0f;
 constexpr float kRayOffset = 1e-4f;
 constexpr uint32_t kLineageStep = 0x9E3779B9u;
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;

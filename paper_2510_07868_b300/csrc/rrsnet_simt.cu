@@ -129,7 +129,7 @@ k_rrsnet_simt(const float* __restrict__ params, const float4* __restrict__ feat,
             float v = out[r];
             ++evals;
             if (!(v >= 0.0f && v <= FLT_MAX)) {
-                v = 0.0f;
+                v = sentinel ? kQRepair : 0.0f;
                 ++nonfinite;
             }
             q[row[r]] = v;

@@ -257,7 +257,7 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         if (active) {
             ++evals;
             if (!(qv >= 0.0f && qv <= FLT_MAX)) {
-                qv = 0.0f;
+                qv = sentinel ? kQRepair : 0.0f;
                 ++nonfinite;
             }
             q[row] = qv;
@@ -466,7 +466,7 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
         if (active) {
             ++evals;
             if (bad || !(qv >= 0.0f && qv <= FLT_MAX)) {
-                qv = 0.0f;
+                qv = sentinel ? kQRepair : 0.0f;
                 ++nonfinite;
             }
             q[row] = qv;

@@ -32,6 +32,29 @@ __device__ __forceinline__ float boxcox(float t, float lambda) {
     return (powf(t, lambda) - 1.0f) / lambda;
 }
 
+// The throughput heuristic (HEUR): q = min(lum(t) / max(I_px, eps_I), q_max) with I_px the
+// mean over RGB of the reference pixel; q = lum(t) before any reference exists.
+__device__ __forceinline__ float heur_factor(float4 t4, const RenderParams& rp, uint32_t pix,
+                                            int has_ref, float eps_I) {
+    const float l = lum(t4.x, t4.y, t4.z);
+    if (!has_ref) return l;
+    const float* rr = rp.ref + 3 * (size_t)pix;
+    const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
+    return den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
+}
+
+// A vertex whose RRSNet factor was non-finite (kQRepair) takes the heuristic's factor, so
+// a failing network degrades to plain heuristic normalised RRS instead of ending paths.
+__device__ __forceinline__ float repaired_q(const WorkView& w, QueueView cur,
+                                           const RenderParams& rp, long long i, float eps_I) {
+    float q = w.q[i];
+    if (q != kQRepair) return q;
+    q = heur_factor(cur.t[i], rp, fbits(w.dep[i].w), w.st->has_ref, eps_I);
+    if (!(q >= 0.0f && q <= FLT_MAX)) q = 0.0f;
+    w.q[i] = q;
+    return q;
+}
+
 // ------------------------------------------------------------------ RRS split rule
 // Eq. rrs_factor with the factor scaled by F (Eq. q_norm / q_norm_rate), decided in
 // FP32: q_used = F * q (one rounding), X = floor(q_used) + [U < q_used - floor(q_used)].
@@ -249,14 +272,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                 } else if (KIND == kFactorPlain) {
                     q = fminf(1.0f, lum(t4.x, t4.y, t4.z));
                 } else if (KIND == kFactorHeur) {
-                    const float l = lum(t4.x, t4.y, t4.z);
-                    if (!has_ref) {
-                        q = l;
-                    } else {
-                        const float* rr = rp.ref + 3 * (size_t)fbits(o4.w);
-                        const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, epsI);
-                        q = den > 0.0f ? fminf(l / den, rp.q_max) : rp.q_max;
-                    }
+                    q = heur_factor(t4, rp, fbits(o4.w), has_ref, epsI);
                 } else {
                     const V3 p = xyz(o4) + d * hh.x;
                     const V3 ns = front ? ng : ng * -1.0f;
@@ -293,14 +309,17 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
     }
 }
 
-// FP64 partial sums of q over a fixed grid-stride assignment, so Sigma q is reproducible.
-__global__ void __launch_bounds__(256) k_sum_q(WorkView w, int depth) {
+// FP64 partial sums of q over a fixed grid-stride assignment, so Sigma q is reproducible;
+// non-finite network factors are replaced by the heuristic's on the way.
+__global__ void __launch_bounds__(256) k_sum_q(WorkView w, QueueView cur, RenderParams rp,
+                                               int depth) {
     __shared__ double sh[32];
     const long long n = w.st->live[depth - 1];
+    const float eps_I = w.st->eps_I;
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        s += (double)w.q[i];
+        s += (double)repaired_q(w, cur, rp, i, eps_I);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) w.part[blockIdx.x] = s;
 }
@@ -340,8 +359,8 @@ __device__ __forceinline__ void block_range(long long n, int* tiles_out, long lo
 // Eq. F_norm per job: the queue holds the jobs one after another (it stays sorted by
 // global pixel), so each block's contiguous slot range meets few jobs; the block writes
 // an FP64 partial sum of q and a slot count for every job (zero where it meets none).
-__global__ void __launch_bounds__(kSplitThreads) k_sum_q_jobs(WorkView w, RenderParams rp,
-                                                              int depth) {
+__global__ void __launch_bounds__(kSplitThreads) k_sum_q_jobs(WorkView w, QueueView cur,
+                                                              RenderParams rp, int depth) {
     __shared__ double shd[32];
     __shared__ unsigned long long shc[32];
     const JobWork& J = rp.jobs;
@@ -361,6 +380,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_sum_q_jobs(WorkView w, Render
             part[j] = 0.0;
             cnt[j] = 0;
         }
+    for (long long i = begin + threadIdx.x; i < end; i += blockDim.x)
+        if (w.q[i] == kQRepair)
+            repaired_q(w, cur, rp, i,
+                       J.eps_I[job_of_pixel(J.job, J.n, fbits(w.dep[i].w))]);
+    __syncthreads();
     for (int j = j0; j <= j1; ++j) {
         const long long pb = J.job[j].pixel_base;
         const long long pe = j + 1 < J.n ? J.job[j + 1].pixel_base : 0x7FFFFFFFFFFFll;
@@ -768,8 +792,9 @@ void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& 
     }
 }
 
-void launch_sum_q(const WorkView& w, int depth, cudaStream_t s) {
-    k_sum_q<<<w.grid_red, 256, 0, s>>>(w, depth);
+void launch_sum_q(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                  cudaStream_t s) {
+    k_sum_q<<<w.grid_red, 256, 0, s>>>(w, cur, rp, depth);
 }
 
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
@@ -801,8 +826,9 @@ void launch_ref_prepare_jobs(const RenderParams& rp, float eps_rel, cudaStream_t
     k_ref_prepare_jobs<<<rp.jobs.n, 256, 0, s>>>(rp.ref, rp, eps_rel);
 }
 
-void launch_sum_q_jobs(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
-    k_sum_q_jobs<<<w.grid_red, kSplitThreads, 0, s>>>(w, rp, depth);
+void launch_sum_q_jobs(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                       cudaStream_t s) {
+    k_sum_q_jobs<<<w.grid_red, kSplitThreads, 0, s>>>(w, cur, rp, depth);
 }
 
 void launch_normalize_jobs(const WorkView& w, const RenderParams& rp, int depth, int normalized,

@@ -139,7 +139,8 @@ void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int dep
                   const JobWork& jobs, cudaStream_t s);
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s);
-void launch_sum_q(const WorkView& w, int depth, cudaStream_t s);
+void launch_sum_q(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                  cudaStream_t s);
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,
                             cudaStream_t s);
 void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,
@@ -151,7 +152,8 @@ void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, floa
                      int update_ref, long long npix, cudaStream_t s);
 // Batched renders: per-job HEUR floors, per-job sums of q and normalisation factors.
 void launch_ref_prepare_jobs(const RenderParams& rp, float eps_rel, cudaStream_t s);
-void launch_sum_q_jobs(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
+void launch_sum_q_jobs(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                       cudaStream_t s);
 void launch_normalize_jobs(const WorkView& w, const RenderParams& rp, int depth, int normalized,
                            cudaStream_t s);
 void launch_camera_jobs(const RenderParams& rp, long long P, QueueView out, cudaStream_t s);

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of devi
                 4: "timeout", 5: "non-finite", 6: "overflow dropped", 7: "unsupported"}
 RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
 GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
-STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
+STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_HEUR_FALLBACK = 1, 2, 4, 8
 MAX_DEPTH = 32
 STAGES = 10
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",

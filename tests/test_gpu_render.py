@@ -171,13 +171,27 @@ def test_determinism(nrrs):
     np.testing.assert_array_equal(sa["live"], sb["live"])
 
 
-def test_nonfinite_weights_terminate_paths(nrrs):
+@pytest.mark.parametrize("precision", [32, 16, 8])
+def test_nonfinite_network_falls_back_to_heuristic(nrrs, precision):
+    """Non-finite network factors take the throughput heuristic's factor: with an
+    infinite output layer the NET render is the HEUR_NORM render, bit for bit, and every
+    network evaluation is reported non-finite."""
     s = I.box_scene(1)
     P = I.rrsnet_init_params(1)
     P[2560:] = np.inf
-    img, st, _ = gpu_render(nrrs, s, 16, 16, 1, 4, nrrs.RRS_NET, params=P, trace=False)
-    assert st["nonfinite"] == 256 and st["status_bits"] & nrrs.STATUS_NONFINITE
-    assert st["live"][1:].sum() == 0 and np.all(np.isfinite(img))
+    ref = torch.from_numpy((np.full((16 * 16, 3), 0.3, dtype=np.float32) *
+                            np.linspace(0.5, 1.5, 256, dtype=np.float32)[:, None])).cuda()
+    sc = nrrs.Scene(s)
+    sc.set_params(P)
+    kw = dict(d_pixel_ref=ref.data_ptr(), update_ref=0, precision=precision)
+    net, st = sc.render(16, 16, 2, 5, nrrs.RRS_NET, **kw)
+    heur, sth = sc.render(16, 16, 2, 5, nrrs.RRS_HEUR_NORM, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(net, heur)
+    np.testing.assert_array_equal(st["live"], sth["live"])
+    assert st["nonfinite"] == st["net_evals"] > 0
+    assert st["status_bits"] & nrrs.STATUS_NONFINITE and np.all(np.isfinite(net.cpu().numpy()))
+    sc.close()
 
 
 def test_full_size_occluded_room_sampled_pixels(nrrs):

@@ -200,6 +200,12 @@ def test_train_step_nonfinite_weights_fall_back(nrrs):
     st = sc.train_step(width=32, height=32, spp=2, max_depth=6)
     assert st["fallback"] == 1 and st["step"] == 1
     np.testing.assert_array_equal(nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET_TRAIN), good)
+    # the next frame renders with the heuristic at the network's depths, the one after
+    # with the network again
+    _, r1 = sc.render(32, 32, 2, 6, nrrs.RRS_NET)
+    assert r1["status_bits"] & nrrs.STATUS_HEUR_FALLBACK and r1["net_evals"] == 0
+    _, r2 = sc.render(32, 32, 2, 6, nrrs.RRS_NET)
+    assert not r2["status_bits"] & nrrs.STATUS_HEUR_FALLBACK and r2["net_evals"] > 0
     sc.close()
 
 

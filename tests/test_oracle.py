@@ -444,12 +444,21 @@ def test_downscale_only_normalisation():
     assert np.all(st["F"] == 1.0)
 
 
-def test_nonfinite_factors_terminate():
+def test_nonfinite_network_factors_fall_back_to_the_heuristic():
+    """A network whose factors come out non-finite degrades to plain heuristic normalised
+    RRS: the NET render equals the HEUR_NORM render exactly, with every network
+    evaluation counted as non-finite."""
     s = I.box_scene(1)
     P = I.rrsnet_init_params(1).astype(np.float64)
     P[2560:] = np.inf
-    img, st, _ = oracle.render(s, 8, 8, 1, 4, oracle.MODE_NET, params=P)
-    assert st["nonfinite"] == 64 and st["live"][0] == 64 and st["live"][1:].sum() == 0
+    ref = np.full((8 * 8, 3), 0.3) * np.linspace(0.5, 1.5, 64)[:, None]
+    net, st, _ = oracle.render(s, 8, 8, 2, 5, oracle.MODE_NET, params=P, pixel_ref=ref)
+    heur, sth, _ = oracle.render(s, 8, 8, 2, 5, oracle.MODE_HEUR_NORM, pixel_ref=ref)
+    np.testing.assert_array_equal(net, heur)
+    np.testing.assert_array_equal(st["live"], sth["live"])
+    # every vertex that was not a miss, black or at the last depth asked the network
+    assert st["nonfinite"] > 0 and sth["nonfinite"] == 0
+    assert st["nonfinite"] <= st["live"][:4].sum()
 
 
 def test_forced_F_subset_equals_whole_frame():
