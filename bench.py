@@ -596,6 +596,36 @@ def run_ours(args, rank, world, local_rank):
     sc.close()
 
 
+def run_rrsnet_only(args):
+    """RRSNet inference alone: `warmup` untimed then `steps` timed queries of 2^21 rows."""
+    import torch
+
+    from paper_2510_07868_b300 import inputs as I
+    from paper_2510_07868_b300 import nrrs
+
+    sc = nrrs.Scene(I.box_scene(1))
+    sc.set_params(I.rrsnet_init_params(1))
+    n = 1 << 21
+    feats = torch.from_numpy(I.random_features(n, seed=3)).cuda()
+    q = torch.empty(n, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sc.query(feats, precision=args.rrsnet_only, out=q)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sc.query(feats, precision=args.rrsnet_only, out=q)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    hbm, _, _ = measured_peaks()
+    print(json.dumps({"metric": "RRSNet inference", "precision": args.rrsnet_only, "rows": n,
+                      "ms_per_launch": ms,
+                      "tflops": RRSNET_FLOP_PER_PATH * n / (ms / 1000) / 1e12,
+                      "hbm_frac": 68 * n / (ms / 1000) / 1e9 / hbm}), flush=True)
+    sc.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -610,7 +640,13 @@ def main():
                     help="launch the bounce loop kernel by kernel instead of as a CUDA graph")
     ap.add_argument("--pretrain", type=int, default=PRETRAIN_STEPS,
                     help="untimed online training steps before the timed region")
+    ap.add_argument("--rrsnet-only", type=int, choices=[32, 16, 8], default=0,
+                    help="time only RRSNet inference at this precision on a 2^21-row batch "
+                         "(the untuned default launch shape), for kernel profiles")
     args = ap.parse_args()
+    if args.rrsnet_only:
+        run_rrsnet_only(args)
+        return
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)

@@ -35,7 +35,10 @@ struct __align__(128) TcSmem {
     unsigned char a1[2][128 * 16 * 2];  // A of layer 1 (hi, lo): 128 rows, K = 16
     unsigned char a2[2][128 * 32 * 2];  // A of layers 2 and 3 (hi, lo): 128 rows, K = 32
     float w4[32];
+    float4 stage[kTcThreads * 4];  // the tile's feature rows, staged by a bulk copy
     unsigned long long bar;
+    unsigned long long tbar;       // completion of the staging copy
+    int staging;                   // a staging copy has been issued and not yet waited for
     uint32_t tmem;
 };
 
@@ -88,6 +91,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
         if (ok) return true;
         if (clock64() - t0 > kWaitCycles) return false;
     }
+}
+
+// Bulk copy (the non-tensor TMA path) of `bytes` contiguous bytes of global memory into
+// shared memory, completing on mbarrier `bar`; both addresses 16-byte aligned and
+// `bytes` a multiple of 16.  Issued by one thread; the caller has ordered every earlier
+// generic read of the destination before it (barrier + proxy fence).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Feature rows of tile `tile` (128 rows of 64 bytes, fewer in the last tile).
+__device__ __forceinline__ void stage_tile(float4* stage, const float4* feat, long long tile,
+                                           long long n, uint32_t bar) {
+    const long long first = tile * 128;
+    const long long rows = n - first < 128 ? n - first : 128;
+    bulk_load(smem_u32(stage), feat + 4 * first, (uint32_t)(rows * 64), bar);
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -163,7 +189,10 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.tbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_tile(sm.stage, feat, blockIdx.x, n, smem_u32(&sm.tbar));  // first tile
+        sm.staging = 1;
     }
     // weights -> split BF16 B operands (W is [out][in] row-major = N rows of K)
     for (int e = tid; e < 32 * 16; e += kTcThreads)
@@ -191,7 +220,8 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         da2[h2] = smem_desc(smem_u32(sm.a2[h2]), 128, 512);
     }
     const uint64_t k16 = 256 >> 4;  // start address step of K = 16 (two core matrices)
-    uint32_t phase = 0;
+    uint32_t phase = 0, tphase = 0;
+    const uint32_t tbar = smem_u32(&sm.tbar);
     unsigned int evals = 0, nonfinite = 0;
     bool failed = false;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads;
@@ -199,12 +229,18 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         const long long row = tile * kTcThreads + tid;
         bool active = row < n;
         if (active && sentinel) active = q[row] < 0.0f;
+        const bool staged = mbar_wait(tbar, tphase);  // this tile's rows are in sm.stage
+        if (__syncthreads_or(!staged)) {
+            failed = true;
+            break;
+        }
+        tphase ^= 1u;
+        if (tid == 0) sm.staging = 0;
         float x[16];
         if (active) {
-            const float4* f = feat + 4 * row;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 v = __ldg(f + k);
+                const float4 v = sm.stage[4 * tid + k];
                 x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
             }
         } else {
@@ -231,6 +267,12 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
                     mma_bf16(tmem, A[0] + o, B[1] + o, 1u);
                 }
                 mma_commit(bar);
+                // every lane has read its staged row (barrier above): stage the next tile
+                // while this one runs through the network
+                if (layer == 0 && tile + gridDim.x < tiles) {
+                    stage_tile(sm.stage, feat, tile + gridDim.x, n, tbar);
+                    sm.staging = 1;
+                }
             }
             const bool ok = mbar_wait(bar, phase);
             phase ^= 1u;
@@ -264,6 +306,10 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         }
         fence_before();
         __syncthreads();  // TMEM reads done before the next tile's MMA overwrites it
+    }
+    if (failed) {  // let a staging copy still in flight land before the CTA leaves
+        __syncthreads();
+        if (sm.staging) mbar_wait(tbar, tphase);
     }
     if (failed && tid == 0 && status) atomicOr(status, (unsigned int)NRRS_STATUS_TIMEOUT);
     if (st) {
@@ -299,6 +345,9 @@ struct __align__(128) Fp8Smem {
     unsigned char w[3][32 * 32];  // B of layers 1-3: N = 32 rows, K = 32 bytes
     unsigned char a[128 * 32];    // A: 128 rows, K = 32 bytes
     float w4[32];
+    float4 stage[128 * 4];  // the tile's feature rows, staged by a bulk copy
+    unsigned long long tbar;
+    int staging;
     float red[4];
     float winv[3];  // 1 / weight scale of layers 1-3
     int wbad;       // a hidden-layer weight is not finite
@@ -369,7 +418,10 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.tbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_tile(sm.stage, feat, blockIdx.x, n, smem_u32(&sm.tbar));  // first tile
+        sm.staging = 1;
     }
     // per-matrix weight scales, then E4M3 B operands (W1 zero-padded to K = 32)
     const int off[3] = {0, 512, 1536}, kin[3] = {16, 32, 32};
@@ -403,7 +455,8 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
     uint64_t dw[3];
 #pragma unroll
     for (int l = 0; l < 3; ++l) dw[l] = smem_desc(smem_u32(sm.w[l]), 128, 256);
-    uint32_t phase = 0;
+    uint32_t phase = 0, tphase = 0;
+    const uint32_t tbar = smem_u32(&sm.tbar);
     unsigned int evals = 0, nonfinite = 0;
     bool failed = false;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads;
@@ -411,14 +464,20 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
         const long long row = tile * kTcThreads + tid;
         bool active = row < n;
         if (active && sentinel) active = q[row] < 0.0f;
+        const bool staged = mbar_wait(tbar, tphase);  // this tile's rows are in sm.stage
+        if (__syncthreads_or(!staged)) {
+            failed = true;
+            break;
+        }
+        tphase ^= 1u;
+        if (tid == 0) sm.staging = 0;
         float h[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) h[k] = 0.0f;
         if (active) {
-            const float4* f = feat + 4 * row;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 v = __ldg(f + k);
+                const float4 v = sm.stage[4 * tid + k];
                 h[4 * k] = v.x; h[4 * k + 1] = v.y; h[4 * k + 2] = v.z; h[4 * k + 3] = v.w;
             }
         }
@@ -440,6 +499,11 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
                 fence_after();
                 mma_e4m3(tmem, da, dw[layer]);
                 mma_commit(bar);
+                // every lane has read its staged row: stage the next tile
+                if (layer == 0 && tile + gridDim.x < tiles) {
+                    stage_tile(sm.stage, feat, tile + gridDim.x, n, tbar);
+                    sm.staging = 1;
+                }
             }
             const bool ok = mbar_wait(bar, phase);
             phase ^= 1u;
@@ -471,6 +535,10 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
             }
             q[row] = qv;
         }
+    }
+    if (failed) {  // let a staging copy still in flight land before the CTA leaves
+        __syncthreads();
+        if (sm.staging) mbar_wait(tbar, tphase);
     }
     if (failed && tid == 0 && status) atomicOr(status, (unsigned int)NRRS_STATUS_TIMEOUT);
     if (st) {
