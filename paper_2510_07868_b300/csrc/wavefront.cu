@@ -489,10 +489,21 @@ k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int dept
             const bool head = i == 0 || fbits(w.dep[i - 1].w) != pix;
             if (head) {
                 float sx = dep.x, sy = dep.y, sz = dep.z;
-                for (long long j = i + 1; j < n; ++j) {
-                    const float4 e = w.dep[j];
-                    if (fbits(e.w) != pix) break;
-                    sx += e.x; sy += e.y; sz += e.z;
+                // the run's deposits in order, eight loads in flight at a time
+                bool more = true;
+                for (long long j0 = i + 1; more && j0 < n; j0 += 8) {
+                    float4 e[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        e[k] = j0 + k < n ? w.dep[j0 + k] : make_float4(0.f, 0.f, 0.f, bitsf(~pix));
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!more || fbits(e[k].w) != pix) {
+                            more = false;
+                        } else {
+                            sx += e[k].x; sy += e[k].y; sz += e[k].z;
+                        }
+                    }
                 }
                 kahan_add(&w.acc_s[pix], &w.acc_c[pix], sx, sy, sz);
             }
@@ -577,7 +588,8 @@ __global__ void k_split_scan(WorkView w, RenderParams rp, int depth) {
 // Scatter of depth `depth`: each parent writes its X children to consecutive slots
 // (stable, parent order) and samples one BSDF direction per child with the child's own
 // lineage; child throughput = t * weight / q_used.  Slots >= C are dropped.
-__global__ void __launch_bounds__(kSplitThreads)
+// 4 blocks of 256 per SM (64 registers): more warps to hide the BSDF sampling's latency
+__global__ void __launch_bounds__(kSplitThreads, 4)
 k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderParams rp,
                 int depth) {
     __shared__ uint32_t sh[33];
