@@ -710,7 +710,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
 
     // the per-frame constants go to device memory ahead of the frame's launches
     launch_frame_consts(ws.fc, o.seed_lo, o.seed_hi ^ o.frame, scene->ref_count, s);
-    unsigned extra_launches = 1;
+    unsigned extra_launches = 1 + (rp.ref ? 1u : 0u);  // + the reference's partial sums
 
     // profile 1 = every stage; otherwise bit (k + 1) selects stage k
     const unsigned pmask = o.profile == 1 ? 0xFFFFFFFFu : ((unsigned)o.profile >> 1);
@@ -729,7 +729,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         CK(tm.end());                \
     } while (0)
         TIMED(NRRS_STAGE_INIT,
-              launch_ref_prepare(rp.ref, npix * 3, o.eps_rel, (double)o.alpha0, P, ws.st, s));
+              launch_ref_prepare(rp.ref, npix * 3, o.eps_rel, (double)o.alpha0, P, ws.st,
+                                 reinterpret_cast<float*>(ws.part), ws.grid_red, s));
         if (batch) TIMED(NRRS_STAGE_INIT, launch_ref_prepare_jobs(rp, o.eps_rel, s));
         QueueView q[2];
         for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
@@ -1485,8 +1486,9 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     (void)have_ref;
     CK(cudaMemsetAsync(t.k, 0, sizeof(int) * npix, s));
     launch_count_samples(t.rec, b, t.k, scene->n_sm * 4, s);
-    launch_mean(t.E, npix, t.scal + 0, s);
-    launch_pixel_terms(t.E, npix, t.scal + 0, t.k, t.scal + 4, s);  // L_min, L_avg, N
+    // Ebar, then L_min, L_avg, N (the partials borrow the gradient scratch)
+    launch_pixel_terms(t.E, npix, t.k, reinterpret_cast<double*>(t.part), t.part_blocks / 2,
+                       t.scal + 0, t.scal + 4, s);
     double host_terms[3];
     CK(cudaMemcpyAsync(host_terms, t.scal + 4, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

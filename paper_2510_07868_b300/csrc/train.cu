@@ -114,33 +114,50 @@ __global__ void k_count_samples(RecordView r, TrainBatch b, int* k) {
     }
 }
 
-// FP64 mean of E over pixels (fixed order).
-__global__ void k_mean(const float* E, long long n, double* out) {
+// Pixel-error terms in FP64, two fixed-order passes: per block (one contiguous chunk of
+// pixels) the sums of E, E^2 and k; then one block folds them into
+// Ebar = sum E / n, L_min = sum_i E_i and L_avg = sum_i (E_i - Ebar)^2 = sum E^2 - n Ebar^2
+// (Eq. loss-function_min / _avg) and N = sum_i k_i, the training samples.
+__global__ void k_pixel_partial(const float* E, long long n, const int* k, double* part) {
     __shared__ double sh[32];
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += E[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) *out = n > 0 ? s / (double)n : 0.0;
-}
-
-// L_min = sum_i E_i, L_avg = sum_i (E_i - Ebar)^2 (Eq. loss-function_min / _avg), and the
-// number of training samples, all in FP64 and fixed order.
-__global__ void k_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
-                              double* out) {
-    __shared__ double sh[32];
-    const double eb = *Ebar;
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
     double a = 0.0, b = 0.0, c = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        a += E[i];
-        b += ((double)E[i] - eb) * ((double)E[i] - eb);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double e = E[i];
+        a += e;
+        b += e * e;
         c += k[i];
     }
     a = block_sum(a, sh);
     b = block_sum(b, sh);
     c = block_sum(c, sh);
     if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = a;
+        part[3 * blockIdx.x + 1] = b;
+        part[3 * blockIdx.x + 2] = c;
+    }
+}
+
+__global__ void k_pixel_final(const double* part, int G, long long n, double* Ebar,
+                              double* out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        a += part[3 * g + 0];
+        b += part[3 * g + 1];
+        c += part[3 * g + 2];
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        const double eb = n > 0 ? a / (double)n : 0.0;
+        *Ebar = eb;
         out[0] = a;
-        out[1] = b;
+        const double v = b - (double)n * eb * eb;
+        out[1] = v > 0.0 ? v : 0.0;
         out[2] = c;
     }
 }
@@ -535,9 +552,6 @@ void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int 
     k_count_samples<<<grid, 256, 0, s>>>(r, b, k);
 }
 
-void launch_mean(const float* E, long long n, double* out, cudaStream_t s) {
-    k_mean<<<1, 1024, 0, s>>>(E, n, out);
-}
 
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s) {
@@ -559,9 +573,10 @@ void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cuda
     k_ref_fold<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(ref, rgb, n3, count);
 }
 
-void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
-                        double* out, cudaStream_t s) {
-    k_pixel_terms<<<1, 1024, 0, s>>>(E, n, Ebar, k, out);
+void launch_pixel_terms(const float* E, long long n, const int* k, double* part, int G,
+                        double* Ebar, double* out, cudaStream_t s) {
+    k_pixel_partial<<<G, 256, 0, s>>>(E, n, k, part);
+    k_pixel_final<<<1, 256, 0, s>>>(part, G, n, Ebar, out);
 }
 
 cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,

@@ -73,7 +73,7 @@ void launch_pixel_error(const RecordView& r, int spp, long long npix, const floa
                         float* V, float* E, cudaStream_t s);
 void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
                           cudaStream_t s);
-void launch_mean(const float* E, long long n, double* out, cudaStream_t s);
+
 // E_acc = temporal EMA of E_cur; E_out = (2r+1)^2 box filter of E_acc (copy when r = 0)
 void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
                             float alpha, int first, int radius, cudaStream_t s);
@@ -81,8 +81,8 @@ void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cuda
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s);
 // out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), out[2] = sum k (samples)
-void launch_pixel_terms(const float* E, long long n, const double* Ebar, const int* k,
-                        double* out, cudaStream_t s);
+void launch_pixel_terms(const float* E, long long n, const int* k, double* part, int G,
+                        double* Ebar, double* out, cudaStream_t s);
 cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
                              const TrainBatch& b, int grid, float* part, double* loss_part,
                              cudaStream_t s);

@@ -152,16 +152,30 @@ __device__ __forceinline__ V3 sample_ggx(V3 n, V3 wo, const nrrs_material& m, fl
 }
 
 // ------------------------------------------------------------------ kernels
+// Sum of the reference image in FP32, in two fixed-order passes: one contiguous chunk per
+// block, then the block sums (no FP64: the reference only sets the HEUR floor).
+__global__ void k_ref_partial(const float* __restrict__ ref, long long n3, float* part) {
+    __shared__ float sh[32];
+    const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = lo + chunk < n3 ? lo + chunk : n3;
+    float s = 0.0f;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += ref[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void k_ref_prepare(const float* __restrict__ ref, long long n3, float eps_rel,
-                              double alpha0, long long P, DevStats* st) {
-    __shared__ double sh[32];
-    double s = 0.0;
+                              double alpha0, long long P, DevStats* st, const float* part,
+                              int G) {
+    __shared__ float sh[32];
+    float s = 0.0f;
     if (ref)
-        for (long long i = threadIdx.x; i < n3; i += blockDim.x) s += (double)ref[i];
+        for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[b];
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
         st->has_ref = ref != nullptr;
-        st->eps_I = ref ? (float)((double)eps_rel * (s / (double)n3)) : 0.0f;
+        st->eps_I = ref ? eps_rel * (s / (float)n3) : 0.0f;
         st->alpha_cur = alpha0;
         st->live[0] = P;
     }
@@ -438,15 +452,15 @@ __global__ void k_normalize_jobs(WorkView w, RenderParams rp, int depth, int nor
 
 // HEUR floor per job: eps_rel * mean of the reference over the job's pixels.
 __global__ void k_ref_prepare_jobs(const float* __restrict__ ref, RenderParams rp, float eps_rel) {
-    __shared__ double sh[32];
+    __shared__ float sh[32];
     const int j = blockIdx.x;
     const JobDev& J = rp.jobs.job[j];
     const long long n3 = 3ll * J.W * J.H;
-    double s = 0.0;
+    float s = 0.0f;
     if (ref)
-        for (long long i = threadIdx.x; i < n3; i += blockDim.x) s += (double)ref[3 * J.pixel_base + i];
+        for (long long i = threadIdx.x; i < n3; i += blockDim.x) s += ref[3 * J.pixel_base + i];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) rp.jobs.eps_I[j] = ref ? (float)((double)eps_rel * (s / (double)n3)) : 0.0f;
+    if (threadIdx.x == 0) rp.jobs.eps_I[j] = ref ? eps_rel * (s / (float)n3) : 0.0f;
 }
 
 __device__ __forceinline__ void kahan_add(float4* s_, float4* c_, float x, float y, float z) {
@@ -783,8 +797,9 @@ k_split_arr_scatter(SplitArrays a, const unsigned long long* boff) {
 int split_block_threads() { return kSplitThreads; }
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0, long long P,
-                        DevStats* st, cudaStream_t s) {
-    k_ref_prepare<<<1, kReduceThreads, 0, s>>>(ref, n3, eps_rel, alpha0, P, st);
+                        DevStats* st, float* part, int G, cudaStream_t s) {
+    if (ref) k_ref_partial<<<G, 256, 0, s>>>(ref, n3, part);
+    k_ref_prepare<<<1, 256, 0, s>>>(ref, n3, eps_rel, alpha0, P, st, part, G);
 }
 
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s) {
@@ -835,7 +850,7 @@ void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, floa
 }
 
 void launch_ref_prepare_jobs(const RenderParams& rp, float eps_rel, cudaStream_t s) {
-    k_ref_prepare_jobs<<<rp.jobs.n, 256, 0, s>>>(rp.ref, rp, eps_rel);
+    k_ref_prepare_jobs<<<rp.jobs.n, 1024, 0, s>>>(rp.ref, rp, eps_rel);
 }
 
 void launch_sum_q_jobs(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,

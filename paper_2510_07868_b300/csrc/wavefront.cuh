@@ -133,7 +133,7 @@ int max_blocks_trace();  // resident blocks per SM
 int trace_stack_entries();  // traversal stack size per ray
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
-                        long long P, DevStats* st, cudaStream_t s);
+                        long long P, DevStats* st, float* part, int G, cudaStream_t s);
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
                   const JobWork& jobs, cudaStream_t s);
