@@ -39,9 +39,9 @@ WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NE
             "+ the 16 spp inference frame")
 # algorithmic bytes per unit of each stage ("Kernels and rooflines")
 BYTES_PER_RAY_SHADE = 48 + 8 + 4 + 16           # path state, hit in; q, deposit out
-BYTES_PER_SLOT_COUNT = 16 + 4 + 48              # deposit, q, path state (Philox keys)
-BYTES_PER_PARENT_SCATTER = 48 + 8 + 4           # path state, hit, q
-BYTES_PER_CHILD_SCATTER = 48                    # child path state
+BYTES_PER_SLOT_DEPOSIT = 16                     # last depth: deposit only
+BYTES_PER_PARENT_SPLIT = 16 + 4 + 48 + 8        # deposit, q, path state, hit
+BYTES_PER_CHILD_SPLIT = 48                      # child path state
 RRSNET_FLOP_PER_PATH = 2 * (16 * 32 + 32 * 32 + 32 * 32 + 32)
 
 
@@ -375,7 +375,7 @@ def run_ours(args, rank, world, local_rank):
     # bracket only the dominant stage's launches, which the roofline needs
     warm_ms = np.zeros(nrrs.STAGES)
     warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
-    warm_live = warm_evals = warm_children = 0
+    warm_live = warm_evals = warm_children = warm_last = 0
     for k in range(args.warmup):
         train(30_000 + k)
         st = render(k, profile=1)
@@ -384,6 +384,7 @@ def run_ours(args, rank, world, local_rank):
         warm_live += int(st["live"].sum())
         warm_evals += st["net_evals"]
         warm_children += int(st["live"][1:].sum())
+        warm_last += int(st["live"][DEPTH - 1])
     dom = int(np.argmax(warm_ms))
     torch.cuda.synchronize()
     clocks.start()
@@ -400,6 +401,7 @@ def run_ours(args, rank, world, local_rank):
     stage_ms = np.zeros(nrrs.STAGES)
     stage_n = np.zeros(nrrs.STAGES, dtype=np.int64)
     live_total = 0
+    live_last = 0
     net_evals = 0
     children = 0
     fallbacks = 0
@@ -417,6 +419,7 @@ def run_ours(args, rank, world, local_rank):
         stage_ms += st["stage_ms"]
         stage_n += st["stage_launches"]
         live_total += int(st["live"].sum())
+        live_last += int(st["live"][DEPTH - 1])
         net_evals += st["net_evals"]
         children += int(st["live"][1:].sum())
     ev1.record(stream)
@@ -495,8 +498,9 @@ def run_ours(args, rank, world, local_rank):
     names = nrrs.STAGE_NAMES
     alg_bytes = {
         "extend": 32 * live_total + 8 * live_total,  # ray in, hit out
-        "split_count": BYTES_PER_SLOT_COUNT * live_total,
-        "split_scatter": BYTES_PER_PARENT_SCATTER * live_total + BYTES_PER_CHILD_SCATTER * children,
+        "split_count": BYTES_PER_SLOT_DEPOSIT * live_last,
+        "split_scatter": BYTES_PER_PARENT_SPLIT * (live_total - live_last)
+        + BYTES_PER_CHILD_SPLIT * children,
     }
     bytes_dom = alg_bytes.get(names[dom])
     per_launch_ms = stage_ms[dom] / max(1, stage_n[dom])
@@ -520,8 +524,9 @@ def run_ours(args, rank, world, local_rank):
         "extend": 40 * warm_live,
         "shade": BYTES_PER_RAY_SHADE * warm_live + 64 * warm_evals,
         "rrsnet": 68 * warm_evals,
-        "split_count": BYTES_PER_SLOT_COUNT * warm_live,
-        "split_scatter": BYTES_PER_PARENT_SCATTER * warm_live + BYTES_PER_CHILD_SCATTER * warm_children,
+        "split_count": BYTES_PER_SLOT_DEPOSIT * warm_last,
+        "split_scatter": BYTES_PER_PARENT_SPLIT * (warm_live - warm_last)
+        + BYTES_PER_CHILD_SPLIT * warm_children,
     }
     stages = {"timed_over": f"{args.warmup} warm-up steps"}
     for i, n in enumerate(names):

@@ -72,6 +72,8 @@ struct Workspace {
     float4* acc_c = nullptr;
     DevStats* st = nullptr;
     FrameConsts* fc = nullptr;
+    unsigned long long* flags = nullptr;  // look-back flags of the fused split
+    long long n_flags = 0;
 
     void release() {
         for (int k = 0; k < 2; ++k) {
@@ -82,7 +84,10 @@ struct Workspace {
         }
         cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(feat); cudaFree(part); cudaFree(bcnt);
         cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st); cudaFree(fc);
+        cudaFree(flags);
         fc = nullptr;
+        flags = nullptr;
+        n_flags = 0;
         hit = nullptr; q = nullptr; dep = nullptr; feat = nullptr; part = nullptr; bcnt = nullptr;
         has_feat = false;
         boff = nullptr; acc_s = acc_c = nullptr; st = nullptr;
@@ -255,6 +260,8 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
     CK(dalloc(&w.acc_c, npix));
     CK(dalloc(&w.st, 1));
     CK(dalloc(&w.fc, 1));
+    w.n_flags = cap / 256 + 2;
+    CK(dalloc(&w.flags, (size_t)w.n_flags));
     w.cap = cap;
     w.npix = npix;
     return NRRS_OK;
@@ -742,6 +749,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         w.hit = ws.hit; w.q = ws.q; w.dep = ws.dep; w.feat = ws.feat; w.part = ws.part;
         w.grid_red = ws.grid_red;
         w.bcnt = ws.bcnt; w.boff = ws.boff; w.grid_split = ws.grid_split;
+        w.flags = ws.flags;
         w.acc_s = ws.acc_s; w.acc_c = ws.acc_c; w.st = ws.st;
         RenderParams r = rp;
         int cur = 0;
@@ -772,15 +780,14 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             } else {
                 TIMED(NRRS_STAGE_NORMALIZE, launch_normalize_depth(w, r, d, normalized, s));
             }
-            const int do_split = d < max_depth;
-            TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, r, d, do_split, s));
-            if (do_split) {
-                TIMED(NRRS_STAGE_SCAN, launch_split_scan(w, r, d, s));
+            if (d < max_depth) {  // count, compaction and scatter in one pass
+                CK(cudaMemsetAsync(ws.flags, 0, sizeof(unsigned long long) * ws.n_flags, s));
                 TIMED(NRRS_STAGE_SCATTER,
-                      launch_split_scatter(scene->view, q[cur], q[cur ^ 1], w, r, d, s));
+                      launch_split_fused(scene->view, q[cur], q[cur ^ 1], w, r, d, s));
                 cur ^= 1;
-            } else if (rec) {
-                CK(cudaMemsetAsync(r.rec_X, 0, sizeof(uint32_t) * C, s));
+            } else {  // the last depth only deposits
+                TIMED(NRRS_STAGE_COUNT, launch_split_count(scene->view, q[cur], w, r, d, 0, s));
+                if (rec) CK(cudaMemsetAsync(r.rec_X, 0, sizeof(uint32_t) * C, s));
             }
         }
         TIMED(NRRS_STAGE_FINALIZE,

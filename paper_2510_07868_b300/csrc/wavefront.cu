@@ -580,69 +580,143 @@ __device__ void scan_counts(const unsigned int* cnt, unsigned long long* off, in
     if (threadIdx.x == blockDim.x - 1) *total_out = sh[threadIdx.x];
 }
 
-__global__ void k_split_scan(WorkView w, RenderParams rp, int depth) {
-    __shared__ unsigned long long total;
-    scan_counts(w.bcnt, w.boff, w.grid_split, &total);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        DevStats* st = w.st;
-        const unsigned long long S = total;
-        const unsigned long long C = (unsigned long long)rp.cap;
-        const unsigned long long nn = S < C ? S : C;
-        st->requested[depth - 1] = (long long)S;
-        st->dropped[depth - 1] = (long long)(S - nn);
-        st->live[depth] = (long long)nn;
-        if (S > nn) {
-            st->alpha_cur *= 0.99;
-            st->status |= NRRS_STATUS_OVERFLOW_DROPPED;
-        }
-    }
-}
+// Split of depth `depth` in one pass (count, compaction and scatter fused; Eq. rrs_factor
+// and the bounded queue of Sec. 3.1).  Blocks claim 256-slot tiles in order; each tile
+// adds its pixels' deposits (run heads, as k_split_count), decides every parent's X, and
+// finds its first child slot by a decoupled look-back over the earlier tiles' published
+// counts (aggregate, or inclusive prefix once known), then writes its children.  Tiles
+// are claimed in increasing order by running blocks, so every tile waited on belongs to
+// a block that is running or done; each wait is bounded all the same (a timeout sets
+// NRRS_STATUS_TIMEOUT and the tile drops its children rather than hang).  The last tile
+// sets the next queue length, the drop count and the alpha back-off (Eq. f_rate_prime).
+constexpr unsigned long long kFlagAggregate = 1ull << 62;
+constexpr unsigned long long kFlagInclusive = 2ull << 62;
+constexpr unsigned long long kFlagValue = (1ull << 62) - 1ull;
+constexpr long long kLookbackCycles = 2000000000ll;  // ~1 s
 
-// Scatter of depth `depth`: each parent writes its X children to consecutive slots
-// (stable, parent order) and samples one BSDF direction per child with the child's own
-// lineage; child throughput = t * weight / q_used.  Slots >= C are dropped.
-// 4 blocks of 256 per SM (64 registers): more warps to hide the BSDF sampling's latency
 __global__ void __launch_bounds__(kSplitThreads, 4)
-k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderParams rp,
-                int depth) {
+k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderParams rp,
+              int depth) {
     __shared__ uint32_t sh[33];
+    __shared__ long long s_tile;
+    __shared__ unsigned long long s_excl;
+    __shared__ int s_ok;
     DevStats* st = w.st;
     const uint32_t key0 = rp.fc->key0, key1 = rp.fc->key1;
     const long long n = st->live[depth - 1];
     const float F = st->F_cur;
-    long long begin, end;
-    int tiles;
-    block_range(n, &tiles, &begin, &end);
-    unsigned long long carry = tiles ? w.boff[blockIdx.x] : 0ull;
-    for (int tile = 0; tile < tiles; ++tile) {
-        const long long i = begin + (long long)tile * kSplitThreads + threadIdx.x;
-        uint32_t X = 0, base = 0;
+    const long long tiles = (n + kSplitThreads - 1) / kSplitThreads;
+    unsigned long long* ctr = &st->tiles[depth - 1];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(ctr, 1ull);
+        __syncthreads();
+        const long long t = s_tile;
+        if (t >= tiles) break;
+        const long long i = t * kSplitThreads + threadIdx.x;
+        uint32_t X = 0, base = 0, lpix = 0;
         float qu = 0.0f;
-        float4 o4, d4, t4;
-        uint32_t lpix = 0;
-        if (i < end) {
+        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = o4, t4 = o4;
+        if (i < n) {
+            // this depth's deposits, summed per pixel run by the run's first slot
+            const float4 dep = w.dep[i];
+            const uint32_t pix = fbits(dep.w);
+            if (i == 0 || fbits(w.dep[i - 1].w) != pix) {
+                float sx = dep.x, sy = dep.y, sz = dep.z;
+                bool more = true;
+                for (long long j0 = i + 1; more && j0 < n; j0 += 8) {
+                    float4 e[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        e[k] = j0 + k < n ? w.dep[j0 + k] : make_float4(0.f, 0.f, 0.f, bitsf(~pix));
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!more || fbits(e[k].w) != pix) {
+                            more = false;
+                        } else {
+                            sx += e[k].x; sy += e[k].y; sz += e[k].z;
+                        }
+                    }
+                }
+                kahan_add(&w.acc_s[pix], &w.acc_c[pix], sx, sy, sz);
+            }
             o4 = cur.o[i];
             d4 = cur.d[i];
             t4 = cur.t[i];
             float Fi = F;
             lpix = fbits(o4.w);
-            if (rp.jobs.job) {
+            if (rp.jobs.job) {  // the job's factor; random numbers by job-local pixel
                 const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, lpix);
                 Fi = rp.jobs.F_cur[j];
                 lpix -= (uint32_t)rp.jobs.job[j].pixel_base;
             }
-            X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w),
-                             (uint32_t)depth, fbits(d4.w), &qu, &base);
+            X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w), (uint32_t)depth,
+                             fbits(d4.w), &qu, &base);
+            if (rp.trace) {
+                const int slot = __float_as_int(w.hit[i].y);
+                uint32_t* r = rp.trace + ((size_t)(depth - 1) * rp.cap + i) * 5;
+                r[0] = fbits(o4.w);
+                r[1] = fbits(t4.w);
+                r[2] = fbits(d4.w);
+                r[3] = slot < 0 ? kNoHit : fbits(__ldg(&sc.tris[3 * slot].w));
+                r[4] = X;
+            }
         }
         uint32_t tile_total;
         const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
-        if (rp.rec_first && i < end) {
-            const unsigned long long f = carry + pre;
-            rp.rec_first[i] = (uint32_t)(f < (unsigned long long)rp.cap ? f : (unsigned long long)rp.cap);
+        if (threadIdx.x < 32) {  // warp 0: publish, then look back 32 tiles at a time
+            const int lane = threadIdx.x;
+            unsigned long long excl = 0;
+            int ok = 1;
+            if (lane == 0)
+                atomicExch(&w.flags[t], (t == 0 ? kFlagInclusive : kFlagAggregate) | tile_total);
+            const long long t0 = clock64();
+            for (long long base = t - 1; base >= 0;) {
+                const long long j = base - lane;  // lane 0 is the nearest predecessor
+                const unsigned long long f =
+                    j >= 0 ? *reinterpret_cast<volatile unsigned long long*>(&w.flags[j])
+                           : (2ull << 62);  // before tile 0: an inclusive prefix of 0
+                const unsigned incl = __ballot_sync(0xffffffffu, (f >> 62) == 2ull);
+                const unsigned none = __ballot_sync(0xffffffffu, (f >> 62) == 0ull);
+                const int stop = incl ? __ffs(incl) - 1 : 31;  // the window's last lane needed
+                const unsigned need = stop == 31 ? 0xffffffffu : (2u << stop) - 1u;
+                if (none & need) {  // a nearer tile has not published yet
+                    if (clock64() - t0 > kLookbackCycles) {
+                        ok = 0;
+                        break;
+                    }
+                    continue;
+                }
+                excl += warp_sum(lane <= stop ? (f & kFlagValue) : 0ull);
+                if (incl) break;
+                base -= 32;
+            }
+            if (lane == 0) {
+                if (t > 0) atomicExch(&w.flags[t], kFlagInclusive | (excl + tile_total));
+                s_excl = excl;
+                s_ok = ok;
+                if (!ok) atomicOr(&st->status, (unsigned int)NRRS_STATUS_TIMEOUT);
+                if (t == tiles - 1) {  // the whole depth's children are counted
+                    const unsigned long long S = excl + tile_total;
+                    const unsigned long long C = (unsigned long long)rp.cap;
+                    const unsigned long long nn = S < C ? S : C;
+                    st->requested[depth - 1] = (long long)S;
+                    st->dropped[depth - 1] = (long long)(S - nn);
+                    st->live[depth] = (long long)nn;
+                    if (S > nn) {
+                        st->alpha_cur *= 0.99;
+                        st->status |= NRRS_STATUS_OVERFLOW_DROPPED;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const unsigned long long first = s_excl + pre;
+        if (rp.rec_first && i < n) {
+            rp.rec_first[i] =
+                (uint32_t)(first < (unsigned long long)rp.cap ? first : (unsigned long long)rp.cap);
             rp.rec_X[i] = X;
         }
-        if (X > 0) {
+        if (X > 0 && s_ok) {
             const float2 hh = w.hit[i];
             const int slot = __float_as_int(hh.y);
             int mi;
@@ -655,7 +729,7 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
             const uint32_t smp = fbits(t4.w);
             const float iq = 1.0f / qu;
             for (uint32_t j = 0; j < X; ++j) {
-                const unsigned long long dst = carry + pre + j;
+                const unsigned long long dst = first + j;
                 if (dst >= (unsigned long long)rp.cap) break;
                 const uint32_t lin = base + j * kLineageStep;
                 const U4 r = draw(key0, key1, lpix, smp, (uint32_t)depth, kPurposeBsdf, lin);
@@ -671,9 +745,8 @@ k_split_scatter(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPa
                 nxt.t[dst] = make_float4(t4.x * wt.x * iq, t4.y * wt.y * iq, t4.z * wt.z * iq, t4.w);
             }
         }
-        carry += tile_total;
+        __syncthreads();  // s_tile, s_excl and sh are reused by the next tile
     }
-    (void)st;
 }
 
 __global__ void k_finalize(WorkView w, RenderParams rp, float* __restrict__ rgb,
@@ -834,13 +907,9 @@ void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,
     k_split_count<<<w.grid_split, kSplitThreads, 0, s>>>(sc, cur, w, rp, depth, do_split);
 }
 
-void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
-    k_split_scan<<<1, kReduceThreads, 0, s>>>(w, rp, depth);
-}
-
-void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
-                          const RenderParams& rp, int depth, cudaStream_t s) {
-    k_split_scatter<<<w.grid_split, kSplitThreads, 0, s>>>(sc, cur, nxt, w, rp, depth);
+void launch_split_fused(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
+                        const RenderParams& rp, int depth, cudaStream_t s) {
+    k_split_fused<<<w.grid_split, kSplitThreads, 0, s>>>(sc, cur, nxt, w, rp, depth);
 }
 
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,

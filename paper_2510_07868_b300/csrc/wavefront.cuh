@@ -39,6 +39,7 @@ struct DevStats {
     long long dropped[kMaxDepth];
     float F[kMaxDepth];
     unsigned long long fetch[kMaxDepth];  // dynamic ray-fetch counters of k_extend
+    unsigned long long tiles[kMaxDepth];  // tile claims of the fused split
     unsigned long long nonfinite;
     unsigned long long net_evals;
     double alpha_cur;               // adaptive alpha (Eq. f_rate_prime), carried over depths
@@ -56,6 +57,7 @@ struct WorkView {
     float4* feat;      // [C][4] RRSNet features (NET depths)
     double* part;      // [grid_red] partial sums of q
     int grid_red;      // blocks of the kernel that produced `part` at this depth
+    unsigned long long* flags;  // [C / 256 + 1] look-back flags of the fused split
     unsigned int* bcnt;  // [grid_split] children per block
     unsigned long long* boff;  // [grid_split] exclusive prefix of bcnt
     int grid_split;
@@ -145,9 +147,8 @@ void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth
                             cudaStream_t s);
 void launch_split_count(const SceneView& sc, QueueView cur, const WorkView& w,
                         const RenderParams& rp, int depth, int do_split, cudaStream_t s);
-void launch_split_scan(const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
-void launch_split_scatter(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
-                          const RenderParams& rp, int depth, cudaStream_t s);
+void launch_split_fused(const SceneView& sc, QueueView cur, QueueView nxt, const WorkView& w,
+                        const RenderParams& rp, int depth, cudaStream_t s);
 void launch_finalize(const WorkView& w, const RenderParams& rp, float* rgb, float* ref_mean,
                      int update_ref, long long npix, cudaStream_t s);
 // Batched renders: per-job HEUR floors, per-job sums of q and normalisation factors.
