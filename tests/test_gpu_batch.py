@@ -98,6 +98,7 @@ def test_batch_of_64_uneven_jobs_full_size(nrrs):
     assert np.array_equal(live[:, :Dm].sum(axis=0), st["live"][:Dm])
     C = 2 * sum(w * h * s for _, w, h, s, _ in jobs)
     assert st["capacity"] == C and st["dropped"].sum() == 0
+    assert not st["status_bits"] & nrrs.STATUS_TIMEOUT
     for j, (_, W, H, spp, D) in enumerate(jobs):
         assert live[j, 0] == W * H * spp and np.all(live[j, D:] == 0)
         assert np.all((F[j, :D] > 0) & (F[j, :D] <= 1))

@@ -38,6 +38,7 @@ def _frame_properties(st, C, D):
     for d in range(D - 1):
         assert live[d + 1] == min(st["requested"][d], C)
     assert np.all((st["F"][:D] > 0) & (st["F"][:D] <= 1)) and st["nonfinite"] == 0
+    assert st["status_bits"] == 0  # no drops, no non-finite factors, no bounded wait ran out
 
 
 def _sampled_pixel_match(s, W, H, spp, D, mode, P, img, st, pix, **kw):

@@ -226,6 +226,7 @@ def test_full_size_net_properties(nrrs):
     assert np.all(np.isfinite(img)) and img.min() >= 0
     assert np.all((st["F"] > 0) & (st["F"] <= 1))
     assert st["net_evals"] > 0 and st["segments"] == st["live"].sum()
+    assert not st["status_bits"] & nrrs.STATUS_TIMEOUT
 
 
 def test_invalid_arguments(nrrs):
