@@ -21,7 +21,7 @@ _SRC_TRAIN = os.path.join(_HERE, "nrrs_oracle_train.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODE_NONE, MODE_PLAIN_RR, MODE_HEUR_NORM, MODE_NET, MODE_NET_MIX = range(5)
-GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
+GATE_NET, GATE_HEUR, GATE_FIXED, GATE_ADRRS = 0, 1, 2, 3
 MAX_DEPTH = 64
 NO_HIT = 0xFFFFFFFF
 
@@ -59,7 +59,8 @@ class RenderArgs(C.Structure):
                 ("f_rate", C.c_double), ("alpha0", C.c_double), ("q_max", C.c_double),
                 ("eps_rel", C.c_double), ("boxcox_lambda", C.c_double), ("gate", C.c_uint64),
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
-                ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p)]
+                ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p),
+                ("stat_params", C.c_void_p)]
 
 
 class RenderStats(C.Structure):
@@ -253,7 +254,8 @@ def bernstein_exponent(f_rate):
 
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
-           params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None):
+           params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None,
+           stat_params=None):
     """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
     With record=True the stats dict also holds "rec": per depth an array [live, 13] of
     (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
@@ -264,9 +266,10 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     capv = cap if cap > 0 else 2 * width * height * spp
     rec = np.zeros((max_depth, capv, 13)) if record else None
     fF = np.ascontiguousarray(forced_F, dtype=np.float32) if forced_F is not None else None
+    SP = np.ascontiguousarray(stat_params, dtype=np.float64) if stat_params is not None else None
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
-                      0 if pix is None else pix.shape[0], _p(rec), _p(fF))
+                      0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP))
     out = np.zeros((height, width, 3))
     st = RenderStats()
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None

@@ -17,6 +17,8 @@
  *   or_mlp_forward     RRSNet, Sec. 4 "Network Architecture" (3 hidden layers of 32,
  *                      Leaky ReLU) and the output activation of Eq. rrsnet_activation
  *   or_mlp_backward    the chain rule through the same network
+ *   or_render          also ADRRS (NN) factors at NET_MIX depths with gate 3 (Sec. 4
+ *                      "Mix-Depth"): lum(t) E[L_o] / I_px from StatNet's predicted mean
  *   or_normalize       Eq. q_norm, Eq. F_norm, Eq. q_norm_rate, Eq. f_rate_prime and
  *                      the downscale-only compromise of Sec. 4 ("Compromise")
  *   or_split           Eq. rrs_factor: N_q = floor(q) + Bernoulli(q - floor(q))
@@ -49,6 +51,8 @@
 #define OR_GATE_NET 0
 #define OR_GATE_HEUR 1
 #define OR_GATE_FIXED 2
+#define OR_GATE_ADRRS 3
+#define OR_ADRRS_FLOOR 0.05  /* smallest ADRRS (NN) factor: RR stays unbiased */
 
 #define OR_PURPOSE_JITTER 0u
 #define OR_PURPOSE_BSDF 1u
@@ -434,6 +438,10 @@ double or_bernstein_exponent(double f_rate) {
     return g * g / (2.0 * f_rate + (2.0 / 3.0) * g);
 }
 
+/* StatNet forward (nrrs_oracle_train.c) */
+void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, double* pre,
+                     double* hid);
+
 /* ------------------------------------------------------------------ render */
 
 typedef struct {
@@ -455,6 +463,7 @@ typedef struct {
     const float* forced_F;  /* optional [D]: the normalisation factor of every depth, taken
                                from a whole-frame render in place of Eq. F_norm over the
                                subset (test hook for sampled pixels of a full frame) */
+    const double* stat_params; /* StatNet weights (ADRRS (NN) depths of NET_MIX) */
 } or_render_args;
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
@@ -507,6 +516,9 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     const int64_t P = (a->pixels ? a->n_pixels : npix) * spp;
     const int64_t cap = a->cap > 0 ? a->cap : 2 * (int64_t)W * H * spp;
     if (a->pixels && or_is_normalized(a->mode) && !a->forced_F) return OR_ERR_ARG;
+    if (a->mode == OR_MODE_NET_MIX && !a->stat_params)
+        for (int32_t d = 1; d <= D; ++d)
+            if (((a->gate >> (2 * (d - 1))) & 3u) == OR_GATE_ADRRS) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
     /* queue storage: the capacity, or for a pixel subset 64 slots per primary path
      * (a subset's queue cannot be capped the way the whole frame's is; running out of
@@ -606,6 +618,35 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 q = fmin(1.0, or_lum(p->t));
             } else if (method == OR_GATE_HEUR) {
                 q = heur;
+            } else if (method == OR_GATE_ADRRS) {
+                /* ADRRS (NN), Sec. 4 "Mix-Depth": the path's expected contribution
+                 * lum(t) E[L_o] from StatNet (its throughput inputs zeroed, as trained),
+                 * relative to the pixel estimate; the heuristic before any estimate */
+                if (!a->pixel_ref) {
+                    q = heur;
+                } else {
+                    double x[OR_NF], out[6];
+                    for (int c = 0; c < 3; ++c) {
+                        double ext = hi[c] - lo[c];
+                        x[c] = ext > 0.0 ? (v->p[c] - lo[c]) / ext : 0.5;
+                    }
+                    x[3] = -d.x; x[4] = -d.y; x[5] = -d.z;
+                    x[6] = ns.x; x[7] = ns.y; x[8] = ns.z;
+                    for (int c = 0; c < 3; ++c) x[9 + c] = m->albedo[c];
+                    x[12] = (double)depth / (double)D;
+                    x[13] = x[14] = x[15] = 0.0;
+                    or_mlpn_forward(a->stat_params, 6, x, out, NULL, NULL);
+                    const double el = (out[0] + out[1] + out[2]) / 3.0;
+                    const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
+                    const double den = fmax((r[0] + r[1] + r[2]) / 3.0, eps_I);
+                    q = den > 0.0 ? or_lum(p->t) * fmax(el, 0.0) / den : a->q_max;
+                    if (!isfinite(q)) {
+                        q = heur;
+                        v->net_fallback = 1;
+                    } else {
+                        q = fmin(fmax(q, OR_ADRRS_FLOOR), a->q_max);
+                    }
+                }
             } else {
                 double x[OR_NF];
                 for (int c = 0; c < 3; ++c) {

@@ -475,3 +475,75 @@ def test_forced_F_subset_equals_whole_frame():
     np.testing.assert_array_equal(sub.reshape(-1, 3)[pix], img.reshape(-1, 3)[pix])
     with pytest.raises(RuntimeError):
         oracle.render(s, 24, 16, 2, 6, oracle.MODE_NET, params=P, pixels=pix)
+
+
+def _statnet_params(seed):
+    """StatNet weights with a non-negative output layer (positive predicted radiance)."""
+    n = oracle.mlpn_param_count(6)
+    rng = np.random.default_rng(seed)
+    P = rng.normal(size=n) * 0.3
+    P[n - 6 * 32:] = np.abs(P[n - 6 * 32:])
+    return P
+
+
+def _adrrs_gate(D, adrrs_depths):
+    g = 0
+    for d in range(D):
+        g |= (oracle.GATE_ADRRS if d in adrrs_depths else oracle.GATE_FIXED) << (2 * d)
+    return g
+
+
+def test_adrrs_without_reference_is_the_heuristic():
+    """ADRRS (NN) compares a path's expected contribution with the pixel estimate; before
+    any estimate exists it is the throughput heuristic, so an all-ADRRS Mix-Depth render
+    equals the HEUR_NORM render exactly."""
+    s = I.box_scene(2)
+    D = 6
+    gate = _adrrs_gate(D, range(D))
+    a, sa, _ = oracle.render(s, 16, 12, 2, D, oracle.MODE_NET_MIX, gate=gate,
+                             stat_params=_statnet_params(1))
+    b, sb, _ = oracle.render(s, 16, 12, 2, D, oracle.MODE_HEUR_NORM)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(sa["live"], sb["live"])
+
+
+def test_adrrs_factor_scales_with_statnet_output():
+    """q_ADRRS is linear in StatNet's predicted mean: doubling the output layer doubles
+    every depth-1 factor exactly (powers of two), except where a clamp applies."""
+    s = I.box_scene(3)
+    D = 4
+    ref = np.full((16 * 12, 3), 0.2) * np.linspace(0.5, 2.0, 16 * 12)[:, None]
+    P = _statnet_params(2)
+    P2 = P.copy()
+    n = P.size
+    P2[n - 6 * 32:] *= 2.0
+    gate = _adrrs_gate(D, range(D))
+    qs = []
+    for params in (P, P2):
+        _, st, _ = oracle.render(s, 16, 12, 2, D, oracle.MODE_NET_MIX, gate=gate, q_max=1e9,
+                                 stat_params=params, pixel_ref=ref, record=True)
+        qs.append(st["rec"][0][:, 9])  # q_orig of the depth-1 vertices
+    q1, q2 = qs
+    free = (q1 > 0.05) & (q2 > 0.05)
+    assert free.sum() > 100
+    np.testing.assert_array_equal(q2[free], 2.0 * q1[free])
+
+
+def test_adrrs_is_unbiased_against_no_rrs():
+    """Mix-Depth with ADRRS (NN) depths stays unbiased (every factor is positive): frame
+    means agree with the no-RRS estimator within 3 standard errors."""
+    s = I.box_scene(2)
+    D = 6
+    gate = _adrrs_gate(D, {1, 2, 3, 4})
+    SP = _statnet_params(3)
+    ref = np.full((16 * 16, 3), 0.25)
+    vals = {0: [], 1: []}
+    for frame in range(16):
+        a, _, _ = oracle.render(s, 16, 16, 4, D, oracle.MODE_NONE, frame=frame)
+        b, _, _ = oracle.render(s, 16, 16, 4, D, oracle.MODE_NET_MIX, frame=frame, gate=gate,
+                                stat_params=SP, pixel_ref=ref)
+        vals[0].append(a.mean())
+        vals[1].append(b.mean())
+    x, y = np.array(vals[0]), np.array(vals[1])
+    se = math.sqrt(x.var(ddof=1) / len(x) + y.var(ddof=1) / len(y))
+    assert abs(x.mean() - y.mean()) < 3 * se
