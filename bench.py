@@ -271,9 +271,11 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------ GPU leg
 def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
     """1/(relMSE x seconds) of the estimators on the same B300: PLAIN_RR (throughput
-    roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet) and NET_MIX (the
-    Mix-Depth gate found by the search), each averaging 16 frames of 16 spp, against a
-    4096-spp plain path-traced reference (256 frames x 16 spp, no RRS)."""
+    roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet), ADRRS_NN (StatNet's
+    radiance over the pixel estimate at every depth), NET_MIX (the Mix-Depth gate over
+    FIXED / HEUR / NET) and NET_MIX_ADRRS (over FIXED / ADRRS (NN) / NET, the paper's
+    set), each averaging 16 frames of 16 spp, against a 4096-spp plain path-traced
+    reference (256 frames x 16 spp, no RRS)."""
     ref = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
     img = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     n_ref = 256
@@ -288,10 +290,16 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
     gate_res = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
                                          d_pixel_ref=None, stream=stream)
     search_s = time.perf_counter() - t0
+    # the paper's candidate set per depth: FIXED, ADRRS (NN), NRRS
+    gate_adrrs = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
+                                           d_pixel_ref=None, adrrs=1, stream=stream)
+    all_adrrs = sum(nrrs.GATE_ADRRS << (2 * d) for d in range(DEPTH))
     res = {}
     for name, mode, gate in (("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0),
-                             ("NET", nrrs.RRS_NET, 0), ("NET_MIX", nrrs.RRS_NET_MIX,
-                                                        gate_res["gate"])):
+                             ("NET", nrrs.RRS_NET, 0),
+                             ("ADRRS_NN", nrrs.RRS_NET_MIX, all_adrrs),
+                             ("NET_MIX", nrrs.RRS_NET_MIX, gate_res["gate"]),
+                             ("NET_MIX_ADRRS", nrrs.RRS_NET_MIX, gate_adrrs["gate"])):
         acc = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
         frames = 16
         segs = 0
@@ -322,7 +330,11 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
         "net_vs_plain_rr": res["NET"]["efficiency"] / base,
         "net_mix_vs_plain_rr": res["NET_MIX"]["efficiency"] / base,
         "heur_norm_vs_plain_rr": res["HEUR_NORM"]["efficiency"] / base,
+        "net_mix_adrrs_vs_plain_rr": res["NET_MIX_ADRRS"]["efficiency"] / base,
+        "net_mix_adrrs_vs_heur_norm": res["NET_MIX_ADRRS"]["efficiency"]
+        / res["HEUR_NORM"]["efficiency"],
         "mixdepth_gate": nrrs.gate_methods(gate_res["gate"], DEPTH),
+        "mixdepth_gate_adrrs": nrrs.gate_methods(gate_adrrs["gate"], DEPTH),
         "mixdepth_candidates": gate_res["evaluated"], "mixdepth_search_s": search_s,
     }
 

@@ -65,6 +65,11 @@ typedef enum nrrs_rrs_mode {
 #define NRRS_GATE_NET 0u
 #define NRRS_GATE_HEUR 1u
 #define NRRS_GATE_FIXED 2u
+#define NRRS_GATE_ADRRS 3u /* ADRRS (NN), Sec. 4 "Mix-Depth": q = lum(t) max(E[L_o], 0) /
+                              max(I_px, eps_I) with E[L_o] the mean over RGB of StatNet's
+                              predicted radiance (throughput inputs zeroed, as it is
+                              trained), clamped to [0.05, q_max]; the throughput heuristic
+                              before any reference exists */
 
 #define NRRS_MAX_DEPTH 32
 #define NRRS_N_FEATURES 16
@@ -484,6 +489,8 @@ typedef struct nrrs_mixdepth_opts {
     uint32_t seed_lo, seed_hi, frame;      /* one key for every candidate render           */
     const float* d_pixel_ref;              /* device [H*W*3] reference, or NULL for the
                                               scene's running mean of its frames            */
+    int32_t adrrs;                         /* candidates per depth: 0 = FIXED, HEUR, NET;
+                                              1 = FIXED, ADRRS (NN), NET (the paper's set) */
 } nrrs_mixdepth_opts;
 
 typedef struct nrrs_mixdepth_result {

@@ -354,7 +354,10 @@ int factor_kind(int mode, uint64_t gate, int depth) {
         case kNet: return kFactorNet;
         default: {
             const unsigned g = (unsigned)((gate >> (2 * (depth - 1))) & 3u);
-            return g == kGateNet ? kFactorNet : g == kGateHeur ? kFactorHeur : kFactorOne;
+            return g == kGateNet    ? kFactorNet
+                   : g == kGateHeur ? kFactorHeur
+                   : g == kGateAdrrs ? kFactorAdrrs
+                                    : kFactorOne;
         }
     }
 }
@@ -541,9 +544,6 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
     if (o.precision != 32 && o.precision != 16 && o.precision != 8)
         return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16 and 8");
-    if (rrs_mode == NRRS_RRS_NET_MIX)
-        for (int d = 1; d <= max_depth; ++d)
-            if (((o.gate >> (2 * (d - 1))) & 3u) == 3u) return fail(NRRS_ERR_INVALID_ARG, "gate value 3");
     const long long C = (long long)width * height * spp * o.cap_factor;
     if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
     return NRRS_OK;
@@ -635,6 +635,8 @@ nrrs_status finish_capture(nrrs_scene* sc, CaptureGuard& cg, uint64_t shape, uin
     return NRRS_OK;
 }
 
+nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s);  // training state (below)
+
 // One frame (see nrrs_render); with `rec` every depth's slots are recorded.
 nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_t spp,
                         int32_t max_depth, int32_t rrs_mode, const nrrs_render_opts& o,
@@ -653,9 +655,16 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         const int k = factor_kind(rrs_mode, o.gate, d);
         return heur_frame && k == kFactorNet ? (int)kFactorHeur : k;
     };
-    bool uses_net = false;
-    for (int d = 1; d <= max_depth; ++d)
+    bool uses_net = false, uses_adrrs = false;  // features are written for both
+    for (int d = 1; d <= max_depth; ++d) {
         if (kind_of(d) == kFactorNet) uses_net = true;
+        if (kind_of(d) == kFactorAdrrs) uses_adrrs = true;
+    }
+    if (uses_adrrs) {  // StatNet's weights (trained by nrrs_train_step)
+        nrrs_status trc = ensure_train_nets(scene, s);
+        if (trc != NRRS_OK) return trc;
+        uses_net = true;
+    }
     nrrs_status rc = ensure_workspace(scene, C, npix, uses_net);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
@@ -773,6 +782,10 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                       launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
                                     &w.st->live[d - 1], 0, w.q, 1, w.st, &w.st->status, s));
                 if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
+            } else if (kind == kFactorAdrrs) {
+                TIMED(NRRS_STAGE_RRSNET,
+                      launch_adrrs(scene->train.stat, w, q[cur], r, d, scene->n_sm * 4, s));
+                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             }
             if (batch) {  // Eq. F_norm per job
                 TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q_jobs(w, q[cur], r, d, s));
@@ -827,6 +840,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)fbits(scene->cam.aspect),
                                (uint64_t)(uintptr_t)scene->jw.part,
                                (uint64_t)(uintptr_t)scene->view.nodes4,
+                               (uint64_t)(uintptr_t)scene->train.stat,
                                (uint64_t)o.cap_factor};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
@@ -1655,8 +1669,11 @@ nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* op
         rc = ensure_record(scene, npix * o.spp * 2, 1, npix);
         if (rc != NRRS_OK) return rc;
     }
-    // method digit order per depth: FIXED, HEUR, NET (cheapest first; ties keep the first)
-    const uint64_t digit_gate[3] = {NRRS_GATE_FIXED, NRRS_GATE_HEUR, NRRS_GATE_NET};
+    // method digit order per depth: FIXED, HEUR or ADRRS (NN), NET (cheapest first; ties
+    // keep the first)
+    const uint64_t digit_gate[3] = {NRRS_GATE_FIXED,
+                                    o.adrrs ? (uint64_t)NRRS_GATE_ADRRS : (uint64_t)NRRS_GATE_HEUR,
+                                    NRRS_GATE_NET};
     uint64_t gate = 0;
     for (int d = 0; d < D; ++d) gate |= (uint64_t)NRRS_GATE_FIXED << (2 * d);
     double best_score = 0.0, best_rel = 0.0;

@@ -25,7 +25,7 @@ constexpr uint32_t kPurposeBsdf = 1u;
 constexpr uint32_t kPurposeRrs = 3u;
 
 enum Mode : int { kNone = 0, kPlainRR = 1, kHeurNorm = 2, kNet = 3, kNetMix = 4 };
-enum Gate : int { kGateNet = 0, kGateHeur = 1, kGateFixed = 2 };
+enum Gate : int { kGateNet = 0, kGateHeur = 1, kGateFixed = 2, kGateAdrrs = 3 };
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., "Parallel Random Numbers: As Easy as 1, 2, 3" (SC 2011): ten rounds

@@ -147,7 +147,86 @@ k_rrsnet_simt(const float* __restrict__ params, const float4* __restrict__ feat,
     }
 }
 
+// ADRRS (NN) factors, Sec. 4 "Mix-Depth": StatNet (16 -> 32 -> 32 -> 32 -> 6, the
+// throughput inputs zeroed as in its training) predicts E[<L>] per channel at each
+// vertex the render marked (q < 0); q = lum(t) max(mean_rgb E[<L>], 0) / max(I_px, eps_I),
+// clamped to [kAdrrsFloor, q_max] so a path predicted dark keeps a small survival
+// probability.  Before any reference exists the factor is the throughput heuristic's.
+// A non-finite prediction is marked for the heuristic stand-in (kQRepair).
+constexpr float kAdrrsFloor = 0.05f;
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, const float4* t,
+             const float4* dep, const long long* n_ptr, float* q, RenderParams rp, DevStats* st) {
+    constexpr int kStatParams = kNH * kNF + 2 * kNH * kNH + 6 * kNH;
+    __shared__ __align__(16) float sW[kStatParams];
+    const long long n = *n_ptr;
+    if ((long long)blockIdx.x * blockDim.x >= n) return;
+    for (int i = threadIdx.x; i < kStatParams / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(stat) + i);
+    __syncthreads();
+    const int has_ref = st->has_ref;
+    unsigned int evals = 0, nonfinite = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!(q[i] < 0.0f)) continue;
+        const float4 t4 = t[i];
+        const uint32_t pix = __float_as_uint(dep[i].w);
+        const float l = lum(t4.x, t4.y, t4.z);
+        float eps_I = st->eps_I;
+        if (rp.jobs.job) eps_I = rp.jobs.eps_I[job_of_pixel(rp.jobs.job, rp.jobs.n, pix)];
+        float v;
+        if (!has_ref) {
+            v = l;
+        } else {
+            float x[1][kNF];
+            load_row(feat, i, x[0]);
+            x[0][13] = x[0][14] = x[0][15] = 0.0f;
+            float h[1][kNH], g[1][kNH];
+            dense<1, kNF>(sW, x, h);
+            dense<1, kNH>(sW + kNH * kNF, h, g);
+            dense<1, kNH>(sW + kNH * kNF + kNH * kNH, g, h);
+            const float* W4 = sW + kNH * kNF + 2 * kNH * kNH;
+            float m = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                float z = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kNH; ++k) z = fmaf(W4[o * kNH + k], h[0][k], z);
+                m += z;
+            }
+            m *= (1.0f / 3.0f);
+            const float* rr = rp.ref + 3 * (size_t)pix;
+            const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
+            v = den > 0.0f ? l * fmaxf(m, 0.0f) / den : rp.q_max;
+            ++evals;
+            if (!(v <= FLT_MAX)) {  // NaN or infinite prediction
+                v = kQRepair;
+                ++nonfinite;
+            } else {
+                v = fminf(fmaxf(v, kAdrrsFloor), rp.q_max);
+            }
+        }
+        q[i] = v;
+    }
+    evals = warp_sum(evals);
+    nonfinite = warp_sum(nonfinite);
+    if ((threadIdx.x & 31) == 0) {
+        if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+        if (nonfinite) {
+            atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+            atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+        }
+    }
+}
+
 }  // namespace
+
+void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
+                  int depth, int grid, cudaStream_t s) {
+    k_adrrs_simt<<<grid, kThreads, 0, s>>>(stat, w.feat, cur.t, w.dep, &w.st->live[depth - 1], w.q,
+                                           rp, w.st);
+}
 
 void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* feat,
                         const long long* n_ptr, long long n_host, float* q, int sentinel,

@@ -287,7 +287,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     q = fminf(1.0f, lum(t4.x, t4.y, t4.z));
                 } else if (KIND == kFactorHeur) {
                     q = heur_factor(t4, rp, fbits(o4.w), has_ref, epsI);
-                } else {
+                } else {  // network depths (RRSNet or StatNet): features, q marked -1
                     const V3 p = xyz(o4) + d * hh.x;
                     const V3 ns = front ? ng : ng * -1.0f;
                     float4* f = w.feat + 4 * i;
@@ -302,7 +302,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                                        boxcox(t4.z, rp.boxcox_lambda));
                     q = -1.0f;  // filled by the RRSNet kernel
                 }
-                if (KIND != kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {
+                if (KIND < kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {
                     q = 0.0f;
                     ++nonfinite;
                 }
@@ -310,9 +310,9 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
         }
         w.q[i] = q;
         w.dep[i] = dep;
-        if (KIND != kFactorNet) qsum += (double)q;
+        if (KIND < kFactorNet) qsum += (double)q;
     }
-    if (KIND != kFactorNet) {
+    if (KIND < kFactorNet) {
         qsum = block_sum(qsum, sh);
         if (threadIdx.x == 0) w.part[blockIdx.x] = qsum;
     }
@@ -888,7 +888,8 @@ void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& 
         case kFactorOne: k_shade<kFactorOne><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
         case kFactorPlain: k_shade<kFactorPlain><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
         case kFactorHeur: k_shade<kFactorHeur><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
-        default: k_shade<kFactorNet><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorNet: k_shade<kFactorNet><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        default: k_shade<kFactorAdrrs><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
     }
 }
 

@@ -127,7 +127,13 @@ struct RenderParams {
     uint32_t* rec_X;      // record mode: children requested by every parent of this depth
 };
 
-enum FactorKind : int { kFactorOne = 0, kFactorPlain = 1, kFactorHeur = 2, kFactorNet = 3 };
+enum FactorKind : int {
+    kFactorOne = 0,
+    kFactorPlain = 1,
+    kFactorHeur = 2,
+    kFactorNet = 3,   // RRSNet
+    kFactorAdrrs = 4  // ADRRS (NN): StatNet's radiance over the pixel estimate
+};
 
 int extend_block_threads();
 int split_block_threads();
@@ -167,6 +173,9 @@ void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_
 void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* feat,
                         const long long* n_ptr, long long n_host, float* q, int sentinel,
                         DevStats* st, cudaStream_t s);
+// ADRRS (NN) factors of the vertices the shade kernel marked (rrsnet_simt.cu).
+void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
+                  int depth, int grid, cudaStream_t s);
 // rrsnet_tc.cu: tensor cores; precision 16 = split BF16 operands, 8 = E4M3 operands with
 // per-tensor scales; FP32 accumulation.
 void launch_rrsnet_tc(int precision, int grid, const float* params, const float4* feat,

@@ -20,7 +20,7 @@ NRRS_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
                 4: "timeout", 5: "non-finite", 6: "overflow dropped", 7: "unsupported"}
 RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
-GATE_NET, GATE_HEUR, GATE_FIXED = 0, 1, 2
+GATE_NET, GATE_HEUR, GATE_FIXED, GATE_ADRRS = 0, 1, 2, 3
 STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_HEUR_FALLBACK = 1, 2, 4, 8
 MAX_DEPTH = 32
 STAGES = 10
@@ -149,7 +149,7 @@ class MixDepthOpts(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
                 ("max_depth", C.c_int32), ("t_d", C.c_int32), ("max_candidates", C.c_int32),
                 ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32),
-                ("d_pixel_ref", C.c_void_p)]
+                ("d_pixel_ref", C.c_void_p), ("adrrs", C.c_int32)]
 
 
 class MixDepthResult(C.Structure):
@@ -467,9 +467,9 @@ def nrrs_mixdepth_candidates(max_depth, t_d):
 
 
 def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1, 0), frame=0,
-                         d_pixel_ref=None, max_candidates=0, stream=None):
+                         d_pixel_ref=None, max_candidates=0, adrrs=0, stream=None):
     o = MixDepthOpts(width, height, spp, max_depth, t_d, max_candidates, seed[0], seed[1], frame,
-                     _ptr(d_pixel_ref))
+                     _ptr(d_pixel_ref), adrrs)
     r = MixDepthResult()
     _check(_lib.nrrs_mixdepth_search(scene, C.byref(o), _stream(stream), C.byref(r)))
     return {name: getattr(r, name) for name, _ in r._fields_}
@@ -481,7 +481,7 @@ def nrrs_relmse(d_img, d_ref, n_pixels, eps, d_out, stream=None):
 
 def gate_methods(gate, max_depth):
     """Per-depth method names of a Mix-Depth gate."""
-    names = {GATE_NET: "NET", GATE_HEUR: "HEUR", GATE_FIXED: "FIXED"}
+    names = {GATE_NET: "NET", GATE_HEUR: "HEUR", GATE_FIXED: "FIXED", GATE_ADRRS: "ADRRS"}
     return [names[(gate >> (2 * d)) & 3] for d in range(max_depth)]
 
 

@@ -143,6 +143,37 @@ def test_net_mix_gate_parity(nrrs):
     compare(gimg, gtr, oimg, otr, W, H)
 
 
+def test_net_mix_with_adrrs_parity(nrrs):
+    """Mix-Depth with all four methods, ADRRS (NN) among them (StatNet's predicted
+    radiance over the pixel reference): decision-matched pixels equal the oracle's."""
+    s = I.box_scene(3)
+    P = I.rrsnet_init_params(2)
+    SP = np.random.default_rng(7).normal(size=nrrs.STATNET_PARAMS).astype(np.float32) * 0.3
+    SP[-6 * 32:] = np.abs(SP[-6 * 32:])
+    gate = 0
+    for d, g in enumerate([2, 3, 0, 3, 1, 3, 0, 3]):
+        gate |= g << (2 * d)
+    W = H = 40
+    ref = (np.full((H * W, 3), 0.3) * np.linspace(0.4, 1.6, H * W)[:, None]).astype(np.float32)
+    sc = nrrs.Scene(s)
+    sc.set_params(P)
+    nrrs.nrrs_set_params(sc.handle, nrrs.NET_STATNET, SP)
+    C = 2 * W * H * 4
+    tr = torch.zeros((8, C, 5), dtype=torch.int32, device="cuda")
+    dref = torch.from_numpy(ref).cuda()
+    img, st = sc.render(W, H, 4, 8, nrrs.RRS_NET_MIX, gate=gate, d_trace=tr.data_ptr(),
+                        d_pixel_ref=dref.data_ptr())
+    torch.cuda.synchronize()
+    trn = tr.cpu().numpy().view(np.uint32)
+    gtr = [trn[d, :st["live"][d]] for d in range(8)]
+    assert st["net_evals"] > 0 and st["nonfinite"] == 0
+    oimg, ost, otr = oracle.render(s, W, H, 4, 8, oracle.MODE_NET_MIX, params=P.astype(np.float64),
+                                   gate=gate, stat_params=SP.astype(np.float64),
+                                   pixel_ref=ref.astype(np.float64), trace=True)
+    compare(img.cpu().numpy().astype(np.float64), gtr, oimg, otr, W, H)
+    sc.close()
+
+
 def test_overflow_and_alpha_backoff(nrrs):
     """Tight capacity with f_rate = 1: drops happen, the queue never exceeds C, alpha
     backs off by 0.99 per overflowing depth (Eq. f_rate_prime), like the oracle."""
@@ -239,9 +270,6 @@ def test_invalid_arguments(nrrs):
             s.render(args["width"], args["height"], args["spp"], args["max_depth"], args["mode"],
                      out=out)
         assert e.value.code == 1
-    with pytest.raises(nrrs.NrrsError) as e:
-        s.render(8, 8, 1, 4, nrrs.RRS_NET_MIX, out=out, gate=3)
-    assert e.value.code == 1
     s.close()
 
 

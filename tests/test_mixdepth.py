@@ -40,8 +40,8 @@ def test_relmse_matches_oracle():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("D,t_d", [(3, 3), (4, 2)])
-def test_search_returns_the_argmin(D, t_d):
+@pytest.mark.parametrize("D,t_d,adrrs", [(3, 3, 0), (4, 2, 0), (4, 2, 1)])
+def test_search_returns_the_argmin(D, t_d, adrrs):
     """The search's gate is the lowest relMSE x segments among the candidates it may
     visit, found here by rendering every candidate through the public API."""
     import torch
@@ -57,9 +57,14 @@ def test_search_returns_the_argmin(D, t_d):
         img, _ = s.render(W, H, 8, D, nrrs.RRS_NONE, frame=100 + f, update_ref=0)
         acc = img.clone() if acc is None else acc + img
     ref.copy_(acc / 16)
-    res = nrrs.nrrs_mixdepth_search(s.handle, W, H, D, t_d=t_d, frame=7, d_pixel_ref=ref)
+    if adrrs:  # StatNet with a non-negative output layer, as after some training
+        sp = np.random.default_rng(5).normal(size=nrrs.STATNET_PARAMS).astype(np.float32) * 0.3
+        sp[-6 * 32:] = np.abs(sp[-6 * 32:])
+        nrrs.nrrs_set_params(s.handle, nrrs.NET_STATNET, sp)
+    res = nrrs.nrrs_mixdepth_search(s.handle, W, H, D, t_d=t_d, frame=7, d_pixel_ref=ref,
+                                    adrrs=adrrs)
     assert res["evaluated"] == nrrs.nrrs_mixdepth_candidates(D, t_d)
-    order = [nrrs.GATE_FIXED, nrrs.GATE_HEUR, nrrs.GATE_NET]
+    order = [nrrs.GATE_FIXED, nrrs.GATE_ADRRS if adrrs else nrrs.GATE_HEUR, nrrs.GATE_NET]
     gate = sum(nrrs.GATE_FIXED << (2 * d) for d in range(D))
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     for start in range(0, D, t_d):
