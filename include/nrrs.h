@@ -65,11 +65,12 @@ typedef enum nrrs_rrs_mode {
 #define NRRS_GATE_NET 0u
 #define NRRS_GATE_HEUR 1u
 #define NRRS_GATE_FIXED 2u
-#define NRRS_GATE_ADRRS 3u /* ADRRS (NN), Sec. 4 "Mix-Depth": q = lum(t) max(E[L_o], 0) /
+#define NRRS_GATE_ADRRS 3u /* ADRRS (NN), Sec. 4 "Mix-Depth": r = lum(t) max(E[L_o], 0) /
                               max(I_px, eps_I) with E[L_o] the mean over RGB of StatNet's
                               predicted radiance (throughput inputs zeroed, as it is
-                              trained), clamped to [0.05, q_max]; the throughput heuristic
-                              before any reference exists */
+                              trained); q = 1 inside the weight window [1/3, 5/3], else r,
+                              clamped to [0.05, q_max]; the throughput heuristic before
+                              any reference exists */
 
 #define NRRS_MAX_DEPTH 32
 #define NRRS_N_FEATURES 16

@@ -53,6 +53,9 @@
 #define OR_GATE_FIXED 2
 #define OR_GATE_ADRRS 3
 #define OR_ADRRS_FLOOR 0.05  /* smallest ADRRS (NN) factor: RR stays unbiased */
+/* ADRRS weight window of ratio 5 around the ideal throughput: bounds 2/(1+5), 5 x that */
+#define OR_ADRRS_WINDOW_LO (2.0 / 6.0)
+#define OR_ADRRS_WINDOW_HI (10.0 / 6.0)
 
 #define OR_PURPOSE_JITTER 0u
 #define OR_PURPOSE_BSDF 1u
@@ -639,11 +642,14 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                     const double el = (out[0] + out[1] + out[2]) / 3.0;
                     const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
                     const double den = fmax((r[0] + r[1] + r[2]) / 3.0, eps_I);
+                    /* r: the path's expected contribution over the pixel estimate; the
+                     * weight window of ADRRS leaves the path alone inside [1/3, 5/3] */
                     q = den > 0.0 ? or_lum(p->t) * fmax(el, 0.0) / den : a->q_max;
                     if (!isfinite(q)) {
                         q = heur;
                         v->net_fallback = 1;
                     } else {
+                        if (q >= OR_ADRRS_WINDOW_LO && q <= OR_ADRRS_WINDOW_HI) q = 1.0;
                         q = fmin(fmax(q, OR_ADRRS_FLOOR), a->q_max);
                     }
                 }

@@ -7,9 +7,13 @@
  *       each hidden layer and no output activation (Sec. 4 "Network Architecture";
  *       StatNet has no output activation, Sec. 4 "Output & Activation").
  *   or_statnet_dloss
- *       Eq. loss-function_StatNet: relative L2, L2(a, b) = (a - b)^2 / (sg(b)^2 + eps),
- *       on the two predicted moments E[<L>] and E[<L>^2] (Sec. 4 "Output & Activation")
- *       against the one-sample targets <L> and <L>^2, per RGB channel.
+ *       Eq. loss-function_StatNet: relative L2 on the two predicted moments E[<L>] and
+ *       E[<L>^2] (Sec. 4 "Output & Activation") against the one-sample targets <L> and
+ *       <L>^2, per RGB channel, normalised by the stop-gradient PREDICTION:
+ *       (a - b)^2 / (sg(a)^2 + eps).  (The printed equation puts sg() on b, the target,
+ *       where it has no effect; the relative L2 it cites normalises by the prediction,
+ *       whose gradient 2 (a - b) / (sg(a)^2 + eps) vanishes in expectation at a = E[b],
+ *       so noisy one-sample targets do not pull the prediction towards zero.)
  *   or_pixel_error
  *       Eq. loss-function_min: E_i = V[<I_i>] / (I_i^2 + eps), V from the spp samples of
  *       the pixel, I_i the reference (Sec. 4 "Compromise": the accumulated earlier frames).
@@ -97,14 +101,16 @@ void or_mlpn_backward(const double* P, int n_out, const double* x, const double*
     }
 }
 
-/* Relative L2 of both moments; returns the loss of one sample, writes d/dpred. */
+/* Relative L2 of both moments; returns the loss of one sample and writes d/dpred with
+ * the normalisation held constant (the stop-gradient). */
 double or_statnet_dloss(const double* pred /*6: m1 rgb, m2 rgb*/, const double* L /*3*/,
                         double eps, double* dpred) {
     double loss = 0.0;
     for (int c = 0; c < 3; ++c) {
         const double t1 = L[c], t2 = L[c] * L[c];
         const double d1 = pred[c] - t1, d2 = pred[3 + c] - t2;
-        const double w1 = 1.0 / (t1 * t1 + eps), w2 = 1.0 / (t2 * t2 + eps);
+        const double w1 = 1.0 / (pred[c] * pred[c] + eps);
+        const double w2 = 1.0 / (pred[3 + c] * pred[3 + c] + eps);
         loss += d1 * d1 * w1 + d2 * d2 * w2;
         dpred[c] = 2.0 * d1 * w1;
         dpred[3 + c] = 2.0 * d2 * w2;

@@ -149,11 +149,16 @@ k_rrsnet_simt(const float* __restrict__ params, const float4* __restrict__ feat,
 
 // ADRRS (NN) factors, Sec. 4 "Mix-Depth": StatNet (16 -> 32 -> 32 -> 32 -> 6, the
 // throughput inputs zeroed as in its training) predicts E[<L>] per channel at each
-// vertex the render marked (q < 0); q = lum(t) max(mean_rgb E[<L>], 0) / max(I_px, eps_I),
-// clamped to [kAdrrsFloor, q_max] so a path predicted dark keeps a small survival
-// probability.  Before any reference exists the factor is the throughput heuristic's.
+// vertex the render marked (q < 0); r = lum(t) max(mean_rgb E[<L>], 0) / max(I_px, eps_I)
+// is the path's expected contribution over the pixel estimate.  As in ADRRS's weight
+// window, q = 1 for r in [1/3, 5/3] and q = r outside, clamped to [kAdrrsFloor, q_max]
+// so a path predicted dark keeps a small survival probability.  Before any reference exists the factor is the throughput heuristic's.
 // A non-finite prediction is marked for the heuristic stand-in (kQRepair).
 constexpr float kAdrrsFloor = 0.05f;
+// ADRRS's weight window (ratio 5 around the ideal throughput): lower bound 2 / (1 + 5),
+// upper bound 5 times that, as fractions of the pixel estimate
+constexpr float kAdrrsWindowLo = (float)(2.0 / 6.0);
+constexpr float kAdrrsWindowHi = (float)(10.0 / 6.0);
 
 __global__ void __launch_bounds__(kThreads, 2)
 k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, const float4* t,
@@ -198,12 +203,15 @@ k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, co
             m *= (1.0f / 3.0f);
             const float* rr = rp.ref + 3 * (size_t)pix;
             const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
+            // r: the path's expected contribution over the pixel estimate; inside the
+            // weight window [1/3, 5/3] the path goes on unchanged
             v = den > 0.0f ? l * fmaxf(m, 0.0f) / den : rp.q_max;
             ++evals;
             if (!(v <= FLT_MAX)) {  // NaN or infinite prediction
                 v = kQRepair;
                 ++nonfinite;
             } else {
+                if (v >= kAdrrsWindowLo && v <= kAdrrsWindowHi) v = 1.0f;
                 v = fminf(fmaxf(v, kAdrrsFloor), rp.q_max);
             }
         }

@@ -204,7 +204,9 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
         for (int c = 0; c < 3; ++c) {
             const float L = tt[c] > 0.0f ? ss[c] / tt[c] : 0.0f;
             const float L2 = L * L;
-            const float w1 = 1.0f / (L2 + a.eps), w2 = 1.0f / (L2 * L2 + a.eps);
+            // relative L2 normalised by the (stop-gradient) prediction
+            const float w1 = 1.0f / (out[c] * out[c] + a.eps);
+            const float w2 = 1.0f / (out[3 + c] * out[3 + c] + a.eps);
             const float d1 = out[c] - L, d2 = out[3 + c] - L2;
             gout[c] = 2.0f * d1 * w1 * a.scale;
             gout[3 + c] = 2.0f * d2 * w2 * a.scale;

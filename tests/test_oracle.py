@@ -508,8 +508,9 @@ def test_adrrs_without_reference_is_the_heuristic():
 
 
 def test_adrrs_factor_scales_with_statnet_output():
-    """q_ADRRS is linear in StatNet's predicted mean: doubling the output layer doubles
-    every depth-1 factor exactly (powers of two), except where a clamp applies."""
+    """q_ADRRS is linear in StatNet's predicted mean outside ADRRS's weight window:
+    doubling the output layer doubles every such depth-1 factor exactly (powers of two);
+    inside the window the factor is 1."""
     s = I.box_scene(3)
     D = 4
     ref = np.full((16 * 12, 3), 0.2) * np.linspace(0.5, 2.0, 16 * 12)[:, None]
@@ -524,9 +525,17 @@ def test_adrrs_factor_scales_with_statnet_output():
                                  stat_params=params, pixel_ref=ref, record=True)
         qs.append(st["rec"][0][:, 9])  # q_orig of the depth-1 vertices
     q1, q2 = qs
-    free = (q1 > 0.05) & (q2 > 0.05)
-    assert free.sum() > 100
+    # outside the weight window [1/3, 5/3] and above the floor in both renders
+    free = (q1 > 0.05) & ((q1 < 1 / 6) | (q1 > 5 / 3))
+    assert free.sum() > 20
     np.testing.assert_array_equal(q2[free], 2.0 * q1[free])
+    # no factor falls strictly inside the window except the window's own 1
+    hits = 0
+    for q in (q1, q2):
+        inwin = (q >= 1 / 3) & (q <= 5 / 3)
+        assert np.all(q[inwin] == 1.0)
+        hits += int(inwin.sum())
+    assert hits > 0
 
 
 def test_adrrs_is_unbiased_against_no_rrs():

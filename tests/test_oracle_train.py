@@ -41,22 +41,28 @@ def test_mlpn_single_output_is_rrsnet_preactivation():
 
 
 def test_statnet_relative_l2():
-    """Eq. loss-function_StatNet: zero at the targets; gradient equals finite differences."""
+    """Eq. loss-function_StatNet with the stop-gradient on the prediction: zero at the
+    targets; the mean gradient over a set of one-sample targets vanishes exactly at their
+    mean (so noisy targets, most of them zero, do not bias the prediction — normalising
+    by the targets instead would stop at a weighted mean); relative (scale invariant)."""
     L = np.array([0.3, 2.0, 0.0])
     loss, d = oracle.statnet_dloss(np.r_[L, L * L], L)
     assert loss == 0.0 and np.all(d == 0)
-    rng = np.random.default_rng(5)
-    pred = rng.normal(size=6)
-    loss, d = oracle.statnet_dloss(pred, L)
-    for i in range(6):
-        e = np.zeros(6)
-        e[i] = 1e-6
-        fd = (oracle.statnet_dloss(pred + e, L)[0] - oracle.statnet_dloss(pred - e, L)[0]) / 2e-6
-        assert abs(fd - d[i]) < 1e-5 * max(1, abs(d[i]))
+    targets = [np.array([0.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]),
+               np.array([4.0, 0.0, 0.5]), np.array([0.0, 3.0, 0.5])]
+    mean1 = np.mean(targets, axis=0)
+    mean2 = np.mean([t * t for t in targets], axis=0)
+    grads = np.array([oracle.statnet_dloss(np.r_[mean1, mean2], t)[1] for t in targets])
+    np.testing.assert_allclose(grads.sum(axis=0), 0.0, atol=1e-12)
+    # away from the mean the summed gradient points back towards it
+    g_hi = sum(oracle.statnet_dloss(np.r_[mean1 * 1.5 + 0.1, mean2], t)[1] for t in targets)
+    assert np.all(g_hi[:3] > 0)
     # relative: scaling targets and predictions together by c leaves the loss unchanged
     # when eps is negligible
-    l1, _ = oracle.statnet_dloss(pred * 0 + np.r_[L, L * L] * 1.5, L, eps=1e-30)
-    l2, _ = oracle.statnet_dloss(np.r_[L * 1000, L * L * 1e6] * 1.5, L * 1000, eps=1e-30)
+    pred = np.random.default_rng(5).normal(size=6)
+    l1, _ = oracle.statnet_dloss(pred * 1.5, L + 0.1, eps=1e-30)
+    l2, _ = oracle.statnet_dloss(np.r_[pred[:3] * 1.5e3, pred[3:] * 1.5e6], (L + 0.1) * 1e3,
+                                 eps=1e-30)
     assert l1 == pytest.approx(l2, rel=1e-9)
 
 
