@@ -513,7 +513,7 @@ def test_adrrs_factor_scales_with_statnet_output():
     inside the window the factor is 1."""
     s = I.box_scene(3)
     D = 4
-    ref = np.full((16 * 12, 3), 0.2) * np.linspace(0.5, 2.0, 16 * 12)[:, None]
+    ref = np.ones((16 * 12, 3)) * np.logspace(-3, 1, 16 * 12)[:, None]  # r across the window
     P = _statnet_params(2)
     P2 = P.copy()
     n = P.size
