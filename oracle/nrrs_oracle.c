@@ -23,6 +23,12 @@
  *                      the downscale-only compromise of Sec. 4 ("Compromise")
  *   or_split           Eq. rrs_factor: N_q = floor(q) + Bernoulli(q - floor(q))
  *   or_render          the level-synchronous loop of Sec. 3.1 / Fig. wavefront
+ *   or_eval_bsdf       f cos and the sampling pdf of a given direction (both lobes),
+ *                      for next-event estimation
+ *   or_render (nee)    next-event estimation, on in the paper's experiments (Sec. 5):
+ *                      one emitter point per vertex (triangle by area, uniform on it),
+ *                      a shadow ray, and multiple importance sampling with the power
+ *                      heuristic (Veach 1997) against emitters hit by BSDF sampling
  *   or_bernstein_exponent  Eq. bernstein_frate
  *
  * Parity notes:
@@ -60,6 +66,8 @@
 #define OR_PURPOSE_JITTER 0u
 #define OR_PURPOSE_BSDF 1u
 #define OR_PURPOSE_RRS 3u
+#define OR_PURPOSE_NEE 5u
+#define OR_SHADOW_MARGIN 1e-4  /* a shadow ray stops at (1 - margin) x the emitter distance */
 
 #define OR_MAX_DEPTH 64
 #define OR_RAY_OFFSET 1e-4
@@ -290,6 +298,35 @@ int or_sample_ggx(const double n_[3], const double wo_[3], double albedo_[3], do
     return 1;
 }
 
+/* f(wo, wi) cos_i per channel and the pdf with which the material's sampling picks wi
+ * (solid angle): Lambertian f = albedo / pi, pdf = cos_i / pi; the GGX mixture as in
+ * or_sample_ggx.  Returns 0 (all zero) when wi or wo is below the shading hemisphere. */
+int or_eval_bsdf(const or_material* m, const double n_[3], const double wo_[3],
+                 const double wi_[3], double fcos[3], double* pdf) {
+    v3 n = mk(n_[0], n_[1], n_[2]), wo = mk(wo_[0], wo_[1], wo_[2]);
+    v3 wi = mk(wi_[0], wi_[1], wi_[2]);
+    double cos_i = dot(wi, n), cos_o = dot(wo, n);
+    fcos[0] = fcos[1] = fcos[2] = 0.0;
+    *pdf = 0.0;
+    if (cos_i <= 0.0 || cos_o <= 0.0) return 0;
+    if (m->type == 0) {
+        for (int c = 0; c < 3; ++c) fcos[c] = m->albedo[c] / M_PI * cos_i;
+        *pdf = cos_i / M_PI;
+        return 1;
+    }
+    double a = m->roughness, F0 = m->F0;
+    v3 h = nrm(add(wo, wi));
+    double cos_h = dot(h, n);
+    double oh = dot(wo, h);
+    double D = or_ggx_D(cos_h, a);
+    double G = or_ggx_G1(cos_o, a) * or_ggx_G1(cos_i, a);
+    double Fr = F0 + (1.0 - F0) * pow(1.0 - dot(wi, h), 5.0);
+    double spec = D * G * Fr / (4.0 * cos_o * cos_i);
+    for (int c = 0; c < 3; ++c) fcos[c] = (spec + (1.0 - F0) * m->albedo[c] / M_PI) * cos_i;
+    *pdf = 0.5 * D * cos_h / (4.0 * fabs(oh)) + 0.5 * cos_i / M_PI;
+    return 1;
+}
+
 /* ------------------------------------------------------------------ RRSNet */
 
 #define OR_NF 16
@@ -467,6 +504,7 @@ typedef struct {
                                from a whole-frame render in place of Eq. F_norm over the
                                subset (test hook for sampled pixels of a full frame) */
     const double* stat_params; /* StatNet weights (ADRRS (NN) depths of NET_MIX) */
+    int32_t nee;            /* next-event estimation with MIS (1) or BSDF sampling only (0) */
 } or_render_args;
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
@@ -486,6 +524,7 @@ typedef struct {
 
 typedef struct {
     double o[3], d[3], t[3];
+    double pdf;             /* solid-angle pdf the direction was sampled with (0: camera) */
     uint32_t pixel, sample, lineage;
 } or_path;
 
@@ -494,9 +533,95 @@ typedef struct {
     double p[3], n[3];      /* hit point, shading normal facing -d */
     double q;               /* q_orig (0 = terminate) */
     int net_fallback;       /* the network's factor was non-finite: q is the heuristic's */
+    double emit_w;          /* MIS weight of the emission found here (1 without NEE) */
+    double nee[3];          /* next-event contribution, 0 when occluded or not taken */
 } or_hitrec;
 
 static double or_lum(const double t[3]) { return 0.2126 * t[0] + 0.7152 * t[1] + 0.0722 * t[2]; }
+
+/* ------------------------------------------------------------------ next-event estimation */
+
+/* Emitters: every triangle whose material emits (some Le channel > 0) and whose area is
+ * positive, in triangle order.  One is chosen with probability area / A (A = their total
+ * area): cdf[k] = fp32(sum of the first k + 1 areas / A), summed in FP64 in triangle
+ * order, the last entry 1; a uniform u picks the first k with u < cdf[k] (u and cdf are
+ * FP32 values, so the comparison is the FP32 one). */
+typedef struct {
+    int32_t n;
+    int32_t* tri;
+    float* cdf;
+    double area;
+} or_emitters;
+
+static double or_tri_area(const or_scene* s, int32_t t) {
+    v3 v0 = or_tri_vertex(s, t, 0);
+    v3 c = cross(sub(or_tri_vertex(s, t, 1), v0), sub(or_tri_vertex(s, t, 2), v0));
+    return 0.5 * sqrt(dot(c, c));
+}
+
+static int or_emits(const or_material* m) { return m->Le[0] > 0.0f || m->Le[1] > 0.0f || m->Le[2] > 0.0f; }
+
+static int or_build_emitters(const or_scene* s, or_emitters* e) {
+    memset(e, 0, sizeof(*e));
+    e->tri = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->n_tri + 1));
+    e->cdf = (float*)malloc(sizeof(float) * (size_t)(s->n_tri + 1));
+    if (!e->tri || !e->cdf) return OR_ERR_OOM;
+    for (int32_t i = 0; i < s->n_tri; ++i)
+        if (or_emits(&s->mats[s->mat_id[i]]) && or_tri_area(s, i) > 0.0) {
+            e->tri[e->n++] = i;
+            e->area += or_tri_area(s, i);
+        }
+    double run = 0.0;
+    for (int32_t k = 0; k < e->n; ++k) {
+        run += or_tri_area(s, e->tri[k]);
+        e->cdf[k] = k == e->n - 1 ? 1.0f : (float)(run / e->area);
+    }
+    return OR_OK;
+}
+
+/* Power heuristic with exponent 2 (Veach 1997): the weight of technique a against b. */
+static double or_power_heuristic(double pa, double pb) {
+    double a2 = pa * pa, b2 = pb * pb;
+    return a2 / (a2 + b2);
+}
+
+/* Next-event estimation at a vertex (hit point hp, shading normal ns, outgoing wo,
+ * throughput t) with the NEE draw w: an emitter triangle by area (w[0]), a uniform
+ * point on it (sqrt(u1) (1 - u2) and sqrt(u1) u2 along its two edges, w[1], w[2]), and a
+ * shadow ray from the offset origin that must reach (1 - margin) of the distance.  The
+ * contribution t f cos_x Le w_light / p_light, with p_light = dist^2 / (|cos_l| A) the
+ * solid-angle density of the emitter sample and w_light the power heuristic against
+ * the BSDF's pdf of the same direction. */
+static void or_nee(const or_scene* s, const or_emitters* E, const or_material* m, v3 hp, v3 ns,
+                   v3 wo, const double t[3], const uint32_t w[4], double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (E->n == 0) return;
+    const double u = or_u01(w[0]);
+    int32_t k = 0;
+    while (k < E->n - 1 && !(u < (double)E->cdf[k])) ++k;
+    const int32_t lt = E->tri[k];
+    const double su = sqrt(or_u01(w[1])), u2 = or_u01(w[2]);
+    v3 v0 = or_tri_vertex(s, lt, 0);
+    v3 e1 = sub(or_tri_vertex(s, lt, 1), v0), e2 = sub(or_tri_vertex(s, lt, 2), v0);
+    v3 y = add(v0, add(scl(e1, su * (1.0 - u2)), scl(e2, su * u2)));
+    v3 org = add(hp, scl(ns, OR_RAY_OFFSET));
+    v3 v = sub(y, org);
+    const double dist2 = dot(v, v);
+    if (!(dist2 > 0.0)) return;
+    const double dist = sqrt(dist2);
+    v3 wl = scl(v, 1.0 / dist);
+    const or_material* me = &s->mats[s->mat_id[lt]];
+    const double cos_l = -dot(nrm(cross(e1, e2)), wl);
+    if (!(cos_l > 0.0 || (me->two_sided && cos_l < 0.0))) return;
+    double n_[3] = {ns.x, ns.y, ns.z}, wo_[3] = {wo.x, wo.y, wo.z}, wi_[3] = {wl.x, wl.y, wl.z};
+    double fcos[3], pb;
+    if (!or_eval_bsdf(m, n_, wo_, wi_, fcos, &pb)) return;
+    const double pl = dist2 / (fabs(cos_l) * E->area);
+    const double wmis = or_power_heuristic(pl, pb);
+    double o_[3] = {org.x, org.y, org.z}, th;
+    if (or_intersect(s, o_, wi_, &th) >= 0 && th < dist * (1.0 - OR_SHADOW_MARGIN)) return;
+    for (int c = 0; c < 3; ++c) out[c] = t[c] * fcos[c] * me->Le[c] * wmis / pl;
+}
 
 static int or_is_normalized(int mode) {
     return mode == OR_MODE_HEUR_NORM || mode == OR_MODE_NET || mode == OR_MODE_NET_MIX;
@@ -523,6 +648,12 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
         for (int32_t d = 1; d <= D; ++d)
             if (((a->gate >> (2 * (d - 1))) & 3u) == OR_GATE_ADRRS) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
+    or_emitters E;
+    memset(&E, 0, sizeof(E));
+    if (a->nee && or_build_emitters(s, &E) != OR_OK) {
+        free(E.tri); free(E.cdf);
+        return OR_ERR_OOM;
+    }
     /* queue storage: the capacity, or for a pixel subset 64 slots per primary path
      * (a subset's queue cannot be capped the way the whole frame's is; running out of
      * that room is reported as OR_ERR_OOM rather than dropping children) */
@@ -534,7 +665,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     double* acc = (double*)calloc((size_t)npix * 3, sizeof(double));
     double* qbuf = (double*)calloc((size_t)room, sizeof(double));
     if (!cur || !nxt || !vx || !acc || !qbuf) {
-        free(cur); free(nxt); free(vx); free(acc); free(qbuf);
+        free(cur); free(nxt); free(vx); free(acc); free(qbuf); free(E.tri); free(E.cdf);
         return OR_ERR_OOM;
     }
     memset(st, 0, sizeof(*st));
@@ -566,6 +697,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             or_path* p = &cur[n++];
             or_camera_ray(s->cam, W, H, pix % W, pix / W, or_u01(w[0]), or_u01(w[1]), p->o, p->d);
             p->t[0] = p->t[1] = p->t[2] = 1.0;
+            p->pdf = 0.0;
             p->pixel = (uint32_t)pix;
             p->sample = (uint32_t)sidx;
             p->lineage = 0;
@@ -585,6 +717,8 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             v->tri = or_intersect(s, p->o, p->d, &t);
             v->q = 0.0;
             v->net_fallback = 0;
+            v->emit_w = 1.0;
+            v->nee[0] = v->nee[1] = v->nee[2] = 0.0;
             if (v->tri < 0) continue;
             v3 o = mk(p->o[0], p->o[1], p->o[2]), d = mk(p->d[0], p->d[1], p->d[2]);
             v3 hp = add(o, scl(d, t));
@@ -597,7 +731,19 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             const or_material* m = &s->mats[s->mat_id[v->tri]];
             int black = m->albedo[0] == 0.0f && m->albedo[1] == 0.0f && m->albedo[2] == 0.0f;
             int dead = p->t[0] == 0.0 && p->t[1] == 0.0 && p->t[2] == 0.0;
+            /* an emitter found by BSDF sampling: its MIS weight against the emitter
+             * sample the previous vertex took (the camera's vertex has none) */
+            if (a->nee && E.n > 0 && p->pdf > 0.0 && or_emits(m) && (front || m->two_sided)) {
+                const double pl = t * t / (fabs(dot(ng, d)) * E.area);
+                v->emit_w = or_power_heuristic(p->pdf, pl);
+            }
             if (black || dead || depth == D) continue;
+            if (a->nee) {
+                uint32_t w[4];
+                or_draw(a->seed_lo, a->seed_hi, a->frame, p->pixel, p->sample, (uint32_t)depth,
+                        OR_PURPOSE_NEE, p->lineage, w);
+                or_nee(s, &E, m, hp, ns, scl(d, -1.0), p->t, w, v->nee);
+            }
             int method;
             switch (a->mode) {
                 case OR_MODE_NONE: method = -1; break;
@@ -672,7 +818,8 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             }
             v->q = q;
         }
-        /* emission deposits, in queue order */
+        /* deposits, in queue order: emission (MIS-weighted with NEE), then the
+         * next-event contribution */
         for (int64_t i = 0; i < n; ++i) {
             const or_path* p = &cur[i];
             const or_hitrec* v = &vx[i];
@@ -681,11 +828,11 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             v3 v0 = or_tri_vertex(s, v->tri, 0);
             v3 ng = cross(sub(or_tri_vertex(s, v->tri, 1), v0), sub(or_tri_vertex(s, v->tri, 2), v0));
             int front = dot(ng, mk(p->d[0], p->d[1], p->d[2])) < 0.0;
-            if (front || m->two_sided)
-                for (int c = 0; c < 3; ++c) {
-                    acc[3 * (int64_t)p->pixel + c] += p->t[c] * m->Le[c];
-                    if (a->rec) a->rec[((int64_t)(depth - 1) * cap + i) * OR_REC + 3 + c] = p->t[c] * m->Le[c];
-                }
+            for (int c = 0; c < 3; ++c) {
+                double e = (front || m->two_sided) ? p->t[c] * m->Le[c] * v->emit_w : 0.0;
+                acc[3 * (int64_t)p->pixel + c] += e + v->nee[c];
+                if (a->rec) a->rec[((int64_t)(depth - 1) * cap + i) * OR_REC + 3 + c] = e + v->nee[c];
+            }
         }
         /* non-finite network factors took the heuristic's; any other non-finite factor
          * terminates its path */
@@ -740,7 +887,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 int64_t slot = S + j;
                 if (slot >= cap) { ++drop; continue; }
                 if (slot >= room) {
-                    free(cur); free(nxt); free(vx); free(acc); free(qbuf);
+                    free(cur); free(nxt); free(vx); free(acc); free(qbuf); free(E.tri); free(E.cdf);
                     return OR_ERR_OOM;
                 }
                 or_path* c = &nxt[slot];
@@ -751,14 +898,19 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 or_draw(a->seed_lo, a->seed_hi, a->frame, c->pixel, c->sample, (uint32_t)depth,
                         OR_PURPOSE_BSDF, c->lineage, w);
                 double wi[3], wt[3];
+                double wo[3] = {-p->d[0], -p->d[1], -p->d[2]};
                 if (m->type == 0) {
                     or_sample_lambert(v->n, or_u01(w[1]), or_u01(w[2]), wi);
                     for (int k = 0; k < 3; ++k) wt[k] = m->albedo[k];
                 } else {
-                    double wo[3] = {-p->d[0], -p->d[1], -p->d[2]};
                     double alb[3] = {m->albedo[0], m->albedo[1], m->albedo[2]};
                     or_sample_ggx(v->n, wo, alb, m->roughness, m->F0, or_u01(w[0]), or_u01(w[1]),
                                   or_u01(w[2]), wi, wt);
+                }
+                c->pdf = 0.0;
+                if (a->nee) {  /* the density the direction was drawn with, for MIS */
+                    double fc[3];
+                    or_eval_bsdf(m, v->n, wo, wi, fc, &c->pdf);
                 }
                 for (int k = 0; k < 3; ++k) {
                     c->o[k] = v->p[k] + OR_RAY_OFFSET * v->n[k];
@@ -792,6 +944,6 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             }
         }
     }
-    free(cur); free(nxt); free(vx); free(acc); free(qbuf);
+    free(cur); free(nxt); free(vx); free(acc); free(qbuf); free(E.tri); free(E.cdf);
     return OR_OK;
 }

@@ -15,6 +15,9 @@ these procedural scenes stand in for them:
                            seed-random small triangles.
 * ``icosphere_room``     - a room of seed-random icospheres and boxes, half Lambertian,
                            half GGX, with 4 ceiling quad lights.
+* ``lit_floor``          - a floor under an a x b rectangular emitter at height c whose
+                           corner lies straight above the one point a pencil camera sees
+                           (direct light there has a closed form).
 
 Binary layouts (shared with ``include/nrrs.h``):
 
@@ -323,6 +326,26 @@ def uneven_jobs(seed: int = 1, n_jobs: int = 64, tri_range=(1_000, 50_000), side
         scene = icosphere_room(1000 * seed + k, min_triangles=n_tri, subdiv=subdiv)
         jobs.append((scene, side, side, spp, D))
     return jobs
+
+
+def lit_floor(a: float = 0.6, b: float = 0.4, c: float = 0.5, Le: float = 10.0,
+              albedo: float = 0.5, floor_type: int = MAT_LAMBERT, roughness: float = 0.2) -> Scene:
+    """A 20 x 20 floor at y = 0 (two-sided) and, at height c, an a x b emitter facing
+    down over [0, a] x [0, b] in (x, z), made of three triangles of areas ab/6, ab/3 and
+    ab/2 (a fan from its corner at x = z = 0).  The camera sees the origin only: it sits
+    at (-0.6, 0.35, -0.6), looks at the origin and has a 0.001 degree field of view."""
+    A = np.array([0.0, c, 0.0])
+    B = np.array([a, c, 0.0])
+    E = np.array([a, c, b / 3.0])
+    Cc = np.array([a, c, b])
+    D = np.array([0.0, c, b])
+    tris = _quad(np.array([-10.0, 0.0, -10.0]), np.array([-10.0, 0.0, 10.0]),
+                 np.array([10.0, 0.0, 10.0]), np.array([10.0, 0.0, -10.0]))
+    tris += [np.r_[A, B, E], np.r_[A, E, Cc], np.r_[A, Cc, D]]
+    mats = [_material(floor_type, albedo, 0.0, roughness=roughness, two_sided=1),
+            _material(MAT_LAMBERT, 0.0, Le, two_sided=0)]
+    cam = _camera((-0.6, 0.35, -0.6), look=(0.6, -0.35, 0.6), vfov=0.001)
+    return Scene(np.array(tris), [0, 0, 1, 1, 1], np.array(mats), cam, "lit_floor")
 
 
 def rrsnet_init_params(seed: int = 1, dtype=np.float32) -> np.ndarray:
