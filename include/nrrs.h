@@ -143,6 +143,14 @@ typedef struct nrrs_render_opts {
                                    and write every vertex's suffix sum S (rgb, pixel bits):
                                    its own deposit plus its children's S, so S / t is the
                                    vertex's outgoing-radiance estimate               [NULL] */
+    int32_t nee;                /* next-event estimation (the paper's experiments run with
+                                   it on, Sec. 5): 1 = at every vertex that goes on, one
+                                   point on an emitting triangle (chosen by area, uniform
+                                   on it) and a shadow ray, combined with the emitters
+                                   that BSDF sampling hits by the power heuristic
+                                   (Veach 1997); a vertex's deposit is then its
+                                   MIS-weighted emission plus its unoccluded next-event
+                                   contribution.  0 = BSDF sampling only            [0]    */
 } nrrs_render_opts;
 
 /* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
@@ -156,7 +164,8 @@ typedef struct nrrs_render_opts {
 #define NRRS_STAGE_RRSNET 7    /* RRSNet (FP32) on the NET depths' features         */
 #define NRRS_STAGE_SHADE 8     /* emission deposit, RRS factor or features, sum q   */
 #define NRRS_STAGE_REVERSE 9   /* record mode: suffix sums, deepest depth first     */
-#define NRRS_N_STAGES 10
+#define NRRS_STAGE_SHADOW 10   /* next-event estimation: any-hit shadow rays        */
+#define NRRS_N_STAGES 11
 
 /* Per-render statistics; filled only when a non-NULL pointer is passed (the call then
  * synchronizes `stream`).  Index d-1 holds depth d (1-based, camera hit = depth 1). */
@@ -365,6 +374,8 @@ typedef struct nrrs_train_opts {
                                               recorded frame by systematic sampling
                                               with a per-step offset; 0 = 2^19
                                               (Sec. 4 "Training")                     [0] */
+    int32_t nee;                           /* next-event estimation in the training frame
+                                              (nrrs_render_opts.nee)                  [0] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {
@@ -492,6 +503,8 @@ typedef struct nrrs_mixdepth_opts {
                                               scene's running mean of its frames            */
     int32_t adrrs;                         /* candidates per depth: 0 = FIXED, HEUR, NET;
                                               1 = FIXED, ADRRS (NN), NET (the paper's set) */
+    int32_t nee;                           /* next-event estimation in the candidate renders
+                                              (nrrs_render_opts.nee)                        */
 } nrrs_mixdepth_opts;
 
 typedef struct nrrs_mixdepth_result {

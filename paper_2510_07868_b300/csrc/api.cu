@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bvh.h"
+#include "emitters.h"
 #include "train.cuh"
 #include "wavefront.cuh"
 
@@ -74,14 +75,25 @@ struct Workspace {
     FrameConsts* fc = nullptr;
     unsigned long long* flags = nullptr;  // look-back flags of the fused split
     long long n_flags = 0;
+    // next-event estimation: sampling pdfs of both queues and the per-slot shadow rays
+    bool has_nee = false;
+    float* qpdf[2] = {nullptr, nullptr};
+    float4* sh_o = nullptr;
+    float4* sh_d = nullptr;
+    float4* sh_c = nullptr;
 
     void release() {
         for (int k = 0; k < 2; ++k) {
             cudaFree(qo[k]);
             cudaFree(qd[k]);
             cudaFree(qt[k]);
+            cudaFree(qpdf[k]);
             qo[k] = qd[k] = qt[k] = nullptr;
+            qpdf[k] = nullptr;
         }
+        cudaFree(sh_o); cudaFree(sh_d); cudaFree(sh_c);
+        sh_o = sh_d = sh_c = nullptr;
+        has_nee = false;
         cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(feat); cudaFree(part); cudaFree(bcnt);
         cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st); cudaFree(fc);
         cudaFree(flags);
@@ -184,6 +196,8 @@ struct nrrs_scene {
     int bvh_width = 2;
     float4* tris = nullptr;
     nrrs_material* mats = nullptr;
+    float4* emit = nullptr;      // next-event estimation: emitter triangles and area CDF
+    float* emit_cdf = nullptr;
     float* params = nullptr;  // RRSNet weights, 2592 floats
     SceneView view{};
     CamView cam{};
@@ -229,13 +243,25 @@ struct nrrs_scene {
 
 namespace {
 
-nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool need_feat) {
+nrrs_status alloc_nee(Workspace& w) {
+    if (w.has_nee) return NRRS_OK;
+    for (int k = 0; k < 2; ++k) CK(dalloc(&w.qpdf[k], (size_t)w.cap));
+    CK(dalloc(&w.sh_o, (size_t)w.cap));
+    CK(dalloc(&w.sh_d, (size_t)w.cap));
+    CK(dalloc(&w.sh_c, (size_t)w.cap));
+    w.has_nee = true;
+    return NRRS_OK;
+}
+
+nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool need_feat,
+                             bool need_nee = false) {
     Workspace& w = sc->ws;
     if (w.cap >= cap && w.npix >= npix && w.st) {
         if (need_feat && !w.has_feat) {
             CK(dalloc(&w.feat, (size_t)w.cap * 4));
             w.has_feat = true;
         }
+        if (need_nee) return alloc_nee(w);
         return NRRS_OK;
     }
     w.release();
@@ -264,6 +290,7 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
     CK(dalloc(&w.flags, (size_t)w.n_flags));
     w.cap = cap;
     w.npix = npix;
+    if (need_nee) return alloc_nee(w);
     return NRRS_OK;
 }
 
@@ -281,6 +308,8 @@ void destroy(nrrs_scene* s) {
     cudaFree(s->nodes4);
     cudaFree(s->tris);
     cudaFree(s->mats);
+    cudaFree(s->emit);
+    cudaFree(s->emit_cdf);
     cudaFree(s->params);
     cudaFree(s->ref_mean);
     delete s;
@@ -386,7 +415,7 @@ CamView cam_view(const nrrs_camera& cam) {
 // (NULL for a batch, whose cameras live in the job table) into a new scene.
 nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri,
                          const nrrs_material* mats, int32_t n_mat, const nrrs_camera* cam,
-                         int device, nrrs_scene** out) {
+                         const EmitterHost& em, int device, nrrs_scene** out) {
     nrrs_scene* s = new nrrs_scene();
     s->device = device;
     s->n_sm = sm_count(device);
@@ -409,6 +438,20 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
     if ((e = cudaMemcpy(s->mats, mats, sizeof(nrrs_material) * n_mat, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy mats");
     if ((e = cudaMemset(s->params, 0, kNParams * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
+    if (!em.cdf.empty()) {
+        if ((e = dalloc(&s->emit, em.tri.size())) != cudaSuccess) return bail(e, "alloc emitters");
+        if ((e = dalloc(&s->emit_cdf, em.cdf.size())) != cudaSuccess) return bail(e, "alloc emitter cdf");
+        if ((e = cudaMemcpy(s->emit, em.tri.data(), sizeof(float4) * em.tri.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy emitters");
+        if ((e = cudaMemcpy(s->emit_cdf, em.cdf.data(), sizeof(float) * em.cdf.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy emitter cdf");
+    }
+    s->view.emit = s->emit;
+    s->view.emit_cdf = s->emit_cdf;
+    s->view.n_emit = (int)em.cdf.size();
+    s->view.inv_area = em.area > 0.0 ? (float)(1.0 / em.area) : 0.0f;
 
     if (bvh4 && !bvh4->nodes.empty()) {
         if ((e = dalloc(&s->nodes4, bvh4->nodes.size() * 8)) != cudaSuccess) return bail(e, "alloc nodes4");
@@ -473,7 +516,8 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     Bvh4Host bvh4;
     collapse_bvh4(bvh, &bvh4);
     const bool wide = bvh4.max_stack <= trace_stack_entries();
-    return upload_scene(bvh, wide ? &bvh4 : nullptr, n_tri, mats, n_mat, cam, device, out);
+    const EmitterHost em = build_emitters(tri, n_tri, tri_mat, mats);
+    return upload_scene(bvh, wide ? &bvh4 : nullptr, n_tri, mats, n_mat, cam, em, device, out);
 }
 
 nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
@@ -544,6 +588,7 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
     if (o.precision != 32 && o.precision != 16 && o.precision != 8)
         return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16 and 8");
+    if (o.nee != 0 && o.nee != 1) return fail(NRRS_ERR_INVALID_ARG, "nee must be 0 or 1");
     const long long C = (long long)width * height * spp * o.cap_factor;
     if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
     return NRRS_OK;
@@ -665,7 +710,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         if (trc != NRRS_OK) return trc;
         uses_net = true;
     }
-    nrrs_status rc = ensure_workspace(scene, C, npix, uses_net);
+    const bool nee = o.nee != 0;
+    nrrs_status rc = ensure_workspace(scene, C, npix, uses_net, nee);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
     if (batch && scene->jw_grid < ws.grid_red) {  // per-block, per-job partials
@@ -705,6 +751,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     rp.ref = uses_heur ? ref : nullptr;
     rp.params = params ? params : scene->params;
     rp.trace = o.d_trace;
+    rp.nee = nee ? 1 : 0;
     if (batch) {
         rp.jobs = scene->jw;
         rp.jobs.cap_factor = o.cap_factor;
@@ -749,7 +796,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                  reinterpret_cast<float*>(ws.part), ws.grid_red, s));
         if (batch) TIMED(NRRS_STAGE_INIT, launch_ref_prepare_jobs(rp, o.eps_rel, s));
         QueueView q[2];
-        for (int k = 0; k < 2; ++k) q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k]};
+        for (int k = 0; k < 2; ++k)
+            q[k] = QueueView{ws.qo[k], ws.qd[k], ws.qt[k], nee ? ws.qpdf[k] : nullptr};
         if (batch)
             TIMED(NRRS_STAGE_INIT, launch_camera_jobs(rp, P, q[0], s));
         else
@@ -760,6 +808,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         w.bcnt = ws.bcnt; w.boff = ws.boff; w.grid_split = ws.grid_split;
         w.flags = ws.flags;
         w.acc_s = ws.acc_s; w.acc_c = ws.acc_c; w.st = ws.st;
+        if (nee) {
+            w.sh_o = ws.sh_o; w.sh_d = ws.sh_d; w.sh_c = ws.sh_c;
+        }
         RenderParams r = rp;
         int cur = 0;
         for (int d = 1; d <= max_depth; ++d) {
@@ -777,6 +828,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             TIMED(NRRS_STAGE_EXTEND,
                   launch_trace(scene->view, q[cur], w, d, scene->grid_trace, r.jobs, s));
             TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
+            if (nee)  // shadow rays: unoccluded contributions join the deposits
+                TIMED(NRRS_STAGE_SHADOW,
+                      launch_shadow(scene->view, w, d, scene->grid_trace, r.jobs, s));
             if (kind == kFactorNet) {
                 TIMED(NRRS_STAGE_RRSNET,
                       launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
@@ -824,7 +878,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         const uint64_t sv[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
                                (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
                                o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile,
-                               (uint64_t)heur_frame};
+                               (uint64_t)heur_frame, (uint64_t)nee};
         for (uint64_t v : sv) shape = mix_key(shape, v);
         uint64_t args = shape;
         auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };
@@ -841,7 +895,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)scene->jw.part,
                                (uint64_t)(uintptr_t)scene->view.nodes4,
                                (uint64_t)(uintptr_t)scene->train.stat,
-                               (uint64_t)o.cap_factor};
+                               (uint64_t)o.cap_factor, (uint64_t)(uintptr_t)ws.sh_o,
+                               (uint64_t)(uintptr_t)ws.qpdf[0]};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -989,6 +1044,7 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
     bool wide = true;
     std::vector<nrrs_material> mats;
     std::vector<JobDev> jd(n_jobs);
+    EmitterHost em_all;  // each job's emitters, one range per job (materials rebased)
     int64_t n_tri = 0;
     long long pbase = 0, prim = 0;
     for (int j = 0; j < n_jobs; ++j) {
@@ -1026,6 +1082,22 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
         mats.insert(mats.end(), J.mats, J.mats + J.n_mat);
         n_tri += J.n_tri;
         JobDev& d = jd[j];
+        const EmitterHost em = build_emitters(J.tri, J.n_tri, J.tri_mat, J.mats);
+        d.emit_base = (int)em_all.cdf.size();
+        d.n_emit = (int)em.cdf.size();
+        d.inv_area = em.area > 0.0 ? (float)(1.0 / em.area) : 0.0f;
+        for (size_t k = 0; k < em.tri.size(); ++k) {
+            float4 v = em.tri[k];
+            if (k % 3 == 0) {
+                uint32_t m;
+                std::memcpy(&m, &v.w, 4);
+                m += (uint32_t)mat_off;
+                std::memcpy(&v.w, &m, 4);
+            }
+            em_all.tri.push_back(v);
+        }
+        em_all.cdf.insert(em_all.cdf.end(), em.cdf.begin(), em.cdf.end());
+        em_all.area += em.area;
         d.pixel_base = pbase;
         d.prim_base = prim;
         d.prims = (long long)J.width * J.height * J.spp;
@@ -1046,7 +1118,7 @@ nrrs_status nrrs_create_batch(const nrrs_job* jobs, int32_t n_jobs, int32_t devi
     }
     nrrs_scene* s = nullptr;
     nrrs_status rc = upload_scene(all, wide ? &all4 : nullptr, n_tri, mats.data(),
-                                  (int32_t)mats.size(), nullptr, device, &s);
+                                  (int32_t)mats.size(), nullptr, em_all, device, &s);
     if (rc != NRRS_OK) return rc;
     s->n_jobs = n_jobs;
     s->jobs_host = jd;
@@ -1438,6 +1510,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     ro.f_rate = o.f_rate;
     ro.d_pixel_ref = o.d_pixel_ref;
     ro.graph = o.graph;
+    ro.nee = o.nee;
     nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, o.max_depth, NRRS_RRS_NET, ro);
     if (rc != NRRS_OK) return rc;
     if (o.warmup_steps < 0 || !(o.eps > 0.0f) || !(o.ema_decay >= 0.0f && o.ema_decay < 1.0f) ||
@@ -1651,6 +1724,7 @@ nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* op
     ro.seed_hi = o.seed_hi;
     ro.frame = o.frame;  // every candidate sees the same random numbers
     ro.update_ref = 0;
+    ro.nee = o.nee;
     nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, D, NRRS_RRS_NET_MIX, ro);
     if (rc != NRRS_OK) return rc;
     DeviceGuard g(scene->device);

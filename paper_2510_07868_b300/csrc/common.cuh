@@ -23,6 +23,9 @@ constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 constexpr uint32_t kPurposeJitter = 0u;
 constexpr uint32_t kPurposeBsdf = 1u;
 constexpr uint32_t kPurposeRrs = 3u;
+constexpr uint32_t kPurposeNee = 5u;
+// A shadow ray ends at (1 - margin) x the distance to its emitter point.
+constexpr float kShadowMargin = 1e-4f;
 
 enum Mode : int { kNone = 0, kPlainRR = 1, kHeurNorm = 2, kNet = 3, kNetMix = 4 };
 enum Gate : int { kGateNet = 0, kGateHeur = 1, kGateFixed = 2, kGateAdrrs = 3 };

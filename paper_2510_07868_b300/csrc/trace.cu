@@ -1,6 +1,7 @@
-// Closest-hit BVH2 traversal for sm_103a: the extension stage of one bounce (Sec. 2,
-// the wavefront formulation the method runs in).  Persistent warps claim rays from the
-// live queue; the traversal stack lives in shared memory.
+// BVH traversal for sm_103a: the closest hit of the extension stage of one bounce (Sec. 2,
+// the wavefront formulation the method runs in) and the any-hit test of next-event
+// estimation's shadow rays.  Persistent warps claim rays from the live queue; the
+// traversal stack lives in shared memory.
 #include <cfloat>
 
 #include "wavefront.cuh"
@@ -36,14 +37,17 @@ __device__ __forceinline__ float safe_rcp(float x) {
     return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x);
 }
 
-__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, int root, Hit& h) {
+// t_max bounds the query; a shadow ray (t_max finite) starts with id 0 so that a hit at
+// exactly t_max does not count (the oracle's test is t < t_max).
+__device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, int root, Hit& h,
+                                         float t_max = FLT_MAX) {
     r.o = o;
     r.d = d;
     r.inv = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     r.node = root;
     r.sp = 0;
-    h = Hit{FLT_MAX, -1, 0xFFFFFFFFu};
+    h = Hit{t_max, -1, t_max == FLT_MAX ? 0xFFFFFFFFu : 0u};
 }
 
 // Moller-Trumbore against triangle reference s; keeps the closest hit, equal distances
@@ -175,14 +179,17 @@ __device__ __forceinline__ void visit_inner(const SceneView& sc, Ray& r, const H
 // test their leaves together.  Each slot's hit depends only on that slot's ray (the
 // closest hit with the lower-index tie rule does not depend on the visiting order), so
 // the result is deterministic.
-template <int WIDTH>
+// ANY: the shadow rays of next-event estimation, one per slot (t_max <= 0: none); the
+// query ends at the first hit before t_max, and an unoccluded ray adds its
+// contribution to the slot's deposit.
+template <int WIDTH, bool ANY>
 __global__ void __launch_bounds__(kExtendThreads, 4)
 k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
     __shared__ int s_stack[kStack * kExtendThreads];
     int* stk = s_stack + threadIdx.x;
     DevStats* st = w.st;
     const long long n = st->live[depth - 1];
-    unsigned long long* ctr = &st->fetch[depth - 1];
+    unsigned long long* ctr = ANY ? &st->sfetch[depth - 1] : &st->fetch[depth - 1];
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     long long idx = -1;
@@ -200,27 +207,33 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
             if (need) {
                 const long long my = (long long)base + __popc(need_mask & lt_mask);
                 if (my < n) {
-                    idx = my;
-                    const float4 o4 = cur.o[idx];
-                    // a batched render starts each ray at the root of its job's scene
-                    int root = 0;
-                    if (jobs.job) {
-                        const JobDev* J =
-                            jobs.job + job_of_pixel(jobs.job, jobs.n, __float_as_uint(o4.w));
-                        root = WIDTH == 4 ? __ldg(&J->root4) : __ldg(&J->root);
+                    const float4 o4 = ANY ? w.sh_o[my] : cur.o[my];
+                    if (!ANY || o4.w > 0.0f) {  // a slot without a shadow ray is skipped
+                        idx = my;
+                        // a batched render starts each ray at the root of its job's scene
+                        int root = 0;
+                        if (jobs.job) {
+                            const uint32_t pix = __float_as_uint(ANY ? w.dep[idx].w : o4.w);
+                            const JobDev* J = jobs.job + job_of_pixel(jobs.job, jobs.n, pix);
+                            root = WIDTH == 4 ? __ldg(&J->root4) : __ldg(&J->root);
+                        }
+                        if (ANY)
+                            ray_init(ray, xyz(o4), xyz(w.sh_d[idx]), root, h, o4.w);
+                        else
+                            ray_init(ray, xyz(o4), xyz(cur.d[idx]), root, h);
                     }
-                    ray_init(ray, xyz(o4), xyz(cur.d[idx]), root, h);
                 } else {
                     exhausted = true;
                 }
             }
         }
-        if (__all_sync(0xffffffffu, idx < 0)) break;
+        // lanes that skipped a slot claim again on the next round
+        if (__all_sync(0xffffffffu, idx < 0 && exhausted)) break;
         if (WIDTH == 4) {
             if (idx < 0) continue;
             bool done = false;
             for (int step = 0; step < kSteps && !done; ++step)
-                done = visit_node4(sc, ray, h, stk, kExtendThreads);
+                done = visit_node4(sc, ray, h, stk, kExtendThreads) || (ANY && h.slot >= 0);
             if (!done) continue;
         } else {
             // every lane of the warp runs the step loop (the vote needs all of them)
@@ -234,9 +247,21 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
             if (idx < 0) continue;
             for (int k = 0; k < cnt0 && leaf0 >= 0; ++k) intersect_tri(sc, ray, h, leaf0 + k);
             for (int k = 0; k < cnt1 && leaf1 >= 0; ++k) intersect_tri(sc, ray, h, leaf1 + k);
+            if (ANY && h.slot >= 0) ray.node = -1;  // occluded: the query is over
             if (ray.node >= 0) continue;
         }
-        w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
+        if (ANY) {
+            if (h.slot < 0) {
+                const float4 c = w.sh_c[idx];
+                float4 e = w.dep[idx];
+                e.x += c.x;
+                e.y += c.y;
+                e.z += c.z;
+                w.dep[idx] = e;
+            }
+        } else {
+            w.hit[idx] = make_float2(h.t, __int_as_float(h.slot));
+        }
         idx = -1;
     }
 }
@@ -248,19 +273,31 @@ int extend_block_threads() { return kExtendThreads; }
 int trace_stack_entries() { return kStack; }
 
 int max_blocks_trace() {
-    int n2 = 1, n4 = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_trace<2>, kExtendThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n4, k_trace<4>, kExtendThreads, 0);
-    const int nb = n2 < n4 ? n2 : n4;
+    int nb = 1 << 30;
+    int n[4] = {1, 1, 1, 1};
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_trace<2, false>, kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_trace<4, false>, kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_trace<2, true>, kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_trace<4, true>, kExtendThreads, 0);
+    for (int k = 0; k < 4; ++k) nb = n[k] < nb ? n[k] : nb;
     return nb < 1 ? 1 : nb;
 }
 
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
                   const JobWork& jobs, cudaStream_t s) {
     if (sc.nodes4)
-        k_trace<4><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+        k_trace<4, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
     else
-        k_trace<2><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+        k_trace<2, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+}
+
+void launch_shadow(const SceneView& sc, const WorkView& w, int depth, int grid,
+                   const JobWork& jobs, cudaStream_t s) {
+    const QueueView none{};
+    if (sc.nodes4)
+        k_trace<4, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
+    else
+        k_trace<2, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
 }
 
 }  // namespace nrrs

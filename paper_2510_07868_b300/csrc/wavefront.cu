@@ -109,9 +109,10 @@ __device__ __forceinline__ V3 cosine_dir(V3 n, float u1, float u2) {  // Shirley
 }
 
 // GGX (Walter et al. 2007) + Lambert mixture, lobes picked with probability 1/2.
-// Returns the weight f cos / pdf per channel (0 below the shading hemisphere).
+// Returns the weight f cos / pdf per channel (0 below the shading hemisphere) and, in
+// pdf_out, the solid-angle pdf of the direction.
 __device__ __forceinline__ V3 sample_ggx(V3 n, V3 wo, const nrrs_material& m, float ulobe,
-                                         float u1, float u2, V3* wi_out) {
+                                         float u1, float u2, V3* wi_out, float* pdf_out) {
     const float a = m.roughness;
     V3 wi;
     if (ulobe < 0.5f) {
@@ -128,6 +129,7 @@ __device__ __forceinline__ V3 sample_ggx(V3 n, V3 wo, const nrrs_material& m, fl
         wi = cosine_dir(n, u1, u2);
     }
     *wi_out = wi;
+    *pdf_out = 0.0f;
     const float cos_i = dot3(wi, n), cos_o = dot3(wo, n);
     if (cos_i <= 0.0f || cos_o <= 0.0f) return v3(0.0f, 0.0f, 0.0f);
     const V3 h = normalize3(wo + wi);
@@ -147,8 +149,92 @@ __device__ __forceinline__ V3 sample_ggx(V3 n, V3 wo, const nrrs_material& m, fl
     const float pdf = 0.5f * D * cos_h / (4.0f * fabsf(oh)) + 0.5f * cos_i / 3.141592653589793f;
     const float kd = (1.0f - m.F0) / 3.141592653589793f;
     const float s = cos_i / pdf;
+    *pdf_out = pdf;
     return v3((spec + kd * m.albedo[0]) * s, (spec + kd * m.albedo[1]) * s,
               (spec + kd * m.albedo[2]) * s);
+}
+
+// f(wo, wi) cos_i per channel for a given direction, and the pdf with which the
+// material's own sampling picks it (Lambertian: albedo / pi and cos_i / pi; the GGX
+// mixture as sampled above).  Zero below the shading hemisphere.
+__device__ __forceinline__ V3 bsdf_eval(V3 n, V3 wo, V3 wi, const nrrs_material& m, float* pdf) {
+    const float cos_i = dot3(wi, n), cos_o = dot3(wo, n);
+    *pdf = 0.0f;
+    if (cos_i <= 0.0f || cos_o <= 0.0f) return v3(0.0f, 0.0f, 0.0f);
+    constexpr float kInvPi = 0.318309886183791f;
+    if (m.type == 0) {
+        *pdf = cos_i * kInvPi;
+        return v3(m.albedo[0] * kInvPi * cos_i, m.albedo[1] * kInvPi * cos_i,
+                  m.albedo[2] * kInvPi * cos_i);
+    }
+    const float a = m.roughness, a2 = a * a;
+    const V3 h = normalize3(wo + wi);
+    const float cos_h = dot3(h, n), oh = dot3(wo, h);
+    const float den = (a2 - 1.0f) * cos_h * cos_h + 1.0f;
+    const float D = a2 / (3.141592653589793f * den * den);
+    auto G1 = [&](float cw) {
+        const float c2 = cw * cw;
+        return 2.0f / (1.0f + sqrtf(1.0f + a2 * (1.0f - c2) / c2));
+    };
+    const float om = 1.0f - dot3(wi, h);
+    const float om2 = om * om;
+    const float Fr = m.F0 + (1.0f - m.F0) * (om2 * om2 * om);
+    const float spec = D * G1(cos_o) * G1(cos_i) * Fr / (4.0f * cos_o * cos_i);
+    const float kd = (1.0f - m.F0) * kInvPi;
+    *pdf = 0.5f * D * cos_h / (4.0f * fabsf(oh)) + 0.5f * cos_i * kInvPi;
+    return v3((spec + kd * m.albedo[0]) * cos_i, (spec + kd * m.albedo[1]) * cos_i,
+              (spec + kd * m.albedo[2]) * cos_i);
+}
+
+// Power heuristic with exponent 2 (Veach 1997), the weight of the technique with
+// density a against b, as 1 / (1 + (b / a)^2) so that large densities do not overflow.
+__device__ __forceinline__ float power_heuristic(float a, float b) {
+    const float r = b / a;
+    return 1.0f / (1.0f + r * r);
+}
+
+// Next-event estimation at one vertex (hit point p, shading normal ns, outgoing wo,
+// throughput t) from the NEE draw r: an emitter by area (r.x), a uniform point on it
+// (sqrt(u1) (1 - u2), sqrt(u1) u2 along its edges; r.y, r.z) and the shadow ray from the
+// offset origin to (1 - margin) of its distance.  The unoccluded contribution is
+// t f cos_x Le w / p_light with p_light = dist^2 / (|cos_l| A) and w the power heuristic
+// against the BSDF's pdf of the direction.  Writes the slot's shadow ray (t_max 0: none).
+__device__ __forceinline__ void nee_vertex(const float4* __restrict__ emit,
+                                           const float* __restrict__ cdf, int n_emit,
+                                           float inv_area, const nrrs_material* mats, V3 p,
+                                           V3 ns, V3 wo, const nrrs_material& m, float4 t4, U4 r,
+                                           float4* sh_o, float4* sh_d, float4* sh_c) {
+    *sh_o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (n_emit <= 0) return;
+    const float u = u01(r.x);
+    int lo = 0, hi = n_emit - 1;
+    while (lo < hi) {  // first k with u < cdf[k]
+        const int mid = (lo + hi) >> 1;
+        if (u < __ldg(&cdf[mid])) hi = mid; else lo = mid + 1;
+    }
+    const float4 a0 = __ldg(&emit[3 * lo]), a1 = __ldg(&emit[3 * lo + 1]),
+                 a2 = __ldg(&emit[3 * lo + 2]);
+    const float su = sqrtf(u01(r.y)), u2 = u01(r.z);
+    const V3 e1 = xyz(a1), e2 = xyz(a2);
+    const V3 y = xyz(a0) + (e1 * (su * (1.0f - u2)) + e2 * (su * u2));
+    const V3 org = p + ns * kRayOffset;
+    const V3 v = y - org;
+    const float dist2 = dot3(v, v);
+    if (!(dist2 > 0.0f)) return;
+    const float dist = sqrtf(dist2);
+    const V3 wl = v * (1.0f / dist);
+    const nrrs_material& me = mats[__float_as_uint(a0.w)];
+    const float cos_l = -dot3(normalize3(cross3(e1, e2)), wl);
+    if (!(cos_l > 0.0f || (me.two_sided && cos_l < 0.0f))) return;
+    float pb;
+    const V3 fc = bsdf_eval(ns, wo, wl, m, &pb);
+    if (!(pb > 0.0f)) return;
+    const float pl = dist2 * inv_area / fabsf(cos_l);
+    const float s = power_heuristic(pl, pb) / pl;
+    *sh_o = make_float4(org.x, org.y, org.z, dist * (1.0f - kShadowMargin));
+    *sh_d = make_float4(wl.x, wl.y, wl.z, 0.0f);
+    *sh_c = make_float4(t4.x * fc.x * me.Le[0] * s, t4.y * fc.y * me.Le[1] * s,
+                        t4.z * fc.z * me.Le[2] * s, 0.0f);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -232,8 +318,10 @@ __global__ void k_camera_jobs(RenderParams rp, long long P, QueueView out) {
 // Extension of depth `depth`, part 2 (fixed grid-stride, coherent): emission deposit,
 // termination, and the RRS factor q_orig of each vertex; NET depths store the 16
 // features and q = -1 for the RRSNet kernel.  Non-NET depths also write the block's
-// FP64 partial sum of q (fixed assignment, so the sum is reproducible).
-template <int KIND>
+// FP64 partial sum of q (fixed assignment, so the sum is reproducible).  With NEE the
+// emission found by BSDF sampling takes its MIS weight, and every vertex that goes on
+// (the ones that get a factor) writes its shadow ray and contribution.
+template <int KIND, bool NEE>
 __global__ void __launch_bounds__(256)
 k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
     __shared__ double sh[32];
@@ -250,6 +338,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
         const float4 o4 = cur.o[i];
         float q = 0.0f;
         float4 dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
+        float4 so = make_float4(0.0f, 0.0f, 0.0f, 0.0f), sd = so, sk = so;
         if (slot >= 0) {
             const float4 d4 = cur.d[i];
             const float4 t4 = cur.t[i];
@@ -258,18 +347,16 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
             const nrrs_material m = sc.mats[mi];
             const V3 d = xyz(d4);
             const bool front = dot3(ng, d) < 0.0f;
-            if (front || m.two_sided) {
-                dep.x = t4.x * m.Le[0];
-                dep.y = t4.y * m.Le[1];
-                dep.z = t4.z * m.Le[2];
-            }
-            const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
-            const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
-            // the job's depth limit, scene box and HEUR floor in a batched render
+            // the job's depth limit, scene box, HEUR floor and emitters in a batched render
             int Dmax = rp.D;
             float lo3[3] = {sc.lo[0], sc.lo[1], sc.lo[2]};
             float ie3[3] = {sc.inv_ext[0], sc.inv_ext[1], sc.inv_ext[2]};
             float epsI = eps_I;
+            uint32_t lpix = fbits(o4.w);
+            const float4* emit = sc.emit;
+            const float* ecdf = sc.emit_cdf;
+            int n_emit = sc.n_emit;
+            float inv_area = sc.inv_area;
             if (rp.jobs.job) {
                 const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, fbits(o4.w));
                 const JobDev* J = rp.jobs.job + j;
@@ -279,8 +366,36 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     ie3[k] = J->inv_ext[k];
                 }
                 epsI = rp.jobs.eps_I[j];
+                lpix -= (uint32_t)J->pixel_base;
+                if (NEE) {
+                    emit += 3 * (size_t)J->emit_base;
+                    ecdf += J->emit_base;
+                    n_emit = J->n_emit;
+                    inv_area = J->inv_area;
+                }
             }
+            if (front || m.two_sided) {
+                float we = 1.0f;  // MIS weight against the previous vertex's emitter sample
+                if (NEE && depth > 1 && n_emit > 0 &&
+                    (m.Le[0] > 0.0f || m.Le[1] > 0.0f || m.Le[2] > 0.0f)) {
+                    const float pb = cur.pdf[i];
+                    if (pb > 0.0f)
+                        we = power_heuristic(pb, hh.x * hh.x * inv_area / fabsf(dot3(ng, d)));
+                }
+                dep.x = t4.x * m.Le[0] * we;
+                dep.y = t4.y * m.Le[1] * we;
+                dep.z = t4.z * m.Le[2] * we;
+            }
+            const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
+            const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
             if (!black && !dead && depth < Dmax) {
+                if (NEE) {
+                    const U4 r = draw(rp.fc->key0, rp.fc->key1, lpix, fbits(t4.w),
+                                      (uint32_t)depth, kPurposeNee, fbits(d4.w));
+                    const V3 ns = front ? ng : ng * -1.0f;
+                    nee_vertex(emit, ecdf, n_emit, inv_area, sc.mats, xyz(o4) + d * hh.x, ns,
+                               d * -1.0f, m, t4, r, &so, &sd, &sk);
+                }
                 if (KIND == kFactorOne) {
                     q = 1.0f;
                 } else if (KIND == kFactorPlain) {
@@ -310,6 +425,13 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
         }
         w.q[i] = q;
         w.dep[i] = dep;
+        if (NEE) {
+            w.sh_o[i] = so;
+            if (so.w > 0.0f) {
+                w.sh_d[i] = sd;
+                w.sh_c[i] = sk;
+            }
+        }
         if (KIND < kFactorNet) qsum += (double)q;
     }
     if (KIND < kFactorNet) {
@@ -734,12 +856,15 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
                 const uint32_t lin = base + j * kLineageStep;
                 const U4 r = draw(key0, key1, lpix, smp, (uint32_t)depth, kPurposeBsdf, lin);
                 V3 wi, wt;
+                float pdf;
                 if (m.type == 0) {
                     wi = cosine_dir(ns, u01(r.y), u01(r.z));
                     wt = v3(m.albedo[0], m.albedo[1], m.albedo[2]);
+                    pdf = fmaxf(dot3(wi, ns), 0.0f) * 0.318309886183791f;
                 } else {
-                    wt = sample_ggx(ns, d * -1.0f, m, u01(r.x), u01(r.y), u01(r.z), &wi);
+                    wt = sample_ggx(ns, d * -1.0f, m, u01(r.x), u01(r.y), u01(r.z), &wi, &pdf);
                 }
+                if (rp.nee) nxt.pdf[dst] = pdf;  // for the MIS weight at the child's hit
                 nxt.o[dst] = make_float4(org.x, org.y, org.z, o4.w);
                 nxt.d[dst] = make_float4(wi.x, wi.y, wi.z, bitsf(lin));
                 nxt.t[dst] = make_float4(t4.x * wt.x * iq, t4.y * wt.y * iq, t4.z * wt.z * iq, t4.w);
@@ -884,13 +1009,17 @@ void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cu
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s) {
     const int G = w.grid_red;
+#define NRRS_SHADE(K)                                                            \
+    (rp.nee ? k_shade<K, true><<<G, 256, 0, s>>>(sc, cur, w, rp, depth)          \
+            : k_shade<K, false><<<G, 256, 0, s>>>(sc, cur, w, rp, depth))
     switch (kind) {
-        case kFactorOne: k_shade<kFactorOne><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
-        case kFactorPlain: k_shade<kFactorPlain><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
-        case kFactorHeur: k_shade<kFactorHeur><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
-        case kFactorNet: k_shade<kFactorNet><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
-        default: k_shade<kFactorAdrrs><<<G, 256, 0, s>>>(sc, cur, w, rp, depth); break;
+        case kFactorOne: NRRS_SHADE(kFactorOne); break;
+        case kFactorPlain: NRRS_SHADE(kFactorPlain); break;
+        case kFactorHeur: NRRS_SHADE(kFactorHeur); break;
+        case kFactorNet: NRRS_SHADE(kFactorNet); break;
+        default: NRRS_SHADE(kFactorAdrrs); break;
     }
+#undef NRRS_SHADE
 }
 
 void launch_sum_q(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,

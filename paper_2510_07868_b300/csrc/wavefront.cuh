@@ -15,6 +15,12 @@ struct SceneView {
     const nrrs_material* mats;
     float lo[3];          // scene box, for the position feature
     float inv_ext[3];     // 1 / extent, 0 for a flat axis (feature = 0.5 there)
+    // next-event estimation: emitting triangles (3 float4 each: v0 + material bits,
+    // e1, e2) and their area CDF; a batch keeps one range per job (JobDev)
+    const float4* emit;
+    const float* emit_cdf;
+    int n_emit;
+    float inv_area;       // 1 / total emitter area
 };
 
 struct CamView {
@@ -28,6 +34,7 @@ struct QueueView {
     float4* o;
     float4* d;
     float4* t;
+    float* pdf;  // next-event estimation: solid-angle pdf the direction was sampled with
 };
 
 // Device-resident per-render statistics; the host copies it once per render.
@@ -40,6 +47,7 @@ struct DevStats {
     float F[kMaxDepth];
     unsigned long long fetch[kMaxDepth];  // dynamic ray-fetch counters of k_extend
     unsigned long long tiles[kMaxDepth];  // tile claims of the fused split
+    unsigned long long sfetch[kMaxDepth]; // dynamic shadow-ray fetch counters
     unsigned long long nonfinite;
     unsigned long long net_evals;
     double alpha_cur;               // adaptive alpha (Eq. f_rate_prime), carried over depths
@@ -64,6 +72,11 @@ struct WorkView {
     float4* acc_s;     // [npix] Kahan sum (rgb)
     float4* acc_c;     // [npix] Kahan compensation (rgb)
     DevStats* st;
+    // next-event estimation, per slot: shadow ray (origin, t_max <= 0: none),
+    // (direction, -), and the unoccluded contribution (rgb, -)
+    float4* sh_o;
+    float4* sh_d;
+    float4* sh_c;
 };
 
 // Per-frame values read by the kernels from device memory, so that one recorded launch
@@ -85,6 +98,8 @@ struct JobDev {
     int root;            // BVH2 root node of the job's scene
     int root4;           // four-wide root node (when the batch has a four-wide tree)
     float lo[3], inv_ext[3];  // the job's scene box (position feature)
+    int emit_base, n_emit;    // the job's emitters in the merged emitter table
+    float inv_area;           // 1 / the job's total emitter area
     CamView cam;
 };
 
@@ -125,6 +140,7 @@ struct RenderParams {
     uint32_t* trace;      // optional per-depth trace
     uint32_t* rec_first;  // record mode: first child slot of every parent of this depth
     uint32_t* rec_X;      // record mode: children requested by every parent of this depth
+    int nee;              // next-event estimation with MIS at every vertex
 };
 
 enum FactorKind : int {
@@ -145,8 +161,13 @@ void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double al
 void launch_camera(const CamView& cam, const RenderParams& rp, QueueView out, cudaStream_t s);
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
                   const JobWork& jobs, cudaStream_t s);
+// Shadow rays of next-event estimation (any hit): adds the contribution of every
+// unoccluded ray to the slot's deposit.
+void launch_shadow(const SceneView& sc, const WorkView& w, int depth, int grid,
+                   const JobWork& jobs, cudaStream_t s);
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s);
+
 void launch_sum_q(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
                   cudaStream_t s);
 void launch_normalize_depth(const WorkView& w, const RenderParams& rp, int depth, int normalized,

@@ -23,9 +23,9 @@ RRS_NONE, RRS_PLAIN_RR, RRS_HEUR_NORM, RRS_NET, RRS_NET_MIX = range(5)
 GATE_NET, GATE_HEUR, GATE_FIXED, GATE_ADRRS = 0, 1, 2, 3
 STATUS_OVERFLOW_DROPPED, STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_HEUR_FALLBACK = 1, 2, 4, 8
 MAX_DEPTH = 32
-STAGES = 10
+STAGES = 11
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
-               "finalize", "rrsnet", "shade", "reverse"]
+               "finalize", "rrsnet", "shade", "reverse", "shadow"]
 NET_RRSNET, NET_RRSNET_TRAIN, NET_STATNET = 0, 1, 2
 STATNET_PARAMS = 2752
 N_FEATURES = 16
@@ -55,13 +55,15 @@ class RenderOpts(C.Structure):
                 ("q_max", C.c_float), ("eps_rel", C.c_float), ("boxcox_lambda", C.c_float),
                 ("precision", C.c_int32), ("gate", C.c_uint64), ("d_pixel_ref", C.c_void_p),
                 ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
-                ("profile", C.c_int32), ("graph", C.c_int32), ("d_suffix", C.c_void_p)]
+                ("profile", C.c_int32), ("graph", C.c_int32), ("d_suffix", C.c_void_p),
+                ("nee", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
                 eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
-                update_ref=1, reset_ref=0, d_trace=None, profile=0, graph=0, d_suffix=None)
+                update_ref=1, reset_ref=0, d_trace=None, profile=0, graph=0, d_suffix=None,
+                nee=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -98,14 +100,14 @@ class TrainOpts(C.Structure):
                 ("gamma3", C.c_float), ("eps", C.c_float), ("ema_decay", C.c_float),
                 ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p), ("alpha_mix", C.c_float),
                 ("error_filter_radius", C.c_int32), ("graph", C.c_int32),
-                ("batch_size", C.c_int32)]
+                ("batch_size", C.c_int32), ("nee", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(width=256, height=256, spp=2, max_depth=16, seed_lo=1, seed_hi=0, frame=0,
                 warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
                 gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None,
-                alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0)
+                alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0, nee=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -149,7 +151,7 @@ class MixDepthOpts(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
                 ("max_depth", C.c_int32), ("t_d", C.c_int32), ("max_candidates", C.c_int32),
                 ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32),
-                ("d_pixel_ref", C.c_void_p), ("adrrs", C.c_int32)]
+                ("d_pixel_ref", C.c_void_p), ("adrrs", C.c_int32), ("nee", C.c_int32)]
 
 
 class MixDepthResult(C.Structure):
@@ -467,9 +469,9 @@ def nrrs_mixdepth_candidates(max_depth, t_d):
 
 
 def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1, 0), frame=0,
-                         d_pixel_ref=None, max_candidates=0, adrrs=0, stream=None):
+                         d_pixel_ref=None, max_candidates=0, adrrs=0, nee=0, stream=None):
     o = MixDepthOpts(width, height, spp, max_depth, t_d, max_candidates, seed[0], seed[1], frame,
-                     _ptr(d_pixel_ref), adrrs)
+                     _ptr(d_pixel_ref), adrrs, nee)
     r = MixDepthResult()
     _check(_lib.nrrs_mixdepth_search(scene, C.byref(o), _stream(stream), C.byref(r)))
     return {name: getattr(r, name) for name, _ in r._fields_}
