@@ -21,6 +21,7 @@ import json
 import os
 import re
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -37,7 +38,7 @@ PRETRAIN_STEPS = 300   # untimed online training before the timed steps (20 warm
 WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P; "
             "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
             "+ the 16 spp inference frame")
-# algorithmic bytes per unit of each stage ("Kernels and rooflines")
+# algorithmic bytes per unit of each stage
 BYTES_PER_RAY_SHADE = 48 + 8 + 4 + 16           # path state, hit in; q, deposit out
 BYTES_PER_SLOT_DEPOSIT = 16                     # last depth: deposit only
 BYTES_PER_PARENT_SPLIT = 16 + 4 + 48 + 8        # deposit, q, path state, hit
@@ -114,8 +115,10 @@ class ClockSampler:
 
     def _launch_smi(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self._path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.index}.csv")
+            # the raw samples go to $NRRS_CLOCKS_DIR (default: the system temp folder)
+            out_dir = os.environ.get("NRRS_CLOCKS_DIR", tempfile.gettempdir())
+            os.makedirs(out_dir, exist_ok=True)
+            self._path = os.path.join(out_dir, f"clocks_gpu{self.index}.csv")
             self._f = open(self._path, "w")
             self._proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.SMI_FIELDS}",
@@ -269,30 +272,32 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU leg
-def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
+def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0):
     """1/(relMSE x seconds) of the estimators on the same B300: PLAIN_RR (throughput
     roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet), ADRRS_NN (StatNet's
     radiance over the pixel estimate at every depth), NET_MIX (the Mix-Depth gate over
     FIXED / HEUR / NET) and NET_MIX_ADRRS (over FIXED / ADRRS (NN) / NET, the paper's
     set), each averaging 16 frames of 16 spp, against a 4096-spp plain path-traced
-    reference (256 frames x 16 spp, no RRS)."""
+    reference (256 frames x 16 spp, no RRS).  nee=1: every render, the reference and the
+    Mix-Depth searches with next-event estimation."""
     ref = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
     img = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     n_ref = 256
     for f in range(n_ref):
         nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NONE,
-                         nrrs.RenderOpts.defaults(frame=50_000 + f, seed_hi=seed_hi, update_ref=0),
+                         nrrs.RenderOpts.defaults(frame=50_000 + f, seed_hi=seed_hi, update_ref=0,
+                                                  nee=nee),
                          img, stream, False)
         ref += img
     ref32 = (ref / n_ref).float().contiguous()
     out = torch.zeros(1, dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
     gate_res = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
-                                         d_pixel_ref=None, stream=stream)
+                                         d_pixel_ref=None, nee=nee, stream=stream)
     search_s = time.perf_counter() - t0
     # the paper's candidate set per depth: FIXED, ADRRS (NN), NRRS
     gate_adrrs = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
-                                           d_pixel_ref=None, adrrs=1, stream=stream)
+                                           d_pixel_ref=None, adrrs=1, nee=nee, stream=stream)
     all_adrrs = sum(nrrs.GATE_ADRRS << (2 * d) for d in range(DEPTH))
     res = {}
     for name, mode, gate in (("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0),
@@ -310,7 +315,7 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
         for f in range(frames):
             st = nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
                                   nrrs.RenderOpts.defaults(frame=90_000 + f, seed_hi=seed_hi,
-                                                           gate=gate, update_ref=0),
+                                                           gate=gate, update_ref=0, nee=nee),
                                   img, stream, True)
             segs += st["segments"]
             acc += img
@@ -325,7 +330,7 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi):
                      "segments": segs, "ray_efficiency": 1.0 / (rel * segs)}
     base = res["PLAIN_RR"]["efficiency"]
     return {
-        "reference": f"no-RRS path tracing, {n_ref * SPP} spp",
+        "reference": f"no-RRS path tracing{' with NEE' if nee else ''}, {n_ref * SPP} spp",
         "frames_per_mode": 16, "modes": res,
         "net_vs_plain_rr": res["NET"]["efficiency"] / base,
         "net_mix_vs_plain_rr": res["NET_MIX"]["efficiency"] / base,
@@ -417,6 +422,9 @@ def run_ours(args, rank, world, local_rank):
     net_evals = 0
     children = 0
     fallbacks = 0
+    # a profiler started with "profile from start off" (ncu --profile-from-start off)
+    # records the timed steps only; without a profiler these calls do nothing
+    torch.cuda.profiler.start()
     ev0.record(stream)
     for k in range(args.steps):
         et0.record(stream)
@@ -436,6 +444,7 @@ def run_ours(args, rank, world, local_rank):
         children += int(st["live"][1:].sum())
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -493,6 +502,21 @@ def run_ours(args, rank, world, local_rank):
     eff = None
     if rank == 0 and not args.no_efficiency:
         eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi)
+        # the same comparison with next-event estimation (on in the paper's experiments,
+        # Sec. 5): a second RRSNet / StatNet pair trained online on NEE frames
+        sc_nee = nrrs.Scene(scene, device=local_rank)
+        sc_nee.set_params(params)
+        sc_nee.tune(32)
+        topts_nee = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP,
+                                            max_depth=DEPTH, seed_hi=seed_hi, graph=graph, nee=1)
+        for k in range(args.pretrain + args.warmup + args.steps):
+            topts_nee.frame = 10_000 + k
+            nrrs.nrrs_train_step(sc_nee.handle, topts_nee, stream)
+            nrrs.nrrs_render(sc_nee.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
+                             nrrs.RenderOpts.defaults(frame=20_000 + k, seed_hi=seed_hi,
+                                                      graph=graph, nee=1), out, stream, False)
+        eff["nee"] = efficiency_section(nrrs, sc_nee, torch, dev, stream, seed_hi, nee=1)
+        sc_nee.close()
 
     if dist:
         t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
@@ -528,7 +552,7 @@ def run_ours(args, rank, world, local_rank):
         else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
         "launches": int(stage_n[dom]),
 
-        "note": "k_trace is latency/divergence bound (see DESIGN.md); 40 B/ray algorithmic",
+        "note": "k_trace is latency/divergence bound; 40 B/ray algorithmic",
     }
     # every render stage against HBM: algorithmic bytes over its summed event time, from
     # the warm-up steps (events around every launch)
