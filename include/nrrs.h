@@ -366,8 +366,9 @@ typedef struct nrrs_train_opts {
                                               scene's running mean of its frames   [NULL] */
     float alpha_mix;                       /* temporal EMA of the error map, Eq.
                                               error_temporal                        [0.5] */
-    int32_t error_filter_radius;           /* (2r+1)^2 box filter on the error map in place
-                                              of the paper's denoiser; 0 = off        [2] */
+    int32_t error_filter_radius;           /* (2r+1)^2 spatial filter on the error map in
+                                              place of the paper's denoiser (Sec. 4
+                                              "Tackle Low Spp"); 0 = off              [2] */
     int32_t graph;                         /* record the training frame through a CUDA
                                               graph (nrrs_render_opts.graph)          [0] */
     int32_t batch_size;                    /* training vertices per step, drawn from the
@@ -376,6 +377,14 @@ typedef struct nrrs_train_opts {
                                               (Sec. 4 "Training")                     [0] */
     int32_t nee;                           /* next-event estimation in the training frame
                                               (nrrs_render_opts.nee)                  [0] */
+    float error_filter_power;              /* guidance by the first-hit normals, as the
+                                              paper's denoiser takes the normal buffer:
+                                              neighbours weigh max(0, n_p . n_q)^power
+                                              (nrrs_error_filter); <= 0 = plain box   [8] */
+    int32_t error_filter_until;            /* the spatial filter is off from this step on
+                                              (the paper disables its denoiser for the last
+                                              part of training, where it biases the
+                                              error); 0 = never off                   [0] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {
@@ -524,6 +533,18 @@ typedef struct nrrs_mixdepth_result {
  * Errors: INVALID_ARG (sizes, no reference, too many candidates); OOM; CUDA. */
 NRRS_API nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* opts,
                                           void* stream, nrrs_mixdepth_result* out);
+
+/* The spatial filter of the training error map (Sec. 4 "Tackle Low Spp"; it stands in
+ * for the paper's normal-guided denoiser).  out[p] = sum_q w_pq in[q] / sum_q w_pq over
+ * the (2r+1)^2 window of pixel p clipped at the image border.  d_normals NULL or
+ * power <= 0: w = 1 (box filter).  Otherwise d_normals is device float [W*H][4] (unit
+ * normal xyz, w > 0 when the pixel has one): a pixel with a normal weighs a neighbour
+ * with one by max(0, n_p . n_q)^power and one without by 0; a pixel without a normal
+ * weighs all by 1; the centre always weighs 1.  d_in, d_out: device float [W*H] (not
+ * overlapping).  Errors: INVALID_ARG (NULL arrays, W or H < 1, radius < 0); CUDA. */
+NRRS_API nrrs_status nrrs_error_filter(const float* d_in, const float* d_normals, int32_t width,
+                                       int32_t height, int32_t radius, float power, float* d_out,
+                                       void* stream);
 
 /* relMSE = mean over pixels and RGB of (I - R)^2 / (R^2 + eps) (Sec. 5), in FP64; device
  * images [n_pixels][3], result written to the device double d_out. */

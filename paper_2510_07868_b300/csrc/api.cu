@@ -150,6 +150,8 @@ struct TrainState {
     int rec_D = 0;
     float *m1 = nullptr, *m2 = nullptr, *V = nullptr, *E = nullptr, *rgb = nullptr;
     float *E_cur = nullptr, *E_acc = nullptr;  // error map: this frame, temporal EMA
+    float4* pnrm = nullptr;                      // pixel normals guiding the spatial filter
+    int filter_launches = 0;                     // of the last step's spatial filter
     bool e_first = true;
     int* k = nullptr;
     bool nets = false;
@@ -167,9 +169,10 @@ struct TrainState {
         cudaFree(rec.dep); cudaFree(rec.q); cudaFree(rec.t); cudaFree(rec.feat);
         cudaFree(rec.first); cudaFree(rec.X); cudaFree(rec.S);
         cudaFree(m1); cudaFree(m2); cudaFree(V); cudaFree(E); cudaFree(k); cudaFree(rgb);
-        cudaFree(E_cur); cudaFree(E_acc);
+        cudaFree(E_cur); cudaFree(E_acc); cudaFree(pnrm);
         rec = RecordView{};
         m1 = m2 = V = E = rgb = E_cur = E_acc = nullptr;
+        pnrm = nullptr;
         e_first = true;
         k = nullptr;
         rec_C = npix = 0;
@@ -613,6 +616,7 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     CK(dalloc(&t.E, npix));
     CK(dalloc(&t.E_cur, npix));
     CK(dalloc(&t.E_acc, npix));
+    CK(dalloc(&t.pnrm, npix));
     CK(dalloc(&t.k, npix));
     CK(dalloc(&t.rgb, npix * 3));
     t.rec.C = C;
@@ -1317,7 +1321,7 @@ nrrs_train_opts train_defaults() {
     o.lr_rrsnet = 3e-4f; o.lr_statnet = 5e-3f;
     o.gamma1 = 0.01f; o.gamma2 = 0.05f; o.gamma3 = 0.01f;
     o.eps = 0.01f; o.ema_decay = 0.99f; o.f_rate = 0.85f;
-    o.alpha_mix = 0.5f; o.error_filter_radius = 2;
+    o.alpha_mix = 0.5f; o.error_filter_radius = 2; o.error_filter_power = 8.0f;
     return o;
 }
 
@@ -1566,12 +1570,19 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     CK(cudaMemcpy(t.Fnd, Fnh, sizeof(float) * D, cudaMemcpyHostToDevice));
 
     // 2. pixel errors against the reference (the mean of the earlier frames), smoothed in
-    //    time (alpha_mix) and space (box filter standing in for the denoiser)
+    //    time (alpha_mix) and space (a filter guided by the first-hit normals, standing in
+    //    for the denoiser; off from step error_filter_until on, as the paper turns its
+    //    denoiser off for the last part of training)
     const bool have_ref = o.d_pixel_ref != nullptr || scene->ref_count > 0;
     const float* ref = o.d_pixel_ref ? o.d_pixel_ref : (scene->ref_count > 0 ? scene->ref_mean : t.rgb);
     launch_pixel_error(t.rec, o.spp, npix, ref, o.eps, t.V, t.E_cur, s);
+    const int radius =
+        o.error_filter_until > 0 && t.step >= o.error_filter_until ? 0 : o.error_filter_radius;
+    const bool guided = radius > 0 && o.error_filter_power > 0.0f;
+    if (guided) launch_pixel_normals(t.rec, o.spp, npix, t.pnrm, s);
+    t.filter_launches = (radius > 0 ? 1 : 0) + (guided ? 1 : 0);
     launch_error_smoothing(t.E_cur, t.E_acc, t.E, o.width, o.height, o.alpha_mix, t.e_first ? 1 : 0,
-                           o.error_filter_radius, s);
+                           radius, guided ? t.pnrm : nullptr, o.error_filter_power, s);
     t.e_first = false;
     if (!o.d_pixel_ref) {
         launch_ref_fold(scene->ref_mean, t.rgb, npix * 3, scene->ref_count, s);
@@ -1675,9 +1686,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         out->loss_rrs = warm ? 0.0 : L_rrs;
         out->phase = warm ? 1 : 2;
         out->fallback = fallback;
-        // frame kernels; pixel error, temporal EMA, box filter, reference fold, sample
-        // counts, mean, loss terms; 2 x (train, reduce grad, reduce loss); 2 Adam; EMA
-        out->kernel_launches = (int64_t)rs.kernel_launches + 2 + (o.error_filter_radius > 0) +
+        // frame kernels; pixel error, temporal EMA, pixel normals + spatial filter,
+        // reference fold, sample counts, mean, loss terms; 2 x (train, reduce grad,
+        // reduce loss); 2 Adam; EMA
+        out->kernel_launches = (int64_t)rs.kernel_launches + 2 + t.filter_launches +
                                (o.d_pixel_ref ? 0 : 1) + 3 + 6 + 2 + (fallback ? 0 : 1);
     }
     return NRRS_OK;
@@ -1705,6 +1717,22 @@ nrrs_status nrrs_relmse(const float* d_img, const float* d_ref, int64_t n_pixels
     if (n_pixels < 0 || !d_out || (n_pixels > 0 && (!d_img || !d_ref)))
         return fail(NRRS_ERR_INVALID_ARG, "bad relmse arguments");
     launch_relmse(d_img, d_ref, n_pixels * 3, eps, d_out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_error_filter(const float* d_in, const float* d_normals, int32_t width,
+                              int32_t height, int32_t radius, float power, float* d_out,
+                              void* stream) {
+    if (!d_in || !d_out || width < 1 || height < 1 || radius < 0)
+        return fail(NRRS_ERR_INVALID_ARG, "bad error filter arguments");
+    const float4* nrm = power > 0.0f ? reinterpret_cast<const float4*>(d_normals) : nullptr;
+    if (radius == 0) {
+        CK(cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)width * height,
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        return NRRS_OK;
+    }
+    launch_error_filter(d_in, nrm, width, height, radius, power, d_out, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NRRS_OK;
 }

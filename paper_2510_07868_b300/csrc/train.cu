@@ -76,20 +76,52 @@ __global__ void k_error_temporal(const float* E_cur, float* E_acc, long long n, 
     E_acc[p] = first ? E_cur[p] : (1.0f - alpha) * E_acc[p] + alpha * E_cur[p];
 }
 
-// Spatial smoothing of the error map, a (2r+1)^2 box filter clipped at the image border
-// (stands in for the denoiser the paper applies to the error map, Sec. 4).
-__global__ void k_error_box(const float* in, int W, int H, int r, float* out) {
+// Spatial smoothing of the error map (stands in for the denoiser the paper applies to
+// the error map, Sec. 4 "Tackle Low Spp", which is guided by the normal buffer): the
+// weighted mean over the (2r+1)^2 window clipped at the image border.  Without normals
+// every weight is 1 (a box filter).  With normals, a pixel that has one weighs a
+// neighbour with a normal by max(0, n_p . n_q)^power and one without by 0; a pixel
+// without a normal weighs every neighbour by 1.  The centre always has weight 1.
+__global__ void k_error_filter(const float* in, const float4* nrm, int W, int H, int r,
+                               float power, float* out) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long long)W * H) return;
     const int x = (int)(p % W), y = (int)(p / W);
-    double s = 0.0;
-    int c = 0;
+    const float4 np = nrm ? nrm[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool guided = nrm && np.w > 0.0f;
+    double s = 0.0, c = 0.0;
     for (int yy = max(0, y - r); yy <= min(H - 1, y + r); ++yy)
         for (int xx = max(0, x - r); xx <= min(W - 1, x + r); ++xx) {
-            s += in[(long long)yy * W + xx];
-            ++c;
+            const long long q = (long long)yy * W + xx;
+            double wq = 1.0;
+            if (guided && q != p) {
+                const float4 nq = nrm[q];
+                const float d = np.x * nq.x + np.y * nq.y + np.z * nq.z;
+                wq = nq.w > 0.0f && d > 0.0f ? pow((double)d, (double)power) : 0.0;
+            }
+            s += wq * in[q];
+            c += wq;
         }
     out[p] = (float)(s / c);
+}
+
+__global__ void k_pixel_normals(RecordView r, int spp, long long npix, float4* nrm) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    int k = 0;
+    for (int s = 0; s < spp; ++s) {
+        const long long i = p * spp + s;
+        if (!(r.q[i] > 0.0f)) continue;  // no vertex went on: no features were written
+        const float4 f1 = r.feat[4 * i + 1], f2 = r.feat[4 * i + 2];
+        nx += f1.z;
+        ny += f1.w;
+        nz += f2.x;
+        ++k;
+    }
+    const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+    nrm[p] = k > 0 && len > 0.0f ? make_float4(nx / len, ny / len, nz / len, 1.0f)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Folds the frame into the running mean of the frames so far.
@@ -561,14 +593,26 @@ void launch_relmse(const float* img, const float* ref, long long n3, double eps,
 }
 
 void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
-                            float alpha, int first, int radius, cudaStream_t s) {
+                            float alpha, int first, int radius, const float4* nrm, float power,
+                            cudaStream_t s) {
     const long long n = (long long)W * H;
     const unsigned g = (unsigned)((n + 255) / 256);
     k_error_temporal<<<g, 256, 0, s>>>(E_cur, E_acc, n, alpha, first);
     if (radius > 0)
-        k_error_box<<<g, 256, 0, s>>>(E_acc, W, H, radius, E_out);
+        k_error_filter<<<g, 256, 0, s>>>(E_acc, nrm, W, H, radius, power, E_out);
     else
         cudaMemcpyAsync(E_out, E_acc, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_error_filter(const float* in, const float4* nrm, int W, int H, int radius,
+                         float power, float* out, cudaStream_t s) {
+    const long long n = (long long)W * H;
+    k_error_filter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, nrm, W, H, radius, power, out);
+}
+
+void launch_pixel_normals(const RecordView& r, int spp, long long npix, float4* nrm,
+                          cudaStream_t s) {
+    k_pixel_normals<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(r, spp, npix, nrm);
 }
 
 void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cudaStream_t s) {

@@ -74,9 +74,18 @@ void launch_pixel_error(const RecordView& r, int spp, long long npix, const floa
 void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int grid,
                           cudaStream_t s);
 
-// E_acc = temporal EMA of E_cur; E_out = (2r+1)^2 box filter of E_acc (copy when r = 0)
+// E_acc = temporal EMA of E_cur; E_out = (2r+1)^2 filter of E_acc, guided by the pixel
+// normals when nrm is not NULL (copy when r = 0)
 void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
-                            float alpha, int first, int radius, cudaStream_t s);
+                            float alpha, int first, int radius, const float4* nrm, float power,
+                            cudaStream_t s);
+// The spatial filter alone (nrrs_error_filter).
+void launch_error_filter(const float* in, const float4* nrm, int W, int H, int radius,
+                         float power, float* out, cudaStream_t s);
+// Per pixel: the normalised mean shading normal of its depth-1 vertices that went on
+// (q > 0), w = 1; w = 0 when none did.
+void launch_pixel_normals(const RecordView& r, int spp, long long npix, float4* nrm,
+                          cudaStream_t s);
 void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cudaStream_t s);
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s);

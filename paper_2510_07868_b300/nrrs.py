@@ -37,7 +37,7 @@ EXPORTED = [
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
-    "nrrs_relmse", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
+    "nrrs_relmse", "nrrs_error_filter", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
 ]
@@ -100,14 +100,16 @@ class TrainOpts(C.Structure):
                 ("gamma3", C.c_float), ("eps", C.c_float), ("ema_decay", C.c_float),
                 ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p), ("alpha_mix", C.c_float),
                 ("error_filter_radius", C.c_int32), ("graph", C.c_int32),
-                ("batch_size", C.c_int32), ("nee", C.c_int32)]
+                ("batch_size", C.c_int32), ("nee", C.c_int32),
+                ("error_filter_power", C.c_float), ("error_filter_until", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(width=256, height=256, spp=2, max_depth=16, seed_lo=1, seed_hi=0, frame=0,
                 warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
                 gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None,
-                alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0, nee=0)
+                alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0, nee=0,
+                error_filter_power=8.0, error_filter_until=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -190,6 +192,7 @@ def _load():
         "nrrs_mixdepth_candidates": ([I32, I32], I64),
         "nrrs_mixdepth_search": ([P, P, P, P], I32),
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
+        "nrrs_error_filter": ([P, P, I32, I32, I32, C.c_float, P, P], I32),
         "nrrs_rrsnet_forward": ([P, P, I64, P, P], I32),
         "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
         "nrrs_tune_rrsnet": ([P, I32, P, P], I32),
@@ -475,6 +478,11 @@ def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1,
     r = MixDepthResult()
     _check(_lib.nrrs_mixdepth_search(scene, C.byref(o), _stream(stream), C.byref(r)))
     return {name: getattr(r, name) for name, _ in r._fields_}
+
+
+def nrrs_error_filter(d_in, d_normals, width, height, radius, power, d_out, stream=None):
+    _check(_lib.nrrs_error_filter(_ptr(d_in), _ptr(d_normals), width, height, radius, power,
+                                  _ptr(d_out), _stream(stream)))
 
 
 def nrrs_relmse(d_img, d_ref, n_pixels, eps, d_out, stream=None):
