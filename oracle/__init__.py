@@ -60,7 +60,7 @@ class RenderArgs(C.Structure):
                 ("eps_rel", C.c_double), ("boxcox_lambda", C.c_double), ("gate", C.c_uint64),
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
                 ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p),
-                ("stat_params", C.c_void_p), ("nee", C.c_int32)]
+                ("stat_params", C.c_void_p), ("nee", C.c_int32), ("rrsnet_inputs", C.c_int32)]
 
 
 class RenderStats(C.Structure):
@@ -255,9 +255,10 @@ def bernstein_exponent(f_rate):
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
            params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None,
-           stat_params=None, nee=0):
+           stat_params=None, nee=0, rrsnet_inputs=0):
     """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
-    nee=1 adds next-event estimation with MIS (power heuristic) at every vertex.
+    nee=1 adds next-event estimation with MIS (power heuristic) at every vertex;
+    rrsnet_inputs=1 feeds RRSNet the NRRS inputs built from StatNet (stat_params).
     With record=True the stats dict also holds "rec": per depth an array [live, 13] of
     (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
     h = _SceneHolder(scene)
@@ -270,7 +271,8 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     SP = np.ascontiguousarray(stat_params, dtype=np.float64) if stat_params is not None else None
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
-                      0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP), int(nee))
+                      0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP), int(nee),
+                      int(rrsnet_inputs))
     out = np.zeros((height, width, 3))
     st = RenderStats()
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None

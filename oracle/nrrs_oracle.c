@@ -19,6 +19,10 @@
  *   or_mlp_backward    the chain rule through the same network
  *   or_render          also ADRRS (NN) factors at NET_MIX depths with gate 3 (Sec. 4
  *                      "Mix-Depth"): lum(t) E[L_o] / I_px from StatNet's predicted mean
+ *   or_render (rrsnet_inputs = 1)  the NRRS network inputs of Sec. 4 "Input Encoding":
+ *                      Box-Cox (lambda 0.5) of StatNet's E[L_o] and E[L_o^2] (per channel,
+ *                      clamped at 0), of the throughput t and of the pixel estimate's
+ *                      mean, and the roughness remapped by 1 - exp(-alpha)
  *   or_normalize       Eq. q_norm, Eq. F_norm, Eq. q_norm_rate, Eq. f_rate_prime and
  *                      the downscale-only compromise of Sec. 4 ("Compromise")
  *   or_split           Eq. rrs_factor: N_q = floor(q) + Bernoulli(q - floor(q))
@@ -505,6 +509,8 @@ typedef struct {
                                subset (test hook for sampled pixels of a full frame) */
     const double* stat_params; /* StatNet weights (ADRRS (NN) depths of NET_MIX) */
     int32_t nee;            /* next-event estimation with MIS (1) or BSDF sampling only (0) */
+    int32_t rrsnet_inputs;  /* RRSNet inputs: 0 = the 16 vertex features, 1 = NRRS inputs
+                               (needs stat_params) */
 } or_render_args;
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
@@ -647,6 +653,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     if (a->mode == OR_MODE_NET_MIX && !a->stat_params)
         for (int32_t d = 1; d <= D; ++d)
             if (((a->gate >> (2 * (d - 1))) & 3u) == OR_GATE_ADRRS) return OR_ERR_ARG;
+    if (a->rrsnet_inputs && !a->stat_params) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
     or_emitters E;
     memset(&E, 0, sizeof(E));
@@ -810,6 +817,27 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 for (int c = 0; c < 3; ++c) x[9 + c] = m->albedo[c];
                 x[12] = (double)depth / (double)D;
                 for (int c = 0; c < 3; ++c) x[13 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
+                if (a->rrsnet_inputs) {
+                    /* NRRS inputs (Sec. 4 "Input Encoding"): StatNet's statistics at the
+                     * vertex (its throughput inputs zeroed, as trained), the throughput,
+                     * the pixel estimate's mean (0 before any) and the remapped roughness
+                     * (a Lambertian surface counts as roughness 1); unused inputs 0 */
+                    double xs[OR_NF], st6[6];
+                    memcpy(xs, x, sizeof(xs));
+                    xs[13] = xs[14] = xs[15] = 0.0;
+                    or_mlpn_forward(a->stat_params, 6, xs, st6, NULL, NULL);
+                    double I = 0.0;
+                    if (a->pixel_ref) {
+                        const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
+                        I = (r[0] + r[1] + r[2]) / 3.0;
+                    }
+                    const double alpha = m->type == 0 ? 1.0 : (double)m->roughness;
+                    for (int c = 0; c < 6; ++c) x[c] = or_boxcox(fmax(st6[c], 0.0), a->boxcox_lambda);
+                    for (int c = 0; c < 3; ++c) x[6 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
+                    x[9] = or_boxcox(fmax(I, 0.0), a->boxcox_lambda);
+                    x[10] = 1.0 - exp(-alpha);
+                    for (int c = 11; c < OR_NF; ++c) x[c] = 0.0;
+                }
                 q = or_mlp_forward(a->params, x, NULL, NULL, NULL);
                 if (!(isfinite(q) && q >= 0.0)) {  /* a failing network: the heuristic */
                     q = heur;
