@@ -252,6 +252,19 @@ NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
  * width not 2 or 4); UNSUPPORTED (4 without a four-wide tree). */
 NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
 
+/* Chooses what RRSNet reads at the network depths of later renders and training steps
+ * (the weights are the caller's to match):
+ *   0 (default) the 16 vertex features: position in the scene box, -w_o, the shading
+ *     normal, albedo, d / D and Box-Cox(t) per channel;
+ *   1 the NRRS inputs of Sec. 4 "Input Encoding": StatNet runs first at every network
+ *     vertex (its throughput inputs zeroed, as trained) and RRSNet reads
+ *     Box-Cox(max(E[L_o], 0)) and Box-Cox(max(E[L_o^2], 0)) per channel, Box-Cox(t) per
+ *     channel, Box-Cox(mean of the pixel estimate; 0 before any), 1 - exp(-roughness)
+ *     (Lambertian surfaces count as roughness 1) and five zeros, Box-Cox with the render's
+ *     boxcox_lambda.  StatNet's weights are the scene's (nrrs_set_params / training).
+ * Errors: INVALID_ARG (NULL scene, mode not 0 or 1). */
+NRRS_API nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode);
+
 /* Free every device buffer of the scene (synchronizes the device). NULL is a no-op. */
 NRRS_API nrrs_status nrrs_destroy_scene(nrrs_scene* scene);
 

@@ -75,6 +75,7 @@ struct Workspace {
     FrameConsts* fc = nullptr;
     unsigned long long* flags = nullptr;  // look-back flags of the fused split
     long long n_flags = 0;
+    float4* feat_net = nullptr;  // NRRS inputs of RRSNet (scenes with rrsnet_inputs = 1)
     // next-event estimation: sampling pdfs of both queues and the per-slot shadow rays
     bool has_nee = false;
     float* qpdf[2] = {nullptr, nullptr};
@@ -93,6 +94,8 @@ struct Workspace {
         }
         cudaFree(sh_o); cudaFree(sh_d); cudaFree(sh_c);
         sh_o = sh_d = sh_c = nullptr;
+        cudaFree(feat_net);
+        feat_net = nullptr;
         has_nee = false;
         cudaFree(hit); cudaFree(q); cudaFree(dep); cudaFree(feat); cudaFree(part); cudaFree(bcnt);
         cudaFree(boff); cudaFree(acc_s); cudaFree(acc_c); cudaFree(st); cudaFree(fc);
@@ -167,6 +170,7 @@ struct TrainState {
 
     void release_record() {
         cudaFree(rec.dep); cudaFree(rec.q); cudaFree(rec.t); cudaFree(rec.feat);
+        cudaFree(rec.feat_net);
         cudaFree(rec.first); cudaFree(rec.X); cudaFree(rec.S);
         cudaFree(m1); cudaFree(m2); cudaFree(V); cudaFree(E); cudaFree(k); cudaFree(rgb);
         cudaFree(E_cur); cudaFree(E_acc); cudaFree(pnrm);
@@ -215,6 +219,8 @@ struct nrrs_scene {
     long long last_P = 0;
     // the last training step fell back: the next render uses the heuristic at NET depths
     bool heur_next = false;
+    // RRSNet inputs: 0 = the 16 vertex features, 1 = the NRRS inputs built from StatNet
+    int rrsnet_inputs = 0;
     // running mean of earlier frames (HEUR reference), [npix * 3]
     float* ref_mean = nullptr;
     int ref_count = 0;
@@ -541,6 +547,18 @@ nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
     return NRRS_OK;
 }
 
+nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode) {
+    if (!scene || (mode != 0 && mode != 1)) return fail(NRRS_ERR_INVALID_ARG, "bad RRSNet input mode");
+    if (mode != scene->rrsnet_inputs) {
+        DeviceGuard g(scene->device);
+        // recorded NRRS inputs of an earlier mode must not feed training
+        cudaFree(scene->train.rec.feat_net);
+        scene->train.rec.feat_net = nullptr;
+    }
+    scene->rrsnet_inputs = mode;
+    return NRRS_OK;
+}
+
 nrrs_status nrrs_scene_info(const nrrs_scene* scene, int64_t* n_nodes, int64_t* n_tri) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
     if (n_nodes) *n_nodes = scene->n_nodes;
@@ -600,7 +618,11 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
 // Record buffers of a frame (every depth's slots) for the reverse pass and training.
 nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     TrainState& t = sc->train;
-    if (t.rec_C >= C && t.rec_D >= D && t.npix >= npix) return NRRS_OK;
+    if (t.rec_C >= C && t.rec_D >= D && t.npix >= npix) {
+        if (sc->rrsnet_inputs && !t.rec.feat_net)
+            CK(dalloc(&t.rec.feat_net, (size_t)t.rec_C * t.rec_D * 4));
+        return NRRS_OK;
+    }
     t.release_record();
     const size_t n = (size_t)C * D;
     CK(dalloc(&t.rec.dep, n));
@@ -619,6 +641,7 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     CK(dalloc(&t.pnrm, npix));
     CK(dalloc(&t.k, npix));
     CK(dalloc(&t.rgb, npix * 3));
+    if (sc->rrsnet_inputs) CK(dalloc(&t.rec.feat_net, n * 4));
     t.rec.C = C;
     t.rec_C = C;
     t.rec_D = D;
@@ -709,7 +732,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         if (kind_of(d) == kFactorNet) uses_net = true;
         if (kind_of(d) == kFactorAdrrs) uses_adrrs = true;
     }
-    if (uses_adrrs) {  // StatNet's weights (trained by nrrs_train_step)
+    // RRSNet fed the NRRS inputs needs StatNet at its depths
+    const bool nrrs_inputs = scene->rrsnet_inputs != 0 && uses_net;
+    if (uses_adrrs || nrrs_inputs) {  // StatNet's weights (trained by nrrs_train_step)
         nrrs_status trc = ensure_train_nets(scene, s);
         if (trc != NRRS_OK) return trc;
         uses_net = true;
@@ -718,6 +743,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     nrrs_status rc = ensure_workspace(scene, C, npix, uses_net, nee);
     if (rc != NRRS_OK) return rc;
     Workspace& ws = scene->ws;
+    if (nrrs_inputs && !ws.feat_net) CK(dalloc(&ws.feat_net, (size_t)ws.cap * 4));
     if (batch && scene->jw_grid < ws.grid_red) {  // per-block, per-job partials
         const int n = scene->n_jobs;
         cudaFree(scene->jw.part);
@@ -817,6 +843,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         }
         RenderParams r = rp;
         int cur = 0;
+        float4* feat_net = ws.feat_net;
         for (int d = 1; d <= max_depth; ++d) {
             const int kind = kind_of(d);
             if (rec) {  // this depth's factors, deposits and features go straight to the record
@@ -824,6 +851,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 w.q = rec->q + off;
                 w.dep = rec->dep + off;
                 w.feat = rec->feat + off * 4;
+                if (nrrs_inputs) feat_net = rec->feat_net + off * 4;
                 r.rec_first = rec->first + off;
                 r.rec_X = rec->X + off;
                 CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C,
@@ -836,9 +864,14 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 TIMED(NRRS_STAGE_SHADOW,
                       launch_shadow(scene->view, w, d, scene->grid_trace, r.jobs, s));
             if (kind == kFactorNet) {
+                if (nrrs_inputs)  // StatNet, then the NRRS inputs of RRSNet
+                    TIMED(NRRS_STAGE_RRSNET,
+                          launch_nrrs_inputs(scene->train.stat, scene->view, w, q[cur], r, d,
+                                             scene->n_sm * 4, feat_net, s));
                 TIMED(NRRS_STAGE_RRSNET,
-                      launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params, w.feat,
-                                    &w.st->live[d - 1], 0, w.q, 1, w.st, &w.st->status, s));
+                      launch_rrsnet(o.precision, net_shape[d - 1], scene->n_sm, r.params,
+                                    nrrs_inputs ? feat_net : w.feat, &w.st->live[d - 1], 0, w.q,
+                                    1, w.st, &w.st->status, s));
                 if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             } else if (kind == kFactorAdrrs) {
                 TIMED(NRRS_STAGE_RRSNET,
@@ -882,7 +915,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         const uint64_t sv[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
                                (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
                                o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile,
-                               (uint64_t)heur_frame, (uint64_t)nee};
+                               (uint64_t)heur_frame, (uint64_t)nee, (uint64_t)nrrs_inputs};
         for (uint64_t v : sv) shape = mix_key(shape, v);
         uint64_t args = shape;
         auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };
@@ -900,7 +933,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)scene->view.nodes4,
                                (uint64_t)(uintptr_t)scene->train.stat,
                                (uint64_t)o.cap_factor, (uint64_t)(uintptr_t)ws.sh_o,
-                               (uint64_t)(uintptr_t)ws.qpdf[0]};
+                               (uint64_t)(uintptr_t)ws.qpdf[0], (uint64_t)(uintptr_t)ws.feat_net,
+                               (uint64_t)(uintptr_t)(rec ? rec->feat_net : nullptr)};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +

@@ -228,7 +228,78 @@ k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, co
     }
 }
 
+// The NRRS inputs of RRSNet (Sec. 4 "Input Encoding") of each row the render marked for
+// the network (q < 0): StatNet on the vertex features (throughput inputs zeroed, as
+// trained) gives E[L_o] and E[L_o^2] per channel; the row becomes Box-Cox(max(E[L_o], 0)),
+// Box-Cox(max(E[L_o^2], 0)), Box-Cox(t), Box-Cox(I_px mean, 0 before any estimate),
+// 1 - exp(-roughness) (Lambertian: roughness 1), then five zeros.
+__device__ __forceinline__ float boxcox_in(float x, float lambda) {
+    if (lambda == 0.5f) return 2.0f * (sqrtf(x) - 1.0f);
+    if (lambda == 0.0f) return logf(x);
+    return (powf(x, lambda) - 1.0f) / lambda;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_nrrs_inputs(const float* __restrict__ stat, SceneView sc, const float4* __restrict__ feat,
+              const float4* t, const float4* dep, const float2* hit, const long long* n_ptr,
+              const float* q, float4* out, RenderParams rp) {
+    constexpr int kStatParams = kNH * kNF + 2 * kNH * kNH + 6 * kNH;
+    __shared__ __align__(16) float sW[kStatParams];
+    const long long n = *n_ptr;
+    if ((long long)blockIdx.x * blockDim.x >= n) return;
+    for (int i = threadIdx.x; i < kStatParams / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(stat) + i);
+    __syncthreads();
+    const float lam = rp.boxcox_lambda;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!(q[i] < 0.0f)) continue;
+        float x[1][kNF];
+        load_row(feat, i, x[0]);
+        x[0][13] = x[0][14] = x[0][15] = 0.0f;
+        float h[1][kNH], g[1][kNH];
+        dense<1, kNF>(sW, x, h);
+        dense<1, kNH>(sW + kNH * kNF, h, g);
+        dense<1, kNH>(sW + kNH * kNF + kNH * kNH, g, h);
+        const float* W4 = sW + kNH * kNF + 2 * kNH * kNH;
+        float f[kNF];
+#pragma unroll
+        for (int o = 0; o < 6; ++o) {
+            float z = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kNH; ++k) z = fmaf(W4[o * kNH + k], h[0][k], z);
+            f[o] = boxcox_in(fmaxf(z, 0.0f), lam);
+        }
+        const float4 t4 = t[i];
+        f[6] = boxcox_in(t4.x, lam);
+        f[7] = boxcox_in(t4.y, lam);
+        f[8] = boxcox_in(t4.z, lam);
+        float I = 0.0f;
+        if (rp.ref) {
+            const float* rr = rp.ref + 3 * (size_t)__float_as_uint(dep[i].w);
+            I = (rr[0] + rr[1] + rr[2]) / 3.0f;
+        }
+        f[9] = boxcox_in(fmaxf(I, 0.0f), lam);
+        const int slot = __float_as_int(hit[i].y);
+        const nrrs_material& m = sc.mats[__float_as_uint(__ldg(&sc.tris[3 * slot + 1].w))];
+        f[10] = 1.0f - expf(-(m.type == 0 ? 1.0f : m.roughness));
+#pragma unroll
+        for (int k = 11; k < kNF; ++k) f[k] = 0.0f;
+        float4* o4 = out + 4 * i;
+        o4[0] = make_float4(f[0], f[1], f[2], f[3]);
+        o4[1] = make_float4(f[4], f[5], f[6], f[7]);
+        o4[2] = make_float4(f[8], f[9], f[10], f[11]);
+        o4[3] = make_float4(f[12], f[13], f[14], f[15]);
+    }
+}
+
 }  // namespace
+
+void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
+                        const RenderParams& rp, int depth, int grid, float4* out, cudaStream_t s) {
+    k_nrrs_inputs<<<grid, kThreads, 0, s>>>(stat, sc, w.feat, cur.t, w.dep, w.hit,
+                                            &w.st->live[depth - 1], w.q, out, rp);
+}
 
 void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
                   int depth, int grid, cudaStream_t s) {

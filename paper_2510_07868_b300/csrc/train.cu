@@ -328,7 +328,10 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             const size_t g = (size_t)d * r.C + i;
             active = ((b.net_mask >> d) & 1u) && r.q[g] > 0.0f;
             if (active) {
-                const float4* f = r.feat + 4 * g;
+                // StatNet learns from the vertex features; RRSNet reads its own inputs
+                // (the NRRS encoding, when the scene uses it)
+                const float4* f =
+                    (MODE != kTrainStatNet && r.feat_net ? r.feat_net : r.feat) + 4 * g;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float4 v = f[k];

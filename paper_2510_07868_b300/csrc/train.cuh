@@ -19,6 +19,7 @@ struct RecordView {
     uint32_t* first;  // first child slot in the next depth
     uint32_t* X;      // children requested
     float4* S;        // suffix sum rgb, pixel bits (reverse pass)
+    float4* feat_net; // NRRS inputs of RRSNet (4 float4 per slot) or NULL: RRSNet reads feat
     long long C;
 };
 

@@ -194,6 +194,10 @@ void launch_frame_consts(FrameConsts* fc, uint32_t key0, uint32_t key1, int ref_
 void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* feat,
                         const long long* n_ptr, long long n_host, float* q, int sentinel,
                         DevStats* st, cudaStream_t s);
+// NRRS inputs (Sec. 4 "Input Encoding") of the rows the shade kernel marked for the
+// network, from StatNet and the vertex state, written to `out` ([C][4] float4).
+void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
+                        const RenderParams& rp, int depth, int grid, float4* out, cudaStream_t s);
 // ADRRS (NN) factors of the vertices the shade kernel marked (rrsnet_simt.cu).
 void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
                   int depth, int grid, cudaStream_t s);

@@ -37,7 +37,7 @@ EXPORTED = [
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
-    "nrrs_relmse", "nrrs_error_filter", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
+    "nrrs_relmse", "nrrs_error_filter", "nrrs_set_rrsnet_inputs", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
 ]
@@ -193,6 +193,7 @@ def _load():
         "nrrs_mixdepth_search": ([P, P, P, P], I32),
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
         "nrrs_error_filter": ([P, P, I32, I32, I32, C.c_float, P, P], I32),
+        "nrrs_set_rrsnet_inputs": ([P, I32], I32),
         "nrrs_rrsnet_forward": ([P, P, I64, P, P], I32),
         "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
         "nrrs_tune_rrsnet": ([P, I32, P, P], I32),
@@ -480,6 +481,10 @@ def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1,
     return {name: getattr(r, name) for name, _ in r._fields_}
 
 
+def nrrs_set_rrsnet_inputs(scene, mode):
+    _check(_lib.nrrs_set_rrsnet_inputs(scene, mode))
+
+
 def nrrs_error_filter(d_in, d_normals, width, height, radius, power, d_out, stream=None):
     _check(_lib.nrrs_error_filter(_ptr(d_in), _ptr(d_normals), width, height, radius, power,
                                   _ptr(d_out), _stream(stream)))
@@ -578,6 +583,9 @@ class Scene:
 
     def set_traversal(self, width):
         nrrs_set_traversal(self.handle, width)
+
+    def set_rrsnet_inputs(self, mode):
+        nrrs_set_rrsnet_inputs(self.handle, mode)
 
     def train_step(self, stream=None, **opts):
         return nrrs_train_step(self.handle, TrainOpts.defaults(**opts), stream)
