@@ -502,21 +502,29 @@ def run_ours(args, rank, world, local_rank):
     eff = None
     if rank == 0 and not args.no_efficiency:
         eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi)
+        def trained_scene(nee, rrsnet_inputs):
+            """A second RRSNet / StatNet pair trained online like the first."""
+            sc2 = nrrs.Scene(scene, device=local_rank)
+            sc2.set_params(params)
+            sc2.set_rrsnet_inputs(rrsnet_inputs)
+            sc2.tune(32)
+            t2 = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP,
+                                         max_depth=DEPTH, seed_hi=seed_hi, graph=graph, nee=nee)
+            for k in range(args.pretrain + args.warmup + args.steps):
+                t2.frame = 10_000 + k
+                nrrs.nrrs_train_step(sc2.handle, t2, stream)
+                nrrs.nrrs_render(sc2.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
+                                 nrrs.RenderOpts.defaults(frame=20_000 + k, seed_hi=seed_hi,
+                                                          graph=graph, nee=nee),
+                                 out, stream, False)
+            return sc2
+
         # the same comparison with next-event estimation (on in the paper's experiments,
-        # Sec. 5): a second RRSNet / StatNet pair trained online on NEE frames
-        sc_nee = nrrs.Scene(scene, device=local_rank)
-        sc_nee.set_params(params)
-        sc_nee.tune(32)
-        topts_nee = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP,
-                                            max_depth=DEPTH, seed_hi=seed_hi, graph=graph, nee=1)
-        for k in range(args.pretrain + args.warmup + args.steps):
-            topts_nee.frame = 10_000 + k
-            nrrs.nrrs_train_step(sc_nee.handle, topts_nee, stream)
-            nrrs.nrrs_render(sc_nee.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
-                             nrrs.RenderOpts.defaults(frame=20_000 + k, seed_hi=seed_hi,
-                                                      graph=graph, nee=1), out, stream, False)
-        eff["nee"] = efficiency_section(nrrs, sc_nee, torch, dev, stream, seed_hi, nee=1)
-        sc_nee.close()
+        # Sec. 5), and with RRSNet on the paper's NRRS inputs (Sec. 4 "Input Encoding")
+        for key, nee, rin in (("nee", 1, 0), ("nrrs_inputs", 0, 1)):
+            sc2 = trained_scene(nee, rin)
+            eff[key] = efficiency_section(nrrs, sc2, torch, dev, stream, seed_hi, nee=nee)
+            sc2.close()
 
     if dist:
         t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)

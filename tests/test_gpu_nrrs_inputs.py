@@ -57,7 +57,8 @@ def test_nrrs_inputs_parity(nrrs, scene_name):
     oimg, ost, otr = oracle.render(s, W, H, 4, 6, oracle.MODE_NET, params=P.astype(np.float64),
                                    stat_params=SP.astype(np.float64), rrsnet_inputs=1,
                                    pixel_ref=ref.astype(np.float32).astype(np.float64), trace=True)
-    np.testing.assert_allclose(gst["sum_q"][:2], ost["sum_q"][:2], rtol=1e-5)
+    # depth 1: the same vertices on both sides, so the sums of the factors agree closely
+    np.testing.assert_allclose(gst["sum_q"][0], ost["sum_q"][0], rtol=1e-6)
     if scene_name == "box":
         compare(gimg, gtr, oimg, otr, W, H, min_match=0.98)
     else:  # GGX directions: the bar of the GGX render test (99 % of matched pixels)
