@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nrrs_oracle.c")
 _SRC_TRAIN = os.path.join(_HERE, "nrrs_oracle_train.c")
+_SRC_ENC = os.path.join(_HERE, "nrrs_oracle_encoding.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODE_NONE, MODE_PLAIN_RR, MODE_HEUR_NORM, MODE_NET, MODE_NET_MIX = range(5)
@@ -29,10 +30,10 @@ NO_HIT = 0xFFFFFFFF
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, OpenMP)."""
     stale = not os.path.exists(_LIB) or any(
-        os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC_TRAIN))
+        os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC_TRAIN, _SRC_ENC))
     if force or stale:
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
-               "-ffp-contract=off", _SRC, _SRC_TRAIN, "-o", _LIB, "-lm"]
+               "-ffp-contract=off", _SRC, _SRC_TRAIN, _SRC_ENC, "-o", _LIB, "-lm"]
         subprocess.run(cmd, check=True)
     return _LIB
 
@@ -60,7 +61,8 @@ class RenderArgs(C.Structure):
                 ("eps_rel", C.c_double), ("boxcox_lambda", C.c_double), ("gate", C.c_uint64),
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
                 ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p),
-                ("stat_params", C.c_void_p), ("nee", C.c_int32), ("rrsnet_inputs", C.c_int32)]
+                ("stat_params", C.c_void_p), ("nee", C.c_int32), ("rrsnet_inputs", C.c_int32),
+                ("stat_encoding", C.c_int32), ("stat_grid", C.c_void_p)]
 
 
 class RenderStats(C.Structure):
@@ -122,6 +124,18 @@ def lib():
         _lib.or_relmse.argtypes = [P, P, C.c_int64, C.c_double]
 
         _lib.or_relmse.restype = C.c_double
+        _lib.or_mlpk_param_count.argtypes = [C.c_int, C.c_int]
+        _lib.or_mlpk_param_count.restype = C.c_int64
+        _lib.or_mlpk_forward.argtypes = [P, C.c_int, C.c_int, P, P, P, P]
+        _lib.or_mlpk_backward.argtypes = [P, C.c_int, C.c_int, P, P, P, P]
+        _lib.or_grid_param_count.argtypes = []
+        _lib.or_grid_param_count.restype = C.c_int64
+        _lib.or_grid_index.argtypes = [C.c_int, C.c_uint32, C.c_uint32, C.c_uint32]
+        _lib.or_grid_index.restype = C.c_uint32
+        _lib.or_grid_encode.argtypes = [P, P, P]
+        _lib.or_grid_backward.argtypes = [P, P, P]
+        _lib.or_one_blob.argtypes = [C.c_double, C.c_int, P]
+        _lib.or_statnet_grid_inputs.argtypes = [P, P, P, C.c_double, P]
     return _lib
 
 
@@ -255,10 +269,12 @@ def bernstein_exponent(f_rate):
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
            params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None,
-           stat_params=None, nee=0, rrsnet_inputs=0):
+           stat_params=None, nee=0, rrsnet_inputs=0, stat_grid=None):
     """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
     nee=1 adds next-event estimation with MIS (power heuristic) at every vertex;
-    rrsnet_inputs=1 feeds RRSNet the NRRS inputs built from StatNet (stat_params).
+    rrsnet_inputs=1 feeds RRSNet the NRRS inputs built from StatNet (stat_params);
+    with stat_grid (the hash-grid table) StatNet reads the encodings of Sec. 4 (32 inputs,
+    stat_params then has 32 inputs) instead of the vertex features.
     With record=True the stats dict also holds "rec": per depth an array [live, 13] of
     (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
     h = _SceneHolder(scene)
@@ -269,10 +285,11 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     rec = np.zeros((max_depth, capv, 13)) if record else None
     fF = np.ascontiguousarray(forced_F, dtype=np.float32) if forced_F is not None else None
     SP = np.ascontiguousarray(stat_params, dtype=np.float64) if stat_params is not None else None
+    SG = np.ascontiguousarray(stat_grid, dtype=np.float64) if stat_grid is not None else None
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
                       0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP), int(nee),
-                      int(rrsnet_inputs))
+                      int(rrsnet_inputs), 0 if SG is None else 1, _p(SG))
     out = np.zeros((height, width, 3))
     st = RenderStats()
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None
@@ -306,6 +323,75 @@ def mlpn_forward(params, n_out, x):
     out = np.zeros(n_out)
     lib().or_mlpn_forward(_p(P), n_out, _p(x), _p(out), None, None)
     return out
+
+
+def mlpk_param_count(n_in, n_out):
+    return int(lib().or_mlpk_param_count(n_in, n_out))
+
+
+def mlpk_forward(params, n_in, n_out, x):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(n_out)
+    lib().or_mlpk_forward(_p(P), n_in, n_out, _p(x), _p(out), None, None)
+    return out
+
+
+def mlpk_backward(params, n_in, n_out, x, dout):
+    """(gradient of sum dout . out with respect to the weights, and to the inputs)."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    d = np.ascontiguousarray(dout, dtype=np.float64)
+    G = np.zeros_like(P)
+    dx = np.zeros(n_in)
+    lib().or_mlpk_backward(_p(P), n_in, n_out, _p(x), _p(d), _p(G), _p(dx))
+    return G, dx
+
+
+GRID_LEVELS, GRID_T = 8, 1 << 18
+
+
+def grid_param_count():
+    return int(lib().or_grid_param_count())
+
+
+def grid_index(level, x, y, z):
+    return int(lib().or_grid_index(level, x, y, z))
+
+
+def grid_encode(table, p):
+    """Hash-grid features [n, 16] of points p [n, 3] in [0, 1]^3."""
+    T = np.ascontiguousarray(table, dtype=np.float64)
+    p = np.ascontiguousarray(np.atleast_2d(p), dtype=np.float64)
+    out = np.zeros((p.shape[0], 16))
+    for i in range(p.shape[0]):
+        lib().or_grid_encode(_p(T), _p(p[i]), _p(out[i]))
+    return out
+
+
+def grid_backward(p, dout):
+    """Table gradient of sum_i dout[i] . encode(p[i])."""
+    p = np.ascontiguousarray(np.atleast_2d(p), dtype=np.float64)
+    d = np.ascontiguousarray(np.atleast_2d(dout), dtype=np.float64)
+    G = np.zeros(grid_param_count())
+    for i in range(p.shape[0]):
+        lib().or_grid_backward(_p(G), _p(p[i]), _p(d[i]))
+    return G
+
+
+def one_blob(v, k):
+    out = np.zeros(k)
+    lib().or_one_blob(float(v), int(k), _p(out))
+    return out
+
+
+def statnet_grid_inputs(table, p, wo, alpha):
+    T = np.ascontiguousarray(table, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    x = np.zeros(32)
+    lib().or_statnet_grid_inputs(_p(T), _p(p), _p(wo), float(alpha), _p(x))
+    return x
 
 
 def mlpn_backward(params, n_out, x, dout):

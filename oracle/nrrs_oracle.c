@@ -482,9 +482,13 @@ double or_bernstein_exponent(double f_rate) {
     return g * g / (2.0 * f_rate + (2.0 / 3.0) * g);
 }
 
-/* StatNet forward (nrrs_oracle_train.c) */
+/* StatNet forward (nrrs_oracle_train.c) and its encodings (nrrs_oracle_encoding.c) */
 void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, double* pre,
                      double* hid);
+void or_mlpk_forward(const double* P, int n_in, int n_out, const double* x, double* out,
+                     double* pre, double* hid);
+void or_statnet_grid_inputs(const double* table, const double p[3], const double wo[3],
+                            double alpha, double x[32]);
 
 /* ------------------------------------------------------------------ render */
 
@@ -511,7 +515,26 @@ typedef struct {
     int32_t nee;            /* next-event estimation with MIS (1) or BSDF sampling only (0) */
     int32_t rrsnet_inputs;  /* RRSNet inputs: 0 = the 16 vertex features, 1 = NRRS inputs
                                (needs stat_params) */
+    int32_t stat_encoding;  /* StatNet inputs: 0 = the 13 vertex features (throughput
+                               inputs zeroed), 1 = hash grid + one-blob (needs stat_grid) */
+    const double* stat_grid;/* StatNet's hash-grid table [8][2^18][2] */
 } or_render_args;
+
+/* StatNet's six outputs at a vertex whose 16 features are x (position in the scene box,
+ * -w_o, ...) and whose roughness is alpha. */
+static void or_statnet_at(const or_render_args* a, const double x[16], double alpha,
+                          double out[6]) {
+    if (a->stat_encoding) {
+        double x32[32];
+        or_statnet_grid_inputs(a->stat_grid, x, x + 3, alpha, x32);
+        or_mlpk_forward(a->stat_params, 32, 6, x32, out, NULL, NULL);
+    } else {
+        double xs[16];
+        memcpy(xs, x, sizeof(xs));
+        xs[13] = xs[14] = xs[15] = 0.0;
+        or_mlpn_forward(a->stat_params, 6, xs, out, NULL, NULL);
+    }
+}
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
  * q_orig, q_used, X, first child slot. */
@@ -654,6 +677,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
         for (int32_t d = 1; d <= D; ++d)
             if (((a->gate >> (2 * (d - 1))) & 3u) == OR_GATE_ADRRS) return OR_ERR_ARG;
     if (a->rrsnet_inputs && !a->stat_params) return OR_ERR_ARG;
+    if (a->stat_encoding && !a->stat_grid) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
     or_emitters E;
     memset(&E, 0, sizeof(E));
@@ -791,7 +815,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                     for (int c = 0; c < 3; ++c) x[9 + c] = m->albedo[c];
                     x[12] = (double)depth / (double)D;
                     x[13] = x[14] = x[15] = 0.0;
-                    or_mlpn_forward(a->stat_params, 6, x, out, NULL, NULL);
+                    or_statnet_at(a, x, m->type == 0 ? 1.0 : (double)m->roughness, out);
                     const double el = (out[0] + out[1] + out[2]) / 3.0;
                     const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
                     const double den = fmax((r[0] + r[1] + r[2]) / 3.0, eps_I);
@@ -822,20 +846,18 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                      * vertex (its throughput inputs zeroed, as trained), the throughput,
                      * the pixel estimate's mean (0 before any) and the remapped roughness
                      * (a Lambertian surface counts as roughness 1); unused inputs 0 */
-                    double xs[OR_NF], st6[6];
-                    memcpy(xs, x, sizeof(xs));
-                    xs[13] = xs[14] = xs[15] = 0.0;
-                    or_mlpn_forward(a->stat_params, 6, xs, st6, NULL, NULL);
+                    double st6[6];
+                    const double rough = m->type == 0 ? 1.0 : (double)m->roughness;
+                    or_statnet_at(a, x, rough, st6);
                     double I = 0.0;
                     if (a->pixel_ref) {
                         const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
                         I = (r[0] + r[1] + r[2]) / 3.0;
                     }
-                    const double alpha = m->type == 0 ? 1.0 : (double)m->roughness;
                     for (int c = 0; c < 6; ++c) x[c] = or_boxcox(fmax(st6[c], 0.0), a->boxcox_lambda);
                     for (int c = 0; c < 3; ++c) x[6 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
                     x[9] = or_boxcox(fmax(I, 0.0), a->boxcox_lambda);
-                    x[10] = 1.0 - exp(-alpha);
+                    x[10] = 1.0 - exp(-rough);
                     for (int c = 11; c < OR_NF; ++c) x[c] = 0.0;
                 }
                 q = or_mlp_forward(a->params, x, NULL, NULL, NULL);

@@ -6,6 +6,10 @@
  *       A bias-free MLP 16 -> 32 -> 32 -> 32 -> n_out with Leaky ReLU (slope 0.01) after
  *       each hidden layer and no output activation (Sec. 4 "Network Architecture";
  *       StatNet has no output activation, Sec. 4 "Output & Activation").
+ *   or_mlpk_forward / or_mlpk_backward
+ *       The same network with n_in inputs (32 for StatNet on the encodings of Sec. 4
+ *       "Input Encoding"); the backward pass also returns the gradient at the inputs,
+ *       which the hash grid's entries receive.
  *   or_statnet_dloss
  *       Eq. loss-function_StatNet: relative L2 on the two predicted moments E[<L>] and
  *       E[<L>^2] (Sec. 4 "Output & Activation") against the one-sample targets <L> and
@@ -36,23 +40,28 @@
 #define NH 32
 #define LEAK 0.01
 
-static void layer_ptrs(const double* P, int n_out, const double* W[4]) {
-    (void)n_out;
+#define NIN_MAX 32
+
+static void layer_ptrs(const double* P, int n_in, const double* W[4]) {
     W[0] = P;
-    W[1] = P + NH * NF;
-    W[2] = P + NH * NF + NH * NH;
-    W[3] = P + NH * NF + 2 * NH * NH;
+    W[1] = P + NH * n_in;
+    W[2] = P + NH * n_in + NH * NH;
+    W[3] = P + NH * n_in + 2 * NH * NH;
 }
 
 int64_t or_mlpn_param_count(int n_out) { return NH * NF + 2 * NH * NH + (int64_t)n_out * NH; }
 
-void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, double* pre,
-                     double* hid) {
+int64_t or_mlpk_param_count(int n_in, int n_out) {
+    return NH * (int64_t)n_in + 2 * NH * NH + (int64_t)n_out * NH;
+}
+
+void or_mlpk_forward(const double* P, int n_in, int n_out, const double* x, double* out,
+                     double* pre, double* hid) {
     const double* W[4];
-    layer_ptrs(P, n_out, W);
-    double in[NH], h[NH];
-    int nin = NF;
-    for (int k = 0; k < NF; ++k) in[k] = x[k];
+    layer_ptrs(P, n_in, W);
+    double in[NIN_MAX > NH ? NIN_MAX : NH], h[NH];
+    int nin = n_in;
+    for (int k = 0; k < n_in; ++k) in[k] = x[k];
     for (int l = 0; l < 3; ++l) {
         for (int j = 0; j < NH; ++j) {
             double a = 0.0;
@@ -71,14 +80,20 @@ void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, d
     }
 }
 
-/* Accumulates into G the gradient of sum_o dout[o] * out[o] with respect to P. */
-void or_mlpn_backward(const double* P, int n_out, const double* x, const double* dout,
-                      double* G) {
+void or_mlpn_forward(const double* P, int n_out, const double* x, double* out, double* pre,
+                     double* hid) {
+    or_mlpk_forward(P, NF, n_out, x, out, pre, hid);
+}
+
+/* Accumulates into G the gradient of sum_o dout[o] * out[o] with respect to P; with
+ * dx != NULL also writes its gradient with respect to the n_in inputs. */
+void or_mlpk_backward(const double* P, int n_in, int n_out, const double* x, const double* dout,
+                      double* G, double* dx) {
     double pre[3 * NH], hid[3 * NH], out[8];
-    or_mlpn_forward(P, n_out, x, out, pre, hid);
+    or_mlpk_forward(P, n_in, n_out, x, out, pre, hid);
     const double* W[4];
-    layer_ptrs(P, n_out, W);
-    double* GW[4] = {G, G + NH * NF, G + NH * NF + NH * NH, G + NH * NF + 2 * NH * NH};
+    layer_ptrs(P, n_in, W);
+    double* GW[4] = {G, G + NH * n_in, G + NH * n_in + NH * NH, G + NH * n_in + 2 * NH * NH};
     double dh[NH], da[NH];
     for (int k = 0; k < NH; ++k) dh[k] = 0.0;
     for (int o = 0; o < n_out; ++o)
@@ -87,7 +102,7 @@ void or_mlpn_backward(const double* P, int n_out, const double* x, const double*
             dh[k] += dout[o] * W[3][o * NH + k];
         }
     for (int l = 2; l >= 0; --l) {
-        const int nin = l == 0 ? NF : NH;
+        const int nin = l == 0 ? n_in : NH;
         const double* input = l == 0 ? x : hid + (l - 1) * NH;
         for (int j = 0; j < NH; ++j) da[j] = dh[j] * (pre[l * NH + j] > 0.0 ? 1.0 : LEAK);
         for (int j = 0; j < NH; ++j)
@@ -98,7 +113,18 @@ void or_mlpn_backward(const double* P, int n_out, const double* x, const double*
                 for (int j = 0; j < NH; ++j) s += W[l][j * nin + k] * da[j];
                 dh[k] = s;
             }
+        else if (dx)
+            for (int k = 0; k < n_in; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < NH; ++j) s += W[0][j * n_in + k] * da[j];
+                dx[k] = s;
+            }
     }
+}
+
+void or_mlpn_backward(const double* P, int n_out, const double* x, const double* dout,
+                      double* G) {
+    or_mlpk_backward(P, NF, n_out, x, dout, G, NULL);
 }
 
 /* Relative L2 of both moments; returns the loss of one sample and writes d/dpred with
