@@ -77,11 +77,16 @@ typedef enum nrrs_rrs_mode {
 #define NRRS_HIDDEN 32
 #define NRRS_RRSNET_PARAMS 2592 /* 32x16 + 32x32 + 32x32 + 1x32, no biases */
 #define NRRS_STATNET_PARAMS 2752 /* 32x16 + 32x32 + 32x32 + 6x32, no biases */
+#define NRRS_STATNET_GRID_PARAMS 3264 /* StatNet on the encodings: 32x32 + 32x32 + 32x32 + 6x32 */
+#define NRRS_GRID_PARAMS 4194304 /* hash grid: 8 levels x 2^18 entries x 2 features */
 
 /* Networks for nrrs_set_params / nrrs_get_params. */
 #define NRRS_NET_RRSNET 0       /* RRSNet weights renders use (the EMA of the trained ones) */
 #define NRRS_NET_RRSNET_TRAIN 1 /* RRSNet weights Adam updates                             */
-#define NRRS_NET_STATNET 2      /* StatNet: 16 -> 32 -> 32 -> 32 -> 6, no output activation */
+#define NRRS_NET_STATNET 2      /* StatNet: 16 -> 32 -> 32 -> 32 -> 6, no output activation
+                                   (32 inputs with the encodings of nrrs_set_statnet_encoding:
+                                   NRRS_STATNET_GRID_PARAMS weights)                       */
+#define NRRS_NET_STATNET_GRID 3 /* StatNet's hash grid, [8][2^18][2] (NRRS_GRID_PARAMS)   */
 
 /* Material record, 40 bytes.  type 0 = Lambertian (albedo), 1 = GGX + Lambert
  * "plastic" mixture (roughness is the GGX alpha, F0 the Schlick reflectance at normal
@@ -265,6 +270,21 @@ NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
  * Errors: INVALID_ARG (NULL scene, mode not 0 or 1). */
 NRRS_API nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode);
 
+/* Chooses StatNet's inputs (everywhere StatNet runs: training, ADRRS (NN), NRRS inputs):
+ *   0 (default) the 13 vertex features of RRSNet with the throughput inputs zeroed
+ *     (16 -> 32 -> 32 -> 32 -> 6, NRRS_STATNET_PARAMS weights);
+ *   1 the encodings of Sec. 4 "Input Encoding": a trainable multiresolution hash grid of
+ *     the position in the scene box (8 levels x 2 features, resolution 16 doubling per
+ *     level, 2^18 entries per level; dense indexing while (N+1)^3 fits, else the spatial
+ *     hash x*1 ^ y*2654435761 ^ z*805459861 mod 2^18; trilinear interpolation), one-blob
+ *     encodings (4 bins) of w_o's spherical coordinates (theta / pi from the z axis,
+ *     (phi + pi) / (2 pi)) and one-blob (8 bins) of 1 - exp(-roughness), 32 inputs
+ *     (NRRS_STATNET_GRID_PARAMS weights + NRRS_GRID_PARAMS grid entries, trained by the
+ *     same Adam steps; the grid with epsilon 1e-15).
+ * A change starts StatNet afresh (default weights, grid entries uniform in +-1e-4).
+ * Errors: INVALID_ARG (NULL scene, mode not 0 or 1); OOM; CUDA. */
+NRRS_API nrrs_status nrrs_set_statnet_encoding(nrrs_scene* scene, int32_t mode);
+
 /* Free every device buffer of the scene (synchronizes the device). NULL is a no-op. */
 NRRS_API nrrs_status nrrs_destroy_scene(nrrs_scene* scene);
 
@@ -444,6 +464,28 @@ NRRS_API nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* pa
 NRRS_API nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_params,
                                    const float* d_x, const float* d_gout, int64_t n, float* d_grad,
                                    void* stream);
+
+/* nrrs_mlp_grad for StatNet on the encodings (32 -> 32 -> 32 -> 32 -> 6): d_x [n][32]
+ * (16-byte aligned), d_gout [n][6], d_params NRRS_STATNET_GRID_PARAMS weights, d_grad the
+ * same size.  Errors: INVALID_ARG; CUDA. */
+NRRS_API nrrs_status nrrs_statnet_grad(nrrs_scene* scene, const float* d_params, const float* d_x,
+                                       const float* d_gout, int64_t n, float* d_grad,
+                                       void* stream);
+
+/* StatNet's 32 encoded inputs (nrrs_set_statnet_encoding(1)) of n vertices: d_feat
+ * [n][16] vertex features as the renders write them (position in the scene box in 0..2,
+ * -w_o in 3..5; 16-byte aligned), d_rough [n] roughness (Lambertian 1), out d_x [n][32],
+ * with the scene's hash grid.  Errors: INVALID_ARG; UNSUPPORTED (no grid); CUDA. */
+NRRS_API nrrs_status nrrs_statnet_inputs(nrrs_scene* scene, const float* d_feat,
+                                         const float* d_rough, int64_t n, float* d_x,
+                                         void* stream);
+
+/* Adds to d_grad (device, NRRS_GRID_PARAMS floats, the grid's layout) the gradient of
+ * sum_i d_dx[i] . grid(p_i) for the positions p_i of d_feat [n][16] (16-byte aligned)
+ * and grid-feature gradients d_dx [n][16]: the adjoint of the encoding, by atomic adds
+ * (the order of the additions is not fixed).  Errors: INVALID_ARG; CUDA. */
+NRRS_API nrrs_status nrrs_grid_backward(nrrs_scene* scene, const float* d_feat, const float* d_dx,
+                                        int64_t n, float* d_grad, void* stream);
 
 /* Autotuner of the RRSNet launch shape (no counterpart in the paper; it serves Sec. 4's
  * network in a queue whose size changes per bounce).  For every queue-size bucket b

@@ -10,6 +10,7 @@
 
 #include "bvh.h"
 #include "emitters.h"
+#include "grid.cuh"
 #include "train.cuh"
 #include "wavefront.cuh"
 
@@ -167,10 +168,19 @@ struct TrainState {
     int part_blocks = 0;
     long long step = 0, full_steps = 0;
     double loss_ema = 0.0, loss_min = 0.0;
+    // StatNet's inputs: 0 = vertex features, 1 = the encodings of Sec. 4 with the hash grid
+    int stat_enc = 0;
+    float *grid = nullptr, *grid_m = nullptr, *grid_v = nullptr, *grid_good = nullptr;
+    float *grid_grad = nullptr, *dx = nullptr;
+    long long dx_cap = 0;
+    int stat_n() const {
+        return (stat_enc ? kNH * kStatGridIn : kNH * kNF) + 2 * kNH * kNH + kStatOut * kNH;
+    }
 
     void release_record() {
         cudaFree(rec.dep); cudaFree(rec.q); cudaFree(rec.t); cudaFree(rec.feat);
         cudaFree(rec.feat_net);
+        cudaFree(rec.rough);
         cudaFree(rec.first); cudaFree(rec.X); cudaFree(rec.S);
         cudaFree(m1); cudaFree(m2); cudaFree(V); cudaFree(E); cudaFree(k); cudaFree(rgb);
         cudaFree(E_cur); cudaFree(E_acc); cudaFree(pnrm);
@@ -185,8 +195,11 @@ struct TrainState {
     void release_all() {
         release_record();
         float* fs[] = {rrs_raw, rrs_m, rrs_v, rrs_good, stat, stat_m, stat_v, stat_good,
-                       grad_rrs, grad_stat, part, Fd, Fnd};
+                       grad_rrs, grad_stat, part, Fd, Fnd,
+                       grid, grid_m, grid_v, grid_good, grid_grad, dx};
         for (float* f : fs) cudaFree(f);
+        grid = grid_m = grid_v = grid_good = grid_grad = dx = nullptr;
+        dx_cap = 0;
         cudaFree(loss_part);
         cudaFree(scal);
         cudaFree(bad);
@@ -621,6 +634,7 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     if (t.rec_C >= C && t.rec_D >= D && t.npix >= npix) {
         if (sc->rrsnet_inputs && !t.rec.feat_net)
             CK(dalloc(&t.rec.feat_net, (size_t)t.rec_C * t.rec_D * 4));
+        if (t.stat_enc && !t.rec.rough) CK(dalloc(&t.rec.rough, (size_t)t.rec_C * t.rec_D));
         return NRRS_OK;
     }
     t.release_record();
@@ -642,6 +656,7 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     CK(dalloc(&t.k, npix));
     CK(dalloc(&t.rgb, npix * 3));
     if (sc->rrsnet_inputs) CK(dalloc(&t.rec.feat_net, n * 4));
+    if (t.stat_enc) CK(dalloc(&t.rec.rough, n));
     t.rec.C = C;
     t.rec_C = C;
     t.rec_D = D;
@@ -782,6 +797,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     rp.params = params ? params : scene->params;
     rp.trace = o.d_trace;
     rp.nee = nee ? 1 : 0;
+    rp.stat_grid = scene->train.nets && scene->train.stat_enc
+                       ? reinterpret_cast<const float2*>(scene->train.grid)
+                       : nullptr;
     if (batch) {
         rp.jobs = scene->jw;
         rp.jobs.cap_factor = o.cap_factor;
@@ -852,6 +870,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 w.dep = rec->dep + off;
                 w.feat = rec->feat + off * 4;
                 if (nrrs_inputs) feat_net = rec->feat_net + off * 4;
+                w.rough = rec->rough ? rec->rough + off : nullptr;
                 r.rec_first = rec->first + off;
                 r.rec_X = rec->X + off;
                 CK(cudaMemcpyAsync(rec->t + off, q[cur].t, sizeof(float4) * C,
@@ -875,7 +894,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             } else if (kind == kFactorAdrrs) {
                 TIMED(NRRS_STAGE_RRSNET,
-                      launch_adrrs(scene->train.stat, w, q[cur], r, d, scene->n_sm * 4, s));
+                      launch_adrrs(scene->train.stat, scene->view, w, q[cur], r, d,
+                                   scene->n_sm * 4, s));
                 if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             }
             if (batch) {  // Eq. F_norm per job
@@ -934,7 +954,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)scene->train.stat,
                                (uint64_t)o.cap_factor, (uint64_t)(uintptr_t)ws.sh_o,
                                (uint64_t)(uintptr_t)ws.qpdf[0], (uint64_t)(uintptr_t)ws.feat_net,
-                               (uint64_t)(uintptr_t)(rec ? rec->feat_net : nullptr)};
+                               (uint64_t)(uintptr_t)(rec ? rec->feat_net : nullptr),
+                               (uint64_t)(uintptr_t)rp.stat_grid,
+                               (uint64_t)(uintptr_t)(rec ? rec->rough : nullptr)};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -1299,8 +1321,8 @@ namespace {
 
 // Xavier-uniform start for StatNet from a fixed linear congruential stream (the library
 // has no other source of randomness for it; callers may overwrite it with nrrs_set_params).
-void default_statnet(std::vector<float>& w) {
-    const int shapes[4][2] = {{kNH, kNF}, {kNH, kNH}, {kNH, kNH}, {kStatOut, kNH}};
+void default_statnet(std::vector<float>& w, int n_in) {
+    const int shapes[4][2] = {{kNH, n_in}, {kNH, kNH}, {kNH, kNH}, {kStatOut, kNH}};
     uint64_t x = 0x5eed5eed12345ull;
     size_t p = 0;
     for (auto& sh : shapes) {
@@ -1313,6 +1335,41 @@ void default_statnet(std::vector<float>& w) {
     }
 }
 
+// StatNet's weights afresh for its current inputs (and the hash grid's entries uniform in
+// +-1e-4, as Instant-NGP starts them, from the same fixed stream), moments zeroed.
+nrrs_status init_statnet(nrrs_scene* sc, cudaStream_t s) {
+    TrainState& t = sc->train;
+    const int n = t.stat_n();
+    std::vector<float> w(n);
+    default_statnet(w, t.stat_enc ? kStatGridIn : kNF);
+    CK(cudaMemcpy(t.stat, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.stat_good, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * n, s));
+    if (t.stat_enc) {
+        if (!t.grid) {
+            CK(dalloc(&t.grid, (size_t)kGridParams));
+            CK(dalloc(&t.grid_m, (size_t)kGridParams));
+            CK(dalloc(&t.grid_v, (size_t)kGridParams));
+            CK(dalloc(&t.grid_good, (size_t)kGridParams));
+            CK(dalloc(&t.grid_grad, (size_t)kGridParams));
+        }
+        std::vector<float> g((size_t)kGridParams);
+        uint64_t x = 0x6a09e667f3bcc908ull;
+        for (auto& v : g) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            v = (float)(((double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * 1e-4);
+        }
+        CK(cudaMemcpy(t.grid, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(t.grid_good, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemsetAsync(t.grid_m, 0, sizeof(float) * g.size(), s));
+        CK(cudaMemsetAsync(t.grid_v, 0, sizeof(float) * g.size(), s));
+    }
+    return NRRS_OK;
+}
+
+constexpr int kStatParamsMax = kNH * kStatGridIn + 2 * kNH * kNH + kStatOut * kNH;
+
 nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     TrainState& t = sc->train;
     if (t.nets) return NRRS_OK;
@@ -1320,14 +1377,14 @@ nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     CK(dalloc(&t.rrs_m, kNParams));
     CK(dalloc(&t.rrs_v, kNParams));
     CK(dalloc(&t.rrs_good, kNParams));
-    CK(dalloc(&t.stat, kStatParams));
-    CK(dalloc(&t.stat_m, kStatParams));
-    CK(dalloc(&t.stat_v, kStatParams));
-    CK(dalloc(&t.stat_good, kStatParams));
+    CK(dalloc(&t.stat, kStatParamsMax));
+    CK(dalloc(&t.stat_m, kStatParamsMax));
+    CK(dalloc(&t.stat_v, kStatParamsMax));
+    CK(dalloc(&t.stat_good, kStatParamsMax));
     CK(dalloc(&t.grad_rrs, kNParams));
-    CK(dalloc(&t.grad_stat, kStatParams));
+    CK(dalloc(&t.grad_stat, kStatParamsMax));
     t.part_blocks = sc->n_sm * 3;
-    CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParams));
+    CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParamsMax));
     CK(dalloc(&t.loss_part, t.part_blocks));
     CK(dalloc(&t.scal, 8));
     CK(dalloc(&t.Fd, kMaxDepth));
@@ -1337,12 +1394,8 @@ nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     CK(cudaMemcpyAsync(t.rrs_good, sc->params, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
     CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
-    std::vector<float> w(kStatParams);
-    default_statnet(w);
-    CK(cudaMemcpy(t.stat, w.data(), sizeof(float) * kStatParams, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(t.stat_good, w.data(), sizeof(float) * kStatParams, cudaMemcpyHostToDevice));
-    CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * kStatParams, s));
-    CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * kStatParams, s));
+    nrrs_status rc = init_statnet(sc, s);
+    if (rc != NRRS_OK) return rc;
     t.nets = true;
     return NRRS_OK;
 }
@@ -1366,34 +1419,61 @@ extern "C" {
 nrrs_status nrrs_set_params(nrrs_scene* scene, int32_t which, const float* params, int32_t n,
                             void* stream) {
     if (!scene || !params) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or params");
-    const int want = which == NRRS_NET_STATNET ? kStatParams : kNParams;
-    if (which < 0 || which > 2 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
     DeviceGuard g(scene->device);
     cudaStream_t s = (cudaStream_t)stream;
     nrrs_status rc = ensure_train_nets(scene, s);
     if (rc != NRRS_OK) return rc;
     TrainState& t = scene->train;
-    float* dst = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw : t.stat;
+    const long long want = which == NRRS_NET_STATNET ? t.stat_n()
+                           : which == NRRS_NET_STATNET_GRID ? kGridParams : kNParams;
+    if (which < 0 || which > 3 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+    if (which == NRRS_NET_STATNET_GRID && !t.stat_enc)
+        return fail(NRRS_ERR_UNSUPPORTED, "StatNet has no hash grid (nrrs_set_statnet_encoding)");
+    float* dst = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw
+                 : which == NRRS_NET_STATNET ? t.stat : t.grid;
     CK(cudaMemcpyAsync(dst, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
-    if (which == NRRS_NET_STATNET) {
-        CK(cudaMemcpyAsync(t.stat_good, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * n, s));
-        CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * n, s));
+    if (which == NRRS_NET_STATNET || which == NRRS_NET_STATNET_GRID) {
+        float* good = which == NRRS_NET_STATNET ? t.stat_good : t.grid_good;
+        float* m = which == NRRS_NET_STATNET ? t.stat_m : t.grid_m;
+        float* v = which == NRRS_NET_STATNET ? t.stat_v : t.grid_v;
+        CK(cudaMemcpyAsync(good, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(m, 0, sizeof(float) * n, s));
+        CK(cudaMemsetAsync(v, 0, sizeof(float) * n, s));
     }
     CK(cudaStreamSynchronize(s));
     return NRRS_OK;
 }
 
+nrrs_status nrrs_set_statnet_encoding(nrrs_scene* scene, int32_t mode) {
+    if (!scene || (mode != 0 && mode != 1)) return fail(NRRS_ERR_INVALID_ARG, "bad StatNet encoding");
+    DeviceGuard g(scene->device);
+    nrrs_status rc = ensure_train_nets(scene, nullptr);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = scene->train;
+    if (t.stat_enc == mode) return NRRS_OK;
+    t.stat_enc = mode;
+    cudaFree(t.rec.rough);  // recorded roughness belongs to the encoded inputs
+    t.rec.rough = nullptr;
+    rc = init_statnet(scene, nullptr);
+    if (rc != NRRS_OK) return rc;
+    CK(cudaDeviceSynchronize());
+    return NRRS_OK;
+}
+
 nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int32_t n, void* stream) {
     if (!scene || !params) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or params");
-    const int want = which == NRRS_NET_STATNET ? kStatParams : kNParams;
-    if (which < 0 || which > 2 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
     DeviceGuard g(scene->device);
     cudaStream_t s = (cudaStream_t)stream;
     nrrs_status rc = ensure_train_nets(scene, s);
     if (rc != NRRS_OK) return rc;
     TrainState& t = scene->train;
-    const float* src = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw : t.stat;
+    const long long want = which == NRRS_NET_STATNET ? t.stat_n()
+                           : which == NRRS_NET_STATNET_GRID ? kGridParams : kNParams;
+    if (which < 0 || which > 3 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+    if (which == NRRS_NET_STATNET_GRID && !t.stat_enc)
+        return fail(NRRS_ERR_UNSUPPORTED, "StatNet has no hash grid (nrrs_set_statnet_encoding)");
+    const float* src = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw
+                       : which == NRRS_NET_STATNET ? t.stat : t.grid;
     CK(cudaMemcpyAsync(params, src, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return NRRS_OK;
@@ -1402,7 +1482,7 @@ nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int
 namespace {
 nrrs_status mlp_grad_impl(nrrs_scene* scene, int32_t n_out, bool at_q, const float* d_params,
                           const float* d_x, const float* d_gout, int64_t n, float* d_grad,
-                          void* stream) {
+                          void* stream, int n_in = kNF) {
     if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_x must be 16-byte aligned");
     DeviceGuard g(scene->device);
@@ -1410,7 +1490,7 @@ nrrs_status mlp_grad_impl(nrrs_scene* scene, int32_t n_out, bool at_q, const flo
     nrrs_status rc = ensure_train_nets(scene, s);
     if (rc != NRRS_OK) return rc;
     TrainState& t = scene->train;
-    const int P = kNH * kNF + 2 * kNH * kNH + n_out * kNH;
+    const int P = kNH * n_in + 2 * kNH * kNH + n_out * kNH;
     TrainArgs a{};
     a.params = d_params;
     a.gin = d_gout;
@@ -1423,7 +1503,7 @@ nrrs_status mlp_grad_impl(nrrs_scene* scene, int32_t n_out, bool at_q, const flo
     b.total = n;
     b.batch = n;
     b.net_mask = 1u;
-    CK(launch_mlp_grad_given(n_out, at_q, a, r, b, t.part_blocks, t.part, t.loss_part, s));
+    CK(launch_mlp_grad_given(n_out, at_q, a, r, b, t.part_blocks, t.part, t.loss_part, s, n_in));
     launch_reduce_grad(t.part, t.part_blocks, P, d_grad, s);
     CK(cudaGetLastError());
     return NRRS_OK;
@@ -1436,6 +1516,45 @@ nrrs_status nrrs_mlp_grad(nrrs_scene* scene, int32_t n_out, const float* d_param
         (n > 0 && (!d_x || !d_gout)))
         return fail(NRRS_ERR_INVALID_ARG, "bad mlp_grad arguments");
     return mlp_grad_impl(scene, n_out, false, d_params, d_x, d_gout, n, d_grad, stream);
+}
+
+nrrs_status nrrs_statnet_grad(nrrs_scene* scene, const float* d_params, const float* d_x,
+                              const float* d_gout, int64_t n, float* d_grad, void* stream) {
+    if (!scene || n < 0 || !d_params || !d_grad || (n > 0 && (!d_x || !d_gout)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad statnet_grad arguments");
+    return mlp_grad_impl(scene, kStatOut, false, d_params, d_x, d_gout, n, d_grad, stream,
+                         kStatGridIn);
+}
+
+nrrs_status nrrs_statnet_inputs(nrrs_scene* scene, const float* d_feat, const float* d_rough,
+                                int64_t n, float* d_x, void* stream) {
+    if (!scene || n < 0 || (n > 0 && (!d_feat || !d_rough || !d_x)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad statnet_inputs arguments");
+    if ((reinterpret_cast<uintptr_t>(d_feat) & 15u) != 0)
+        return fail(NRRS_ERR_INVALID_ARG, "d_feat must be 16-byte aligned");
+    if (!scene->train.nets || !scene->train.stat_enc)
+        return fail(NRRS_ERR_UNSUPPORTED, "StatNet has no hash grid (nrrs_set_statnet_encoding)");
+    if (n == 0) return NRRS_OK;
+    DeviceGuard g(scene->device);
+    launch_statnet_inputs(reinterpret_cast<const float4*>(d_feat), d_rough, n,
+                          reinterpret_cast<const float2*>(scene->train.grid), d_x,
+                          (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_grid_backward(nrrs_scene* scene, const float* d_feat, const float* d_dx,
+                               int64_t n, float* d_grad, void* stream) {
+    if (!scene || n < 0 || !d_grad || (n > 0 && (!d_feat || !d_dx)))
+        return fail(NRRS_ERR_INVALID_ARG, "bad grid_backward arguments");
+    if ((reinterpret_cast<uintptr_t>(d_feat) & 15u) != 0)
+        return fail(NRRS_ERR_INVALID_ARG, "d_feat must be 16-byte aligned");
+    if (n == 0) return NRRS_OK;
+    DeviceGuard g(scene->device);
+    launch_grid_backward(reinterpret_cast<const float4*>(d_feat), d_dx, n, d_grad,
+                         (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
 }
 
 nrrs_status nrrs_rrsnet_backward(nrrs_scene* scene, const float* d_params, const float* d_x,
@@ -1649,9 +1768,27 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     a.g3 = o.gamma3;
     a.params = t.stat;
     a.scale = N > 0 ? (float)(1.0 / N) : 0.0f;
+    const int stat_n = t.stat_n();
+    if (t.stat_enc) {  // StatNet on the encodings: its hash grid and the feature gradients
+        if (t.dx_cap < b.batch) {
+            cudaFree(t.dx);
+            t.dx = nullptr;
+            t.dx_cap = 0;
+            CK(dalloc(&t.dx, (size_t)b.batch * 16));
+            t.dx_cap = b.batch;
+        }
+        a.grid = reinterpret_cast<const float2*>(t.grid);
+        a.dx = t.dx;
+    }
     CK(launch_mlp_train(kTrainStatNet, a, t.rec, b, t.part_blocks, t.part, t.loss_part, s));
-    launch_reduce_grad(t.part, t.part_blocks, kStatParams, t.grad_stat, s);
+    launch_reduce_grad(t.part, t.part_blocks, stat_n, t.grad_stat, s);
     launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 1, s);
+    if (t.stat_enc) {
+        CK(cudaMemsetAsync(t.grid_grad, 0, sizeof(float) * (size_t)kGridParams, s));
+        launch_grid_scatter(a, t.rec, b, scene->n_sm * 8, t.grid_grad, s);
+    }
+    a.grid = nullptr;
+    a.dx = nullptr;
     const bool warm = t.step < o.warmup_steps;
     a.params = t.rrs_raw;
     a.scale = warm ? (N > 0 ? (float)(1.0 / N) : 0.0f) : 1.0f;
@@ -1663,8 +1800,11 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     // 4. Adam for both networks (Sec. 4 "Training": lr 0.005 StatNet, 0.0003 RRSNet)
     CK(cudaMemsetAsync(t.bad, 0, sizeof(int), s));
     const int step = (int)t.step + 1;
-    launch_adam(t.stat, t.grad_stat, t.stat_m, t.stat_v, kStatParams, step, o.lr_statnet, 0.9f,
+    launch_adam(t.stat, t.grad_stat, t.stat_m, t.stat_v, stat_n, step, o.lr_statnet, 0.9f,
                 0.999f, 1e-8f, t.bad, s);
+    if (t.stat_enc)  // the grid's entries take tiny gradients: Instant-NGP's epsilon 1e-15
+        launch_adam(t.grid, t.grid_grad, t.grid_m, t.grid_v, (int)kGridParams, step,
+                    o.lr_statnet, 0.9f, 0.999f, 1e-15f, t.bad, s);
     launch_adam(t.rrs_raw, t.grad_rrs, t.rrs_m, t.rrs_v, kNParams, step, o.lr_rrsnet, 0.9f, 0.999f,
                 1e-8f, t.bad, s);
     int bad = 0;
@@ -1690,17 +1830,26 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     if (fallback) {  // restore the last good weights and forget the moments
         scene->heur_next = true;
         CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(t.stat, t.stat_good, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.stat, t.stat_good, sizeof(float) * stat_n, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
         CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
-        CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * kStatParams, s));
-        CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * kStatParams, s));
+        CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * stat_n, s));
+        CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * stat_n, s));
+        if (t.stat_enc) {
+            CK(cudaMemcpyAsync(t.grid, t.grid_good, sizeof(float) * (size_t)kGridParams,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(t.grid_m, 0, sizeof(float) * (size_t)kGridParams, s));
+            CK(cudaMemsetAsync(t.grid_v, 0, sizeof(float) * (size_t)kGridParams, s));
+        }
         if (fallback == 2) {
             t.loss_ema = t.loss_min;
         }
     } else {
         CK(cudaMemcpyAsync(t.rrs_good, t.rrs_raw, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(t.stat_good, t.stat, sizeof(float) * kStatParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.stat_good, t.stat, sizeof(float) * stat_n, cudaMemcpyDeviceToDevice, s));
+        if (t.stat_enc)
+            CK(cudaMemcpyAsync(t.grid_good, t.grid, sizeof(float) * (size_t)kGridParams,
+                               cudaMemcpyDeviceToDevice, s));
         // inference weights: EMA of the trained weights (Sec. 4 "Training", as in NRC), with
         // the usual warm start decay_t = min(decay, (1 + t) / (10 + t))
         const float warm_decay = (float)(1.0 + (double)t.step) / (float)(10.0 + (double)t.step);
@@ -1724,6 +1873,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         // reference fold, sample counts, mean, loss terms; 2 x (train, reduce grad,
         // reduce loss); 2 Adam; EMA
         out->kernel_launches = (int64_t)rs.kernel_launches + 2 + t.filter_launches +
+                               (t.stat_enc ? 2 : 0) +
                                (o.d_pixel_ref ? 0 : 1) + 3 + 6 + 2 + (fallback ? 0 : 1);
     }
     return NRRS_OK;

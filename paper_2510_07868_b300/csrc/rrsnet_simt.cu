@@ -7,6 +7,7 @@
 // Each row's sums run in the same order whatever ROWS is, so results are identical.
 #include <cfloat>
 
+#include "grid.cuh"
 #include "wavefront.cuh"
 
 namespace nrrs {
@@ -147,6 +148,56 @@ k_rrsnet_simt(const float* __restrict__ params, const float4* __restrict__ feat,
     }
 }
 
+// StatNet's weights in shared memory: sized for the 32-input (encoded) network.
+constexpr int kStatSmem = kNH * kStatGridIn + 2 * kNH * kNH + 6 * kNH;
+
+// Roughness of the surface a row's ray hit (Lambertian: 1).
+__device__ __forceinline__ float hit_roughness(const SceneView& sc, const float2* hit, long long i) {
+    const int slot = __float_as_int(hit[i].y);
+    const nrrs_material& m = sc.mats[__float_as_uint(__ldg(&sc.tris[3 * slot + 1].w))];
+    return m.type == 0 ? 1.0f : m.roughness;
+}
+
+// StatNet's six outputs at row i (Sec. 3.2, 4): with a hash grid on the encodings of
+// Sec. 4 "Input Encoding" (position, w_o, roughness), else on the vertex features with the
+// throughput inputs zeroed.  sW: the weights in shared memory.
+__device__ __forceinline__ void statnet_outputs(const float* sW, const float4* __restrict__ feat,
+                                                long long i, const float2* grid, float alpha,
+                                                float* out) {
+    float h[1][kNH], g[1][kNH];
+    int kin;
+    if (grid) {
+        float x[1][kStatGridIn];
+        const float4 f0 = feat[4 * i], f1 = feat[4 * i + 1];
+        statnet_grid_inputs(grid, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, alpha, x[0]);
+        dense<1, kStatGridIn>(sW, x, h);
+        kin = kStatGridIn;
+    } else {
+        float x[1][kNF];
+        load_row(feat, i, x[0]);
+        x[0][13] = x[0][14] = x[0][15] = 0.0f;
+        dense<1, kNF>(sW, x, h);
+        kin = kNF;
+    }
+    const float* W2 = sW + kNH * kin;
+    dense<1, kNH>(W2, h, g);
+    dense<1, kNH>(W2 + kNH * kNH, g, h);
+    const float* W4 = W2 + 2 * kNH * kNH;
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        float z = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kNH; ++k) z = fmaf(W4[o * kNH + k], h[0][k], z);
+        out[o] = z;
+    }
+}
+
+__device__ __forceinline__ void load_statnet(const float* __restrict__ stat, bool grid, float* sW) {
+    const int n = (grid ? kNH * kStatGridIn : kNH * kNF) + 2 * kNH * kNH + 6 * kNH;
+    for (int i = threadIdx.x; i < n / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(stat) + i);
+}
+
 // ADRRS (NN) factors, Sec. 4 "Mix-Depth": StatNet (16 -> 32 -> 32 -> 32 -> 6, the
 // throughput inputs zeroed as in its training) predicts E[<L>] per channel at each
 // vertex the render marked (q < 0); r = lum(t) max(mean_rgb E[<L>], 0) / max(I_px, eps_I)
@@ -161,14 +212,13 @@ constexpr float kAdrrsWindowLo = (float)(2.0 / 6.0);
 constexpr float kAdrrsWindowHi = (float)(10.0 / 6.0);
 
 __global__ void __launch_bounds__(kThreads, 2)
-k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, const float4* t,
-             const float4* dep, const long long* n_ptr, float* q, RenderParams rp, DevStats* st) {
-    constexpr int kStatParams = kNH * kNF + 2 * kNH * kNH + 6 * kNH;
-    __shared__ __align__(16) float sW[kStatParams];
+k_adrrs_simt(const float* __restrict__ stat, SceneView sc, const float4* __restrict__ feat,
+             const float4* t, const float4* dep, const float2* hit, const long long* n_ptr,
+             float* q, RenderParams rp, DevStats* st) {
+    __shared__ __align__(16) float sW[kStatSmem];
     const long long n = *n_ptr;
     if ((long long)blockIdx.x * blockDim.x >= n) return;
-    for (int i = threadIdx.x; i < kStatParams / 4; i += blockDim.x)
-        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(stat) + i);
+    load_statnet(stat, rp.stat_grid != nullptr, sW);
     __syncthreads();
     const int has_ref = st->has_ref;
     unsigned int evals = 0, nonfinite = 0;
@@ -184,23 +234,10 @@ k_adrrs_simt(const float* __restrict__ stat, const float4* __restrict__ feat, co
         if (!has_ref) {
             v = l;
         } else {
-            float x[1][kNF];
-            load_row(feat, i, x[0]);
-            x[0][13] = x[0][14] = x[0][15] = 0.0f;
-            float h[1][kNH], g[1][kNH];
-            dense<1, kNF>(sW, x, h);
-            dense<1, kNH>(sW + kNH * kNF, h, g);
-            dense<1, kNH>(sW + kNH * kNF + kNH * kNH, g, h);
-            const float* W4 = sW + kNH * kNF + 2 * kNH * kNH;
-            float m = 0.0f;
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                float z = 0.0f;
-#pragma unroll
-                for (int k = 0; k < kNH; ++k) z = fmaf(W4[o * kNH + k], h[0][k], z);
-                m += z;
-            }
-            m *= (1.0f / 3.0f);
+            float so[6];
+            statnet_outputs(sW, feat, i, rp.stat_grid,
+                            rp.stat_grid ? hit_roughness(sc, hit, i) : 0.0f, so);
+            const float m = (so[0] + so[1] + so[2]) * (1.0f / 3.0f);
             const float* rr = rp.ref + 3 * (size_t)pix;
             const float den = fmaxf((rr[0] + rr[1] + rr[2]) / 3.0f, eps_I);
             // r: the path's expected contribution over the pixel estimate; inside the
@@ -243,33 +280,21 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_nrrs_inputs(const float* __restrict__ stat, SceneView sc, const float4* __restrict__ feat,
               const float4* t, const float4* dep, const float2* hit, const long long* n_ptr,
               const float* q, float4* out, RenderParams rp) {
-    constexpr int kStatParams = kNH * kNF + 2 * kNH * kNH + 6 * kNH;
-    __shared__ __align__(16) float sW[kStatParams];
+    __shared__ __align__(16) float sW[kStatSmem];
     const long long n = *n_ptr;
     if ((long long)blockIdx.x * blockDim.x >= n) return;
-    for (int i = threadIdx.x; i < kStatParams / 4; i += blockDim.x)
-        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(stat) + i);
+    load_statnet(stat, rp.stat_grid != nullptr, sW);
     __syncthreads();
     const float lam = rp.boxcox_lambda;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (!(q[i] < 0.0f)) continue;
-        float x[1][kNF];
-        load_row(feat, i, x[0]);
-        x[0][13] = x[0][14] = x[0][15] = 0.0f;
-        float h[1][kNH], g[1][kNH];
-        dense<1, kNF>(sW, x, h);
-        dense<1, kNH>(sW + kNH * kNF, h, g);
-        dense<1, kNH>(sW + kNH * kNF + kNH * kNH, g, h);
-        const float* W4 = sW + kNH * kNF + 2 * kNH * kNH;
+        const float rough = hit_roughness(sc, hit, i);
+        float so[6];
+        statnet_outputs(sW, feat, i, rp.stat_grid, rough, so);
         float f[kNF];
 #pragma unroll
-        for (int o = 0; o < 6; ++o) {
-            float z = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kNH; ++k) z = fmaf(W4[o * kNH + k], h[0][k], z);
-            f[o] = boxcox_in(fmaxf(z, 0.0f), lam);
-        }
+        for (int o = 0; o < 6; ++o) f[o] = boxcox_in(fmaxf(so[o], 0.0f), lam);
         const float4 t4 = t[i];
         f[6] = boxcox_in(t4.x, lam);
         f[7] = boxcox_in(t4.y, lam);
@@ -280,9 +305,7 @@ k_nrrs_inputs(const float* __restrict__ stat, SceneView sc, const float4* __rest
             I = (rr[0] + rr[1] + rr[2]) / 3.0f;
         }
         f[9] = boxcox_in(fmaxf(I, 0.0f), lam);
-        const int slot = __float_as_int(hit[i].y);
-        const nrrs_material& m = sc.mats[__float_as_uint(__ldg(&sc.tris[3 * slot + 1].w))];
-        f[10] = 1.0f - expf(-(m.type == 0 ? 1.0f : m.roughness));
+        f[10] = 1.0f - expf(-rough);
 #pragma unroll
         for (int k = 11; k < kNF; ++k) f[k] = 0.0f;
         float4* o4 = out + 4 * i;
@@ -301,10 +324,10 @@ void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& 
                                             &w.st->live[depth - 1], w.q, out, rp);
 }
 
-void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
-                  int depth, int grid, cudaStream_t s) {
-    k_adrrs_simt<<<grid, kThreads, 0, s>>>(stat, w.feat, cur.t, w.dep, &w.st->live[depth - 1], w.q,
-                                           rp, w.st);
+void launch_adrrs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
+                  const RenderParams& rp, int depth, int grid, cudaStream_t s) {
+    k_adrrs_simt<<<grid, kThreads, 0, s>>>(stat, sc, w.feat, cur.t, w.dep, w.hit,
+                                           &w.st->live[depth - 1], w.q, rp, w.st);
 }
 
 void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* feat,

@@ -4,6 +4,7 @@
 // Adam and the EMA of the weights.
 #include <cfloat>
 
+#include "grid.cuh"
 #include "train.cuh"
 
 namespace nrrs {
@@ -208,11 +209,12 @@ __global__ void k_relmse(const float* img, const float* ref, long long n3, doubl
 }
 
 // ------------------------------------------------------------------ MLP training
-// Shared-memory layout of one tile (kTile samples): inputs X[kTile][16], hidden
+// Shared-memory layout of one tile (kTile samples): inputs X[kTile][KIN], hidden
 // activations A1..A3[kTile][32] (post Leaky ReLU; their sign is the sign of the
 // pre-activation), output gradients G[kTile][8], then the weights.
+template <int KIN>
 struct TrainSmem {
-    float X[kTile][kNF];
+    float X[kTile][KIN];
     float A[3][kTile][kNH];
     float G[kTile][8];
 };
@@ -278,26 +280,29 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
 }
 
 // Weight-gradient ownership (register blocking): thread t owns row j = t / 4 of the
-// gradients of W1, W2 and W3, columns [4 (t % 4), +4) of W1 and [8 (t % 4), +8) of W2 and
-// W3, and entries t and t + kTile of W4.  Per sample it reads delta[j] once (shared by the
-// row's 4 threads) and its inputs with 128-bit loads.
-template <int NOUT, int MODE>
-__global__ void __launch_bounds__(kTile, 3)
+// gradients of W1, W2 and W3, columns [KIN/4 (t % 4), +KIN/4) of W1 and [8 (t % 4), +8) of
+// W2 and W3, and entries t and t + kTile of W4.  Per sample it reads delta[j] once (shared
+// by the row's 4 threads) and its inputs with 128-bit loads.
+// KIN = 32: StatNet on the encodings of Sec. 4 (hash grid of the position, one-blob w_o
+// and roughness), which also writes the gradient at its 16 grid features per slot.
+template <int NOUT, int MODE, int KIN = kNF>
+__global__ void __launch_bounds__(kTile, KIN == kNF ? 3 : 2)  // 32 inputs: 2 tiles fit in smem
 k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
-    float* W = reinterpret_cast<float*>(smem_raw + sizeof(TrainSmem));
-    constexpr int P = kNH * kNF + 2 * kNH * kNH + NOUT * kNH;
+    TrainSmem<KIN>& sm = *reinterpret_cast<TrainSmem<KIN>*>(smem_raw);
+    float* W = reinterpret_cast<float*>(smem_raw + sizeof(TrainSmem<KIN>));
+    constexpr int P = kNH * KIN + 2 * kNH * kNH + NOUT * kNH;
+    constexpr int C1 = KIN / 4;  // W1 gradient columns per thread
     for (int p = threadIdx.x; p < P; p += blockDim.x) W[p] = a.params[p];
     const float* W1 = W;
-    const float* W2 = W + kNH * kNF;
+    const float* W2 = W + kNH * KIN;
     const float* W3 = W2 + kNH * kNH;
     const float* W4 = W3 + kNH * kNH;
     const int tid = threadIdx.x;
     const int gj = tid >> 2, gq = tid & 3;
-    float g1[4], g2[8], g3[8], g4[2];
+    float g1[C1], g2[8], g3[8], g4[2];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) g1[e] = 0.0f;
+    for (int e = 0; e < C1; ++e) g1[e] = 0.0f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) g2[e] = g3[e] = 0.0f;
     g4[0] = g4[1] = 0.0f;
@@ -310,15 +315,15 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         const long long u = MODE == kTrainGiven || MODE == kTrainGivenQ ? slot
                             : slot < b.batch ? batch_vertex(b, slot) : b.total;
         // ---- forward of this thread's sample
-        float x[kNF];
+        float x[KIN];
         bool active = false;
         int d = 0;
         long long i = 0;
         if ((MODE == kTrainGiven || MODE == kTrainGivenQ) && u < b.total) {
             active = true;
-            const float4* f = r.feat + 4 * u;
+            const float4* f = r.feat + (KIN / 4) * u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < KIN / 4; ++k) {
                 const float4 v = f[k];
                 x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
             }
@@ -327,7 +332,11 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             i = u - b.offset[d];
             const size_t g = (size_t)d * r.C + i;
             active = ((b.net_mask >> d) & 1u) && r.q[g] > 0.0f;
-            if (active) {
+            if (active && KIN == kStatGridIn) {
+                // StatNet's encoded inputs: position and w_o from the vertex features
+                const float4 f0 = r.feat[4 * g], f1 = r.feat[4 * g + 1];
+                statnet_grid_inputs(a.grid, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, r.rough[g], x);
+            } else if (active) {
                 // StatNet learns from the vertex features; RRSNet reads its own inputs
                 // (the NRRS encoding, when the scene uses it)
                 const float4* f =
@@ -342,16 +351,16 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         }
         if (!active) {
 #pragma unroll
-            for (int k = 0; k < kNF; ++k) x[k] = 0.0f;
+            for (int k = 0; k < KIN; ++k) x[k] = 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < kNF; ++k) sm.X[tid][k] = x[k];
+        for (int k = 0; k < KIN; ++k) sm.X[tid][k] = x[k];
         float h[kNH], hn[kNH];
 #pragma unroll
         for (int j = 0; j < kNH; ++j) {
             float s = 0.0f;
 #pragma unroll
-            for (int k = 0; k < kNF; ++k) s = fmaf(W1[j * kNF + k], x[k], s);
+            for (int k = 0; k < KIN; ++k) s = fmaf(W1[j * KIN + k], x[k], s);
             h[j] = lrelu(s);
             sm.A[0][tid][j] = h[j];
         }
@@ -464,6 +473,17 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             for (int j = 0; j < kNH; ++j) sacc = fmaf(W2[j * kNH + k], h[j], sacc);
             dl[k] = sacc * (sm.A[0][tid][k] > 0.0f ? 1.0f : kLeak);
         }
+        if (KIN == kStatGridIn && a.dx && slot < b.batch) {
+            // gradient at the 16 grid features: W1^T delta1 (zero for a sample that does
+            // not train); the grid's entries receive it in k_grid_scatter
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                float sacc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < kNH; ++j) sacc = fmaf(W1[j * KIN + c], dl[j], sacc);
+                a.dx[slot * 16 + c] = sacc;
+            }
+        }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kNH; ++k) sm.A[0][tid][k] = dl[k];  // A1 now holds delta1
@@ -471,24 +491,29 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         // ---- W1 gradients: sum_s delta1[s][j] X[s][k]
         for (int q = 0; q < kTile; ++q) {
             const float dj = sm.A[0][q][gj];
-            const float4 x0 = *reinterpret_cast<const float4*>(&sm.X[q][4 * gq]);
-            g1[0] = fmaf(dj, x0.x, g1[0]); g1[1] = fmaf(dj, x0.y, g1[1]);
-            g1[2] = fmaf(dj, x0.z, g1[2]); g1[3] = fmaf(dj, x0.w, g1[3]);
+#pragma unroll
+            for (int c4 = 0; c4 < C1 / 4; ++c4) {
+                const float4 x0 = *reinterpret_cast<const float4*>(&sm.X[q][C1 * gq + 4 * c4]);
+                g1[4 * c4 + 0] = fmaf(dj, x0.x, g1[4 * c4 + 0]);
+                g1[4 * c4 + 1] = fmaf(dj, x0.y, g1[4 * c4 + 1]);
+                g1[4 * c4 + 2] = fmaf(dj, x0.z, g1[4 * c4 + 2]);
+                g1[4 * c4 + 3] = fmaf(dj, x0.w, g1[4 * c4 + 3]);
+            }
         }
         __syncthreads();
     }
     float* pb = part + (size_t)blockIdx.x * P;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) pb[gj * kNF + 4 * gq + e] = g1[e];
+    for (int e = 0; e < C1; ++e) pb[gj * KIN + C1 * gq + e] = g1[e];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        pb[kNH * kNF + gj * kNH + 8 * gq + e] = g2[e];
-        pb[kNH * kNF + kNH * kNH + gj * kNH + 8 * gq + e] = g3[e];
+        pb[kNH * KIN + gj * kNH + 8 * gq + e] = g2[e];
+        pb[kNH * KIN + kNH * kNH + gj * kNH + 8 * gq + e] = g3[e];
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int p = tid + e * kTile;
-        if (p < NOUT * kNH) pb[kNH * kNF + 2 * kNH * kNH + p] = g4[e];
+        if (p < NOUT * kNH) pb[kNH * KIN + 2 * kNH * kNH + p] = g4[e];
     }
     __shared__ double shl[32];
     loss = block_sum(loss, shl);
@@ -554,20 +579,42 @@ __global__ void k_rrsnet_dloss(const float* q_nrrs, const float* F, const float*
     dq[s] = dLdV * dV * F[s] + g3 * 2.0f * (q_nrrs[s] - Fn[s] * q_nrrs[s]);
 }
 
-template <int NOUT, int MODE>
+template <int NOUT, int MODE, int KIN = kNF>
 size_t train_smem() {
-    return sizeof(TrainSmem) + sizeof(float) * (kNH * kNF + 2 * kNH * kNH + NOUT * kNH);
+    return sizeof(TrainSmem<KIN>) + sizeof(float) * (kNH * KIN + 2 * kNH * kNH + NOUT * kNH);
 }
 
-template <int NOUT, int MODE>
+template <int NOUT, int MODE, int KIN = kNF>
 cudaError_t launch_train_t(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
                            float* part, double* loss_part, cudaStream_t s) {
-    const size_t smem = train_smem<NOUT, MODE>();
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_train<NOUT, MODE>,
+    const size_t smem = train_smem<NOUT, MODE, KIN>();
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train<NOUT, MODE, KIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_mlp_train<NOUT, MODE><<<grid, kTile, smem, s>>>(a, r, b, part, loss_part);
+    k_mlp_train<NOUT, MODE, KIN><<<grid, kTile, smem, s>>>(a, r, b, part, loss_part);
     return cudaGetLastError();
+}
+
+// The hash grid's gradient: every training slot adds its grid-feature gradient (from the
+// StatNet pass) to the 8 corner entries of its position's cell on every level.
+__global__ void k_grid_scatter(TrainArgs a, RecordView r, TrainBatch b, float* grad) {
+    for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < b.batch;
+         slot += (long long)gridDim.x * blockDim.x) {
+        float dx[16];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            dx[c] = a.dx[slot * 16 + c];
+            any = any || dx[c] != 0.0f;
+        }
+        if (!any) continue;
+        const long long u = batch_vertex(b, slot);
+        int d = 0;
+        while (d + 1 < b.D && b.offset[d + 1] <= u) ++d;
+        const size_t g = (size_t)d * r.C + (u - b.offset[d]);
+        const float4 f0 = r.feat[4 * g];
+        grid_scatter(grad, f0.x, f0.y, f0.z, dx);
+    }
 }
 
 }  // namespace
@@ -632,7 +679,11 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
                              const TrainBatch& b, int grid, float* part, double* loss_part,
                              cudaStream_t s) {
     switch (which) {
-        case kTrainStatNet: return launch_train_t<6, kTrainStatNet>(a, r, b, grid, part, loss_part, s);
+        case kTrainStatNet:
+            if (a.grid)
+                return launch_train_t<6, kTrainStatNet, kStatGridIn>(a, r, b, grid, part,
+                                                                     loss_part, s);
+            return launch_train_t<6, kTrainStatNet>(a, r, b, grid, part, loss_part, s);
         case kTrainRrsWarmup: return launch_train_t<1, kTrainRrsWarmup>(a, r, b, grid, part, loss_part, s);
         default: return launch_train_t<1, kTrainRrsFull>(a, r, b, grid, part, loss_part, s);
     }
@@ -640,10 +691,51 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
 
 cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
                                   const TrainBatch& b, int grid, float* part, double* loss_part,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int n_in) {
+    if (n_in == kStatGridIn)
+        return launch_train_t<6, kTrainGiven, kStatGridIn>(a, r, b, grid, part, loss_part, s);
     if (at_q) return launch_train_t<1, kTrainGivenQ>(a, r, b, grid, part, loss_part, s);
     return n_out == 1 ? launch_train_t<1, kTrainGiven>(a, r, b, grid, part, loss_part, s)
                       : launch_train_t<6, kTrainGiven>(a, r, b, grid, part, loss_part, s);
+}
+
+void launch_grid_scatter(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
+                         float* grad, cudaStream_t s) {
+    k_grid_scatter<<<grid, 256, 0, s>>>(a, r, b, grad);
+}
+
+namespace {
+__global__ void k_statnet_inputs_rows(const float4* feat, const float* rough, long long n,
+                                      const float2* table, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 f0 = feat[4 * i], f1 = feat[4 * i + 1];
+    float x[kStatGridIn];
+    statnet_grid_inputs(table, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, rough[i], x);
+#pragma unroll
+    for (int k = 0; k < kStatGridIn; ++k) out[i * kStatGridIn + k] = x[k];
+}
+
+__global__ void k_grid_backward_rows(const float4* feat, const float* dx, long long n,
+                                     float* grad) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float d[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) d[c] = dx[i * 16 + c];
+    const float4 f0 = feat[4 * i];
+    grid_scatter(grad, f0.x, f0.y, f0.z, d);
+}
+}  // namespace
+
+void launch_statnet_inputs(const float4* feat, const float* rough, long long n,
+                           const float2* table, float* out, cudaStream_t s) {
+    k_statnet_inputs_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, rough, n, table, out);
+}
+
+void launch_grid_backward(const float4* feat, const float* dx, long long n, float* grad,
+                          cudaStream_t s) {
+    k_grid_backward_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, dx, n, grad);
 }
 
 void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream_t s) {

@@ -20,6 +20,7 @@ struct RecordView {
     uint32_t* X;      // children requested
     float4* S;        // suffix sum rgb, pixel bits (reverse pass)
     float4* feat_net; // NRRS inputs of RRSNet (4 float4 per slot) or NULL: RRSNet reads feat
+    float* rough;     // roughness of each network vertex (StatNet's encoded inputs)
     long long C;
 };
 
@@ -65,6 +66,8 @@ struct TrainArgs {
     float eps, g1, g2, g3;
     float scale;          // factor on every sample's gradient (1/N for mean losses)
     const float* gin;     // kTrainGiven: output gradients [n][n_out]
+    const float2* grid;   // StatNet on the encodings of Sec. 4: its hash grid, else NULL
+    float* dx;            // with grid: gradient at the 16 grid features per training slot
 };
 
 int train_tile();
@@ -98,8 +101,19 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
                              cudaStream_t s);
 cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
                                   const TrainBatch& b, int grid, float* part, double* loss_part,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int n_in = 16);
+// StatNet's encoded inputs [n][32] of vertex features [n][16] and roughness [n].
+void launch_statnet_inputs(const float4* feat, const float* rough, long long n,
+                           const float2* table, float* out, cudaStream_t s);
+// Adds to grad the hash-grid gradient of rows with features [n][16] and grid-feature
+// gradients dx [n][16].
+void launch_grid_backward(const float4* feat, const float* dx, long long n, float* grad,
+                          cudaStream_t s);
 void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream_t s);
+// Adds every training slot's grid-feature gradient (TrainArgs::dx) to the hash grid's
+// entries (atomics; the order of the additions varies from run to run).
+void launch_grid_scatter(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
+                         float* grad, cudaStream_t s);
 void launch_reduce_loss(const double* part, int G, double* out, cudaStream_t s);
 void launch_adam(float* P, const float* G, float* m, float* v, int n, int step, float lr,
                  float b1, float b2, float eps, int* bad, cudaStream_t s);

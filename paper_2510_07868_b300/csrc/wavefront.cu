@@ -415,6 +415,7 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
                     f[3] = make_float4((float)depth / (float)Dmax, boxcox(t4.x, rp.boxcox_lambda),
                                        boxcox(t4.y, rp.boxcox_lambda),
                                        boxcox(t4.z, rp.boxcox_lambda));
+                    if (w.rough) w.rough[i] = m.type == 0 ? 1.0f : m.roughness;
                     q = -1.0f;  // filled by the RRSNet kernel
                 }
                 if (KIND < kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {

@@ -77,6 +77,7 @@ struct WorkView {
     float4* sh_o;
     float4* sh_d;
     float4* sh_c;
+    float* rough;      // [C] roughness of each network vertex (training of the grid StatNet)
 };
 
 // Per-frame values read by the kernels from device memory, so that one recorded launch
@@ -141,6 +142,8 @@ struct RenderParams {
     uint32_t* rec_first;  // record mode: first child slot of every parent of this depth
     uint32_t* rec_X;      // record mode: children requested by every parent of this depth
     int nee;              // next-event estimation with MIS at every vertex
+    const float2* stat_grid;  // StatNet's hash grid (StatNet reads the encodings of Sec. 4)
+                              // or NULL (StatNet reads the vertex features)
 };
 
 enum FactorKind : int {
@@ -199,8 +202,8 @@ void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* f
 void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
                         const RenderParams& rp, int depth, int grid, float4* out, cudaStream_t s);
 // ADRRS (NN) factors of the vertices the shade kernel marked (rrsnet_simt.cu).
-void launch_adrrs(const float* stat, const WorkView& w, QueueView cur, const RenderParams& rp,
-                  int depth, int grid, cudaStream_t s);
+void launch_adrrs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
+                  const RenderParams& rp, int depth, int grid, cudaStream_t s);
 // rrsnet_tc.cu: tensor cores; precision 16 = split BF16 operands, 8 = E4M3 operands with
 // per-tensor scales; FP32 accumulation.
 void launch_rrsnet_tc(int precision, int grid, const float* params, const float4* feat,

@@ -26,8 +26,10 @@ MAX_DEPTH = 32
 STAGES = 11
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
                "finalize", "rrsnet", "shade", "reverse", "shadow"]
-NET_RRSNET, NET_RRSNET_TRAIN, NET_STATNET = 0, 1, 2
+NET_RRSNET, NET_RRSNET_TRAIN, NET_STATNET, NET_STATNET_GRID = 0, 1, 2, 3
 STATNET_PARAMS = 2752
+STATNET_GRID_PARAMS = 3264  # StatNet on the encodings (32 inputs)
+GRID_PARAMS = 8 * (1 << 18) * 2
 N_FEATURES = 16
 RRSNET_PARAMS = 2592
 
@@ -37,7 +39,9 @@ EXPORTED = [
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
     "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
-    "nrrs_relmse", "nrrs_error_filter", "nrrs_set_rrsnet_inputs", "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
+    "nrrs_relmse", "nrrs_error_filter", "nrrs_set_rrsnet_inputs", "nrrs_set_statnet_encoding",
+    "nrrs_statnet_grad", "nrrs_statnet_inputs", "nrrs_grid_backward",
+    "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
 ]
@@ -194,6 +198,10 @@ def _load():
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
         "nrrs_error_filter": ([P, P, I32, I32, I32, C.c_float, P, P], I32),
         "nrrs_set_rrsnet_inputs": ([P, I32], I32),
+        "nrrs_set_statnet_encoding": ([P, I32], I32),
+        "nrrs_statnet_grad": ([P, P, P, P, I64, P, P], I32),
+        "nrrs_statnet_inputs": ([P, P, P, I64, P, P], I32),
+        "nrrs_grid_backward": ([P, P, P, I64, P, P], I32),
         "nrrs_rrsnet_forward": ([P, P, I64, P, P], I32),
         "nrrs_rrsnet_backward": ([P, P, P, P, I64, P, P], I32),
         "nrrs_tune_rrsnet": ([P, I32, P, P], I32),
@@ -383,8 +391,11 @@ def nrrs_set_params(scene, which, params, stream=None):
     _check(_lib.nrrs_set_params(scene, which, p.ctypes.data, p.size, _stream(stream)))
 
 
-def nrrs_get_params(scene, which, stream=None):
-    n = STATNET_PARAMS if which == NET_STATNET else RRSNET_PARAMS
+def nrrs_get_params(scene, which, stream=None, n=None):
+    """Weights of network `which`; StatNet on the encodings has STATNET_GRID_PARAMS (pass
+    n), its grid GRID_PARAMS."""
+    if n is None:
+        n = {NET_STATNET: STATNET_PARAMS, NET_STATNET_GRID: GRID_PARAMS}.get(which, RRSNET_PARAMS)
     p = np.zeros(n, dtype=np.float32)
     _check(_lib.nrrs_get_params(scene, which, p.ctypes.data, n, _stream(stream)))
     return p
@@ -483,6 +494,25 @@ def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1,
 
 def nrrs_set_rrsnet_inputs(scene, mode):
     _check(_lib.nrrs_set_rrsnet_inputs(scene, mode))
+
+
+def nrrs_set_statnet_encoding(scene, mode):
+    _check(_lib.nrrs_set_statnet_encoding(scene, mode))
+
+
+def nrrs_statnet_grad(scene, d_params, d_x, d_gout, n, d_grad, stream=None):
+    _check(_lib.nrrs_statnet_grad(scene, _ptr(d_params), _ptr(d_x), _ptr(d_gout), n, _ptr(d_grad),
+                                  _stream(stream)))
+
+
+def nrrs_statnet_inputs(scene, d_feat, d_rough, n, d_x, stream=None):
+    _check(_lib.nrrs_statnet_inputs(scene, _ptr(d_feat), _ptr(d_rough), n, _ptr(d_x),
+                                    _stream(stream)))
+
+
+def nrrs_grid_backward(scene, d_feat, d_dx, n, d_grad, stream=None):
+    _check(_lib.nrrs_grid_backward(scene, _ptr(d_feat), _ptr(d_dx), n, _ptr(d_grad),
+                                   _stream(stream)))
 
 
 def nrrs_error_filter(d_in, d_normals, width, height, radius, power, d_out, stream=None):
@@ -586,6 +616,9 @@ class Scene:
 
     def set_rrsnet_inputs(self, mode):
         nrrs_set_rrsnet_inputs(self.handle, mode)
+
+    def set_statnet_encoding(self, mode):
+        nrrs_set_statnet_encoding(self.handle, mode)
 
     def train_step(self, stream=None, **opts):
         return nrrs_train_step(self.handle, TrainOpts.defaults(**opts), stream)
