@@ -502,11 +502,12 @@ def run_ours(args, rank, world, local_rank):
     eff = None
     if rank == 0 and not args.no_efficiency:
         eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi)
-        def trained_scene(nee, rrsnet_inputs):
+        def trained_scene(nee, rrsnet_inputs, statnet_encoding):
             """A second RRSNet / StatNet pair trained online like the first."""
             sc2 = nrrs.Scene(scene, device=local_rank)
             sc2.set_params(params)
             sc2.set_rrsnet_inputs(rrsnet_inputs)
+            sc2.set_statnet_encoding(statnet_encoding)
             sc2.tune(32)
             t2 = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP,
                                          max_depth=DEPTH, seed_hi=seed_hi, graph=graph, nee=nee)
@@ -520,9 +521,11 @@ def run_ours(args, rank, world, local_rank):
             return sc2
 
         # the same comparison with next-event estimation (on in the paper's experiments,
-        # Sec. 5), and with RRSNet on the paper's NRRS inputs (Sec. 4 "Input Encoding")
-        for key, nee, rin in (("nee", 1, 0), ("nrrs_inputs", 0, 1)):
-            sc2 = trained_scene(nee, rin)
+        # Sec. 5), with RRSNet on the paper's NRRS inputs (Sec. 4 "Input Encoding"), and
+        # with StatNet on the paper's encodings too (hash grid, one-blob)
+        for key, nee, rin, enc in (("nee", 1, 0, 0), ("nrrs_inputs", 0, 1, 0),
+                                   ("nrrs_inputs_grid_statnet", 0, 1, 1)):
+            sc2 = trained_scene(nee, rin, enc)
             eff[key] = efficiency_section(nrrs, sc2, torch, dev, stream, seed_hi, nee=nee)
             sc2.close()
 
