@@ -62,7 +62,7 @@ class RenderArgs(C.Structure):
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
                 ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p),
                 ("stat_params", C.c_void_p), ("nee", C.c_int32), ("rrsnet_inputs", C.c_int32),
-                ("stat_encoding", C.c_int32), ("stat_grid", C.c_void_p)]
+                ("stat_encoding", C.c_int32), ("stat_grid", C.c_void_p), ("rrs_grid", C.c_void_p)]
 
 
 class RenderStats(C.Structure):
@@ -136,6 +136,7 @@ def lib():
         _lib.or_grid_backward.argtypes = [P, P, P]
         _lib.or_one_blob.argtypes = [C.c_double, C.c_int, P]
         _lib.or_statnet_grid_inputs.argtypes = [P, P, P, C.c_double, P]
+        _lib.or_aid_inputs.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, P]
     return _lib
 
 
@@ -269,12 +270,13 @@ def bernstein_exponent(f_rate):
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
            params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None,
-           stat_params=None, nee=0, rrsnet_inputs=0, stat_grid=None):
+           stat_params=None, nee=0, rrsnet_inputs=0, stat_grid=None, rrs_grid=None):
     """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
     nee=1 adds next-event estimation with MIS (power heuristic) at every vertex;
     rrsnet_inputs=1 feeds RRSNet the NRRS inputs built from StatNet (stat_params);
     with stat_grid (the hash-grid table) StatNet reads the encodings of Sec. 4 (32 inputs,
-    stat_params then has 32 inputs) instead of the vertex features.
+    stat_params then has 32 inputs) instead of the vertex features; rrsnet_inputs=2 with
+    rrs_grid is AID-NRRS (RRSNet on 32 encoded inputs, params then has 32 inputs).
     With record=True the stats dict also holds "rec": per depth an array [live, 13] of
     (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
     h = _SceneHolder(scene)
@@ -286,10 +288,11 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     fF = np.ascontiguousarray(forced_F, dtype=np.float32) if forced_F is not None else None
     SP = np.ascontiguousarray(stat_params, dtype=np.float64) if stat_params is not None else None
     SG = np.ascontiguousarray(stat_grid, dtype=np.float64) if stat_grid is not None else None
+    RG = np.ascontiguousarray(rrs_grid, dtype=np.float64) if rrs_grid is not None else None
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
                       0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP), int(nee),
-                      int(rrsnet_inputs), 0 if SG is None else 1, _p(SG))
+                      int(rrsnet_inputs), 0 if SG is None else 1, _p(SG), _p(RG))
     out = np.zeros((height, width, 3))
     st = RenderStats()
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None
@@ -391,6 +394,16 @@ def statnet_grid_inputs(table, p, wo, alpha):
     wo = np.ascontiguousarray(wo, dtype=np.float64)
     x = np.zeros(32)
     lib().or_statnet_grid_inputs(_p(T), _p(p), _p(wo), float(alpha), _p(x))
+    return x
+
+
+def aid_inputs(table, p, wo, t, I, alpha, lam=0.5):
+    T = np.ascontiguousarray(table, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    x = np.zeros(32)
+    lib().or_aid_inputs(_p(T), _p(p), _p(wo), _p(t), float(I), float(alpha), float(lam), _p(x))
     return x
 
 

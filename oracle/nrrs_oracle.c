@@ -19,6 +19,8 @@
  *   or_mlp_backward    the chain rule through the same network
  *   or_render          also ADRRS (NN) factors at NET_MIX depths with gate 3 (Sec. 4
  *                      "Mix-Depth"): lum(t) E[L_o] / I_px from StatNet's predicted mean
+ *   or_render (rrsnet_inputs = 2)  AID-NRRS: RRSNet (32 inputs) on its own hash grid of
+ *                      the position, one-blob w_o and roughness, Box-Cox t and I_px
  *   or_render (rrsnet_inputs = 1)  the NRRS network inputs of Sec. 4 "Input Encoding":
  *                      Box-Cox (lambda 0.5) of StatNet's E[L_o] and E[L_o^2] (per channel,
  *                      clamped at 0), of the throughput t and of the pixel estimate's
@@ -489,6 +491,8 @@ void or_mlpk_forward(const double* P, int n_in, int n_out, const double* x, doub
                      double* pre, double* hid);
 void or_statnet_grid_inputs(const double* table, const double p[3], const double wo[3],
                             double alpha, double x[32]);
+void or_aid_inputs(const double* table, const double p[3], const double wo[3], const double t[3],
+                   double I, double alpha, double lambda, double x[32]);
 
 /* ------------------------------------------------------------------ render */
 
@@ -514,10 +518,12 @@ typedef struct {
     const double* stat_params; /* StatNet weights (ADRRS (NN) depths of NET_MIX) */
     int32_t nee;            /* next-event estimation with MIS (1) or BSDF sampling only (0) */
     int32_t rrsnet_inputs;  /* RRSNet inputs: 0 = the 16 vertex features, 1 = NRRS inputs
-                               (needs stat_params) */
+                               (needs stat_params), 2 = AID-NRRS inputs (needs rrs_grid;
+                               params then has 32 inputs) */
     int32_t stat_encoding;  /* StatNet inputs: 0 = the 13 vertex features (throughput
                                inputs zeroed), 1 = hash grid + one-blob (needs stat_grid) */
     const double* stat_grid;/* StatNet's hash-grid table [8][2^18][2] */
+    const double* rrs_grid; /* RRSNet's hash-grid table (AID-NRRS inputs) */
 } or_render_args;
 
 /* StatNet's six outputs at a vertex whose 16 features are x (position in the scene box,
@@ -676,7 +682,8 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     if (a->mode == OR_MODE_NET_MIX && !a->stat_params)
         for (int32_t d = 1; d <= D; ++d)
             if (((a->gate >> (2 * (d - 1))) & 3u) == OR_GATE_ADRRS) return OR_ERR_ARG;
-    if (a->rrsnet_inputs && !a->stat_params) return OR_ERR_ARG;
+    if (a->rrsnet_inputs == 1 && !a->stat_params) return OR_ERR_ARG;
+    if (a->rrsnet_inputs == 2 && !a->rrs_grid) return OR_ERR_ARG;
     if (a->stat_encoding && !a->stat_grid) return OR_ERR_ARG;
     if (P > cap) return OR_ERR_ARG;
     or_emitters E;
@@ -841,7 +848,20 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 for (int c = 0; c < 3; ++c) x[9 + c] = m->albedo[c];
                 x[12] = (double)depth / (double)D;
                 for (int c = 0; c < 3; ++c) x[13 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
-                if (a->rrsnet_inputs) {
+                if (a->rrsnet_inputs == 2) {
+                    /* AID-NRRS inputs (Sec. 4 "Input Encoding"): RRSNet's own grid of the
+                     * position, one-blob w_o and roughness, Box-Cox t and I_px */
+                    double I = 0.0, x32[32], z;
+                    if (a->pixel_ref) {
+                        const double* r = a->pixel_ref + 3 * (int64_t)p->pixel;
+                        I = (r[0] + r[1] + r[2]) / 3.0;
+                    }
+                    or_aid_inputs(a->rrs_grid, x, x + 3, p->t, I,
+                                  m->type == 0 ? 1.0 : (double)m->roughness, a->boxcox_lambda,
+                                  x32);
+                    or_mlpk_forward(a->params, 32, 1, x32, &z, NULL, NULL);
+                    q = or_softplus_mod(z);
+                } else if (a->rrsnet_inputs) {
                     /* NRRS inputs (Sec. 4 "Input Encoding"): StatNet's statistics at the
                      * vertex (its throughput inputs zeroed, as trained), the throughput,
                      * the pixel estimate's mean (0 before any) and the remapped roughness
@@ -860,7 +880,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                     x[10] = 1.0 - exp(-rough);
                     for (int c = 11; c < OR_NF; ++c) x[c] = 0.0;
                 }
-                q = or_mlp_forward(a->params, x, NULL, NULL, NULL);
+                if (a->rrsnet_inputs != 2) q = or_mlp_forward(a->params, x, NULL, NULL, NULL);
                 if (!(isfinite(q) && q >= 0.0)) {  /* a failing network: the heuristic */
                     q = heur;
                     v->net_fallback = 1;

@@ -21,6 +21,11 @@
  *       with 4 bins of each spherical coordinate of w_o (theta / pi from the z axis and
  *       (phi + pi) / (2 pi)), and of the roughness remapped by 1 - exp(-alpha) with 8
  *       bins.
+ *   or_aid_inputs
+ *       AID-NRRS's 32 RRSNet inputs (Sec. 4 "Input Encoding"): the position and w_o
+ *       encoded as for StatNet (with RRSNet's own grid), Box-Cox (the render's lambda,
+ *       0.5 in the paper) of the throughput per channel and of the pixel estimate's mean
+ *       (clamped at 0), and the remapped roughness one-blob encoded with 4 bins.
  */
 #include <math.h>
 #include <stdint.h>
@@ -108,4 +113,17 @@ void or_statnet_grid_inputs(const double* table, const double p[3], const double
     or_one_blob(theta, 4, x + 16);
     or_one_blob(phi, 4, x + 20);
     or_one_blob(1.0 - exp(-alpha), 8, x + 24);
+}
+
+double or_boxcox(double t, double lambda);  /* nrrs_oracle.c */
+
+void or_aid_inputs(const double* table, const double p[3], const double wo[3], const double t[3],
+                   double I, double alpha, double lambda, double x[32]) {
+    or_grid_encode(table, p, x);
+    double z = wo[2] < -1.0 ? -1.0 : wo[2] > 1.0 ? 1.0 : wo[2];
+    or_one_blob(acos(z) / M_PI, 4, x + 16);
+    or_one_blob((atan2(wo[1], wo[0]) + M_PI) / (2.0 * M_PI), 4, x + 20);
+    for (int c = 0; c < 3; ++c) x[24 + c] = or_boxcox(t[c], lambda);
+    x[27] = or_boxcox(I > 0.0 ? I : 0.0, lambda);
+    or_one_blob(1.0 - exp(-alpha), 4, x + 28);
 }

@@ -104,3 +104,72 @@ def test_nrrs_inputs_need_statnet():
     with pytest.raises(RuntimeError):
         oracle.render(I.box_scene(1), 4, 4, 1, 2, oracle.MODE_NET, params=_selector(1, [0]),
                       rrsnet_inputs=1)
+
+
+# ------------------------------------------------------------------ AID-NRRS inputs
+def _selector32(k):
+    """RRSNet with 32 inputs whose pre-activation is K * x[k] for either sign."""
+    W1 = np.zeros((NH, 32))
+    W2 = np.zeros((NH, NH))
+    W3 = np.zeros((NH, NH))
+    W4 = np.zeros((1, NH))
+    W1[0, k], W1[1, k] = 1.0, -1.0
+    W2[0, 0] = W2[1, 1] = W3[0, 0] = W3[1, 1] = 1.0
+    W4[0, 0], W4[0, 1] = 1.0, -1.0
+    return np.concatenate([W1.ravel(), W2.ravel(), W3.ravel(), W4.ravel()])
+
+
+def test_aid_inputs_layout():
+    tab = np.random.default_rng(11).normal(size=oracle.grid_param_count())
+    p = np.array([0.25, 0.5, 0.75])
+    x = oracle.aid_inputs(tab, p, [0.0, 0.0, 1.0], [1.0, 4.0, 0.25], 4.0, 0.0)
+    np.testing.assert_allclose(x[:16], oracle.grid_encode(tab, p)[0], atol=1e-15)
+    np.testing.assert_allclose(x[16:20], oracle.one_blob(0.0, 4), atol=1e-15)
+    np.testing.assert_allclose(x[20:24], oracle.one_blob(0.5, 4), atol=1e-15)
+    np.testing.assert_allclose(x[24:27], [0.0, 2.0, -1.0], atol=1e-15)  # Box-Cox of t
+    assert x[27] == 2.0  # Box-Cox of I = 4
+    np.testing.assert_allclose(x[28:32], oracle.one_blob(0.0, 4), atol=1e-15)
+    x = oracle.aid_inputs(tab, p, [0.0, 0.0, 1.0], [1.0, 1.0, 1.0], -3.0, 1.0)
+    assert x[27] == -2.0  # a negative estimate counts as 0
+    np.testing.assert_allclose(x[28:32], oracle.one_blob(1 - np.exp(-1.0), 4), atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [16, 20, 24, 25, 26, 27, 28, 29, 30, 31])
+def test_aid_inputs_in_render(k):
+    """The render's AID-NRRS path feeds RRSNet the encoding: at depth 1 (throughput 1)
+    of the Lambertian box each input has a closed form or the oracle's encoding value."""
+    s = I.box_scene(4)
+    tab = np.random.default_rng(12).normal(size=oracle.grid_param_count()) * 0.1
+    ref_value = 2.25
+    W = H = 8
+    ref = np.full((H * W, 3), ref_value)
+    _, st, tr = oracle.render(s, W, H, 2, 2, oracle.MODE_NET, params=_selector32(k),
+                              rrsnet_inputs=2, rrs_grid=tab, pixel_ref=ref, record=True,
+                              trace=True)
+    rec = st["rec"][0]
+    went_on = rec[:, 9] > 0
+    q = rec[went_on, 9]
+    assert q.size > 50
+    if 24 <= k <= 26:
+        f = np.zeros_like(q)
+    elif k == 27:
+        f = np.full_like(q, _boxcox(ref_value))
+    elif k >= 28:
+        f = np.full_like(q, oracle.one_blob(1 - np.exp(-1.0), 4)[k - 28])
+    else:  # one-blob of w_o: in (0, 1], recomputed from each camera ray
+        pix = tr[0][went_on, 0].astype(np.int64)
+        smp = tr[0][went_on, 1]
+        f = np.empty_like(q)
+        for j, (pp, ss) in enumerate(zip(pix, smp)):
+            w = oracle.philox([pp, ss, 0, 0], [1, 0])
+            _, d = oracle.camera_ray(s, W, H, int(pp % W), int(pp // W), (w[0] >> 8) / 2 ** 24,
+                                     (w[1] >> 8) / 2 ** 24)
+            x = oracle.aid_inputs(tab, [0.5, 0.5, 0.5], -d, [1.0, 1.0, 1.0], 0.0, 1.0)
+            f[j] = x[k]
+    np.testing.assert_allclose(q, _softplus_mod(K * f), rtol=1e-6)
+
+
+def test_aid_inputs_need_grid():
+    with pytest.raises(RuntimeError):
+        oracle.render(I.box_scene(1), 4, 4, 1, 2, oracle.MODE_NET, params=_selector32(0),
+                      rrsnet_inputs=2)
