@@ -87,6 +87,9 @@ typedef enum nrrs_rrs_mode {
                                    (32 inputs with the encodings of nrrs_set_statnet_encoding:
                                    NRRS_STATNET_GRID_PARAMS weights)                       */
 #define NRRS_NET_STATNET_GRID 3 /* StatNet's hash grid, [8][2^18][2] (NRRS_GRID_PARAMS)   */
+#define NRRS_NET_RRSNET_GRID 4  /* AID-NRRS: RRSNet's hash grid renders use (EMA)          */
+#define NRRS_NET_RRSNET_GRID_TRAIN 5 /* AID-NRRS: RRSNet's hash grid Adam updates         */
+#define NRRS_AID_RRSNET_PARAMS 3104 /* RRSNet on the AID-NRRS inputs: 32x32 + 32x32x2 + 32 */
 
 /* Material record, 40 bytes.  type 0 = Lambertian (albedo), 1 = GGX + Lambert
  * "plastic" mixture (roughness is the GGX alpha, F0 the Schlick reflectance at normal
@@ -258,7 +261,8 @@ NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
 NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
 
 /* Chooses what RRSNet reads at the network depths of later renders and training steps
- * (the weights are the caller's to match):
+ * (the weights are the caller's to match; a change between modes 0/1 and 2 changes the
+ * network's shape and starts RRSNet afresh):
  *   0 (default) the 16 vertex features: position in the scene box, -w_o, the shading
  *     normal, albedo, d / D and Box-Cox(t) per channel;
  *   1 the NRRS inputs of Sec. 4 "Input Encoding": StatNet runs first at every network
@@ -266,8 +270,14 @@ NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
  *     Box-Cox(max(E[L_o], 0)) and Box-Cox(max(E[L_o^2], 0)) per channel, Box-Cox(t) per
  *     channel, Box-Cox(mean of the pixel estimate; 0 before any), 1 - exp(-roughness)
  *     (Lambertian surfaces count as roughness 1) and five zeros, Box-Cox with the render's
- *     boxcox_lambda.  StatNet's weights are the scene's (nrrs_set_params / training).
- * Errors: INVALID_ARG (NULL scene, mode not 0 or 1). */
+ *     boxcox_lambda.  StatNet's weights are the scene's (nrrs_set_params / training);
+ *   2 the AID-NRRS inputs of Sec. 4 "Input Encoding": RRSNet (32 -> 32 -> 32 -> 32 -> 1,
+ *     NRRS_AID_RRSNET_PARAMS weights, FP32 only) reads its own trainable hash grid of the
+ *     position (as nrrs_set_statnet_encoding describes; NRRS_NET_RRSNET_GRID for renders,
+ *     the EMA of NRRS_NET_RRSNET_GRID_TRAIN), one-blob (4 bins) of w_o's spherical
+ *     coordinates, Box-Cox(t) per channel, Box-Cox(max(mean I_px, 0)) and one-blob (4
+ *     bins) of 1 - exp(-roughness); nrrs_query_factors refuses this mode.
+ * Errors: INVALID_ARG (NULL scene, mode not 0, 1 or 2); OOM; CUDA. */
 NRRS_API nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode);
 
 /* Chooses StatNet's inputs (everywhere StatNet runs: training, ADRRS (NN), NRRS inputs):

@@ -173,6 +173,9 @@ struct TrainState {
     float *grid = nullptr, *grid_m = nullptr, *grid_v = nullptr, *grid_good = nullptr;
     float *grid_grad = nullptr, *dx = nullptr;
     long long dx_cap = 0;
+    // AID-NRRS: RRSNet's hash grid, trained (raw) and its EMA for rendering
+    float *rgrid = nullptr, *rgrid_raw = nullptr, *rgrid_m = nullptr, *rgrid_v = nullptr;
+    float *rgrid_good = nullptr, *rgrid_grad = nullptr;
     int stat_n() const {
         return (stat_enc ? kNH * kStatGridIn : kNH * kNF) + 2 * kNH * kNH + kStatOut * kNH;
     }
@@ -196,9 +199,11 @@ struct TrainState {
         release_record();
         float* fs[] = {rrs_raw, rrs_m, rrs_v, rrs_good, stat, stat_m, stat_v, stat_good,
                        grad_rrs, grad_stat, part, Fd, Fnd,
-                       grid, grid_m, grid_v, grid_good, grid_grad, dx};
+                       grid, grid_m, grid_v, grid_good, grid_grad, dx,
+                       rgrid, rgrid_raw, rgrid_m, rgrid_v, rgrid_good, rgrid_grad};
         for (float* f : fs) cudaFree(f);
         grid = grid_m = grid_v = grid_good = grid_grad = dx = nullptr;
+        rgrid = rgrid_raw = rgrid_m = rgrid_v = rgrid_good = rgrid_grad = nullptr;
         dx_cap = 0;
         cudaFree(loss_part);
         cudaFree(scal);
@@ -264,6 +269,12 @@ struct nrrs_scene {
 };
 
 namespace {
+
+// RRSNet's weight count: 16 inputs, or 32 with the AID-NRRS inputs.
+int rrs_n(const nrrs_scene* sc) { return sc->rrsnet_inputs == 2 ? kAidParams : kNParams; }
+// RRSNet's weights (and, with the AID-NRRS inputs, its hash grid) afresh for the current
+// input mode (below).
+nrrs_status init_rrsnet_shape(nrrs_scene* sc);
 
 nrrs_status alloc_nee(Workspace& w) {
     if (w.has_nee) return NRRS_OK;
@@ -452,14 +463,14 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
     if ((e = dalloc(&s->nodes, bvh.nodes.size() * 4)) != cudaSuccess) return bail(e, "alloc nodes");
     if ((e = dalloc(&s->tris, (size_t)bvh.n_ref * 3)) != cudaSuccess) return bail(e, "alloc tris");
     if ((e = dalloc(&s->mats, n_mat)) != cudaSuccess) return bail(e, "alloc mats");
-    if ((e = dalloc(&s->params, kNParams)) != cudaSuccess) return bail(e, "alloc params");
+    if ((e = dalloc(&s->params, kRrsParamsMax)) != cudaSuccess) return bail(e, "alloc params");
     if ((e = cudaMemcpy(s->nodes, bvh.nodes.data(), bvh.nodes.size() * 64, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy nodes");
     if ((e = cudaMemcpy(s->tris, bvh.tris.data(), (size_t)bvh.n_ref * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy tris");
     if ((e = cudaMemcpy(s->mats, mats, sizeof(nrrs_material) * n_mat, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "copy mats");
-    if ((e = cudaMemset(s->params, 0, kNParams * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
+    if ((e = cudaMemset(s->params, 0, kRrsParamsMax * sizeof(float))) != cudaSuccess) return bail(e, "zero params");
     if (!em.cdf.empty()) {
         if ((e = dalloc(&s->emit, em.tri.size())) != cudaSuccess) return bail(e, "alloc emitters");
         if ((e = dalloc(&s->emit_cdf, em.cdf.size())) != cudaSuccess) return bail(e, "alloc emitter cdf");
@@ -561,14 +572,17 @@ nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
 }
 
 nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode) {
-    if (!scene || (mode != 0 && mode != 1)) return fail(NRRS_ERR_INVALID_ARG, "bad RRSNet input mode");
-    if (mode != scene->rrsnet_inputs) {
-        DeviceGuard g(scene->device);
-        // recorded NRRS inputs of an earlier mode must not feed training
-        cudaFree(scene->train.rec.feat_net);
-        scene->train.rec.feat_net = nullptr;
-    }
+    if (!scene || mode < 0 || mode > 2) return fail(NRRS_ERR_INVALID_ARG, "bad RRSNet input mode");
+    if (mode == scene->rrsnet_inputs) return NRRS_OK;
+    DeviceGuard g(scene->device);
+    // recorded inputs of an earlier mode must not feed training
+    cudaFree(scene->train.rec.feat_net);
+    scene->train.rec.feat_net = nullptr;
+    cudaFree(scene->train.rec.rough);
+    scene->train.rec.rough = nullptr;
+    const bool reshape = (mode == 2) != (scene->rrsnet_inputs == 2);
     scene->rrsnet_inputs = mode;
+    if (reshape) return init_rrsnet_shape(scene);  // 16 <-> 32 inputs: weights afresh
     return NRRS_OK;
 }
 
@@ -580,19 +594,21 @@ nrrs_status nrrs_scene_info(const nrrs_scene* scene, int64_t* n_nodes, int64_t* 
 }
 
 nrrs_status nrrs_set_rrsnet_params(nrrs_scene* scene, const float* params, int32_t n, void* stream) {
-    if (!scene || !params || n != kNParams) return fail(NRRS_ERR_INVALID_ARG, "need 2592 host floats");
+    if (!scene || !params || n != rrs_n(scene))
+        return fail(NRRS_ERR_INVALID_ARG, "need 2592 host floats (3104 with AID-NRRS inputs)");
     DeviceGuard g(scene->device);
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(scene->params, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(scene->params, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return NRRS_OK;
 }
 
 nrrs_status nrrs_get_rrsnet_params(nrrs_scene* scene, float* params, int32_t n, void* stream) {
-    if (!scene || !params || n != kNParams) return fail(NRRS_ERR_INVALID_ARG, "need 2592 host floats");
+    if (!scene || !params || n != rrs_n(scene))
+        return fail(NRRS_ERR_INVALID_ARG, "need 2592 host floats (3104 with AID-NRRS inputs)");
     DeviceGuard g(scene->device);
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(params, scene->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(params, scene->params, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return NRRS_OK;
 }
@@ -623,6 +639,8 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
     if (o.precision != 32 && o.precision != 16 && o.precision != 8)
         return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16 and 8");
     if (o.nee != 0 && o.nee != 1) return fail(NRRS_ERR_INVALID_ARG, "nee must be 0 or 1");
+    if (scene->rrsnet_inputs == 2 && o.precision != 32)
+        return fail(NRRS_ERR_UNSUPPORTED, "AID-NRRS inputs run in FP32 (precision 32)");
     const long long C = (long long)width * height * spp * o.cap_factor;
     if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
     return NRRS_OK;
@@ -634,7 +652,8 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     if (t.rec_C >= C && t.rec_D >= D && t.npix >= npix) {
         if (sc->rrsnet_inputs && !t.rec.feat_net)
             CK(dalloc(&t.rec.feat_net, (size_t)t.rec_C * t.rec_D * 4));
-        if (t.stat_enc && !t.rec.rough) CK(dalloc(&t.rec.rough, (size_t)t.rec_C * t.rec_D));
+        if ((t.stat_enc || sc->rrsnet_inputs == 2) && !t.rec.rough)
+            CK(dalloc(&t.rec.rough, (size_t)t.rec_C * t.rec_D));
         return NRRS_OK;
     }
     t.release_record();
@@ -656,7 +675,7 @@ nrrs_status ensure_record(nrrs_scene* sc, long long C, int D, long long npix) {
     CK(dalloc(&t.k, npix));
     CK(dalloc(&t.rgb, npix * 3));
     if (sc->rrsnet_inputs) CK(dalloc(&t.rec.feat_net, n * 4));
-    if (t.stat_enc) CK(dalloc(&t.rec.rough, n));
+    if (t.stat_enc || sc->rrsnet_inputs == 2) CK(dalloc(&t.rec.rough, n));
     t.rec.C = C;
     t.rec_C = C;
     t.rec_D = D;
@@ -748,7 +767,12 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         if (kind_of(d) == kFactorAdrrs) uses_adrrs = true;
     }
     // RRSNet fed the NRRS inputs needs StatNet at its depths
-    const bool nrrs_inputs = scene->rrsnet_inputs != 0 && uses_net;
+    const bool nrrs_inputs = scene->rrsnet_inputs == 1 && uses_net;
+    const bool aid_inputs = scene->rrsnet_inputs == 2 && uses_net;
+    if (aid_inputs) {  // RRSNet's hash grid lives with the training state
+        nrrs_status trc = ensure_train_nets(scene, s);
+        if (trc != NRRS_OK) return trc;
+    }
     if (uses_adrrs || nrrs_inputs) {  // StatNet's weights (trained by nrrs_train_step)
         nrrs_status trc = ensure_train_nets(scene, s);
         if (trc != NRRS_OK) return trc;
@@ -882,7 +906,12 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             if (nee)  // shadow rays: unoccluded contributions join the deposits
                 TIMED(NRRS_STAGE_SHADOW,
                       launch_shadow(scene->view, w, d, scene->grid_trace, r.jobs, s));
-            if (kind == kFactorNet) {
+            if (kind == kFactorNet && aid_inputs) {  // AID-NRRS: RRSNet on its grid, FP32
+                TIMED(NRRS_STAGE_RRSNET,
+                      launch_aid_rrsnet(r.params, reinterpret_cast<const float2*>(scene->train.rgrid),
+                                        scene->view, w, q[cur], r, d, scene->n_sm * 4, s));
+                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
+            } else if (kind == kFactorNet) {
                 if (nrrs_inputs)  // StatNet, then the NRRS inputs of RRSNet
                     TIMED(NRRS_STAGE_RRSNET,
                           launch_nrrs_inputs(scene->train.stat, scene->view, w, q[cur], r, d,
@@ -956,7 +985,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)ws.qpdf[0], (uint64_t)(uintptr_t)ws.feat_net,
                                (uint64_t)(uintptr_t)(rec ? rec->feat_net : nullptr),
                                (uint64_t)(uintptr_t)rp.stat_grid,
-                               (uint64_t)(uintptr_t)(rec ? rec->rough : nullptr)};
+                               (uint64_t)(uintptr_t)(rec ? rec->rough : nullptr),
+                               (uint64_t)scene->rrsnet_inputs,
+                               (uint64_t)(uintptr_t)scene->train.rgrid};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -1257,6 +1288,8 @@ nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64
         return fail(NRRS_ERR_INVALID_ARG, "bad query arguments");
     if (precision != 32 && precision != 16 && precision != 8)
         return fail(NRRS_ERR_UNSUPPORTED, "precision must be 32, 16 or 8");
+    if (scene->rrsnet_inputs == 2)
+        return fail(NRRS_ERR_UNSUPPORTED, "the AID-NRRS network encodes its inputs inside the render");
     if (n == 0) return NRRS_OK;
     if ((reinterpret_cast<uintptr_t>(d_features) & 15u) != 0)
         return fail(NRRS_ERR_INVALID_ARG, "d_features must be 16-byte aligned");
@@ -1373,15 +1406,15 @@ constexpr int kStatParamsMax = kNH * kStatGridIn + 2 * kNH * kNH + kStatOut * kN
 nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     TrainState& t = sc->train;
     if (t.nets) return NRRS_OK;
-    CK(dalloc(&t.rrs_raw, kNParams));
-    CK(dalloc(&t.rrs_m, kNParams));
-    CK(dalloc(&t.rrs_v, kNParams));
-    CK(dalloc(&t.rrs_good, kNParams));
+    CK(dalloc(&t.rrs_raw, kRrsParamsMax));
+    CK(dalloc(&t.rrs_m, kRrsParamsMax));
+    CK(dalloc(&t.rrs_v, kRrsParamsMax));
+    CK(dalloc(&t.rrs_good, kRrsParamsMax));
     CK(dalloc(&t.stat, kStatParamsMax));
     CK(dalloc(&t.stat_m, kStatParamsMax));
     CK(dalloc(&t.stat_v, kStatParamsMax));
     CK(dalloc(&t.stat_good, kStatParamsMax));
-    CK(dalloc(&t.grad_rrs, kNParams));
+    CK(dalloc(&t.grad_rrs, kRrsParamsMax));
     CK(dalloc(&t.grad_stat, kStatParamsMax));
     t.part_blocks = sc->n_sm * 3;
     CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParamsMax));
@@ -1390,13 +1423,55 @@ nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     CK(dalloc(&t.Fd, kMaxDepth));
     CK(dalloc(&t.Fnd, kMaxDepth));
     CK(dalloc(&t.bad, 1));
-    CK(cudaMemcpyAsync(t.rrs_raw, sc->params, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(t.rrs_good, sc->params, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
-    CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
+    const int nr = rrs_n(sc);
+    CK(cudaMemcpyAsync(t.rrs_raw, sc->params, sizeof(float) * nr, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t.rrs_good, sc->params, sizeof(float) * nr, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * nr, s));
+    CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * nr, s));
     nrrs_status rc = init_statnet(sc, s);
     if (rc != NRRS_OK) return rc;
     t.nets = true;
+    return NRRS_OK;
+}
+
+nrrs_status init_rrsnet_shape(nrrs_scene* sc) {
+    nrrs_status rc = ensure_train_nets(sc, nullptr);
+    if (rc != NRRS_OK) return rc;
+    TrainState& t = sc->train;
+    const int nr = rrs_n(sc);
+    std::vector<float> w(nr, 0.0f);
+    if (sc->rrsnet_inputs == 2) {
+        // Xavier-uniform start of the 32-input network (fixed stream), grid entries +-1e-4
+        const int shapes[4][2] = {{kNH, kAidIn}, {kNH, kNH}, {kNH, kNH}, {1, kNH}};
+        uint64_t x = 0x3c6ef372fe94f82bull;
+        size_t p = 0;
+        for (auto& sh : shapes) {
+            const double a = std::sqrt(6.0 / (sh[0] + sh[1]));
+            for (int i = 0; i < sh[0] * sh[1]; ++i) {
+                x = x * 6364136223846793005ull + 1442695040888963407ull;
+                w[p++] = (float)(((double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * a);
+            }
+        }
+        if (!t.rgrid) {
+            float** gs[] = {&t.rgrid, &t.rgrid_raw, &t.rgrid_m, &t.rgrid_v, &t.rgrid_good,
+                            &t.rgrid_grad};
+            for (float** gp : gs) CK(dalloc(gp, (size_t)kGridParams));
+        }
+        std::vector<float> g((size_t)kGridParams);
+        for (auto& v : g) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            v = (float)(((double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * 1e-4);
+        }
+        for (float* gd : {t.rgrid, t.rgrid_raw, t.rgrid_good})
+            CK(cudaMemcpy(gd, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemset(t.rgrid_m, 0, sizeof(float) * g.size()));
+        CK(cudaMemset(t.rgrid_v, 0, sizeof(float) * g.size()));
+    }
+    for (float* d : {sc->params, t.rrs_raw, t.rrs_good})
+        CK(cudaMemcpy(d, w.data(), sizeof(float) * nr, cudaMemcpyHostToDevice));
+    CK(cudaMemset(t.rrs_m, 0, sizeof(float) * nr));
+    CK(cudaMemset(t.rrs_v, 0, sizeof(float) * nr));
+    CK(cudaDeviceSynchronize());
     return NRRS_OK;
 }
 
@@ -1425,13 +1500,23 @@ nrrs_status nrrs_set_params(nrrs_scene* scene, int32_t which, const float* param
     if (rc != NRRS_OK) return rc;
     TrainState& t = scene->train;
     const long long want = which == NRRS_NET_STATNET ? t.stat_n()
-                           : which == NRRS_NET_STATNET_GRID ? kGridParams : kNParams;
-    if (which < 0 || which > 3 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+                           : which == NRRS_NET_STATNET_GRID || which >= NRRS_NET_RRSNET_GRID
+                               ? kGridParams
+                               : rrs_n(scene);
+    if (which < 0 || which > 5 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
     if (which == NRRS_NET_STATNET_GRID && !t.stat_enc)
         return fail(NRRS_ERR_UNSUPPORTED, "StatNet has no hash grid (nrrs_set_statnet_encoding)");
+    if (which >= NRRS_NET_RRSNET_GRID && scene->rrsnet_inputs != 2)
+        return fail(NRRS_ERR_UNSUPPORTED, "RRSNet has no hash grid (nrrs_set_rrsnet_inputs(2))");
     float* dst = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw
-                 : which == NRRS_NET_STATNET ? t.stat : t.grid;
+                 : which == NRRS_NET_STATNET ? t.stat : which == NRRS_NET_STATNET_GRID ? t.grid
+                 : which == NRRS_NET_RRSNET_GRID ? t.rgrid : t.rgrid_raw;
     CK(cudaMemcpyAsync(dst, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    if (which == NRRS_NET_RRSNET_GRID_TRAIN) {
+        CK(cudaMemcpyAsync(t.rgrid_good, params, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(t.rgrid_m, 0, sizeof(float) * n, s));
+        CK(cudaMemsetAsync(t.rgrid_v, 0, sizeof(float) * n, s));
+    }
     if (which == NRRS_NET_STATNET || which == NRRS_NET_STATNET_GRID) {
         float* good = which == NRRS_NET_STATNET ? t.stat_good : t.grid_good;
         float* m = which == NRRS_NET_STATNET ? t.stat_m : t.grid_m;
@@ -1468,12 +1553,17 @@ nrrs_status nrrs_get_params(nrrs_scene* scene, int32_t which, float* params, int
     if (rc != NRRS_OK) return rc;
     TrainState& t = scene->train;
     const long long want = which == NRRS_NET_STATNET ? t.stat_n()
-                           : which == NRRS_NET_STATNET_GRID ? kGridParams : kNParams;
-    if (which < 0 || which > 3 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
+                           : which == NRRS_NET_STATNET_GRID || which >= NRRS_NET_RRSNET_GRID
+                               ? kGridParams
+                               : rrs_n(scene);
+    if (which < 0 || which > 5 || n != want) return fail(NRRS_ERR_INVALID_ARG, "bad network or size");
     if (which == NRRS_NET_STATNET_GRID && !t.stat_enc)
         return fail(NRRS_ERR_UNSUPPORTED, "StatNet has no hash grid (nrrs_set_statnet_encoding)");
+    if (which >= NRRS_NET_RRSNET_GRID && scene->rrsnet_inputs != 2)
+        return fail(NRRS_ERR_UNSUPPORTED, "RRSNet has no hash grid (nrrs_set_rrsnet_inputs(2))");
     const float* src = which == NRRS_NET_RRSNET ? scene->params : which == NRRS_NET_RRSNET_TRAIN ? t.rrs_raw
-                       : which == NRRS_NET_STATNET ? t.stat : t.grid;
+                       : which == NRRS_NET_STATNET ? t.stat : which == NRRS_NET_STATNET_GRID ? t.grid
+                       : which == NRRS_NET_RRSNET_GRID ? t.rgrid : t.rgrid_raw;
     CK(cudaMemcpyAsync(params, src, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return NRRS_OK;
@@ -1769,7 +1859,9 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     a.params = t.stat;
     a.scale = N > 0 ? (float)(1.0 / N) : 0.0f;
     const int stat_n = t.stat_n();
-    if (t.stat_enc) {  // StatNet on the encodings: its hash grid and the feature gradients
+    const int rrs_np = rrs_n(scene);
+    const bool aid = scene->rrsnet_inputs == 2;
+    if (t.stat_enc || aid) {  // a hash grid trains: gradients at its features per slot
         if (t.dx_cap < b.batch) {
             cudaFree(t.dx);
             t.dx = nullptr;
@@ -1777,9 +1869,12 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
             CK(dalloc(&t.dx, (size_t)b.batch * 16));
             t.dx_cap = b.batch;
         }
+    }
+    if (t.stat_enc) {  // StatNet on the encodings: its hash grid
         a.grid = reinterpret_cast<const float2*>(t.grid);
         a.dx = t.dx;
     }
+    a.lambda = 0.5f;  // the training frame's Box-Cox lambda (render default)
     CK(launch_mlp_train(kTrainStatNet, a, t.rec, b, t.part_blocks, t.part, t.loss_part, s));
     launch_reduce_grad(t.part, t.part_blocks, stat_n, t.grad_stat, s);
     launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 1, s);
@@ -1792,10 +1887,18 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     const bool warm = t.step < o.warmup_steps;
     a.params = t.rrs_raw;
     a.scale = warm ? (N > 0 ? (float)(1.0 / N) : 0.0f) : 1.0f;
+    if (aid) {  // AID-NRRS: RRSNet on its own hash grid
+        a.grid = reinterpret_cast<const float2*>(t.rgrid_raw);
+        a.dx = t.dx;
+    }
     CK(launch_mlp_train(warm ? kTrainRrsWarmup : kTrainRrsFull, a, t.rec, b, t.part_blocks, t.part,
                         t.loss_part, s));
-    launch_reduce_grad(t.part, t.part_blocks, kNParams, t.grad_rrs, s);
+    launch_reduce_grad(t.part, t.part_blocks, rrs_np, t.grad_rrs, s);
     launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 2, s);
+    if (aid) {
+        CK(cudaMemsetAsync(t.rgrid_grad, 0, sizeof(float) * (size_t)kGridParams, s));
+        launch_grid_scatter(a, t.rec, b, scene->n_sm * 8, t.rgrid_grad, s);
+    }
 
     // 4. Adam for both networks (Sec. 4 "Training": lr 0.005 StatNet, 0.0003 RRSNet)
     CK(cudaMemsetAsync(t.bad, 0, sizeof(int), s));
@@ -1805,8 +1908,11 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     if (t.stat_enc)  // the grid's entries take tiny gradients: Instant-NGP's epsilon 1e-15
         launch_adam(t.grid, t.grid_grad, t.grid_m, t.grid_v, (int)kGridParams, step,
                     o.lr_statnet, 0.9f, 0.999f, 1e-15f, t.bad, s);
-    launch_adam(t.rrs_raw, t.grad_rrs, t.rrs_m, t.rrs_v, kNParams, step, o.lr_rrsnet, 0.9f, 0.999f,
+    launch_adam(t.rrs_raw, t.grad_rrs, t.rrs_m, t.rrs_v, rrs_np, step, o.lr_rrsnet, 0.9f, 0.999f,
                 1e-8f, t.bad, s);
+    if (aid)
+        launch_adam(t.rgrid_raw, t.rgrid_grad, t.rgrid_m, t.rgrid_v, (int)kGridParams, step,
+                    o.lr_rrsnet, 0.9f, 0.999f, 1e-15f, t.bad, s);
     int bad = 0;
     double losses[2];
     CK(cudaMemcpyAsync(&bad, t.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1829,10 +1935,16 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     }
     if (fallback) {  // restore the last good weights and forget the moments
         scene->heur_next = true;
-        CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.rrs_raw, t.rrs_good, sizeof(float) * rrs_np, cudaMemcpyDeviceToDevice, s));
+        if (aid) {
+            CK(cudaMemcpyAsync(t.rgrid_raw, t.rgrid_good, sizeof(float) * (size_t)kGridParams,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(t.rgrid_m, 0, sizeof(float) * (size_t)kGridParams, s));
+            CK(cudaMemsetAsync(t.rgrid_v, 0, sizeof(float) * (size_t)kGridParams, s));
+        }
         CK(cudaMemcpyAsync(t.stat, t.stat_good, sizeof(float) * stat_n, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * kNParams, s));
-        CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * kNParams, s));
+        CK(cudaMemsetAsync(t.rrs_m, 0, sizeof(float) * rrs_np, s));
+        CK(cudaMemsetAsync(t.rrs_v, 0, sizeof(float) * rrs_np, s));
         CK(cudaMemsetAsync(t.stat_m, 0, sizeof(float) * stat_n, s));
         CK(cudaMemsetAsync(t.stat_v, 0, sizeof(float) * stat_n, s));
         if (t.stat_enc) {
@@ -1845,7 +1957,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
             t.loss_ema = t.loss_min;
         }
     } else {
-        CK(cudaMemcpyAsync(t.rrs_good, t.rrs_raw, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(t.rrs_good, t.rrs_raw, sizeof(float) * rrs_np, cudaMemcpyDeviceToDevice, s));
+        if (aid)
+            CK(cudaMemcpyAsync(t.rgrid_good, t.rgrid_raw, sizeof(float) * (size_t)kGridParams,
+                               cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(t.stat_good, t.stat, sizeof(float) * stat_n, cudaMemcpyDeviceToDevice, s));
         if (t.stat_enc)
             CK(cudaMemcpyAsync(t.grid_good, t.grid, sizeof(float) * (size_t)kGridParams,
@@ -1853,7 +1968,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         // inference weights: EMA of the trained weights (Sec. 4 "Training", as in NRC), with
         // the usual warm start decay_t = min(decay, (1 + t) / (10 + t))
         const float warm_decay = (float)(1.0 + (double)t.step) / (float)(10.0 + (double)t.step);
-        launch_ema(scene->params, t.rrs_raw, kNParams, std::min(o.ema_decay, warm_decay), s);
+        launch_ema(scene->params, t.rrs_raw, rrs_np, std::min(o.ema_decay, warm_decay), s);
+        if (aid)  // the rendering grid is the EMA of the trained one, as the weights are
+            launch_ema(t.rgrid, t.rgrid_raw, (int)kGridParams, std::min(o.ema_decay, warm_decay),
+                       s);
         t.step++;
     }
     CK(cudaGetLastError());
@@ -1873,7 +1991,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         // reference fold, sample counts, mean, loss terms; 2 x (train, reduce grad,
         // reduce loss); 2 Adam; EMA
         out->kernel_launches = (int64_t)rs.kernel_launches + 2 + t.filter_launches +
-                               (t.stat_enc ? 2 : 0) +
+                               (t.stat_enc ? 2 : 0) + (aid ? 3 : 0) +
                                (o.d_pixel_ref ? 0 : 1) + 3 + 6 + 2 + (fallback ? 0 : 1);
     }
     return NRRS_OK;

@@ -11,6 +11,9 @@ constexpr int kMaxDepth = 32;
 constexpr int kNF = 16;        // RRSNet input features
 constexpr int kNH = 32;        // RRSNet hidden width (Sec. 4 "Network Architecture")
 constexpr int kNParams = kNH * kNF + 2 * kNH * kNH + kNH;  // 2592
+constexpr int kAidIn = 32;                                    // AID-NRRS inputs of RRSNet
+constexpr int kAidParams = kNH * kAidIn + 2 * kNH * kNH + kNH;  // 3104
+constexpr int kRrsParamsMax = kAidParams;
 constexpr float kLeak = 0.01f; // Leaky ReLU slope
 // Marks a vertex whose RRSNet factor came out non-finite during a render; the sum of q
 // that follows replaces it with the throughput heuristic's factor.

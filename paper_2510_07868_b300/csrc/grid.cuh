@@ -108,4 +108,29 @@ __device__ __forceinline__ void statnet_grid_inputs(const float2* __restrict__ t
     one_blob<8>(1.0f - expf(-alpha), x + 24);
 }
 
+__device__ __forceinline__ float boxcox_l(float x, float lambda) {
+    if (lambda == 0.5f) return 2.0f * (sqrtf(x) - 1.0f);
+    if (lambda == 0.0f) return logf(x);
+    return (powf(x, lambda) - 1.0f) / lambda;
+}
+
+// AID-NRRS's 32 RRSNet inputs (Sec. 4 "Input Encoding"): RRSNet's own grid of the
+// position (16), one-blob w_o as for StatNet (8), Box-Cox of the throughput (3) and of the
+// pixel estimate's mean clamped at 0 (1), one-blob(1 - exp(-alpha), 4).
+__device__ __forceinline__ void aid_inputs(const float2* __restrict__ table, float px, float py,
+                                           float pz, float wx, float wy, float wz, float tx,
+                                           float ty, float tz, float I, float alpha,
+                                           float lambda, float* x) {
+    grid_encode(table, px, py, pz, x);
+    const float theta = acosf(fminf(fmaxf(wz, -1.0f), 1.0f)) * 0.318309886183791f;
+    const float phi = (atan2f(wy, wx) + 3.141592653589793f) * 0.159154943091895f;
+    one_blob<4>(theta, x + 16);
+    one_blob<4>(phi, x + 20);
+    x[24] = boxcox_l(tx, lambda);
+    x[25] = boxcox_l(ty, lambda);
+    x[26] = boxcox_l(tz, lambda);
+    x[27] = boxcox_l(fmaxf(I, 0.0f), lambda);
+    one_blob<4>(1.0f - expf(-alpha), x + 28);
+}
+
 }  // namespace nrrs

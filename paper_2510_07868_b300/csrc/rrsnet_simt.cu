@@ -316,7 +316,68 @@ k_nrrs_inputs(const float* __restrict__ stat, SceneView sc, const float4* __rest
     }
 }
 
+// AID-NRRS (Sec. 4 "Input Encoding"): RRSNet (32 -> 32 -> 32 -> 32 -> 1, FP32) on its own
+// hash grid of the position, one-blob w_o and roughness, Box-Cox throughput and pixel
+// estimate, for every row the render marked (q < 0); output through Eq. rrsnet_activation,
+// a non-finite factor marked for the heuristic stand-in (kQRepair).
+__global__ void __launch_bounds__(kThreads, 2)
+k_aid_rrsnet(const float* __restrict__ params, const float2* __restrict__ rgrid, SceneView sc,
+             const float4* __restrict__ feat, const float4* t, const float4* dep, const float2* hit,
+             const long long* n_ptr, float* q, RenderParams rp, DevStats* st) {
+    __shared__ __align__(16) float sW[kAidParams];
+    const long long n = *n_ptr;
+    if ((long long)blockIdx.x * blockDim.x >= n) return;
+    for (int i = threadIdx.x; i < kAidParams / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(sW)[i] = __ldg(reinterpret_cast<const float4*>(params) + i);
+    __syncthreads();
+    unsigned int evals = 0, nonfinite = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!(q[i] < 0.0f)) continue;
+        const float4 f0 = feat[4 * i], f1 = feat[4 * i + 1], t4 = t[i];
+        float I = 0.0f;
+        if (rp.ref) {
+            const float* rr = rp.ref + 3 * (size_t)__float_as_uint(dep[i].w);
+            I = (rr[0] + rr[1] + rr[2]) / 3.0f;
+        }
+        float x[1][kAidIn];
+        aid_inputs(rgrid, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, t4.x, t4.y, t4.z, I,
+                   hit_roughness(sc, hit, i), rp.boxcox_lambda, x[0]);
+        float h[1][kNH], g[1][kNH];
+        dense<1, kAidIn>(sW, x, h);
+        dense<1, kNH>(sW + kNH * kAidIn, h, g);
+        dense<1, kNH>(sW + kNH * kAidIn + kNH * kNH, g, h);
+        const float* W4 = sW + kNH * kAidIn + 2 * kNH * kNH;
+        float z = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kNH; ++k) z = fmaf(W4[k], h[0][k], z);
+        float v = softplus_mod(z);
+        ++evals;
+        if (!(v >= 0.0f && v <= FLT_MAX)) {
+            v = kQRepair;
+            ++nonfinite;
+        }
+        q[i] = v;
+    }
+    evals = warp_sum(evals);
+    nonfinite = warp_sum(nonfinite);
+    if ((threadIdx.x & 31) == 0) {
+        if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+        if (nonfinite) {
+            atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+            atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+        }
+    }
+}
+
 }  // namespace
+
+void launch_aid_rrsnet(const float* params, const float2* rgrid, const SceneView& sc,
+                       const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                       int grid, cudaStream_t s) {
+    k_aid_rrsnet<<<grid, kThreads, 0, s>>>(params, rgrid, sc, w.feat, cur.t, w.dep, w.hit,
+                                           &w.st->live[depth - 1], w.q, rp, w.st);
+}
 
 void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
                         const RenderParams& rp, int depth, int grid, float4* out, cudaStream_t s) {

@@ -332,10 +332,19 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             i = u - b.offset[d];
             const size_t g = (size_t)d * r.C + i;
             active = ((b.net_mask >> d) & 1u) && r.q[g] > 0.0f;
-            if (active && KIN == kStatGridIn) {
+            if (active && KIN == kStatGridIn && MODE == kTrainStatNet) {
                 // StatNet's encoded inputs: position and w_o from the vertex features
                 const float4 f0 = r.feat[4 * g], f1 = r.feat[4 * g + 1];
                 statnet_grid_inputs(a.grid, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, r.rough[g], x);
+            } else if (active && KIN == kAidIn) {
+                // AID-NRRS inputs of RRSNet: its grid, w_o, throughput, pixel estimate
+                const float4 f0 = r.feat[4 * g], f1 = r.feat[4 * g + 1], tt = r.t[g];
+                const uint32_t pix = fb(r.dep[g].w);
+                const float I = a.ref ? (a.ref[3 * pix] + a.ref[3 * pix + 1] + a.ref[3 * pix + 2]) *
+                                            (1.0f / 3.0f)
+                                      : 0.0f;
+                aid_inputs(a.grid, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, tt.x, tt.y, tt.z, I,
+                           r.rough[g], a.lambda, x);
             } else if (active) {
                 // StatNet learns from the vertex features; RRSNet reads its own inputs
                 // (the NRRS encoding, when the scene uses it)
@@ -473,7 +482,7 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
             for (int j = 0; j < kNH; ++j) sacc = fmaf(W2[j * kNH + k], h[j], sacc);
             dl[k] = sacc * (sm.A[0][tid][k] > 0.0f ? 1.0f : kLeak);
         }
-        if (KIN == kStatGridIn && a.dx && slot < b.batch) {
+        if (KIN == 32 && a.dx && slot < b.batch) {
             // gradient at the 16 grid features: W1^T delta1 (zero for a sample that does
             // not train); the grid's entries receive it in k_grid_scatter
 #pragma unroll
@@ -684,8 +693,14 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
                 return launch_train_t<6, kTrainStatNet, kStatGridIn>(a, r, b, grid, part,
                                                                      loss_part, s);
             return launch_train_t<6, kTrainStatNet>(a, r, b, grid, part, loss_part, s);
-        case kTrainRrsWarmup: return launch_train_t<1, kTrainRrsWarmup>(a, r, b, grid, part, loss_part, s);
-        default: return launch_train_t<1, kTrainRrsFull>(a, r, b, grid, part, loss_part, s);
+        case kTrainRrsWarmup:
+            if (a.grid)
+                return launch_train_t<1, kTrainRrsWarmup, kAidIn>(a, r, b, grid, part, loss_part, s);
+            return launch_train_t<1, kTrainRrsWarmup>(a, r, b, grid, part, loss_part, s);
+        default:
+            if (a.grid)
+                return launch_train_t<1, kTrainRrsFull, kAidIn>(a, r, b, grid, part, loss_part, s);
+            return launch_train_t<1, kTrainRrsFull>(a, r, b, grid, part, loss_part, s);
     }
 }
 

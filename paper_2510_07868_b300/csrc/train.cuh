@@ -66,8 +66,10 @@ struct TrainArgs {
     float eps, g1, g2, g3;
     float scale;          // factor on every sample's gradient (1/N for mean losses)
     const float* gin;     // kTrainGiven: output gradients [n][n_out]
-    const float2* grid;   // StatNet on the encodings of Sec. 4: its hash grid, else NULL
+    const float2* grid;   // the trained network's hash grid (StatNet on the encodings of
+                          // Sec. 4, or RRSNet on the AID-NRRS inputs), else NULL
     float* dx;            // with grid: gradient at the 16 grid features per training slot
+    float lambda;         // Box-Cox lambda of the AID-NRRS inputs
 };
 
 int train_tile();

@@ -201,6 +201,10 @@ void launch_rrsnet_simt(int rows, int grid, const float* params, const float4* f
 // network, from StatNet and the vertex state, written to `out` ([C][4] float4).
 void launch_nrrs_inputs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
                         const RenderParams& rp, int depth, int grid, float4* out, cudaStream_t s);
+// AID-NRRS factors (RRSNet on its hash grid and encoded inputs, FP32) of the marked rows.
+void launch_aid_rrsnet(const float* params, const float2* rgrid, const SceneView& sc,
+                       const WorkView& w, QueueView cur, const RenderParams& rp, int depth,
+                       int grid, cudaStream_t s);
 // ADRRS (NN) factors of the vertices the shade kernel marked (rrsnet_simt.cu).
 void launch_adrrs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
                   const RenderParams& rp, int depth, int grid, cudaStream_t s);

@@ -27,6 +27,8 @@ STAGES = 11
 STAGE_NAMES = ["init", "extend", "normalize", "split_count", "split_scan", "split_scatter",
                "finalize", "rrsnet", "shade", "reverse", "shadow"]
 NET_RRSNET, NET_RRSNET_TRAIN, NET_STATNET, NET_STATNET_GRID = 0, 1, 2, 3
+NET_RRSNET_GRID, NET_RRSNET_GRID_TRAIN = 4, 5
+AID_RRSNET_PARAMS = 3104  # RRSNet on the AID-NRRS inputs (32)
 STATNET_PARAMS = 2752
 STATNET_GRID_PARAMS = 3264  # StatNet on the encodings (32 inputs)
 GRID_PARAMS = 8 * (1 << 18) * 2
@@ -332,8 +334,9 @@ def nrrs_set_rrsnet_params(scene, params, stream=None):
     _check(_lib.nrrs_set_rrsnet_params(scene, p.ctypes.data, p.size, _stream(stream)))
 
 
-def nrrs_get_rrsnet_params(scene, stream=None):
-    p = np.zeros(RRSNET_PARAMS, dtype=np.float32)
+def nrrs_get_rrsnet_params(scene, stream=None, n=RRSNET_PARAMS):
+    """The rendering weights of RRSNet (AID_RRSNET_PARAMS with the AID-NRRS inputs)."""
+    p = np.zeros(n, dtype=np.float32)
     _check(_lib.nrrs_get_rrsnet_params(scene, p.ctypes.data, p.size, _stream(stream)))
     return p
 
@@ -395,7 +398,9 @@ def nrrs_get_params(scene, which, stream=None, n=None):
     """Weights of network `which`; StatNet on the encodings has STATNET_GRID_PARAMS (pass
     n), its grid GRID_PARAMS."""
     if n is None:
-        n = {NET_STATNET: STATNET_PARAMS, NET_STATNET_GRID: GRID_PARAMS}.get(which, RRSNET_PARAMS)
+        n = {NET_STATNET: STATNET_PARAMS, NET_STATNET_GRID: GRID_PARAMS,
+             NET_RRSNET_GRID: GRID_PARAMS, NET_RRSNET_GRID_TRAIN: GRID_PARAMS}.get(which,
+                                                                                    RRSNET_PARAMS)
     p = np.zeros(n, dtype=np.float32)
     _check(_lib.nrrs_get_params(scene, which, p.ctypes.data, n, _stream(stream)))
     return p
