@@ -521,10 +521,11 @@ def run_ours(args, rank, world, local_rank):
             return sc2
 
         # the same comparison with next-event estimation (on in the paper's experiments,
-        # Sec. 5), with RRSNet on the paper's NRRS inputs (Sec. 4 "Input Encoding"), and
-        # with StatNet on the paper's encodings too (hash grid, one-blob)
+        # Sec. 5), with RRSNet on the paper's NRRS inputs (Sec. 4 "Input Encoding"), with
+        # StatNet on the paper's encodings too (hash grid, one-blob), and AID-NRRS
         for key, nee, rin, enc in (("nee", 1, 0, 0), ("nrrs_inputs", 0, 1, 0),
-                                   ("nrrs_inputs_grid_statnet", 0, 1, 1)):
+                                   ("nrrs_inputs_grid_statnet", 0, 1, 1),
+                                   ("aid_nrrs", 0, 2, 1)):
             sc2 = trained_scene(nee, rin, enc)
             eff[key] = efficiency_section(nrrs, sc2, torch, dev, stream, seed_hi, nee=nee)
             sc2.close()
