@@ -126,5 +126,5 @@ def test_nrrs_inputs_training_and_graph(nrrs):
     assert torch.isfinite(outs[0]).all()
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     with pytest.raises(nrrs.NrrsError):
-        sc.set_rrsnet_inputs(2)
+        sc.set_rrsnet_inputs(3)  # 0, 1 (NRRS inputs) and 2 (AID-NRRS) exist
     sc.close()
