@@ -272,6 +272,23 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU leg
+def replica_seed(rank):
+    """Philox key high word of a replica: every rank renders other random numbers."""
+    return rank
+
+
+def combine_ranks(dist, device, ms, e2e_s, segs, e2e_segs):
+    """Whole-job figures of N replicas: the slowest rank's times (max over ranks) and the
+    path segments every rank traced (sum), so value = all segments / the slowest time."""
+    import torch
+
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([segs, e2e_segs], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(c[0]), int(c[1])
+
+
 def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0):
     """1/(relMSE x seconds) of the estimators on the same B300: PLAIN_RR (throughput
     roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet), ADRRS_NN (StatNet's
@@ -364,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         sc.set_traversal(4)
     out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    seed_hi = rank  # independent replicas: different Philox streams per rank
+    seed_hi = replica_seed(rank)  # independent replicas: different Philox streams per rank
     graph = 0 if args.no_graph else 1
     topts = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP, max_depth=DEPTH,
                                     seed_hi=seed_hi, graph=graph)
@@ -531,12 +548,7 @@ def run_ours(args, rank, world, local_rank):
             sc2.close()
 
     if dist:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
-        c = torch.tensor([segs, e2e_segs], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        segs, e2e_segs = int(c[0]), int(c[1])
+        ms, e2e_s, segs, e2e_segs = combine_ranks(dist, dev, ms, e2e_s, segs, e2e_segs)
     if rank != 0:
         return
     hbm, bf16, peak_kind = measured_peaks()
