@@ -138,3 +138,43 @@ def test_batch_of_64_uneven_jobs_full_size(nrrs):
           f"relMSE vs 8-frame NONE mean: NET median {np.median(e_net):.3e}, plain RR median "
           f"{np.median(e_rr):.3e}, NET better on {int(np.sum(e_net < e_rr))} of {n} jobs")
     b.close()
+
+
+@pytest.mark.parametrize("inputs", [1, 2])
+def test_batch_with_paper_inputs_equals_single_renders(nrrs, inputs):
+    """Batched jobs with RRSNet on the NRRS inputs (StatNet first) or on the AID-NRRS
+    inputs (its own hash grid), NEE on: every job equals its render alone when the
+    per-job factors agree."""
+    jobs = [(I.box_scene(1), 24, 16, 3, 6),
+            (I.icosphere_room(3, min_triangles=1500, subdiv=2), 20, 12, 4, 5)]
+    rng = np.random.default_rng(40 + inputs)
+    n_p = nrrs.AID_RRSNET_PARAMS if inputs == 2 else nrrs.RRSNET_PARAMS
+    P = (rng.normal(size=n_p) * 0.3).astype(np.float32)
+    G = (rng.normal(size=nrrs.GRID_PARAMS) * 0.3).astype(np.float32)
+    ref = None
+
+    def setup(handle):
+        nrrs.nrrs_set_rrsnet_inputs(handle, inputs)
+        nrrs.nrrs_set_rrsnet_params(handle, P)
+        if inputs == 2:
+            nrrs.nrrs_set_params(handle, nrrs.NET_RRSNET_GRID, G)
+
+    b = nrrs.Batch(jobs)
+    setup(b.handle)
+    kw = dict(frame=5, update_ref=0, nee=1)
+    imgs, st, live, F, sq = b.render(nrrs.RRS_NET, **kw)
+    torch.cuda.synchronize()
+    assert st["net_evals"] > 0 and st["nonfinite"] == 0
+    same = 0
+    for j, (scene, W, H, spp, D) in enumerate(jobs):
+        sc = nrrs.Scene(scene)
+        setup(sc.handle)
+        img, rst = sc.render(W, H, spp, D, nrrs.RRS_NET, **kw)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(sq[j, :D], rst["sum_q"][:D], rtol=1e-12, atol=0)
+        if np.array_equal(F[j, :D], rst["F"][:D]):
+            assert torch.equal(imgs[j], img), j
+            same += 1
+        sc.close()
+    assert same >= 1
+    b.close()
