@@ -152,8 +152,12 @@ __device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* l
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         ph[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        const float2 f = __bfloat1622float2(ph[j]);
-        pl[j] = __floats2bfloat162_rn(v[2 * j] - f.x, v[2 * j + 1] - f.y);
+        // hi as FP32 (a BF16 is the top half of its FP32), then both residuals in one
+        // packed subtraction (sm_100+), each rounded as a scalar one would be
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(&ph[j]);
+        const float2 f = make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+        const float2 d = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), make_float2(-f.x, -f.y));
+        pl[j] = __floats2bfloat162_rn(d.x, d.y);
     }
     const uint32_t off = kmajor_off(r, 8 * c, K);
     *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<uint4*>(ph);
@@ -282,8 +286,13 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
             }
             fence_after();
             tmem_ld32(taddr, h);
+            // Leaky ReLU as max(x, slope x) (slope < 1), the scaling two lanes at a time
 #pragma unroll
-            for (int j = 0; j < 32; ++j) h[j] = h[j] > 0.0f ? h[j] : kLeak * h[j];
+            for (int j = 0; j < 32; j += 2) {
+                const float2 s = __fmul2_rn(make_float2(h[j], h[j + 1]), make_float2(kLeak, kLeak));
+                h[j] = fmaxf(h[j], s.x);
+                h[j + 1] = fmaxf(h[j + 1], s.y);
+            }
             if (layer < 2) {
                 fence_before();
                 __syncthreads();  // every lane's MMA reads of a2 are complete (barrier fired)
