@@ -197,3 +197,20 @@ def test_nee_train_step(nrrs):
         st = sc.train_step(width=64, height=64, spp=2, max_depth=8, nee=1)
     assert st["samples"] > 0 and np.isfinite(st["loss_statnet"]) and not st["fallback"]
     sc.close()
+
+
+def test_nee_without_emitters(nrrs):
+    """A scene with no emitting triangle: NEE has nothing to sample and the image is 0,
+    alone and as a job next to a lit one (each job samples its own emitters)."""
+    dark = I.box_scene(2)
+    dark.mats["Le"][:] = 0.0
+    sc = nrrs.Scene(dark)
+    img, st = sc.render(32, 32, 4, 6, nrrs.RRS_HEUR_NORM, nee=1)
+    torch.cuda.synchronize()
+    assert st["status_bits"] == 0 and float(img.abs().max()) == 0.0
+    sc.close()
+    b = nrrs.Batch([(dark, 16, 16, 2, 5), (I.box_scene(1), 16, 16, 2, 5)])
+    imgs, st, _, _, _ = b.render(nrrs.RRS_HEUR_NORM, nee=1, update_ref=0)
+    torch.cuda.synchronize()
+    assert float(imgs[0].abs().max()) == 0.0 and float(imgs[1].max()) > 0.0
+    b.close()
