@@ -325,6 +325,11 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0):
         acc = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
         frames = 16
         segs = 0
+        # one untimed frame first, so that no mode's time holds its first graph capture
+        nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
+                         nrrs.RenderOpts.defaults(frame=89_999, seed_hi=seed_hi, gate=gate,
+                                                  update_ref=0, nee=nee),
+                         img, stream, True)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)

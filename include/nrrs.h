@@ -260,6 +260,16 @@ NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
  * width not 2 or 4); UNSUPPORTED (4 without a four-wide tree). */
 NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
 
+/* Chooses the box precision of the BVH2 that later renders traverse: 16 (default) =
+ * a copy of the tree with every child box rounded outward to IEEE binary16 (32-byte
+ * nodes, one memory sector per visit), 32 = the FP32 boxes (64-byte nodes).  The
+ * rounded boxes contain the FP32 ones, so both give the same closest hits (a few more
+ * boxes pass the slab test).  The four-wide tree of nrrs_set_traversal(4) keeps FP32
+ * boxes.  Errors: INVALID_ARG (NULL scene, bits not 16 or 32); UNSUPPORTED (16 when
+ * the scene has no FP16 copy: a leaf with more than 31 references, or 2^26 or more
+ * references). */
+NRRS_API nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits);
+
 /* Chooses what RRSNet reads at the network depths of later renders and training steps
  * (the weights are the caller's to match; a change between modes 0/1 and 2 changes the
  * network's shape and starts RRSNet afresh):

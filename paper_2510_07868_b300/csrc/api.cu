@@ -218,6 +218,7 @@ struct nrrs_scene {
     int64_t n_nodes = 0, n_tri = 0;
     float4* nodes = nullptr;
     float4* nodes4 = nullptr;  // four-wide tree (NULL when its stack bound exceeds the kernel's)
+    uint4* nodes_h = nullptr;  // BVH2 with FP16 boxes (NULL when a leaf does not fit its code)
     int bvh_width = 2;
     float4* tris = nullptr;
     nrrs_material* mats = nullptr;
@@ -339,6 +340,7 @@ void destroy(nrrs_scene* s) {
     s->ws.release();
     cudaFree(s->nodes);
     cudaFree(s->nodes4);
+    cudaFree(s->nodes_h);
     cudaFree(s->tris);
     cudaFree(s->mats);
     cudaFree(s->emit);
@@ -492,8 +494,16 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(e, "copy nodes4");
     }
+    std::vector<BvhNodeH> half;
+    if (pack_half_nodes(bvh, &half)) {
+        if ((e = dalloc(&s->nodes_h, half.size() * 2)) != cudaSuccess) return bail(e, "alloc half nodes");
+        if ((e = cudaMemcpy(s->nodes_h, half.data(), half.size() * sizeof(BvhNodeH),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy half nodes");
+    }
     s->view.nodes = s->nodes;
     s->view.nodes4 = nullptr;  // the BVH2 unless nrrs_set_traversal(4): measured no faster
+    s->view.nodes_h = s->nodes_h;  // FP16 boxes unless nrrs_set_bvh_precision(32)
     s->view.tris = s->tris;
     s->view.mats = s->mats;
     for (int k = 0; k < 3; ++k) {
@@ -568,6 +578,15 @@ nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
         return fail(NRRS_ERR_UNSUPPORTED, "no four-wide tree (its stack bound is too deep)");
     scene->bvh_width = width;
     scene->view.nodes4 = width == 4 ? scene->nodes4 : nullptr;
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (bits != 16 && bits != 32) return fail(NRRS_ERR_INVALID_ARG, "bits must be 16 or 32");
+    if (bits == 16 && !scene->nodes_h)
+        return fail(NRRS_ERR_UNSUPPORTED, "no FP16 nodes (a leaf does not fit the packed code)");
+    scene->view.nodes_h = bits == 16 ? scene->nodes_h : nullptr;
     return NRRS_OK;
 }
 
@@ -980,6 +999,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)fbits(scene->cam.aspect),
                                (uint64_t)(uintptr_t)scene->jw.part,
                                (uint64_t)(uintptr_t)scene->view.nodes4,
+                               (uint64_t)(uintptr_t)scene->view.nodes_h,
                                (uint64_t)(uintptr_t)scene->train.stat,
                                (uint64_t)o.cap_factor, (uint64_t)(uintptr_t)ws.sh_o,
                                (uint64_t)(uintptr_t)ws.qpdf[0], (uint64_t)(uintptr_t)ws.feat_net,

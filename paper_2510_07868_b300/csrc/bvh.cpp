@@ -7,6 +7,8 @@
 //   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   d = (child0, child1, count0, count1)   child >= 0: inner node index;
 //                                          child <  0: leaf, first triangle ~child.
+// A copy with half-precision boxes rounded outward (32 bytes per node, bvh.h) is what
+// the traversal reads by default.
 // Triangles (48 bytes, 3 x float4, in BVH leaf order):
 //   (v0.xyz, original index), (e1 = v1 - v0, material id), (e2 = v2 - v0, 0)
 //
@@ -374,6 +376,58 @@ struct Collapser {
 };
 
 }  // namespace
+
+// From the binary16 format: 1 sign bit, 5 exponent bits (bias 15), 10 fraction bits;
+// normal values 2^e (1 + f / 1024) for e in [-14, 15], subnormals f 2^-24.  Every
+// finite FP32 value is exact in FP64, so the magnitude's position between two
+// neighbouring binary16 values is computed exactly and rounded by floor or ceil.
+uint16_t half_directed(float x, bool up) {
+    if (std::isnan(x)) return 0x7E00;
+    const uint16_t sgn = std::signbit(x) ? 0x8000 : 0;
+    const double a = std::fabs((double)x);
+    if (a == 0.0) return sgn;
+    const bool away = (sgn == 0) == up;  // the magnitude rounds away from zero
+    if (a > 65504.0) return (uint16_t)(sgn | (away ? 0x7C00 : 0x7BFF));  // inf, or the largest
+    int E;
+    std::frexp(a, &E);                       // a = m 2^E, m in [0.5, 1)
+    const int e = std::max(E - 1, -14);      // binary exponent, subnormals at -14
+    const double steps = a / std::ldexp(1.0, e - 10);  // a in units of the spacing there
+    const uint32_t k = (uint32_t)(away ? std::ceil(steps) : std::floor(steps));
+    if (e == -14 && k < 1024u) return (uint16_t)(sgn | k);  // subnormal (k = 1024: 2^-14)
+    // k in [1024, 2048]; 2048 carries into the next exponent
+    const int ee = k == 2048u ? e + 1 : e;
+    const uint32_t frac = k == 2048u ? 0u : k - 1024u;
+    if (ee > 15) return (uint16_t)(sgn | 0x7C00);
+    return (uint16_t)(sgn | ((uint32_t)(ee + 15) << 10) | frac);
+}
+
+bool pack_half_nodes(const BvhHost& b2, std::vector<BvhNodeH>* out) {
+    out->assign(b2.nodes.size(), BvhNodeH{});
+    for (size_t i = 0; i < b2.nodes.size(); ++i) {
+        const BvhNode& n = b2.nodes[i];
+        // (lo, hi) per axis: child 0 then child 1
+        const float lohi[12] = {n.a[0], n.a[1], n.a[2], n.a[3], n.c[0], n.c[1],
+                                n.b[0], n.b[1], n.b[2], n.b[3], n.c[2], n.c[3]};
+        BvhNodeH& o = (*out)[i];
+        for (int k = 0; k < 6; ++k)
+            o.box[k] = (uint32_t)half_directed(lohi[2 * k], false) |
+                       ((uint32_t)half_directed(lohi[2 * k + 1], true) << 16);
+        for (int c = 0; c < 2; ++c) {
+            const int32_t code = n.d[c];
+            if (code >= 0) {
+                o.child[c] = code;
+                continue;
+            }
+            const uint32_t first = ~(uint32_t)code, count = (uint32_t)n.d[2 + c];
+            if (first > kLeafFirstMask || count >= 32u) {
+                out->clear();
+                return false;
+            }
+            o.child[c] = (int32_t)~(first | (count << kLeafFirstBits));
+        }
+    }
+    return true;
+}
 
 void collapse_bvh4(const BvhHost& b2, Bvh4Host* out) {
     out->nodes.clear();

@@ -38,4 +38,27 @@ struct Bvh4Host {
 
 void collapse_bvh4(const BvhHost& b2, Bvh4Host* out);
 
+// The BVH2 with half-precision boxes (32 bytes per node, two 16-byte rows): the six
+// bounds of child 0 then of child 1, each (lo, hi) pair one word holding two IEEE
+// binary16 values (lo in the low half), then the two child codes.  Each lower bound is
+// rounded toward -inf and each upper bound toward +inf, so a box only grows: a ray that
+// reaches a triangle through the FP32 box still reaches it, and the closest hit is
+// unchanged (a few more boxes pass the slab test).  A leaf code is
+// ~(first | count << 26).
+struct BvhNodeH {
+    uint32_t box[6];  // x0, y0, z0, x1, y1, z1: (lo | hi << 16)
+    int32_t child[2];
+};
+static_assert(sizeof(BvhNodeH) == 32, "node is 2 x uint4");
+
+constexpr uint32_t kLeafFirstBits = 26;
+constexpr uint32_t kLeafFirstMask = (1u << kLeafFirstBits) - 1u;
+
+// IEEE binary16 bits of x rounded toward +inf (up) or -inf.
+uint16_t half_directed(float x, bool up);
+
+// Packs the BVH2's nodes; false (out cleared) when a leaf does not fit the code (more
+// than 31 references, or a first reference at or above 2^26).
+bool pack_half_nodes(const BvhHost& b2, std::vector<BvhNodeH>* out);
+
 }  // namespace nrrs

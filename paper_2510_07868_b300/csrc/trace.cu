@@ -3,7 +3,9 @@
 // estimation's shadow rays.  Persistent warps claim rays from the live queue; the
 // traversal stack lives in shared memory.
 #include <cfloat>
+#include <cuda_fp16.h>
 
+#include "bvh.h"
 #include "wavefront.cuh"
 
 namespace nrrs {
@@ -142,22 +144,55 @@ __device__ __forceinline__ bool visit_node4(const SceneView& sc, Ray& r, Hit& h,
     return false;
 }
 
+// The (lo, hi) pair of binary16 values in one word of a half-precision node.
+__device__ __forceinline__ float2 half_pair(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+
 // Inner-node step of the postponed-leaf traversal: tests both child boxes; leaf children
 // hit become the lane's pending leaves (tested later, together with the other lanes'),
 // inner children are entered near-first.  node < 0 afterwards: nothing left to visit.
+// Reads the 32-byte nodes with FP16 boxes rounded outward when the scene has them (one
+// 32-byte sector per visit instead of two; the same closest hits), else the FP32 nodes.
 __device__ __forceinline__ void visit_inner(const SceneView& sc, Ray& r, const Hit& h, int* stk,
                                             int stride, int* leaf0, int* cnt0, int* leaf1,
                                             int* cnt1) {
-    const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
-    const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
-    const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
-    const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
     float t0n, t1n;
-    bool h0 = slab(r, h.t, a.x, a.y, a.z, a.w, c.x, c.y, &t0n);
-    bool h1 = slab(r, h.t, b.x, b.y, b.z, b.w, c.z, c.w, &t1n);
-    int c0 = e.x, c1 = e.y;
-    if (h0 && c0 < 0) { *leaf0 = ~c0; *cnt0 = e.z; h0 = false; }
-    if (h1 && c1 < 0) { *leaf1 = ~c1; *cnt1 = e.w; h1 = false; }
+    bool h0, h1;
+    int c0, c1;
+    if (sc.nodes_h) {
+        const uint4 p = __ldg(&sc.nodes_h[2 * r.node + 0]);
+        const uint4 q = __ldg(&sc.nodes_h[2 * r.node + 1]);
+        const float2 x0 = half_pair(p.x), y0 = half_pair(p.y), z0 = half_pair(p.z);
+        const float2 x1 = half_pair(p.w), y1 = half_pair(q.x), z1 = half_pair(q.y);
+        h0 = slab(r, h.t, x0.x, x0.y, y0.x, y0.y, z0.x, z0.y, &t0n);
+        h1 = slab(r, h.t, x1.x, x1.y, y1.x, y1.y, z1.x, z1.y, &t1n);
+        c0 = (int)q.z;
+        c1 = (int)q.w;
+        if (h0 && c0 < 0) {
+            const uint32_t v = ~(uint32_t)c0;
+            *leaf0 = (int)(v & kLeafFirstMask);
+            *cnt0 = (int)(v >> kLeafFirstBits);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            const uint32_t v = ~(uint32_t)c1;
+            *leaf1 = (int)(v & kLeafFirstMask);
+            *cnt1 = (int)(v >> kLeafFirstBits);
+            h1 = false;
+        }
+    } else {
+        const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
+        const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
+        const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
+        const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
+        h0 = slab(r, h.t, a.x, a.y, a.z, a.w, c.x, c.y, &t0n);
+        h1 = slab(r, h.t, b.x, b.y, b.z, b.w, c.z, c.w, &t1n);
+        c0 = e.x;
+        c1 = e.y;
+        if (h0 && c0 < 0) { *leaf0 = ~c0; *cnt0 = e.z; h0 = false; }
+        if (h1 && c1 < 0) { *leaf1 = ~c1; *cnt1 = e.w; h1 = false; }
+    }
     if (h0 && h1) {
         if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
         if (r.sp < kStack) stk[(r.sp++) * stride] = c1;

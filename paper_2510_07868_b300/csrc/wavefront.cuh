@@ -11,6 +11,7 @@ namespace nrrs {
 struct SceneView {
     const float4* nodes;  // 4 float4 per node (bvh.cpp)
     const float4* nodes4; // four-wide tree, 8 float4 per node; NULL = traverse the BVH2
+    const uint4* nodes_h; // the BVH2 with FP16 boxes, 2 uint4 per node; NULL = FP32 nodes
     const float4* tris;   // 3 float4 per triangle, BVH order
     const nrrs_material* mats;
     float lo[3];          // scene box, for the position feature

@@ -46,6 +46,7 @@ EXPORTED = [
     "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
+    "nrrs_set_bvh_precision",
 ]
 
 
@@ -212,6 +213,7 @@ def _load():
         "nrrs_render_batch": ([P, I32, P, P, P, P, P, P, P], I32),
         "nrrs_batch_info": ([P, P, P, P], I32),
         "nrrs_set_traversal": ([P, I32], I32),
+        "nrrs_set_bvh_precision": ([P, I32], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -317,6 +319,10 @@ def nrrs_batch_info(batch):
 
 def nrrs_set_traversal(scene, width):
     _check(_lib.nrrs_set_traversal(scene, width))
+
+
+def nrrs_set_bvh_precision(scene, bits):
+    _check(_lib.nrrs_set_bvh_precision(scene, bits))
 
 
 def nrrs_destroy_scene(scene):
@@ -618,6 +624,9 @@ class Scene:
 
     def set_traversal(self, width):
         nrrs_set_traversal(self.handle, width)
+
+    def set_bvh_precision(self, bits):
+        nrrs_set_bvh_precision(self.handle, bits)
 
     def set_rrsnet_inputs(self, mode):
         nrrs_set_rrsnet_inputs(self.handle, mode)

@@ -350,24 +350,42 @@ def test_graph_captured_train_step_matches(nrrs):
 
 
 @pytest.mark.parametrize("scene_name", ["box", "occluded", "ggx", "three_rooms"])
-def test_four_wide_traversal_equals_bvh2(nrrs, scene_name):
-    """The four-wide tree collapsed from the BVH2 finds the same closest hits (same
-    triangle test, same tie rule), so whole renders are bit-identical."""
+def test_tree_formats_give_identical_renders(nrrs, scene_name):
+    """The BVH2 with FP16 boxes rounded outward (the default), the BVH2 with FP32 boxes
+    and the four-wide tree collapsed from it find the same closest hits (same triangle
+    test, same tie rule; the FP16 boxes contain the FP32 ones), so whole renders are
+    bit-identical; so are next-event estimation's any-hit shadow queries."""
     s = {"box": lambda: I.box_scene(2), "occluded": lambda: I.occluded_room(1),
          "ggx": lambda: I.icosphere_room(4, min_triangles=20000, subdiv=2),
          "three_rooms": lambda: I.three_rooms(1)}[scene_name]()
     P = I.rrsnet_init_params(3)
     W, H, spp, D = (128, 96, 8, 12) if scene_name != "three_rooms" else (320, 180, 4, 16)
+    runs = [(nrrs.RRS_NONE, 0), (nrrs.RRS_NET, 0), (nrrs.RRS_NET, 1)]
     out = []
-    for width in (2, 4):
+    for width, bits in ((2, 16), (2, 32), (4, 32)):
         sc = nrrs.Scene(s)
         sc.set_params(P)
+        sc.set_bvh_precision(bits)
         sc.set_traversal(width)
-        for mode in (nrrs.RRS_NONE, nrrs.RRS_NET):
-            img, st = sc.render(W, H, spp, D, mode, frame=1)
+        for mode, nee in runs:
+            img, st = sc.render(W, H, spp, D, mode, frame=1, nee=nee)
             torch.cuda.synchronize()
             out.append((img.cpu().numpy(), st))
         sc.close()
-    for (a, sa), (b, sb) in zip(out[:2], out[2:]):
-        np.testing.assert_array_equal(a, b)
-        np.testing.assert_array_equal(sa["live"], sb["live"])
+    n = len(runs)
+    if scene_name != "three_rooms":  # there light from the third room seldom reaches room 1
+        assert np.abs(out[0][0]).sum() > 0
+    for k in (1, 2):
+        for (a, sa), (b, sb) in zip(out[:n], out[k * n:(k + 1) * n]):
+            np.testing.assert_array_equal(a, b)
+            np.testing.assert_array_equal(sa["live"], sb["live"])
+
+
+def test_bvh_precision_arguments(nrrs):
+    sc = nrrs.Scene(I.box_scene(1))
+    for bad in (0, 8, 64):
+        with pytest.raises(nrrs.NrrsError):
+            sc.set_bvh_precision(bad)
+    sc.set_bvh_precision(32)
+    sc.set_bvh_precision(16)
+    sc.close()
