@@ -83,8 +83,19 @@ __global__ void k_error_temporal(const float* E_cur, float* E_acc, long long n, 
 // every weight is 1 (a box filter).  With normals, a pixel that has one weighs a
 // neighbour with a normal by max(0, n_p . n_q)^power and one without by 0; a pixel
 // without a normal weighs every neighbour by 1.  The centre always has weight 1.
+// An integral power (ipow >= 0) is raised by repeated squaring (FP64 pow is slow on
+// this GPU; the squarings differ from it by a few FP64 roundings).
+__device__ __forceinline__ double pow_by_squaring(double b, int n) {
+    double r = 1.0;
+    for (; n > 0; n >>= 1) {
+        if (n & 1) r *= b;
+        b *= b;
+    }
+    return r;
+}
+
 __global__ void k_error_filter(const float* in, const float4* nrm, int W, int H, int r,
-                               float power, float* out) {
+                               float power, int ipow, float* out) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long long)W * H) return;
     const int x = (int)(p % W), y = (int)(p / W);
@@ -98,7 +109,9 @@ __global__ void k_error_filter(const float* in, const float4* nrm, int W, int H,
             if (guided && q != p) {
                 const float4 nq = nrm[q];
                 const float d = np.x * nq.x + np.y * nq.y + np.z * nq.z;
-                wq = nq.w > 0.0f && d > 0.0f ? pow((double)d, (double)power) : 0.0;
+                wq = !(nq.w > 0.0f && d > 0.0f) ? 0.0
+                     : ipow >= 0                   ? pow_by_squaring((double)d, ipow)
+                                                   : pow((double)d, (double)power);
             }
             s += wq * in[q];
             c += wq;
@@ -651,6 +664,11 @@ void launch_relmse(const float* img, const float* ref, long long n3, double eps,
     k_relmse<<<1, 1024, 0, s>>>(img, ref, n3, eps, out);
 }
 
+// power as an exponent for repeated squaring, or -1 when it is not a small integer
+static int integral_power(float power) {
+    return power >= 0.0f && power <= 1024.0f && power == floorf(power) ? (int)power : -1;
+}
+
 void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int W, int H,
                             float alpha, int first, int radius, const float4* nrm, float power,
                             cudaStream_t s) {
@@ -658,7 +676,8 @@ void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int 
     const unsigned g = (unsigned)((n + 255) / 256);
     k_error_temporal<<<g, 256, 0, s>>>(E_cur, E_acc, n, alpha, first);
     if (radius > 0)
-        k_error_filter<<<g, 256, 0, s>>>(E_acc, nrm, W, H, radius, power, E_out);
+        k_error_filter<<<g, 256, 0, s>>>(E_acc, nrm, W, H, radius, power, integral_power(power),
+                                         E_out);
     else
         cudaMemcpyAsync(E_out, E_acc, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
 }
@@ -666,7 +685,8 @@ void launch_error_smoothing(const float* E_cur, float* E_acc, float* E_out, int 
 void launch_error_filter(const float* in, const float4* nrm, int W, int H, int radius,
                          float power, float* out, cudaStream_t s) {
     const long long n = (long long)W * H;
-    k_error_filter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, nrm, W, H, radius, power, out);
+    k_error_filter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, nrm, W, H, radius, power,
+                                                               integral_power(power), out);
 }
 
 void launch_pixel_normals(const RecordView& r, int spp, long long npix, float4* nrm,

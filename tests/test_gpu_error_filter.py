@@ -37,9 +37,10 @@ def _filter_reference(E, N, W, H, r, power):
     return out
 
 
-@pytest.mark.parametrize("guided", [False, True])
-def test_error_filter_matches_definition(nrrs, guided):
-    W, H, r, power = 37, 23, 2, 8.0
+@pytest.mark.parametrize("guided,power", [(False, 8.0), (True, 8.0), (True, 5.0), (True, 2.5)])
+def test_error_filter_matches_definition(nrrs, guided, power):
+    """Integral powers take repeated squaring, others pow; both against the definition."""
+    W, H, r = 37, 23, 2
     rng = np.random.default_rng(5)
     E = rng.exponential(size=W * H).astype(np.float32)
     N = None
