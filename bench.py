@@ -643,7 +643,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
                    "parallelism": f"replicas{world}",
                    "bounce_loop": "CUDA graph per frame" if graph else "stream launches",
-                   "bvh": "four-wide" if args.bvh4 else "BVH2",
+                   "bvh": "four-wide, FP32 boxes" if args.bvh4 else "BVH2, FP16 boxes rounded outward",
                    "l2": "no flush: each step rewrites ~0.3 GB of path queues and records (> 126 MB L2)"},
         "step_breakdown": {"train_step_ms": train_ms / args.steps,
                            "render_ms": (ms - train_ms) / args.steps,
