@@ -381,11 +381,19 @@ def test_tree_formats_give_identical_renders(nrrs, scene_name):
             np.testing.assert_array_equal(sa["live"], sb["live"])
 
 
-def test_bvh_precision_arguments(nrrs):
-    sc = nrrs.Scene(I.box_scene(1))
+def test_bvh_precision_arguments_and_graph_switch(nrrs):
+    """Bad widths fail loudly; switching the node format between graph-launched renders
+    of one scene takes effect (the graph is keyed by the tree it reads) and gives the
+    same image."""
+    sc = nrrs.Scene(I.occluded_room(1))
     for bad in (0, 8, 64):
         with pytest.raises(nrrs.NrrsError):
             sc.set_bvh_precision(bad)
-    sc.set_bvh_precision(32)
-    sc.set_bvh_precision(16)
+    imgs = []
+    for bits in (16, 32, 16):
+        sc.set_bvh_precision(bits)
+        img, _ = sc.render(96, 64, 4, 8, nrrs.RRS_HEUR_NORM, frame=2, update_ref=0, graph=1)
+        torch.cuda.synchronize()
+        imgs.append(img.clone())
+    assert torch.equal(imgs[0], imgs[1]) and torch.equal(imgs[0], imgs[2])
     sc.close()
