@@ -260,12 +260,13 @@ NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
  * width not 2 or 4); UNSUPPORTED (4 without a four-wide tree). */
 NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
 
-/* Chooses the box precision of the BVH2 that later renders traverse: 16 (default) =
- * a copy of the tree with every child box rounded outward to IEEE binary16 (32-byte
- * nodes, one memory sector per visit), 32 = the FP32 boxes (64-byte nodes).  The
- * rounded boxes contain the FP32 ones, so both give the same closest hits (a few more
- * boxes pass the slab test).  The four-wide tree of nrrs_set_traversal(4) keeps FP32
- * boxes.  Errors: INVALID_ARG (NULL scene, bits not 16 or 32); UNSUPPORTED (16 when
+/* Chooses the box precision of the BVH2 that later renders traverse: 16 = a copy of
+ * the tree with every child box rounded outward to IEEE binary16 (32-byte nodes, one
+ * memory sector per visit), 32 = the FP32 boxes (64-byte nodes).  The rounded boxes
+ * contain the FP32 ones, so both give the same closest hits (a few more boxes pass the
+ * slab test).  The default is 16 unless the rounding grows the child boxes' summed
+ * surface area (the expected box visits) by more than 10 % (a scene far from the origin,
+ * where binary16 is coarse), then 32.  The four-wide tree of nrrs_set_traversal(4) keeps FP32 boxes.  Errors: INVALID_ARG (NULL scene, bits not 16 or 32); UNSUPPORTED (16 when
  * the scene has no FP16 copy: a leaf with more than 31 references, or 2^26 or more
  * references). */
 NRRS_API nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits);

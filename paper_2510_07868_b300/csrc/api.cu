@@ -495,7 +495,9 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
             return bail(e, "copy nodes4");
     }
     std::vector<BvhNodeH> half;
+    bool half_default = false;
     if (pack_half_nodes(bvh, &half)) {
+        half_default = half_node_growth(bvh, half) <= kMaxHalfGrowth;
         if ((e = dalloc(&s->nodes_h, half.size() * 2)) != cudaSuccess) return bail(e, "alloc half nodes");
         if ((e = cudaMemcpy(s->nodes_h, half.data(), half.size() * sizeof(BvhNodeH),
                             cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -503,7 +505,8 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
     }
     s->view.nodes = s->nodes;
     s->view.nodes4 = nullptr;  // the BVH2 unless nrrs_set_traversal(4): measured no faster
-    s->view.nodes_h = s->nodes_h;  // FP16 boxes unless nrrs_set_bvh_precision(32)
+    // FP16 boxes unless rounding grows them too much, or nrrs_set_bvh_precision(32)
+    s->view.nodes_h = half_default ? s->nodes_h : nullptr;
     s->view.tris = s->tris;
     s->view.mats = s->mats;
     for (int k = 0; k < 3; ++k) {

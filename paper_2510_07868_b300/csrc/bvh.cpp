@@ -429,6 +429,44 @@ bool pack_half_nodes(const BvhHost& b2, std::vector<BvhNodeH>* out) {
     return true;
 }
 
+namespace {
+
+double half_value(uint32_t bits16) {
+    const uint32_t e = (bits16 >> 10) & 31u, f = bits16 & 1023u;
+    const double mag = e == 31u ? HUGE_VAL : e == 0u ? std::ldexp((double)f, -24)
+                                                      : std::ldexp(1024.0 + f, (int)e - 25);
+    return (bits16 & 0x8000u) ? -mag : mag;
+}
+
+double box_area(const double* lo, const double* hi) {
+    const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+}
+
+}  // namespace
+
+double half_node_growth(const BvhHost& b2, const std::vector<BvhNodeH>& h) {
+    double sum = 0.0, qsum = 0.0;
+    for (size_t i = 0; i < b2.nodes.size() && i < h.size(); ++i) {
+        const BvhNode& nd = b2.nodes[i];
+        const float lohi[12] = {nd.a[0], nd.a[1], nd.a[2], nd.a[3], nd.c[0], nd.c[1],
+                                nd.b[0], nd.b[1], nd.b[2], nd.b[3], nd.c[2], nd.c[3]};
+        for (int c = 0; c < 2; ++c) {
+            if (nd.d[c] < 0 && nd.d[2 + c] == 0) continue;  // the empty child of a one-leaf root
+            double lo[3], hi[3], qlo[3], qhi[3];
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = lohi[6 * c + 2 * k];
+                hi[k] = lohi[6 * c + 2 * k + 1];
+                qlo[k] = half_value(h[i].box[3 * c + k] & 0xFFFFu);
+                qhi[k] = half_value(h[i].box[3 * c + k] >> 16);
+            }
+            sum += box_area(lo, hi);
+            qsum += box_area(qlo, qhi);
+        }
+    }
+    return sum > 0.0 ? std::min(qsum / sum - 1.0, 1e6) : 0.0;
+}
+
 void collapse_bvh4(const BvhHost& b2, Bvh4Host* out) {
     out->nodes.clear();
     out->nodes.reserve(b2.nodes.size() / 2 + 1);

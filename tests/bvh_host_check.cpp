@@ -6,6 +6,8 @@
 //                                       BvhNodeH[nodes]>
 //   limit <unused>                    <out: int32[3] = pack results for a leaf of 31
 //                                       references, of 32, and a first reference 2^26>
+//   growth <in: as pack>              <out: float64 mean surface-area growth of the
+//                                       packed child boxes>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -39,7 +41,7 @@ int main(int argc, char** argv) {
             const uint16_t r[2] = {half_directed(x, false), half_directed(x, true)};
             std::fwrite(r, 2, 2, out);
         }
-    } else if (!std::strcmp(argv[1], "pack")) {
+    } else if (!std::strcmp(argv[1], "pack") || !std::strcmp(argv[1], "growth")) {
         int32_t n;
         std::memcpy(&n, in.data(), 4);
         std::vector<float> tri((size_t)n * 9);
@@ -49,6 +51,12 @@ int main(int argc, char** argv) {
         build_bvh(tri.data(), n, mat.data(), &b);
         std::vector<BvhNodeH> h;
         const int32_t ok = pack_half_nodes(b, &h) ? 1 : 0;
+        if (!std::strcmp(argv[1], "growth")) {
+            const double g = half_node_growth(b, h);
+            std::fwrite(&g, 8, 1, out);
+            std::fclose(out);
+            return 0;
+        }
         const int64_t nn = (int64_t)b.nodes.size();
         std::fwrite(&nn, 8, 1, out);
         std::fwrite(b.nodes.data(), sizeof(BvhNode), b.nodes.size(), out);

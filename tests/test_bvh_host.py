@@ -82,7 +82,8 @@ def test_packed_nodes_contain_the_fp32_boxes(driver, tmp_path, scene):
     words = half[:, :6].reshape(nn, 2, 3)
     lo = _f16(words & 0xFFFF)
     hi = _f16(words >> 16)
-    used = nodes["d"][:, :2] != ~0  # an empty child (code ~0, no references) has no box
+    # an empty child (a leaf of no references) has no box
+    used = ~((nodes["d"][:, :2] < 0) & (nodes["d"][:, 2:] == 0))
     flo, fhi = f32[..., 0::2].astype(np.float64), f32[..., 1::2].astype(np.float64)
     assert np.all((lo <= flo)[used]) and np.all((hi >= fhi)[used])
     # outward by less than one binary16 spacing (2^-10 relative, or 2^-24 near zero)
@@ -101,3 +102,44 @@ def test_packed_nodes_contain_the_fp32_boxes(driver, tmp_path, scene):
 def test_pack_refuses_leaves_beyond_the_code(driver, tmp_path):
     res = np.frombuffer(_run(driver, tmp_path, "limit", b"\0"), dtype=np.int32)
     assert res.tolist() == [1, 0, 0]  # 31 references fit; 32, or a first at 2^26, do not
+
+
+def _growth_numpy(out):
+    """Growth of the packed child boxes' summed surface area, from the pack output."""
+    nn = int(np.frombuffer(out[:8], dtype=np.int64)[0])
+    rec = np.dtype([("a", "<f4", 4), ("b", "<f4", 4), ("c", "<f4", 4), ("d", "<i4", 4)])
+    nodes = np.frombuffer(out[8:8 + 64 * nn], dtype=rec)
+    half = np.frombuffer(out[12 + 64 * nn:], dtype=np.uint32).reshape(nn, 8)
+    f32 = np.stack([np.concatenate([nodes["a"], nodes["c"][:, :2]], axis=1),
+                    np.concatenate([nodes["b"], nodes["c"][:, 2:]], axis=1)], axis=1)
+    words = half[:, :6].reshape(nn, 2, 3)
+    with np.errstate(over="ignore", invalid="ignore"):
+        q = np.stack([_f16(words & 0xFFFF), _f16(words >> 16)], axis=-1)
+        f = np.stack([f32[..., 0::2], f32[..., 1::2]], axis=-1).astype(np.float64)
+
+        def area(b):
+            e = b[..., 1] - b[..., 0]
+            return 2 * (e[..., 0] * e[..., 1] + e[..., 1] * e[..., 2] + e[..., 2] * e[..., 0])
+
+        a, qa = area(f), area(q)
+        used = ~((nodes["d"][:, :2] < 0) & (nodes["d"][:, 2:] == 0))
+        return float(min(qa[used].sum() / a[used].sum() - 1.0, 1e6))
+
+
+def test_growth_of_packed_boxes_picks_the_default(driver, tmp_path):
+    """Near the origin the rounded boxes' summed area grows by well under the 10 % that
+    keeps FP16 the default; the same scene moved to x ~ 2000 (binary16 spacing 1 or 2
+    there) grows far beyond it, so it defaults to the FP32 nodes.  The library's figure
+    equals the one computed here from the packed tree."""
+    s = I.occluded_room(1)
+    far = s.tri.copy()
+    far[:, 0::3] += 2000.0
+    for tri, lo_bound in ((s.tri, None), (far, 0.10)):
+        payload = np.int32(len(tri)).tobytes() + tri.astype(np.float32).tobytes()
+        g = float(np.frombuffer(_run(driver, tmp_path, "growth", payload), dtype=np.float64)[0])
+        ref = _growth_numpy(_run(driver, tmp_path, "pack", payload))
+        assert g == pytest.approx(ref, rel=1e-9)
+        if lo_bound is None:
+            assert 0.0 < g < 0.10
+        else:
+            assert g > lo_bound

@@ -381,6 +381,29 @@ def test_tree_formats_give_identical_renders(nrrs, scene_name):
             np.testing.assert_array_equal(sa["live"], sb["live"])
 
 
+def test_scene_far_from_origin_renders_the_same_with_either_node_format(nrrs):
+    """At x ~ 2000 binary16 is coarse (spacing 1 or 2), so the rounded boxes are far
+    larger than the FP32 ones: the scene defaults to FP32 nodes, and the FP16 nodes,
+    still conservative, give the same image, only slower."""
+    s = I.box_scene(2)
+    tri = s.tri.copy()
+    tri[:, 0::3] += 2000.0
+    cam = s.cam.copy()
+    cam["pos"][:, 0] += 2000.0
+    far = I.Scene(tri, s.mat_id, s.mats, cam, "box_far")
+    sc = nrrs.Scene(far)
+    imgs = []
+    for bits in (None, 16, 32):
+        if bits:
+            sc.set_bvh_precision(bits)
+        img, _ = sc.render(64, 48, 4, 8, nrrs.RRS_HEUR_NORM, frame=3, update_ref=0)
+        torch.cuda.synchronize()
+        imgs.append(img.clone())
+    assert torch.abs(imgs[0]).sum() > 0
+    assert torch.equal(imgs[0], imgs[1]) and torch.equal(imgs[0], imgs[2])
+    sc.close()
+
+
 def test_bvh_precision_arguments_and_graph_switch(nrrs):
     """Bad widths fail loudly; switching the node format between graph-launched renders
     of one scene takes effect (the graph is keyed by the tree it reads) and gives the
