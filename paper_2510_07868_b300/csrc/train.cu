@@ -224,12 +224,14 @@ __global__ void k_relmse(const float* img, const float* ref, long long n3, doubl
 // ------------------------------------------------------------------ MLP training
 // Shared-memory layout of one tile (kTile samples): inputs X[kTile][KIN], hidden
 // activations A1..A3[kTile][32] (post Leaky ReLU; their sign is the sign of the
-// pre-activation), output gradients G[kTile][8], then the weights.
+// pre-activation), output gradients G[kTile][8], then the weights.  Each sample's row
+// is padded by one float: with 32-float rows the warp's 32 samples would store into the
+// same bank (32-way conflicts); with 33 every lane has its own.
 template <int KIN>
 struct TrainSmem {
-    float X[kTile][KIN];
-    float A[3][kTile][kNH];
-    float G[kTile][8];
+    float X[kTile][KIN + 1];
+    float A[3][kTile][kNH + 1];
+    float G[kTile][9];
 };
 
 __device__ __forceinline__ float lrelu(float a) { return a > 0.0f ? a : kLeak * a; }
@@ -458,12 +460,9 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         // ---- W3 gradients: sum_s delta3[s][j] A2[s][k]
         for (int q = 0; q < kTile; ++q) {
             const float dj = sm.A[2][q][gj];
-            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[1][q][8 * gq]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[1][q][8 * gq + 4]);
-            g3[0] = fmaf(dj, a0.x, g3[0]); g3[1] = fmaf(dj, a0.y, g3[1]);
-            g3[2] = fmaf(dj, a0.z, g3[2]); g3[3] = fmaf(dj, a0.w, g3[3]);
-            g3[4] = fmaf(dj, a1.x, g3[4]); g3[5] = fmaf(dj, a1.y, g3[5]);
-            g3[6] = fmaf(dj, a1.z, g3[6]); g3[7] = fmaf(dj, a1.w, g3[7]);
+            const float* ar = &sm.A[1][q][8 * gq];  // padded rows: no 16-byte loads
+#pragma unroll
+            for (int e = 0; e < 8; ++e) g3[e] = fmaf(dj, ar[e], g3[e]);
         }
         // delta2 = (W3^T delta3) * lrelu'(a2)
 #pragma unroll
@@ -480,12 +479,9 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         // ---- W2 gradients: sum_s delta2[s][j] A1[s][k]
         for (int q = 0; q < kTile; ++q) {
             const float dj = sm.A[1][q][gj];
-            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[0][q][8 * gq]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[0][q][8 * gq + 4]);
-            g2[0] = fmaf(dj, a0.x, g2[0]); g2[1] = fmaf(dj, a0.y, g2[1]);
-            g2[2] = fmaf(dj, a0.z, g2[2]); g2[3] = fmaf(dj, a0.w, g2[3]);
-            g2[4] = fmaf(dj, a1.x, g2[4]); g2[5] = fmaf(dj, a1.y, g2[5]);
-            g2[6] = fmaf(dj, a1.z, g2[6]); g2[7] = fmaf(dj, a1.w, g2[7]);
+            const float* ar = &sm.A[0][q][8 * gq];  // padded rows: no 16-byte loads
+#pragma unroll
+            for (int e = 0; e < 8; ++e) g2[e] = fmaf(dj, ar[e], g2[e]);
         }
         // delta1 = (W2^T delta2) * lrelu'(a1); a1 is still in A1 for this thread
 #pragma unroll
@@ -513,14 +509,9 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         // ---- W1 gradients: sum_s delta1[s][j] X[s][k]
         for (int q = 0; q < kTile; ++q) {
             const float dj = sm.A[0][q][gj];
+            const float* xr = &sm.X[q][C1 * gq];
 #pragma unroll
-            for (int c4 = 0; c4 < C1 / 4; ++c4) {
-                const float4 x0 = *reinterpret_cast<const float4*>(&sm.X[q][C1 * gq + 4 * c4]);
-                g1[4 * c4 + 0] = fmaf(dj, x0.x, g1[4 * c4 + 0]);
-                g1[4 * c4 + 1] = fmaf(dj, x0.y, g1[4 * c4 + 1]);
-                g1[4 * c4 + 2] = fmaf(dj, x0.z, g1[4 * c4 + 2]);
-                g1[4 * c4 + 3] = fmaf(dj, x0.w, g1[4 * c4 + 3]);
-            }
+            for (int c = 0; c < C1; ++c) g1[c] = fmaf(dj, xr[c], g1[c]);
         }
         __syncthreads();
     }
