@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's CPU
 baseline leg load it.  The product package never imports this module, and this
 module never imports the product package.
 
-Parity unpinned: the GGX lobe (``or_sample_ggx``) has no formula in the paper; it is
-checked only against closed forms (energy bound, reciprocity of the weight) in tests/.
+The paper prints no BSDF; the GGX lobe (``or_ggx_D``, ``or_ggx_G1``, ``or_sample_ggx``,
+``or_eval_bsdf``) is pinned in tests/ by the identities of the microfacet model
+(normalisation of D, Smith's masking identity, the expected sampling weight equal to the
+quadrature of f cos, the normal-incidence closed form).
 """
 from __future__ import annotations
 
@@ -90,6 +92,17 @@ def lib():
         _lib.or_sample_ggx.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
                                        C.c_double, P, P]
         _lib.or_sample_ggx.restype = C.c_int
+        _lib.or_ggx_D.argtypes = [C.c_double, C.c_double]
+        _lib.or_ggx_D.restype = C.c_double
+        _lib.or_ggx_G1.argtypes = [C.c_double, C.c_double]
+        _lib.or_ggx_G1.restype = C.c_double
+        _lib.or_eval_ggx.argtypes = [P, P, P, P, C.c_double, C.c_double, P, P]
+        _lib.or_eval_ggx.restype = C.c_int
+        _lib.or_sample_ggx_batch.argtypes = [P, P, P, C.c_double, C.c_double, P, C.c_int64, P, P]
+        _lib.or_eval_ggx_batch.argtypes = [P, P, P, C.c_int64, P, C.c_double, C.c_double, P, P]
+        _lib.or_error_temporal.argtypes = [P, P, C.c_int64, C.c_double, C.c_int]
+        _lib.or_error_filter.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_double, P]
+        _lib.or_pixel_normals.argtypes = [P, P, C.c_int64, C.c_int32, P]
         _lib.or_softplus_mod.argtypes = [C.c_double]
         _lib.or_softplus_mod.restype = C.c_double
         _lib.or_softplus_mod_grad.argtypes = [C.c_double]
@@ -198,6 +211,80 @@ def sample_ggx(n, wo, albedo, rough, F0, ulobe, u1, u2):
     return ok, wi, w
 
 
+def ggx_D(cos_h, a):
+    """GGX normal distribution at cos(theta_h) for roughness a."""
+    return float(lib().or_ggx_D(float(cos_h), float(a)))
+
+
+def ggx_G1(cos_w, a):
+    """Smith masking term of GGX for a direction at cos(theta)."""
+    return float(lib().or_ggx_G1(float(cos_w), float(a)))
+
+
+def eval_ggx(n, wo, wi, albedo, rough, F0):
+    """f cos_i per channel and the sampling pdf of wi for the GGX + Lambert mixture."""
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    alb = np.ascontiguousarray(albedo, dtype=np.float64)
+    fc = np.zeros(3)
+    pdf = np.zeros(1)
+    ok = lib().or_eval_ggx(_p(n), _p(wo), _p(wi), _p(alb), rough, F0, _p(fc), _p(pdf))
+    return ok, fc, float(pdf[0])
+
+
+def sample_ggx_batch(n, wo, albedo, rough, F0, u):
+    """or_sample_ggx over rows of u [m][3] = (ulobe, u1, u2): directions and weights."""
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    alb = np.ascontiguousarray(albedo, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    m = u.shape[0]
+    wi = np.zeros((m, 3))
+    w = np.zeros((m, 3))
+    lib().or_sample_ggx_batch(_p(n), _p(wo), _p(alb), rough, F0, _p(u), m, _p(wi), _p(w))
+    return wi, w
+
+
+def eval_ggx_batch(n, wo, wi, albedo, rough, F0):
+    """or_eval_ggx over rows of wi [m][3]: f cos per channel and the sampling pdf."""
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wo = np.ascontiguousarray(wo, dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    alb = np.ascontiguousarray(albedo, dtype=np.float64)
+    m = wi.shape[0]
+    fc = np.zeros((m, 3))
+    pdf = np.zeros(m)
+    lib().or_eval_ggx_batch(_p(n), _p(wo), _p(wi), m, _p(alb), rough, F0, _p(fc), _p(pdf))
+    return fc, pdf
+
+
+def error_temporal(E_cur, E_acc, alpha=0.5, first=False):
+    """Temporal EMA of the error map; returns the new E_acc (E_acc is not modified)."""
+    Ec = np.ascontiguousarray(E_cur, dtype=np.float64)
+    Ea = np.array(E_acc if E_acc is not None else np.zeros_like(Ec), dtype=np.float64)
+    lib().or_error_temporal(_p(Ec), _p(Ea), Ec.size, float(alpha), int(bool(first)))
+    return Ea
+
+
+def error_filter(E, W, H, radius, normals=None, power=8.0):
+    """The normal-guided (2r+1)^2 spatial filter of the error map."""
+    Ein = np.ascontiguousarray(E, dtype=np.float64)
+    N = np.ascontiguousarray(normals, dtype=np.float64) if normals is not None else None
+    out = np.zeros(W * H)
+    lib().or_error_filter(_p(Ein), _p(N), W, H, radius, float(power), _p(out))
+    return out
+
+
+def pixel_normals(feat1, q1, npix, spp):
+    """Per-pixel normals guiding the filter from the depth-1 features [npix*spp][16]."""
+    f = np.ascontiguousarray(feat1, dtype=np.float64)
+    q = np.ascontiguousarray(q1, dtype=np.float64)
+    out = np.zeros((npix, 4))
+    lib().or_pixel_normals(_p(f), _p(q), npix, spp, _p(out))
+    return out
+
+
 def softplus_mod(x):
     return lib().or_softplus_mod(float(x))
 
@@ -277,14 +364,15 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     with stat_grid (the hash-grid table) StatNet reads the encodings of Sec. 4 (32 inputs,
     stat_params then has 32 inputs) instead of the vertex features; rrsnet_inputs=2 with
     rrs_grid is AID-NRRS (RRSNet on 32 encoded inputs, params then has 32 inputs).
-    With record=True the stats dict also holds "rec": per depth an array [live, 13] of
-    (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child)."""
+    With record=True the stats dict also holds "rec": per depth an array [live, 30] of
+    (S rgb, deposit rgb, t rgb, q_orig, q_used, X, first child, pixel, the 16 vertex
+    features)."""
     h = _SceneHolder(scene)
     P = np.ascontiguousarray(params, dtype=np.float64) if params is not None else None
     ref = np.ascontiguousarray(pixel_ref, dtype=np.float64) if pixel_ref is not None else None
     pix = np.ascontiguousarray(pixels, dtype=np.int32) if pixels is not None else None
     capv = cap if cap > 0 else 2 * width * height * spp
-    rec = np.zeros((max_depth, capv, 13)) if record else None
+    rec = np.zeros((max_depth, capv, 30)) if record else None
     fF = np.ascontiguousarray(forced_F, dtype=np.float32) if forced_F is not None else None
     SP = np.ascontiguousarray(stat_params, dtype=np.float64) if stat_params is not None else None
     SG = np.ascontiguousarray(stat_grid, dtype=np.float64) if stat_grid is not None else None

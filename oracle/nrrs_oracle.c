@@ -250,13 +250,18 @@ void or_sample_lambert(const double n_[3], double u1, double u2, double wi[3]) {
     wi[0] = w.x; wi[1] = w.y; wi[2] = w.z;
 }
 
-static double or_ggx_D(double cos_h, double a) {
+/* GGX normal distribution (Walter et al. 2007, Eq. 33) at cos(theta_h), roughness a:
+ * D = a^2 / (pi ((a^2 - 1) cos^2 + 1)^2), normalised so that the projected microfacet
+ * area integrates to one: integral of D(h) (n.h) over the hemisphere = 1. */
+double or_ggx_D(double cos_h, double a) {
     double a2 = a * a, c2 = cos_h * cos_h;
     double den = (a2 - 1.0) * c2 + 1.0;
     return a2 / (M_PI * den * den);
 }
 
-static double or_ggx_G1(double cos_w, double a) {
+/* Smith masking of GGX (Walter et al. 2007, Eq. 34) for a direction at cos(theta):
+ * G1 = 2 / (1 + sqrt(1 + a^2 tan^2 theta)). */
+double or_ggx_G1(double cos_w, double a) {
     double c2 = cos_w * cos_w;
     double tan2 = (1.0 - c2) / c2;
     return 2.0 / (1.0 + sqrt(1.0 + a * a * tan2));
@@ -331,6 +336,33 @@ int or_eval_bsdf(const or_material* m, const double n_[3], const double wo_[3],
     for (int c = 0; c < 3; ++c) fcos[c] = (spec + (1.0 - F0) * m->albedo[c] / M_PI) * cos_i;
     *pdf = 0.5 * D * cos_h / (4.0 * fabs(oh)) + 0.5 * cos_i / M_PI;
     return 1;
+}
+
+/* or_eval_bsdf for a GGX-mixture material given by its parameters (for the tests). */
+int or_eval_ggx(const double n_[3], const double wo_[3], const double wi_[3],
+                const double albedo[3], double rough, double F0, double fcos[3], double* pdf) {
+    or_material m;
+    memset(&m, 0, sizeof(m));
+    m.type = 1;
+    for (int c = 0; c < 3; ++c) m.albedo[c] = (float)albedo[c];
+    m.roughness = (float)rough;
+    m.F0 = (float)F0;
+    return or_eval_bsdf(&m, n_, wo_, wi_, fcos, pdf);
+}
+
+/* Loops of or_sample_ggx and or_eval_ggx over m directions / sample triples (tests). */
+void or_sample_ggx_batch(const double n_[3], const double wo_[3], double albedo[3], double rough,
+                         double F0, const double* u, int64_t m, double* wi, double* w) {
+    for (int64_t k = 0; k < m; ++k)
+        or_sample_ggx(n_, wo_, albedo, rough, F0, u[3 * k], u[3 * k + 1], u[3 * k + 2],
+                      wi + 3 * k, w + 3 * k);
+}
+
+void or_eval_ggx_batch(const double n_[3], const double wo_[3], const double* wi, int64_t m,
+                       const double albedo[3], double rough, double F0, double* fcos,
+                       double* pdf) {
+    for (int64_t k = 0; k < m; ++k)
+        or_eval_ggx(n_, wo_, wi + 3 * k, albedo, rough, F0, fcos + 3 * k, pdf + k);
 }
 
 /* ------------------------------------------------------------------ RRSNet */
@@ -463,15 +495,15 @@ int64_t or_split(const float* q_orig, int64_t n, float F32, const uint32_t* pixe
                                   depth, lineage[i], &qu, &base);
         X[i] = x;
         prefix[i] = S;
-        for (uint32_t j = 0; j < x; ++j) {
-            int64_t slot = S + j;
-            if (slot < cap) {
-                child_parent[slot] = (uint32_t)i;
-                child_lineage[slot] = base + j * OR_LINEAGE_STEP;
-            } else {
-                ++drop;
-            }
+        /* slots S .. S + x - 1; those at or beyond cap are dropped (counted, not written) */
+        int64_t kept = cap - S;
+        if (kept < 0) kept = 0;
+        if (kept > (int64_t)x) kept = (int64_t)x;
+        for (int64_t j = 0; j < kept; ++j) {
+            child_parent[S + j] = (uint32_t)i;
+            child_lineage[S + j] = base + (uint32_t)j * OR_LINEAGE_STEP;
         }
+        drop += (int64_t)x - kept;
         S += x;
     }
     *dropped = drop;
@@ -543,8 +575,10 @@ static void or_statnet_at(const or_render_args* a, const double x[16], double al
 }
 
 /* Per-vertex record: suffix sum S (rgb), own deposit (rgb), prefix throughput (rgb),
- * q_orig, q_used, X, first child slot. */
-#define OR_REC 13
+ * q_orig, q_used, X, first child slot, pixel, and the 16 vertex features RRSNet reads
+ * (position in the scene box, w_o, shading normal, albedo, d / D, Box-Cox t; zero at
+ * vertices that did not go on to a factor decision). */
+#define OR_REC 30
 
 typedef struct {
     int64_t live[OR_MAX_DEPTH + 1];
@@ -570,6 +604,7 @@ typedef struct {
     int net_fallback;       /* the network's factor was non-finite: q is the heuristic's */
     double emit_w;          /* MIS weight of the emission found here (1 without NEE) */
     double nee[3];          /* next-event contribution, 0 when occluded or not taken */
+    double feat[16];        /* the vertex features (record mode) */
 } or_hitrec;
 
 static double or_lum(const double t[3]) { return 0.2126 * t[0] + 0.7152 * t[1] + 0.0722 * t[2]; }
@@ -757,6 +792,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             v->net_fallback = 0;
             v->emit_w = 1.0;
             v->nee[0] = v->nee[1] = v->nee[2] = 0.0;
+            memset(v->feat, 0, sizeof(v->feat));
             if (v->tri < 0) continue;
             v3 o = mk(p->o[0], p->o[1], p->o[2]), d = mk(p->d[0], p->d[1], p->d[2]);
             v3 hp = add(o, scl(d, t));
@@ -776,6 +812,17 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 v->emit_w = or_power_heuristic(p->pdf, pl);
             }
             if (black || dead || depth == D) continue;
+            {  /* the 16 vertex features of the record (RRSNet's inputs at NET depths) */
+                for (int c = 0; c < 3; ++c) {
+                    double ext = hi[c] - lo[c];
+                    v->feat[c] = ext > 0.0 ? (v->p[c] - lo[c]) / ext : 0.5;
+                }
+                v->feat[3] = -d.x; v->feat[4] = -d.y; v->feat[5] = -d.z;
+                v->feat[6] = ns.x; v->feat[7] = ns.y; v->feat[8] = ns.z;
+                for (int c = 0; c < 3; ++c) v->feat[9 + c] = m->albedo[c];
+                v->feat[12] = (double)depth / (double)D;
+                for (int c = 0; c < 3; ++c) v->feat[13 + c] = or_boxcox(p->t[c], a->boxcox_lambda);
+            }
             if (a->nee) {
                 uint32_t w[4];
                 or_draw(a->seed_lo, a->seed_hi, a->frame, p->pixel, p->sample, (uint32_t)depth,
@@ -945,6 +992,8 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
                 r[10] = (double)qu;
                 r[11] = (double)X;
                 r[12] = (double)S;
+                r[13] = (double)p->pixel;
+                for (int c = 0; c < 16; ++c) r[14 + c] = v->feat[c];
             }
             if (trace) {
                 uint32_t* r = trace + ((int64_t)(depth - 1) * cap + i) * 5;

@@ -28,6 +28,10 @@
  *       Eq. gradient_transfer_splitting_mc (q_used >= 1), the pixel loss shared 1/k_i
  *       among the pixel's k_i training samples (Sec. 3.2), and q_used = F q_nrrs with F
  *       held constant.
+ *   or_error_temporal, or_error_filter, or_pixel_normals
+ *       Sec. 4 "Tackle Low Spp": the temporal EMA of the error map (alpha_mix), and the
+ *       normal-guided spatial filter that stands in for the paper's denoiser, with the
+ *       per-pixel first-hit normals that guide it.
  *   or_adam_step, or_ema
  *       Adam (Kingma & Ba) and the exponential moving average of the weights used for
  *       inference (Sec. 4 "Training").
@@ -205,6 +209,65 @@ void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const dou
     terms[0] = Lavg;
     terms[1] = Lmin;
     terms[2] = Lrrs;
+}
+
+/* Temporal smoothing of the pixel error map, Sec. 4 "Tackle Low Spp" (Eq. error_temporal
+ * applied to the error map, with alpha_mix): E_acc = (1 - alpha) E_acc + alpha E_cur,
+ * and E_acc = E_cur on the first frame. */
+void or_error_temporal(const double* E_cur, double* E_acc, int64_t n, double alpha, int first) {
+    for (int64_t p = 0; p < n; ++p)
+        E_acc[p] = first ? E_cur[p] : (1.0 - alpha) * E_acc[p] + alpha * E_cur[p];
+}
+
+/* The spatial filter of the error map, standing in for the normal-guided denoiser of
+ * Sec. 4 "Tackle Low Spp": out[p] = sum_q w_pq in[q] / sum_q w_pq over the (2r+1)^2
+ * window of p clipped at the image border.  nrm [W*H][4] (unit normal, w > 0 when the
+ * pixel has one) or NULL.  w_pp = 1; without normals, or when p has none or power <= 0,
+ * every w_pq = 1; otherwise w_pq = max(0, n_p . n_q)^power for a neighbour with a
+ * normal and 0 for one without. */
+void or_error_filter(const double* in, const double* nrm, int32_t W, int32_t H, int32_t r,
+                     double power, double* out) {
+    for (int32_t y = 0; y < H; ++y)
+        for (int32_t x = 0; x < W; ++x) {
+            const int64_t p = (int64_t)y * W + x;
+            const int guided = nrm != NULL && power > 0.0 && nrm[4 * p + 3] > 0.0;
+            double s = 0.0, c = 0.0;
+            for (int32_t yy = y - r; yy <= y + r; ++yy)
+                for (int32_t xx = x - r; xx <= x + r; ++xx) {
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    const int64_t q = (int64_t)yy * W + xx;
+                    double w = 1.0;
+                    if (guided && q != p) {
+                        const double d = nrm[4 * p] * nrm[4 * q] + nrm[4 * p + 1] * nrm[4 * q + 1] +
+                                         nrm[4 * p + 2] * nrm[4 * q + 2];
+                        w = nrm[4 * q + 3] > 0.0 && d > 0.0 ? pow(d, power) : 0.0;
+                    }
+                    s += w * in[q];
+                    c += w;
+                }
+            out[p] = s / c;
+        }
+}
+
+/* Normals guiding the filter: per pixel the normalised mean shading normal of its
+ * depth-1 vertices whose factor went on (q_orig > 0), w = 1; (0, 0, 0, 0) when none did.
+ * feat1 [npix * spp][16] holds the vertex features of depth 1 (shading normal at
+ * 6..8), q1 [npix * spp] their q_orig; the samples of pixel p are p * spp .. + spp - 1. */
+void or_pixel_normals(const double* feat1, const double* q1, int64_t npix, int32_t spp,
+                      double* nrm) {
+    for (int64_t p = 0; p < npix; ++p) {
+        double n[3] = {0.0, 0.0, 0.0};
+        int k = 0;
+        for (int32_t s = 0; s < spp; ++s) {
+            const int64_t i = p * spp + s;
+            if (!(q1[i] > 0.0)) continue;
+            for (int c = 0; c < 3; ++c) n[c] += feat1[16 * i + 6 + c];
+            ++k;
+        }
+        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int c = 0; c < 3; ++c) nrm[4 * p + c] = k > 0 && len > 0.0 ? n[c] / len : 0.0;
+        nrm[4 * p + 3] = k > 0 && len > 0.0 ? 1.0 : 0.0;
+    }
 }
 
 /* Adam (Kingma & Ba 2015), step number `step` >= 1. */
