@@ -159,6 +159,16 @@ typedef struct nrrs_render_opts {
                                    (Veach 1997); a vertex's deposit is then its
                                    MIS-weighted emission plus its unoccluded next-event
                                    contribution.  0 = BSDF sampling only            [0]    */
+    const uint8_t* d_trace_mask; /* device [H*W] or NULL: with d_trace, record only the
+                                   queue slots of pixels whose byte is non-zero, as a
+                                   compact list: d_trace is then device [trace_rows][6]
+                                   u32 of (depth, pixel, sample, lineage, triangle or
+                                   0xFFFFFFFF, X) in no fixed order, for sampled pixels
+                                   of frames too large for a whole trace; for tests [NULL] */
+    uint64_t* d_trace_count;    /* with d_trace_mask: device u64 the render adds the rows
+                                   it recorded to (zero it first); rows beyond trace_rows
+                                   are counted, not written                         [NULL] */
+    int64_t trace_rows;         /* rows d_trace holds with d_trace_mask             [0]    */
 } nrrs_render_opts;
 
 /* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
@@ -385,13 +395,19 @@ NRRS_API nrrs_status nrrs_split(nrrs_scene* scene, const float* d_q_orig, int64_
  * engine that gave all device memory to its own arena at start-up, or a frame loop
  * that cannot afford the device-wide synchronization cudaMalloc / cudaFree may cause.
  * Same arguments, layouts, outputs and results as nrrs_split (without `scene`); it
- * runs on the current device.  Its per-block scratch (192 KiB) is a fixed array
- * compiled into the library, present on every GPU that loads it until the process
- * exits; no cudaMalloc, cudaFree or other allocating routine is called.
+ * runs on the current device.  Its per-block scratch (256 KiB: a 64-bit child count
+ * and offset per block) is a fixed array compiled into the library, present on every
+ * GPU that loads it until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called.
  * Limit: n <= 67,108,864 parents (4096 per block, 16384 blocks); larger n returns
  * NRRS_ERR_INVALID_ARG with a message in nrrs_last_error().
- * The first call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture.  Every call shares the one array,
+ * The first call on a device looks up the array's device address (once per device).
+ * Under CUDA's lazy module loading (the default) that lookup is also what loads this
+ * part of the library onto the device: the driver then places its code and the array
+ * in device memory once, which allocates and may synchronize.  A caller that cannot
+ * take that stall makes one call at start-up (n = 0 and cap = 0 suffice; d_F,
+ * d_total and d_dropped must still be device pointers), on each device it will use,
+ * before any stream capture; later calls allocate nothing.  Every call shares the one array,
  * so calls that overlap on the GPU (for example on two streams) race and corrupt each
  * other's results; keep them ordered on one stream. */
 NRRS_API nrrs_status nrrs_split_noalloc(const float* d_q_orig, int64_t n, const float* d_F,
@@ -403,6 +419,24 @@ NRRS_API nrrs_status nrrs_split_noalloc(const float* d_q_orig, int64_t n, const 
                                         int64_t* d_total, int64_t* d_dropped, void* stream);
 
 /* ------------------------------------------------------------------ training */
+
+/* What one training step computed, for checking the step against a reference
+ * implementation: host buffers, each nullable, that nrrs_train_step fills after both
+ * networks' gradients are summed and before its Adam updates (filling them synchronizes
+ * the stream).  Sizes: W*H for the per-pixel arrays; the weight counts of
+ * nrrs_get_params for the gradients. */
+typedef struct nrrs_train_debug {
+    float* grad_statnet;   /* summed StatNet weight gradient the step applies (1/N mean) */
+    float* grad_rrsnet;    /* summed RRSNet weight gradient (warm-up: 1/N mean; full loss:
+                              the sum of Eq. loss-function_rrsnet's gradient)            */
+    float* pixel_var;      /* V_i of the recorded frame (variance of the pixel estimate)  */
+    float* pixel_error;    /* E_i after the temporal EMA and the spatial filter: the map
+                              the loss uses                                              */
+    int32_t* samples;      /* k_i, training samples per pixel                            */
+    float ebar;            /* out: mean of pixel_error                                   */
+    int64_t vertices;      /* out: vertices recorded in the frame                        */
+    int64_t batch;         /* out: training slots drawn from them                        */
+} nrrs_train_debug;
 
 /* One online training step (Sec. 3.2 "Loss Design", Sec. 4 "Training").  Options (NULL =
  * defaults in brackets). */
@@ -439,6 +473,8 @@ typedef struct nrrs_train_opts {
                                               (the paper disables its denoiser for the last
                                               part of training, where it biases the
                                               error); 0 = never off                   [0] */
+    nrrs_train_debug* debug;               /* host, nullable: filled as described at
+                                              nrrs_train_debug                     [NULL] */
 } nrrs_train_opts;
 
 typedef struct nrrs_train_stats {
@@ -572,6 +608,14 @@ NRRS_API nrrs_status nrrs_adam_step(float* d_params, const float* d_grad, float*
                                     int32_t n, int32_t step, float lr, float b1, float b2,
                                     float eps, void* stream);
 
+/* The exponential moving average of the weights that rendering uses (Sec. 4
+ * "Training", as in NRC): d_avg[i] = decay d_avg[i] + (1 - decay) d_params[i] in FP32,
+ * device arrays [n].  nrrs_train_step applies it with decay min(ema_decay,
+ * (1 + t) / (10 + t)) at step t.  Errors: INVALID_ARG (n < 0, NULL with n > 0, decay
+ * outside [0, 1]); CUDA. */
+NRRS_API nrrs_status nrrs_ema(float* d_avg, const float* d_params, int32_t n, float decay,
+                              void* stream);
+
 /* ------------------------------------------------------------------ Mix-Depth */
 
 /* Candidates Mix-Depth evaluates (Sec. 3.3): the depths are cut into segments of t_d
@@ -590,6 +634,8 @@ typedef struct nrrs_mixdepth_opts {
                                               1 = FIXED, ADRRS (NN), NET (the paper's set) */
     int32_t nee;                           /* next-event estimation in the candidate renders
                                               (nrrs_render_opts.nee)                        */
+    int32_t precision;                     /* RRSNet arithmetic of the candidate renders
+                                              (nrrs_render_opts.precision); 0 = 32          */
 } nrrs_mixdepth_opts;
 
 typedef struct nrrs_mixdepth_result {

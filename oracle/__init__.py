@@ -131,6 +131,9 @@ def lib():
         _lib.or_pixel_error.argtypes = [P, C.c_int64, C.c_int32, P, C.c_double, P, P]
         _lib.or_rrsnet_dloss.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int64, P, P, P,
                                          C.c_double, C.c_double, C.c_double, C.c_double, P, P]
+        _lib.or_rrsnet_dloss_at.argtypes = [C.c_int64, P, P, P, P, P, P, P, P, C.c_int64, P, P,
+                                            P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                            P, P]
         _lib.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                       C.c_double, C.c_double]
         _lib.or_ema.argtypes = [P, P, C.c_int64, C.c_double]
@@ -522,7 +525,10 @@ def pixel_error(S1, spp, ref, eps=0.01):
     return V, E
 
 
-def rrsnet_dloss(q_nrrs, F, Fn, t, pixel, m1, m2, E, Iref, k, eps=0.01, g=(0.01, 0.05, 0.01)):
+def rrsnet_dloss(q_nrrs, F, Fn, t, pixel, m1, m2, E, Iref, k, eps=0.01, g=(0.01, 0.05, 0.01),
+                 q_used=None):
+    """d L_RRSNet / d q_nrrs per sample and (L_avg, L_min, L_rrs); q_used: the factor the
+    frame was split with (default F q_nrrs)."""
     a = [np.ascontiguousarray(v, dtype=np.float64) for v in (q_nrrs, F, Fn, t, m1, m2)]
     pixel = np.ascontiguousarray(pixel, dtype=np.int32)
     E = np.ascontiguousarray(E, dtype=np.float64)
@@ -531,9 +537,10 @@ def rrsnet_dloss(q_nrrs, F, Fn, t, pixel, m1, m2, E, Iref, k, eps=0.01, g=(0.01,
     n = a[0].shape[0]
     dq = np.zeros(n)
     terms = np.zeros(3)
-    lib().or_rrsnet_dloss(n, _p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), _p(pixel), _p(a[4]), _p(a[5]),
-                          E.shape[0], _p(E), _p(Iref), _p(k), eps, g[0], g[1], g[2], _p(dq),
-                          _p(terms))
+    qu = np.ascontiguousarray(q_used, dtype=np.float64) if q_used is not None else None
+    lib().or_rrsnet_dloss_at(n, _p(a[0]), _p(a[1]), _p(a[2]), _p(qu), _p(a[3]), _p(pixel),
+                             _p(a[4]), _p(a[5]), E.shape[0], _p(E), _p(Iref), _p(k), eps, g[0],
+                             g[1], g[2], _p(dq), _p(terms))
     return dq, terms
 
 

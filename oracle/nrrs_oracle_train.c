@@ -177,11 +177,16 @@ void or_pixel_error(const double* S1, int64_t npix, int32_t spp, const double* r
  * Fn of Eq. F_norm without rate control (q_norm = Fn q_nrrs, a constant), the mean
  * prefix throughput t, the pixel, and the StatNet moments m1 = E[<H>], m2 = E[<H>^2]
  * (means over RGB).  Per pixel: E_i, the reference I_i (mean over RGB) and the count k_i
- * of training samples.  terms[0..2] receive L_avg, L_min and L_rrs. */
-void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const double* Fn,
-                     const double* t, const int32_t* pixel, const double* m1, const double* m2,
-                     int64_t npix, const double* E, const double* Iref, const int64_t* k,
-                     double eps, double g1, double g2, double g3, double* dq, double* terms) {
+ * of training samples.  terms[0..2] receive L_avg, L_min and L_rrs.
+ * q_used (nullable) is the factor each sample's frame was split with; the gradient
+ * transfer of Eq. gradient_transfer_rr_mc / splitting_mc is taken at it, since the
+ * variance it differentiates is that of the frame as sampled (NULL: q_used = F q_nrrs,
+ * the case when the frame was rendered with the trained weights). */
+void or_rrsnet_dloss_at(int64_t n, const double* q_nrrs, const double* F, const double* Fn,
+                        const double* q_used, const double* t, const int32_t* pixel,
+                        const double* m1, const double* m2, int64_t npix, const double* E,
+                        const double* Iref, const int64_t* k, double eps, double g1, double g2,
+                        double g3, double* dq, double* terms) {
     double Ebar = 0.0;
     for (int64_t p = 0; p < npix; ++p) Ebar += E[p];
     Ebar /= (double)npix;
@@ -192,7 +197,7 @@ void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const dou
     }
     for (int64_t s = 0; s < n; ++s) {
         const int32_t i = pixel[s];
-        const double qu = F[s] * q_nrrs[s];
+        const double qu = q_used ? q_used[s] : F[s] * q_nrrs[s];
         /* dV_i/dq_used: Eq. gradient_transfer_rr_mc for roulette (q_used < 1),
          * Eq. gradient_transfer_splitting_mc for splitting (q_used >= 1) */
         const double VH = fmax(m2[s] - m1[s] * m1[s], 0.0);
@@ -209,6 +214,14 @@ void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const dou
     terms[0] = Lavg;
     terms[1] = Lmin;
     terms[2] = Lrrs;
+}
+
+void or_rrsnet_dloss(int64_t n, const double* q_nrrs, const double* F, const double* Fn,
+                     const double* t, const int32_t* pixel, const double* m1, const double* m2,
+                     int64_t npix, const double* E, const double* Iref, const int64_t* k,
+                     double eps, double g1, double g2, double g3, double* dq, double* terms) {
+    or_rrsnet_dloss_at(n, q_nrrs, F, Fn, NULL, t, pixel, m1, m2, npix, E, Iref, k, eps, g1, g2,
+                       g3, dq, terms);
 }
 
 /* Temporal smoothing of the pixel error map, Sec. 4 "Tackle Low Spp" (Eq. error_temporal

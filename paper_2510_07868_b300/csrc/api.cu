@@ -68,7 +68,7 @@ struct Workspace {
     float4* dep = nullptr;
     float4* feat = nullptr;
     double* part = nullptr;
-    unsigned int* bcnt = nullptr;
+    unsigned long long* bcnt = nullptr;
     unsigned long long* boff = nullptr;
     float4* acc_s = nullptr;
     float4* acc_c = nullptr;
@@ -114,7 +114,7 @@ struct Workspace {
 // Scratch for the plain-array stage entry points called without a scene.
 struct Pool {
     double* part = nullptr;
-    unsigned int* bcnt = nullptr;
+    unsigned long long* bcnt = nullptr;
     unsigned long long* boff = nullptr;
     int grid = 0;
 };
@@ -162,7 +162,11 @@ struct TrainState {
     float *rrs_raw = nullptr, *rrs_m = nullptr, *rrs_v = nullptr, *rrs_good = nullptr;
     float *stat = nullptr, *stat_m = nullptr, *stat_v = nullptr, *stat_good = nullptr;
     float *grad_rrs = nullptr, *grad_stat = nullptr, *part = nullptr;
-    double *loss_part = nullptr, *scal = nullptr;
+    float* loss_part = nullptr;
+    double* scal = nullptr;       // relMSE of the Mix-Depth candidates (nrrs_relmse's layout)
+    float* fscal = nullptr;       // [0] Ebar, [1] L_min, [2] L_avg, [3] StatNet loss, [4] RRSNet loss
+    long long* kpart = nullptr;   // per-block sample counts of the pixel terms
+    long long* nsamp = nullptr;   // training samples N
     float *Fd = nullptr, *Fnd = nullptr;
     int* bad = nullptr;
     int part_blocks = 0;
@@ -207,6 +211,9 @@ struct TrainState {
         dx_cap = 0;
         cudaFree(loss_part);
         cudaFree(scal);
+        cudaFree(fscal);
+        cudaFree(kpart);
+        cudaFree(nsamp);
         cudaFree(bad);
         nets = false;
     }
@@ -665,6 +672,8 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
         return fail(NRRS_ERR_UNSUPPORTED, "AID-NRRS inputs run in FP32 (precision 32)");
     const long long C = (long long)width * height * spp * o.cap_factor;
     if (C >= (1ll << 31)) return fail(NRRS_ERR_INVALID_ARG, "capacity W*H*spp*cap_factor >= 2^31");
+    if (o.d_trace && o.d_trace_mask && (!o.d_trace_count || o.trace_rows < 1))
+        return fail(NRRS_ERR_INVALID_ARG, "a masked trace needs d_trace_count and trace_rows >= 1");
     return NRRS_OK;
 }
 
@@ -842,6 +851,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     rp.ref = uses_heur ? ref : nullptr;
     rp.params = params ? params : scene->params;
     rp.trace = o.d_trace;
+    rp.trace_mask = o.d_trace ? o.d_trace_mask : nullptr;
+    rp.trace_count = reinterpret_cast<unsigned long long*>(o.d_trace_count);
+    rp.trace_rows = o.trace_rows;
     rp.nee = nee ? 1 : 0;
     rp.stat_grid = scene->train.nets && scene->train.stat_enc
                        ? reinterpret_cast<const float2*>(scene->train.grid)
@@ -1010,7 +1022,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)rp.stat_grid,
                                (uint64_t)(uintptr_t)(rec ? rec->rough : nullptr),
                                (uint64_t)scene->rrsnet_inputs,
-                               (uint64_t)(uintptr_t)scene->train.rgrid};
+                               (uint64_t)(uintptr_t)scene->train.rgrid,
+                               (uint64_t)(uintptr_t)rp.trace_mask,
+                               (uint64_t)(uintptr_t)rp.trace_count, (uint64_t)rp.trace_rows};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -1443,6 +1457,9 @@ nrrs_status ensure_train_nets(nrrs_scene* sc, cudaStream_t s) {
     CK(dalloc(&t.part, (size_t)t.part_blocks * kStatParamsMax));
     CK(dalloc(&t.loss_part, t.part_blocks));
     CK(dalloc(&t.scal, 8));
+    CK(dalloc(&t.fscal, 8));
+    CK(dalloc(&t.kpart, t.part_blocks));
+    CK(dalloc(&t.nsamp, 1));
     CK(dalloc(&t.Fd, kMaxDepth));
     CK(dalloc(&t.Fnd, kMaxDepth));
     CK(dalloc(&t.bad, 1));
@@ -1754,8 +1771,16 @@ nrrs_status nrrs_rrsnet_dloss(const float* d_q_nrrs, const float* d_F, const flo
     if (n < 0 || (n > 0 && (!d_q_nrrs || !d_F || !d_Fn || !d_t || !d_pixel || !d_m1 || !d_m2 ||
                             !d_E || !d_Iref || !d_k || !d_dq)))
         return fail(NRRS_ERR_INVALID_ARG, "bad rrsnet_dloss arguments");
-    launch_rrsnet_dloss(d_q_nrrs, d_F, d_Fn, d_t, d_pixel, d_m1, d_m2, d_E, Ebar, d_Iref, d_k, n,
+    launch_rrsnet_dloss(d_q_nrrs, d_F, d_Fn, d_t, d_pixel, d_m1, d_m2, d_E, (float)Ebar, d_Iref, d_k, n,
                         eps, g1, g2, g3, d_dq, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_ema(float* d_avg, const float* d_params, int32_t n, float decay, void* stream) {
+    if (n < 0 || (n > 0 && (!d_avg || !d_params)) || !(decay >= 0.0f && decay <= 1.0f))
+        return fail(NRRS_ERR_INVALID_ARG, "bad ema arguments");
+    if (n > 0) launch_ema(d_avg, d_params, n, decay, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NRRS_OK;
 }
@@ -1830,7 +1855,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;  // splitmix64 finaliser
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
-        b.phase = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        b.phase = (uint32_t)(z >> 32);
     }
     CK(cudaMemcpy(t.Fd, Fh, sizeof(float) * D, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(t.Fnd, Fnh, sizeof(float) * D, cudaMemcpyHostToDevice));
@@ -1858,12 +1883,15 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     CK(cudaMemsetAsync(t.k, 0, sizeof(int) * npix, s));
     launch_count_samples(t.rec, b, t.k, scene->n_sm * 4, s);
     // Ebar, then L_min, L_avg, N (the partials borrow the gradient scratch)
-    launch_pixel_terms(t.E, npix, t.k, reinterpret_cast<double*>(t.part), t.part_blocks / 2,
-                       t.scal + 0, t.scal + 4, s);
-    double host_terms[3];
-    CK(cudaMemcpyAsync(host_terms, t.scal + 4, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    launch_pixel_terms(t.E, npix, t.k, t.part, t.kpart, t.part_blocks, t.fscal + 0, t.fscal + 1,
+                       t.nsamp, s);
+    float fterms[2];
+    long long n_samples = 0;
+    CK(cudaMemcpyAsync(fterms, t.fscal + 1, sizeof(float) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&n_samples, t.nsamp, sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double N = host_terms[2];
+    const double host_terms[2] = {fterms[0], fterms[1]};  // L_min, L_avg
+    const double N = (double)n_samples;
 
     // 3. StatNet (moments for the gradient transfer), then RRSNet
     TrainArgs a{};
@@ -1872,7 +1900,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     a.F = t.Fd;
     a.Fn = t.Fnd;
     a.E = t.E;
-    a.Ebar = t.scal + 0;
+    a.Ebar = t.fscal + 0;
     a.ref = ref;
     a.k = t.k;
     a.eps = o.eps;
@@ -1900,7 +1928,7 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     a.lambda = 0.5f;  // the training frame's Box-Cox lambda (render default)
     CK(launch_mlp_train(kTrainStatNet, a, t.rec, b, t.part_blocks, t.part, t.loss_part, s));
     launch_reduce_grad(t.part, t.part_blocks, stat_n, t.grad_stat, s);
-    launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 1, s);
+    launch_reduce_loss(t.loss_part, t.part_blocks, t.fscal + 3, s);
     if (t.stat_enc) {
         CK(cudaMemsetAsync(t.grid_grad, 0, sizeof(float) * (size_t)kGridParams, s));
         launch_grid_scatter(a, t.rec, b, scene->n_sm * 8, t.grid_grad, s);
@@ -1917,7 +1945,26 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
     CK(launch_mlp_train(warm ? kTrainRrsWarmup : kTrainRrsFull, a, t.rec, b, t.part_blocks, t.part,
                         t.loss_part, s));
     launch_reduce_grad(t.part, t.part_blocks, rrs_np, t.grad_rrs, s);
-    launch_reduce_loss(t.loss_part, t.part_blocks, t.scal + 2, s);
+    launch_reduce_loss(t.loss_part, t.part_blocks, t.fscal + 4, s);
+    if (o.debug) {  // what the step is about to apply, for checks against a reference
+        nrrs_train_debug& dbg = *o.debug;
+        if (dbg.grad_statnet)
+            CK(cudaMemcpyAsync(dbg.grad_statnet, t.grad_stat, sizeof(float) * stat_n,
+                               cudaMemcpyDeviceToHost, s));
+        if (dbg.grad_rrsnet)
+            CK(cudaMemcpyAsync(dbg.grad_rrsnet, t.grad_rrs, sizeof(float) * rrs_np,
+                               cudaMemcpyDeviceToHost, s));
+        if (dbg.pixel_var)
+            CK(cudaMemcpyAsync(dbg.pixel_var, t.V, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
+        if (dbg.pixel_error)
+            CK(cudaMemcpyAsync(dbg.pixel_error, t.E, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
+        if (dbg.samples)
+            CK(cudaMemcpyAsync(dbg.samples, t.k, sizeof(int) * npix, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&dbg.ebar, t.fscal + 0, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        dbg.vertices = b.total;
+        dbg.batch = b.batch;
+    }
     if (aid) {
         CK(cudaMemsetAsync(t.rgrid_grad, 0, sizeof(float) * (size_t)kGridParams, s));
         launch_grid_scatter(a, t.rec, b, scene->n_sm * 8, t.rgrid_grad, s);
@@ -1937,10 +1984,11 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         launch_adam(t.rgrid_raw, t.rgrid_grad, t.rgrid_m, t.rgrid_v, (int)kGridParams, step,
                     o.lr_rrsnet, 0.9f, 0.999f, 1e-15f, t.bad, s);
     int bad = 0;
-    double losses[2];
+    float flosses[2];
     CK(cudaMemcpyAsync(&bad, t.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(losses, t.scal + 1, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(flosses, t.fscal + 3, sizeof(float) * 2, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const double losses[2] = {flosses[0], flosses[1]};
     const double loss_stat = N > 0 ? losses[0] / N : 0.0;
     const double loss_rrs_warm = N > 0 ? losses[1] / N : 0.0;
     const double L_rrs = losses[1];
@@ -2078,6 +2126,7 @@ nrrs_status nrrs_mixdepth_search(nrrs_scene* scene, const nrrs_mixdepth_opts* op
     ro.frame = o.frame;  // every candidate sees the same random numbers
     ro.update_ref = 0;
     ro.nee = o.nee;
+    ro.precision = o.precision == 0 ? 32 : o.precision;
     nrrs_status rc = validate_render(scene, o.width, o.height, o.spp, D, NRRS_RRS_NET_MIX, ro);
     if (rc != NRRS_OK) return rc;
     DeviceGuard g(scene->device);

@@ -11,7 +11,10 @@
 // The scratch below lives in every GPU that loads the library until the process exits.
 // Host code may not use `g_split_scratch` as a device address (on the host it names a
 // stand-in object); the device address comes from cudaGetSymbolAddress, taken once
-// per device with that device current, on the first call made on that device.
+// per device with that device current, on the first call made on that device.  With
+// lazy module loading (CUDA's default) that lookup is what loads this file's module on
+// the device, which places its code and the array in device memory once; callers that
+// cannot take that one-time allocation make a first call at start-up.
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -29,10 +32,10 @@ constexpr long long kNoAllocMaxN = kNoAllocChunk * kNoAllocMaxBlocks;
 
 struct SplitScratch {
     unsigned long long boff[kNoAllocMaxBlocks];  // exclusive prefix of the block counts
-    unsigned int bcnt[kNoAllocMaxBlocks];        // children requested per block
+    unsigned long long bcnt[kNoAllocMaxBlocks];  // children requested per block
 };
 
-// 192 KiB per device, shared by every call.
+// 256 KiB per device, shared by every call.
 static __device__ __align__(256) SplitScratch g_split_scratch;
 
 constexpr int kMaxDevices = 64;

@@ -15,6 +15,73 @@ constexpr int kTile = 128;  // samples per block tile of the training kernel
 
 __device__ __forceinline__ uint32_t fb(float f) { return __float_as_uint(f); }
 
+// Compensated (Kahan) sum in FP32: the running error of the additions is carried in c.
+struct KahanSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// Count, mean and sum of squared deviations of a set of values (Welford), merged with
+// Chan et al.'s pairwise rule, in FP32: the sum of squared deviations is accumulated
+// directly, never as the difference sum x^2 - n mean^2.
+struct Moments {
+    float n = 0.0f, mean = 0.0f, m2 = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        n += 1.0f;
+        const float d = x - mean;
+        mean += d / n;
+        m2 += d * (x - mean);
+    }
+    __device__ __forceinline__ void merge(const Moments& b) {
+        const float nn = n + b.n;
+        if (b.n == 0.0f) return;
+        if (n == 0.0f) { *this = b; return; }
+        const float d = b.mean - mean;
+        const float f = b.n / nn;
+        mean += d * f;
+        m2 += b.m2 + d * d * n * f;
+        n = nn;
+    }
+};
+
+// Block-wide merge of per-thread moments in a fixed order (lane i takes lane i + o,
+// then warp 0 merges the warp results); thread 0 returns the result.
+__device__ Moments block_merge(Moments v, float* sh /* 3 * 32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Moments u;
+        u.n = __shfl_down_sync(0xffffffffu, v.n, o);
+        u.mean = __shfl_down_sync(0xffffffffu, v.mean, o);
+        u.m2 = __shfl_down_sync(0xffffffffu, v.m2, o);
+        if ((lane & (2 * o - 1)) == 0 && lane + o < 32) v.merge(u);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[3 * wid] = v.n;
+        sh[3 * wid + 1] = v.mean;
+        sh[3 * wid + 2] = v.m2;
+    }
+    __syncthreads();
+    Moments r;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) {
+            Moments u;
+            u.n = sh[3 * w];
+            u.mean = sh[3 * w + 1];
+            u.m2 = sh[3 * w + 2];
+            r.merge(u);
+        }
+    __syncthreads();
+    return r;
+}
+
 // ------------------------------------------------------------------ reverse pass
 // Suffix sums of depth d: S = own deposit + sum of the children's S (children of slot i
 // are the slots [first_i, first_i + X_i) of depth d+1 that fit in the queue).  S / t is
@@ -47,25 +114,27 @@ __global__ void k_pixel_error(RecordView r, int spp, long long npix, const float
                               float* V, float* E) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    double v = 0.0;
+    // two passes per channel in FP32: the mean, then the squared deviations from it
+    float v = 0.0f;
     for (int c = 0; c < 3; ++c) {
-        double m = 0.0;
+        KahanSum m;
         for (int s = 0; s < spp; ++s) {
             const float4 S = r.S[p * spp + s];
-            m += c == 0 ? S.x : c == 1 ? S.y : S.z;
+            m.add(c == 0 ? S.x : c == 1 ? S.y : S.z);
         }
-        m /= spp;
-        double q = 0.0;
+        const float mean = m.value() / (float)spp;
+        KahanSum q;
         for (int s = 0; s < spp; ++s) {
             const float4 S = r.S[p * spp + s];
-            const double dd = (c == 0 ? S.x : c == 1 ? S.y : S.z) - m;
-            q += dd * dd;
+            const float dd = (c == 0 ? S.x : c == 1 ? S.y : S.z) - mean;
+            q.add(dd * dd);
         }
-        v += spp > 1 ? q / (spp - 1) / spp : 0.0;
+        v += spp > 1 ? q.value() / (float)(spp - 1) / (float)spp : 0.0f;
     }
-    V[p] = (float)(v / 3.0);
-    const double I = ref ? ((double)ref[3 * p] + ref[3 * p + 1] + ref[3 * p + 2]) / 3.0 : 0.0;
-    E[p] = (float)(v / 3.0 / (I * I + eps));
+    v *= 1.0f / 3.0f;
+    V[p] = v;
+    const float I = ref ? (ref[3 * p] + ref[3 * p + 1] + ref[3 * p + 2]) * (1.0f / 3.0f) : 0.0f;
+    E[p] = v / (I * I + eps);
 }
 
 // Temporal smoothing of the error map (Sec. 4 "Tackle Low Spp", Eq. error_temporal with
@@ -83,10 +152,10 @@ __global__ void k_error_temporal(const float* E_cur, float* E_acc, long long n, 
 // every weight is 1 (a box filter).  With normals, a pixel that has one weighs a
 // neighbour with a normal by max(0, n_p . n_q)^power and one without by 0; a pixel
 // without a normal weighs every neighbour by 1.  The centre always has weight 1.
-// An integral power (ipow >= 0) is raised by repeated squaring (FP64 pow is slow on
-// this GPU; the squarings differ from it by a few FP64 roundings).
-__device__ __forceinline__ double pow_by_squaring(double b, int n) {
-    double r = 1.0;
+// An integral power (ipow >= 0) is raised by repeated squaring, others by powf; the
+// window's sums are compensated FP32 sums.
+__device__ __forceinline__ float pow_by_squaring(float b, int n) {
+    float r = 1.0f;
     for (; n > 0; n >>= 1) {
         if (n & 1) r *= b;
         b *= b;
@@ -101,22 +170,22 @@ __global__ void k_error_filter(const float* in, const float4* nrm, int W, int H,
     const int x = (int)(p % W), y = (int)(p / W);
     const float4 np = nrm ? nrm[p] : make_float4(0.f, 0.f, 0.f, 0.f);
     const bool guided = nrm && np.w > 0.0f;
-    double s = 0.0, c = 0.0;
+    KahanSum s, c;
     for (int yy = max(0, y - r); yy <= min(H - 1, y + r); ++yy)
         for (int xx = max(0, x - r); xx <= min(W - 1, x + r); ++xx) {
             const long long q = (long long)yy * W + xx;
-            double wq = 1.0;
+            float wq = 1.0f;
             if (guided && q != p) {
                 const float4 nq = nrm[q];
                 const float d = np.x * nq.x + np.y * nq.y + np.z * nq.z;
-                wq = !(nq.w > 0.0f && d > 0.0f) ? 0.0
-                     : ipow >= 0                   ? pow_by_squaring((double)d, ipow)
-                                                   : pow((double)d, (double)power);
+                wq = !(nq.w > 0.0f && d > 0.0f) ? 0.0f
+                     : ipow >= 0                   ? pow_by_squaring(d, ipow)
+                                                   : powf(d, power);
             }
-            s += wq * in[q];
-            c += wq;
+            s.add(wq * in[q]);
+            c.add(wq);
         }
-    out[p] = (float)(s / c);
+    out[p] = s.value() / c.value();
 }
 
 __global__ void k_pixel_normals(RecordView r, int spp, long long npix, float4* nrm) {
@@ -160,65 +229,73 @@ __global__ void k_count_samples(RecordView r, TrainBatch b, int* k) {
     }
 }
 
-// Pixel-error terms in FP64, two fixed-order passes: per block (one contiguous chunk of
-// pixels) the sums of E, E^2 and k; then one block folds them into
-// Ebar = sum E / n, L_min = sum_i E_i and L_avg = sum_i (E_i - Ebar)^2 = sum E^2 - n Ebar^2
-// (Eq. loss-function_min / _avg) and N = sum_i k_i, the training samples.
-__global__ void k_pixel_partial(const float* E, long long n, const int* k, double* part) {
-    __shared__ double sh[32];
+// Pixel-error terms, two fixed-order passes in FP32: per block (one contiguous chunk
+// of pixels) the count, mean and sum of squared deviations of E (Welford per thread,
+// Chan's merge across threads) and the exact integer sum of k; then one block merges
+// the blocks in order into Ebar = mean E, L_min = sum_i E_i = n Ebar and
+// L_avg = sum_i (E_i - Ebar)^2 (Eq. loss-function_min / _avg), and N = sum_i k_i, the
+// training samples.
+__global__ void k_pixel_partial(const float* E, long long n, const int* k, float* part,
+                                long long* kpart) {
+    __shared__ float sh[96];
+    __shared__ long long shk[32];
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk;
     const long long hi = lo + chunk < n ? lo + chunk : n;
-    double a = 0.0, b = 0.0, c = 0.0;
+    Moments m;
+    long long c = 0;
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double e = E[i];
-        a += e;
-        b += e * e;
+        m.add(E[i]);
         c += k[i];
     }
-    a = block_sum(a, sh);
-    b = block_sum(b, sh);
-    c = block_sum(c, sh);
+    m = block_merge(m, sh);
+    c = block_sum(c, shk);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x + 0] = a;
-        part[3 * blockIdx.x + 1] = b;
-        part[3 * blockIdx.x + 2] = c;
+        part[3 * blockIdx.x + 0] = m.n;
+        part[3 * blockIdx.x + 1] = m.mean;
+        part[3 * blockIdx.x + 2] = m.m2;
+        kpart[blockIdx.x] = c;
     }
 }
 
-__global__ void k_pixel_final(const double* part, int G, long long n, double* Ebar,
-                              double* out) {
-    __shared__ double sh[32];
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        a += part[3 * g + 0];
-        b += part[3 * g + 1];
-        c += part[3 * g + 2];
+__global__ void k_pixel_final(const float* part, const long long* kpart, int G, float* Ebar,
+                              float* out, long long* nsamples) {
+    __shared__ float sh[96];
+    __shared__ long long shk[32];
+    Moments m;
+    long long c = 0;
+    // each thread merges a contiguous run of blocks, so the order stays the blocks'
+    const int per = (G + blockDim.x - 1) / blockDim.x;
+    for (int g = threadIdx.x * per; g < (int)(threadIdx.x + 1) * per && g < G; ++g) {
+        Moments u;
+        u.n = part[3 * g + 0];
+        u.mean = part[3 * g + 1];
+        u.m2 = part[3 * g + 2];
+        m.merge(u);
+        c += kpart[g];
     }
-    a = block_sum(a, sh);
-    b = block_sum(b, sh);
-    c = block_sum(c, sh);
+    m = block_merge(m, sh);
+    c = block_sum(c, shk);
     if (threadIdx.x == 0) {
-        const double eb = n > 0 ? a / (double)n : 0.0;
-        *Ebar = eb;
-        out[0] = a;
-        const double v = b - (double)n * eb * eb;
-        out[1] = v > 0.0 ? v : 0.0;
-        out[2] = c;
+        *Ebar = m.mean;
+        out[0] = m.mean * m.n;
+        out[1] = m.m2 > 0.0f ? m.m2 : 0.0f;
+        *nsamples = c;
     }
 }
 
-// relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + eps), FP64, fixed order.
-__global__ void k_relmse(const float* img, const float* ref, long long n3, double eps,
+// relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + eps), fixed order:
+// compensated FP32 sums per thread, then the block's sum.
+__global__ void k_relmse(const float* img, const float* ref, long long n3, float eps,
                          double* out) {
-    __shared__ double sh[32];
-    double s = 0.0;
+    __shared__ float sh[32];
+    KahanSum k;
     for (long long i = threadIdx.x; i < n3; i += blockDim.x) {
-        const double d = (double)img[i] - ref[i];
-        s += d * d / ((double)ref[i] * ref[i] + eps);
+        const float d = img[i] - ref[i];
+        k.add(d * d / (ref[i] * ref[i] + eps));
     }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) *out = n3 > 0 ? s / (double)n3 : 0.0;
+    const float s = block_sum(k.value(), sh);
+    if (threadIdx.x == 0) *out = n3 > 0 ? (double)(s / (float)n3) : 0.0;
 }
 
 // ------------------------------------------------------------------ MLP training
@@ -241,7 +318,7 @@ __device__ __forceinline__ float lrelu(float a) { return a > 0.0f ? a : kLeak * 
 template <int MODE>
 __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView& r, int d,
                                             long long i, const float* out, float* gout,
-                                            double* loss) {
+                                            KahanSum* loss) {
     const size_t g = (size_t)d * r.C + i;
     const float4 dep = r.dep[g];
     const float4 t = r.t[g];
@@ -259,7 +336,7 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
             const float d1 = out[c] - L, d2 = out[3 + c] - L2;
             gout[c] = 2.0f * d1 * w1 * a.scale;
             gout[3 + c] = 2.0f * d2 * w2 * a.scale;
-            *loss += (double)(d1 * d1 * w1 + d2 * d2 * w2);
+            loss->add(d1 * d1 * w1 + d2 * d2 * w2);
         }
         return true;
     }
@@ -271,7 +348,7 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
     if (MODE == kTrainRrsWarmup) {
         // Sec. 4 "Training" step (1): regress to 1 with the relative L2 loss
         dq = 2.0f * (q - 1.0f) / (1.0f + a.eps);
-        *loss += (double)((q - 1.0f) * (q - 1.0f) / (1.0f + a.eps));
+        loss->add((q - 1.0f) * (q - 1.0f) / (1.0f + a.eps));
     } else {
         const float F = a.F[d], Fn = a.Fn[d];
         const float qu = F * r.q[g];  // factor the frame actually used
@@ -284,11 +361,11 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
         const float I = a.ref ? (a.ref[3 * pix] + a.ref[3 * pix + 1] + a.ref[3 * pix + 2]) *
                                     (1.0f / 3.0f)
                               : 0.0f;
-        const float dLdE = a.g1 * 2.0f * (a.E[pix] - (float)*a.Ebar) + a.g2;
+        const float dLdE = a.g1 * 2.0f * (a.E[pix] - *a.Ebar) + a.g2;
         const float dLdV = dLdE / (I * I + a.eps) / (float)max(a.k[pix], 1);
         const float qn = Fn * q;  // stop-gradient target of L_rrs
         dq = dLdV * dV * F + a.g3 * 2.0f * (q - qn);
-        *loss += (double)((q - qn) * (q - qn));
+        loss->add((q - qn) * (q - qn));
     }
     gout[0] = dq * dqdz * a.scale;
     return true;
@@ -302,7 +379,7 @@ __device__ __forceinline__ bool sample_grad(const TrainArgs& a, const RecordView
 // and roughness), which also writes the gradient at its 16 grid features per slot.
 template <int NOUT, int MODE, int KIN = kNF>
 __global__ void __launch_bounds__(kTile, KIN == kNF ? 3 : 2)  // 32 inputs: 2 tiles fit in smem
-k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_part) {
+k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, float* loss_part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem<KIN>& sm = *reinterpret_cast<TrainSmem<KIN>*>(smem_raw);
     float* W = reinterpret_cast<float*>(smem_raw + sizeof(TrainSmem<KIN>));
@@ -321,7 +398,7 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
 #pragma unroll
     for (int e = 0; e < 8; ++e) g2[e] = g3[e] = 0.0f;
     g4[0] = g4[1] = 0.0f;
-    double loss = 0.0;
+    KahanSum loss;
     const long long tiles = (b.batch + kTile - 1) / kTile;
     __syncthreads();
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -528,9 +605,9 @@ k_mlp_train(TrainArgs a, RecordView r, TrainBatch b, float* part, double* loss_p
         const int p = tid + e * kTile;
         if (p < NOUT * kNH) pb[kNH * KIN + 2 * kNH * kNH + p] = g4[e];
     }
-    __shared__ double shl[32];
-    loss = block_sum(loss, shl);
-    if (tid == 0) loss_part[blockIdx.x] = loss;
+    __shared__ float shl[32];
+    const float lsum = block_sum(loss.value(), shl);
+    if (tid == 0) loss_part[blockIdx.x] = lsum;
 }
 
 // Sum of the per-block gradients in block order (deterministic).
@@ -542,11 +619,11 @@ __global__ void k_reduce_grad(const float* part, int G, int P, float* grad) {
     grad[p] = s;
 }
 
-__global__ void k_reduce_loss(const double* part, int G, double* out) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[b];
-    s = block_sum(s, sh);
+__global__ void k_reduce_loss(const float* part, int G, float* out) {
+    __shared__ float sh[32];
+    KahanSum k;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) k.add(part[b]);
+    const float s = block_sum(k.value(), sh);
     if (threadIdx.x == 0) *out = s;
 }
 
@@ -577,7 +654,7 @@ __global__ void k_ema(float* E, const float* P, int n, float decay) {
 // Stand-alone loss gradient on plain arrays (for parity tests): one thread per sample.
 __global__ void k_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn,
                                const float* t, const int* pixel, const float* m1, const float* m2,
-                               const float* E, double Ebar, const float* Iref,
+                               const float* E, float Ebar, const float* Iref,
                                const int* k, long long n, float eps, float g1, float g2,
                                float g3, float* dq) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -587,7 +664,7 @@ __global__ void k_rrsnet_dloss(const float* q_nrrs, const float* F, const float*
     const float VH = fmaxf(m2[s] - m1[s] * m1[s], 0.0f);
     const float H = qu < 1.0f ? m2[s] : VH;
     const float dV = -t[s] * t[s] * H / (qu * qu);
-    const float dLdE = g1 * 2.0f * (E[i] - (float)Ebar) + g2;
+    const float dLdE = g1 * 2.0f * (E[i] - Ebar) + g2;
     const float dLdV = dLdE / (Iref[i] * Iref[i] + eps) / (float)max(k[i], 1);
     dq[s] = dLdV * dV * F[s] + g3 * 2.0f * (q_nrrs[s] - Fn[s] * q_nrrs[s]);
 }
@@ -599,7 +676,7 @@ size_t train_smem() {
 
 template <int NOUT, int MODE, int KIN = kNF>
 cudaError_t launch_train_t(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
-                           float* part, double* loss_part, cudaStream_t s) {
+                           float* part, float* loss_part, cudaStream_t s) {
     const size_t smem = train_smem<NOUT, MODE, KIN>();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train<NOUT, MODE, KIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -652,7 +729,7 @@ void launch_count_samples(const RecordView& r, const TrainBatch& b, int* k, int 
 
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s) {
-    k_relmse<<<1, 1024, 0, s>>>(img, ref, n3, eps, out);
+    k_relmse<<<1, 1024, 0, s>>>(img, ref, n3, (float)eps, out);
 }
 
 // power as an exponent for repeated squaring, or -1 when it is not a small integer
@@ -689,14 +766,15 @@ void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cuda
     k_ref_fold<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(ref, rgb, n3, count);
 }
 
-void launch_pixel_terms(const float* E, long long n, const int* k, double* part, int G,
-                        double* Ebar, double* out, cudaStream_t s) {
-    k_pixel_partial<<<G, 256, 0, s>>>(E, n, k, part);
-    k_pixel_final<<<1, 256, 0, s>>>(part, G, n, Ebar, out);
+void launch_pixel_terms(const float* E, long long n, const int* k, float* part,
+                        long long* kpart, int G, float* Ebar, float* out, long long* nsamples,
+                        cudaStream_t s) {
+    k_pixel_partial<<<G, 256, 0, s>>>(E, n, k, part, kpart);
+    k_pixel_final<<<1, 256, 0, s>>>(part, kpart, G, Ebar, out, nsamples);
 }
 
 cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
-                             const TrainBatch& b, int grid, float* part, double* loss_part,
+                             const TrainBatch& b, int grid, float* part, float* loss_part,
                              cudaStream_t s) {
     switch (which) {
         case kTrainStatNet:
@@ -716,7 +794,7 @@ cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
 }
 
 cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
-                                  const TrainBatch& b, int grid, float* part, double* loss_part,
+                                  const TrainBatch& b, int grid, float* part, float* loss_part,
                                   cudaStream_t s, int n_in) {
     if (n_in == kStatGridIn)
         return launch_train_t<6, kTrainGiven, kStatGridIn>(a, r, b, grid, part, loss_part, s);
@@ -768,7 +846,7 @@ void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream
     k_reduce_grad<<<(P + 255) / 256, 256, 0, s>>>(part, G, P, grad);
 }
 
-void launch_reduce_loss(const double* part, int G, double* out, cudaStream_t s) {
+void launch_reduce_loss(const float* part, int G, float* out, cudaStream_t s) {
     k_reduce_loss<<<1, 256, 0, s>>>(part, G, out);
 }
 
@@ -783,7 +861,7 @@ void launch_ema(float* E, const float* P, int n, float decay, cudaStream_t s) {
 
 void launch_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn, const float* t,
                          const int* pixel, const float* m1, const float* m2, const float* E,
-                         double Ebar, const float* Iref, const int* k, long long n,
+                         float Ebar, const float* Iref, const int* k, long long n,
                          float eps, float g1, float g2, float g3, float* dq, cudaStream_t s) {
     if (n <= 0) return;
     k_rrsnet_dloss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q_nrrs, F, Fn, t, pixel, m1, m2, E,

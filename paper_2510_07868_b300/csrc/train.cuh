@@ -29,17 +29,22 @@ struct TrainBatch {
     long long offset[kMaxDepth + 1];  // offset[d] = first batch index of depth d
     long long total;    // recorded vertices of the frame
     long long batch;    // training slots: min(total, batch size)
-    double phase;       // systematic-sampling offset in [0, 1)
+    uint32_t phase;     // systematic-sampling offset phase / 2^32 in [0, 1)
     int D;
     uint32_t net_mask;  // depths whose slots carry RRSNet features
 };
 
 // Vertex of training slot i: systematic sampling of `batch` of the `total` recorded
-// vertices with a random offset (every vertex has inclusion probability batch / total;
-// the identity when batch == total).
+// vertices with a random offset phi = phase / 2^32 (every vertex has inclusion
+// probability batch / total; the identity when batch == total), in integers:
+// floor((i + phi) total / batch) = floor((i total + floor(phi total)) / batch), since
+// no multiple of batch lies strictly between two consecutive integers.
 __host__ __device__ __forceinline__ long long batch_vertex(const TrainBatch& b, long long i) {
     if (b.batch >= b.total) return i;
-    const long long u = (long long)(((double)i + b.phase) * ((double)b.total / (double)b.batch));
+    const unsigned long long total = (unsigned long long)b.total;
+    const unsigned long long shift = (total * (unsigned long long)b.phase) >> 32;
+    const unsigned __int128 num = (unsigned __int128)(unsigned long long)i * total + shift;
+    const long long u = (long long)(num / (unsigned long long)b.batch);
     return u < b.total ? u : b.total - 1;
 }
 
@@ -60,7 +65,7 @@ struct TrainArgs {
     const float* F;       // applied factor per depth
     const float* Fn;      // normalization factor without rate control per depth
     const float* E;       // pixel errors
-    const double* Ebar;   // mean pixel error
+    const float* Ebar;    // mean pixel error
     const float* ref;     // reference image [npix * 3] or null
     const int* k;         // training samples per pixel
     float eps, g1, g2, g3;
@@ -95,14 +100,16 @@ void launch_pixel_normals(const RecordView& r, int spp, long long npix, float4* 
 void launch_ref_fold(float* ref, const float* rgb, long long n3, int count, cudaStream_t s);
 void launch_relmse(const float* img, const float* ref, long long n3, double eps, double* out,
                    cudaStream_t s);
-// out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), out[2] = sum k (samples)
-void launch_pixel_terms(const float* E, long long n, const int* k, double* part, int G,
-                        double* Ebar, double* out, cudaStream_t s);
+// out[0] = sum E (L_min), out[1] = sum (E - Ebar)^2 (L_avg), *nsamples = sum k; part
+// [3 G] and kpart [G] are scratch
+void launch_pixel_terms(const float* E, long long n, const int* k, float* part,
+                        long long* kpart, int G, float* Ebar, float* out, long long* nsamples,
+                        cudaStream_t s);
 cudaError_t launch_mlp_train(int which, const TrainArgs& a, const RecordView& r,
-                             const TrainBatch& b, int grid, float* part, double* loss_part,
+                             const TrainBatch& b, int grid, float* part, float* loss_part,
                              cudaStream_t s);
 cudaError_t launch_mlp_grad_given(int n_out, bool at_q, const TrainArgs& a, const RecordView& r,
-                                  const TrainBatch& b, int grid, float* part, double* loss_part,
+                                  const TrainBatch& b, int grid, float* part, float* loss_part,
                                   cudaStream_t s, int n_in = 16);
 // StatNet's encoded inputs [n][32] of vertex features [n][16] and roughness [n].
 void launch_statnet_inputs(const float4* feat, const float* rough, long long n,
@@ -116,13 +123,13 @@ void launch_reduce_grad(const float* part, int G, int P, float* grad, cudaStream
 // entries (atomics; the order of the additions varies from run to run).
 void launch_grid_scatter(const TrainArgs& a, const RecordView& r, const TrainBatch& b, int grid,
                          float* grad, cudaStream_t s);
-void launch_reduce_loss(const double* part, int G, double* out, cudaStream_t s);
+void launch_reduce_loss(const float* part, int G, float* out, cudaStream_t s);
 void launch_adam(float* P, const float* G, float* m, float* v, int n, int step, float lr,
                  float b1, float b2, float eps, int* bad, cudaStream_t s);
 void launch_ema(float* E, const float* P, int n, float decay, cudaStream_t s);
 void launch_rrsnet_dloss(const float* q_nrrs, const float* F, const float* Fn, const float* t,
                          const int* pixel, const float* m1, const float* m2, const float* E,
-                         double Ebar, const float* Iref, const int* k, long long n,
+                         float Ebar, const float* Iref, const int* k, long long n,
                          float eps, float g1, float g2, float g3, float* dq, cudaStream_t s);
 
 }  // namespace nrrs

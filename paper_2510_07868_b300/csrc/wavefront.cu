@@ -586,6 +586,36 @@ __global__ void k_ref_prepare_jobs(const float* __restrict__ ref, RenderParams r
     if (threadIdx.x == 0) rp.jobs.eps_I[j] = ref ? eps_rel * (s / (float)n3) : 0.0f;
 }
 
+// The decision trace of slot i at `depth` (tests): (pixel, sample, lineage, original
+// triangle id or kNoHit, X) at its slot, or with a pixel mask a compact row
+// (depth, pixel, sample, lineage, triangle, X) for marked pixels only.
+__device__ __forceinline__ void trace_record(const SceneView& sc, const WorkView& w,
+                                             const RenderParams& rp, int depth, long long i,
+                                             float4 o4, float4 d4, float4 t4, uint32_t X) {
+    const int slot = __float_as_int(w.hit[i].y);
+    const uint32_t tri = slot < 0 ? kNoHit : fbits(__ldg(&sc.tris[3 * slot].w));
+    const uint32_t pix = fbits(o4.w);
+    if (rp.trace_mask) {
+        if (!rp.trace_mask[pix]) return;
+        const unsigned long long k = atomicAdd(rp.trace_count, 1ull);
+        if (k >= (unsigned long long)rp.trace_rows) return;
+        uint32_t* r = rp.trace + (size_t)k * 6;
+        r[0] = (uint32_t)depth;
+        r[1] = pix;
+        r[2] = fbits(t4.w);
+        r[3] = fbits(d4.w);
+        r[4] = tri;
+        r[5] = X;
+        return;
+    }
+    uint32_t* r = rp.trace + ((size_t)(depth - 1) * rp.cap + i) * 5;
+    r[0] = pix;
+    r[1] = fbits(t4.w);
+    r[2] = fbits(d4.w);
+    r[3] = tri;
+    r[4] = X;
+}
+
 __device__ __forceinline__ void kahan_add(float4* s_, float4* c_, float x, float y, float z) {
     float4 s = *s_, c = *c_;
     float in[3] = {x, y, z};
@@ -659,27 +689,19 @@ k_split_count(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int dept
                 }
                 X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w),
                                  (uint32_t)depth, fbits(d4.w), &qu, &base);
-                if (rp.trace) {
-                    const int slot = __float_as_int(w.hit[i].y);
-                    uint32_t* r = rp.trace + ((size_t)(depth - 1) * rp.cap + i) * 5;
-                    r[0] = fbits(o4.w);
-                    r[1] = fbits(t4.w);
-                    r[2] = fbits(d4.w);
-                    r[3] = slot < 0 ? kNoHit : fbits(__ldg(&sc.tris[3 * slot].w));
-                    r[4] = X;
-                }
+                if (rp.trace) trace_record(sc, w, rp, depth, i, o4, d4, t4, X);
             }
         }
         total += (unsigned long long)X;
     }
     if (!do_split) return;
     total = block_sum(total, sh);
-    if (threadIdx.x == 0) w.bcnt[blockIdx.x] = (unsigned int)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+    if (threadIdx.x == 0) w.bcnt[blockIdx.x] = total;
 }
 
 // Exclusive scan of the per-block counts in 64-bit; sets the next queue length
 // min(S, C), the drop count and the alpha back-off (Eq. f_rate_prime, epsilon 0.01).
-__device__ void scan_counts(const unsigned int* cnt, unsigned long long* off, int G,
+__device__ void scan_counts(const unsigned long long* cnt, unsigned long long* off, int G,
                             unsigned long long* total_out) {
     __shared__ unsigned long long sh[kReduceThreads];
     const int per = (G + blockDim.x - 1) / blockDim.x;
@@ -774,15 +796,7 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
             }
             X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w), (uint32_t)depth,
                              fbits(d4.w), &qu, &base);
-            if (rp.trace) {
-                const int slot = __float_as_int(w.hit[i].y);
-                uint32_t* r = rp.trace + ((size_t)(depth - 1) * rp.cap + i) * 5;
-                r[0] = fbits(o4.w);
-                r[1] = fbits(t4.w);
-                r[2] = fbits(d4.w);
-                r[3] = slot < 0 ? kNoHit : fbits(__ldg(&sc.tris[3 * slot].w));
-                r[4] = X;
-            }
+            if (rp.trace) trace_record(sc, w, rp, depth, i, o4, d4, t4, X);
         }
         uint32_t tile_total;
         const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
@@ -927,7 +941,7 @@ __global__ void k_norm_final(const double* part, int G, double budget, double f_
 }
 
 __global__ void __launch_bounds__(kSplitThreads)
-k_split_arr_count(SplitArrays a, unsigned int* bcnt) {
+k_split_arr_count(SplitArrays a, unsigned long long* bcnt) {
     __shared__ unsigned long long sh[32];
     const float F = *a.F;
     long long begin, end;
@@ -946,10 +960,10 @@ k_split_arr_count(SplitArrays a, unsigned int* bcnt) {
         }
     }
     total = block_sum(total, sh);
-    if (threadIdx.x == 0) bcnt[blockIdx.x] = (unsigned int)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = total;
 }
 
-__global__ void k_split_arr_scan(SplitArrays a, const unsigned int* bcnt, unsigned long long* boff,
+__global__ void k_split_arr_scan(SplitArrays a, const unsigned long long* bcnt, unsigned long long* boff,
                                  int G) {
     __shared__ unsigned long long total;
     scan_counts(bcnt, boff, G, &total);
@@ -1087,7 +1101,7 @@ void launch_normalize_array(const float* q, long long n, double budget, double f
     k_norm_final<<<1, kReduceThreads, 0, s>>>(part, grid, budget, f_rate, alpha, F, sum);
 }
 
-void launch_split_arrays(const SplitArrays& a, unsigned int* bcnt, unsigned long long* boff,
+void launch_split_arrays(const SplitArrays& a, unsigned long long* bcnt, unsigned long long* boff,
                          int grid, cudaStream_t s) {
     k_split_arr_count<<<grid, kSplitThreads, 0, s>>>(a, bcnt);
     k_split_arr_scan<<<1, kReduceThreads, 0, s>>>(a, bcnt, boff, grid);

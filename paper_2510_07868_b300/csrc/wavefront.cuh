@@ -67,7 +67,8 @@ struct WorkView {
     double* part;      // [grid_red] partial sums of q
     int grid_red;      // blocks of the kernel that produced `part` at this depth
     unsigned long long* flags;  // [C / 256 + 1] look-back flags of the fused split
-    unsigned int* bcnt;  // [grid_split] children per block
+    unsigned long long* bcnt;  // [grid_split] children per block (64-bit: a block's
+                               // parents may request up to 2^23 children each)
     unsigned long long* boff;  // [grid_split] exclusive prefix of bcnt
     int grid_split;
     float4* acc_s;     // [npix] Kahan sum (rgb)
@@ -140,6 +141,9 @@ struct RenderParams {
     const float* ref;     // reference image [npix*3] (running mean or caller's) or null
     const float* params;  // RRSNet weights (device, 2592 floats)
     uint32_t* trace;      // optional per-depth trace
+    const uint8_t* trace_mask;         // with trace: compact rows for the marked pixels only
+    unsigned long long* trace_count;   // rows recorded (compact form)
+    long long trace_rows;              // capacity of the compact form
     uint32_t* rec_first;  // record mode: first child slot of every parent of this depth
     uint32_t* rec_X;      // record mode: children requested by every parent of this depth
     int nee;              // next-event estimation with MIS at every vertex
@@ -250,7 +254,7 @@ struct SplitArrays {
     long long* total;
     long long* dropped;
 };
-void launch_split_arrays(const SplitArrays& a, unsigned int* bcnt, unsigned long long* boff,
+void launch_split_arrays(const SplitArrays& a, unsigned long long* bcnt, unsigned long long* boff,
                          int grid, cudaStream_t s);
 
 }  // namespace nrrs

@@ -361,6 +361,19 @@ def rrsnet_init_params(seed: int = 1, dtype=np.float32) -> np.ndarray:
     return np.concatenate(parts).astype(dtype)
 
 
+def statnet_init_params(seed: int = 1, n_in: int = N_FEATURES, dtype=np.float32) -> np.ndarray:
+    """Xavier-uniform draw of StatNet's weights (n_in -> 32 -> 32 -> 32 -> 6), packed
+    W1|W2|W3|W4 row-major like RRSNet's; the output weights scaled by 1/4 so that the
+    untrained moments start small."""
+    rng = np.random.default_rng(seed + 7919)
+    parts = []
+    for k, (fan_out, fan_in) in enumerate(((HIDDEN, n_in), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN),
+                                           (6, HIDDEN))):
+        a = np.sqrt(6.0 / (fan_in + fan_out)) * (0.25 if k == 3 else 1.0)
+        parts.append(rng.uniform(-a, a, fan_out * fan_in))
+    return np.concatenate(parts).astype(dtype)
+
+
 def random_features(n: int, seed: int = 1) -> np.ndarray:
     """``n`` feature rows [n][16] with the ranges the renderer produces.
 

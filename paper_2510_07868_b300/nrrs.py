@@ -40,7 +40,7 @@ EXPORTED = [
     "nrrs_scene_info", "nrrs_set_rrsnet_params", "nrrs_get_rrsnet_params", "nrrs_render",
     "nrrs_query_factors", "nrrs_normalize", "nrrs_split", "nrrs_split_noalloc",
     "nrrs_train_step", "nrrs_set_params", "nrrs_get_params", "nrrs_mlp_grad",
-    "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
+    "nrrs_rrsnet_dloss", "nrrs_adam_step", "nrrs_ema", "nrrs_mixdepth_candidates", "nrrs_mixdepth_search",
     "nrrs_relmse", "nrrs_error_filter", "nrrs_set_rrsnet_inputs", "nrrs_set_statnet_encoding",
     "nrrs_statnet_grad", "nrrs_statnet_inputs", "nrrs_grid_backward",
     "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
@@ -63,14 +63,15 @@ class RenderOpts(C.Structure):
                 ("precision", C.c_int32), ("gate", C.c_uint64), ("d_pixel_ref", C.c_void_p),
                 ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
                 ("profile", C.c_int32), ("graph", C.c_int32), ("d_suffix", C.c_void_p),
-                ("nee", C.c_int32)]
+                ("nee", C.c_int32), ("d_trace_mask", C.c_void_p), ("d_trace_count", C.c_void_p),
+                ("trace_rows", C.c_int64)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
                 eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
                 update_ref=1, reset_ref=0, d_trace=None, profile=0, graph=0, d_suffix=None,
-                nee=0)
+                nee=0, d_trace_mask=None, d_trace_count=None, trace_rows=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -108,7 +109,8 @@ class TrainOpts(C.Structure):
                 ("f_rate", C.c_float), ("d_pixel_ref", C.c_void_p), ("alpha_mix", C.c_float),
                 ("error_filter_radius", C.c_int32), ("graph", C.c_int32),
                 ("batch_size", C.c_int32), ("nee", C.c_int32),
-                ("error_filter_power", C.c_float), ("error_filter_until", C.c_int32)]
+                ("error_filter_power", C.c_float), ("error_filter_until", C.c_int32),
+                ("debug", C.c_void_p)]
 
     @classmethod
     def defaults(cls, **kw):
@@ -116,7 +118,7 @@ class TrainOpts(C.Structure):
                 warmup_steps=20, lr_rrsnet=3e-4, lr_statnet=5e-3, gamma1=0.01, gamma2=0.05,
                 gamma3=0.01, eps=0.01, ema_decay=0.99, f_rate=0.85, d_pixel_ref=None,
                 alpha_mix=0.5, error_filter_radius=2, graph=0, batch_size=0, nee=0,
-                error_filter_power=8.0, error_filter_until=0)
+                error_filter_power=8.0, error_filter_until=0, debug=None)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -146,6 +148,26 @@ class TuneReport(C.Structure):
                 "ms_best": list(self.ms_best[:n]), "ms_default": list(self.ms_default[:n])}
 
 
+class TrainDebug(C.Structure):
+    """nrrs_train_debug: host buffers a training step fills before its Adam updates."""
+    _fields_ = [("grad_statnet", C.c_void_p), ("grad_rrsnet", C.c_void_p),
+                ("pixel_var", C.c_void_p), ("pixel_error", C.c_void_p), ("samples", C.c_void_p),
+                ("ebar", C.c_float), ("vertices", C.c_int64), ("batch", C.c_int64)]
+
+    @classmethod
+    def with_buffers(cls, npix, n_stat, n_rrs):
+        """A debug record with numpy buffers attached (kept alive on the object)."""
+        d = cls()
+        d.arrays = {"grad_statnet": np.zeros(n_stat, np.float32),
+                    "grad_rrsnet": np.zeros(n_rrs, np.float32),
+                    "pixel_var": np.zeros(npix, np.float32),
+                    "pixel_error": np.zeros(npix, np.float32),
+                    "samples": np.zeros(npix, np.int32)}
+        for k, a in d.arrays.items():
+            setattr(d, k, a.ctypes.data)
+        return d
+
+
 class TrainStats(C.Structure):
     _fields_ = [("step", C.c_int64), ("samples", C.c_int64), ("segments", C.c_int64),
                 ("loss_statnet", C.c_double), ("loss_rrsnet", C.c_double),
@@ -160,7 +182,8 @@ class MixDepthOpts(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
                 ("max_depth", C.c_int32), ("t_d", C.c_int32), ("max_candidates", C.c_int32),
                 ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32),
-                ("d_pixel_ref", C.c_void_p), ("adrrs", C.c_int32), ("nee", C.c_int32)]
+                ("d_pixel_ref", C.c_void_p), ("adrrs", C.c_int32), ("nee", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class MixDepthResult(C.Structure):
@@ -196,6 +219,7 @@ def _load():
                                C.c_float, C.c_float, P, P], I32),
         "nrrs_adam_step": ([P, P, P, P, I32, I32, C.c_float, C.c_float, C.c_float, C.c_float, P],
                            I32),
+        "nrrs_ema": ([P, P, I32, C.c_float, P], I32),
         "nrrs_mixdepth_candidates": ([I32, I32], I64),
         "nrrs_mixdepth_search": ([P, P, P, P], I32),
         "nrrs_relmse": ([P, P, I64, D, P, P], I32),
@@ -490,14 +514,19 @@ def nrrs_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, b1=0.9, b2=0.999, ep
                                b1, b2, eps, _stream(stream)))
 
 
+def nrrs_ema(d_avg, d_params, n, decay, stream=None):
+    _check(_lib.nrrs_ema(_ptr(d_avg), _ptr(d_params), n, decay, _stream(stream)))
+
+
 def nrrs_mixdepth_candidates(max_depth, t_d):
     return int(_lib.nrrs_mixdepth_candidates(max_depth, t_d))
 
 
 def nrrs_mixdepth_search(scene, width, height, max_depth, t_d=6, spp=1, seed=(1, 0), frame=0,
-                         d_pixel_ref=None, max_candidates=0, adrrs=0, nee=0, stream=None):
+                         d_pixel_ref=None, max_candidates=0, adrrs=0, nee=0, precision=32,
+                         stream=None):
     o = MixDepthOpts(width, height, spp, max_depth, t_d, max_candidates, seed[0], seed[1], frame,
-                     _ptr(d_pixel_ref), adrrs, nee)
+                     _ptr(d_pixel_ref), adrrs, nee, precision)
     r = MixDepthResult()
     _check(_lib.nrrs_mixdepth_search(scene, C.byref(o), _stream(stream), C.byref(r)))
     return {name: getattr(r, name) for name, _ in r._fields_}

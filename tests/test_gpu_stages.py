@@ -76,6 +76,26 @@ def test_split_bit_exact(nrrs, n, F, scale, capmul):
         assert g[5] > 0
 
 
+@pytest.mark.parametrize("n", [4096, 1_000_000])
+def test_split_block_counts_beyond_32_bits(nrrs, n):
+    """Factors just below 2^23 at F = 1: every parent asks for about 2^23 children, so a
+    block's child count passes 2^32 (4096 parents in one block of the no-allocation
+    variant; about 850 per block of the pooled grid at n = 10^6).  Totals, prefixes and
+    the kept children must still equal the oracle's."""
+    rng = np.random.default_rng(n + 5)
+    q = (8388607.5 - rng.integers(0, 64, n) * 0.5).astype(np.float32)
+    pix = np.arange(n, dtype=np.uint32)
+    smp = rng.integers(0, 16, n).astype(np.uint32)
+    lin = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    cap = 1 << 22
+    o = oracle.split(q, np.float32(1.0), pix, smp, lin, 4, seed=(3, 9), frame=1, cap=cap)
+    assert o[4] > 2**32 * (n // 4096 if n > 4096 else 1)
+    g = _gpu_split(nrrs, q, 1.0, pix, smp, lin, 4, (3, 9), 1, cap)
+    for k in range(4):
+        np.testing.assert_array_equal(g[k], o[k])
+    assert g[4] == o[4] and g[5] == o[5]
+
+
 def test_split_empty_queue(nrrs):
     q = np.zeros(0, np.float32)
     e = np.zeros(0, np.uint32)

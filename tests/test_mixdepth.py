@@ -36,7 +36,10 @@ def test_relmse_matches_oracle():
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     nrrs.nrrs_relmse(torch.from_numpy(img).cuda(), torch.from_numpy(ref).cuda(), n, 0.01, out)
     torch.cuda.synchronize()
-    assert out.item() == pytest.approx(oracle.relmse(img, ref, 0.01), rel=1e-12)
+    # the GPU sums in FP32 (compensated per thread, then a tree over 1024 threads): each
+    # term (i - r)^2 / (r^2 + eps) carries at most 4 roundings (4 u, u = 2^-24) and the
+    # tree 10 more, so the mean is within 14 u < 1e-6 relative of the FP64 oracle's
+    assert out.item() == pytest.approx(oracle.relmse(img, ref, 0.01), rel=1e-6)
 
 
 @pytest.mark.gpu

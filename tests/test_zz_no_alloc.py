@@ -26,6 +26,11 @@ def _inputs(n, seed):
     return dev(q), dev(pix), dev(smp), dev(lin)
 
 
+def _empty_inputs():
+    z = lambda dt: torch.zeros(1, dtype=dt, device="cuda")  # noqa: E731
+    return z(torch.float32), z(torch.int32), z(torch.int32), z(torch.int32)
+
+
 def _outputs(n, cap):
     return (torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda"),
             torch.full((max(n, 1),), -7, dtype=torch.int64, device="cuda"),
@@ -65,6 +70,41 @@ def test_noalloc_matches_split_on_two_calls_in_a_row():
             np.testing.assert_array_equal(a, b)
         assert ref[4:] == got[4:]
     assert got[5] > 0  # the second call dropped children at the capacity
+
+
+@pytest.mark.parametrize("n", [0, 1, 255, 4095, 4096, 4097])
+def test_noalloc_matches_split_at_chunk_edges(n):
+    """Sizes where the no-allocation variant's grid (one block per 4096 parents) leaves a
+    block with no tile or a one-parent tail, while nrrs_split spreads the same parents
+    over its fixed grid: both must agree bit for bit."""
+    from paper_2510_07868_b300 import nrrs
+
+    for call in range(2):
+        ins = _inputs(n, seed=n + 17 * call) if n else _empty_inputs()
+        cap = 2 * n + 8
+        ref = _run(nrrs, "split", ins, n, 0.8, 2 + call, call, cap)
+        got = _run(nrrs, "noalloc", ins, n, 0.8, 2 + call, call, cap)
+        for a, b in zip(ref[:4], got[:4]):
+            np.testing.assert_array_equal(a, b)
+        assert ref[4:] == got[4:]
+
+
+def test_noalloc_block_counts_beyond_32_bits():
+    """4096 parents in one block, each asking for about 2^23 children: the block's count
+    passes 2^32 and must not saturate (the totals and prefixes equal nrrs_split's)."""
+    from paper_2510_07868_b300 import nrrs
+
+    n = 4096
+    rng = np.random.default_rng(23)
+    q = torch.from_numpy((8388607.5 - rng.integers(0, 64, n) * 0.5).astype(np.float32)).cuda()
+    _, pix, smp, lin = _inputs(n, seed=23)
+    cap = 1 << 20
+    ref = _run(nrrs, "split", (q, pix, smp, lin), n, 1.0, 4, 1, cap)
+    got = _run(nrrs, "noalloc", (q, pix, smp, lin), n, 1.0, 4, 1, cap)
+    assert ref[4] > 2**32
+    for a, b in zip(ref[:4], got[:4]):
+        np.testing.assert_array_equal(a, b)
+    assert ref[4:] == got[4:]
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
