@@ -1,17 +1,24 @@
 """Benchmark of the NRRS bounce loop on B300.
 
-Step = one online NRRS frame through the C ABI: nrrs_train_step (a recorded 256 x 256 x
-2 spp frame, reverse pass, pixel errors, StatNet and RRSNet forward/backward, Adam, EMA)
-and nrrs_render (camera rays, then for every depth the traversal, shading, RRSNet FP32
-factors, normalization, split counts + accumulation, scan and scatter with BSDF sampling,
-and the frame estimate).  Workload: the occluded room (2,018 triangles), 256 x 256 px,
-16 spp, max depth 16, queue capacity 2 x pixels x spp.
+Headline (`value`): the Mix-Depth workload on one GPU -- the three-room scene with
+1,000,000 random triangles (60 % GGX) joined by narrow doorways, 1920 x 1080 px, depth
+32, 128 spp rendered as 8 frames of 16 spp.  A step is one 16-spp frame through
+nrrs_render (camera rays, then per depth the traversal, shading, RRSNet at the depths
+the Mix-Depth gate marks -- tensor cores, split BF16 operands -- and heuristic factors
+elsewhere, normalization, split counts with the per-pixel accumulation, compaction and
+BSDF sampling of the children, the frame estimate), graph-captured, with the launch
+shapes the autotuner chose per queue-size bucket.  Set-up, untimed: the BVH build,
+online training of RRSNet and StatNet on 480 x 270 x 4 spp frames of the same scene,
+the tuner, and the Mix-Depth search on 480 x 270 x 1 spp renders.
 
-`value` is path segments per second (rays traced, summed over depths and ranks) with
-the scene, weights and queues resident on the device; `e2e` is the same metric through
-the public API with the per-frame weights copied from pinned host memory and the frame
-read back every step.  `--impl reference` times the FP64 CPU oracle on the host cores
-on a bounded sample of the same workload.
+`value` is path segments per second (rays traced, summed over depths and ranks) with the
+scene, weights and queues resident on the device; `e2e` is the same metric through the
+public API with the weights copied from pinned host memory and the frame read back every
+step.  Second section, `online_step`: the online NRRS step on the occluded room (2,018
+triangles, 256 x 256 px, 16 spp, depth 16): nrrs_train_step on a recorded 256 x 256 x
+2 spp frame plus the 16-spp inference frame, with the estimators' efficiency
+1 / (relMSE x s) over several seeds.  `--impl reference` times the FP64 CPU oracle on
+the host cores on a bounded crop of the headline workload.
 """
 from __future__ import annotations
 
@@ -32,13 +39,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "efficiency 1/(relMSE·s) vs plain RR, same B300; path segments/s; RRSNet TFLOP/s"
 UNIT = "path segments/s"
+# headline: the Mix-Depth configuration
+HL_W, HL_H, HL_SPP, HL_DEPTH = 1920, 1080, 16, 32
+HL_FRAMES = 8                        # 8 frames x 16 spp = 128 spp
+HL_TRAIN = (480, 270, 4)             # online training frames of the same scene
+HL_PRETRAIN = 120                    # untimed training steps before the search
+HL_SEARCH = (480, 270)               # Mix-Depth estimation renders (1 spp)
+HL_PRECISION = 16                    # RRSNet on the tensor cores, split BF16 operands
+HL_WORKLOAD = ("three_rooms (1,000,000 random triangles, 60 % GGX) 1920x1080 px, depth 32, "
+               "128 spp as 8 frames x 16 spp; step = one 16-spp frame, NET_MIX (searched "
+               "Mix-Depth gate), RRSNet split-BF16 tensor cores at gated depths, heuristic "
+               "elsewhere, tuned launch shapes, CUDA-graph bounce loop, cap 2*P")
+# second section: the online training step
 W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
 TRAIN_SPP = 2          # recorded training frame: 256x256x2 spp ~ 2^19 training vertices
 PRETRAIN_STEPS = 300   # untimed online training before the timed steps (20 warm-up + 280 full)
 WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P; "
             "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
             "+ the 16 spp inference frame")
+EFF_SEEDS = 5          # independent render seeds per estimator in the efficiency tables
 # algorithmic bytes per unit of each stage
+BYTES_PER_RAY_EXTEND = 32 + 16                  # ray in, hit record out
 BYTES_PER_RAY_SHADE = 48 + 8 + 4 + 16           # path state, hit in; q, deposit out
 BYTES_PER_SLOT_DEPOSIT = 16                     # last depth: deposit only
 BYTES_PER_PARENT_SPLIT = 16 + 4 + 48 + 8        # deposit, q, path state, hit
@@ -190,50 +211,78 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(sm)}
 
 
-def traffic_from_profiles(kernel_tag):
-    """DRAM bytes per unit (ray / slot) recorded by ncu for `kernel_tag`, if the recorded
-    source hash still matches the current kernel source (else None).  The traversal's
-    hash covers its kernel file and the BVH builder that lays out what it reads."""
+def profile_record(kernel_tag, key):
+    """A figure `key` per unit recorded from an ncu capture of `kernel_tag` in profiles/
+    (lines `<key> <tag> source_sha=<sha> value=<x>`), if the recorded source hash still
+    matches the current kernel source (else None).  The traversal's hash covers its
+    kernel file and the BVH builder that lays out what it reads."""
     csrc = os.path.join(ROOT, "paper_2510_07868_b300", "csrc")
     files = {"extend": ["trace.cu", "bvh.cpp"]}.get(kernel_tag, ["wavefront.cu"])
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     sha = h.hexdigest()[:12]
-    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(
-            os.path.join(ROOT, "profiles")) else []:
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
         if not fn.endswith((".md", ".txt")):
             continue
-        for line in open(os.path.join(ROOT, "profiles", fn)):
-            m = re.match(r"traffic\s+(\S+)\s+source_sha=(\w+)\s+bytes_per_unit=([\d.]+)", line)
-            if m and m.group(1) == kernel_tag and m.group(2) == sha:
-                return float(m.group(3))
+        for line in open(os.path.join(pdir, fn)):
+            m = re.match(r"(\w+)\s+(\S+)\s+source_sha=(\w+)\s+value=([\d.eE+-]+)", line.strip("` \n"))
+            if m and m.group(1) == key and m.group(2) == kernel_tag and m.group(3) == sha:
+                return float(m.group(4))
     return None
 
 
-# ------------------------------------------------------------------ CPU oracle legs
-def oracle_sample(seconds_target=15.0, mode=None):
-    """Times the FP64 oracle on a reduced image of the same scene, spp, depth and mode;
-    returns (segments/s, cores, sample description, wall seconds)."""
-    import oracle
-    from paper_2510_07868_b300 import inputs as I
+def source_sha(kernel_tag):
+    csrc = os.path.join(ROOT, "paper_2510_07868_b300", "csrc")
+    files = {"extend": ["trace.cu", "bvh.cpp"]}.get(kernel_tag, ["wavefront.cu"])
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
 
-    scene = I.occluded_room(1)
-    params = I.rrsnet_init_params(1).astype(np.float64)
-    mode = oracle.MODE_NET if mode is None else mode
-    side = 16
+
+# ------------------------------------------------------------------ CPU oracle legs
+def crop_pixels(side, W=HL_W, H=HL_H):
+    """Pixel ids of a side x side window at the image centre."""
+    x0, y0 = (W - side) // 2, (H - side) // 2
+    ys, xs = np.meshgrid(np.arange(y0, y0 + side), np.arange(x0, x0 + side), indexing="ij")
+    return (ys * W + xs).ravel().astype(np.int32)
+
+
+def oracle_headline_sample(scene, params, gate, pixel_ref, forced_F, seconds_target=15.0,
+                           frame=0):
+    """Times the FP64 oracle on a centred crop of the headline frame at 1 spp (same scene,
+    depth, mode and gate), growing the crop toward `seconds_target` of work; returns
+    (segments/s, cores, sample description, seconds, side)."""
+    import oracle
+
+    side = 8
     while True:
+        pix = crop_pixels(side)
         t0 = time.perf_counter()
-        _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, mode, params=params)
+        _, st, _ = oracle.render(scene, HL_W, HL_H, 1, HL_DEPTH, oracle.MODE_NET_MIX,
+                                 params=params, gate=gate, pixel_ref=pixel_ref, pixels=pix,
+                                 forced_F=forced_F, frame=frame)
         dt = time.perf_counter() - t0
-        if dt >= 0.25 * seconds_target or side >= W_IMG:
+        if dt >= 0.25 * seconds_target or side >= 128:
             break
-        # grow the image toward about `seconds_target` of work (at most 4x area per try)
-        side = int(min(W_IMG, side * min(2.0, np.sqrt(seconds_target / max(dt, 1e-3)))))
+        side = int(min(128, side * min(2.0, np.sqrt(seconds_target / max(dt, 1e-3)))))
     cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
-    desc = (f"occluded_room {side}x{side} px (of 256x256), 16 spp, depth 16, NET factors, "
-            f"cap 2*P; {st['segments']} segments in {dt:.2f} s")
+    desc = (f"three_rooms centred {side}x{side} px crop of 1920x1080 at 1 spp (the GPU step "
+            f"renders 16 spp over 2,073,600 px), depth 32, NET_MIX; {st['segments']} segments "
+            f"in {dt:.2f} s")
     return st["segments"] / dt, cores, desc, dt, side
+
+
+def reference_gate():
+    """The fixed Mix-Depth gate the reference arm uses (it cannot train): FIXED at depths
+    1-2, RRSNet at depths 3-8, the heuristic beyond."""
+    g = 0
+    for d in range(HL_DEPTH):
+        m = 2 if d < 2 else 0 if d < 8 else 1  # NRRS_GATE_FIXED / _NET / _HEUR
+        g |= m << (2 * d)
+    return g
 
 
 def run_reference(args, rank, world):
@@ -244,26 +293,38 @@ def run_reference(args, rank, world):
     from paper_2510_07868_b300 import inputs as I
 
     oracle.build()
-    scene = I.occluded_room(1)
-    params = I.rrsnet_init_params(1).astype(np.float64)
-    _, _, _, _, side = oracle_sample(seconds_target=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+    scene = I.three_rooms(1)
+    params = I.rrsnet_init_params(2).astype(np.float64)
+    gate = reference_gate()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    # a crop cannot see the whole frame's sum of factors: F = 1 at every depth (the frame's
+    # own F stays near 1 here, its budget 2 P being far above the factors' sum)
+    F1 = np.ones(HL_DEPTH, dtype=np.float32)
+    _, _, _, _, side = oracle_headline_sample(scene, params, gate, None, F1,
+                                              seconds_target=per_step)
+    pix = crop_pixels(side)
     for k in range(args.warmup):
-        oracle.render(scene, side, side, SPP, DEPTH, oracle.MODE_NET, params=params, frame=k)
+        oracle.render(scene, HL_W, HL_H, 1, HL_DEPTH, oracle.MODE_NET_MIX, params=params,
+                      gate=gate, pixels=pix, forced_F=F1, frame=k)
     segs = 0
     t0 = time.perf_counter()
     for k in range(args.steps):
-        _, st, _ = oracle.render(scene, side, side, SPP, DEPTH, oracle.MODE_NET, params=params,
+        _, st, _ = oracle.render(scene, HL_W, HL_H, 1, HL_DEPTH, oracle.MODE_NET_MIX,
+                                 params=params, gate=gate, pixels=pix, forced_F=F1,
                                  frame=args.warmup + k)
         segs += st["segments"]
     dt = time.perf_counter() - t0
     value = segs / dt
     cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
-    sample = f"occluded_room {side}x{side} px per step (of 256x256), 16 spp, depth 16, NET"
+    sample = (f"three_rooms centred {side}x{side} px crop of 1920x1080 per step at 1 spp, depth "
+              f"32, NET_MIX with a fixed gate (FIXED 1-2, RRSNet 3-8, heuristic beyond) and "
+              f"the untrained RRSNet (the oracle cannot train; its cost per segment does not "
+              f"depend on the weights' values)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "data": "synthetic", "config": {"workload": HL_WORKLOAD, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -289,94 +350,135 @@ def combine_ranks(dist, device, ms, e2e_s, segs, e2e_segs):
     return float(t[0]), float(t[1]), int(c[0]), int(c[1])
 
 
-def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0):
-    """1/(relMSE x seconds) of the estimators on the same B300: PLAIN_RR (throughput
-    roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet), ADRRS_NN (StatNet's
-    radiance over the pixel estimate at every depth), NET_MIX (the Mix-Depth gate over
-    FIXED / HEUR / NET) and NET_MIX_ADRRS (over FIXED / ADRRS (NN) / NET, the paper's
-    set), each averaging 16 frames of 16 spp, against a 4096-spp plain path-traced
-    reference (256 frames x 16 spp, no RRS).  nee=1: every render, the reference and the
-    Mix-Depth searches with next-event estimation."""
+def mean_se(xs):
+    x = np.asarray(xs, dtype=np.float64)
+    return float(x.mean()), float(x.std(ddof=1) / np.sqrt(len(x))) if len(x) > 1 else 0.0
+
+
+def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0, seeds=EFF_SEEDS,
+                       precisions=(32,)):
+    """1/(relMSE x seconds) of the estimators on the same B300 -- PLAIN_RR (throughput
+    roulette), HEUR_NORM (plain normalised RRS), NET (trained RRSNet at every depth),
+    ADRRS_NN (StatNet's radiance over the pixel estimate at every depth), NET_MIX (the
+    Mix-Depth gate over FIXED / HEUR / NET) and NET_MIX_ADRRS (over FIXED / ADRRS (NN) /
+    NET, the paper's set), NET and NET_MIX again at every tensor-core precision asked
+    for (16 = split BF16, 8 = E4M3) -- each averaging 16 frames of 16 spp, against a
+    4096-spp plain path-traced reference (256 frames x 16 spp, no RRS), repeated with
+    `seeds` independent render seeds: mean and standard error per estimator.  nee=1:
+    every render, the reference and the Mix-Depth searches with next-event estimation."""
     ref = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
     img = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
     n_ref = 256
     for f in range(n_ref):
         nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NONE,
-                         nrrs.RenderOpts.defaults(frame=50_000 + f, seed_hi=seed_hi, update_ref=0,
-                                                  nee=nee),
+                         nrrs.RenderOpts.defaults(frame=50_000 + f, seed_hi=seed_hi + 1000,
+                                                  update_ref=0, nee=nee),
                          img, stream, False)
         ref += img
     ref32 = (ref / n_ref).float().contiguous()
     out = torch.zeros(1, dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
-    gate_res = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
-                                         d_pixel_ref=None, nee=nee, stream=stream)
+    gates = {}
+    for prec in precisions:
+        gates[prec] = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6,
+                                                frame=777, d_pixel_ref=None, nee=nee,
+                                                precision=prec, stream=stream)
     search_s = time.perf_counter() - t0
     # the paper's candidate set per depth: FIXED, ADRRS (NN), NRRS
     gate_adrrs = nrrs.nrrs_mixdepth_search(sc.handle, W_IMG, H_IMG, DEPTH, t_d=6, frame=777,
                                            d_pixel_ref=None, adrrs=1, nee=nee, stream=stream)
     all_adrrs = sum(nrrs.GATE_ADRRS << (2 * d) for d in range(DEPTH))
+    modes = [("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0, 32), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0, 32),
+             ("ADRRS_NN", nrrs.RRS_NET_MIX, all_adrrs, 32),
+             ("NET_MIX_ADRRS", nrrs.RRS_NET_MIX, gate_adrrs["gate"], 32)]
+    tag = {32: "", 16: "_BF16", 8: "_E4M3"}
+    for prec in precisions:
+        modes.append(("NET" + tag[prec], nrrs.RRS_NET, 0, prec))
+        modes.append(("NET_MIX" + tag[prec], nrrs.RRS_NET_MIX, gates[prec]["gate"], prec))
+    frames = 16
     res = {}
-    for name, mode, gate in (("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0),
-                             ("NET", nrrs.RRS_NET, 0),
-                             ("ADRRS_NN", nrrs.RRS_NET_MIX, all_adrrs),
-                             ("NET_MIX", nrrs.RRS_NET_MIX, gate_res["gate"]),
-                             ("NET_MIX_ADRRS", nrrs.RRS_NET_MIX, gate_adrrs["gate"])):
-        acc = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
-        frames = 16
-        segs = 0
+    for name, mode, gate, prec in modes:
+        per = {"relmse": [], "seconds": [], "efficiency": [], "segments": [], "ray_efficiency": []}
         # one untimed frame first, so that no mode's time holds its first graph capture
         nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
                          nrrs.RenderOpts.defaults(frame=89_999, seed_hi=seed_hi, gate=gate,
-                                                  update_ref=0, nee=nee),
+                                                  update_ref=0, nee=nee, precision=prec,
+                                                  graph=1),
                          img, stream, True)
-        torch.cuda.synchronize()
+        for k in range(seeds):
+            acc = torch.zeros((H_IMG, W_IMG, 3), dtype=torch.float64, device=dev)
+            segs = 0
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for f in range(frames):
+                st = nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
+                                      nrrs.RenderOpts.defaults(frame=90_000 + f,
+                                                               seed_hi=seed_hi + 17 * k,
+                                                               gate=gate, update_ref=0, nee=nee,
+                                                               precision=prec, graph=1),
+                                      img, stream, True)
+                segs += st["segments"]
+                acc += img
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0
+            mean = (acc / frames).float().contiguous()
+            nrrs.nrrs_relmse(mean, ref32, W_IMG * H_IMG, 0.01, out, stream)
+            torch.cuda.synchronize()
+            rel = out.item()
+            per["relmse"].append(rel)
+            per["seconds"].append(sec)
+            per["efficiency"].append(1.0 / (rel * sec))
+            per["segments"].append(segs)
+            per["ray_efficiency"].append(1.0 / (rel * segs))
+        res[name] = {}
+        for key, xs in per.items():
+            m, se = mean_se(xs)
+            res[name][key] = m
+            res[name][key + "_se"] = se
+    base = res["PLAIN_RR"]["efficiency"]
+    heur = res["HEUR_NORM"]["efficiency"]
+    summary = {
+        "reference": f"no-RRS path tracing{' with NEE' if nee else ''}, {n_ref * SPP} spp",
+        "frames_per_seed": frames, "seeds": seeds, "modes": res,
+        "mixdepth_gates": {str(p): nrrs.gate_methods(g["gate"], DEPTH) for p, g in gates.items()},
+        "mixdepth_gate_adrrs": nrrs.gate_methods(gate_adrrs["gate"], DEPTH),
+        "mixdepth_candidates": gates[precisions[0]]["evaluated"], "mixdepth_search_s": search_s,
+    }
+    for name in res:
+        if name not in ("PLAIN_RR", "HEUR_NORM"):
+            summary[name.lower() + "_vs_heur_norm"] = res[name]["efficiency"] / heur
+    summary["heur_norm_vs_plain_rr"] = heur / base
+    return summary
+
+
+def time_rrsnet_queries(nrrs, sc, torch, dev, stream, I):
+    """Stand-alone RRSNet throughput on a live-queue-sized batch at each precision."""
+    n_q = 1 << 21
+    feats = torch.from_numpy(I.random_features(n_q, seed=3)).to(dev)
+    qout = torch.empty(n_q, dtype=torch.float32, device=dev)
+    ms = {}
+    for prec in (32, 16, 8):
+        for _ in range(3):
+            sc.query(feats, out=qout, precision=prec)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for f in range(frames):
-            st = nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, mode,
-                                  nrrs.RenderOpts.defaults(frame=90_000 + f, seed_hi=seed_hi,
-                                                           gate=gate, update_ref=0, nee=nee),
-                                  img, stream, True)
-            segs += st["segments"]
-            acc += img
+        for _ in range(10):
+            sc.query(feats, out=qout, precision=prec)
         e1.record(stream)
         torch.cuda.synchronize()
-        sec = e0.elapsed_time(e1) / 1000.0
-        mean = (acc / frames).float().contiguous()
-        nrrs.nrrs_relmse(mean, ref32, W_IMG * H_IMG, 0.01, out, stream)
-        torch.cuda.synchronize()
-        rel = out.item()
-        res[name] = {"relmse": rel, "seconds": sec, "efficiency": 1.0 / (rel * sec),
-                     "segments": segs, "ray_efficiency": 1.0 / (rel * segs)}
-    base = res["PLAIN_RR"]["efficiency"]
-    return {
-        "reference": f"no-RRS path tracing{' with NEE' if nee else ''}, {n_ref * SPP} spp",
-        "frames_per_mode": 16, "modes": res,
-        "net_vs_plain_rr": res["NET"]["efficiency"] / base,
-        "net_mix_vs_plain_rr": res["NET_MIX"]["efficiency"] / base,
-        "heur_norm_vs_plain_rr": res["HEUR_NORM"]["efficiency"] / base,
-        "net_mix_adrrs_vs_plain_rr": res["NET_MIX_ADRRS"]["efficiency"] / base,
-        "net_mix_adrrs_vs_heur_norm": res["NET_MIX_ADRRS"]["efficiency"]
-        / res["HEUR_NORM"]["efficiency"],
-        "mixdepth_gate": nrrs.gate_methods(gate_res["gate"], DEPTH),
-        "mixdepth_gate_adrrs": nrrs.gate_methods(gate_adrrs["gate"], DEPTH),
-        "mixdepth_candidates": gate_res["evaluated"], "mixdepth_search_s": search_s,
-    }
+        ms[prec] = e0.elapsed_time(e1) / 10
+    return n_q, ms
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-
+def online_section(args, nrrs, torch, dev, stream, seed_hi, local_rank, rank):
+    """The online NRRS step on the occluded room: one training step and one inference
+    frame per step (the first section of earlier versions of this benchmark), its stage
+    breakdown and the efficiency tables."""
     from paper_2510_07868_b300 import inputs as I
-    from paper_2510_07868_b300 import nrrs
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
 
     scene = I.occluded_room(1)
     params = I.rrsnet_init_params(1)
@@ -385,8 +487,6 @@ def run_ours(args, rank, world, local_rank):
     if args.bvh4:
         sc.set_traversal(4)
     out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    seed_hi = replica_seed(rank)  # independent replicas: different Philox streams per rank
     graph = 0 if args.no_graph else 1
     topts = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP, max_depth=DEPTH,
                                     seed_hi=seed_hi, graph=graph)
@@ -401,129 +501,59 @@ def run_ours(args, rank, world, local_rank):
                                                          profile=profile, graph=graph),
                                 out, stream, True)
 
-    # set-up (untimed): RRSNet launch shapes per queue-size bucket for each precision
     tuner = {p: sc.tune(p) for p in (32, 16, 8)}
-    # online training through the warm-up phase into the full loss
-    pre = []
     for k in range(args.pretrain):
-        pre.append(train(10_000 + k))
+        train(10_000 + k)
         render(20_000 + k)
-    clocks = ClockSampler(local_rank)
-    clocks.launch()
-    # warm-up steps time every render stage (events around each launch); the timed steps
-    # bracket only the dominant stage's launches, which the roofline needs
     warm_ms = np.zeros(nrrs.STAGES)
     warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
-    warm_live = warm_evals = warm_children = warm_last = 0
     for k in range(args.warmup):
         train(30_000 + k)
         st = render(k, profile=1)
         warm_ms += st["stage_ms"]
         warm_n += st["stage_launches"]
-        warm_live += int(st["live"].sum())
-        warm_evals += st["net_evals"]
-        warm_children += int(st["live"][1:].sum())
-        warm_last += int(st["live"][DEPTH - 1])
-    dom = int(np.argmax(warm_ms))
-    torch.cuda.synchronize()
-    clocks.start()
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     et0 = torch.cuda.Event(enable_timing=True)
     et1 = torch.cuda.Event(enable_timing=True)
-    segs = render_segs = 0
-    launches = 0
+    segs = render_segs = launches = fallbacks = 0
     train_ms = 0.0
-    stage_ms = np.zeros(nrrs.STAGES)
-    stage_n = np.zeros(nrrs.STAGES, dtype=np.int64)
-    live_total = 0
-    live_last = 0
-    net_evals = 0
-    children = 0
-    fallbacks = 0
-    # a profiler started with "profile from start off" (ncu --profile-from-start off)
-    # records the timed steps only; without a profiler these calls do nothing
-    torch.cuda.profiler.start()
+    steps = max(1, args.online_steps)
     ev0.record(stream)
-    for k in range(args.steps):
+    for k in range(steps):
         et0.record(stream)
         ts = train(40_000 + k)
         et1.record(stream)
-        st = render(args.warmup + k, profile=1 << (dom + 1))
+        st = render(args.warmup + k)
         train_ms += et0.elapsed_time(et1)
         segs += st["segments"] + ts["segments"]
         render_segs += st["segments"]
         launches += st["kernel_launches"] + ts["kernel_launches"]
         fallbacks += ts["fallback"] != 0
-        stage_ms += st["stage_ms"]
-        stage_n += st["stage_launches"]
-        live_total += int(st["live"].sum())
-        live_last += int(st["live"][DEPTH - 1])
-        net_evals += st["net_evals"]
-        children += int(st["live"][1:].sum())
     ev1.record(stream)
     torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    last_train = ts
-
-    # end to end through the public API: weights from pinned host memory in, frame out
-    pinned_params = torch.from_numpy(nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET)).pin_memory()
-    pinned_out = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32).pin_memory()
-    e2e_segs = 0
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        nrrs.nrrs_set_rrsnet_params(sc.handle, pinned_params.numpy(), stream)
-        ts = train(60_000 + k)
-        st = render(70_000 + k)
-        e2e_segs += st["segments"] + ts["segments"]
-        pinned_out.copy_(out, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    e2e_s = time.perf_counter() - t0
-
-    # stand-alone RRSNet throughput on a live-queue-sized batch
-    n_q = 1 << 21
-    feats = torch.from_numpy(I.random_features(n_q, seed=3)).to(dev)
-    qout = torch.empty(n_q, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        sc.query(feats, out=qout)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(10):
-        sc.query(feats, out=qout)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    q_ms = e0.elapsed_time(e1) / 10
-    for _ in range(3):
-        sc.query(feats, out=qout, precision=16)
-    e0.record(stream)
-    for _ in range(10):
-        sc.query(feats, out=qout, precision=16)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    q16_ms = e0.elapsed_time(e1) / 10
-    for _ in range(3):
-        sc.query(feats, out=qout, precision=8)
-    e0.record(stream)
-    for _ in range(10):
-        sc.query(feats, out=qout, precision=8)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    q8_ms = e0.elapsed_time(e1) / 10
-
+    names = nrrs.STAGE_NAMES
+    stages = {n: {"ms_per_frame": float(warm_ms[i] / max(1, args.warmup)),
+                  "share": float(warm_ms[i] / warm_ms.sum())}
+              for i, n in enumerate(names) if warm_n[i] > 0}
+    sec = {
+        "workload": WORKLOAD, "scene_triangles": scene.n_tri, "value": segs / (ms / 1000.0),
+        "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "train_step_ms": train_ms / steps, "render_ms": (ms - train_ms) / steps,
+        "render_segments_per_s": render_segs / ((ms - train_ms) / 1000.0),
+        "train_phase": ts["phase"], "train_fallbacks": fallbacks,
+        "train_loss_rrsnet": ts["loss_rrsnet"], "train_loss_statnet": ts["loss_statnet"],
+        "pretrain_steps": args.pretrain, "gpu_launches": int(launches),
+        "stages": stages,
+        "tuned_shapes": {str(p): {"variant": r["variant"], "blocks_per_sm": r["blocks_per_sm"]}
+                         for p, r in tuner.items()},
+    }
     eff = None
     if rank == 0 and not args.no_efficiency:
-        eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi)
+        eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, precisions=(32, 16, 8))
+
         def trained_scene(nee, rrsnet_inputs, statnet_encoding):
             """A second RRSNet / StatNet pair trained online like the first."""
             sc2 = nrrs.Scene(scene, device=local_rank)
@@ -533,7 +563,7 @@ def run_ours(args, rank, world, local_rank):
             sc2.tune(32)
             t2 = nrrs.TrainOpts.defaults(width=W_IMG, height=H_IMG, spp=TRAIN_SPP,
                                          max_depth=DEPTH, seed_hi=seed_hi, graph=graph, nee=nee)
-            for k in range(args.pretrain + args.warmup + args.steps):
+            for k in range(args.pretrain + args.warmup + steps):
                 t2.frame = 10_000 + k
                 nrrs.nrrs_train_step(sc2.handle, t2, stream)
                 nrrs.nrrs_render(sc2.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
@@ -551,9 +581,144 @@ def run_ours(args, rank, world, local_rank):
             sc2 = trained_scene(nee, rin, enc)
             eff[key] = efficiency_section(nrrs, sc2, torch, dev, stream, seed_hi, nee=nee)
             sc2.close()
+    sec["efficiency"] = eff
+    n_q, qms = time_rrsnet_queries(nrrs, sc, torch, dev, stream, I)
+    sc.close()
+    return sec, (n_q, qms, tuner)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2510_07868_b300 import inputs as I
+    from paper_2510_07868_b300 import nrrs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    stream = torch.cuda.current_stream()
+    seed_hi = replica_seed(rank)  # independent replicas: different Philox streams per rank
+    graph = 0 if args.no_graph else 1
+
+    # ---- set-up of the headline workload (untimed)
+    scene = I.three_rooms(1)
+    t_build = time.perf_counter()
+    sc = nrrs.Scene(scene, device=local_rank)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t_build
+    params0 = I.rrsnet_init_params(2)
+    sc.set_params(params0)
+    tuner = {p: sc.tune(p) for p in (HL_PRECISION, 32)}
+    tw, th, tspp = HL_TRAIN
+    topts = nrrs.TrainOpts.defaults(width=tw, height=th, spp=tspp, max_depth=HL_DEPTH,
+                                    seed_hi=seed_hi, graph=graph)
+    t_train = time.perf_counter()
+    last_ts = None
+    for k in range(args.hl_pretrain):
+        topts.frame = 10_000 + k
+        last_ts = nrrs.nrrs_train_step(sc.handle, topts, stream)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    t_search = time.perf_counter()
+    search = nrrs.nrrs_mixdepth_search(sc.handle, HL_SEARCH[0], HL_SEARCH[1], HL_DEPTH, t_d=6,
+                                       frame=777, d_pixel_ref=None, precision=HL_PRECISION,
+                                       stream=stream)
+    search_s = time.perf_counter() - t_search
+    gate = search["gate"]
+    out = torch.empty((HL_H, HL_W, 3), dtype=torch.float32, device=dev)
+
+    def render(frame, profile=0, d_out=out):
+        return nrrs.nrrs_render(sc.handle, HL_W, HL_H, HL_SPP, HL_DEPTH, nrrs.RRS_NET_MIX,
+                                nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi, gate=gate,
+                                                         precision=HL_PRECISION, graph=graph,
+                                                         profile=profile),
+                                d_out, stream, True)
+
+    clocks = ClockSampler(local_rank)
+    clocks.launch()
+    # warm-up frames time every render stage (events around each launch); the timed frames
+    # bracket only the dominant stage's launches, which the roofline needs
+    warm_ms = np.zeros(nrrs.STAGES)
+    warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
+    warm = {"live": 0, "evals": 0, "children": 0, "last": 0}
+    for k in range(args.warmup):
+        st = render(k, profile=1)
+        warm_ms += st["stage_ms"]
+        warm_n += st["stage_launches"]
+        warm["live"] += int(st["live"].sum())
+        warm["evals"] += st["net_evals"]
+        warm["children"] += int(st["live"][1:].sum())
+        warm["last"] += int(st["live"][HL_DEPTH - 1])
+    dom = int(np.argmax(warm_ms))
+    torch.cuda.synchronize()
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    segs = launches = live_total = net_evals = 0
+    stage_ms = np.zeros(nrrs.STAGES)
+    stage_n = np.zeros(nrrs.STAGES, dtype=np.int64)
+    status = 0
+    # a profiler started with "profile from start off" (ncu --profile-from-start off)
+    # records the timed frames only; without a profiler these calls do nothing
+    torch.cuda.profiler.start()
+    ev0.record(stream)
+    for k in range(args.steps):
+        st = render(args.warmup + k, profile=1 << (dom + 1))
+        segs += st["segments"]
+        launches += st["kernel_launches"]
+        stage_ms += st["stage_ms"]
+        stage_n += st["stage_launches"]
+        live_total += int(st["live"].sum())
+        net_evals += st["net_evals"]
+        status |= st["status_bits"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    last_F = np.array(st["F"][:HL_DEPTH], dtype=np.float32)
+
+    # end to end through the public API: weights from pinned host memory in, frame out
+    trained = nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET)
+    pinned_params = torch.from_numpy(trained).pin_memory()
+    pinned_out = torch.empty((HL_H, HL_W, 3), dtype=torch.float32).pin_memory()
+    e2e_segs = 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        nrrs.nrrs_set_rrsnet_params(sc.handle, pinned_params.numpy(), stream)
+        st = render(70_000 + k)
+        e2e_segs += st["segments"]
+        pinned_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    ref_img = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the reference image the gate's heuristic depths saw (the scene's running mean)
+        ref_img = out.cpu().numpy().astype(np.float64)
 
     if dist:
         ms, e2e_s, segs, e2e_segs = combine_ranks(dist, dev, ms, e2e_s, segs, e2e_segs)
+    hl_stats = {"live_total": live_total, "net_evals": net_evals, "stage_ms": stage_ms,
+                "stage_n": stage_n, "warm_ms": warm_ms, "warm_n": warm_n, "warm": warm,
+                "dom": dom, "status": status}
+    sc.close()
+
+    # ---- second section: the online training step on the occluded room
+    online = None
+    qstats = None
+    if not args.no_online:
+        online, qstats = online_section(args, nrrs, torch, dev, stream, seed_hi, local_rank, rank)
     if rank != 0:
         return
     hbm, bf16, peak_kind = measured_peaks()
@@ -561,18 +726,16 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant render stage (event times on the launching stream)
     names = nrrs.STAGE_NAMES
-    alg_bytes = {
-        "extend": 32 * live_total + 8 * live_total,  # ray in, hit out
-        "split_count": BYTES_PER_SLOT_DEPOSIT * live_last,
-        "split_scatter": BYTES_PER_PARENT_SPLIT * (live_total - live_last)
-        + BYTES_PER_CHILD_SPLIT * children,
-    }
-    bytes_dom = alg_bytes.get(names[dom])
+    warm = hl_stats["warm"]
+    alg_bytes_per_unit = {"extend": BYTES_PER_RAY_EXTEND}
+    bytes_dom = (BYTES_PER_RAY_EXTEND * live_total) if names[dom] == "extend" else None
     per_launch_ms = stage_ms[dom] / max(1, stage_n[dom])
     achieved = (bytes_dom / (stage_ms[dom] / 1000.0) / 1e9) if bytes_dom else None
-    per_unit = traffic_from_profiles(names[dom])
     units_per_launch = live_total / max(1, stage_n[dom])
+    per_unit = profile_record(names[dom], "traffic")
     traffic = per_unit * units_per_launch if per_unit is not None else None
+    inst_per_ray = profile_record(names[dom], "warp_inst_per_ray")
+    issue_active = profile_record(names[dom], "issue_active")
     roofline = {
         "kernel": "k_trace" if names[dom] == "extend" else names[dom], "bound": "hbm",
         "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -580,21 +743,28 @@ def run_ours(args, rank, world, local_rank):
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
         else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
         "launches": int(stage_n[dom]),
-        "note": ("k_trace is issue-bound, not HBM-bound (ncu: 80 % / 69 % issue activity at "
-                 "depths 1 / 2, ALU pipe busiest, DRAM < 2 %); 40 B/ray algorithmic"
+        "bytes_per_unit": alg_bytes_per_unit.get(names[dom]),
+        "issue": {"warp_inst_per_ray": inst_per_ray, "issue_active_frac": issue_active,
+                  "source": "ncu capture in profiles/ (null when the kernel changed since)",
+                  "issue_peak_warp_inst_per_s": 148 * 4 * 2.032e9,
+                  "achieved_warp_inst_per_s": (inst_per_ray * units_per_launch / (per_launch_ms / 1e3))
+                  if inst_per_ray else None},
+        "note": ("the traversal is bound by instruction issue, not HBM: the BVH and the "
+                 "triangles stay in L2; 48 B/ray algorithmic (32 B ray in, 16 B hit out)"
                  if names[dom] == "extend" else f"{names[dom]} stage against HBM"),
     }
-    # every render stage against HBM: algorithmic bytes over its summed event time, from
-    # the warm-up steps (events around every launch)
+    if inst_per_ray:
+        roofline["issue"]["frac_of_issue_peak"] = (roofline["issue"]["achieved_warp_inst_per_s"]
+                                                   / roofline["issue"]["issue_peak_warp_inst_per_s"])
     stage_bytes = {
-        "extend": 40 * warm_live,
-        "shade": BYTES_PER_RAY_SHADE * warm_live + 64 * warm_evals,
-        "rrsnet": 68 * warm_evals,
-        "split_count": BYTES_PER_SLOT_DEPOSIT * warm_last,
-        "split_scatter": BYTES_PER_PARENT_SPLIT * (warm_live - warm_last)
-        + BYTES_PER_CHILD_SPLIT * warm_children,
+        "extend": BYTES_PER_RAY_EXTEND * warm["live"],
+        "shade": BYTES_PER_RAY_SHADE * warm["live"] + 64 * warm["evals"],
+        "rrsnet": 68 * warm["evals"],
+        "split_count": BYTES_PER_SLOT_DEPOSIT * warm["last"],
+        "split_scatter": BYTES_PER_PARENT_SPLIT * (warm["live"] - warm["last"])
+        + BYTES_PER_CHILD_SPLIT * warm["children"],
     }
-    stages = {"timed_over": f"{args.warmup} warm-up steps"}
+    stages = {"timed_over": f"{args.warmup} warm-up frames"}
     for i, n in enumerate(names):
         if warm_n[i] == 0:
             continue
@@ -605,66 +775,68 @@ def run_ours(args, rank, world, local_rank):
             e.update({"achieved_gbs": gbs, "frac_of_hbm": gbs / hbm})
         stages[n] = e
     roofline["stages"] = stages
-    fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
-    tf16 = RRSNET_FLOP_PER_PATH * n_q / (q16_ms / 1000) / 1e12
-    tf8 = RRSNET_FLOP_PER_PATH * n_q / (q8_ms / 1000) / 1e12  # FP8 peak: 2x BF16 (nominal)
-    rows_per_s_hbm = hbm * 1e9 / (16 * 4 + 4)  # FP32 features in, factor out
+    rr_ms = warm_ms[names.index("rrsnet")]
     rrsnet = {
-        "tflops_tensor_bf16x3": tf16,
-        "tensor_roofline": {"bound": "hbm", "achieved_gbs": 68 * n_q / (q16_ms / 1000) / 1e9,
-                            "peak": hbm, "frac": 68 * n_q / (q16_ms / 1000) / 1e9 / hbm,
-                            "flop_cap_at_hbm_tflops": RRSNET_FLOP_PER_PATH * rows_per_s_hbm / 1e12,
-                            "frac_of_bf16_tensor_peak": tf16 / bf16,
-                            "note": "algorithmic FLOP (5184/row); the split BF16 runs 3 MMAs "
-                                    "per product"},
-        "tflops_tensor_e4m3": tf8,
-        "e4m3_hbm_frac": 68 * n_q / (q8_ms / 1000) / 1e9 / hbm,
-        "frac_of_fp8_tensor_peak": tf8 / (2 * bf16),
-        "tflops_standalone_fp32": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12,
-        "fp32_simt_peak_tflops": fp32_peak,
-        "frac_of_fp32_peak": RRSNET_FLOP_PER_PATH * n_q / (q_ms / 1000) / 1e12 / fp32_peak,
-        "tflops_in_render": RRSNET_FLOP_PER_PATH * warm_evals / (warm_ms[7] / 1000) / 1e12
-        if warm_ms[7] > 0 else None,
-        "batch": n_q,
-        "tuned_shapes": {
-            str(p): {"rows": r["rows"], "variant": r["variant"],
-                     "blocks_per_sm": r["blocks_per_sm"],
-                     "speedup_vs_default": [d / b if b > 0 else None
-                                            for b, d in zip(r["ms_best"], r["ms_default"])]}
-            for p, r in tuner.items()},
+        "in_render": {"precision": "split BF16 (tensor cores)", "evaluations_per_frame":
+                      warm["evals"] / max(1, args.warmup),
+                      "ms_per_frame": float(rr_ms / max(1, args.warmup)),
+                      "tflops": RRSNET_FLOP_PER_PATH * warm["evals"] / (rr_ms / 1000) / 1e12
+                      if rr_ms > 0 else None},
     }
+    if qstats:
+        n_q, qms, tuner2 = qstats
+        fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock
+        rows_per_s_hbm = hbm * 1e9 / (16 * 4 + 4)  # FP32 features in, factor out
+        tf = {p: RRSNET_FLOP_PER_PATH * n_q / (qms[p] / 1000) / 1e12 for p in qms}
+        rrsnet["standalone"] = {
+            "batch": n_q, "ms": qms,
+            "tflops_fp32": tf[32], "fp32_simt_peak_tflops": fp32_peak,
+            "frac_of_fp32_peak": tf[32] / fp32_peak,
+            "tflops_tensor_bf16x3": tf[16], "tflops_tensor_e4m3": tf[8],
+            "hbm_frac_bf16x3": 68 * n_q / (qms[16] / 1000) / 1e9 / hbm,
+            "hbm_frac_e4m3": 68 * n_q / (qms[8] / 1000) / 1e9 / hbm,
+            "flop_cap_at_hbm_tflops": RRSNET_FLOP_PER_PATH * rows_per_s_hbm / 1e12,
+            "frac_of_bf16_tensor_peak": tf[16] / bf16,
+            "frac_of_fp8_tensor_peak": tf[8] / (2 * bf16),
+            "note": "algorithmic FLOP (5184/row); the split BF16 runs 3 MMAs per product; "
+                    "FP8 peak taken as 2x the measured BF16 (nominal ratio)",
+        }
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, cores, desc, _, _ = oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        v, cores, desc, _, _ = oracle_headline_sample(
+            scene, trained.astype(np.float64), gate, ref_img, last_F)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": desc + "; the GPU run's trained weights, gate and per-depth F"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "scene_triangles": scene.n_tri,
+        "config": {"workload": HL_WORKLOAD, "scene_triangles": scene.n_tri,
                    "parallelism": f"replicas{world}",
                    "bounce_loop": "CUDA graph per frame" if graph else "stream launches",
-                   "bvh": "four-wide, FP32 boxes" if args.bvh4 else "BVH2, FP16 boxes rounded outward",
-                   "l2": "no flush: each step rewrites ~0.3 GB of path queues and records (> 126 MB L2)"},
-        "step_breakdown": {"train_step_ms": train_ms / args.steps,
-                           "render_ms": (ms - train_ms) / args.steps,
-                           "render_segments_per_s": render_segs / ((ms - train_ms) / 1000.0),
-                           "train_phase": last_train["phase"], "train_fallbacks": fallbacks,
-                           "train_loss_rrsnet": last_train["loss_rrsnet"],
-                           "train_loss_statnet": last_train["loss_statnet"],
-                           "pretrain_steps": args.pretrain},
+                   "bvh": "BVH2, FP16 boxes rounded outward",
+                   "mixdepth_gate": nrrs.gate_methods(gate, HL_DEPTH),
+                   "l2": "no flush: each step writes ~3 GB of path queues (> 126 MB L2)"},
+        "setup": {"bvh_build_s": build_s, "pretrain_steps": args.hl_pretrain,
+                  "pretrain_s": train_s, "train_frame": list(HL_TRAIN),
+                  "last_train_phase": last_ts["phase"] if last_ts else None,
+                  "mixdepth_search_s": search_s, "mixdepth_candidates": search["evaluated"],
+                  "search_frame": list(HL_SEARCH),
+                  "tuned_shapes": {str(p): {"variant": r["variant"],
+                                            "blocks_per_sm": r["blocks_per_sm"]}
+                                   for p, r in tuner.items()}},
+        "frame_status_bits": int(hl_stats["status"]),
         "e2e": {"value": e2e_segs / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(params.nbytes),
-                "d2h_bytes_per_step": int(W_IMG * H_IMG * 3 * 4)},
+                "h2d_bytes_per_step": int(trained.nbytes),
+                "d2h_bytes_per_step": int(HL_W * HL_H * 3 * 4)},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "rrsnet": rrsnet,
-        "efficiency": eff,
+        "online_step": online,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
-    sc.close()
 
 
 def run_rrsnet_only(args):
@@ -715,7 +887,13 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the bounce loop kernel by kernel instead of as a CUDA graph")
     ap.add_argument("--pretrain", type=int, default=PRETRAIN_STEPS,
-                    help="untimed online training steps before the timed region")
+                    help="untimed online training steps of the online-step section")
+    ap.add_argument("--hl-pretrain", type=int, default=HL_PRETRAIN,
+                    help="untimed online training steps on the headline scene")
+    ap.add_argument("--online-steps", type=int, default=20,
+                    help="timed steps of the online-step section")
+    ap.add_argument("--no-online", action="store_true",
+                    help="skip the online-step section (occluded room)")
     ap.add_argument("--rrsnet-only", type=int, choices=[32, 16, 8], default=0,
                     help="time only RRSNet inference at this precision on a 2^21-row batch "
                          "(the untuned default launch shape), for kernel profiles")
