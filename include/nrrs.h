@@ -121,7 +121,8 @@ typedef struct nrrs_scene nrrs_scene; /* opaque; owns every device buffer it all
 typedef struct nrrs_render_opts {
     uint32_t seed_lo, seed_hi;  /* Philox key = (seed_lo, seed_hi ^ frame)         [1, 0] */
     uint32_t frame;             /* frame index                                      [0]    */
-    int32_t cap_factor;         /* queue capacity C = cap_factor * W * H * spp      [2]    */
+    int32_t cap_factor;         /* queue capacity C = cap_factor * W * H * spp (children
+                                   beyond it are dropped and counted)               [2]    */
     float f_rate;               /* rate-control factor, Eq. q_norm_rate             [0.85] */
     float alpha0;               /* initial adaptive alpha, Eq. f_rate_prime         [1]    */
     float q_max;                /* HEUR cap                                         [16]   */
@@ -169,6 +170,12 @@ typedef struct nrrs_render_opts {
                                    it recorded to (zero it first); rows beyond trace_rows
                                    are counted, not written                         [NULL] */
     int64_t trace_rows;         /* rows d_trace holds with d_trace_mask             [0]    */
+    int32_t budget_factor;      /* N_px of Eq. F_norm, the paths each depth may expect
+                                   before rate control: budget_factor * W * H * spp.  0 or
+                                   1 = the primary queue's size (Sec. 3.1: "the
+                                   preallocated size of the primary workqueue"); the
+                                   queue's capacity C (cap_factor) is enforced on integers
+                                   on top and must hold it (budget_factor <= cap_factor) [0] */
 } nrrs_render_opts;
 
 /* Stages of one render, indexing nrrs_render_stats.stage_ms / stage_launches. */
@@ -263,12 +270,40 @@ NRRS_API nrrs_status nrrs_render_batch(nrrs_scene* batch, int32_t rrs_mode,
 NRRS_API nrrs_status nrrs_batch_info(const nrrs_scene* scene, int32_t* n_jobs,
                                      int64_t* pixel_base, int64_t* n_pixels_total);
 
-/* Chooses the traversal tree of later renders: 2 = the BVH2 (default), 4 = a four-wide
+/* Chooses the traversal tree of later renders (the paper traces with OptiX, Sec. 4
+ * "System"; these are its stand-ins): 2 = the host-built BVH2 (default), 4 = a four-wide
  * tree collapsed from it (available when its worst-case traversal stack fits the
- * kernel's 40 entries; half the node visits, but no faster on the measured scenes).
- * Both give the same closest hits.  Errors: INVALID_ARG (NULL scene,
- * width not 2 or 4); UNSUPPORTED (4 without a four-wide tree). */
+ * kernel's 40 entries), 8 = a compressed eight-wide tree built on the device on first
+ * use (Morton order, PLOC clustering, collapse to eight children with leaves of up to
+ * 2 triangles, child boxes quantised to one byte per plane against a per-node origin
+ * and power-of-two scales, 80 bytes per node; Ylitie, Karras & Laine 2017), traversed
+ * nearest child first with the remaining children as node groups on the stack in the
+ * ray's octant order.  Every tree gives the same closest hits; on the measured scenes
+ * the BVH2 with FP16 boxes traverses fastest.  The first call with 8 builds (device memory about 200 bytes per
+ * triangle while it runs, 80 bytes per node and 48 per triangle after) and synchronizes
+ * the device.  Errors: INVALID_ARG (NULL scene, width not 2, 4 or 8); UNSUPPORTED (4
+ * without a four-wide tree; 8 on a batch, or a tree deeper than the 40-entry stack);
+ * CUDA, OOM. */
 NRRS_API nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width);
+
+/* The device-built eight-wide tree (nrrs_set_traversal(8)); all zero before it is built. */
+typedef struct nrrs_bvh8_stats {
+    int64_t nodes;       /* eight-wide nodes                                        */
+    int64_t triangles;   /* triangles in its leaves (each once)                     */
+    int32_t depth;       /* node levels                                             */
+    int32_t iterations;  /* clustering rounds of the build                          */
+    float build_ms;      /* wall time of the build, including its synchronization  */
+} nrrs_bvh8_stats;
+NRRS_API nrrs_status nrrs_bvh8_info(const nrrs_scene* scene, nrrs_bvh8_stats* out);
+
+/* Host copies of the eight-wide tree, for tests: nodes [nodes][20] u32 (five 16-byte rows
+ * per node: origin xyz as FP32 bits and exponents | inner mask << 24; first inner
+ * child, first triangle, leaf meta bytes; then the lower x, y, z and upper x, y, z bytes
+ * of the eight child boxes), tris [triangles][12] float (v0, original id bits; e1,
+ * material id bits; e2, 0).  Errors: INVALID_ARG (NULL, buffers too small); UNSUPPORTED
+ * (not built); CUDA. */
+NRRS_API nrrs_status nrrs_bvh8_export(const nrrs_scene* scene, uint32_t* nodes,
+                                      int64_t max_nodes, float* tris, int64_t max_tris);
 
 /* Chooses the box precision of the BVH2 that later renders traverse: 16 = a copy of
  * the tree with every child box rounded outward to IEEE binary16 (32-byte nodes, one

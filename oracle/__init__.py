@@ -64,7 +64,8 @@ class RenderArgs(C.Structure):
                 ("params", C.c_void_p), ("pixel_ref", C.c_void_p), ("pixels", C.c_void_p),
                 ("n_pixels", C.c_int64), ("rec", C.c_void_p), ("forced_F", C.c_void_p),
                 ("stat_params", C.c_void_p), ("nee", C.c_int32), ("rrsnet_inputs", C.c_int32),
-                ("stat_encoding", C.c_int32), ("stat_grid", C.c_void_p), ("rrs_grid", C.c_void_p)]
+                ("stat_encoding", C.c_int32), ("stat_grid", C.c_void_p), ("rrs_grid", C.c_void_p),
+                ("budget", C.c_int64)]
 
 
 class RenderStats(C.Structure):
@@ -360,7 +361,7 @@ def bernstein_exponent(f_rate):
 def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap=0,
            f_rate=0.85, alpha0=1.0, q_max=16.0, eps_rel=0.01, boxcox_lambda=0.5, gate=0,
            params=None, pixel_ref=None, pixels=None, trace=False, record=False, forced_F=None,
-           stat_params=None, nee=0, rrsnet_inputs=0, stat_grid=None, rrs_grid=None):
+           stat_params=None, nee=0, rrsnet_inputs=0, stat_grid=None, rrs_grid=None, budget=0):
     """One oracle render; returns (rgb [H,W,3] float64, stats dict, trace or None).
     nee=1 adds next-event estimation with MIS (power heuristic) at every vertex;
     rrsnet_inputs=1 feeds RRSNet the NRRS inputs built from StatNet (stat_params);
@@ -383,7 +384,7 @@ def render(scene, width, height, spp, max_depth, mode, seed=(1, 0), frame=0, cap
     args = RenderArgs(width, height, spp, max_depth, mode, seed[0], seed[1], frame, cap, f_rate,
                       alpha0, q_max, eps_rel, boxcox_lambda, gate, _p(P), _p(ref), _p(pix),
                       0 if pix is None else pix.shape[0], _p(rec), _p(fF), _p(SP), int(nee),
-                      int(rrsnet_inputs), 0 if SG is None else 1, _p(SG), _p(RG))
+                      int(rrsnet_inputs), 0 if SG is None else 1, _p(SG), _p(RG), int(budget))
     out = np.zeros((height, width, 3))
     st = RenderStats()
     tr = np.zeros((max_depth, capv, 5), dtype=np.uint32) if trace else None

@@ -556,6 +556,8 @@ typedef struct {
                                inputs zeroed), 1 = hash grid + one-blob (needs stat_grid) */
     const double* stat_grid;/* StatNet's hash-grid table [8][2^18][2] */
     const double* rrs_grid; /* RRSNet's hash-grid table (AID-NRRS inputs) */
+    int64_t budget;         /* N_px of Eq. F_norm: the expected paths per depth before rate
+                               control; 0 = W * H * spp, the primary queue (Sec. 3.1) */
 } or_render_args;
 
 /* StatNet's six outputs at a vertex whose 16 features are x (position in the scene box,
@@ -713,6 +715,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
     const int64_t npix = (int64_t)W * H;
     const int64_t P = (a->pixels ? a->n_pixels : npix) * spp;
     const int64_t cap = a->cap > 0 ? a->cap : 2 * (int64_t)W * H * spp;
+    const int64_t budget = a->budget > 0 ? a->budget : (int64_t)W * H * spp;
     if (a->pixels && or_is_normalized(a->mode) && !a->forced_F) return OR_ERR_ARG;
     if (a->mode == OR_MODE_NET_MIX && !a->stat_params)
         for (int32_t d = 1; d <= D; ++d)
@@ -969,7 +972,7 @@ int or_render(const or_scene* s, const or_render_args* a, double* out_rgb,
             F32 = a->forced_F[depth - 1];
         } else if (or_is_normalized(a->mode)) {
             double sum;
-            double F = or_normalize(qbuf, n, (double)cap, a->f_rate, alpha, &sum);
+            double F = or_normalize(qbuf, n, (double)budget, a->f_rate, alpha, &sum);
             st->sum_q[depth] = sum;
             F32 = (float)F;
         } else {

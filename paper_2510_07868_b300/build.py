@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnrrs.so")
-SOURCES = ["api.cu", "wavefront.cu", "trace.cu", "rrsnet_simt.cu", "rrsnet_tc.cu", "tune.cu", "train.cu", "noalloc.cu", "bvh.cpp", "emitters.cpp"]
+SOURCES = ["api.cu", "wavefront.cu", "trace.cu", "rrsnet_simt.cu", "rrsnet_tc.cu", "tune.cu", "train.cu", "noalloc.cu", "bvh8.cu", "bvh.cpp", "emitters.cpp"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

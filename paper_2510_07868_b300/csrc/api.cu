@@ -1,5 +1,6 @@
 // C ABI of the NRRS bounce (include/nrrs.h): scene set-up, the per-depth launch
 // sequence of one render, and the stand-alone stage entry points.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "bvh.h"
+#include "bvh8.h"
 #include "emitters.h"
 #include "grid.cuh"
 #include "train.cuh"
@@ -228,6 +230,13 @@ struct nrrs_scene {
     uint4* nodes_h = nullptr;  // BVH2 with FP16 boxes (NULL when a leaf does not fit its code)
     int bvh_width = 2;
     float4* tris = nullptr;
+    // the input triangles ([n_tri][9] vertices, material ids) for the device-built
+    // eight-wide tree, and that tree once built (nrrs_set_traversal(8))
+    float* tri_raw = nullptr;
+    int32_t* mat_raw = nullptr;
+    float scene_lo[3] = {0, 0, 0}, scene_hi[3] = {0, 0, 0};
+    Bvh8Device bvh8;
+    float bvh8_build_ms = 0.0f;
     nrrs_material* mats = nullptr;
     float4* emit = nullptr;      // next-event estimation: emitter triangles and area CDF
     float* emit_cdf = nullptr;
@@ -349,6 +358,10 @@ void destroy(nrrs_scene* s) {
     cudaFree(s->nodes4);
     cudaFree(s->nodes_h);
     cudaFree(s->tris);
+    cudaFree(s->tri_raw);
+    cudaFree(s->mat_raw);
+    cudaFree(s->bvh8.nodes);
+    cudaFree(s->bvh8.tris);
     cudaFree(s->mats);
     cudaFree(s->emit);
     cudaFree(s->emit_cdf);
@@ -570,7 +583,25 @@ nrrs_status nrrs_create_scene(const float* tri, int32_t n_tri, const int32_t* tr
     collapse_bvh4(bvh, &bvh4);
     const bool wide = bvh4.max_stack <= trace_stack_entries();
     const EmitterHost em = build_emitters(tri, n_tri, tri_mat, mats);
-    return upload_scene(bvh, wide ? &bvh4 : nullptr, n_tri, mats, n_mat, cam, em, device, out);
+    nrrs_status rc = upload_scene(bvh, wide ? &bvh4 : nullptr, n_tri, mats, n_mat, cam, em, device, out);
+    if (rc != NRRS_OK) return rc;
+    nrrs_scene* s = *out;
+    for (int k = 0; k < 3; ++k) {
+        s->scene_lo[k] = bvh.lo[k];
+        s->scene_hi[k] = bvh.hi[k];
+    }
+    cudaError_t e = dalloc(&s->tri_raw, (size_t)n_tri * 9);
+    if (e == cudaSuccess) e = dalloc(&s->mat_raw, (size_t)n_tri);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->tri_raw, tri, sizeof(float) * 9 * (size_t)n_tri, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->mat_raw, tri_mat, sizeof(int32_t) * (size_t)n_tri, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        destroy(s);
+        *out = nullptr;
+        return cuda_fail(e, "upload triangles");
+    }
+    return NRRS_OK;
 }
 
 nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
@@ -583,11 +614,64 @@ nrrs_status nrrs_destroy_scene(nrrs_scene* scene) {
 
 nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
-    if (width != 2 && width != 4) return fail(NRRS_ERR_INVALID_ARG, "width must be 2 or 4");
+    if (width != 2 && width != 4 && width != 8)
+        return fail(NRRS_ERR_INVALID_ARG, "width must be 2, 4 or 8");
     if (width == 4 && !scene->nodes4)
         return fail(NRRS_ERR_UNSUPPORTED, "no four-wide tree (its stack bound is too deep)");
+    if (width == 8) {
+        if (scene->n_jobs > 0 || !scene->tri_raw)
+            return fail(NRRS_ERR_UNSUPPORTED, "the eight-wide tree is built for single scenes");
+        if (!scene->bvh8.nodes) {
+            DeviceGuard g(scene->device);
+            if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+            const auto t0 = std::chrono::steady_clock::now();
+            Bvh8Device b;
+            cudaError_t e = build_bvh8(scene->tri_raw, scene->mat_raw, (int)scene->n_tri,
+                                       scene->scene_lo, scene->scene_hi, nullptr, &b);
+            if (e != cudaSuccess) return cuda_fail(e, "eight-wide BVH build");
+            scene->bvh8_build_ms = std::chrono::duration<float, std::milli>(
+                                       std::chrono::steady_clock::now() - t0).count();
+            if (b.depth > trace_stack_entries()) {
+                cudaFree(b.nodes);
+                cudaFree(b.tris);
+                return fail(NRRS_ERR_UNSUPPORTED, "eight-wide tree deeper than the traversal stack");
+            }
+            scene->bvh8 = b;
+        }
+        scene->view.nodes8 = scene->bvh8.nodes;
+        scene->view.tris = scene->bvh8.tris;
+        scene->view.nodes4 = nullptr;
+    } else {
+        scene->view.nodes8 = nullptr;
+        scene->view.tris = scene->tris;
+        scene->view.nodes4 = width == 4 ? scene->nodes4 : nullptr;
+    }
     scene->bvh_width = width;
-    scene->view.nodes4 = width == 4 ? scene->nodes4 : nullptr;
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_bvh8_info(const nrrs_scene* scene, nrrs_bvh8_stats* out) {
+    if (!scene || !out) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or out");
+    std::memset(out, 0, sizeof(*out));
+    out->nodes = scene->bvh8.n_nodes;
+    out->triangles = scene->bvh8.nodes ? scene->n_tri : 0;
+    out->depth = scene->bvh8.depth;
+    out->iterations = scene->bvh8.ploc_iterations;
+    out->build_ms = scene->bvh8_build_ms;
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_bvh8_export(const nrrs_scene* scene, uint32_t* nodes, int64_t max_nodes,
+                             float* tris, int64_t max_tris) {
+    if (!scene || !nodes || !tris) return fail(NRRS_ERR_INVALID_ARG, "NULL argument");
+    if (!scene->bvh8.nodes) return fail(NRRS_ERR_UNSUPPORTED, "no eight-wide tree built");
+    if (max_nodes < (int64_t)scene->bvh8.n_nodes || max_tris < scene->n_tri)
+        return fail(NRRS_ERR_INVALID_ARG, "export buffers too small");
+    DeviceGuard g(scene->device);
+    CK(cudaMemcpy(nodes, scene->bvh8.nodes, sizeof(uint4) * 5 * (size_t)scene->bvh8.n_nodes,
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tris, scene->bvh8.tris, sizeof(float4) * 3 * (size_t)scene->n_tri,
+                  cudaMemcpyDeviceToHost));
     return NRRS_OK;
 }
 
@@ -663,6 +747,8 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
     if (rrs_mode < NRRS_RRS_NONE || rrs_mode > NRRS_RRS_NET_MIX)
         return fail(NRRS_ERR_INVALID_ARG, "unknown rrs_mode");
     if (o.cap_factor < 1) return fail(NRRS_ERR_INVALID_ARG, "cap_factor < 1");
+    if (o.budget_factor < 0 || o.budget_factor > o.cap_factor)
+        return fail(NRRS_ERR_INVALID_ARG, "budget_factor must lie in [0, cap_factor]");
     if (!(o.f_rate > 0.0f && o.f_rate <= 1.0f) || !(o.alpha0 > 0.0f && o.alpha0 <= 1.0f))
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
     if (o.precision != 32 && o.precision != 16 && o.precision != 8)
@@ -844,6 +930,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     RenderParams rp{};
     rp.W = width; rp.H = height; rp.spp = spp; rp.D = max_depth;
     rp.cap = C;
+    rp.budget = (double)P * (double)(o.budget_factor > 0 ? o.budget_factor : 1);
     rp.fc = ws.fc;
     rp.f_rate = o.f_rate;
     rp.q_max = o.q_max;
@@ -861,6 +948,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     if (batch) {
         rp.jobs = scene->jw;
         rp.jobs.cap_factor = o.cap_factor;
+        rp.jobs.budget_factor = o.budget_factor > 0 ? o.budget_factor : 1;
     } else {
         scene->cam.aspect = (float)width / (float)height;
     }
@@ -1002,7 +1090,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         for (uint64_t v : sv) shape = mix_key(shape, v);
         uint64_t args = shape;
         auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };
-        const uint64_t av[] = {(uint64_t)o.cap_factor, fbits(o.f_rate), fbits(o.alpha0),
+        const uint64_t av[] = {(uint64_t)o.cap_factor, (uint64_t)o.budget_factor,
+                               fbits(o.f_rate), fbits(o.alpha0),
                                fbits(o.q_max), fbits(o.eps_rel), fbits(o.boxcox_lambda),
                                (uint64_t)update, (uint64_t)(uintptr_t)rp.ref,
                                (uint64_t)(uintptr_t)rp.params, (uint64_t)(uintptr_t)o.d_trace,
@@ -1024,7 +1113,9 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)scene->rrsnet_inputs,
                                (uint64_t)(uintptr_t)scene->train.rgrid,
                                (uint64_t)(uintptr_t)rp.trace_mask,
-                               (uint64_t)(uintptr_t)rp.trace_count, (uint64_t)rp.trace_rows};
+                               (uint64_t)(uintptr_t)rp.trace_count, (uint64_t)rp.trace_rows,
+                               (uint64_t)(uintptr_t)scene->view.nodes8,
+                               (uint64_t)(uintptr_t)scene->view.tris};
         for (uint64_t v : av) args = mix_key(args, v);
         for (int d = 1; d <= max_depth; ++d)
             args = mix_key(args, (uint64_t)(net_shape[d - 1].variant * 64 +
@@ -1841,8 +1932,10 @@ nrrs_status nrrs_train_step(nrrs_scene* scene, const nrrs_train_opts* opts, void
         b.offset[d] = off;
         off += rs.live[d];
         Fh[d] = rs.F[d];
-        const double fn = rs.sum_q[d] > 0.0 ? (double)C / rs.sum_q[d] : 1.0;
-        Fnh[d] = (float)(fn < 1.0 ? fn : 1.0);  // Eq. F_norm, downscale only, no rate control
+        // Eq. F_norm with the frame's budget N_px (the primary queue), downscale only, no
+        // rate control
+        const double fn = rs.sum_q[d] > 0.0 ? (double)(npix * o.spp) / rs.sum_q[d] : 1.0;
+        Fnh[d] = (float)(fn < 1.0 ? fn : 1.0);
     }
     b.offset[D] = off;
     b.total = off;

@@ -257,9 +257,14 @@ void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* 
     out->nodes.clear();
     Box all;
     for (const Prim& p : prims) all.grow(p.box);
-    float ext = 0.0f;
-    for (int k = 0; k < 3; ++k) ext = std::max(ext, all.hi[k] - all.lo[k]);
-    Builder bld{prims, out->nodes, 1e-5f * ext + 1e-30f};
+    float ext = 0.0f, mag = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        ext = std::max(ext, all.hi[k] - all.lo[k]);
+        mag = std::max(mag, std::max(std::fabs(all.lo[k]), std::fabs(all.hi[k])));
+    }
+    // the margin covers the slab test's rounding: 1e-5 of the scene's size, and at least
+    // 4 ulp of the largest coordinate (the products o * (1/d) round relative to |o|)
+    Builder bld{prims, out->nodes, 1e-5f * ext + 4.0f * 0x1p-23f * mag + 1e-30f};
     Box root_box;
     int32_t root_count = 0;
     int32_t root = bld.build(0, n_ref, 0, &root_box, &root_count);

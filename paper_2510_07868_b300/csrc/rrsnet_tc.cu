@@ -12,7 +12,11 @@
 // Shared-memory operands use the canonical K-major layout without swizzle: 8-row x
 // 16-byte core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups
 // (K / 8) * 128 bytes apart (SBO).  One CTA of 128 threads owns one TMEM allocation of 32
-// columns; thread t of the tile is row t and TMEM lane t.
+// columns; thread t of the tile is row t and TMEM lane t.  One A buffer (K = 32 layout)
+// serves all three layers: layer 1 reads its first 16 columns (the 8-row groups stay
+// 512 bytes apart), and each layer's output overwrites it only after that layer's MMAs
+// have completed.  Every thread loads its own feature row from global memory one tile
+// ahead, so the CTA needs about 26 KB of shared memory and eight fit on an SM.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -32,13 +36,9 @@ struct __align__(128) TcSmem {
     unsigned char w1[2][32 * 16 * 2];   // B of layer 1 (hi, lo): N = 32 rows, K = 16
     unsigned char w2[2][32 * 32 * 2];   // B of layer 2 (hi, lo)
     unsigned char w3[2][32 * 32 * 2];   // B of layer 3 (hi, lo)
-    unsigned char a1[2][128 * 16 * 2];  // A of layer 1 (hi, lo): 128 rows, K = 16
-    unsigned char a2[2][128 * 32 * 2];  // A of layers 2 and 3 (hi, lo): 128 rows, K = 32
+    unsigned char a[2][128 * 32 * 2];   // A of every layer (hi, lo): 128 rows, K = 32 layout
     float w4[32];
-    float4 stage[kTcThreads * 4];  // the tile's feature rows, staged by a bulk copy
     unsigned long long bar;
-    unsigned long long tbar;       // completion of the staging copy
-    int staging;                   // a staging copy has been issued and not yet waited for
     uint32_t tmem;
 };
 
@@ -177,7 +177,7 @@ __device__ __forceinline__ float softplus_mod_tc(float z) {
 
 // n_ptr: device row count (render) or null with n_host (stand-alone).  q_in: when set,
 // only rows with q_in < 0 are written (the render's NET slots).
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, 8)  // 8 CTAs (8 tiles in flight) per SM
 k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
             const long long* n_ptr, long long n_host, float* q, int sentinel, DevStats* st,
             unsigned int* status) {
@@ -193,10 +193,7 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.tbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        stage_tile(sm.stage, feat, blockIdx.x, n, smem_u32(&sm.tbar));  // first tile
-        sm.staging = 1;
     }
     // weights -> split BF16 B operands (W is [out][in] row-major = N rows of K)
     for (int e = tid; e < 32 * 16; e += kTcThreads)
@@ -214,45 +211,34 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
     const uint32_t tmem = sm.tmem;
     const uint32_t bar = smem_u32(&sm.bar);
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-    uint64_t dw1[2], dw2[2], dw3[2], da1[2], da2[2];
-#pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-        dw1[h2] = smem_desc(smem_u32(sm.w1[h2]), 128, 256);
-        dw2[h2] = smem_desc(smem_u32(sm.w2[h2]), 128, 512);
-        dw3[h2] = smem_desc(smem_u32(sm.w3[h2]), 128, 512);
-        da1[h2] = smem_desc(smem_u32(sm.a1[h2]), 128, 256);
-        da2[h2] = smem_desc(smem_u32(sm.a2[h2]), 128, 512);
-    }
     const uint64_t k16 = 256 >> 4;  // start address step of K = 16 (two core matrices)
-    uint32_t phase = 0, tphase = 0;
-    const uint32_t tbar = smem_u32(&sm.tbar);
+    uint32_t phase = 0;
     unsigned int evals = 0, nonfinite = 0;
     bool failed = false;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    // this thread's feature row of the first tile (zeros past the end)
+    float4 xr[4];
+    auto load_row = [&](long long tile) {
+        const long long row = tile * kTcThreads + tid;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            xr[k] = row < n ? __ldg(feat + 4 * row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    load_row(blockIdx.x);
     for (long long tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
         const long long row = tile * kTcThreads + tid;
         bool active = row < n;
         if (active && sentinel) active = q[row] < 0.0f;
-        const bool staged = mbar_wait(tbar, tphase);  // this tile's rows are in sm.stage
-        if (__syncthreads_or(!staged)) {
-            failed = true;
-            break;
-        }
-        tphase ^= 1u;
-        if (tid == 0) sm.staging = 0;
         float x[16];
-        if (active) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float4 v = sm.stage[4 * tid + k];
-                x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = active ? xr[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
         }
-        store_split8(sm.a1[0], sm.a1[1], tid, 0, 16, x);
-        store_split8(sm.a1[0], sm.a1[1], tid, 1, 16, x + 8);
+        // the next tile's row is fetched while this one runs through the network
+        if (tile + gridDim.x < tiles) load_row(tile + gridDim.x);
+        store_split8(sm.a[0], sm.a[1], tid, 0, 32, x);
+        store_split8(sm.a[0], sm.a[1], tid, 1, 32, x + 8);
         float h[32];
         for (int layer = 0; layer < 3 && !failed; ++layer) {
             fence_async_smem();
@@ -261,22 +247,20 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
             if (tid == 0) {
                 fence_after();
                 // hi*hi + lo*hi + hi*lo for every K = 16 step, one FP32 accumulator
-                const uint64_t* A = layer == 0 ? da1 : da2;
-                const uint64_t* B = layer == 0 ? dw1 : layer == 1 ? dw2 : dw3;
+                const unsigned char* wb = layer == 0 ? sm.w1[0] : layer == 1 ? sm.w2[0] : sm.w3[0];
+                const uint32_t wstep = layer == 0 ? 32 * 16 * 2 : 32 * 32 * 2;  // hi -> lo
+                const uint64_t b0 = smem_desc(smem_u32(wb), 128, layer == 0 ? 256 : 512);
+                const uint64_t b1 = smem_desc(smem_u32(wb) + wstep, 128, layer == 0 ? 256 : 512);
+                const uint64_t a0 = smem_desc(smem_u32(sm.a[0]), 128, 512);
+                const uint64_t a1 = smem_desc(smem_u32(sm.a[1]), 128, 512);
                 const int ksteps = layer == 0 ? 1 : 2;
                 for (int ks = 0; ks < ksteps; ++ks) {
                     const uint64_t o = ks * k16;
-                    mma_bf16(tmem, A[0] + o, B[0] + o, ks > 0 ? 1u : 0u);
-                    mma_bf16(tmem, A[1] + o, B[0] + o, 1u);
-                    mma_bf16(tmem, A[0] + o, B[1] + o, 1u);
+                    mma_bf16(tmem, a0 + o, b0 + o, ks > 0 ? 1u : 0u);
+                    mma_bf16(tmem, a1 + o, b0 + o, 1u);
+                    mma_bf16(tmem, a0 + o, b1 + o, 1u);
                 }
                 mma_commit(bar);
-                // every lane has read its staged row (barrier above): stage the next tile
-                // while this one runs through the network
-                if (layer == 0 && tile + gridDim.x < tiles) {
-                    stage_tile(sm.stage, feat, tile + gridDim.x, n, tbar);
-                    sm.staging = 1;
-                }
             }
             const bool ok = mbar_wait(bar, phase);
             phase ^= 1u;
@@ -294,10 +278,10 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
                 h[j + 1] = fmaxf(h[j + 1], s.y);
             }
             if (layer < 2) {
-                fence_before();
-                __syncthreads();  // every lane's MMA reads of a2 are complete (barrier fired)
+                // every MMA read of the A buffer is complete (the commit barrier fired and
+                // every lane has passed it): the next layer's operand overwrites it
 #pragma unroll
-                for (int c = 0; c < 4; ++c) store_split8(sm.a2[0], sm.a2[1], tid, c, 32, h + 8 * c);
+                for (int c = 0; c < 4; ++c) store_split8(sm.a[0], sm.a[1], tid, c, 32, h + 8 * c);
             }
         }
         if (failed) break;
@@ -315,10 +299,6 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         }
         fence_before();
         __syncthreads();  // TMEM reads done before the next tile's MMA overwrites it
-    }
-    if (failed) {  // let a staging copy still in flight land before the CTA leaves
-        __syncthreads();
-        if (sm.staging) mbar_wait(tbar, tphase);
     }
     if (failed && tid == 0 && status) atomicOr(status, (unsigned int)NRRS_STATUS_TIMEOUT);
     if (st) {

@@ -144,6 +144,124 @@ __device__ __forceinline__ bool visit_node4(const SceneView& sc, Ray& r, Hit& h,
     return false;
 }
 
+// ------------------------------------------------------------------ eight-wide tree
+// Key order of a node's children for a ray of direction octant `oct` (bit k set when the
+// direction's component k is negative): slot s (bit k set = the child's centre on the +
+// side of axis k) gets key s ^ oct, so the children nearest the corner the ray comes
+// from come first.  Permutes an 8-bit mask of slots into key order.
+__device__ __forceinline__ uint32_t slot_to_key_mask(uint32_t m, uint32_t oct) {
+    if (oct & 1u) m = ((m & 0x55u) << 1) | ((m & 0xAAu) >> 1);
+    if (oct & 2u) m = ((m & 0x33u) << 2) | ((m & 0xCCu) >> 2);
+    if (oct & 4u) m = ((m & 0x0Fu) << 4) | ((m & 0xF0u) >> 4);
+    return m;
+}
+
+// Byte c of the pair as the float 2^23 + byte: one byte permute builds its bits
+// (0x4B00_00bb), so no integer-to-float conversion is needed.
+__device__ __forceinline__ float byte_f(uint2 w, int c) {
+    return __uint_as_float(__byte_perm(c < 4 ? w.x : w.y, 0x4B000000u, 0x7650u + (uint32_t)(c & 3)));
+}
+
+// Visits one eight-wide node (bvh8.cu's layout): decodes the eight quantised child
+// boxes (origin plus byte times a power of two per axis, the near and far planes picked
+// by the ray's direction signs), intersects the triangles of the leaf children it
+// enters, and returns the inner children entered that are still in reach as a mask in
+// key order, with the node's first-child index and inner mask.  A plane's distance is
+// fma(2^23 + byte, s, a - 2^23 s) with s = 2^e / d: the bias term rounds by at most half
+// a step of s, inside the one-step widening the builder gives every box.
+__device__ __forceinline__ uint32_t visit_node8(const SceneView& sc, const Ray& r, Hit& h,
+                                                int node, uint32_t oct, uint32_t* base,
+                                                uint32_t* imask, int* first) {
+    const uint4* N = sc.nodes8 + 5 * (size_t)node;
+    const uint4 w0 = __ldg(N + 0), w1 = __ldg(N + 1);
+    const uint4 w2 = __ldg(N + 2), w3 = __ldg(N + 3), w4 = __ldg(N + 4);
+    const float sx = __uint_as_float((w0.w & 0xFFu) << 23) * r.inv.x;
+    const float sy = __uint_as_float(((w0.w >> 8) & 0xFFu) << 23) * r.inv.y;
+    const float sz = __uint_as_float(((w0.w >> 16) & 0xFFu) << 23) * r.inv.z;
+    const float ax = fmaf(__uint_as_float(w0.x), r.inv.x, -r.oi.x) - 8388608.0f * sx;
+    const float ay = fmaf(__uint_as_float(w0.y), r.inv.y, -r.oi.y) - 8388608.0f * sy;
+    const float az = fmaf(__uint_as_float(w0.z), r.inv.z, -r.oi.z) - 8388608.0f * sz;
+    const uint2 lox = make_uint2(w2.x, w2.y), loy = make_uint2(w2.z, w2.w);
+    const uint2 loz = make_uint2(w3.x, w3.y), hix = make_uint2(w3.z, w3.w);
+    const uint2 hiy = make_uint2(w4.x, w4.y), hiz = make_uint2(w4.z, w4.w);
+    const uint2 nx = (oct & 1u) ? hix : lox, fx = (oct & 1u) ? lox : hix;
+    const uint2 ny = (oct & 2u) ? hiy : loy, fy = (oct & 2u) ? loy : hiy;
+    const uint2 nz = (oct & 4u) ? hiz : loz, fz = (oct & 4u) ? loz : hiz;
+    const uint32_t im = w0.w >> 24;
+    float tn[8];
+    uint32_t hits = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float n0 = fmaxf(fmaf(byte_f(nx, c), sx, ax), fmaf(byte_f(ny, c), sy, ay));
+        const float f0 = fminf(fmaf(byte_f(fx, c), sx, ax), fmaf(byte_f(fy, c), sy, ay));
+        tn[c] = fmaxf(n0, fmaxf(fmaf(byte_f(nz, c), sz, az), 0.0f));
+        const float tf = fminf(f0, fminf(fmaf(byte_f(fz, c), sz, az), h.t));
+        hits |= (tn[c] <= tf ? 1u : 0u) << c;
+    }
+    // leaf children entered: their triangles now (they can shorten h.t for the rest)
+    uint32_t leaves = hits & ~im;
+    while (leaves) {
+        const int c = __ffs(leaves) - 1;
+        leaves &= leaves - 1u;
+        const uint32_t meta = ((c < 4 ? w1.z : w1.w) >> (8 * (c & 3))) & 0xFFu;
+        const int first = (int)(w1.y + (meta & 31u));
+        for (int j = 0; j < (int)(meta >> 5); ++j) intersect_tri(sc, r, h, first + j);
+    }
+    uint32_t inner = 0;
+    float best = FLT_MAX;
+    int nearest = -1;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if ((hits & im & (1u << c)) && tn[c] <= h.t) {
+            inner |= 1u << c;
+            if (tn[c] < best) {
+                best = tn[c];
+                nearest = c;
+            }
+        }
+    *base = w1.x;
+    *imask = im;
+    *first = nearest;
+    return slot_to_key_mask(inner, oct);
+}
+
+// One step of the eight-wide traversal: visit r.node, then descend into its nearest
+// child entered (least entry distance; the others wait on the stack in key order), or
+// take the next child of the last group on the stack.  A stack entry is (node << 8 | the mask of its children still to visit, in key
+// order); the node's first-child index and inner mask are read again on the pop.  At
+// most one entry per tree level, so the build's depth bound keeps it within kStack.
+// Returns true when the query ends.
+__device__ __forceinline__ bool step_node8(const SceneView& sc, Ray& r, Hit& h, int* stk,
+                                           int stride, uint32_t oct) {
+    uint32_t base, imask;
+    int nearest;
+    uint32_t keys = visit_node8(sc, r, h, r.node, oct, &base, &imask, &nearest);
+    uint32_t group = (uint32_t)r.node;
+    if (keys) {
+        // descend into the nearest child entered first; the others wait in key order
+        const uint32_t k = (uint32_t)nearest ^ oct;
+        keys &= ~(1u << k);
+        if (keys) stk[(r.sp++) * stride] = (int)(group << 8 | keys);
+        r.node = (int)(base + (uint32_t)__popc(imask & ((1u << nearest) - 1u)));
+        return false;
+    }
+    {
+        if (r.sp == 0) return true;
+        const uint32_t e = (uint32_t)stk[(--r.sp) * stride];
+        group = e >> 8;
+        keys = e & 0xFFu;
+        const uint4* N = sc.nodes8 + 5 * (size_t)group;
+        imask = __ldg(&N[0].w) >> 24;
+        base = __ldg(&N[1].x);
+    }
+    const uint32_t k = (uint32_t)(__ffs(keys) - 1);
+    keys &= keys - 1u;
+    const uint32_t slot = k ^ oct;
+    if (keys) stk[(r.sp++) * stride] = (int)(group << 8 | keys);
+    r.node = (int)(base + (uint32_t)__popc(imask & ((1u << slot) - 1u)));
+    return false;
+}
+
 // The (lo, hi) pair of binary16 values in one word of a half-precision node.
 __device__ __forceinline__ float2 half_pair(uint32_t w) {
     return __half22float2(*reinterpret_cast<const __half2*>(&w));
@@ -250,7 +368,7 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
                         if (jobs.job) {
                             const uint32_t pix = __float_as_uint(ANY ? w.dep[idx].w : o4.w);
                             const JobDev* J = jobs.job + job_of_pixel(jobs.job, jobs.n, pix);
-                            root = WIDTH == 4 ? __ldg(&J->root4) : __ldg(&J->root);
+                            root = WIDTH == 4 ? __ldg(&J->root4) : WIDTH == 8 ? 0 : __ldg(&J->root);
                         }
                         if (ANY)
                             ray_init(ray, xyz(o4), xyz(w.sh_d[idx]), root, h, o4.w);
@@ -264,7 +382,15 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
         }
         // lanes that skipped a slot claim again on the next round
         if (__all_sync(0xffffffffu, idx < 0 && exhausted)) break;
-        if (WIDTH == 4) {
+        if (WIDTH == 8) {
+            if (idx < 0) continue;
+            const uint32_t oct = (ray.inv.x < 0.0f ? 1u : 0u) | (ray.inv.y < 0.0f ? 2u : 0u) |
+                                 (ray.inv.z < 0.0f ? 4u : 0u);
+            bool done = false;
+            for (int step = 0; step < kSteps && !done; ++step)
+                done = step_node8(sc, ray, h, stk, kExtendThreads, oct) || (ANY && h.slot >= 0);
+            if (!done) continue;
+        } else if (WIDTH == 4) {
             if (idx < 0) continue;
             bool done = false;
             for (int step = 0; step < kSteps && !done; ++step)
@@ -309,18 +435,22 @@ int trace_stack_entries() { return kStack; }
 
 int max_blocks_trace() {
     int nb = 1 << 30;
-    int n[4] = {1, 1, 1, 1};
+    int n[6] = {1, 1, 1, 1, 1, 1};
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_trace<2, false>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_trace<4, false>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_trace<2, true>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_trace<4, true>, kExtendThreads, 0);
-    for (int k = 0; k < 4; ++k) nb = n[k] < nb ? n[k] : nb;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[4], k_trace<8, false>, kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[5], k_trace<8, true>, kExtendThreads, 0);
+    for (int k = 0; k < 6; ++k) nb = n[k] < nb ? n[k] : nb;
     return nb < 1 ? 1 : nb;
 }
 
 void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int depth, int grid,
                   const JobWork& jobs, cudaStream_t s) {
-    if (sc.nodes4)
+    if (sc.nodes8)
+        k_trace<8, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+    else if (sc.nodes4)
         k_trace<4, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
     else
         k_trace<2, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
@@ -329,7 +459,9 @@ void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int dep
 void launch_shadow(const SceneView& sc, const WorkView& w, int depth, int grid,
                    const JobWork& jobs, cudaStream_t s) {
     const QueueView none{};
-    if (sc.nodes4)
+    if (sc.nodes8)
+        k_trace<8, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
+    else if (sc.nodes4)
         k_trace<4, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
     else
         k_trace<2, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);

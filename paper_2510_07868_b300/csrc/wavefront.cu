@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(256) k_sum_q(WorkView w, QueueView cur, Render
 }
 
 // Eq. F_norm / q_norm_rate / f_rate_prime, downscale only:
-// F = min(1, f_rate * alpha * C / sum q), computed in FP64 and rounded to FP32.
+// F = min(1, f_rate * alpha * N_px / sum q), computed in FP64 and rounded to FP32.
 __global__ void k_normalize_depth(WorkView w, RenderParams rp, int depth, int normalized) {
     __shared__ double sh[32];
     DevStats* st = w.st;
@@ -473,7 +473,7 @@ __global__ void k_normalize_depth(WorkView w, RenderParams rp, int depth, int no
         const double alpha = st->alpha_cur;
         double F = 1.0;
         if (normalized && s > 0.0) {
-            F = (double)rp.f_rate * alpha * (double)rp.cap / s;
+            F = (double)rp.f_rate * alpha * rp.budget / s;
             if (F > 1.0) F = 1.0;
         }
         st->sum_q[depth - 1] = s;
@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_sum_q_jobs(WorkView w, QueueV
     }
 }
 
-// F_j = min(1, f_rate * alpha * C_j / sum_j q), summed over the blocks in a fixed order.
+// F_j = min(1, f_rate * alpha * N_j / sum_j q) with job j's budget N_j, summed over the
+// blocks in a fixed order.
 __global__ void k_normalize_jobs(WorkView w, RenderParams rp, int depth, int normalized,
                                  int G) {
     const JobWork& J = rp.jobs;
@@ -558,7 +559,7 @@ __global__ void k_normalize_jobs(WorkView w, RenderParams rp, int depth, int nor
         }
         double F = 1.0;
         if (normalized && s > 0.0) {
-            F = (double)rp.f_rate * alpha * (double)J.cap_factor * (double)J.job[j].prims / s;
+            F = (double)rp.f_rate * alpha * (double)J.budget_factor * (double)J.job[j].prims / s;
             if (F > 1.0) F = 1.0;
         }
         J.F_cur[j] = (float)F;
@@ -727,9 +728,10 @@ __device__ void scan_counts(const unsigned long long* cnt, unsigned long long* o
 
 // Split of depth `depth` in one pass (count, compaction and scatter fused; Eq. rrs_factor
 // and the bounded queue of Sec. 3.1).  Blocks claim 256-slot tiles in order; each tile
-// adds its pixels' deposits (run heads, as k_split_count), decides every parent's X, and
-// finds its first child slot by a decoupled look-back over the earlier tiles' published
-// counts (aggregate, or inclusive prefix once known), then writes its children.  Tiles
+// decides every parent's X, finds its first child slot by a decoupled look-back over the
+// earlier tiles' published counts (aggregate, or inclusive prefix once known) while the
+// other warps add the tile's deposits per pixel run (run heads, as k_split_count), then
+// writes its children.  Tiles
 // are claimed in increasing order by running blocks, so every tile waited on belongs to
 // a block that is running or done; each wait is bounded all the same (a timeout sets
 // NRRS_STATUS_TIMEOUT and the tile drops its children rather than hang).  The last tile
@@ -762,28 +764,6 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
         float qu = 0.0f;
         float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = o4, t4 = o4;
         if (i < n) {
-            // this depth's deposits, summed per pixel run by the run's first slot
-            const float4 dep = w.dep[i];
-            const uint32_t pix = fbits(dep.w);
-            if (i == 0 || fbits(w.dep[i - 1].w) != pix) {
-                float sx = dep.x, sy = dep.y, sz = dep.z;
-                bool more = true;
-                for (long long j0 = i + 1; more && j0 < n; j0 += 8) {
-                    float4 e[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        e[k] = j0 + k < n ? w.dep[j0 + k] : make_float4(0.f, 0.f, 0.f, bitsf(~pix));
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (!more || fbits(e[k].w) != pix) {
-                            more = false;
-                        } else {
-                            sx += e[k].x; sy += e[k].y; sz += e[k].z;
-                        }
-                    }
-                }
-                kahan_add(&w.acc_s[pix], &w.acc_c[pix], sx, sy, sz);
-            }
             o4 = cur.o[i];
             d4 = cur.d[i];
             t4 = cur.t[i];
@@ -844,6 +824,32 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
                         st->status |= NRRS_STATUS_OVERFLOW_DROPPED;
                     }
                 }
+            }
+        }
+        // this depth's deposits, summed per pixel run by the run's first slot: after the
+        // tile's count is published, so the serial run sums of the other warps overlap
+        // warp 0's look-back instead of delaying the tiles that wait on this one
+        if (i < n) {
+            const float4 dep = w.dep[i];
+            const uint32_t pix = fbits(dep.w);
+            if (i == 0 || fbits(w.dep[i - 1].w) != pix) {
+                float sx = dep.x, sy = dep.y, sz = dep.z;
+                bool more = true;
+                for (long long j0 = i + 1; more && j0 < n; j0 += 8) {
+                    float4 e[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        e[k] = j0 + k < n ? w.dep[j0 + k] : make_float4(0.f, 0.f, 0.f, bitsf(~pix));
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!more || fbits(e[k].w) != pix) {
+                            more = false;
+                        } else {
+                            sx += e[k].x; sy += e[k].y; sz += e[k].z;
+                        }
+                    }
+                }
+                kahan_add(&w.acc_s[pix], &w.acc_c[pix], sx, sy, sz);
             }
         }
         __syncthreads();

@@ -12,6 +12,8 @@ struct SceneView {
     const float4* nodes;  // 4 float4 per node (bvh.cpp)
     const float4* nodes4; // four-wide tree, 8 float4 per node; NULL = traverse the BVH2
     const uint4* nodes_h; // the BVH2 with FP16 boxes, 2 uint4 per node; NULL = FP32 nodes
+    const uint4* nodes8;  // compressed eight-wide tree (bvh8.cu), 5 uint4 per node; when set
+                          // it is traversed and `tris` is that tree's triangle order
     const float4* tris;   // 3 float4 per triangle, BVH order
     const nrrs_material* mats;
     float lo[3];          // scene box, for the position feature
@@ -111,6 +113,7 @@ struct JobWork {
     const JobDev* job;   // [n]
     int n;
     int cap_factor;
+    int budget_factor;   // job j's normalisation budget = budget_factor * prims
     float* F_cur;        // [n] normalisation factor of the current depth
     float* eps_I;        // [n] HEUR floor of each job
     double* part;        // [grid_red][n] per-block partial sums of q
@@ -133,6 +136,7 @@ __device__ __forceinline__ int job_of_pixel(const JobDev* job, int n, uint32_t p
 struct RenderParams {
     int W, H, spp, D;
     long long cap;        // C
+    double budget;        // N_px of Eq. F_norm (single scene; a batch: JobWork::budget_factor)
     const FrameConsts* fc;
     JobWork jobs;         // batched render (jobs.job != nullptr), else unused
     float f_rate;

@@ -269,12 +269,14 @@ def icosphere_room(seed: int = 1, min_triangles: int = 200_000, subdiv: int = 3)
 
 
 def three_rooms(seed: int = 1, n_random: int = 1_000_000, tri_size: float = 0.01,
-                n_palette: int = 64) -> Scene:
+                n_palette: int = 64, emitter_room: int = 2) -> Scene:
     """Three unit rooms along x ([0,3] x [0,1] x [0,1]) joined by doorways 0.1 wide
     (z in [0.45, 0.55]) and 0.2 high (y in [0, 0.2]) in the walls at x = 1 and x = 2.
 
-    One 0.1 x 0.1 emitter of radiance 200 under the ceiling of room 3 (centre x = 2.5,
-    z = 0.5), the camera in room 1 at (0.05, 0.1, 0.5) looking +x, through both doorways.  ``n_random``
+    One 0.1 x 0.1 emitter of radiance 200 under the ceiling of room ``emitter_room``
+    (centre x = room - 0.5, z = 0.5; room 2 by default: from room 3 almost no light reaches
+    the camera through the dust and both doorways), the camera in room 1 at
+    (0.05, 0.1, 0.5) looking +x, through both doorways.  ``n_random``
     two-sided triangles (centre uniform in the rooms, vertices centre +
     U[-s/2, s/2]^3) draw their material from a palette of ``n_palette``: 60% GGX plastic
     (roughness U[0.05, 0.5], F0 0.04), the rest Lambertian; albedo U[0.1, 0.9].
@@ -290,7 +292,7 @@ def three_rooms(seed: int = 1, n_random: int = 1_000_000, tri_size: float = 0.01
                                  (0.45, 0.55, 0.2, 1.0)):
             tris += _quad(P(x, y0, z0), P(x, y0, z1), P(x, y1, z1), P(x, y1, z0))
             mat_id += [2, 2]
-    tris += _ceiling_emitter(2.5, 0.5, 0.1)
+    tris += _ceiling_emitter(emitter_room - 0.5, 0.5, 0.1)
     mat_id += [1, 1]
     first = len(mats)
     n_ggx = int(round(0.6 * n_palette))

@@ -46,7 +46,7 @@ EXPORTED = [
     "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
-    "nrrs_set_bvh_precision",
+    "nrrs_set_bvh_precision", "nrrs_bvh8_info", "nrrs_bvh8_export",
 ]
 
 
@@ -64,14 +64,14 @@ class RenderOpts(C.Structure):
                 ("update_ref", C.c_int32), ("reset_ref", C.c_int32), ("d_trace", C.c_void_p),
                 ("profile", C.c_int32), ("graph", C.c_int32), ("d_suffix", C.c_void_p),
                 ("nee", C.c_int32), ("d_trace_mask", C.c_void_p), ("d_trace_count", C.c_void_p),
-                ("trace_rows", C.c_int64)]
+                ("trace_rows", C.c_int64), ("budget_factor", C.c_int32)]
 
     @classmethod
     def defaults(cls, **kw):
         o = cls(seed_lo=1, seed_hi=0, frame=0, cap_factor=2, f_rate=0.85, alpha0=1.0, q_max=16.0,
                 eps_rel=0.01, boxcox_lambda=0.5, precision=32, gate=0, d_pixel_ref=None,
                 update_ref=1, reset_ref=0, d_trace=None, profile=0, graph=0, d_suffix=None,
-                nee=0, d_trace_mask=None, d_trace_count=None, trace_rows=0)
+                nee=0, d_trace_mask=None, d_trace_count=None, trace_rows=0, budget_factor=0)
         for k, v in kw.items():
             setattr(o, k, v)
         return o
@@ -146,6 +146,14 @@ class TuneReport(C.Structure):
         return {"precision": self.precision, "rows": list(self.rows[:n]),
                 "variant": list(self.variant[:n]), "blocks_per_sm": list(self.blocks_per_sm[:n]),
                 "ms_best": list(self.ms_best[:n]), "ms_default": list(self.ms_default[:n])}
+
+
+class Bvh8Stats(C.Structure):
+    _fields_ = [("nodes", C.c_int64), ("triangles", C.c_int64), ("depth", C.c_int32),
+                ("iterations", C.c_int32), ("build_ms", C.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class TrainDebug(C.Structure):
@@ -238,6 +246,8 @@ def _load():
         "nrrs_batch_info": ([P, P, P, P], I32),
         "nrrs_set_traversal": ([P, I32], I32),
         "nrrs_set_bvh_precision": ([P, I32], I32),
+        "nrrs_bvh8_info": ([P, P], I32),
+        "nrrs_bvh8_export": ([P, P, I64, P, I64], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -516,6 +526,22 @@ def nrrs_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, b1=0.9, b2=0.999, ep
 
 def nrrs_ema(d_avg, d_params, n, decay, stream=None):
     _check(_lib.nrrs_ema(_ptr(d_avg), _ptr(d_params), n, decay, _stream(stream)))
+
+
+def nrrs_bvh8_info(scene):
+    st = Bvh8Stats()
+    _check(_lib.nrrs_bvh8_info(scene, C.byref(st)))
+    return st.as_dict()
+
+
+def nrrs_bvh8_export(scene):
+    """Host copies of the eight-wide tree: nodes [n][20] uint32, tris [n_tri][12] float32."""
+    info = nrrs_bvh8_info(scene)
+    nodes = np.zeros((max(1, info["nodes"]), 20), dtype=np.uint32)
+    tris = np.zeros((max(1, info["triangles"]), 12), dtype=np.float32)
+    _check(_lib.nrrs_bvh8_export(scene, nodes.ctypes.data, nodes.shape[0], tris.ctypes.data,
+                                 tris.shape[0]))
+    return nodes, tris
 
 
 def nrrs_mixdepth_candidates(max_depth, t_d):

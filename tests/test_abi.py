@@ -59,7 +59,7 @@ def test_struct_layouts_match_header():
 
     from paper_2510_07868_b300 import inputs, nrrs
 
-    assert ctypes.sizeof(nrrs.RenderOpts) == 120
+    assert ctypes.sizeof(nrrs.RenderOpts) == 128
     assert ctypes.sizeof(nrrs.RenderStats) == 32 * (8 + 8 + 4 + 8 + 8 + 8) + 4 * 8 + 8 + 96
     assert inputs.MATERIAL_DTYPE.itemsize == 40 and inputs.CAMERA_DTYPE.itemsize == 40
 

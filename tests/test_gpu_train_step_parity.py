@@ -92,10 +92,10 @@ def _oracle_step(scene, P, S, ref, frame, E_acc_prev, full):
     if not full:
         dq = 2.0 * (q - 1.0) / (1.0 + EPS) / N
     else:
-        C_ = 2 * W * H * SPP
+        N_px = W * H * SPP  # Eq. F_norm's budget: the primary queue
         F = st["F"].astype(np.float64)
         sq = st["sum_q"]
-        Fn = np.where(sq > 0, np.minimum(1.0, C_ / np.where(sq > 0, sq, 1.0)), 1.0)
+        Fn = np.where(sq > 0, np.minimum(1.0, N_px / np.where(sq > 0, sq, 1.0)), 1.0)
         Iref = ref.reshape(-1, 3).mean(axis=1)
         dq, _ = oracle.rrsnet_dloss(q, F[depth], Fn[depth], t.mean(axis=1), pix, m1, m2, E, Iref,
                                     k, eps=EPS, g=GAMMA, q_used=r[:, 10])

@@ -438,10 +438,18 @@ def test_adaptive_alpha_backoff():
 def test_downscale_only_normalisation():
     """Sec. 4 "Compromise": F >= 1 is never applied (q is only scaled down)."""
     s = I.box_scene(1)
+    P = 16 * 16 * 4
     img, st, _ = oracle.render(s, 16, 16, 4, 8, oracle.MODE_HEUR_NORM, frame=0)
     assert np.all(st["F"] <= 1.0)
-    # first frame, q = lum(t) <= 1 and the queue shrinks: no depth is rescaled
-    assert np.all(st["F"] == 1.0)
+    # budget N_px = P (the primary queue): F = min(1, 0.85 P / sum q) at every depth; the
+    # first frame has q = lum(t) <= 1, so only the first depths can exceed 0.85 P
+    sq = st["sum_q"]
+    expect = np.where(sq > 0, np.minimum(1.0, 0.85 * P / np.where(sq > 0, sq, 1.0)), 1.0)
+    np.testing.assert_array_equal(st["F"], expect.astype(np.float32))
+    assert st["F"][0] < 1.0 and st["F"][-1] == 1.0
+    # budget 2 P: the queue never asks for more than 0.85 x 2 P, so no depth is rescaled
+    _, st2, _ = oracle.render(s, 16, 16, 4, 8, oracle.MODE_HEUR_NORM, frame=0, budget=2 * P)
+    assert np.all(st2["F"] == 1.0)
 
 
 def test_nonfinite_network_factors_fall_back_to_the_heuristic():
