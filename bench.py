@@ -43,7 +43,7 @@ UNIT = "path segments/s"
 HL_W, HL_H, HL_SPP, HL_DEPTH = 1920, 1080, 16, 32
 HL_FRAMES = 8                        # 8 frames x 16 spp = 128 spp
 HL_TRAIN = (480, 270, 4)             # online training frames of the same scene
-HL_PRETRAIN = 120                    # untimed training steps before the search
+HL_PRETRAIN = 200                    # untimed training steps before the search
 HL_SEARCH = (480, 270)               # Mix-Depth estimation renders (1 spp)
 HL_PRECISION = 16                    # RRSNet on the tensor cores, split BF16 operands
 HL_WORKLOAD = ("three_rooms (1,000,000 random triangles, 60 % GGX) 1920x1080 px, depth 32, "
@@ -54,9 +54,10 @@ HL_WORKLOAD = ("three_rooms (1,000,000 random triangles, 60 % GGX) 1920x1080 px,
 W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
 TRAIN_SPP = 2          # recorded training frame: 256x256x2 spp ~ 2^19 training vertices
 PRETRAIN_STEPS = 300   # untimed online training before the timed steps (20 warm-up + 280 full)
-WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet FP32 factors (NET), cap 2*P; "
-            "step = online RRSNet/StatNet training step on a recorded 256x256x2 spp frame "
-            "+ the 16 spp inference frame")
+ONLINE_PRECISION = 16  # inference frame's RRSNet: split-BF16 tensor cores
+WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet split-BF16 tensor-core factors "
+            "(NET), budget P, cap 2*P; step = online RRSNet/StatNet training step on a recorded "
+            "256x256x2 spp frame + the 16 spp inference frame")
 EFF_SEEDS = 5          # independent render seeds per estimator in the efficiency tables
 # algorithmic bytes per unit of each stage
 BYTES_PER_RAY_EXTEND = 32 + 16                  # ray in, hit record out
@@ -460,7 +461,7 @@ def time_rrsnet_queries(nrrs, sc, torch, dev, stream, I):
     feats = torch.from_numpy(I.random_features(n_q, seed=3)).to(dev)
     qout = torch.empty(n_q, dtype=torch.float32, device=dev)
     ms = {}
-    for prec in (32, 16, 8):
+    for prec in (32, 16, 17, 8):
         for _ in range(3):
             sc.query(feats, out=qout, precision=prec)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -498,13 +499,15 @@ def online_section(args, nrrs, torch, dev, stream, seed_hi, local_rank, rank):
     def render(frame, profile=0):
         return nrrs.nrrs_render(sc.handle, W_IMG, H_IMG, SPP, DEPTH, nrrs.RRS_NET,
                                 nrrs.RenderOpts.defaults(frame=frame, seed_hi=seed_hi,
-                                                         profile=profile, graph=graph),
+                                                         profile=profile, graph=graph,
+                                                         precision=ONLINE_PRECISION),
                                 out, stream, True)
 
     tuner = {p: sc.tune(p) for p in (32, 16, 8)}
     for k in range(args.pretrain):
         train(10_000 + k)
-        render(20_000 + k)
+        if k % 4 == 3 or k >= args.pretrain - 8:  # the scene's running mean of frames
+            render(20_000 + k)
     warm_ms = np.zeros(nrrs.STAGES)
     warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
     for k in range(args.warmup):
@@ -792,8 +795,10 @@ def run_ours(args, rank, world, local_rank):
             "batch": n_q, "ms": qms,
             "tflops_fp32": tf[32], "fp32_simt_peak_tflops": fp32_peak,
             "frac_of_fp32_peak": tf[32] / fp32_peak,
-            "tflops_tensor_bf16x3": tf[16], "tflops_tensor_e4m3": tf[8],
+            "tflops_tensor_bf16x3": tf[16], "tflops_tensor_bf16": tf[17],
+            "tflops_tensor_e4m3": tf[8],
             "hbm_frac_bf16x3": 68 * n_q / (qms[16] / 1000) / 1e9 / hbm,
+            "hbm_frac_bf16": 68 * n_q / (qms[17] / 1000) / 1e9 / hbm,
             "hbm_frac_e4m3": 68 * n_q / (qms[8] / 1000) / 1e9 / hbm,
             "flop_cap_at_hbm_tflops": RRSNET_FLOP_PER_PATH * rows_per_s_hbm / 1e12,
             "frac_of_bf16_tensor_peak": tf[16] / bf16,
@@ -894,7 +899,7 @@ def main():
                     help="timed steps of the online-step section")
     ap.add_argument("--no-online", action="store_true",
                     help="skip the online-step section (occluded room)")
-    ap.add_argument("--rrsnet-only", type=int, choices=[32, 16, 8], default=0,
+    ap.add_argument("--rrsnet-only", type=int, choices=[32, 16, 17, 8], default=0,
                     help="time only RRSNet inference at this precision on a 2^21-row batch "
                          "(the untuned default launch shape), for kernel profiles")
     ap.add_argument("--tuned", action="store_true",

@@ -129,8 +129,9 @@ typedef struct nrrs_render_opts {
     float eps_rel;              /* HEUR: eps_I = eps_rel * mean(I_ref)              [0.01] */
     float boxcox_lambda;        /* throughput feature encoding                      [0.5]  */
     int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT), 16 (split BF16
-                                   operands) or 8 (E4M3 operands), tensor cores with
-                                   FP32 accumulation                                [32]   */
+                                   operands), 17 (BF16 operands rounded once) or 8
+                                   (E4M3 operands), tensor cores with FP32
+                                   accumulation                                     [32]   */
     uint64_t gate;              /* NET_MIX method per depth (NRRS_GATE_*)           [0]    */
     const float* d_pixel_ref;   /* device [H*W*3] reference I_px for HEUR, or NULL to use
                                    the scene's running mean of earlier frames       [NULL] */
@@ -316,6 +317,19 @@ NRRS_API nrrs_status nrrs_bvh8_export(const nrrs_scene* scene, uint32_t* nodes,
  * references). */
 NRRS_API nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits);
 
+/* Rebuilds the scene's BVH2 (and its FP16 copy and four-wide collapse) with another
+ * builder: 0 = the host binned-SAH builder of nrrs_create_scene (the default), 1 = the
+ * device build of the eight-wide tree stopped before its collapse (Morton order, then
+ * PLOC clustering; one triangle per leaf, depth-first node order).  Both trees hold every
+ * triangle with the same vertices and the traversal returns the closest hit with the
+ * lower-id tie rule, so renders do not depend on the builder; only the traversal cost
+ * does.  The FP16 choice is redone for the new tree (rule of nrrs_set_bvh_precision).
+ * build_ms (may be NULL) gets the build's wall time.  Synchronizes the device and drops
+ * the scene's captured graphs.  Errors: INVALID_ARG (NULL scene, builder not 0 or 1);
+ * UNSUPPORTED (a batch scene, fewer than two triangles, a device tree deeper than the
+ * traversal stack); CUDA / OOM (the old tree is kept). */
+NRRS_API nrrs_status nrrs_set_bvh_builder(nrrs_scene* scene, int32_t builder, float* build_ms);
+
 /* Chooses what RRSNet reads at the network depths of later renders and training steps
  * (the weights are the caller's to match; a change between modes 0/1 and 2 changes the
  * network's shape and starts RRSNet afresh):
@@ -384,14 +398,16 @@ NRRS_API nrrs_status nrrs_render(nrrs_scene* scene, int32_t width, int32_t heigh
  * d_q [n] float.
  * precision 32 = FP32 SIMT; 16 = tensor cores (tcgen05.mma kind::f16) with every MMA
  * operand split into two BF16 numbers (hi + lo, three MMAs per product) and FP32
- * accumulation; 8 = tensor cores (kind::f8f6f4) with E4M3 operands, one scale per weight
- * matrix and per 128-row activation tile, a power of two putting its largest magnitude
- * in (224, 448], FP32 accumulation.  The 32 -> 1 output layer and the activation run in FP32 in all three.
+ * accumulation; 17 = the same tensor cores with every operand rounded once to BF16
+ * (one MMA per product); 8 = tensor cores (kind::f8f6f4) with E4M3 operands, one scale
+ * per weight matrix and per 128-row activation tile, a power of two putting its largest
+ * magnitude in (224, 448], FP32 accumulation.  The 32 -> 1 output layer and the
+ * activation run in FP32 in all of them.
  * Feature layout (16 raw features in place of the paper's
  * encoded inputs of Sec. 4 "Input Encoding"): position normalised to the scene box (3),
  * outgoing direction (3), shading normal (3), albedo (3), depth / max_depth (1),
  * Box-Cox(t) with lambda = boxcox_lambda per throughput channel (3).
- * Errors: INVALID_ARG (n < 0, NULL with n > 0, unknown precision). */
+ * Errors: INVALID_ARG (n < 0, NULL with n > 0); UNSUPPORTED (unknown precision). */
 NRRS_API nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64_t n,
                                int32_t precision, float* d_q, void* stream);
 
@@ -582,7 +598,7 @@ NRRS_API nrrs_status nrrs_grid_backward(nrrs_scene* scene, const float* d_feat, 
 /* Autotuner of the RRSNet launch shape (no counterpart in the paper; it serves Sec. 4's
  * network in a queue whose size changes per bounce).  For every queue-size bucket b
  * (floor(log2 n) = b + 8, clamped to 0 .. NRRS_TUNE_BUCKETS - 1) it times each candidate
- * shape of the `precision` kernel (32: rows per thread 1 or 2 x blocks per SM; 16 and 8:
+ * shape of the `precision` kernel (32: rows per thread 1 or 2 x blocks per SM; 16, 17, 8:
  * tensor-core CTAs per SM) on 1.5 x 2^(b + 8) synthetic rows (at most 12,582,912) with
  * the scene's weights, and keeps the fastest for the scene.  Later renders pick the shape
  * of each depth from the bucket of that depth's queue size in the last frame rendered

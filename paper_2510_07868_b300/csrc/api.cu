@@ -245,9 +245,10 @@ struct nrrs_scene {
     CamView cam{};
     Workspace ws;
     int grid_trace = 0, grid_sum = 0;
-    // RRSNet launch shapes per queue-size bucket (FP32, BF16, E4M3), set by the tuner
-    RrsnetChoice tune[3][kTuneBuckets];
-    bool tuned[3] = {false, false, false};
+    // RRSNet launch shapes per queue-size bucket (FP32, split BF16, E4M3, BF16), set by
+    // the tuner
+    RrsnetChoice tune[4][kTuneBuckets];
+    bool tuned[4] = {false, false, false, false};
     // live counts of the last render that returned stats: the queue sizes expected at
     // each depth of the next frame (scaled by its primary count)
     long long last_live[NRRS_MAX_DEPTH] = {};
@@ -283,6 +284,7 @@ struct nrrs_scene {
         std::vector<int> stage_of;  // stage of every bracketed launch (profiled graphs)
     };
     std::vector<GraphEntry> graphs;
+    int32_t bvh_builder = 0;  // 0 host binned SAH, 1 device PLOC (nrrs_set_bvh_builder)
 };
 
 namespace {
@@ -422,7 +424,9 @@ struct StageTimer {
     }
 };
 
-int precision_index(int precision) { return precision == 32 ? 0 : precision == 16 ? 1 : 2; }
+int precision_index(int precision) {
+    return precision == 32 ? 0 : precision == 16 ? 1 : precision == 8 ? 2 : 3;
+}
 
 // Launch shape of the RRSNet kernel for a queue of about n rows.
 RrsnetChoice rrsnet_choice(const nrrs_scene* sc, int precision, long long n) {
@@ -650,6 +654,91 @@ nrrs_status nrrs_set_traversal(nrrs_scene* scene, int32_t width) {
     return NRRS_OK;
 }
 
+nrrs_status nrrs_set_bvh_builder(nrrs_scene* scene, int32_t builder, float* build_ms) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (builder != 0 && builder != 1)
+        return fail(NRRS_ERR_INVALID_ARG, "builder must be 0 (host binned SAH) or 1 (device PLOC)");
+    if (scene->n_jobs > 0 || !scene->tri_raw || scene->n_tri < 2)
+        return fail(NRRS_ERR_UNSUPPORTED, "the BVH2 is rebuilt for single scenes of two or more triangles");
+    DeviceGuard g(scene->device);
+    if (!g.ok) return fail(NRRS_ERR_CUDA, "cudaSetDevice failed");
+    CK(cudaDeviceSynchronize());
+    const size_t nt = (size_t)scene->n_tri;
+    std::vector<float> tri(nt * 9);
+    std::vector<int32_t> mat(nt);
+    CK(cudaMemcpy(tri.data(), scene->tri_raw, sizeof(float) * tri.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mat.data(), scene->mat_raw, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost));
+    const auto t0 = std::chrono::steady_clock::now();
+    BvhHost bvh;
+    if (builder == 0) {
+        build_bvh(tri.data(), (int32_t)nt, mat.data(), &bvh);
+    } else {
+        int depth = 0;
+        const cudaError_t e = build_bvh2_ploc(scene->tri_raw, tri.data(), mat.data(), (int)nt,
+                                              scene->scene_lo, scene->scene_hi,
+                                              trace_stack_entries() - 2, nullptr, &bvh, &depth);
+        if (e == cudaErrorNotSupported)
+            return fail(NRRS_ERR_UNSUPPORTED, "device-built BVH2 deeper than the traversal stack");
+        if (e != cudaSuccess) return cuda_fail(e, "device BVH2 build");
+    }
+    if (build_ms)
+        *build_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    Bvh4Host bvh4;
+    collapse_bvh4(bvh, &bvh4);
+    std::vector<BvhNodeH> half;
+    const bool has_half = pack_half_nodes(bvh, &half);
+    float4 *nodes = nullptr, *tris = nullptr, *nodes4 = nullptr;
+    uint4* nodes_h = nullptr;
+    auto bail = [&](cudaError_t e, const char* what) {
+        cudaFree(nodes);
+        cudaFree(tris);
+        cudaFree(nodes4);
+        cudaFree(nodes_h);
+        return cuda_fail(e, what);
+    };
+    cudaError_t e;
+    if ((e = dalloc(&nodes, bvh.nodes.size() * 4)) != cudaSuccess) return bail(e, "alloc nodes");
+    if ((e = dalloc(&tris, (size_t)bvh.n_ref * 3)) != cudaSuccess) return bail(e, "alloc tris");
+    if ((e = cudaMemcpy(nodes, bvh.nodes.data(), bvh.nodes.size() * 64, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "copy nodes");
+    if ((e = cudaMemcpy(tris, bvh.tris.data(), (size_t)bvh.n_ref * 48, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "copy tris");
+    if (bvh4.max_stack <= trace_stack_entries() && !bvh4.nodes.empty()) {
+        if ((e = dalloc(&nodes4, bvh4.nodes.size() * 8)) != cudaSuccess) return bail(e, "alloc nodes4");
+        if ((e = cudaMemcpy(nodes4, bvh4.nodes.data(), bvh4.nodes.size() * 128,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy nodes4");
+    }
+    if (has_half) {
+        if ((e = dalloc(&nodes_h, half.size() * 2)) != cudaSuccess) return bail(e, "alloc half nodes");
+        if ((e = cudaMemcpy(nodes_h, half.data(), half.size() * sizeof(BvhNodeH),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "copy half nodes");
+    }
+    const bool half_on = nodes_h && half_node_growth(bvh, half) <= kMaxHalfGrowth;
+    // captured graphs hold the old tree's addresses: drop them before freeing it
+    for (auto& ge : scene->graphs) cudaGraphExecDestroy(ge.exec);
+    scene->graphs.clear();
+    cudaFree(scene->nodes);
+    cudaFree(scene->tris);
+    cudaFree(scene->nodes4);
+    cudaFree(scene->nodes_h);
+    scene->nodes = nodes;
+    scene->tris = tris;
+    scene->nodes4 = nodes4;
+    scene->nodes_h = nodes_h;
+    scene->n_nodes = (int64_t)bvh.nodes.size();
+    scene->view.nodes = nodes;
+    scene->view.nodes_h = half_on ? nodes_h : nullptr;
+    if (scene->bvh_width == 4 && !nodes4) scene->bvh_width = 2;
+    if (scene->bvh_width != 8) {
+        scene->view.tris = tris;
+        scene->view.nodes4 = scene->bvh_width == 4 ? nodes4 : nullptr;
+    }
+    scene->bvh_builder = builder;
+    return NRRS_OK;
+}
+
 nrrs_status nrrs_bvh8_info(const nrrs_scene* scene, nrrs_bvh8_stats* out) {
     if (!scene || !out) return fail(NRRS_ERR_INVALID_ARG, "NULL scene or out");
     std::memset(out, 0, sizeof(*out));
@@ -751,8 +840,8 @@ nrrs_status validate_render(nrrs_scene* scene, int32_t width, int32_t height, in
         return fail(NRRS_ERR_INVALID_ARG, "budget_factor must lie in [0, cap_factor]");
     if (!(o.f_rate > 0.0f && o.f_rate <= 1.0f) || !(o.alpha0 > 0.0f && o.alpha0 <= 1.0f))
         return fail(NRRS_ERR_INVALID_ARG, "f_rate and alpha0 must lie in (0, 1]");
-    if (o.precision != 32 && o.precision != 16 && o.precision != 8)
-        return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16 and 8");
+    if (o.precision != 32 && o.precision != 16 && o.precision != 8 && o.precision != 17)
+        return fail(NRRS_ERR_UNSUPPORTED, "render supports precision 32, 16, 17 and 8");
     if (o.nee != 0 && o.nee != 1) return fail(NRRS_ERR_INVALID_ARG, "nee must be 0 or 1");
     if (scene->rrsnet_inputs == 2 && o.precision != 32)
         return fail(NRRS_ERR_UNSUPPORTED, "AID-NRRS inputs run in FP32 (precision 32)");
@@ -1414,8 +1503,8 @@ nrrs_status nrrs_query_factors(nrrs_scene* scene, const float* d_features, int64
                                int32_t precision, float* d_q, void* stream) {
     if (!scene || n < 0 || (n > 0 && (!d_features || !d_q)))
         return fail(NRRS_ERR_INVALID_ARG, "bad query arguments");
-    if (precision != 32 && precision != 16 && precision != 8)
-        return fail(NRRS_ERR_UNSUPPORTED, "precision must be 32, 16 or 8");
+    if (precision != 32 && precision != 16 && precision != 8 && precision != 17)
+        return fail(NRRS_ERR_UNSUPPORTED, "precision must be 32, 16, 17 or 8");
     if (scene->rrsnet_inputs == 2)
         return fail(NRRS_ERR_UNSUPPORTED, "the AID-NRRS network encodes its inputs inside the render");
     if (n == 0) return NRRS_OK;
@@ -1788,8 +1877,8 @@ nrrs_status nrrs_rrsnet_backward(nrrs_scene* scene, const float* d_params, const
 nrrs_status nrrs_tune_rrsnet(nrrs_scene* scene, int32_t precision, void* stream,
                              nrrs_tune_report* report) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
-    if (precision != 32 && precision != 16 && precision != 8)
-        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16 or 8");
+    if (precision != 32 && precision != 16 && precision != 8 && precision != 17)
+        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16, 17 or 8");
     static_assert(NRRS_TUNE_BUCKETS == kTuneBuckets, "bucket count");
     DeviceGuard g(scene->device);
     RrsnetChoice table[kTuneBuckets];
@@ -1823,8 +1912,8 @@ nrrs_status nrrs_tune_rrsnet(nrrs_scene* scene, int32_t precision, void* stream,
 nrrs_status nrrs_set_rrsnet_shape(nrrs_scene* scene, int32_t precision, int32_t bucket,
                                   int32_t variant, int32_t blocks_per_sm) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
-    if (precision != 32 && precision != 16 && precision != 8)
-        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16 or 8");
+    if (precision != 32 && precision != 16 && precision != 8 && precision != 17)
+        return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16, 17 or 8");
     if (bucket < -1 || bucket >= kTuneBuckets) return fail(NRRS_ERR_INVALID_ARG, "bad bucket");
     const bool ok_variant = precision == 32 ? (variant == 1 || variant == 2) : variant == 0;
     if (!ok_variant || blocks_per_sm < 1 || blocks_per_sm > 32)

@@ -43,6 +43,10 @@
 
 #include "bvh8.h"
 
+#include <algorithm>
+#include <cstring>
+#include <utility>
+
 namespace nrrs {
 
 namespace {
@@ -551,12 +555,20 @@ cudaError_t scan_u32(const uint32_t* in, int n, uint32_t* out, uint32_t* sums, u
     return cudaGetLastError();
 }
 
-}  // namespace
+// The clustered BVH2 of the build's first two steps (device arrays owned by `tmp`).
+struct PlocTree {
+    uint32_t* vals = nullptr;  // triangle of each leaf (sorted order)
+    float4 *blo = nullptr, *bhi = nullptr;  // node boxes: leaves 0..n-1, merges n..2n-2
+    uint32_t* cnt = nullptr;   // triangles under each node
+    int2* kids = nullptr;      // children of merge node n + k at k
+    uint32_t* sums = nullptr;  // scan scratch
+    uint32_t* total = nullptr;
+    uint32_t root = 0;
+    int iters = 0;
+};
 
-cudaError_t build_bvh8(const float* d_tri, const int32_t* d_mat, int n, const float lo[3],
-                       const float hi[3], cudaStream_t s, Bvh8Device* out) {
-    if (n < 1 || n >= (1 << 24)) return cudaErrorInvalidValue;
-    DevBuf tmp;
+cudaError_t ploc_build(const float* d_tri, int n, const float lo[3], const float hi[3],
+                       cudaStream_t s, DevBuf& tmp, PlocTree* t) {
     cudaError_t e;
 #define BK(x)                      \
     do {                           \
@@ -627,9 +639,41 @@ cudaError_t build_bvh8(const float* d_tri, const int32_t* d_mat, int n, const fl
         m = (int)h[1];
         std::swap(C, C2);
     }
-    uint32_t root_id = 0;
-    BK(cudaMemcpyAsync(&root_id, C, 4, cudaMemcpyDeviceToHost, s));
+    BK(cudaMemcpyAsync(&t->root, C, 4, cudaMemcpyDeviceToHost, s));
     BK(cudaStreamSynchronize(s));
+    t->vals = vals;
+    t->blo = blo;
+    t->bhi = bhi;
+    t->cnt = cnt;
+    t->kids = kids;
+    t->sums = sums;
+    t->total = total;
+    t->iters = iters;
+    return cudaSuccess;
+#undef BK
+}
+
+}  // namespace
+
+cudaError_t build_bvh8(const float* d_tri, const int32_t* d_mat, int n, const float lo[3],
+                       const float hi[3], cudaStream_t s, Bvh8Device* out) {
+    if (n < 1 || n >= (1 << 24)) return cudaErrorInvalidValue;
+    DevBuf tmp;
+    PlocTree t;
+    cudaError_t e = ploc_build(d_tri, n, lo, hi, s, tmp, &t);
+    if (e != cudaSuccess) return e;
+    uint32_t* vals = t.vals;
+    float4 *blo = t.blo, *bhi = t.bhi;
+    uint32_t* cnt = t.cnt;
+    int2* kids = t.kids;
+    uint32_t *sums = t.sums, *total = t.total;
+    const uint32_t root_id = t.root;
+    const int iters = t.iters;
+#define BK(x)                      \
+    do {                           \
+        e = (x);                   \
+        if (e != cudaSuccess) return e; \
+    } while (0)
     // collapse, one level per round
     const size_t max_nodes = (size_t)n;  // every eight-wide node has >= 2 children
     uint4* nodes;
@@ -689,6 +733,83 @@ cudaError_t build_bvh8(const float* d_tri, const int32_t* d_mat, int n, const fl
     out->ploc_iterations = iters;
     return cudaSuccess;
 #undef BK
+}
+
+cudaError_t build_bvh2_ploc(const float* d_tri, const float* h_tri, const int32_t* h_mat, int n,
+                            const float lo[3], const float hi[3], int max_depth, cudaStream_t s,
+                            BvhHost* out, int* depth_out) {
+    if (n < 2 || n >= (1 << 24)) return cudaErrorInvalidValue;
+    DevBuf tmp;
+    PlocTree t;
+    cudaError_t e = ploc_build(d_tri, n, lo, hi, s, tmp, &t);
+    if (e != cudaSuccess) return e;
+    std::vector<int2> kids((size_t)n - 1);
+    std::vector<float4> blo(2 * (size_t)n), bhi(2 * (size_t)n);
+    std::vector<uint32_t> vals((size_t)n);
+    if ((e = cudaMemcpy(kids.data(), t.kids, sizeof(int2) * (n - 1), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(blo.data(), t.blo, sizeof(float4) * 2 * (size_t)n, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(bhi.data(), t.bhi, sizeof(float4) * 2 * (size_t)n, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(vals.data(), t.vals, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost)))
+        return e;
+    // depth-first preorder: inner nodes numbered as the BVH2 builder numbers them (self
+    // before its subtrees, left first), leaves in the order they are met
+    std::vector<int32_t> idx(2 * (size_t)n, -1);
+    std::vector<int32_t> leaf_order;
+    leaf_order.reserve(n);
+    std::vector<std::pair<uint32_t, int>> stack;
+    stack.emplace_back(t.root, 0);
+    int32_t inner = 0, deepest = 0;
+    while (!stack.empty()) {
+        const auto [id, d] = stack.back();
+        stack.pop_back();
+        if (id < (uint32_t)n) {
+            idx[id] = (int32_t)leaf_order.size();
+            leaf_order.push_back((int32_t)id);
+            continue;
+        }
+        idx[id] = inner++;
+        deepest = std::max(deepest, d);
+        const int2 k = kids[id - n];
+        stack.emplace_back((uint32_t)k.y, d + 1);
+        stack.emplace_back((uint32_t)k.x, d + 1);
+    }
+    if (depth_out) *depth_out = deepest;
+    if (deepest > max_depth) return cudaErrorNotSupported;
+    out->nodes.assign((size_t)inner, BvhNode{});
+    for (uint32_t id = (uint32_t)n; id < 2u * (uint32_t)n - 1u; ++id) {
+        if (idx[id] < 0) continue;
+        const int2 k = kids[id - n];
+        BvhNode& nd = out->nodes[(size_t)idx[id]];
+        const uint32_t c[2] = {(uint32_t)k.x, (uint32_t)k.y};
+        for (int j = 0; j < 2; ++j) {
+            const float4 a = blo[c[j]], b = bhi[c[j]];
+            float* xy = j == 0 ? nd.a : nd.b;
+            xy[0] = a.x; xy[1] = b.x; xy[2] = a.y; xy[3] = b.y;
+            nd.c[2 * j] = a.z;
+            nd.c[2 * j + 1] = b.z;
+            nd.d[j] = c[j] < (uint32_t)n ? ~idx[c[j]] : idx[c[j]];
+            nd.d[2 + j] = c[j] < (uint32_t)n ? 1 : 0;
+        }
+    }
+    out->n_ref = n;
+    out->tris.assign((size_t)n * 12, 0.0f);
+    for (int32_t sidx = 0; sidx < n; ++sidx) {
+        const int32_t i = (int32_t)vals[leaf_order[sidx]];
+        const float* v = h_tri + (size_t)i * 9;
+        float* o = out->tris.data() + (size_t)sidx * 12;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = v[k];
+            o[4 + k] = v[3 + k] - v[k];  // correctly rounded FP32 differences
+            o[8 + k] = v[6 + k] - v[k];
+        }
+        std::memcpy(&o[3], &i, 4);
+        std::memcpy(&o[7], &h_mat[i], 4);
+    }
+    for (int k = 0; k < 3; ++k) {
+        out->lo[k] = lo[k];
+        out->hi[k] = hi[k];
+    }
+    return cudaSuccess;
 }
 
 }  // namespace nrrs

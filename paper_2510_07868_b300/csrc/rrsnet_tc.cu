@@ -32,11 +32,15 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kTmemCols = 32;
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz: a wait this long is a fault
 
+// SPLIT: every operand as the BF16 pair (hi, lo), three MMAs per product; otherwise one
+// BF16 rounding per operand and one MMA (precision 17).
+template <bool SPLIT>
 struct __align__(128) TcSmem {
-    unsigned char w1[2][32 * 16 * 2];   // B of layer 1 (hi, lo): N = 32 rows, K = 16
-    unsigned char w2[2][32 * 32 * 2];   // B of layer 2 (hi, lo)
-    unsigned char w3[2][32 * 32 * 2];   // B of layer 3 (hi, lo)
-    unsigned char a[2][128 * 32 * 2];   // A of every layer (hi, lo): 128 rows, K = 32 layout
+    static constexpr int NB = SPLIT ? 2 : 1;
+    unsigned char w1[NB][32 * 16 * 2];   // B of layer 1 (hi, lo): N = 32 rows, K = 16
+    unsigned char w2[NB][32 * 32 * 2];   // B of layer 2 (hi, lo)
+    unsigned char w3[NB][32 * 32 * 2];   // B of layer 3 (hi, lo)
+    unsigned char a[NB][128 * 32 * 2];   // A of every layer (hi, lo): 128 rows, K = 32 layout
     float w4[32];
     unsigned long long bar;
     uint32_t tmem;
@@ -164,6 +168,15 @@ __device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* l
     *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<uint4*>(pl);
 }
 
+// Writes 8 consecutive values of row r (columns 8c .. 8c+7) into a K-major tile as BF16.
+__device__ __forceinline__ void store_bf16_8(unsigned char* hi, int r, int c, int K,
+                                             const float* v) {
+    __nv_bfloat162 ph[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ph[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    *reinterpret_cast<uint4*>(hi + kmajor_off(r, 8 * c, K)) = *reinterpret_cast<uint4*>(ph);
+}
+
 __device__ __forceinline__ void store_split1(unsigned char* hi, unsigned char* lo, uint32_t off,
                                              float v) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -177,11 +190,13 @@ __device__ __forceinline__ float softplus_mod_tc(float z) {
 
 // n_ptr: device row count (render) or null with n_host (stand-alone).  q_in: when set,
 // only rows with q_in < 0 are written (the render's NET slots).
+template <bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 8)  // 8 CTAs (8 tiles in flight) per SM
 k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
             const long long* n_ptr, long long n_host, float* q, int sentinel, DevStats* st,
             unsigned int* status) {
-    __shared__ TcSmem sm;
+    __shared__ TcSmem<SPLIT> sm;
+    constexpr int LO = SPLIT ? 1 : 0;  // index of the lo half (aliases hi without a split)
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long n = n_ptr ? *n_ptr : n_host;
     if ((long long)blockIdx.x * kTcThreads >= n) return;  // no tile: allocate nothing
@@ -196,12 +211,18 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // weights -> split BF16 B operands (W is [out][in] row-major = N rows of K)
+    auto store_w = [&](unsigned char* hi, unsigned char* lo, uint32_t off, float v) {
+        if (SPLIT)
+            store_split1(hi, lo, off, v);
+        else
+            *reinterpret_cast<__nv_bfloat16*>(hi + off) = __float2bfloat16_rn(v);
+    };
     for (int e = tid; e < 32 * 16; e += kTcThreads)
-        store_split1(sm.w1[0], sm.w1[1], kmajor_off(e / 16, e % 16, 16), params[e]);
+        store_w(sm.w1[0], sm.w1[LO], kmajor_off(e / 16, e % 16, 16), params[e]);
     for (int e = tid; e < 32 * 32; e += kTcThreads) {
         const uint32_t off = kmajor_off(e / 32, e % 32, 32);
-        store_split1(sm.w2[0], sm.w2[1], off, params[512 + e]);
-        store_split1(sm.w3[0], sm.w3[1], off, params[1536 + e]);
+        store_w(sm.w2[0], sm.w2[LO], off, params[512 + e]);
+        store_w(sm.w3[0], sm.w3[LO], off, params[1536 + e]);
     }
     if (tid < 32) sm.w4[tid] = params[2560 + tid];
     fence_async_smem();
@@ -237,8 +258,13 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
         }
         // the next tile's row is fetched while this one runs through the network
         if (tile + gridDim.x < tiles) load_row(tile + gridDim.x);
-        store_split8(sm.a[0], sm.a[1], tid, 0, 32, x);
-        store_split8(sm.a[0], sm.a[1], tid, 1, 32, x + 8);
+        if (SPLIT) {
+            store_split8(sm.a[0], sm.a[LO], tid, 0, 32, x);
+            store_split8(sm.a[0], sm.a[LO], tid, 1, 32, x + 8);
+        } else {
+            store_bf16_8(sm.a[0], tid, 0, 32, x);
+            store_bf16_8(sm.a[0], tid, 1, 32, x + 8);
+        }
         float h[32];
         for (int layer = 0; layer < 3 && !failed; ++layer) {
             fence_async_smem();
@@ -252,17 +278,20 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
                 const uint64_t b0 = smem_desc(smem_u32(wb), 128, layer == 0 ? 256 : 512);
                 const uint64_t b1 = smem_desc(smem_u32(wb) + wstep, 128, layer == 0 ? 256 : 512);
                 const uint64_t a0 = smem_desc(smem_u32(sm.a[0]), 128, 512);
-                const uint64_t a1 = smem_desc(smem_u32(sm.a[1]), 128, 512);
+                const uint64_t a1 = smem_desc(smem_u32(sm.a[LO]), 128, 512);
                 const int ksteps = layer == 0 ? 1 : 2;
                 for (int ks = 0; ks < ksteps; ++ks) {
                     const uint64_t o = ks * k16;
                     mma_bf16(tmem, a0 + o, b0 + o, ks > 0 ? 1u : 0u);
-                    mma_bf16(tmem, a1 + o, b0 + o, 1u);
-                    mma_bf16(tmem, a0 + o, b1 + o, 1u);
+                    if (SPLIT) {
+                        mma_bf16(tmem, a1 + o, b0 + o, 1u);
+                        mma_bf16(tmem, a0 + o, b1 + o, 1u);
+                    }
                 }
                 mma_commit(bar);
             }
-            const bool ok = mbar_wait(bar, phase);
+            // one thread waits for the MMAs; the barrier releases the others (no spinning)
+            const bool ok = tid == 0 ? mbar_wait(bar, phase) : true;
             phase ^= 1u;
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -281,13 +310,24 @@ k_rrsnet_tc(const float* __restrict__ params, const float4* __restrict__ feat,
                 // every MMA read of the A buffer is complete (the commit barrier fired and
                 // every lane has passed it): the next layer's operand overwrites it
 #pragma unroll
-                for (int c = 0; c < 4; ++c) store_split8(sm.a[0], sm.a[1], tid, c, 32, h + 8 * c);
+                for (int c = 0; c < 4; ++c) {
+                    if (SPLIT)
+                        store_split8(sm.a[0], sm.a[LO], tid, c, 32, h + 8 * c);
+                    else
+                        store_bf16_8(sm.a[0], tid, c, 32, h + 8 * c);
+                }
             }
         }
         if (failed) break;
         float z = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) z = fmaf(sm.w4[k], h[k], z);
+        for (int k = 0; k < 32; k += 4) {  // the output row read as 128-bit broadcasts
+            const float4 wv = *reinterpret_cast<const float4*>(&sm.w4[k]);
+            z = fmaf(wv.x, h[k], z);
+            z = fmaf(wv.y, h[k + 1], z);
+            z = fmaf(wv.z, h[k + 2], z);
+            z = fmaf(wv.w, h[k + 3], z);
+        }
         float qv = softplus_mod_tc(z);
         if (active) {
             ++evals;
@@ -494,7 +534,8 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
                     sm.staging = 1;
                 }
             }
-            const bool ok = mbar_wait(bar, phase);
+            // one thread waits for the MMAs; the barrier releases the others (no spinning)
+            const bool ok = tid == 0 ? mbar_wait(bar, phase) : true;
             phase ^= 1u;
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -514,7 +555,13 @@ k_rrsnet_fp8(const float* __restrict__ params, const float4* __restrict__ feat,
         if (failed) break;
         float z = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) z = fmaf(sm.w4[k], h[k], z);
+        for (int k = 0; k < 32; k += 4) {  // the output row read as 128-bit broadcasts
+            const float4 wv = *reinterpret_cast<const float4*>(&sm.w4[k]);
+            z = fmaf(wv.x, h[k], z);
+            z = fmaf(wv.y, h[k + 1], z);
+            z = fmaf(wv.z, h[k + 2], z);
+            z = fmaf(wv.w, h[k + 3], z);
+        }
         float qv = softplus_mod_tc(z);
         if (active) {
             ++evals;
@@ -558,9 +605,12 @@ void launch_rrsnet_tc(int precision, int grid, const float* params, const float4
     if (precision == 8)
         k_rrsnet_fp8<<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel, st,
                                                  status);
+    else if (precision == 17)
+        k_rrsnet_tc<false><<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel,
+                                                       st, status);
     else
-        k_rrsnet_tc<<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel, st,
-                                                status);
+        k_rrsnet_tc<true><<<grid, kTcThreads, 0, s>>>(params, feat, n_ptr, n_host, q, sentinel,
+                                                      st, status);
 }
 
 }  // namespace nrrs

@@ -46,7 +46,7 @@ EXPORTED = [
     "nrrs_rrsnet_forward", "nrrs_rrsnet_backward", "nrrs_tune_rrsnet",
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
-    "nrrs_set_bvh_precision", "nrrs_bvh8_info", "nrrs_bvh8_export",
+    "nrrs_set_bvh_precision", "nrrs_set_bvh_builder", "nrrs_bvh8_info", "nrrs_bvh8_export",
 ]
 
 
@@ -246,6 +246,7 @@ def _load():
         "nrrs_batch_info": ([P, P, P, P], I32),
         "nrrs_set_traversal": ([P, I32], I32),
         "nrrs_set_bvh_precision": ([P, I32], I32),
+        "nrrs_set_bvh_builder": ([P, I32, P], I32),
         "nrrs_bvh8_info": ([P, P], I32),
         "nrrs_bvh8_export": ([P, P, I64, P, I64], I32),
     }
@@ -357,6 +358,14 @@ def nrrs_set_traversal(scene, width):
 
 def nrrs_set_bvh_precision(scene, bits):
     _check(_lib.nrrs_set_bvh_precision(scene, bits))
+
+
+def nrrs_set_bvh_builder(scene, builder):
+    """Rebuilds the BVH2 with builder 0 (host binned SAH) or 1 (device PLOC); returns
+    the build's wall time in ms."""
+    ms = C.c_float()
+    _check(_lib.nrrs_set_bvh_builder(scene, builder, C.byref(ms)))
+    return ms.value
 
 
 def nrrs_destroy_scene(scene):
@@ -682,6 +691,9 @@ class Scene:
 
     def set_bvh_precision(self, bits):
         nrrs_set_bvh_precision(self.handle, bits)
+
+    def set_bvh_builder(self, builder):
+        return nrrs_set_bvh_builder(self.handle, builder)
 
     def set_rrsnet_inputs(self, mode):
         nrrs_set_rrsnet_inputs(self.handle, mode)

@@ -166,3 +166,61 @@ def test_bvh8_full_size_scenes_render_identically(nrrs):
         assert out[2][1]["segments"] > 0
         np.testing.assert_array_equal(out[8][0], out[2][0])
         assert out[8][1]["segments"] == out[2][1]["segments"]
+
+
+def _render_builders(nrrs, scene, W, H, spp, D, mode, trace=False, **opts):
+    out = {}
+    for builder in (0, 1):
+        sc = nrrs.Scene(scene)
+        sc.set_params(I.rrsnet_init_params(1))
+        if builder:
+            ms = sc.set_bvh_builder(1)
+            assert ms > 0.0
+        tr = None
+        kw = dict(opts)
+        if trace:
+            tr = torch.zeros((D, 2 * W * H * spp, 5), dtype=torch.int32, device="cuda")
+            kw["d_trace"] = tr.data_ptr()
+        img, st = sc.render(W, H, spp, D, mode, **kw)
+        torch.cuda.synchronize()
+        out[builder] = (img.cpu().numpy(), st, tr.cpu().numpy() if trace else None,
+                        nrrs.nrrs_scene_info(sc.handle)[0])
+        sc.close()
+    return out
+
+
+@pytest.mark.parametrize("mode_name,nee", [("NET", 0), ("HEUR_NORM", 1)])
+def test_device_built_bvh2_renders_equal_the_host_tree(nrrs, mode_name, nee):
+    """The PLOC BVH2 (nrrs_set_bvh_builder(1)) and the host SAH tree give identical
+    closest hits, so identical images and traced decisions, through the FP16 and the FP32
+    boxes alike."""
+    mode = getattr(nrrs, "RRS_" + mode_name)
+    for scene, W, H, spp, D in ((I.box_scene(1), 48, 40, 4, 8),
+                                (I.occluded_room(1), 64, 64, 4, 12)):
+        out = _render_builders(nrrs, scene, W, H, spp, D, mode, trace=True, nee=nee, graph=1)
+        np.testing.assert_array_equal(out[1][0], out[0][0])
+        np.testing.assert_array_equal(out[1][2], out[0][2])
+        # one triangle per PLOC leaf: n - 1 inner nodes
+        assert out[1][3] == scene.n_tri - 1
+
+
+def test_device_built_bvh2_full_size_and_switching(nrrs):
+    scene = I.three_rooms(1)
+    out = _render_builders(nrrs, scene, 960, 540, 4, 32, nrrs.RRS_HEUR_NORM, graph=1)
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    assert out[1][1]["segments"] == out[0][1]["segments"] > 0
+    # switching back to the host tree, after a captured graph, reproduces the first image
+    sc = nrrs.Scene(scene)
+    sc.set_params(I.rrsnet_init_params(1))
+    a, _ = sc.render(320, 180, 2, 16, nrrs.RRS_NET, graph=1)
+    sc.set_bvh_builder(1)
+    sc.set_bvh_precision(32)
+    b, _ = sc.render(320, 180, 2, 16, nrrs.RRS_NET, graph=1)
+    sc.set_bvh_builder(0)
+    c, _ = sc.render(320, 180, 2, 16, nrrs.RRS_NET, graph=1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    np.testing.assert_array_equal(a.cpu().numpy(), c.cpu().numpy())
+    with pytest.raises(nrrs.NrrsError):
+        sc.set_bvh_builder(2)
+    sc.close()
