@@ -30,6 +30,9 @@ struct Hit {
 struct Ray {
     V3 o, d, inv, oi;
     int node, sp;
+    // per axis the byte selector that orders a binary16 (lo, hi) word as (near, far) for
+    // this direction: identity when the component is positive, a half swap when negative
+    uint32_t sel_x, sel_y, sel_z;
 };
 
 // A direction component that is exactly zero would make the slab products 0 * inf and
@@ -47,6 +50,9 @@ __device__ __forceinline__ void ray_init(Ray& r, V3 o, V3 d, int root, Hit& h,
     r.d = d;
     r.inv = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    r.sel_x = r.inv.x < 0.0f ? 0x1032u : 0x3210u;
+    r.sel_y = r.inv.y < 0.0f ? 0x1032u : 0x3210u;
+    r.sel_z = r.inv.z < 0.0f ? 0x1032u : 0x3210u;
     r.node = root;
     r.sp = 0;
     h = Hit{t_max, -1, t_max == FLT_MAX ? 0xFFFFFFFFu : 0u};
@@ -267,69 +273,142 @@ __device__ __forceinline__ float2 half_pair(uint32_t w) {
     return __half22float2(*reinterpret_cast<const __half2*>(&w));
 }
 
-// Inner-node step of the postponed-leaf traversal: tests both child boxes; leaf children
-// hit become the lane's pending leaves (tested later, together with the other lanes'),
-// inner children are entered near-first.  node < 0 afterwards: nothing left to visit.
-// Reads the 32-byte nodes with FP16 boxes rounded outward when the scene has them (one
-// 32-byte sector per visit instead of two; the same closest hits), else the FP32 nodes.
-__device__ __forceinline__ void visit_inner(const SceneView& sc, Ray& r, const Hit& h, int* stk,
-                                            int stride, int* leaf0, int* cnt0, int* leaf1,
-                                            int* cnt1) {
+// Three-operand minimum and maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Slab test of a binary16 box whose axis words hold (lo, hi): each word is first put in
+// (near, far) order for the ray's direction, so no per-axis min/max is needed.  With
+// lo <= hi and a fixed sign of 1/d the rounded plane distances keep their order, so the
+// entry and exit distances equal slab()'s bit for bit.
+__device__ __forceinline__ bool slab_half(const Ray& r, float hit_t, uint32_t wx, uint32_t wy,
+                                          uint32_t wz, float* tn) {
+    const float2 x = half_pair(__byte_perm(wx, 0u, r.sel_x));
+    const float2 y = half_pair(__byte_perm(wy, 0u, r.sel_y));
+    const float2 z = half_pair(__byte_perm(wz, 0u, r.sel_z));
+    // (near, far) distances per axis, two correctly rounded FMAs per instruction
+    const float2 tx = __ffma2_rn(x, make_float2(r.inv.x, r.inv.x), make_float2(-r.oi.x, -r.oi.x));
+    const float2 ty = __ffma2_rn(y, make_float2(r.inv.y, r.inv.y), make_float2(-r.oi.y, -r.oi.y));
+    const float2 tz = __ffma2_rn(z, make_float2(r.inv.z, r.inv.z), make_float2(-r.oi.z, -r.oi.z));
+    const float n = max3f(tx.x, ty.x, fmaxf(tz.x, 0.0f));
+    const float f = min3f(tx.y, ty.y, fminf(tz.y, hit_t));
+    *tn = n;
+    return n <= f;
+}
+
+// One inner-node step of the BVH2 traversal for every lane of the warp, free of divergent
+// branches: a lane that does not go (`go` false) reads the root's node and keeps its
+// state, so all lanes issue the same instructions.  Both child boxes are tested; leaf
+// children entered are not intersected here but held as their raw child codes in the
+// first free of three slots (leaf tests are postponed, see k_trace); inner children
+// entered are descended near-first with the far one pushed; with neither, the next
+// node comes off the stack (node -1: nothing left).  HALF: the 32-byte binary16 nodes
+// (boxes rounded outward: one memory sector per visit, the same closest hits; a leaf's
+// code packs its first reference and count), else the 64-byte FP32 nodes (a leaf's code
+// is ~first, its count a field of its own, held in n0..n2 beside the slots).
+template <bool HALF>
+__device__ __forceinline__ void step_bvh2(const SceneView& sc, Ray& r, const Hit& h, int* stk,
+                                          int stride, bool go, int& code0, int& code1,
+                                          int& code2, int& n0, int& n1, int& n2) {
+    const int node = go ? r.node : 0;
     float t0n, t1n;
-    bool h0, h1;
-    int c0, c1;
-    if (sc.nodes_h) {
-        const uint4 p = __ldg(&sc.nodes_h[2 * r.node + 0]);
-        const uint4 q = __ldg(&sc.nodes_h[2 * r.node + 1]);
-        const float2 x0 = half_pair(p.x), y0 = half_pair(p.y), z0 = half_pair(p.z);
-        const float2 x1 = half_pair(p.w), y1 = half_pair(q.x), z1 = half_pair(q.y);
-        h0 = slab(r, h.t, x0.x, x0.y, y0.x, y0.y, z0.x, z0.y, &t0n);
-        h1 = slab(r, h.t, x1.x, x1.y, y1.x, y1.y, z1.x, z1.y, &t1n);
+    bool b0, b1;
+    int c0, c1, k0 = 0, k1 = 0;
+    if (HALF) {
+        const uint4 p = __ldg(&sc.nodes_h[2 * node + 0]);
+        const uint4 q = __ldg(&sc.nodes_h[2 * node + 1]);
+        b0 = slab_half(r, h.t, p.x, p.y, p.z, &t0n);
+        b1 = slab_half(r, h.t, p.w, q.x, q.y, &t1n);
         c0 = (int)q.z;
         c1 = (int)q.w;
-        if (h0 && c0 < 0) {
-            const uint32_t v = ~(uint32_t)c0;
-            *leaf0 = (int)(v & kLeafFirstMask);
-            *cnt0 = (int)(v >> kLeafFirstBits);
-            h0 = false;
-        }
-        if (h1 && c1 < 0) {
-            const uint32_t v = ~(uint32_t)c1;
-            *leaf1 = (int)(v & kLeafFirstMask);
-            *cnt1 = (int)(v >> kLeafFirstBits);
-            h1 = false;
-        }
     } else {
-        const float4 a = __ldg(&sc.nodes[4 * r.node + 0]);
-        const float4 b = __ldg(&sc.nodes[4 * r.node + 1]);
-        const float4 c = __ldg(&sc.nodes[4 * r.node + 2]);
-        const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * r.node + 3]));
-        h0 = slab(r, h.t, a.x, a.y, a.z, a.w, c.x, c.y, &t0n);
-        h1 = slab(r, h.t, b.x, b.y, b.z, b.w, c.z, c.w, &t1n);
+        const float4 a = __ldg(&sc.nodes[4 * node + 0]);
+        const float4 b = __ldg(&sc.nodes[4 * node + 1]);
+        const float4 c = __ldg(&sc.nodes[4 * node + 2]);
+        const int4 e = __ldg(reinterpret_cast<const int4*>(&sc.nodes[4 * node + 3]));
+        b0 = slab(r, h.t, a.x, a.y, a.z, a.w, c.x, c.y, &t0n);
+        b1 = slab(r, h.t, b.x, b.y, b.z, b.w, c.z, c.w, &t1n);
         c0 = e.x;
         c1 = e.y;
-        if (h0 && c0 < 0) { *leaf0 = ~c0; *cnt0 = e.z; h0 = false; }
-        if (h1 && c1 < 0) { *leaf1 = ~c1; *cnt1 = e.w; h1 = false; }
+        k0 = e.z;
+        k1 = e.w;
     }
-    if (h0 && h1) {
-        if (t1n < t0n) { const int tmp = c0; c0 = c1; c1 = tmp; }
-        if (r.sp < kStack) stk[(r.sp++) * stride] = c1;
-        r.node = c0;
-    } else if (h0) {
-        r.node = c0;
-    } else if (h1) {
-        r.node = c1;
-    } else {
-        r.node = r.sp == 0 ? -1 : stk[(--r.sp) * stride];
+    b0 = b0 && go;
+    b1 = b1 && go;
+    // leaves entered fill the free slots in order; a lane holding one leaf goes on
+    // descending (it stops at two), so a node can add at most two more
+    const int na = b0 && c0 < 0 ? c0 : 0, nb = b1 && c1 < 0 ? c1 : 0;
+    const bool empty = code0 == 0;
+    const int first = na != 0 ? na : nb, second = na != 0 ? nb : 0;
+    if (!HALF) {
+        const int kf = na != 0 ? k0 : k1, ks = na != 0 ? k1 : 0;
+        n2 = go && !empty ? ks : n2;
+        n1 = go ? (empty ? ks : kf) : n1;
+        n0 = go && empty ? kf : n0;
     }
+    code2 = go && !empty ? second : code2;
+    code1 = go ? (empty ? second : first) : code1;
+    code0 = go && empty ? first : code0;
+    const bool i0 = b0 && c0 >= 0, i1 = b1 && c1 >= 0;
+    const bool first1 = i1 && (!i0 || t1n < t0n);
+    const int near_c = first1 ? c1 : c0;
+    const int far_c = first1 ? c0 : c1;
+    const bool push = i0 && i1 && r.sp < kStack;
+    const bool none = go && !i0 && !i1;
+    const bool pop = none && r.sp > 0;
+    int* slot = stk + (pop ? r.sp - 1 : r.sp) * stride;
+    if (push) *slot = far_c;
+    const int popped = pop ? *slot : -1;
+    r.sp += push ? 1 : pop ? -1 : 0;
+    r.node = none ? popped : (go ? near_c : r.node);
+}
+
+// Intersects the triangles of a held leaf (raw child code, 0 = an empty slot; n its
+// count in the FP32 nodes).
+template <bool HALF>
+__device__ __forceinline__ void test_leaf(const SceneView& sc, const Ray& r, Hit& h, int code,
+                                          int n) {
+    if (code >= 0) return;
+    const uint32_t v = ~(uint32_t)code;
+    const int first = HALF ? (int)(v & kLeafFirstMask) : (int)v;
+    const int count = HALF ? (int)(v >> kLeafFirstBits) : n;
+    for (int k = 0; k < count; ++k) intersect_tri(sc, r, h, first + k);
+}
+
+// One round of the BVH2 traversal for the warp: up to kSteps inner-node steps, then the
+// tests of the leaves held.  The warp keeps stepping while some lane that still
+// traverses holds no leaf yet; lanes that hold one step along speculatively (Aila and
+// Laine's speculative while-while), which keeps lanes busy that would otherwise wait.
+template <bool HALF>
+__device__ __forceinline__ void round_bvh2(const SceneView& sc, Ray& r, Hit& h, int* stk,
+                                           int stride, bool active) {
+    bool go = active && r.node >= 0;
+    int code0 = 0, code1 = 0, code2 = 0, n0 = 0, n1 = 0, n2 = 0;
+#pragma unroll
+    for (int step = 0; step < kSteps; ++step) {
+        step_bvh2<HALF>(sc, r, h, stk, stride, go, code0, code1, code2, n0, n1, n2);
+        go = go && r.node >= 0 && (code1 | code2) == 0;
+        if (!__any_sync(0xffffffffu, go && code0 == 0)) break;
+    }
+    test_leaf<HALF>(sc, r, h, code0, n0);
+    test_leaf<HALF>(sc, r, h, code1, n1);
+    test_leaf<HALF>(sc, r, h, code2, n2);
 }
 
 // Extension of depth `depth`, part 1: the closest hit of every live ray.  Persistent
 // warps fetch rays dynamically: a lane whose query has ended stores its hit and takes
 // the next unclaimed slot, so lanes stay busy despite divergent traversal lengths.  On
-// the BVH2 the leaf tests are postponed (Aila & Laine's "while-while"): lanes descend
-// through inner nodes until every lane of the warp holds a leaf or has finished, then
-// test their leaves together.  Each slot's hit depends only on that slot's ray (the
+// the BVH2 the leaf tests are postponed (Aila and Laine's while-while traversal): lanes
+// descend through inner nodes until every lane of the warp holds a leaf or has
+// finished, then test their leaves together (round_bvh2).  Each slot's hit depends only on that slot's ray (the
 // closest hit with the lower-index tie rule does not depend on the visiting order), so
 // the result is deterministic.
 // ANY: the shadow rays of next-event estimation, one per slot (t_max <= 0: none); the
@@ -397,17 +476,12 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
                 done = visit_node4(sc, ray, h, stk, kExtendThreads) || (ANY && h.slot >= 0);
             if (!done) continue;
         } else {
-            // every lane of the warp runs the step loop (the vote needs all of them)
-            int leaf0 = -1, cnt0 = 0, leaf1 = -1, cnt1 = 0;
-            for (int step = 0; step < kSteps; ++step) {
-                const bool go = idx >= 0 && ray.node >= 0 && leaf0 < 0 && leaf1 < 0;
-                if (go) visit_inner(sc, ray, h, stk, kExtendThreads, &leaf0, &cnt0, &leaf1, &cnt1);
-                const bool more = idx >= 0 && ray.node >= 0 && leaf0 < 0 && leaf1 < 0;
-                if (!__any_sync(0xffffffffu, more)) break;
-            }
+            // every lane of the warp runs the round (its votes need all of them)
+            if (sc.nodes_h)
+                round_bvh2<true>(sc, ray, h, stk, kExtendThreads, idx >= 0);
+            else
+                round_bvh2<false>(sc, ray, h, stk, kExtendThreads, idx >= 0);
             if (idx < 0) continue;
-            for (int k = 0; k < cnt0 && leaf0 >= 0; ++k) intersect_tri(sc, ray, h, leaf0 + k);
-            for (int k = 0; k < cnt1 && leaf1 >= 0; ++k) intersect_tri(sc, ray, h, leaf1 + k);
             if (ANY && h.slot >= 0) ray.node = -1;  // occluded: the query is over
             if (ray.node >= 0) continue;
         }
