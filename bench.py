@@ -244,8 +244,9 @@ def source_sha(kernel_tag):
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def crop_pixels(side, W=HL_W, H=HL_H):
+def crop_pixels(side, W=None, H=None):
     """Pixel ids of a side x side window at the image centre."""
+    W, H = W or HL_W, H or HL_H
     x0, y0 = (W - side) // 2, (H - side) // 2
     ys, xs = np.meshgrid(np.arange(y0, y0 + side), np.arange(x0, x0 + side), indexing="ij")
     return (ys * W + xs).ravel().astype(np.int32)
@@ -270,8 +271,8 @@ def oracle_headline_sample(scene, params, gate, pixel_ref, forced_F, seconds_tar
             break
         side = int(min(128, side * min(2.0, np.sqrt(seconds_target / max(dt, 1e-3)))))
     cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
-    desc = (f"three_rooms centred {side}x{side} px crop of 1920x1080 at 1 spp (the GPU step "
-            f"renders 16 spp over 2,073,600 px), depth 32, NET_MIX; {st['segments']} segments "
+    desc = (f"three_rooms centred {side}x{side} px crop of {HL_W}x{HL_H} at 1 spp (the GPU step "
+            f"renders 16 spp over {HL_W * HL_H:,} px), depth 32, NET_MIX; {st['segments']} segments "
             f"in {dt:.2f} s")
     return st["segments"] / dt, cores, desc, dt, side
 
@@ -317,7 +318,7 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     value = segs / dt
     cores = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
-    sample = (f"three_rooms centred {side}x{side} px crop of 1920x1080 per step at 1 spp, depth "
+    sample = (f"three_rooms centred {side}x{side} px crop of {HL_W}x{HL_H} per step at 1 spp, depth "
               f"32, NET_MIX with a fixed gate (FIXED 1-2, RRSNet 3-8, heuristic beyond) and "
               f"the untrained RRSNet (the oracle cannot train; its cost per segment does not "
               f"depend on the weights' values)")
@@ -688,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     last_F = np.array(st["F"][:HL_DEPTH], dtype=np.float32)
+    last_live = [int(v) for v in st["live"][:HL_DEPTH]]
 
     # end to end through the public API: weights from pinned host memory in, frame out
     trained = nrrs.nrrs_get_params(sc.handle, nrrs.NET_RRSNET)
@@ -714,7 +716,7 @@ def run_ours(args, rank, world, local_rank):
         ms, e2e_s, segs, e2e_segs = combine_ranks(dist, dev, ms, e2e_s, segs, e2e_segs)
     hl_stats = {"live_total": live_total, "net_evals": net_evals, "stage_ms": stage_ms,
                 "stage_n": stage_n, "warm_ms": warm_ms, "warm_n": warm_n, "warm": warm,
-                "dom": dom, "status": status}
+                "dom": dom, "status": status, "last_live": last_live}
     sc.close()
 
     # ---- second section: the online training step on the occluded room
@@ -739,6 +741,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = per_unit * units_per_launch if per_unit is not None else None
     inst_per_ray = profile_record(names[dom], "warp_inst_per_ray")
     issue_active = profile_record(names[dom], "issue_active")
+    alu_active = profile_record(names[dom], "alu_pipe_active")
     roofline = {
         "kernel": "k_trace" if names[dom] == "extend" else names[dom], "bound": "hbm",
         "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -747,18 +750,20 @@ def run_ours(args, rank, world, local_rank):
         else "fallback 6.4 TB/s", "avg_launch_ms": per_launch_ms,
         "launches": int(stage_n[dom]),
         "bytes_per_unit": alg_bytes_per_unit.get(names[dom]),
-        "issue": {"warp_inst_per_ray": inst_per_ray, "issue_active_frac": issue_active,
-                  "source": "ncu capture in profiles/ (null when the kernel changed since)",
+        "issue": {"warp_inst_per_ray_depth1": inst_per_ray,
+                  "issue_active_frac": issue_active, "alu_pipe_active_frac": alu_active,
+                  "source": "ncu capture in profiles/ of the same kernel on a smaller image of "
+                            "the same scene (depths 1 and 2, time-weighted; null when the "
+                            "kernel changed since)",
                   "issue_peak_warp_inst_per_s": 148 * 4 * 2.032e9,
-                  "achieved_warp_inst_per_s": (inst_per_ray * units_per_launch / (per_launch_ms / 1e3))
-                  if inst_per_ray else None},
+                  "achieved_warp_inst_per_s": issue_active * 148 * 4 * 2.032e9
+                  if issue_active else None},
         "note": ("the traversal is bound by instruction issue, not HBM: the BVH and the "
                  "triangles stay in L2; 48 B/ray algorithmic (32 B ray in, 16 B hit out)"
                  if names[dom] == "extend" else f"{names[dom]} stage against HBM"),
     }
-    if inst_per_ray:
-        roofline["issue"]["frac_of_issue_peak"] = (roofline["issue"]["achieved_warp_inst_per_s"]
-                                                   / roofline["issue"]["issue_peak_warp_inst_per_s"])
+    if issue_active:
+        roofline["issue"]["frac_of_issue_peak"] = issue_active
     stage_bytes = {
         "extend": BYTES_PER_RAY_EXTEND * warm["live"],
         "shade": BYTES_PER_RAY_SHADE * warm["live"] + 64 * warm["evals"],
@@ -831,6 +836,7 @@ def run_ours(args, rank, world, local_rank):
                                             "blocks_per_sm": r["blocks_per_sm"]}
                                    for p, r in tuner.items()}},
         "frame_status_bits": int(hl_stats["status"]),
+        "queue_per_depth_last_frame": hl_stats["last_live"],
         "e2e": {"value": e2e_segs / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(trained.nbytes),
                 "d2h_bytes_per_step": int(HL_W * HL_H * 3 * 4)},
@@ -905,7 +911,16 @@ def main():
     ap.add_argument("--tuned", action="store_true",
                     help="with --rrsnet-only: run the launch-shape tuner first, so the "
                          "queries take the tuned shape of their bucket")
+    ap.add_argument("--hl-image", default="",
+                    help="WxH: render the headline scene at this image size instead of "
+                         "1920x1080 (a smaller workload for kernel profiles; the JSON line "
+                         "names the size)")
     args = ap.parse_args()
+    if args.hl_image:
+        global HL_W, HL_H, HL_WORKLOAD
+        w, h = (int(v) for v in args.hl_image.lower().split("x"))
+        HL_WORKLOAD = HL_WORKLOAD.replace(f"{HL_W}x{HL_H}", f"{w}x{h}")
+        HL_W, HL_H = w, h
     if args.rrsnet_only:
         run_rrsnet_only(args)
         return
