@@ -42,8 +42,10 @@
  *     in: q_used = fp32(F) * fp32(q_orig) rounded to FP32, r = q_used - floor(q_used)
  *     (exact), X = floor(q_used) + [U < r] with U = (w >> 8) * 2^-24.
  *   - Everything else is FP64.
- *   - Parity of the GGX lobe against the paper is unpinned (the paper uses no GGX
- *     formula of its own); it is pinned only by the closed-form checks in tests/.
+ *   - The paper prints no GGX formula of its own; the lobe is pinned by identities of
+ *     the microfacet model (normalised D, Smith's masking identity, the sampler's
+ *     expected weight against quadrature, the closed form at normal incidence) and its
+ *     Fresnel term by the exact dielectric Fresnel equations within Schlick's error.
  */
 #include <math.h>
 #include <stdint.h>

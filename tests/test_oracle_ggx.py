@@ -11,10 +11,13 @@ correct implementation satisfies, each evaluated by quadrature written here:
   the integral of f cos over the hemisphere (so the sampler draws from the pdf it
   divides by);
 * at normal incidence f cos and pdf take closed forms (D(n) = 1 / (pi a^2), G1 = 1,
-  Fresnel = F0).
+  Fresnel = F0);
+* away from normal incidence the Fresnel term stays within Schlick's published error of
+  the exact Fresnel equations of the dielectric with the same normal reflectance.
 
 A dropped 1/pi in D, a instead of a^2, a wrong Smith term, a missing factor 4 in the
-half-vector Jacobian or a wrong Fresnel base each fail one of them.  The heuristic factor
+half-vector Jacobian, a wrong Fresnel base or a wrong Schlick exponent each fail one of
+them.  The heuristic factor
 of Sec. 4 ("Compromise": the reference is the accumulated estimate) is pinned by its
 closed form at depth 1, where the throughput is 1; the temporal EMA and the spatial
 filter of Sec. 4 "Tackle Low Spp" by closed forms and by library convolutions.
@@ -123,6 +126,44 @@ def test_ggx_normal_incidence_closed_form(a):
     np.testing.assert_allclose(fc, spec + (1.0 - F032) * alb32 / math.pi, rtol=1e-12)
     assert math.isclose(pdf, 0.5 / (4.0 * math.pi * a32 * a32) + 0.5 / math.pi, rel_tol=1e-12)
     assert math.isclose(oracle.ggx_D(1.0, a), 1.0 / (math.pi * a * a), rel_tol=1e-12)
+
+
+def _fresnel_dielectric(cos_i, eta):
+    """Unpolarised Fresnel reflectance of a smooth dielectric interface (the exact
+    equations for the s and p polarisations, averaged)."""
+    sin_t = math.sqrt(max(0.0, 1.0 - cos_i * cos_i)) / eta
+    cos_t = math.sqrt(1.0 - sin_t * sin_t)
+    rs = (cos_i - eta * cos_t) / (cos_i + eta * cos_t)
+    rp = (cos_t - eta * cos_i) / (cos_t + eta * cos_i)
+    return 0.5 * (rs * rs + rp * rp)
+
+
+@pytest.mark.parametrize("a", ROUGH)
+def test_ggx_fresnel_term_follows_the_dielectric_away_from_normal_incidence(a):
+    """The lobe's Fresnel term, read back at the mirror direction, against the exact
+    Fresnel equations of the dielectric whose normal reflectance is F0 (eta = 1.5 for
+    F0 = 0.04).  Along the mirror direction h = n, so with albedo 0 the value is
+    D(n) G1(o)^2 F(cos t) / (4 cos^2 t) and F follows from the separately pinned D and G1.
+    Schlick's approximation stays within 0.036 of the exact reflectance up to 85 degrees;
+    an exponent of 4 or 6 in place of 5 misses by 0.10 or 0.055."""
+    n = np.array([0.0, 0.0, 1.0])
+    F0 = float(np.float32(0.04))
+    eta = (1.0 + math.sqrt(F0)) / (1.0 - math.sqrt(F0))
+    a32 = float(np.float32(a))
+    worst = 0.0
+    for deg in np.linspace(0.0, 85.0, 35):
+        t = math.radians(deg)
+        wo = np.array([math.sin(t), 0.0, math.cos(t)])
+        wi = np.array([-math.sin(t), 0.0, math.cos(t)])
+        ok, fc, _ = oracle.eval_ggx(n, wo, wi, np.zeros(3), a, 0.04)
+        assert ok == 1
+        c = math.cos(t)
+        F = fc[0] * 4.0 * c / (oracle.ggx_D(1.0, a32) * oracle.ggx_G1(c, a32) ** 2)
+        assert abs(fc[0] - fc[1]) <= 1e-15 * abs(fc[0]) and abs(fc[0] - fc[2]) <= 1e-15 * abs(fc[0])
+        worst = max(worst, abs(F - _fresnel_dielectric(c, eta)))
+        if deg == 0.0:
+            assert math.isclose(F, F0, rel_tol=1e-12)
+    assert worst <= 0.037, worst
 
 
 # ----------------------------------------------------------------------------- HEUR
