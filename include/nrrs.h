@@ -598,8 +598,9 @@ NRRS_API nrrs_status nrrs_grid_backward(nrrs_scene* scene, const float* d_feat, 
 /* Autotuner of the RRSNet launch shape (no counterpart in the paper; it serves Sec. 4's
  * network in a queue whose size changes per bounce).  For every queue-size bucket b
  * (floor(log2 n) = b + 8, clamped to 0 .. NRRS_TUNE_BUCKETS - 1) it times each candidate
- * shape of the `precision` kernel (32: rows per thread 1 or 2 x blocks per SM; 16, 17, 8:
- * tensor-core CTAs per SM) on 1.5 x 2^(b + 8) synthetic rows (at most 12,582,912) with
+ * shape of the `precision` kernel (32: rows per thread 1 or 2 x blocks per SM; 16, 17:
+ * one or two 128-row tiles in flight per CTA x CTAs per SM; 8: tensor-core CTAs per SM)
+ * on 1.5 x 2^(b + 8) synthetic rows (at most 12,582,912) with
  * the scene's weights, and keeps the fastest for the scene.  Later renders pick the shape
  * of each depth from the bucket of that depth's queue size in the last frame rendered
  * with stats (W*H*spp before any), nrrs_query_factors from its n.  Every shape gives
@@ -611,7 +612,8 @@ typedef struct nrrs_tune_report {
     int32_t precision;
     int32_t n_buckets;                        /* NRRS_TUNE_BUCKETS                   */
     int64_t rows[NRRS_TUNE_BUCKETS];          /* rows timed per bucket               */
-    int32_t variant[NRRS_TUNE_BUCKETS];       /* FP32: rows per thread; else 0       */
+    int32_t variant[NRRS_TUNE_BUCKETS];       /* FP32: rows per thread; 16, 17: tiles
+                                                 in flight per CTA - 1; 8: 0           */
     int32_t blocks_per_sm[NRRS_TUNE_BUCKETS]; /* grid = SMs x blocks_per_sm          */
     float ms_best[NRRS_TUNE_BUCKETS];         /* mean launch time, chosen shape      */
     float ms_default[NRRS_TUNE_BUCKETS];      /* mean launch time, untuned shape     */
@@ -620,8 +622,10 @@ NRRS_API nrrs_status nrrs_tune_rrsnet(nrrs_scene* scene, int32_t precision, void
                                       nrrs_tune_report* report);
 
 /* Sets the RRSNet launch shape of one queue-size bucket (or of all, bucket = -1) by hand,
- * as nrrs_tune_rrsnet would: variant 1 or 2 rows per thread at precision 32, 0 for the
- * tensor-core precisions; 1 <= blocks_per_sm <= 32.  Results do not depend on it.
+ * as nrrs_tune_rrsnet would: variant 1 or 2 rows per thread at precision 32, 0 (one tile
+ * in flight per CTA) or 1 (two) at precisions 16 and 17, 0 at precision 8;
+ * 1 <= blocks_per_sm <= 32 (the two-tile kernel runs at most as many CTAs per SM as stay
+ * resident).  Results do not depend on it.
  * Errors: INVALID_ARG (NULL scene, unknown precision, bucket or shape out of range). */
 NRRS_API nrrs_status nrrs_set_rrsnet_shape(nrrs_scene* scene, int32_t precision, int32_t bucket,
                                            int32_t variant, int32_t blocks_per_sm);

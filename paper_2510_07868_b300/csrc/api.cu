@@ -1915,7 +1915,9 @@ nrrs_status nrrs_set_rrsnet_shape(nrrs_scene* scene, int32_t precision, int32_t 
     if (precision != 32 && precision != 16 && precision != 8 && precision != 17)
         return fail(NRRS_ERR_INVALID_ARG, "precision must be 32, 16, 17 or 8");
     if (bucket < -1 || bucket >= kTuneBuckets) return fail(NRRS_ERR_INVALID_ARG, "bad bucket");
-    const bool ok_variant = precision == 32 ? (variant == 1 || variant == 2) : variant == 0;
+    const bool ok_variant = precision == 32   ? (variant == 1 || variant == 2)
+                            : precision == 8 ? variant == 0
+                                             : (variant == 0 || variant == 1);
     if (!ok_variant || blocks_per_sm < 1 || blocks_per_sm > 32)
         return fail(NRRS_ERR_INVALID_ARG, "bad launch shape");
     const int p = precision_index(precision);

@@ -42,13 +42,22 @@ RrsnetChoice default_choice(int precision) {
 
 std::vector<RrsnetChoice> tune_candidates(int precision) {
     if (precision == 32) return {{1, 2}, {1, 1}, {1, 4}, {2, 1}, {2, 2}};
-    return {{0, 8}, {0, 1}, {0, 2}, {0, 4}, {0, 6}};
+    if (precision == 8) return {{0, 8}, {0, 1}, {0, 2}, {0, 4}, {0, 6}};
+    // the one-tile kernel (default first), then the two-tile kernel
+    std::vector<RrsnetChoice> c{default_choice(precision), {0, 2}, {0, 4}, {0, 6}};
+    const int mx = rrsnet_tc2_max_blocks(precision);
+    for (int b : {1, 2, 3, 4, 6, 8})
+        if (b <= mx) c.push_back({1, b});
+    return c;
 }
 
 void launch_rrsnet(int precision, RrsnetChoice c, int n_sm, const float* params,
                    const float4* feat, const long long* n_ptr, long long n_host, float* q,
                    int sentinel, DevStats* st, unsigned int* status, cudaStream_t s) {
-    long long grid = (long long)n_sm * std::max(1, c.blocks_per_sm);
+    int bps = std::max(1, c.blocks_per_sm);
+    // a persistent two-tile grid no larger than what stays resident
+    if (precision != 32 && c.variant == 1) bps = std::min(bps, rrsnet_tc2_max_blocks(precision));
+    long long grid = (long long)n_sm * bps;
     if (!n_ptr) {  // the row count is known here: no more blocks than there is work
         if (n_host <= 0) return;
         const long long need = precision == 32
@@ -60,7 +69,7 @@ void launch_rrsnet(int precision, RrsnetChoice c, int n_sm, const float* params,
         launch_rrsnet_simt(c.variant == 2 ? 2 : 1, (int)grid, params, feat, n_ptr, n_host, q,
                            sentinel, st, s);
     else
-        launch_rrsnet_tc(precision, (int)grid, params, feat, n_ptr, n_host, q, sentinel, st,
+        launch_rrsnet_tc(precision, c.variant, (int)grid, params, feat, n_ptr, n_host, q, sentinel, st,
                          status, s);
 }
 

@@ -217,15 +217,18 @@ void launch_aid_rrsnet(const float* params, const float2* rgrid, const SceneView
 // ADRRS (NN) factors of the vertices the shade kernel marked (rrsnet_simt.cu).
 void launch_adrrs(const float* stat, const SceneView& sc, const WorkView& w, QueueView cur,
                   const RenderParams& rp, int depth, int grid, cudaStream_t s);
-// rrsnet_tc.cu: tensor cores; precision 16 = split BF16 operands, 8 = E4M3 operands with
-// per-tensor scales; FP32 accumulation.
-void launch_rrsnet_tc(int precision, int grid, const float* params, const float4* feat,
-                      const long long* n_ptr, long long n_host, float* q, int sentinel,
-                      DevStats* st, unsigned int* status, cudaStream_t s);
+// rrsnet_tc.cu: tensor cores; precision 16 = split BF16 operands, 17 = BF16 operands, 8 =
+// E4M3 operands with per-tensor scales; FP32 accumulation.  Variant 0: one tile in flight
+// per CTA; variant 1 (precisions 16 and 17): two tiles per CTA, the same factors.
+void launch_rrsnet_tc(int precision, int variant, int grid, const float* params,
+                      const float4* feat, const long long* n_ptr, long long n_host, float* q,
+                      int sentinel, DevStats* st, unsigned int* status, cudaStream_t s);
+// Resident CTAs per SM of the two-tile kernel at precision 16 or 17 (at least 1).
+int rrsnet_tc2_max_blocks(int precision);
 
 // Launch shape of the RRSNet kernel for one queue size: the autotuner's unit (tune.cu).
 struct RrsnetChoice {
-    int variant;        // FP32: rows per thread (1 or 2); tensor cores: 0
+    int variant;        // FP32: rows per thread (1 or 2); tensor cores: tiles per CTA - 1
     int blocks_per_sm;  // grid = SMs x blocks_per_sm (extra blocks exit at once)
 };
 constexpr int kTuneBuckets = 17;  // bucket b: floor(log2 n) = b + 8, clamped to [0, 16]

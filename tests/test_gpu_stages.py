@@ -357,12 +357,16 @@ def test_rrsnet_launch_shapes_give_identical_factors(nrrs, precision):
     sc.set_params(I.rrsnet_init_params(7))
     shapes = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2)] if precision == 32 else \
         [(0, 1), (0, 2), (0, 4), (0, 6), (0, 8)]
+    if precision in (16, 17):  # two tiles in flight per CTA
+        shapes += [(1, 1), (1, 3), (1, 8)]
     for n in (1, 300, 5000, 100_003, (1 << 21) + 7):
         X = _dev(I.random_features(n, seed=n))
         ref = None
         for v, b in shapes:
             nrrs.nrrs_set_rrsnet_shape(sc.handle, precision, -1, v, b)
-            q = sc.query(X, precision=precision).cpu().numpy()
+            # NaN first: a launch that wrote nothing cannot pass on stale memory
+            q = torch.full((n,), float("nan"), dtype=torch.float32, device=X.device)
+            q = sc.query(X, precision=precision, out=q).cpu().numpy()
             if ref is None:
                 ref = q
             np.testing.assert_array_equal(q, ref)
@@ -384,7 +388,7 @@ def test_tuner_table_and_render_invariance(nrrs, precision):
     rep = a.tune(precision)
     assert rep["rows"] == [min(12582912, 3 << (k + 7)) for k in range(17)]
     assert all(x <= y for x, y in zip(rep["ms_best"], rep["ms_default"]))
-    ok = {1, 2} if precision == 32 else {0}
+    ok = {1, 2} if precision == 32 else {0} if precision == 8 else {0, 1}
     assert set(rep["variant"]) <= ok and min(rep["blocks_per_sm"]) >= 1
     for frame in range(3):
         for graph in (0, 1):
