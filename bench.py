@@ -4,7 +4,8 @@ Headline (`value`): the Mix-Depth workload on one GPU -- the three-room scene wi
 1,000,000 random triangles (60 % GGX) joined by narrow doorways, 1920 x 1080 px, depth
 32, 128 spp rendered as 8 frames of 16 spp.  A step is one 16-spp frame through
 nrrs_render (camera rays, then per depth the traversal, shading, RRSNet at the depths
-the Mix-Depth gate marks -- tensor cores, split BF16 operands -- and heuristic factors
+the Mix-Depth gate marks -- BF16 tensor cores, fused with the shading of those depths --
+and heuristic factors
 elsewhere, normalization, split counts with the per-pixel accumulation, compaction and
 BSDF sampling of the children, the frame estimate), graph-captured, with the launch
 shapes the autotuner chose per queue-size bucket.  Set-up, untimed: the BVH build,
@@ -45,17 +46,17 @@ HL_FRAMES = 8                        # 8 frames x 16 spp = 128 spp
 HL_TRAIN = (480, 270, 4)             # online training frames of the same scene
 HL_PRETRAIN = 200                    # untimed training steps before the search
 HL_SEARCH = (480, 270)               # Mix-Depth estimation renders (1 spp)
-HL_PRECISION = 16                    # RRSNet on the tensor cores, split BF16 operands
+HL_PRECISION = 17                    # RRSNet on the tensor cores, BF16 operands
 HL_WORKLOAD = ("three_rooms (1,000,000 random triangles, 60 % GGX) 1920x1080 px, depth 32, "
                "128 spp as 8 frames x 16 spp; step = one 16-spp frame, NET_MIX (searched "
-               "Mix-Depth gate), RRSNet split-BF16 tensor cores at gated depths, heuristic "
+               "Mix-Depth gate), RRSNet BF16 tensor cores fused with shading at gated depths, heuristic "
                "elsewhere, tuned launch shapes, CUDA-graph bounce loop, cap 2*P")
 # second section: the online training step
 W_IMG, H_IMG, SPP, DEPTH = 256, 256, 16, 16
 TRAIN_SPP = 2          # recorded training frame: 256x256x2 spp ~ 2^19 training vertices
 PRETRAIN_STEPS = 300   # untimed online training before the timed steps (20 warm-up + 280 full)
-ONLINE_PRECISION = 16  # inference frame's RRSNet: split-BF16 tensor cores
-WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet split-BF16 tensor-core factors "
+ONLINE_PRECISION = 17  # inference frame's RRSNet: BF16 tensor cores
+WORKLOAD = ("occluded_room 256x256 px, 16 spp, depth 16, RRSNet BF16 tensor-core factors "
             "(NET), budget P, cap 2*P; step = online RRSNet/StatNet training step on a recorded "
             "256x256x2 spp frame + the 16 spp inference frame")
 EFF_SEEDS = 5          # independent render seeds per estimator in the efficiency tables
@@ -364,7 +365,7 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0, seeds=EFF_S
     ADRRS_NN (StatNet's radiance over the pixel estimate at every depth), NET_MIX (the
     Mix-Depth gate over FIXED / HEUR / NET) and NET_MIX_ADRRS (over FIXED / ADRRS (NN) /
     NET, the paper's set), NET and NET_MIX again at every tensor-core precision asked
-    for (16 = split BF16, 8 = E4M3) -- each averaging 16 frames of 16 spp, against a
+    for (17 = BF16, 16 = split BF16, 8 = E4M3) -- each averaging 16 frames of 16 spp, against a
     4096-spp plain path-traced reference (256 frames x 16 spp, no RRS), repeated with
     `seeds` independent render seeds: mean and standard error per estimator.  nee=1:
     every render, the reference and the Mix-Depth searches with next-event estimation."""
@@ -393,7 +394,7 @@ def efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, nee=0, seeds=EFF_S
     modes = [("PLAIN_RR", nrrs.RRS_PLAIN_RR, 0, 32), ("HEUR_NORM", nrrs.RRS_HEUR_NORM, 0, 32),
              ("ADRRS_NN", nrrs.RRS_NET_MIX, all_adrrs, 32),
              ("NET_MIX_ADRRS", nrrs.RRS_NET_MIX, gate_adrrs["gate"], 32)]
-    tag = {32: "", 16: "_BF16", 8: "_E4M3"}
+    tag = {32: "", 17: "_BF16", 16: "_BF16X3", 8: "_E4M3"}
     for prec in precisions:
         modes.append(("NET" + tag[prec], nrrs.RRS_NET, 0, prec))
         modes.append(("NET_MIX" + tag[prec], nrrs.RRS_NET_MIX, gates[prec]["gate"], prec))
@@ -556,7 +557,8 @@ def online_section(args, nrrs, torch, dev, stream, seed_hi, local_rank, rank):
     }
     eff = None
     if rank == 0 and not args.no_efficiency:
-        eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi, precisions=(32, 16, 8))
+        eff = efficiency_section(nrrs, sc, torch, dev, stream, seed_hi,
+                                 precisions=(32, 17, 16, 8))
 
         def trained_scene(nee, rrsnet_inputs, statnet_encoding):
             """A second RRSNet / StatNet pair trained online like the first."""
@@ -647,12 +649,16 @@ def run_ours(args, rank, world, local_rank):
     # bracket only the dominant stage's launches, which the roofline needs
     warm_ms = np.zeros(nrrs.STAGES)
     warm_n = np.zeros(nrrs.STAGES, dtype=np.int64)
-    warm = {"live": 0, "evals": 0, "children": 0, "last": 0}
+    warm = {"live": 0, "evals": 0, "children": 0, "last": 0, "live_net": 0}
+    gate_names = nrrs.gate_methods(gate, HL_DEPTH)
     for k in range(args.warmup):
         st = render(k, profile=1)
         warm_ms += st["stage_ms"]
         warm_n += st["stage_launches"]
         warm["live"] += int(st["live"].sum())
+        # slots of the depths whose shading runs fused with RRSNet
+        warm["live_net"] += int(sum(st["live"][d] for d in range(HL_DEPTH - 1)
+                                    if gate_names[d] == "NET"))
         warm["evals"] += st["net_evals"]
         warm["children"] += int(st["live"][1:].sum())
         warm["last"] += int(st["live"][HL_DEPTH - 1])
@@ -766,8 +772,9 @@ def run_ours(args, rank, world, local_rank):
         roofline["issue"]["frac_of_issue_peak"] = issue_active
     stage_bytes = {
         "extend": BYTES_PER_RAY_EXTEND * warm["live"],
-        "shade": BYTES_PER_RAY_SHADE * warm["live"] + 64 * warm["evals"],
-        "rrsnet": 68 * warm["evals"],
+        # the last depth only deposits (split_count); NET depths shade in the fused kernel
+        "shade": BYTES_PER_RAY_SHADE * (warm["live"] - warm["last"] - warm["live_net"]),
+        "rrsnet": BYTES_PER_RAY_SHADE * warm["live_net"],
         "split_count": BYTES_PER_SLOT_DEPOSIT * warm["last"],
         "split_scatter": BYTES_PER_PARENT_SPLIT * (warm["live"] - warm["last"])
         + BYTES_PER_CHILD_SPLIT * warm["children"],
@@ -785,12 +792,19 @@ def run_ours(args, rank, world, local_rank):
     roofline["stages"] = stages
     rr_ms = warm_ms[names.index("rrsnet")]
     rrsnet = {
-        "in_render": {"precision": "split BF16 (tensor cores)", "evaluations_per_frame":
-                      warm["evals"] / max(1, args.warmup),
+        "in_render": {"precision": "BF16 (tensor cores)",
+                      "kernel": "k_shade_rrsnet_tc: shading and RRSNet fused at NET depths "
+                                "(the features stay in shared memory); the time includes the "
+                                "shading of those depths",
+                      "evaluations_per_frame": warm["evals"] / max(1, args.warmup),
                       "ms_per_frame": float(rr_ms / max(1, args.warmup)),
                       "tflops": RRSNET_FLOP_PER_PATH * warm["evals"] / (rr_ms / 1000) / 1e12
-                      if rr_ms > 0 else None},
+                      if rr_ms > 0 else None,
+                      "bf16_peak_tflops": bf16},
     }
+    ir = rrsnet["in_render"]
+    if ir["tflops"]:
+        ir["frac_of_bf16_tensor_peak"] = ir["tflops"] / bf16
     if qstats:
         n_q, qms, tuner2 = qstats
         fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12  # FP32 SIMT FMA lanes x max clock

@@ -317,6 +317,16 @@ NRRS_API nrrs_status nrrs_bvh8_export(const nrrs_scene* scene, uint32_t* nodes,
  * references). */
 NRRS_API nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits);
 
+/* Chooses how later renders evaluate RRSNet at their NET depths on the tensor cores
+ * (precisions 16 and 17, the 16 vertex features of Sec. 4 "Network Architecture"):
+ * on = 1 (the default) shades the depth's vertices and runs the network in one kernel,
+ * the features going from registers into shared memory as the first layer's operand;
+ * on = 0 writes them to device memory (64 bytes per vertex) for a separate RRSNet kernel.
+ * Both give the same factors, deposits and images, bit for bit.  Training frames (which
+ * record the features) and the NRRS / AID inputs always take the separate kernels.
+ * Errors: INVALID_ARG (NULL scene, on not 0 or 1). */
+NRRS_API nrrs_status nrrs_set_shade_fusion(nrrs_scene* scene, int32_t on);
+
 /* Rebuilds the scene's BVH2 (and its FP16 copy and four-wide collapse) with another
  * builder: 0 = the host binned-SAH builder of nrrs_create_scene (the default), 1 = the
  * device build of the eight-wide tree stopped before its collapse (Morton order, then

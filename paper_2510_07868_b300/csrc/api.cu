@@ -224,6 +224,9 @@ struct TrainState {
 struct nrrs_scene {
     int device = 0;
     int n_sm = 148;
+    // NET depths at precisions 16 and 17 shade and run RRSNet in one kernel (features in
+    // shared memory); off: k_shade, then k_rrsnet_tc on the features in HBM
+    bool fuse_net = true;
     int64_t n_nodes = 0, n_tri = 0;
     float4* nodes = nullptr;
     float4* nodes4 = nullptr;  // four-wide tree (NULL when its stack bound exceeds the kernel's)
@@ -773,6 +776,13 @@ nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits) {
     return NRRS_OK;
 }
 
+nrrs_status nrrs_set_shade_fusion(nrrs_scene* scene, int32_t on) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (on != 0 && on != 1) return fail(NRRS_ERR_INVALID_ARG, "on must be 0 or 1");
+    scene->fuse_net = on != 0;
+    return NRRS_OK;
+}
+
 nrrs_status nrrs_set_rrsnet_inputs(nrrs_scene* scene, int32_t mode) {
     if (!scene || mode < 0 || mode > 2) return fail(NRRS_ERR_INVALID_ARG, "bad RRSNet input mode");
     if (mode == scene->rrsnet_inputs) return NRRS_OK;
@@ -1044,6 +1054,10 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
     const int normalized = rrs_mode == NRRS_RRS_HEUR_NORM || rrs_mode == NRRS_RRS_NET ||
                            rrs_mode == NRRS_RRS_NET_MIX;
     const int update = o.update_ref && !o.d_pixel_ref;
+    // the fused shade + RRSNet kernel serves the tensor-core precisions on the 16 vertex
+    // features (not the NRRS or AID inputs, which need StatNet or the grid first)
+    const bool fuse = scene->fuse_net && (o.precision == 16 || o.precision == 17) &&
+                      !nrrs_inputs && !aid_inputs;
 
     // RRSNet launch shape per depth, from the queue sizes of the last frame
     RrsnetChoice net_shape[NRRS_MAX_DEPTH];
@@ -1113,7 +1127,15 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
             }
             TIMED(NRRS_STAGE_EXTEND,
                   launch_trace(scene->view, q[cur], w, d, scene->grid_trace, r.jobs, s));
-            TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
+            // NET depths on the tensor cores: shading and RRSNet in one kernel (the
+            // features stay in shared memory) unless they must be recorded
+            const bool fused = fuse && kind == kFactorNet && !rec;
+            if (fused)
+                TIMED(NRRS_STAGE_RRSNET,
+                      launch_shade_rrsnet(o.precision, scene->n_sm, scene->view, q[cur], w, r, d,
+                                          s));
+            else
+                TIMED(NRRS_STAGE_SHADE, launch_shade(kind, scene->view, q[cur], w, r, d, s));
             if (nee)  // shadow rays: unoccluded contributions join the deposits
                 TIMED(NRRS_STAGE_SHADOW,
                       launch_shadow(scene->view, w, d, scene->grid_trace, r.jobs, s));
@@ -1121,6 +1143,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                 TIMED(NRRS_STAGE_RRSNET,
                       launch_aid_rrsnet(r.params, reinterpret_cast<const float2*>(scene->train.rgrid),
                                         scene->view, w, q[cur], r, d, scene->n_sm * 4, s));
+                if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
+            } else if (kind == kFactorNet && fused) {
                 if (!batch) TIMED(NRRS_STAGE_NORMALIZE, launch_sum_q(w, q[cur], r, d, s));
             } else if (kind == kFactorNet) {
                 if (nrrs_inputs)  // StatNet, then the NRRS inputs of RRSNet
@@ -1175,7 +1199,8 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
         const uint64_t sv[] = {(uint64_t)width, (uint64_t)height, (uint64_t)spp,
                                (uint64_t)max_depth, (uint64_t)rrs_mode, (uint64_t)o.precision,
                                o.gate, (uint64_t)(rec != nullptr), (uint64_t)o.profile,
-                               (uint64_t)heur_frame, (uint64_t)nee, (uint64_t)nrrs_inputs};
+                               (uint64_t)heur_frame, (uint64_t)nee, (uint64_t)nrrs_inputs,
+                               (uint64_t)fuse};
         for (uint64_t v : sv) shape = mix_key(shape, v);
         uint64_t args = shape;
         auto fbits = [](float f) { uint32_t u; std::memcpy(&u, &f, 4); return (uint64_t)u; };

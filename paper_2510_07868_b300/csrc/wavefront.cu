@@ -6,6 +6,7 @@
 #include <cfloat>
 #include <cstdio>
 
+#include "tc.cuh"
 #include "wavefront.cuh"
 
 namespace nrrs {
@@ -315,12 +316,115 @@ __global__ void k_camera_jobs(RenderParams rp, long long P, QueueView out) {
     out.t[i] = make_float4(1.0f, 1.0f, 1.0f, bitsf(sample));
 }
 
-// Extension of depth `depth`, part 2 (fixed grid-stride, coherent): emission deposit,
-// termination, and the RRS factor q_orig of each vertex; NET depths store the 16
-// features and q = -1 for the RRSNet kernel.  Non-NET depths also write the block's
-// FP64 partial sum of q (fixed assignment, so the sum is reproducible).  With NEE the
-// emission found by BSDF sampling takes its MIS weight, and every vertex that goes on
-// (the ones that get a factor) writes its shadow ray and contribution.
+// Extension of depth `depth`, part 2, for slot i: the emission deposit, termination, and
+// the RRS factor q_orig of the vertex; at NET depths the 16 features (f) and q = -1 for
+// the network.  With NEE the emission found by BSDF sampling takes its MIS weight, and
+// every vertex that goes on (the ones that get a factor) writes its shadow ray and
+// contribution (so, sd, sk).  Returns q.
+template <int KIND, bool NEE>
+__device__ __forceinline__ float shade_slot(const SceneView& sc, const QueueView& cur,
+                                            const WorkView& w, const RenderParams& rp,
+                                            int depth, long long i, float eps_I, int has_ref,
+                                            float4& dep, float4& so, float4& sd, float4& sk,
+                                            float4 (&f)[4], unsigned int& nonfinite) {
+    const float2 hh = w.hit[i];
+    const int slot = __float_as_int(hh.y);
+    const float4 o4 = cur.o[i];
+    float q = 0.0f;
+    dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
+    so = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    sd = so;
+    sk = so;
+    if (slot >= 0) {
+        const float4 d4 = cur.d[i];
+        const float4 t4 = cur.t[i];
+        int mi;
+        const V3 ng = tri_geom_normal(sc, slot, &mi);
+        const nrrs_material m = sc.mats[mi];
+        const V3 d = xyz(d4);
+        const bool front = dot3(ng, d) < 0.0f;
+        // the job's depth limit, scene box, HEUR floor and emitters in a batched render
+        int Dmax = rp.D;
+        float lo3[3] = {sc.lo[0], sc.lo[1], sc.lo[2]};
+        float ie3[3] = {sc.inv_ext[0], sc.inv_ext[1], sc.inv_ext[2]};
+        float epsI = eps_I;
+        uint32_t lpix = fbits(o4.w);
+        const float4* emit = sc.emit;
+        const float* ecdf = sc.emit_cdf;
+        int n_emit = sc.n_emit;
+        float inv_area = sc.inv_area;
+        if (rp.jobs.job) {
+            const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, fbits(o4.w));
+            const JobDev* J = rp.jobs.job + j;
+            Dmax = J->D;
+            for (int k = 0; k < 3; ++k) {
+                lo3[k] = J->lo[k];
+                ie3[k] = J->inv_ext[k];
+            }
+            epsI = rp.jobs.eps_I[j];
+            lpix -= (uint32_t)J->pixel_base;
+            if (NEE) {
+                emit += 3 * (size_t)J->emit_base;
+                ecdf += J->emit_base;
+                n_emit = J->n_emit;
+                inv_area = J->inv_area;
+            }
+        }
+        if (front || m.two_sided) {
+            float we = 1.0f;  // MIS weight against the previous vertex's emitter sample
+            if (NEE && depth > 1 && n_emit > 0 &&
+                (m.Le[0] > 0.0f || m.Le[1] > 0.0f || m.Le[2] > 0.0f)) {
+                const float pb = cur.pdf[i];
+                if (pb > 0.0f)
+                    we = power_heuristic(pb, hh.x * hh.x * inv_area / fabsf(dot3(ng, d)));
+            }
+            dep.x = t4.x * m.Le[0] * we;
+            dep.y = t4.y * m.Le[1] * we;
+            dep.z = t4.z * m.Le[2] * we;
+        }
+        const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
+        const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
+        if (!black && !dead && depth < Dmax) {
+            if (NEE) {
+                const U4 r = draw(rp.fc->key0, rp.fc->key1, lpix, fbits(t4.w),
+                                  (uint32_t)depth, kPurposeNee, fbits(d4.w));
+                const V3 ns = front ? ng : ng * -1.0f;
+                nee_vertex(emit, ecdf, n_emit, inv_area, sc.mats, xyz(o4) + d * hh.x, ns,
+                           d * -1.0f, m, t4, r, &so, &sd, &sk);
+            }
+            if (KIND == kFactorOne) {
+                q = 1.0f;
+            } else if (KIND == kFactorPlain) {
+                q = fminf(1.0f, lum(t4.x, t4.y, t4.z));
+            } else if (KIND == kFactorHeur) {
+                q = heur_factor(t4, rp, fbits(o4.w), has_ref, epsI);
+            } else {  // network depths (RRSNet or StatNet): features, q marked -1
+                const V3 p = xyz(o4) + d * hh.x;
+                const V3 ns = front ? ng : ng * -1.0f;
+                f[0] = make_float4(
+                    ie3[0] > 0.0f ? (p.x - lo3[0]) * ie3[0] : 0.5f,
+                    ie3[1] > 0.0f ? (p.y - lo3[1]) * ie3[1] : 0.5f,
+                    ie3[2] > 0.0f ? (p.z - lo3[2]) * ie3[2] : 0.5f, -d.x);
+                f[1] = make_float4(-d.y, -d.z, ns.x, ns.y);
+                f[2] = make_float4(ns.z, m.albedo[0], m.albedo[1], m.albedo[2]);
+                f[3] = make_float4((float)depth / (float)Dmax, boxcox(t4.x, rp.boxcox_lambda),
+                                   boxcox(t4.y, rp.boxcox_lambda),
+                                   boxcox(t4.z, rp.boxcox_lambda));
+                if (w.rough) w.rough[i] = m.type == 0 ? 1.0f : m.roughness;
+                q = -1.0f;  // filled by the RRSNet kernel
+            }
+            if (KIND < kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {
+                q = 0.0f;
+                ++nonfinite;
+            }
+        }
+    }
+    return q;
+}
+
+// Extension of depth `depth`, part 2 (fixed grid-stride, coherent): shade_slot for every
+// live slot; NET depths store the features for the RRSNet kernel.  Non-NET depths also
+// write the block's FP64 partial sum of q (fixed assignment, so the sum is reproducible).
 template <int KIND, bool NEE>
 __global__ void __launch_bounds__(256)
 k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
@@ -333,96 +437,15 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
     unsigned int nonfinite = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 hh = w.hit[i];
-        const int slot = __float_as_int(hh.y);
-        const float4 o4 = cur.o[i];
-        float q = 0.0f;
-        float4 dep = make_float4(0.0f, 0.0f, 0.0f, o4.w);
-        float4 so = make_float4(0.0f, 0.0f, 0.0f, 0.0f), sd = so, sk = so;
-        if (slot >= 0) {
-            const float4 d4 = cur.d[i];
-            const float4 t4 = cur.t[i];
-            int mi;
-            const V3 ng = tri_geom_normal(sc, slot, &mi);
-            const nrrs_material m = sc.mats[mi];
-            const V3 d = xyz(d4);
-            const bool front = dot3(ng, d) < 0.0f;
-            // the job's depth limit, scene box, HEUR floor and emitters in a batched render
-            int Dmax = rp.D;
-            float lo3[3] = {sc.lo[0], sc.lo[1], sc.lo[2]};
-            float ie3[3] = {sc.inv_ext[0], sc.inv_ext[1], sc.inv_ext[2]};
-            float epsI = eps_I;
-            uint32_t lpix = fbits(o4.w);
-            const float4* emit = sc.emit;
-            const float* ecdf = sc.emit_cdf;
-            int n_emit = sc.n_emit;
-            float inv_area = sc.inv_area;
-            if (rp.jobs.job) {
-                const int j = job_of_pixel(rp.jobs.job, rp.jobs.n, fbits(o4.w));
-                const JobDev* J = rp.jobs.job + j;
-                Dmax = J->D;
-                for (int k = 0; k < 3; ++k) {
-                    lo3[k] = J->lo[k];
-                    ie3[k] = J->inv_ext[k];
-                }
-                epsI = rp.jobs.eps_I[j];
-                lpix -= (uint32_t)J->pixel_base;
-                if (NEE) {
-                    emit += 3 * (size_t)J->emit_base;
-                    ecdf += J->emit_base;
-                    n_emit = J->n_emit;
-                    inv_area = J->inv_area;
-                }
-            }
-            if (front || m.two_sided) {
-                float we = 1.0f;  // MIS weight against the previous vertex's emitter sample
-                if (NEE && depth > 1 && n_emit > 0 &&
-                    (m.Le[0] > 0.0f || m.Le[1] > 0.0f || m.Le[2] > 0.0f)) {
-                    const float pb = cur.pdf[i];
-                    if (pb > 0.0f)
-                        we = power_heuristic(pb, hh.x * hh.x * inv_area / fabsf(dot3(ng, d)));
-                }
-                dep.x = t4.x * m.Le[0] * we;
-                dep.y = t4.y * m.Le[1] * we;
-                dep.z = t4.z * m.Le[2] * we;
-            }
-            const bool black = m.albedo[0] == 0.0f && m.albedo[1] == 0.0f && m.albedo[2] == 0.0f;
-            const bool dead = t4.x == 0.0f && t4.y == 0.0f && t4.z == 0.0f;
-            if (!black && !dead && depth < Dmax) {
-                if (NEE) {
-                    const U4 r = draw(rp.fc->key0, rp.fc->key1, lpix, fbits(t4.w),
-                                      (uint32_t)depth, kPurposeNee, fbits(d4.w));
-                    const V3 ns = front ? ng : ng * -1.0f;
-                    nee_vertex(emit, ecdf, n_emit, inv_area, sc.mats, xyz(o4) + d * hh.x, ns,
-                               d * -1.0f, m, t4, r, &so, &sd, &sk);
-                }
-                if (KIND == kFactorOne) {
-                    q = 1.0f;
-                } else if (KIND == kFactorPlain) {
-                    q = fminf(1.0f, lum(t4.x, t4.y, t4.z));
-                } else if (KIND == kFactorHeur) {
-                    q = heur_factor(t4, rp, fbits(o4.w), has_ref, epsI);
-                } else {  // network depths (RRSNet or StatNet): features, q marked -1
-                    const V3 p = xyz(o4) + d * hh.x;
-                    const V3 ns = front ? ng : ng * -1.0f;
-                    float4* f = w.feat + 4 * i;
-                    f[0] = make_float4(
-                        ie3[0] > 0.0f ? (p.x - lo3[0]) * ie3[0] : 0.5f,
-                        ie3[1] > 0.0f ? (p.y - lo3[1]) * ie3[1] : 0.5f,
-                        ie3[2] > 0.0f ? (p.z - lo3[2]) * ie3[2] : 0.5f, -d.x);
-                    f[1] = make_float4(-d.y, -d.z, ns.x, ns.y);
-                    f[2] = make_float4(ns.z, m.albedo[0], m.albedo[1], m.albedo[2]);
-                    f[3] = make_float4((float)depth / (float)Dmax, boxcox(t4.x, rp.boxcox_lambda),
-                                       boxcox(t4.y, rp.boxcox_lambda),
-                                       boxcox(t4.z, rp.boxcox_lambda));
-                    if (w.rough) w.rough[i] = m.type == 0 ? 1.0f : m.roughness;
-                    q = -1.0f;  // filled by the RRSNet kernel
-                }
-                if (KIND < kFactorNet && !(q >= 0.0f && q <= FLT_MAX)) {
-                    q = 0.0f;
-                    ++nonfinite;
-                }
-            }
+        float4 dep, so, sd, sk, f[4];
+        const float q = shade_slot<KIND, NEE>(sc, cur, w, rp, depth, i, eps_I, has_ref, dep, so,
+                                              sd, sk, f, nonfinite);
+        if (KIND >= kFactorNet && q == -1.0f) {  // RRSNet or StatNet (ADRRS) depths
+            float4* fo = w.feat + 4 * i;
+            fo[0] = f[0];
+            fo[1] = f[1];
+            fo[2] = f[2];
+            fo[3] = f[3];
         }
         w.q[i] = q;
         w.dep[i] = dep;
@@ -444,6 +467,94 @@ k_shade(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
         atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
         atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
     }
+}
+
+// NET depths in one pass (shade and RRSNet fused): each CTA of 128 threads shades 128
+// consecutive slots (shade_slot), writes the features of the vertices that need a factor
+// straight into shared memory as the BF16 operand of RRSNet's first layer (no round trip
+// of the 64-byte feature rows through HBM), and runs the network on the tensor cores
+// (tc_hidden_layers, tc_output), so the factor replaces the -1 mark before q is stored.
+// The factors equal those k_rrsnet_tc computes from the same features, bit for bit; a
+// non-finite one is stored as kQRepair for k_sum_q to replace by the heuristic's.
+template <bool SPLIT, bool NEE>
+__global__ void __launch_bounds__(kTcThreads, 6)
+k_shade_rrsnet_tc(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int depth) {
+    __shared__ TcSmem<SPLIT> sm;
+    DevStats* st = w.st;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long n = st->live[depth - 1];
+    if ((long long)blockIdx.x * kTcThreads >= n) return;  // no tile: allocate nothing
+    tc_setup(&sm.tmem, &sm.bar, kTmemCols);
+    tc_stage_weights<SPLIT>(sm, rp.params, tid);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t bar = smem_u32(&sm.bar);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    const int has_ref = st->has_ref;
+    const float eps_I = st->eps_I;
+    uint32_t phase = 0;
+    unsigned int evals = 0, nonfinite = 0, unused = 0;
+    bool failed = false;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long i = tile * kTcThreads + tid;
+        float q = 0.0f;
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+        if (i < n) {
+            float4 dep, so, sd, sk, f[4];
+            q = shade_slot<kFactorNet, NEE>(sc, cur, w, rp, depth, i, eps_I, has_ref, dep, so,
+                                            sd, sk, f, unused);
+            w.dep[i] = dep;
+            if (NEE) {
+                w.sh_o[i] = so;
+                if (so.w > 0.0f) {
+                    w.sh_d[i] = sd;
+                    w.sh_c[i] = sk;
+                }
+            }
+            if (q == -1.0f) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    x[4 * k] = f[k].x; x[4 * k + 1] = f[k].y;
+                    x[4 * k + 2] = f[k].z; x[4 * k + 3] = f[k].w;
+                }
+            }
+        }
+        const bool net = i < n && q == -1.0f;
+        tc_store_input<SPLIT>(sm, tid, x);
+        float h[32];
+        if (!tc_hidden_layers<SPLIT>(sm, tmem, bar, taddr, phase, h)) {
+            failed = true;
+            break;
+        }
+        if (net) {
+            q = tc_output(sm.w4, h);
+            ++evals;
+            if (!(q >= 0.0f && q <= FLT_MAX)) {
+                q = kQRepair;
+                ++nonfinite;
+            }
+        }
+        if (i < n) w.q[i] = q;
+        fence_before();
+        __syncthreads();  // TMEM reads done before the next tile's MMA overwrites it
+    }
+    if (failed && tid == 0) atomicOr(&st->status, (unsigned int)NRRS_STATUS_TIMEOUT);
+    evals = warp_sum(evals);
+    nonfinite = warp_sum(nonfinite);
+    if ((tid & 31) == 0) {
+        if (evals) atomicAdd(&st->net_evals, (unsigned long long)evals);
+        if (nonfinite) {
+            atomicAdd(&st->nonfinite, (unsigned long long)nonfinite);
+            atomicOr(&st->status, (unsigned int)NRRS_STATUS_NONFINITE);
+        }
+    }
+    tc_teardown(tmem, kTmemCols);
 }
 
 // FP64 partial sums of q over a fixed grid-stride assignment, so Sigma q is reproducible;
@@ -1041,6 +1152,22 @@ void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& 
         default: NRRS_SHADE(kFactorAdrrs); break;
     }
 #undef NRRS_SHADE
+}
+
+void launch_shade_rrsnet(int precision, int n_sm, const SceneView& sc, QueueView cur,
+                         const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s) {
+    const int G = n_sm * 6;  // persistent: six CTAs per SM stay resident
+    if (precision == 17) {
+        if (rp.nee)
+            k_shade_rrsnet_tc<false, true><<<G, kTcThreads, 0, s>>>(sc, cur, w, rp, depth);
+        else
+            k_shade_rrsnet_tc<false, false><<<G, kTcThreads, 0, s>>>(sc, cur, w, rp, depth);
+    } else {
+        if (rp.nee)
+            k_shade_rrsnet_tc<true, true><<<G, kTcThreads, 0, s>>>(sc, cur, w, rp, depth);
+        else
+            k_shade_rrsnet_tc<true, false><<<G, kTcThreads, 0, s>>>(sc, cur, w, rp, depth);
+    }
 }
 
 void launch_sum_q(const WorkView& w, QueueView cur, const RenderParams& rp, int depth,

@@ -177,6 +177,11 @@ void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int dep
 // unoccluded ray to the slot's deposit.
 void launch_shadow(const SceneView& sc, const WorkView& w, int depth, int grid,
                    const JobWork& jobs, cudaStream_t s);
+// NET depths with shading and the tensor-core RRSNet (precision 16: split BF16, 17:
+// BF16) fused in one kernel; the features stay in shared memory.  Same q, deposits and
+// shadow rays as launch_shade(kFactorNet) followed by launch_rrsnet with sentinel.
+void launch_shade_rrsnet(int precision, int n_sm, const SceneView& sc, QueueView cur,
+                         const WorkView& w, const RenderParams& rp, int depth, cudaStream_t s);
 void launch_shade(int kind, const SceneView& sc, QueueView cur, const WorkView& w,
                   const RenderParams& rp, int depth, cudaStream_t s);
 

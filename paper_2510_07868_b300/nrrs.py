@@ -47,6 +47,7 @@ EXPORTED = [
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
     "nrrs_set_bvh_precision", "nrrs_set_bvh_builder", "nrrs_bvh8_info", "nrrs_bvh8_export",
+    "nrrs_set_shade_fusion",
 ]
 
 
@@ -246,6 +247,7 @@ def _load():
         "nrrs_batch_info": ([P, P, P, P], I32),
         "nrrs_set_traversal": ([P, I32], I32),
         "nrrs_set_bvh_precision": ([P, I32], I32),
+        "nrrs_set_shade_fusion": ([P, I32], I32),
         "nrrs_set_bvh_builder": ([P, I32, P], I32),
         "nrrs_bvh8_info": ([P, P], I32),
         "nrrs_bvh8_export": ([P, P, I64, P, I64], I32),
@@ -358,6 +360,10 @@ def nrrs_set_traversal(scene, width):
 
 def nrrs_set_bvh_precision(scene, bits):
     _check(_lib.nrrs_set_bvh_precision(scene, bits))
+
+
+def nrrs_set_shade_fusion(scene, on):
+    _check(_lib.nrrs_set_shade_fusion(scene, on))
 
 
 def nrrs_set_bvh_builder(scene, builder):
@@ -691,6 +697,9 @@ class Scene:
 
     def set_bvh_precision(self, bits):
         nrrs_set_bvh_precision(self.handle, bits)
+
+    def set_shade_fusion(self, on):
+        nrrs_set_shade_fusion(self.handle, int(on))
 
     def set_bvh_builder(self, builder):
         return nrrs_set_bvh_builder(self.handle, builder)
