@@ -317,6 +317,24 @@ NRRS_API nrrs_status nrrs_bvh8_export(const nrrs_scene* scene, uint32_t* nodes,
  * references). */
 NRRS_API nrrs_status nrrs_set_bvh_precision(nrrs_scene* scene, int32_t bits);
 
+/* The BVH2 traversal's stack (no counterpart in the paper; its renderer traces with
+ * OptiX).  A ray holds at most one pushed sibling per inner node on its current path, so
+ * a tree whose root-to-leaf paths hold at most 24 inner nodes (the height) is traversed
+ * with a 24-entry stack, otherwise with the 40-entry one the build's depth cap fits;
+ * the short stack leaves 16 KB more of each SM's on-chip memory to the L1 cache that
+ * holds the nodes.  entries = 0 (the default) chooses by the height, 40 always takes the
+ * long stack, 24 the short one.  Both find the same closest hits.  The choice follows
+ * later tree rebuilds (nrrs_set_bvh_builder); the eight- and four-wide trees keep their
+ * own stacks.  Errors: INVALID_ARG (NULL scene, entries not 0, 24 or 40); UNSUPPORTED
+ * (24 for a taller tree, or one whose height is unknown). */
+NRRS_API nrrs_status nrrs_set_traversal_stack(nrrs_scene* scene, int32_t entries);
+
+/* The BVH2's height (-1 when its node order does not allow computing it) and the stack
+ * entries per ray the BVH2 traversal uses now.  Either pointer may be NULL.
+ * Errors: INVALID_ARG (NULL scene). */
+NRRS_API nrrs_status nrrs_traversal_stack_info(const nrrs_scene* scene, int32_t* height,
+                                               int32_t* entries);
+
 /* Chooses how later renders evaluate RRSNet at their NET depths on the tensor cores
  * (precisions 16 and 17, the 16 vertex features of Sec. 4 "Network Architecture"):
  * on = 1 (the default) shades the depth's vertices and runs the network in one kernel,

@@ -227,6 +227,10 @@ struct nrrs_scene {
     // NET depths at precisions 16 and 17 shade and run RRSNet in one kernel (features in
     // shared memory); off: k_shade, then k_rrsnet_tc on the features in HBM
     bool fuse_net = true;
+    // the BVH2's height (most inner nodes on a root-to-leaf path, -1 unknown) and the
+    // traversal stack asked for (0: the short stack when the tree fits it)
+    int bvh2_h = -1;
+    int stack_req = 0;
     int64_t n_nodes = 0, n_tri = 0;
     float4* nodes = nullptr;
     float4* nodes4 = nullptr;  // four-wide tree (NULL when its stack bound exceeds the kernel's)
@@ -475,6 +479,13 @@ CamView cam_view(const nrrs_camera& cam) {
 
 // Uploads a built BVH (and its triangle references), the materials and the camera
 // (NULL for a batch, whose cameras live in the job table) into a new scene.
+// The BVH2 traversal takes the short stack when the tree is known to fit it, unless the
+// long one was asked for.
+int short_stack_on(const nrrs_scene* s) {
+    const bool fits = s->bvh2_h >= 0 && s->bvh2_h <= trace_short_stack_entries();
+    return fits && s->stack_req != trace_stack_entries() ? 1 : 0;
+}
+
 nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri,
                          const nrrs_material* mats, int32_t n_mat, const nrrs_camera* cam,
                          const EmitterHost& em, int device, nrrs_scene** out) {
@@ -534,6 +545,8 @@ nrrs_status upload_scene(const BvhHost& bvh, const Bvh4Host* bvh4, int64_t n_tri
     s->view.nodes4 = nullptr;  // the BVH2 unless nrrs_set_traversal(4): measured no faster
     // FP16 boxes unless rounding grows them too much, or nrrs_set_bvh_precision(32)
     s->view.nodes_h = half_default ? s->nodes_h : nullptr;
+    s->bvh2_h = bvh2_height(bvh.nodes);
+    s->view.short_stack = short_stack_on(s);
     s->view.tris = s->tris;
     s->view.mats = s->mats;
     for (int k = 0; k < 3; ++k) {
@@ -733,6 +746,11 @@ nrrs_status nrrs_set_bvh_builder(nrrs_scene* scene, int32_t builder, float* buil
     scene->n_nodes = (int64_t)bvh.nodes.size();
     scene->view.nodes = nodes;
     scene->view.nodes_h = half_on ? nodes_h : nullptr;
+    scene->bvh2_h = bvh2_height(bvh.nodes);
+    if (scene->stack_req == trace_short_stack_entries() &&
+        !(scene->bvh2_h >= 0 && scene->bvh2_h <= trace_short_stack_entries()))
+        scene->stack_req = 0;  // the new tree is too tall for the stack asked for
+    scene->view.short_stack = short_stack_on(scene);
     if (scene->bvh_width == 4 && !nodes4) scene->bvh_width = 2;
     if (scene->bvh_width != 8) {
         scene->view.tris = tris;
@@ -780,6 +798,28 @@ nrrs_status nrrs_set_shade_fusion(nrrs_scene* scene, int32_t on) {
     if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
     if (on != 0 && on != 1) return fail(NRRS_ERR_INVALID_ARG, "on must be 0 or 1");
     scene->fuse_net = on != 0;
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_set_traversal_stack(nrrs_scene* scene, int32_t entries) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (entries != 0 && entries != trace_short_stack_entries() &&
+        entries != trace_stack_entries())
+        return fail(NRRS_ERR_INVALID_ARG, "entries must be 0, 24 or 40");
+    if (entries == trace_short_stack_entries() &&
+        !(scene->bvh2_h >= 0 && scene->bvh2_h <= entries))
+        return fail(NRRS_ERR_UNSUPPORTED, "the BVH2 is taller than the short stack");
+    scene->stack_req = entries;
+    scene->view.short_stack = short_stack_on(scene);
+    return NRRS_OK;
+}
+
+nrrs_status nrrs_traversal_stack_info(const nrrs_scene* scene, int32_t* height,
+                                      int32_t* entries) {
+    if (!scene) return fail(NRRS_ERR_INVALID_ARG, "scene is NULL");
+    if (height) *height = scene->bvh2_h;
+    if (entries)
+        *entries = scene->view.short_stack ? trace_short_stack_entries() : trace_stack_entries();
     return NRRS_OK;
 }
 
@@ -1218,6 +1258,7 @@ nrrs_status render_impl(nrrs_scene* scene, int32_t width, int32_t height, int32_
                                (uint64_t)(uintptr_t)scene->jw.part,
                                (uint64_t)(uintptr_t)scene->view.nodes4,
                                (uint64_t)(uintptr_t)scene->view.nodes_h,
+                               (uint64_t)scene->view.short_stack,
                                (uint64_t)(uintptr_t)scene->train.stat,
                                (uint64_t)o.cap_factor, (uint64_t)(uintptr_t)ws.sh_o,
                                (uint64_t)(uintptr_t)ws.qpdf[0], (uint64_t)(uintptr_t)ws.feat_net,

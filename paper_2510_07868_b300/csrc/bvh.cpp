@@ -236,6 +236,22 @@ struct Builder {
 
 }  // namespace
 
+int bvh2_height(const std::vector<BvhNode>& nodes) {
+    const size_t n = nodes.size();
+    std::vector<int> h(n, 1);
+    int best = 0;
+    for (size_t k = n; k-- > 0;) {  // children before their parents
+        for (int c = 0; c < 2; ++c) {
+            const int32_t ch = nodes[k].d[c];
+            if (ch < 0) continue;  // a leaf
+            if ((size_t)ch <= k || (size_t)ch >= n) return -1;
+            h[k] = std::max(h[k], 1 + h[ch]);
+        }
+        best = std::max(best, h[k]);
+    }
+    return best;
+}
+
 void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* out) {
     Box scene_box;
     for (int64_t i = 0; i < (int64_t)n_tri * 3; ++i) scene_box.grow(tri + i * 3);

@@ -20,6 +20,12 @@ struct BvhHost {
 
 void build_bvh(const float* tri, int32_t n_tri, const int32_t* mat_id, BvhHost* out);
 
+// Most inner nodes on any root-to-leaf path of the node array (one tree, or several
+// trees appended one after another as in a batch), which bounds the traversal stack: a
+// ray holds at most one pushed sibling per inner node on its current path.  Relies on
+// every child being stored after its parent (depth-first preorder); -1 when it is not.
+int bvh2_height(const std::vector<BvhNode>& nodes);
+
 // Four-wide tree collapsed from the BVH2 (bvh.cpp): 128 bytes per node, the children's
 // boxes as six float4 rows (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of children 0..3), then the
 // child codes (as BvhNode) and the leaf reference counts.  An unused slot is a leaf with

@@ -14,6 +14,10 @@ namespace {
 
 constexpr int kExtendThreads = 256;
 constexpr int kStack = 40;  // BVH build depth is capped below this
+// A BVH2 whose deepest path holds at most this many inner nodes (the three-room scene's
+// 1,000,026 triangles: 24) is traversed with a stack of this size: 16 KB less shared
+// memory per block, which the SM gives to the L1 cache that holds the nodes.
+constexpr int kShortStack = 24;
 constexpr int kSteps = 8;   // node visits between ray fetch rounds
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
@@ -314,7 +318,7 @@ __device__ __forceinline__ bool slab_half(const Ray& r, float hit_t, uint32_t wx
 // (boxes rounded outward: one memory sector per visit, the same closest hits; a leaf's
 // code packs its first reference and count), else the 64-byte FP32 nodes (a leaf's code
 // is ~first, its count a field of its own, held in n0..n2 beside the slots).
-template <bool HALF>
+template <bool HALF, int STACK>
 __device__ __forceinline__ void step_bvh2(const SceneView& sc, Ray& r, const Hit& h, int* stk,
                                           int stride, bool go, int& code0, int& code1,
                                           int& code2, int& n0, int& n1, int& n2) {
@@ -361,7 +365,7 @@ __device__ __forceinline__ void step_bvh2(const SceneView& sc, Ray& r, const Hit
     const bool first1 = i1 && (!i0 || t1n < t0n);
     const int near_c = first1 ? c1 : c0;
     const int far_c = first1 ? c0 : c1;
-    const bool push = i0 && i1 && r.sp < kStack;
+    const bool push = i0 && i1 && r.sp < STACK;
     const bool none = go && !i0 && !i1;
     const bool pop = none && r.sp > 0;
     int* slot = stk + (pop ? r.sp - 1 : r.sp) * stride;
@@ -387,14 +391,14 @@ __device__ __forceinline__ void test_leaf(const SceneView& sc, const Ray& r, Hit
 // tests of the leaves held.  The warp keeps stepping while some lane that still
 // traverses holds no leaf yet; lanes that hold one step along speculatively (Aila and
 // Laine's speculative while-while), which keeps lanes busy that would otherwise wait.
-template <bool HALF>
+template <bool HALF, int STACK>
 __device__ __forceinline__ void round_bvh2(const SceneView& sc, Ray& r, Hit& h, int* stk,
                                            int stride, bool active) {
     bool go = active && r.node >= 0;
     int code0 = 0, code1 = 0, code2 = 0, n0 = 0, n1 = 0, n2 = 0;
 #pragma unroll
     for (int step = 0; step < kSteps; ++step) {
-        step_bvh2<HALF>(sc, r, h, stk, stride, go, code0, code1, code2, n0, n1, n2);
+        step_bvh2<HALF, STACK>(sc, r, h, stk, stride, go, code0, code1, code2, n0, n1, n2);
         go = go && r.node >= 0 && (code1 | code2) == 0;
         if (!__any_sync(0xffffffffu, go && code0 == 0)) break;
     }
@@ -414,10 +418,10 @@ __device__ __forceinline__ void round_bvh2(const SceneView& sc, Ray& r, Hit& h, 
 // ANY: the shadow rays of next-event estimation, one per slot (t_max <= 0: none); the
 // query ends at the first hit before t_max, and an unoccluded ray adds its
 // contribution to the slot's deposit.
-template <int WIDTH, bool ANY>
+template <int WIDTH, bool ANY, int STACK = kStack>
 __global__ void __launch_bounds__(kExtendThreads, 4)
 k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
-    __shared__ int s_stack[kStack * kExtendThreads];
+    __shared__ int s_stack[STACK * kExtendThreads];
     int* stk = s_stack + threadIdx.x;
     DevStats* st = w.st;
     const long long n = st->live[depth - 1];
@@ -478,9 +482,9 @@ k_trace(SceneView sc, QueueView cur, WorkView w, int depth, JobWork jobs) {
         } else {
             // every lane of the warp runs the round (its votes need all of them)
             if (sc.nodes_h)
-                round_bvh2<true>(sc, ray, h, stk, kExtendThreads, idx >= 0);
+                round_bvh2<true, STACK>(sc, ray, h, stk, kExtendThreads, idx >= 0);
             else
-                round_bvh2<false>(sc, ray, h, stk, kExtendThreads, idx >= 0);
+                round_bvh2<false, STACK>(sc, ray, h, stk, kExtendThreads, idx >= 0);
             if (idx < 0) continue;
             if (ANY && h.slot >= 0) ray.node = -1;  // occluded: the query is over
             if (ray.node >= 0) continue;
@@ -507,16 +511,22 @@ int extend_block_threads() { return kExtendThreads; }
 
 int trace_stack_entries() { return kStack; }
 
+int trace_short_stack_entries() { return kShortStack; }
+
 int max_blocks_trace() {
     int nb = 1 << 30;
-    int n[6] = {1, 1, 1, 1, 1, 1};
+    int n[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_trace<2, false>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_trace<4, false>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_trace<2, true>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_trace<4, true>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[4], k_trace<8, false>, kExtendThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[5], k_trace<8, true>, kExtendThreads, 0);
-    for (int k = 0; k < 6; ++k) nb = n[k] < nb ? n[k] : nb;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[6], k_trace<2, false, kShortStack>,
+                                                  kExtendThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[7], k_trace<2, true, kShortStack>,
+                                                  kExtendThreads, 0);
+    for (int k = 0; k < 8; ++k) nb = n[k] < nb ? n[k] : nb;
     return nb < 1 ? 1 : nb;
 }
 
@@ -526,6 +536,8 @@ void launch_trace(const SceneView& sc, QueueView cur, const WorkView& w, int dep
         k_trace<8, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
     else if (sc.nodes4)
         k_trace<4, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
+    else if (sc.short_stack)
+        k_trace<2, false, kShortStack><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
     else
         k_trace<2, false><<<grid, kExtendThreads, 0, s>>>(sc, cur, w, depth, jobs);
 }
@@ -537,6 +549,8 @@ void launch_shadow(const SceneView& sc, const WorkView& w, int depth, int grid,
         k_trace<8, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
     else if (sc.nodes4)
         k_trace<4, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
+    else if (sc.short_stack)
+        k_trace<2, true, kShortStack><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
     else
         k_trace<2, true><<<grid, kExtendThreads, 0, s>>>(sc, none, w, depth, jobs);
 }

@@ -24,6 +24,7 @@ struct SceneView {
     const float* emit_cdf;
     int n_emit;
     float inv_area;       // 1 / total emitter area
+    int short_stack;      // 1: the BVH2's deepest path fits the short traversal stack
 };
 
 struct CamView {
@@ -167,6 +168,7 @@ int extend_block_threads();
 int split_block_threads();
 int max_blocks_trace();  // resident blocks per SM
 int trace_stack_entries();  // traversal stack size per ray
+int trace_short_stack_entries();  // the short stack, for BVH2s no taller than it
 
 void launch_ref_prepare(const float* ref, long long n3, float eps_rel, double alpha0,
                         long long P, DevStats* st, float* part, int G, cudaStream_t s);

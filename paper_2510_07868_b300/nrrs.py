@@ -47,7 +47,7 @@ EXPORTED = [
     "nrrs_set_rrsnet_shape", "nrrs_create_batch", "nrrs_render_batch", "nrrs_batch_info",
     "nrrs_set_traversal",
     "nrrs_set_bvh_precision", "nrrs_set_bvh_builder", "nrrs_bvh8_info", "nrrs_bvh8_export",
-    "nrrs_set_shade_fusion",
+    "nrrs_set_shade_fusion", "nrrs_set_traversal_stack", "nrrs_traversal_stack_info",
 ]
 
 
@@ -248,6 +248,8 @@ def _load():
         "nrrs_set_traversal": ([P, I32], I32),
         "nrrs_set_bvh_precision": ([P, I32], I32),
         "nrrs_set_shade_fusion": ([P, I32], I32),
+        "nrrs_set_traversal_stack": ([P, I32], I32),
+        "nrrs_traversal_stack_info": ([P, P, P], I32),
         "nrrs_set_bvh_builder": ([P, I32, P], I32),
         "nrrs_bvh8_info": ([P, P], I32),
         "nrrs_bvh8_export": ([P, P, I64, P, I64], I32),
@@ -364,6 +366,17 @@ def nrrs_set_bvh_precision(scene, bits):
 
 def nrrs_set_shade_fusion(scene, on):
     _check(_lib.nrrs_set_shade_fusion(scene, on))
+
+
+def nrrs_set_traversal_stack(scene, entries):
+    _check(_lib.nrrs_set_traversal_stack(scene, entries))
+
+
+def nrrs_traversal_stack_info(scene):
+    """(BVH2 height, stack entries per ray in use)."""
+    h, e = C.c_int32(), C.c_int32()
+    _check(_lib.nrrs_traversal_stack_info(scene, C.byref(h), C.byref(e)))
+    return h.value, e.value
 
 
 def nrrs_set_bvh_builder(scene, builder):
@@ -697,6 +710,12 @@ class Scene:
 
     def set_bvh_precision(self, bits):
         nrrs_set_bvh_precision(self.handle, bits)
+
+    def set_traversal_stack(self, entries):
+        nrrs_set_traversal_stack(self.handle, entries)
+
+    def traversal_stack_info(self):
+        return nrrs_traversal_stack_info(self.handle)
 
     def set_shade_fusion(self, on):
         nrrs_set_shade_fusion(self.handle, int(on))
