@@ -496,7 +496,7 @@ k_shade_rrsnet_tc(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int 
     const int has_ref = st->has_ref;
     const float eps_I = st->eps_I;
     uint32_t phase = 0;
-    unsigned int evals = 0, nonfinite = 0, unused = 0;
+    unsigned int evals = 0, nonfinite = 0, shade_bad = 0;  // shade_bad stays 0 at NET depths
     bool failed = false;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -508,7 +508,7 @@ k_shade_rrsnet_tc(SceneView sc, QueueView cur, WorkView w, RenderParams rp, int 
         if (i < n) {
             float4 dep, so, sd, sk, f[4];
             q = shade_slot<kFactorNet, NEE>(sc, cur, w, rp, depth, i, eps_I, has_ref, dep, so,
-                                            sd, sk, f, unused);
+                                            sd, sk, f, shade_bad);
             w.dep[i] = dep;
             if (NEE) {
                 w.sh_o[i] = so;

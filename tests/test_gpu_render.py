@@ -202,11 +202,13 @@ def test_determinism(nrrs):
     np.testing.assert_array_equal(sa["live"], sb["live"])
 
 
-@pytest.mark.parametrize("precision", [32, 16, 8])
-def test_nonfinite_network_falls_back_to_heuristic(nrrs, precision):
+@pytest.mark.parametrize("precision,fuse", [(32, 1), (16, 1), (16, 0), (17, 1), (17, 0),
+                                            (8, 1)])
+def test_nonfinite_network_falls_back_to_heuristic(nrrs, precision, fuse):
     """Non-finite network factors take the throughput heuristic's factor: with an
     infinite output layer the NET render is the HEUR_NORM render, bit for bit, and every
-    network evaluation is reported non-finite."""
+    network evaluation is reported non-finite (tensor-core precisions with the fused
+    shade + RRSNet kernel and with the separate kernels)."""
     s = I.box_scene(1)
     P = I.rrsnet_init_params(1)
     P[2560:] = np.inf
@@ -214,6 +216,7 @@ def test_nonfinite_network_falls_back_to_heuristic(nrrs, precision):
                             np.linspace(0.5, 1.5, 256, dtype=np.float32)[:, None])).cuda()
     sc = nrrs.Scene(s)
     sc.set_params(P)
+    sc.set_shade_fusion(fuse)
     kw = dict(d_pixel_ref=ref.data_ptr(), update_ref=0, precision=precision)
     net, st = sc.render(16, 16, 2, 5, nrrs.RRS_NET, **kw)
     heur, sth = sc.render(16, 16, 2, 5, nrrs.RRS_HEUR_NORM, **kw)
