@@ -345,7 +345,7 @@ nrrs_status ensure_workspace(nrrs_scene* sc, long long cap, long long npix, bool
     CK(dalloc(&w.acc_c, npix));
     CK(dalloc(&w.st, 1));
     CK(dalloc(&w.fc, 1));
-    w.n_flags = cap / 256 + 2;
+    w.n_flags = cap / split_block_threads() + 2;  // one look-back flag per split tile
     CK(dalloc(&w.flags, (size_t)w.n_flags));
     w.cap = cap;
     w.npix = npix;
