@@ -873,11 +873,16 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
         const long long i = t * kSplitThreads + threadIdx.x;
         uint32_t X = 0, base = 0, lpix = 0;
         float qu = 0.0f;
-        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = o4, t4 = o4;
+        // a parent with children: its hit and hit triangle's edges, fetched ahead so that
+        // their latency overlaps the scan and the look-back (the path state is read
+        // again for the children instead of being held across them)
+        float2 hh = make_float2(0.f, 0.f);
+        float4 te1 = make_float4(0.f, 0.f, 0.f, 0.f), te2 = te1;
         if (i < n) {
-            o4 = cur.o[i];
-            d4 = cur.d[i];
-            t4 = cur.t[i];
+            const float4 o4 = cur.o[i];
+            const float4 d4 = cur.d[i];
+            const float4 t4 = cur.t[i];
+            hh = w.hit[i];
             float Fi = F;
             lpix = fbits(o4.w);
             if (rp.jobs.job) {  // the job's factor; random numbers by job-local pixel
@@ -888,6 +893,11 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
             X = split_decide(Fi, w.q[i], key0, key1, lpix, fbits(t4.w), (uint32_t)depth,
                              fbits(d4.w), &qu, &base);
             if (rp.trace) trace_record(sc, w, rp, depth, i, o4, d4, t4, X);
+            if (X > 0) {
+                const int slot = __float_as_int(hh.y);
+                te1 = __ldg(&sc.tris[3 * slot + 1]);
+                te2 = __ldg(&sc.tris[3 * slot + 2]);
+            }
         }
         uint32_t tile_total;
         const uint32_t pre = block_exclusive_scan(X, sh, &tile_total);
@@ -971,10 +981,11 @@ k_split_fused(SceneView sc, QueueView cur, QueueView nxt, WorkView w, RenderPara
             rp.rec_X[i] = X;
         }
         if (X > 0 && s_ok) {
-            const float2 hh = w.hit[i];
-            const int slot = __float_as_int(hh.y);
-            int mi;
-            const V3 ng = tri_geom_normal(sc, slot, &mi);
+            const float4 o4 = cur.o[i];
+            const float4 d4 = cur.d[i];
+            const float4 t4 = cur.t[i];
+            const int mi = (int)fbits(te1.w);
+            const V3 ng = normalize3(cross3(xyz(te1), xyz(te2)));
             const nrrs_material m = sc.mats[mi];
             const V3 d = xyz(d4);
             const V3 ns = dot3(ng, d) < 0.0f ? ng : ng * -1.0f;
