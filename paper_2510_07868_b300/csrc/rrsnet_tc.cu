@@ -4,10 +4,13 @@
 // output.  Layers 1-3 are M=128 x N=32 MMAs (K = 16, then K = 32 as two K = 16 steps);
 // the 32 -> 1 output layer and the activation run in FP32 on the CUDA cores.
 //
-// Every operand v is split into two BF16 numbers, hi = bf16(v) and lo = bf16(v - hi), and
-// each product is taken as hi*hi + lo*hi + hi*lo (three MMAs into the same FP32
+// Precision 17 rounds every operand once to BF16 (one MMA per K step).  Precision 16
+// splits every operand v into two BF16 numbers, hi = bf16(v) and lo = bf16(v - hi), and
+// takes each product as hi*hi + lo*hi + hi*lo (three MMAs into the same FP32
 // accumulator); the dropped lo*lo term and the rounding of lo leave a relative error near
-// 2^-16 per product instead of the 2^-8 of one BF16 pass.
+// 2^-16 per product instead of the 2^-8 of one BF16 pass.  Precision 8 (further down)
+// uses E4M3 operands with power-of-two scales.  The layer building blocks are in tc.cuh,
+// shared with the fused shade + RRSNet kernel of wavefront.cu.
 //
 // Shared-memory operands use the canonical K-major layout without swizzle: 8-row x
 // 16-byte core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups
@@ -16,7 +19,7 @@
 // serves all three layers: layer 1 reads its first 16 columns (the 8-row groups stay
 // 512 bytes apart), and each layer's output overwrites it only after that layer's MMAs
 // have completed.  Every thread loads its own feature row from global memory one tile
-// ahead, so the CTA needs about 26 KB of shared memory and eight fit on an SM.
+// ahead, so the CTA needs about 26 KB of shared memory (split) and eight fit on an SM.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
