@@ -131,7 +131,9 @@ typedef struct nrrs_render_opts {
     int32_t precision;          /* RRSNet arithmetic: 32 (FP32 SIMT), 16 (split BF16
                                    operands), 17 (BF16 operands rounded once) or 8
                                    (E4M3 operands), tensor cores with FP32
-                                   accumulation                                     [32]   */
+                                   accumulation; at 16 and 17 the NET depths shade
+                                   and evaluate RRSNet in one kernel unless
+                                   nrrs_set_shade_fusion(scene, 0)              [32]   */
     uint64_t gate;              /* NET_MIX method per depth (NRRS_GATE_*)           [0]    */
     const float* d_pixel_ref;   /* device [H*W*3] reference I_px for HEUR, or NULL to use
                                    the scene's running mean of earlier frames       [NULL] */
